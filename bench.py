@@ -1,0 +1,373 @@
+#!/usr/bin/env python
+"""Benchmark of the divide-and-conquer CheFSI pass on GB300.
+
+Workload (default): 64-atom Si (2x2x2 conventional cells, seeded displacements sigma = 0.05 bohr),
+global 48^3 grid (h = 0.4275 bohr), 8 subdomains with 1-cell cores and 0.5-cell buffers (48^3
+points each, periodic because the buffer covers the cell), 160 states per subdomain (the state
+count that holds the subdomain's electrons, 1.2 x N_e/2 rounded up to 16), Chebyshev degree 20.
+V_eff is the seeded stand-in potential of `synth` (erf-Coulomb wells).  One step = one full
+CheFSI pass over all subdomains (filter, projection, eigensolve, rotation, interior weights)
+followed by the Fermi level, energies and the density on the global grid.
+
+metric: CheFSI throughput in Gpt.vec/s = sum_alpha m N_d N_s / (pass time), one point-vector
+being one Hamiltonian application (+ recurrence) to one grid value of one vector.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+METRIC = "CheFSI pass time & filter Gpt·vec/s, mixed vs FP64 at ΔE≤1e-5 Ha/atom"
+UNIT = "Gpt*vec/s"
+
+
+def parse_args():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=5)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    p.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
+    p.add_argument("--fp64-steps", type=int, default=1, help="FP64 passes timed for the mixed-vs-FP64 factor")
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--cpu-baseline-worker", action="store_true", help=argparse.SUPPRESS)
+    p.add_argument("--sample-states", type=int, default=32)
+    return p.parse_args()
+
+
+def bench_workload():
+    import synth
+    w = synth.workload(1)
+    return w, synth.veff_erf_wells(w)
+
+
+def point_vectors(w) -> float:
+    return float(sum(w.sub_points(a) * int(w.n_states[a]) for a in range(w.n_sub))) * w.degree
+
+
+# ---------------------------------------------------------------------------------------------
+# CPU baseline: the FP64 oracle as it stands, single thread, on a bounded sample
+# ---------------------------------------------------------------------------------------------
+def cpu_sample_pass(n_states: int, steps: int = 1, warmup: int = 0) -> dict:
+    """Oracle CheFSI pass (filter, projection, eigensolve, rotation) on subdomain 0 of the
+    workload restricted to the first n_states start vectors; returns the rate in Gpt.vec/s."""
+    import synth
+    from oracle import chefsi, dc, pseudo
+    w, V = bench_workload()
+    subs = dc.partition(w)
+    H = dc.subdomain_operator(w, subs[0], V, pseudo.projector_norms(w))
+    psi = synth.psi0_block(w.psi_seed, subs[0].N, int(w.n_states[0]))[:n_states]
+    b = chefsi.lanczos_upper_bound(H, synth.lanczos_start(H.N))
+    lam = chefsi.ritz_values(H, psi)
+    times = []
+    for it in range(warmup + steps):
+        t0 = time.perf_counter()
+        lam, psi = chefsi.chefsi_pass(H, psi, w.degree, a=float(lam[-1]), b=b, a0=float(lam[0]))
+        dc.interior_weights(psi, subs[0])
+        t = time.perf_counter() - t0
+        if it >= warmup:
+            times.append(t)
+    t = float(np.mean(times))
+    units = float(H.N) * n_states * w.degree
+    return {"value": units / t / 1e9, "seconds_per_pass": t, "units": units}
+
+
+def run_cpu_baseline(n_states: int) -> dict:
+    env = dict(os.environ)
+    for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS", "BLIS_NUM_THREADS"):
+        env[k] = "1"
+    r = subprocess.run([sys.executable, os.path.abspath(__file__), "--cpu-baseline-worker",
+                        "--sample-states", str(n_states)], capture_output=True, text=True, env=env, timeout=900)
+    if r.returncode != 0:
+        return {"value": None, "unit": UNIT, "cores": 1, "kind": "oracle", "error": r.stderr[-400:]}
+    out = json.loads(r.stdout.strip().splitlines()[-1])
+    return {"value": out["value"], "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"subdomain 0 of 8, first {n_states} of 160 vectors, one full pass (degree-20 filter, "
+                      f"projection, eigensolve, rotation), FP64 numpy, 1 thread; {out['seconds_per_pass']:.1f} s"}
+
+
+# ---------------------------------------------------------------------------------------------
+# clocks during the timed region
+# ---------------------------------------------------------------------------------------------
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_{os.getpid()}.csv")
+
+    def start(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"], stdout=self.f,
+                                         stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        self.proc.wait(timeout=10)
+        self.f.close()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ---------------------------------------------------------------------------------------------
+def dist_setup():
+    import torch
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    return ws, rank, local
+
+
+def barrier(ws):
+    if ws > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def allreduce_max(x: float, ws: int) -> float:
+    if ws == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], device="cuda", dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def stencil_bytes_per_launch(w, elem: int) -> float:
+    """Algorithmic HBM bytes of one filter-step stencil launch over all subdomains: read Y_k and
+    Y_{k-1}, write Y_{k+1} (3 x elem per point-vector) plus V once per subdomain point."""
+    tot = 0.0
+    for a in range(w.n_sub):
+        nd = w.sub_points(a)
+        tot += 3.0 * elem * nd * int(w.n_states[a]) + elem * nd
+    return tot
+
+
+def run_ours(args):
+    import torch
+    from paper_2609_13115_gb300 import xls
+    ws, rank, local = dist_setup()
+    xls.load()
+    w, V = bench_workload()
+    stream = torch.cuda.current_stream()
+    prec = xls.XLS_MIXED_BF16 if args.precision == "mixed" else xls.XLS_FP64
+    ng = int(np.prod(w.n))
+    rho_dev = torch.zeros(ng, dtype=torch.float64, device="cuda")
+
+    def make(p):
+        g = xls.Grid(w, p, stream=stream.cuda_stream)
+        g.set_hamiltonian(V)
+        xls.xls_orbitals_random(g.h, w.psi_seed)
+        return g
+
+    g = make(prec)
+
+    def step(gh):
+        xls.xls_chefsi_batch(gh, w.degree, 1)
+        return xls.xls_density(gh, w.n_electrons, w.kT, rho_dev)
+
+    for _ in range(args.warmup):
+        step(g.h)
+    xls.xls_set_profiling(g.h, 1)
+    kms = np.zeros(8)
+    kcnt = np.zeros(8)
+    sampler = ClockSampler(local)
+    sampler.start()
+    barrier(ws)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        step(g.h)
+        ms, cnt = xls.xls_get_kernel_times(g.h)
+        kms += ms
+        kcnt += cnt
+    e1.record(stream)
+    torch.cuda.synchronize()
+    barrier(ws)
+    clocks = sampler.stop()
+    ms_step = e0.elapsed_time(e1) / args.steps
+    ms_step = allreduce_max(ms_step, ws)
+    _, launches_pass = xls.xls_get_timings(g.h)
+    stage_ms, _ = xls.xls_get_timings(g.h)
+    mu, eb_mixed, _ = xls.xls_density(g.h, w.n_electrons, w.kT)
+    xls.xls_set_profiling(g.h, 0)
+
+    # end to end through the C ABI with host buffers: H2D of every start block from pinned host
+    # memory, the pass, Fermi level and the density read back to the host
+    host_in = [torch.empty((int(w.n_states[a]), w.sub_points(a)), dtype=torch.float64).pin_memory()
+               for a in range(w.n_sub)]
+    for a in range(w.n_sub):
+        xls.xls_orbitals_get(g.h, a, host_in[a].numpy())
+    rho_host = torch.empty(ng, dtype=torch.float64).pin_memory()
+    h2d = sum(t.numel() * 8 for t in host_in)
+    d2h = ng * 8 + 3 * 8
+    torch.cuda.synchronize()
+    e2e_times = []
+    for it in range(max(2, args.steps // 2) + 1):
+        t0 = time.perf_counter()
+        for a in range(w.n_sub):
+            xls.xls_orbitals_set(g.h, a, host_in[a].numpy())
+        xls.xls_chefsi_batch(g.h, w.degree, 1)
+        xls.xls_density(g.h, w.n_electrons, w.kT, rho_host.numpy())
+        if it > 0:
+            e2e_times.append(time.perf_counter() - t0)
+    e2e_s = allreduce_max(float(np.mean(e2e_times)), ws)
+    g.close()
+
+    units = point_vectors(w)
+    value = units * ws / (ms_step / 1e3) / 1e9
+    # roofline of the dominant kernel (the stencil launches of the filter)
+    elem = 4 if prec == xls.XLS_MIXED_BF16 else 8
+    stencil_avg_ms = kms[0] / max(kcnt[0], 1)
+    bytes_launch = stencil_bytes_per_launch(w, elem)
+    peaks = {}
+    pk_path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(pk_path):
+        peaks = json.load(open(pk_path))
+    peak = peaks.get("hbm_gbs", 6800.0)
+    achieved = bytes_launch / (stencil_avg_ms / 1e3) / 1e9
+    roofline = {"bound": "hbm", "kernel": "k_stencil", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
+                "frac": round(achieved / peak, 4), "traffic": None,
+                "peak_source": "measured" if "hbm_gbs" in peaks else "fallback",
+                "bytes_per_launch": bytes_launch, "avg_launch_ms": round(stencil_avg_ms, 4)}
+    kernel_share = {n: round(float(kms[i] / max(kms.sum(), 1e-9)), 4)
+                    for i, n in enumerate(["stencil", "nl_project", "nl_back", "gram", "eig", "rotate", "other"])}
+
+    # FP64 form of the same pass for the mixed-vs-FP64 factor and Delta E
+    fp64 = None
+    if prec == xls.XLS_MIXED_BF16 and args.fp64_steps > 0:
+        g64 = make(xls.XLS_FP64)
+        gm = make(xls.XLS_MIXED_BF16)
+        n_cmp = args.warmup + 1
+        for _ in range(n_cmp - 1):
+            step(g64.h)
+            step(gm.h)
+        torch.cuda.synchronize()
+        f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        f0.record(stream)
+        for _ in range(args.fp64_steps):
+            step(g64.h)
+        f1.record(stream)
+        torch.cuda.synchronize()
+        ms64 = f0.elapsed_time(f1) / args.fp64_steps
+        step(gm.h)
+        for _ in range(args.fp64_steps - 1):
+            step(gm.h)
+        _, eb64, _ = xls.xls_density(g64.h, w.n_electrons, w.kT)
+        _, ebm, _ = xls.xls_density(gm.h, w.n_electrons, w.kT)
+        g64.close()
+        gm.close()
+        fp64 = {"ms_per_step": round(ms64, 3), "mixed_speedup": round(ms64 / ms_step, 2),
+                "delta_e_band_per_atom": abs(ebm - eb64) / len(w.pos), "passes_compared": n_cmp}
+
+    cpu = None
+    if rank == 0 and not args.no_cpu_baseline:
+        cpu = run_cpu_baseline(args.sample_states)
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": round(value, 3), "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": round(ms_step, 3), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32+bf16x3 (f64 eig/fermi)" if prec == xls.XLS_MIXED_BF16 else "f64",
+            "data": "synthetic",
+            "config": {"workload": w.name, "subdomains": w.n_sub, "points_per_subdomain": w.sub_points(0),
+                       "states": int(w.n_states[0]), "degree": w.degree,
+                       "l2": "inputs larger than L2 (each orbital block 566 MB)",
+                       "parallelism": f"replicas x{ws}" if ws > 1 else "single GPU"},
+            "stage_ms": {k: round(float(v), 3) for k, v in zip(["filter", "projection", "eig", "rotation"], stage_ms)},
+            "kernel_share": kernel_share,
+            "roofline": roofline,
+            "cpu_baseline": cpu,
+            "e2e": {"value": round(units * ws / e2e_s / 1e9, 3), "unit": UNIT, "h2d_bytes_per_step": h2d,
+                    "d2h_bytes_per_step": d2h},
+            "gpu_launches": int(launches_pass + 2) * args.steps,
+            "clocks": clocks,
+            "fp64": fp64,
+            "mu": mu, "e_band_per_atom": eb_mixed / len(w.pos),
+        }
+        print(json.dumps(line))
+    if ws > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    res = []
+    for it in range(args.warmup + args.steps):
+        r = cpu_sample_pass(args.sample_states)
+        if it >= args.warmup:
+            res.append(r)
+    value = float(np.mean([r["value"] for r in res]))
+    sec = float(np.mean([r["seconds_per_pass"] for r in res]))
+    w, _ = bench_workload()
+    cores = 1 if os.environ.get("OMP_NUM_THREADS") == "1" else (os.cpu_count() or 1)
+    line = {"impl": "reference", "metric": METRIC, "value": round(value, 6), "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(sec * 1e3, 1), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": w.name, "subdomains": w.n_sub, "points_per_subdomain": w.sub_points(0),
+                       "states": int(w.n_states[0]), "degree": w.degree},
+            "cpu_baseline": {"kind": "oracle", "cores": cores, "value": round(value, 6), "unit": UNIT,
+                             "sample": f"subdomain 0, first {args.sample_states} of 160 vectors, one full pass"},
+            "e2e": {"value": round(value, 6), "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+
+
+def main():
+    args = parse_args()
+    if args.cpu_baseline_worker:
+        print(json.dumps(cpu_sample_pass(args.sample_states)))
+        return
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

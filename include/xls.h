@@ -1,0 +1,166 @@
+/*
+ * xls.h - C ABI of libxls: the per-subdomain CheFSI pass of divide-and-conquer Kohn-Sham DFT
+ * (arXiv 2609.13115, "XLSDFT"), on one GB300 GPU.
+ *
+ * The library owns every device buffer it uses (allocated at xls_grid_create, freed at
+ * xls_grid_destroy).  Pointers passed in are only read (or written, for outputs) during the
+ * call; "on_device" flags say whether a pointer is device memory of the current CUDA device
+ * (else host memory).  All work is queued on the stream given at creation; calls that return
+ * host results synchronise that stream.  No call throws or exits: every call returns an
+ * xls_status, and xls_last_error() describes the last failure of the calling thread (with the
+ * failing subdomain where there is one).  Errors detected by kernels (non-SPD Gram matrix,
+ * non-finite values, a Fermi level that cannot be bracketed) are reported by the next call
+ * that synchronises.
+ *
+ * Grid conventions.  A global periodic orthorhombic cell of edges L[3] (bohr) carries n[3]
+ * grid points, spacing h = L/n, point (i,j,k) at (i h_x, j h_y, k h_z), flat index
+ * i + n_x (j + n_y k) (x fastest).  Subdomain alpha (Sec. 5.A.2, the partition equation) is
+ * a core box of core_n points starting at global index core_lo, extended by buf points on
+ * each side; along an axis where core_n + 2 buf >= n the subdomain is the whole period and
+ * periodic, elsewhere the Hamiltonian is Dirichlet-zero outside it.  A block of vectors of a
+ * subdomain is stored vector-major: vector v occupies N_d consecutive values (x fastest).
+ */
+#ifndef XLS_H
+#define XLS_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct xls_grid_s* xls_grid;
+
+typedef enum {
+  XLS_OK = 0,
+  XLS_EINVAL = 1,     /* bad argument (sizes, pointers, state) */
+  XLS_ENOMEM = 2,     /* device allocation failed or exceeds the HBM budget */
+  XLS_ECUDA = 3,      /* a CUDA runtime/driver call failed */
+  XLS_ENOTSPD = 4,    /* Gram matrix M_s not positive definite (Cholesky pivot <= 0) */
+  XLS_ENOCONV = 5,    /* Fermi level not bracketed: N_e outside the capacity of the states */
+  XLS_ETIMEOUT = 6,   /* a bounded device wait gave up */
+  XLS_ENONFINITE = 7  /* NaN/Inf detected in a result */
+} xls_status;
+
+typedef enum {
+  XLS_FP64 = 0,        /* every step in FP64 */
+  XLS_MIXED_BF16 = 1   /* FP32 filter, split-BF16 tensor-core Gram/rotation with FP32 accumulation,
+                          FP64 Cholesky / eigensolve / Fermi level / energies */
+} xls_precision;
+
+typedef struct {
+  double L[3];        /* cell edges, bohr */
+  int n[3];           /* global grid points per axis */
+} xls_cell;
+
+typedef struct {
+  int n_sub;               /* number of subdomains (>= 1) */
+  const int* core_lo;      /* [3*n_sub] global index of the first core point per axis */
+  const int* core_n;       /* [3*n_sub] core points per axis (cores must tile the grid) */
+  const int* buf;          /* [3*n_sub] buffer points on each side per axis */
+  const int* n_states;     /* [n_sub] vectors per subdomain, N_s^alpha (1..1024) */
+} xls_dc;
+
+typedef struct {
+  double Zv;       /* valence charge (enters only through the electron count given by the caller) */
+  double rc_loc;   /* local-potential radius (unused by the pass; V_eff is an input) */
+  double w_proj;   /* projector Gaussian width w: chi_s = exp(-r^2/2w^2), chi_p = x_a chi_s */
+  double r_cut;    /* projectors vanish for r >= r_cut (must be < half of every cell edge) */
+  double E_s;      /* Kleinman-Bylander energy of the s projector, Ha */
+  double E_p;      /* Kleinman-Bylander energy of each p projector, Ha */
+} xls_species;
+
+/* Create a grid handle: validates the partition, allocates the blocks of every subdomain in
+ * the requested precision and the subspace workspaces.  hbm_budget_bytes (0 = no limit) caps
+ * the device memory the handle may allocate (XLS_ENOMEM beyond it).  cuda_stream may be NULL
+ * (legacy default stream).  Sec. 5.A.2 (partition), Sec. 5.B (data kept resident in HBM). */
+xls_status xls_grid_create(const xls_cell* cell, const xls_dc* dc, int precision,
+                           size_t hbm_budget_bytes, void* cuda_stream, xls_grid* out);
+
+xls_status xls_grid_destroy(xls_grid g);
+
+/* Restrict V_eff (global grid, n_x*n_y*n_z doubles) to every subdomain and build the
+ * nonlocal projector tables of every atom whose r_cut sphere meets it (minimum periodic
+ * image; each chi normalised on the global grid, sum chi^2 dV = 1), then compute each
+ * subdomain's spectrum upper bound b by a 10-step Lanczos run from a fixed SplitMix64 start
+ * vector (seed 0x1A4C705, stream position = subdomain point index).  pos: [3*n_atoms] bohr;
+ * species: [n_atoms] indices into sp[0..n_species).  Sec. 5.A.5 "Restriction of effective
+ * potentials", Sec. 5.B.2 (projectors grouped by atom). */
+xls_status xls_hamiltonian_set(xls_grid g, const double* veff, int veff_on_device, int n_atoms,
+                               const double* pos, const int* species, int n_species,
+                               const xls_species* sp);
+
+/* Load the start block of subdomain `sub` (N_s x N_d doubles, vector-major) into the grid's
+ * orbital storage (rounded to FP32 on the mixed path). */
+xls_status xls_orbitals_set(xls_grid g, int sub, const double* psi, int on_device);
+
+/* Fill every subdomain's start block with U[-0.5, 0.5) from SplitMix64 (Steele et al. 2014):
+ * value k of the concatenated blocks (subdomains in order, each vector-major) is the top 53
+ * bits of output k of the stream of `seed`, times 2^-53, minus 0.5. */
+xls_status xls_orbitals_random(xls_grid g, uint64_t seed);
+
+/* Copy subdomain `sub`'s current orbital block (N_s x N_d, vector-major) out as doubles. */
+xls_status xls_orbitals_get(xls_grid g, int sub, double* psi_out, int on_device);
+
+/* n_passes CheFSI iterations on every subdomain (Sec. 5.A.3 steps (1)-(4)):
+ *   (1) scaled Chebyshev filter of degree `degree` on [a, b] (three-term recurrence,
+ *       Zhou et al. 2006): Psi_f = C_m((H-c)/e) Psi / C_m((a0-c)/e), e = (b-a)/2, c = (b+a)/2;
+ *   (2) M_s = Psi_f^T Psi_f, H_s = Psi_f^T H Psi_f;
+ *   (3) H_s y = lambda M_s y by Cholesky reduction and a symmetric eigensolve (FP64);
+ *   (4) Psi = Psi_f Y; then the interior weights c_n = sum over core points of psi_n^2.
+ * bounds: NULL, or [3*n_sub] (b, a, a0) per subdomain for the first pass; with NULL the
+ * first pass of a fresh start block takes b from xls_hamiltonian_set and (a, a0) = the
+ * (largest, smallest) Ritz values of the unfiltered block, and later passes take (a, a0)
+ * from the previous pass's Ritz values.  Every subdomain runs in the same launches. */
+xls_status xls_chefsi_batch(xls_grid g, int degree, int n_passes, const double* bounds);
+
+/* Stage-wise entry points with the same arithmetic as one pass of xls_chefsi_batch, for
+ * checking each step on its own.  stage 1: filter only (the orbital block becomes Psi_f);
+ * stage 2: projection of the current block into M_s, H_s; stage 3: eigensolve of the current
+ * M_s, H_s (lambda, Y); stage 4: rotation of the current block by Y and interior weights. */
+xls_status xls_chefsi_stage(xls_grid g, int stage, int degree, const double* bounds);
+
+/* Apply H^alpha to k <= N_s vectors x (k x N_d, vector-major) of subdomain `sub`, giving y.
+ * Uses (and overwrites) the subdomain's first k work vectors; in the grid's precision. */
+xls_status xls_hamiltonian_apply(xls_grid g, int sub, int k, const double* x, double* y, int on_device);
+
+/* Fermi level, density and energies (Sec. 5.A.4-5): mu solves
+ * 2 sum_alpha sum_n g((lambda_n - mu)/kT) c_n = n_electrons by FP64 bisection on
+ * [min lambda - 1, max lambda + 1] to a bracket below 1e-14 Ha (XLS_ENOCONV if not bracketed);
+ * rho (optional, global grid) = (2/dV) sum_n g_n psi_n^2 on each core point from its own
+ * subdomain; E_band = 2 sum sum g c lambda; E_entropy = -2 kT sum sum c s(g). */
+xls_status xls_density(xls_grid g, double n_electrons, double kT, double* mu_out, double* rho_out,
+                       int rho_on_device, double* e_band_out, double* e_entropy_out);
+
+/* Read back lambda (ascending) and c of subdomain `sub` (N_s doubles each; either may be NULL). */
+xls_status xls_get_eigs(xls_grid g, int sub, double* lambda_out, double* c_out);
+
+/* Read back M_s and H_s (N_s x N_s, row-major) of subdomain `sub` from the last projection. */
+xls_status xls_get_subspace(xls_grid g, int sub, double* Ms_out, double* Hs_out);
+
+/* Read back the (b, a, a0) filter bounds the next pass will use, [3*n_sub]. */
+xls_status xls_get_bounds(xls_grid g, double* bounds_out);
+
+/* Per-stage device time (ms) of the last xls_chefsi_batch pass: [filter, projection, eigensolve,
+ * rotation+weights] and the number of kernel launches of that pass. */
+xls_status xls_get_timings(xls_grid g, double* ms4_out, int* launches_out);
+
+/* Turn on (1) or off (0) per-kernel timing: CUDA events around every launch of each pass on
+ * the grid's stream (a few microseconds of overhead per launch).  Library-specific: the
+ * paper has no counterpart; it feeds roofline measurements. */
+xls_status xls_set_profiling(xls_grid g, int on);
+
+/* Device time (ms) and launch count per kernel class in the last profiled pass: [0] stencil,
+ * [1] nonlocal projection, [2] nonlocal back-projection, [3] Gram/projection GEMM,
+ * [4] eigensolve, [5] rotation GEMM, [6] other, [7] unused.  Either pointer may be NULL. */
+xls_status xls_get_kernel_times(xls_grid g, double* ms8_out, int* count8_out);
+
+/* Message of the calling thread's last failure ("" if none). */
+const char* xls_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* XLS_H */

@@ -1,0 +1,535 @@
+// Subspace contractions on SIMT cores (FP64 path), interior weights, Fermi level, density,
+// and the small set-up kernels (restriction, projector norms, Lanczos bound, random start).
+#include "xls_internal.h"
+
+namespace xls {
+
+__device__ __forceinline__ int wrapd(int i, int n) {
+  i %= n;
+  return i < 0 ? i + n : i;
+}
+
+template <typename T>
+__device__ __forceinline__ T block_sum(T v, T* red) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31, nw = (blockDim.x + 31) >> 5;
+  __syncthreads();
+  if (l == 0) red[w] = v;
+  __syncthreads();
+  T s = (T)0;
+  for (int i = 0; i < nw; ++i) s += red[i];
+  __syncthreads();
+  return s;
+}
+
+// ---- projection: M_s = F F^T, H_s = F HF^T over the grid (Sec. 5.A.3 step (2)) -------------
+// Blocks: (subdomain, 32x32 output tile, K-chunk of the grid); FP64 atomics combine K-chunks.
+constexpr int kGT = 32, kGK = 32, kGChunk = 4096;
+
+template <typename T>
+__global__ void __launch_bounds__(256)
+k_gram(const SubDev* __restrict__ subs, const T* __restrict__ F, const T* __restrict__ HF, double* Ms, double* Hs) {
+  const SubDev& S = subs[blockIdx.z];
+  const int ns = S.ns;
+  const int nt = (ns + kGT - 1) / kGT;
+  const int ti = blockIdx.y % nt, tj = blockIdx.y / nt;
+  if (tj >= nt) return;
+  const long long g0 = (long long)blockIdx.x * kGChunk;
+  if (g0 >= S.nd) return;
+  const long long g1 = min(S.nd, g0 + kGChunk);
+  __shared__ T A[kGK][kGT + 1], B[kGK][kGT + 1], C[kGK][kGT + 1];
+  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;  // 8 x 32
+  const T* f = F + S.off_blk;
+  const T* hf = HF + S.off_blk;
+  T m[4] = {0, 0, 0, 0}, h[4] = {0, 0, 0, 0};
+  for (long long k0 = g0; k0 < g1; k0 += kGK) {
+    // load rows (i0 + r) and (j0 + r), points k0 + tx
+#pragma unroll
+    for (int rr = 0; rr < 4; ++rr) {
+      const int r = ty * 4 + rr;
+      const long long g = k0 + tx;
+      const int i = ti * kGT + r, j = tj * kGT + r;
+      const bool okg = g < g1;
+      A[tx][r] = (okg && i < ns) ? f[(long long)i * S.nd + g] : (T)0;
+      B[tx][r] = (okg && j < ns) ? f[(long long)j * S.nd + g] : (T)0;
+      C[tx][r] = (okg && j < ns) ? hf[(long long)j * S.nd + g] : (T)0;
+    }
+    __syncthreads();
+#pragma unroll 8
+    for (int k = 0; k < kGK; ++k) {
+      const T b = B[k][tx], c = C[k][tx];
+#pragma unroll
+      for (int rr = 0; rr < 4; ++rr) {
+        const T a = A[k][ty * 4 + rr];
+        m[rr] += a * b;
+        h[rr] += a * c;
+      }
+    }
+    __syncthreads();
+  }
+  const int j = tj * kGT + tx;
+  if (j >= ns) return;
+#pragma unroll
+  for (int rr = 0; rr < 4; ++rr) {
+    const int i = ti * kGT + ty * 4 + rr;
+    if (i < ns) {
+      atomicAdd(Ms + S.off_ss + (long long)i * ns + j, (double)m[rr]);
+      atomicAdd(Hs + S.off_ss + (long long)i * ns + j, (double)h[rr]);
+    }
+  }
+}
+
+template <typename T>
+void launch_gram(const SubDev* d_subs, int n_sub, int max_ns, long long max_nd, const T* F, const T* HF, double* Ms,
+                 double* Hs, cudaStream_t st) {
+  const int nt = (max_ns + kGT - 1) / kGT;
+  dim3 grid((unsigned)((max_nd + kGChunk - 1) / kGChunk), nt * nt, n_sub);
+  k_gram<T><<<grid, 256, 0, st>>>(d_subs, F, HF, Ms, Hs);
+}
+
+// ---- rotation: Out[n][g] = sum_k Y[k][n] F[k][g] (Sec. 5.A.3 step (4)) ----------------------
+constexpr int kRG = 64, kRN = 64, kRK = 16;
+
+template <typename T>
+__global__ void __launch_bounds__(256)
+k_rotate(const SubDev* __restrict__ subs, const T* __restrict__ F, const double* __restrict__ Y, T* Out) {
+  const SubDev& S = subs[blockIdx.z];
+  const int ns = S.ns;
+  const long long g0 = (long long)blockIdx.x * kRG;
+  const int n0 = blockIdx.y * kRN;
+  if (g0 >= S.nd || n0 >= ns) return;
+  __shared__ T Fs[kRK][kRG];
+  __shared__ T Ys[kRK][kRN];
+  const int tg = threadIdx.x & 15, tn = threadIdx.x >> 4;  // 16 x 16
+  const T* f = F + S.off_blk;
+  const double* y = Y + S.off_ss;
+  T acc[4][4];
+#pragma unroll
+  for (int a = 0; a < 4; ++a)
+#pragma unroll
+    for (int b = 0; b < 4; ++b) acc[a][b] = (T)0;
+  for (int k0 = 0; k0 < ns; k0 += kRK) {
+    for (int s = threadIdx.x; s < kRK * kRG; s += 256) {
+      const int kk = s / kRG, gg = s % kRG;
+      const int k = k0 + kk;
+      const long long g = g0 + gg;
+      Fs[kk][gg] = (k < ns && g < S.nd) ? f[(long long)k * S.nd + g] : (T)0;
+    }
+    for (int s = threadIdx.x; s < kRK * kRN; s += 256) {
+      const int kk = s / kRN, nn = s % kRN;
+      const int k = k0 + kk, n = n0 + nn;
+      Ys[kk][nn] = (k < ns && n < ns) ? (T)y[(long long)k * ns + n] : (T)0;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int kk = 0; kk < kRK; ++kk) {
+      T fv[4], yv[4];
+#pragma unroll
+      for (int a = 0; a < 4; ++a) fv[a] = Fs[kk][tg + 16 * a];
+#pragma unroll
+      for (int b = 0; b < 4; ++b) yv[b] = Ys[kk][tn * 4 + b];
+#pragma unroll
+      for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int b = 0; b < 4; ++b) acc[a][b] += fv[a] * yv[b];
+    }
+    __syncthreads();
+  }
+  T* o = Out + S.off_blk;
+#pragma unroll
+  for (int b = 0; b < 4; ++b) {
+    const int n = n0 + tn * 4 + b;
+    if (n >= ns) continue;
+#pragma unroll
+    for (int a = 0; a < 4; ++a) {
+      const long long g = g0 + tg + 16 * a;
+      if (g < S.nd) o[(long long)n * S.nd + g] = acc[a][b];
+    }
+  }
+}
+
+template <typename T>
+void launch_rotate(const SubDev* d_subs, int n_sub, int max_ns, long long max_nd, const T* F, const double* Y, T* Out,
+                   cudaStream_t st) {
+  dim3 grid((unsigned)((max_nd + kRG - 1) / kRG), (max_ns + kRN - 1) / kRN, n_sub);
+  k_rotate<T><<<grid, 256, 0, st>>>(d_subs, F, Y, Out);
+}
+
+// ---- interior weights c_n = sum over core points of psi_n^2 (Sec. 5.A.4) ------------------
+template <typename T>
+__global__ void __launch_bounds__(256) k_core_weights(const SubDev* __restrict__ subs, const T* __restrict__ Psi, double* c) {
+  const SubDev& S = subs[blockIdx.y];
+  const int v = blockIdx.x;
+  if (v >= S.ns) return;
+  const T* p = Psi + S.off_blk + (long long)v * S.nd;
+  const int cx = S.core_n[0], cy = S.core_n[1], cz = S.core_n[2];
+  const long long ncore = (long long)cx * cy * cz;
+  double acc = 0.0;
+  for (long long q = threadIdx.x; q < ncore; q += blockDim.x) {
+    const int i = (int)(q % cx), j = (int)((q / cx) % cy), k = (int)(q / ((long long)cx * cy));
+    const long long g = ((long long)(S.core_lo[2] + k) * S.n[1] + (S.core_lo[1] + j)) * S.n[0] + (S.core_lo[0] + i);
+    const double x = (double)p[g];
+    acc += x * x;
+  }
+  __shared__ double red[32];
+  acc = block_sum(acc, red);
+  if (threadIdx.x == 0) c[S.off_state + v] = acc;
+}
+
+template <typename T>
+void launch_core_weights(const SubDev* d_subs, int n_sub, int max_ns, const T* Psi, double* c, cudaStream_t st) {
+  dim3 grid(max_ns, n_sub);
+  k_core_weights<T><<<grid, 256, 0, st>>>(d_subs, Psi, c);
+}
+
+// ---- density on the core points: rho = (2/dV) sum_n occ_n psi_n^2 (Eq. density) ----------
+template <typename T>
+__global__ void __launch_bounds__(256)
+k_density(const SubDev* __restrict__ subs, const T* __restrict__ Psi, const double* __restrict__ occ, int gnx, int gny,
+          double* rho) {
+  const SubDev& S = subs[blockIdx.y];
+  const int cx = S.core_n[0], cy = S.core_n[1], cz = S.core_n[2];
+  const long long ncore = (long long)cx * cy * cz;
+  const long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (q >= ncore) return;
+  const int i = (int)(q % cx), j = (int)((q / cx) % cy), k = (int)(q / ((long long)cx * cy));
+  const long long g = ((long long)(S.core_lo[2] + k) * S.n[1] + (S.core_lo[1] + j)) * S.n[0] + (S.core_lo[0] + i);
+  const T* p = Psi + S.off_blk + g;
+  const double* o = occ + S.off_state;
+  double acc = 0.0;
+  for (int v = 0; v < S.ns; ++v) {
+    const double x = (double)p[(long long)v * S.nd];
+    acc += o[v] * x * x;
+  }
+  const long long G = ((long long)(S.core_glo[2] + k) * gny + (S.core_glo[1] + j)) * gnx + (S.core_glo[0] + i);
+  rho[G] = 2.0 * acc / S.dV;
+}
+
+template <typename T>
+void launch_density_occ(const SubDev* d_subs, int n_sub, long long max_core, const T* Psi, const double* occ,
+                        const int gn[3], double* rho, cudaStream_t st) {
+  dim3 grid((unsigned)((max_core + 255) / 256), n_sub);
+  k_density<T><<<grid, 256, 0, st>>>(d_subs, Psi, occ, gn[0], gn[1], rho);
+}
+
+// ---- Fermi level by FP64 bisection, occupations and energies (Sec. 5.A.4-5) ----------------
+__device__ __forceinline__ double fermi_fn(double x) {
+  if (x > 0) {
+    const double e = exp(-x);
+    return e / (1.0 + e);
+  }
+  return 1.0 / (1.0 + exp(x));
+}
+
+// out: [0] mu, [1] E_band, [2] E_entropy, [3] N_e(mu); occ[n] = g_n.
+__global__ void __launch_bounds__(1024)
+k_fermi(const double* __restrict__ lam, const double* __restrict__ c, int n, double ne, double kT, double* out,
+        double* occ, int* status) {
+  __shared__ double red[32];
+  __shared__ double s_lo, s_hi;
+  double lmin = 1e300, lmax = -1e300;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) {
+    lmin = fmin(lmin, lam[i]);
+    lmax = fmax(lmax, lam[i]);
+  }
+  // block min/max via shuffles + shared
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    lmin = fmin(lmin, __shfl_xor_sync(0xffffffffu, lmin, o));
+    lmax = fmax(lmax, __shfl_xor_sync(0xffffffffu, lmax, o));
+  }
+  __shared__ double smin[32], smax[32];
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31, nw = blockDim.x >> 5;
+  if (l == 0) { smin[w] = lmin; smax[w] = lmax; }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double a = 1e300, b = -1e300;
+    for (int i = 0; i < nw; ++i) { a = fmin(a, smin[i]); b = fmax(b, smax[i]); }
+    s_lo = a - 1.0;
+    s_hi = b + 1.0;
+  }
+  __syncthreads();
+  auto count = [&](double mu) -> double {
+    double acc = 0.0;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) acc += fermi_fn((lam[i] - mu) / kT) * c[i];
+    return 2.0 * block_sum(acc, red);
+  };
+  double lo = s_lo, hi = s_hi;
+  const double nlo = count(lo), nhi = count(hi);
+  if (!(nlo <= ne && ne <= nhi)) {
+    if (threadIdx.x == 0) { *status = XLS_ENOCONV; out[0] = out[1] = out[2] = out[3] = 0.0; }
+    return;
+  }
+  for (int it = 0; it < 200; ++it) {
+    if (hi - lo <= 1e-14) break;
+    const double mid = 0.5 * (lo + hi);
+    if (mid == lo || mid == hi) break;
+    const double nm = count(mid);
+    if (nm < ne) lo = mid; else hi = mid;
+  }
+  const double mu = 0.5 * (lo + hi);
+  double eb = 0.0, es = 0.0, nn = 0.0;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) {
+    const double g = fermi_fn((lam[i] - mu) / kT);
+    occ[i] = g;
+    eb += g * c[i] * lam[i];
+    const double q = 1.0 - g;
+    const double s = (g > 0 ? g * log(g) : 0.0) + (q > 0 ? q * log(q) : 0.0);
+    es += c[i] * s;
+    nn += g * c[i];
+  }
+  eb = block_sum(eb, red);
+  es = block_sum(es, red);
+  nn = block_sum(nn, red);
+  if (threadIdx.x == 0) {
+    out[0] = mu;
+    out[1] = 2.0 * eb;
+    out[2] = -2.0 * kT * es;
+    out[3] = 2.0 * nn;
+  }
+}
+
+void launch_fermi_occ(const double* lam, const double* c, int n_tot, double n_e, double kT, double* out4, double* occ,
+                      int* status, cudaStream_t st) {
+  k_fermi<<<1, 1024, 0, st>>>(lam, c, n_tot, n_e, kT, out4, occ, status);
+}
+
+// ---- filter coefficients of the scaled recurrence (Zhou et al. 2006) ----------------------
+// bounds[3a..3a+2] = (b, a, a0); coef[a][1..m]; coef[a][kMaxDegree-1] = (1, 0, 0) = plain H.
+__global__ void k_filter_coef(int n_sub, const double* bounds, int m, StepCoef* coef) {
+  const int a = blockIdx.x * blockDim.x + threadIdx.x;
+  if (a >= n_sub) return;
+  const double b = bounds[3 * a], lo = bounds[3 * a + 1], a0 = bounds[3 * a + 2];
+  const double e = (b - lo) / 2.0, c = (b + lo) / 2.0;
+  const double sigma1 = e / (a0 - c);
+  double sigma = sigma1;
+  StepCoef* cf = coef + (long long)a * kMaxDegree;
+  cf[0] = StepCoef{0.0, 0.0, 0.0, 0.0};
+  cf[1] = StepCoef{sigma1 / e, c, 0.0, 0.0};
+  for (int k = 2; k <= m && k < kMaxDegree - 1; ++k) {
+    const double sigma2 = 1.0 / (2.0 / sigma1 - sigma);
+    cf[k] = StepCoef{2.0 * sigma2 / e, c, sigma * sigma2, 0.0};
+    sigma = sigma2;
+  }
+  cf[kMaxDegree - 1] = StepCoef{1.0, 0.0, 0.0, 0.0};
+}
+
+void launch_filter_coef(int n_sub, const double* bounds, int degree, StepCoef* coef, cudaStream_t st) {
+  k_filter_coef<<<(n_sub + 127) / 128, 128, 0, st>>>(n_sub, bounds, degree, coef);
+}
+
+// next pass: a = largest, a0 = smallest Ritz value (ascending lambda); b unchanged
+__global__ void k_bounds_from_ritz(const SubDev* subs, int n_sub, const double* lam, double* bounds) {
+  const int a = blockIdx.x * blockDim.x + threadIdx.x;
+  if (a >= n_sub) return;
+  const SubDev& S = subs[a];
+  bounds[3 * a + 1] = lam[S.off_state + S.ns - 1];
+  bounds[3 * a + 2] = lam[S.off_state];
+}
+
+void launch_bounds_from_ritz(const SubDev* d_subs, int n_sub, const double* lam, double* bounds, cudaStream_t st) {
+  k_bounds_from_ritz<<<(n_sub + 127) / 128, 128, 0, st>>>(d_subs, n_sub, lam, bounds);
+}
+
+// ---- restriction of V_eff to the subdomains (Sec. 5.A.5) ----------------------------------
+__global__ void k_restrict(const SubDev* __restrict__ subs, const double* __restrict__ Vg, int gx, int gy, int gz,
+                           double* V, float* Vf) {
+  const SubDev& S = subs[blockIdx.y];
+  for (long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x; q < S.nd; q += (long long)gridDim.x * blockDim.x) {
+    const int i = (int)(q % S.n[0]), j = (int)((q / S.n[0]) % S.n[1]), k = (int)(q / ((long long)S.n[0] * S.n[1]));
+    const int I = wrapd(S.start[0] + i, gx), J = wrapd(S.start[1] + j, gy), K = wrapd(S.start[2] + k, gz);
+    const double v = Vg[((long long)K * gy + J) * gx + I];
+    V[S.off_pt + q] = v;
+    Vf[S.off_pt + q] = (float)v;
+  }
+}
+
+void launch_restrict(const SubDev* d_subs, int n_sub, long long max_nd, const double* Vg, const int gn[3], double* V,
+                     float* Vf, cudaStream_t st) {
+  dim3 grid((unsigned)min((max_nd + 255) / 256, 1024LL), n_sub);
+  k_restrict<<<grid, 256, 0, st>>>(d_subs, Vg, gn[0], gn[1], gn[2], V, Vf);
+}
+
+// ---- projector normalisation on the global periodic grid ----------------------------------
+__global__ void k_proj_norms(const AtomImg* __restrict__ imgs, const ProjSlot* __restrict__ slots, double hx,
+                             double hy, double hz, double* norms) {
+  const AtomImg& A = imgs[blockIdx.x];
+  const ProjSlot& Q = slots[blockIdx.x];
+  const int bx = A.box_n[0], by = A.box_n[1];
+  const int npts = bx * by * A.box_n[2];
+  double s[4] = {0, 0, 0, 0};
+  for (int p = threadIdx.x; p < npts; p += blockDim.x) {
+    const int i = A.box_lo[0] + p % bx, j = A.box_lo[1] + (p / bx) % by, k = A.box_lo[2] + p / (bx * by);
+    const double dx = i * hx - A.R[0], dy = j * hy - A.R[1], dz = k * hz - A.R[2];
+    const double r2 = dx * dx + dy * dy + dz * dz;
+    if (r2 >= Q.rcut2) continue;
+    const double e = exp(-r2 / (2.0 * Q.w * Q.w));
+    s[0] += e * e;
+    s[1] += dx * dx * e * e;
+    s[2] += dy * dy * e * e;
+    s[3] += dz * dz * e * e;
+  }
+  __shared__ double red[32];
+  const double dV = hx * hy * hz;
+  for (int l = 0; l < 4; ++l) {
+    const double t = block_sum(s[l], red);
+    if (threadIdx.x == 0) norms[4 * blockIdx.x + l] = 1.0 / sqrt(t * dV);
+  }
+}
+
+void launch_proj_norms(const AtomImg* d_imgs_global, const ProjSlot* d_slots_global, int n_atoms, const int gn[3],
+                       const double gh[3], double* norms, cudaStream_t st) {
+  if (n_atoms == 0) return;
+  (void)gn;
+  k_proj_norms<<<n_atoms, 256, 0, st>>>(d_imgs_global, d_slots_global, gh[0], gh[1], gh[2], norms);
+}
+
+// ---- SplitMix64 (Steele, Lea & Flood 2014), counter form: output i = mix(seed + (i+1) gamma)
+__device__ __forceinline__ double splitmix_u(uint64_t seed, unsigned long long i) {
+  uint64_t z = seed + (uint64_t)(i + 1ULL) * 0x9E3779B97F4A7C15ULL;
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ULL;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBULL;
+  z = z ^ (z >> 31);
+  return (double)(z >> 11) * 0x1.0p-53 - 0.5;
+}
+
+template <typename T>
+__global__ void k_splitmix_fill(T* out, long long count, uint64_t seed, long long offset) {
+  for (long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x; q < count; q += (long long)gridDim.x * blockDim.x)
+    out[q] = (T)splitmix_u(seed, (unsigned long long)(offset + q));
+}
+
+void launch_splitmix_fill_f64(double* out, long long count, uint64_t seed, long long offset, cudaStream_t st) {
+  k_splitmix_fill<double><<<4 * 152, 256, 0, st>>>(out, count, seed, offset);
+}
+void launch_splitmix_fill_f32(float* out, long long count, uint64_t seed, long long offset, cudaStream_t st) {
+  k_splitmix_fill<float><<<4 * 152, 256, 0, st>>>(out, count, seed, offset);
+}
+
+__global__ void k_f64_to_f32(const double* in, float* out, long long n) {
+  for (long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x; q < n; q += (long long)gridDim.x * blockDim.x)
+    out[q] = (float)in[q];
+}
+__global__ void k_f32_to_f64(const float* in, double* out, long long n) {
+  for (long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x; q < n; q += (long long)gridDim.x * blockDim.x)
+    out[q] = (double)in[q];
+}
+void launch_convert_f64_f32(const double* in, float* out, long long count, cudaStream_t st) {
+  k_f64_to_f32<<<4 * 152, 256, 0, st>>>(in, out, count);
+}
+void launch_convert_f32_f64(const float* in, double* out, long long count, cudaStream_t st) {
+  k_f32_to_f64<<<4 * 152, 256, 0, st>>>(in, out, count);
+}
+
+// ---- Lanczos upper bound (k steps, per subdomain, FP64) ------------------------------------
+// Single-vector views: v, vprev, f hold one vector per subdomain at S.off_blk (ns = 1).
+__global__ void __launch_bounds__(1024) k_lz_init(const SubDev* __restrict__ subs, double* v) {
+  const SubDev& S = subs[blockIdx.x];
+  double* p = v + S.off_blk;
+  double acc = 0.0;
+  for (long long q = threadIdx.x; q < S.nd; q += blockDim.x) {
+    const double x = splitmix_u(0x1A4C705ULL, (unsigned long long)q);
+    p[q] = x;
+    acc += x * x;
+  }
+  __shared__ double red[32];
+  const double inv = 1.0 / sqrt(block_sum(acc, red));
+  for (long long q = threadIdx.x; q < S.nd; q += blockDim.x) p[q] *= inv;
+}
+
+void launch_lanczos_init(const SubDev* d_subs, int n_sub, double* v, cudaStream_t st) {
+  k_lz_init<<<n_sub, 1024, 0, st>>>(d_subs, v);
+}
+
+// Step j (given Hv = H v): f = Hv - beta_j vprev (j > 0); alpha_j = v.f; f -= alpha_j v;
+// beta_{j+1} = |f|; then vprev <- v, v <- f / beta_{j+1} for the next step.
+__global__ void __launch_bounds__(1024)
+k_lz_step(const SubDev* __restrict__ subs, int j, const double* __restrict__ Hv, double* v, double* vprev, double* f,
+          double* alpha, double* beta) {
+  const int a = blockIdx.x;
+  const SubDev& S = subs[a];
+  const long long o = S.off_blk;
+  const double bj = (j > 0) ? beta[a * 16 + j] : 0.0;
+  double acc = 0.0;
+  for (long long q = threadIdx.x; q < S.nd; q += blockDim.x) {
+    double x = Hv[o + q];
+    if (j > 0) x -= bj * vprev[o + q];
+    f[o + q] = x;
+    acc += v[o + q] * x;
+  }
+  __shared__ double red[32];
+  const double al = block_sum(acc, red);
+  acc = 0.0;
+  for (long long q = threadIdx.x; q < S.nd; q += blockDim.x) {
+    const double x = f[o + q] - al * v[o + q];
+    f[o + q] = x;
+    acc += x * x;
+  }
+  const double nb = sqrt(block_sum(acc, red));
+  if (threadIdx.x == 0) {
+    alpha[a * 16 + j] = al;
+    beta[a * 16 + j + 1] = nb;
+  }
+  const double inv = nb > 0 ? 1.0 / nb : 0.0;
+  for (long long q = threadIdx.x; q < S.nd; q += blockDim.x) {
+    const double vv = v[o + q];
+    vprev[o + q] = vv;
+    v[o + q] = f[o + q] * inv;
+  }
+}
+
+void launch_lanczos_step(const SubDev* d_subs, int n_sub, int j, const double* Hv, double* v, double* vprev, double* f,
+                         double* alpha, double* beta, cudaStream_t st) {
+  k_lz_step<<<n_sub, 1024, 0, st>>>(d_subs, j, Hv, v, vprev, f, alpha, beta);
+}
+
+// b = max eigenvalue of the k x k Lanczos matrix (bisection on Sturm counts) + |f_k|
+__global__ void k_lz_finish(int n_sub, int k, const double* alpha, const double* beta, double* bounds) {
+  const int a = blockIdx.x * blockDim.x + threadIdx.x;
+  if (a >= n_sub) return;
+  const double* al = alpha + a * 16;
+  const double* be = beta + a * 16;  // be[1..k-1] off-diagonals, be[k] = |f_k|
+  double lo = 1e300, hi = -1e300;
+  for (int i = 0; i < k; ++i) {
+    const double r = (i > 0 ? fabs(be[i]) : 0.0) + (i + 1 < k ? fabs(be[i + 1]) : 0.0);
+    lo = fmin(lo, al[i] - r);
+    hi = fmax(hi, al[i] + r);
+  }
+  // largest eigenvalue: smallest x with count(eigs < x) == k
+  for (int it = 0; it < 200 && hi - lo > 1e-13 * fmax(1.0, fabs(hi)); ++it) {
+    const double x = 0.5 * (lo + hi);
+    int cnt = 0;
+    double d = al[0] - x;
+    if (d < 0) ++cnt;
+    for (int i = 1; i < k; ++i) {
+      if (d == 0.0) d = 1e-300;
+      d = al[i] - x - be[i] * be[i] / d;
+      if (d < 0) ++cnt;
+    }
+    if (cnt >= k) hi = x; else lo = x;
+  }
+  bounds[3 * a] = hi + be[k];
+}
+
+void launch_lanczos_finish(int n_sub, int k, const double* alpha, const double* beta, const SubDev*, const double*,
+                           double* bounds, cudaStream_t st) {
+  k_lz_finish<<<(n_sub + 127) / 128, 128, 0, st>>>(n_sub, k, alpha, beta, bounds);
+}
+
+template void launch_gram<double>(const SubDev*, int, int, long long, const double*, const double*, double*, double*,
+                                  cudaStream_t);
+template void launch_gram<float>(const SubDev*, int, int, long long, const float*, const float*, double*, double*,
+                                 cudaStream_t);
+template void launch_rotate<double>(const SubDev*, int, int, long long, const double*, const double*, double*,
+                                    cudaStream_t);
+template void launch_rotate<float>(const SubDev*, int, int, long long, const float*, const double*, float*,
+                                   cudaStream_t);
+template void launch_core_weights<double>(const SubDev*, int, int, const double*, double*, cudaStream_t);
+template void launch_core_weights<float>(const SubDev*, int, int, const float*, double*, cudaStream_t);
+template void launch_density_occ<double>(const SubDev*, int, long long, const double*, const double*, const int*,
+                                         double*, cudaStream_t);
+template void launch_density_occ<float>(const SubDev*, int, long long, const float*, const double*, const int*,
+                                        double*, cudaStream_t);
+
+}  // namespace xls

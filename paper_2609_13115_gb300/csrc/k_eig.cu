@@ -1,0 +1,487 @@
+// Generalised symmetric eigensolve H_s y = lambda M_s y of every subdomain, FP64 (Sec. 5.A.3
+// step (3); the paper's "dense generalized eigensolver", specialised DSYGVD in Sec. 5.B.3).
+//
+//   1. M_s = L L^T                   k_cholesky      one CTA per subdomain
+//   2. W = L^-1 H_s, A = L^-1 W^T    k_trsm_lower x2 column-parallel CTAs
+//   3. A = Q T Q^T (Householder)     k_tridiag       one CTA per subdomain
+//   4. T = Z_T diag(lambda) Z_T^T    k_tri_eig       FP32 Sturm bisection for shifts, FP64
+//                                                    inverse iteration + Gram-Schmidt per
+//                                                    cluster, FP64 Rayleigh-Ritz (Jacobi) inside
+//                                                    each cluster of close eigenvalues
+//   5. Z = Q Z_T                     k_backtransform column-parallel CTAs
+//   6. Y = L^-T Z                    k_trsm_upper    column-parallel CTAs
+//
+// Matrices are n x n row-major at S.off_ss; per-subdomain vectors at 8 * S.off_state.
+#include "xls_internal.h"
+
+namespace xls {
+
+constexpr int kEigScratchThreads = 64;
+
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+__device__ double block_sum_d(double v, double* red) {
+  v = warp_sum(v);
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31, nw = (blockDim.x + 31) >> 5;
+  __syncthreads();
+  if (l == 0) red[w] = v;
+  __syncthreads();
+  double s = 0.0;
+  for (int i = 0; i < nw; ++i) s += red[i];
+  __syncthreads();
+  return s;
+}
+
+__device__ void set_status(int* status, int code, int sub) {
+  if (atomicCAS(status, 0, code) == 0) status[1] = sub;
+}
+
+// ---- 1. Cholesky, left-looking by columns; warp per row for the column update -------------
+__global__ void __launch_bounds__(512) k_cholesky(const SubDev* __restrict__ subs, double* Ms, int* status) {
+  const SubDev& S = subs[blockIdx.x];
+  const int n = S.ns;
+  double* L = Ms + S.off_ss;
+  __shared__ double red[32];
+  __shared__ double s_piv;
+  __shared__ int s_fail;
+  if (threadIdx.x == 0) s_fail = 0;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nwarp = blockDim.x >> 5;
+  for (int j = 0; j < n; ++j) {
+    double acc = 0.0;
+    for (int k = threadIdx.x; k < j; k += blockDim.x) acc += L[(long long)j * n + k] * L[(long long)j * n + k];
+    acc = block_sum_d(acc, red);
+    if (threadIdx.x == 0) {
+      const double dj = L[(long long)j * n + j] - acc;
+      if (!(dj > 0.0) || !isfinite(dj)) {
+        s_fail = 1;
+        set_status(status, XLS_ENOTSPD, blockIdx.x);
+        s_piv = 1.0;
+      } else {
+        s_piv = sqrt(dj);
+      }
+      L[(long long)j * n + j] = s_piv;
+    }
+    __syncthreads();
+    if (s_fail) return;
+    const double piv = s_piv;
+    for (int i = j + 1 + warp; i < n; i += nwarp) {
+      double a = 0.0;
+      for (int k = lane; k < j; k += 32) a += L[(long long)i * n + k] * L[(long long)j * n + k];
+      a = warp_sum(a);
+      if (lane == 0) L[(long long)i * n + j] = (L[(long long)i * n + j] - a) / piv;
+    }
+    __syncthreads();
+  }
+  // clear the strict upper triangle
+  for (long long q = threadIdx.x; q < (long long)n * n; q += blockDim.x) {
+    const int i = (int)(q / n), k = (int)(q % n);
+    if (k > i) L[q] = 0.0;
+  }
+}
+
+// ---- 2./6. triangular solves, one thread per right-hand-side column ------------------------
+// lower:  X = L^-1 B  (B[i][c] = trans ? Bm[c][i] : Bm[i][c]);  upper: X = L^-T B.
+template <bool kUpper>
+__global__ void __launch_bounds__(128)
+k_trsm(const SubDev* __restrict__ subs, const double* __restrict__ Lm, const double* Bm, int trans, double* Xm) {
+  const SubDev& S = subs[blockIdx.y];
+  const int n = S.ns;
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= n) return;
+  const double* L = Lm + S.off_ss;
+  const double* B = Bm + S.off_ss;
+  double* X = Xm + S.off_ss;
+  if (!kUpper) {
+    for (int i = 0; i < n; ++i) {
+      double s = trans ? B[(long long)c * n + i] : B[(long long)i * n + c];
+      const double* Li = L + (long long)i * n;
+      for (int k = 0; k < i; ++k) s -= Li[k] * X[(long long)k * n + c];
+      X[(long long)i * n + c] = s / Li[i];
+    }
+  } else {
+    for (int i = n - 1; i >= 0; --i) {
+      double s = B[(long long)i * n + c];
+      for (int k = i + 1; k < n; ++k) s -= L[(long long)k * n + i] * X[(long long)k * n + c];
+      X[(long long)i * n + c] = s / L[(long long)i * n + i];
+    }
+  }
+}
+
+// ---- 3. Householder tridiagonalisation of A (lower, reflectors kept below the subdiagonal) -
+// vec layout (8n per subdomain): d[0..n), e[n..2n), tau[2n..3n), lam32[3n..4n), cluster[4n..5n)
+__global__ void __launch_bounds__(512) k_tridiag(const SubDev* __restrict__ subs, double* Am, double* vecs) {
+  const SubDev& S = subs[blockIdx.x];
+  const int n = S.ns;
+  double* A = Am + S.off_ss;
+  double* d = vecs + 8LL * S.off_state;
+  double* e = d + n;
+  double* tau = d + 2 * n;
+  extern __shared__ double sm[];
+  double* sv = sm;          // reflector v (length <= n)
+  double* sw = sm + n;      // p, then w
+  __shared__ double red[32];
+  __shared__ double s_tau, s_K;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nwarp = blockDim.x >> 5;
+  // symmetrise
+  for (long long q = threadIdx.x; q < (long long)n * n; q += blockDim.x) {
+    const int i = (int)(q / n), k = (int)(q % n);
+    if (k > i) {
+      const double m = 0.5 * (A[(long long)i * n + k] + A[(long long)k * n + i]);
+      A[(long long)i * n + k] = m;
+      A[(long long)k * n + i] = m;
+    }
+  }
+  __syncthreads();
+  for (int k = 0; k + 1 < n; ++k) {
+    const int m = n - k - 1;
+    double acc = 0.0;
+    for (int i = 1 + threadIdx.x; i < m; i += blockDim.x) {
+      const double x = A[(long long)(k + 1 + i) * n + k];
+      acc += x * x;
+    }
+    const double xn2 = block_sum_d(acc, red);
+    const double alpha = A[(long long)(k + 1) * n + k];
+    double beta, t, scal;
+    if (xn2 == 0.0) {
+      t = 0.0;
+      beta = alpha;
+      scal = 0.0;
+    } else {
+      beta = -copysign(sqrt(alpha * alpha + xn2), alpha);
+      t = (beta - alpha) / beta;
+      scal = 1.0 / (alpha - beta);
+    }
+    for (int i = threadIdx.x; i < m; i += blockDim.x) {
+      const double v = (i == 0) ? 1.0 : A[(long long)(k + 1 + i) * n + k] * scal;
+      sv[i] = v;
+      if (i > 0) A[(long long)(k + 1 + i) * n + k] = v;
+    }
+    if (threadIdx.x == 0) {
+      e[k] = beta;
+      tau[k] = t;
+      d[k] = A[(long long)k * n + k];
+      s_tau = t;
+    }
+    __syncthreads();
+    if (s_tau != 0.0) {
+      // p = tau A22 v
+      for (int i = warp; i < m; i += nwarp) {
+        const double* row = A + (long long)(k + 1 + i) * n + (k + 1);
+        double a = 0.0;
+        for (int j = lane; j < m; j += 32) a += row[j] * sv[j];
+        a = warp_sum(a);
+        if (lane == 0) sw[i] = s_tau * a;
+      }
+      __syncthreads();
+      double pv = 0.0;
+      for (int i = threadIdx.x; i < m; i += blockDim.x) pv += sw[i] * sv[i];
+      pv = block_sum_d(pv, red);
+      if (threadIdx.x == 0) s_K = 0.5 * s_tau * pv;
+      __syncthreads();
+      const double K = s_K;
+      for (int i = threadIdx.x; i < m; i += blockDim.x) sw[i] -= K * sv[i];
+      __syncthreads();
+      for (long long q = threadIdx.x; q < (long long)m * m; q += blockDim.x) {
+        const int i = (int)(q / m), j = (int)(q % m);
+        A[(long long)(k + 1 + i) * n + (k + 1 + j)] -= sv[i] * sw[j] + sw[i] * sv[j];
+      }
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    d[n - 1] = A[(long long)(n - 1) * n + (n - 1)];
+    e[n - 1] = 0.0;
+    tau[n - 1] = 0.0;
+  }
+}
+
+// ---- 4. eigenpairs of the tridiagonal T ----------------------------------------------------
+__device__ __forceinline__ int sturm_count_f(const float* d, const float* e2, int n, float x, float pivmin) {
+  int cnt = 0;
+  float q = d[0] - x;
+  if (fabsf(q) < pivmin) q = -pivmin;
+  if (q < 0.f) ++cnt;
+  for (int j = 1; j < n; ++j) {
+    q = d[j] - x - e2[j - 1] / q;
+    if (fabsf(q) < pivmin) q = -pivmin;
+    if (q < 0.f) ++cnt;
+  }
+  return cnt;
+}
+
+__device__ __forceinline__ double hash_unit(unsigned a, unsigned b) {
+  unsigned h = a * 2654435761u ^ (b * 40503u + 0x9E3779B9u);
+  h ^= h >> 15;
+  h *= 0x2C1B3C6Du;
+  h ^= h >> 12;
+  h *= 0x297A2D39u;
+  h ^= h >> 15;
+  return (double)(h & 0xFFFFFFu) * (1.0 / 16777216.0) - 0.5;
+}
+
+// y = T x (tridiagonal, FP64)
+__device__ __forceinline__ double tri_mv(const double* d, const double* e, const double* x, int n, int j) {
+  double s = d[j] * x[j];
+  if (j > 0) s += e[j - 1] * x[j - 1];
+  if (j + 1 < n) s += e[j] * x[j + 1];
+  return s;
+}
+
+// Per-thread scratch: m_[n], U0[n], U1[n], U2[n], piv(as double)[n], x[n]  (6n doubles)
+__global__ void __launch_bounds__(kEigScratchThreads)
+k_tri_eig(const SubDev* __restrict__ subs, double* vecs, double* Zm, double* scratch_all, long long scr_stride,
+          double* Rm, double* lam_out) {
+  const SubDev& S = subs[blockIdx.x];
+  const int n = S.ns;
+  double* d = vecs + 8LL * S.off_state;
+  double* e = d + n;
+  double* lam32 = d + 3 * n;
+  double* cl = d + 4 * n;  // cluster start flags
+  double* Z = Zm + S.off_ss;
+  double* Rb = Rm + S.off_ss;
+  extern __shared__ float smf[];
+  float* df = smf;
+  float* e2f = smf + n;
+  __shared__ float s_gl, s_gu, s_pivmin;
+  __shared__ double s_tnorm;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) {
+    df[i] = (float)d[i];
+    e2f[i] = (float)(e[i] * e[i]);
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double gl = 1e300, gu = -1e300, emax2 = 0.0;
+    for (int i = 0; i < n; ++i) {
+      const double r = (i > 0 ? fabs(e[i - 1]) : 0.0) + (i + 1 < n ? fabs(e[i]) : 0.0);
+      gl = fmin(gl, d[i] - r);
+      gu = fmax(gu, d[i] + r);
+      if (i + 1 < n) emax2 = fmax(emax2, e[i] * e[i]);
+    }
+    const double tn = fmax(fabs(gl), fabs(gu));
+    s_tnorm = tn > 0 ? tn : 1.0;
+    s_gl = (float)(gl - 1e-5 * s_tnorm - 1e-30);
+    s_gu = (float)(gu + 1e-5 * s_tnorm + 1e-30);
+    s_pivmin = (float)fmax(1e-30, 1e-30 * emax2);
+  }
+  __syncthreads();
+  // FP32 bisection for every eigenvalue index
+  for (int i = threadIdx.x; i < n; i += blockDim.x) {
+    float lo = s_gl, hi = s_gu;
+    for (int it = 0; it < 48; ++it) {
+      const float mid = 0.5f * (lo + hi);
+      if (mid == lo || mid == hi) break;
+      if (sturm_count_f(df, e2f, n, mid, s_pivmin) > i) hi = mid; else lo = mid;
+    }
+    lam32[i] = 0.5 * ((double)lo + (double)hi);
+  }
+  __syncthreads();
+  const double tnorm = s_tnorm;
+  const double ctol = 1e-4 * tnorm;
+  if (threadIdx.x == 0) {
+    for (int i = 0; i < n; ++i) cl[i] = (i == 0 || lam32[i] - lam32[i - 1] > ctol) ? 1.0 : 0.0;
+  }
+  __syncthreads();
+  double* scr = scratch_all + ((long long)blockIdx.x * kEigScratchThreads + threadIdx.x) * scr_stride;
+  double* mlt = scr;
+  double* U0 = scr + n;
+  double* U1 = scr + 2 * n;
+  double* U2 = scr + 3 * n;
+  double* pv = scr + 4 * n;
+  double* x = scr + 5 * n;
+  const double tiny = 1e-15 * tnorm;
+  // clusters are handed out round-robin by their index among cluster starts
+  int cidx = -1;
+  for (int s = 0; s < n; ++s) {
+    if (cl[s] == 0.0) continue;
+    ++cidx;
+    if (cidx % (int)blockDim.x != (int)threadIdx.x) continue;
+    int t = s + 1;
+    while (t < n && cl[t] == 0.0) ++t;
+    const int k = t - s;
+    for (int mbr = s; mbr < t; ++mbr) {
+      const double sigma = lam32[mbr];
+      // LU with partial pivoting of T - sigma I
+      double r0 = d[0] - sigma, r1 = (n > 1) ? e[0] : 0.0;
+      for (int i = 0; i + 1 < n; ++i) {
+        const double n0 = e[i], n1 = d[i + 1] - sigma, n2 = (i + 2 < n) ? e[i + 1] : 0.0;
+        double P0, P1, P2, O0, O1, O2;
+        if (fabs(n0) > fabs(r0)) {
+          P0 = n0; P1 = n1; P2 = n2; O0 = r0; O1 = r1; O2 = 0.0; pv[i] = 1.0;
+        } else {
+          P0 = r0; P1 = r1; P2 = 0.0; O0 = n0; O1 = n1; O2 = n2; pv[i] = 0.0;
+        }
+        if (fabs(P0) < tiny) P0 = (P0 < 0 ? -tiny : tiny);
+        const double mm = O0 / P0;
+        U0[i] = P0; U1[i] = P1; U2[i] = P2; mlt[i] = mm;
+        r0 = O1 - mm * P1;
+        r1 = O2 - mm * P2;
+      }
+      if (fabs(r0) < tiny) r0 = (r0 < 0 ? -tiny : tiny);
+      U0[n - 1] = r0; U1[n - 1] = 0.0; U2[n - 1] = 0.0;
+      for (int j = 0; j < n; ++j) x[j] = hash_unit((unsigned)mbr + 1u, (unsigned)j);
+      for (int iter = 0; iter < 4; ++iter) {
+        // forward: apply swaps and multipliers
+        for (int i = 0; i + 1 < n; ++i) {
+          if (pv[i] != 0.0) { const double tmp = x[i]; x[i] = x[i + 1]; x[i + 1] = tmp; }
+          x[i + 1] -= mlt[i] * x[i];
+        }
+        // back substitution
+        for (int i = n - 1; i >= 0; --i) {
+          double v = x[i];
+          if (i + 1 < n) v -= U1[i] * x[i + 1];
+          if (i + 2 < n) v -= U2[i] * x[i + 2];
+          x[i] = v / U0[i];
+        }
+        // Gram-Schmidt against earlier members of the cluster (twice), then normalise
+        for (int pass = 0; pass < 2; ++pass)
+          for (int q = s; q < mbr; ++q) {
+            double dot = 0.0;
+            for (int j = 0; j < n; ++j) dot += Z[(long long)j * n + q] * x[j];
+            for (int j = 0; j < n; ++j) x[j] -= dot * Z[(long long)j * n + q];
+          }
+        double nrm = 0.0;
+        for (int j = 0; j < n; ++j) nrm += x[j] * x[j];
+        nrm = 1.0 / sqrt(nrm);
+        for (int j = 0; j < n; ++j) x[j] *= nrm;
+      }
+      for (int j = 0; j < n; ++j) Z[(long long)j * n + mbr] = x[j];
+    }
+    // Rayleigh-Ritz inside the cluster: Sm = Zc^T T Zc (k x k), Jacobi, rotate
+    double* Sm = Rb + (long long)s * n;            // k*k <= k*n doubles of this cluster's slice
+    double* Rr = Sm + (long long)k * k;            // needs 2 k^2 <= k n  <=> k <= n/2 ...
+    const bool fits = (2LL * k * k <= (long long)k * n) && k <= 64;
+    if (k == 1 || !fits) {
+      for (int mbr = s; mbr < t; ++mbr) {
+        double rq = 0.0;
+        for (int j = 0; j < n; ++j) {
+          double tx = d[j] * Z[(long long)j * n + mbr];
+          if (j > 0) tx += e[j - 1] * Z[(long long)(j - 1) * n + mbr];
+          if (j + 1 < n) tx += e[j] * Z[(long long)(j + 1) * n + mbr];
+          rq += Z[(long long)j * n + mbr] * tx;
+        }
+        lam_out[S.off_state + mbr] = rq;
+      }
+      continue;
+    }
+    for (int a = 0; a < k; ++a)
+      for (int b = a; b < k; ++b) {
+        double acc = 0.0;
+        for (int j = 0; j < n; ++j) {
+          double tx = d[j] * Z[(long long)j * n + s + b];
+          if (j > 0) tx += e[j - 1] * Z[(long long)(j - 1) * n + s + b];
+          if (j + 1 < n) tx += e[j] * Z[(long long)(j + 1) * n + s + b];
+          acc += Z[(long long)j * n + s + a] * tx;
+        }
+        Sm[a * k + b] = acc;
+        Sm[b * k + a] = acc;
+      }
+    for (int a = 0; a < k; ++a)
+      for (int b = 0; b < k; ++b) Rr[a * k + b] = (a == b) ? 1.0 : 0.0;
+    for (int sweep = 0; sweep < 30; ++sweep) {
+      double off = 0.0, tot = 0.0;
+      for (int a = 0; a < k; ++a)
+        for (int b = 0; b < k; ++b) {
+          tot += Sm[a * k + b] * Sm[a * k + b];
+          if (a != b) off += Sm[a * k + b] * Sm[a * k + b];
+        }
+      if (off <= 1e-30 * tot || off == 0.0) break;
+      for (int p = 0; p < k - 1; ++p)
+        for (int q = p + 1; q < k; ++q) {
+          const double apq = Sm[p * k + q];
+          if (apq == 0.0) continue;
+          const double theta = (Sm[q * k + q] - Sm[p * k + p]) / (2.0 * apq);
+          const double tt = copysign(1.0, theta) / (fabs(theta) + sqrt(theta * theta + 1.0));
+          const double c = 1.0 / sqrt(tt * tt + 1.0), sn = tt * c;
+          for (int r = 0; r < k; ++r) {  // columns p, q
+            const double sp = Sm[r * k + p], sq = Sm[r * k + q];
+            Sm[r * k + p] = c * sp - sn * sq;
+            Sm[r * k + q] = sn * sp + c * sq;
+          }
+          for (int r = 0; r < k; ++r) {  // rows p, q
+            const double sp = Sm[p * k + r], sq = Sm[q * k + r];
+            Sm[p * k + r] = c * sp - sn * sq;
+            Sm[q * k + r] = sn * sp + c * sq;
+          }
+          for (int r = 0; r < k; ++r) {
+            const double rp = Rr[r * k + p], rq = Rr[r * k + q];
+            Rr[r * k + p] = c * rp - sn * rq;
+            Rr[r * k + q] = sn * rp + c * rq;
+          }
+        }
+    }
+    // sort ascending (selection) and rotate the cluster's vectors row by row
+    int order[64];
+    const int kk = k < 64 ? k : 64;
+    for (int a = 0; a < kk; ++a) order[a] = a;
+    for (int a = 0; a < kk; ++a)
+      for (int b = a + 1; b < kk; ++b)
+        if (Sm[order[b] * k + order[b]] < Sm[order[a] * k + order[a]]) { const int tmp = order[a]; order[a] = order[b]; order[b] = tmp; }
+    for (int j = 0; j < n; ++j) {
+      double row[64];
+      for (int b = 0; b < kk; ++b) {
+        double acc = 0.0;
+        for (int a = 0; a < k; ++a) acc += Z[(long long)j * n + s + a] * Rr[a * k + order[b]];
+        row[b] = acc;
+      }
+      for (int b = 0; b < kk; ++b) Z[(long long)j * n + s + b] = row[b];
+    }
+    for (int b = 0; b < kk; ++b) lam_out[S.off_state + s + b] = Sm[order[b] * k + order[b]];
+  }
+}
+
+// ---- 5. back-transformation Z = Q Z_T, Q = H_0 H_1 ... H_{n-2} --------------------------
+__global__ void __launch_bounds__(256)
+k_backtransform(const SubDev* __restrict__ subs, const double* __restrict__ Am, const double* __restrict__ vecs,
+                double* Zm) {
+  const SubDev& S = subs[blockIdx.y];
+  const int n = S.ns;
+  const int c0 = blockIdx.x * 32;
+  if (c0 >= n) return;
+  const double* A = Am + S.off_ss;
+  const double* tau = vecs + 8LL * S.off_state + 2 * n;
+  double* Z = Zm + S.off_ss;
+  extern __shared__ double sm[];
+  double* v = sm;              // n
+  double* part = sm + n;       // 8 x 32
+  const int col = threadIdx.x & 31, rg = threadIdx.x >> 5;
+  const int c = c0 + col;
+  for (int k = n - 2; k >= 0; --k) {
+    const double t = tau[k];
+    if (t == 0.0) continue;
+    for (int i = k + 1 + threadIdx.x; i < n; i += blockDim.x) v[i] = (i == k + 1) ? 1.0 : A[(long long)i * n + k];
+    __syncthreads();
+    double acc = 0.0;
+    if (c < n)
+      for (int i = k + 1 + rg; i < n; i += 8) acc += v[i] * Z[(long long)i * n + c];
+    part[rg * 32 + col] = acc;
+    __syncthreads();
+    double dot = 0.0;
+#pragma unroll
+    for (int r = 0; r < 8; ++r) dot += part[r * 32 + col];
+    if (c < n)
+      for (int i = k + 1 + rg; i < n; i += 8) Z[(long long)i * n + c] -= t * v[i] * dot;
+    __syncthreads();
+  }
+}
+
+void launch_eig(const SubDev* d_subs, int n_sub, int max_ns, double* Ms, double* Hs, double* Y, double* W, double* lam,
+                double* vecs, int* status, double* scratch, double* R, cudaStream_t st) {
+  k_cholesky<<<n_sub, 512, 0, st>>>(d_subs, Ms, status);
+  dim3 gt((max_ns + 127) / 128, n_sub);
+  k_trsm<false><<<gt, 128, 0, st>>>(d_subs, Ms, Hs, 0, W);     // W = L^-1 H_s
+  k_trsm<false><<<gt, 128, 0, st>>>(d_subs, Ms, W, 1, Hs);     // A = L^-1 W^T
+  k_tridiag<<<n_sub, 512, 2 * max_ns * sizeof(double), st>>>(d_subs, Hs, vecs);
+  k_tri_eig<<<n_sub, kEigScratchThreads, 2 * max_ns * sizeof(float), st>>>(d_subs, vecs, W, scratch, 6LL * max_ns,
+                                                                            R, lam);
+  dim3 gb((max_ns + 31) / 32, n_sub);
+  k_backtransform<<<gb, 256, (max_ns + 256) * sizeof(double), st>>>(d_subs, Hs, vecs, W);
+  k_trsm<true><<<gt, 128, 0, st>>>(d_subs, Ms, W, 0, Y);       // Y = L^-T Z
+}
+
+size_t eig_scratch_doubles(int n_sub, int max_ns) { return (size_t)n_sub * kEigScratchThreads * 6 * max_ns; }
+
+}  // namespace xls

@@ -1,0 +1,293 @@
+// Chebyshev-filter step kernels: 12th-order FD stencil + local potential + recurrence, and the
+// Kleinman-Bylander nonlocal projection / back-projection (Sec. 5.A.3 step (1); Sec. 5.B.2).
+//
+// One filter step computes, for every subdomain alpha and every vector of its block,
+//   Y_out = scale * (H Y_in - c Y_in) - shift * Y_prev,
+//   H Y = -1/2 Delta_h Y + V Y + sum_I sum_l chi_Il P_Il,   P_Il = E_l dV <chi_Il, Y>.
+// The local part is one launch (k_stencil); the nonlocal part is a projection launch before it
+// (k_nl_project, P from Y_in) and a back-projection launch after it (k_nl_back, adds
+// scale * chi P into Y_out).  All subdomains of a step share each launch.
+#include "xls_internal.h"
+
+namespace xls {
+
+__constant__ double c_fdw[kN0 + 1] = {-5369.0 / 1800.0, 12.0 / 7.0, -15.0 / 56.0, 10.0 / 189.0,
+                                      -1.0 / 112.0,     2.0 / 1925.0, -1.0 / 16632.0};
+
+__device__ __forceinline__ int wrapi(int i, int n) {
+  i %= n;
+  return i < 0 ? i + n : i;
+}
+
+__device__ __forceinline__ int find_sub(const int* blk_off, int n_sub, int b) {
+  int lo = 0, hi = n_sub;  // blk_off[lo] <= b < blk_off[hi]
+  while (hi - lo > 1) {
+    int mid = (lo + hi) >> 1;
+    if (blk_off[mid] <= b) lo = mid; else hi = mid;
+  }
+  return lo;
+}
+
+constexpr int kTX = 32, kTY = 8;
+
+int stencil_blocks(const int n[3], int ns) {
+  return ((n[0] + kTX - 1) / kTX) * ((n[1] + kTY - 1) / kTY) * ns;
+}
+
+// 2.5-D blocking: a CTA owns a kTX x kTY column tile of one vector and marches along z.  The
+// 13 z-values of each column live in a register queue; each xy-plane (with its 6-point halo)
+// is staged in shared memory for the x/y neighbours.  Out-of-box points are zero (Dirichlet)
+// or wrapped (periodic).
+template <typename T>
+__global__ void __launch_bounds__(kTX * kTY)
+k_stencil(const SubDev* __restrict__ subs, int n_sub, const int* __restrict__ blk_off,
+          const T* __restrict__ Yin, const T* Yprev, T* Yout, const T* __restrict__ Vall,
+          const StepCoef* __restrict__ coef, int step) {
+  __shared__ T tile[kTY + 2 * kN0][kTX + 2 * kN0];
+  const int b = blockIdx.x;
+  const int a = find_sub(blk_off, n_sub, b);
+  const SubDev& S = subs[a];
+  const int nx = S.n[0], ny = S.n[1], nz = S.n[2];
+  const int px = S.periodic[0], py = S.periodic[1], pz = S.periodic[2];
+  const int ntx = (nx + kTX - 1) / kTX, nty = (ny + kTY - 1) / kTY;
+  const int local = b - blk_off[a];
+  const int t = local % (ntx * nty);
+  const long long vec = local / (ntx * nty);
+  const int x0 = (t % ntx) * kTX, y0 = (t / ntx) * kTY;
+  const long long base = S.off_blk + vec * S.nd;
+  const T* __restrict__ yin = Yin + base;
+  const T* yprev = Yprev ? Yprev + base : nullptr;
+  T* yout = Yout + base;
+  const T* __restrict__ V = Vall + S.off_pt;
+  const StepCoef cf = coef[a * kMaxDegree + step];
+  const T scale = (T)cf.scale, cshift = (T)cf.c, pshift = (T)cf.shift;
+
+  T wx[kN0 + 1], wy[kN0 + 1], wz[kN0 + 1];
+  {
+    const double ix = -0.5 / (S.h[0] * S.h[0]), iy = -0.5 / (S.h[1] * S.h[1]), iz = -0.5 / (S.h[2] * S.h[2]);
+#pragma unroll
+    for (int p = 0; p <= kN0; ++p) {
+      wx[p] = (T)(c_fdw[p] * ix);
+      wy[p] = (T)(c_fdw[p] * iy);
+      wz[p] = (T)(c_fdw[p] * iz);
+    }
+  }
+  const T wc = (T)(c_fdw[0] * (-0.5 / (S.h[0] * S.h[0]) - 0.5 / (S.h[1] * S.h[1]) - 0.5 / (S.h[2] * S.h[2])));
+
+  const int tx = threadIdx.x, ty = threadIdx.y;
+  const int x = x0 + tx, y = y0 + ty;
+  const bool active = (x < nx) && (y < ny);
+  // this thread's column in the (boundary-mapped) grid; -1 = zero column
+  int cx = x, cy = y;
+  if (cx >= nx) cx = px ? wrapi(cx, nx) : -1;
+  if (cy >= ny) cy = py ? wrapi(cy, ny) : -1;
+  const bool has_col = (cx >= 0) && (cy >= 0);
+  const long long plane = (long long)nx * ny;
+  auto load_col = [&](int z) -> T {
+    if (!has_col) return (T)0;
+    if (z < 0 || z >= nz) {
+      if (!pz) return (T)0;
+      z = wrapi(z, nz);
+    }
+    return yin[z * plane + (long long)cy * nx + cx];
+  };
+
+  T q[2 * kN0 + 1];
+#pragma unroll
+  for (int k = 0; k < 2 * kN0 + 1; ++k) q[k] = load_col(k - kN0);
+
+  const int tid = ty * kTX + tx;
+  constexpr int RW = kTX + 2 * kN0, RH = kTY + 2 * kN0;
+  for (int z = 0; z < nz; ++z) {
+    tile[ty + kN0][tx + kN0] = q[kN0];
+    // halo ring of the plane
+    for (int s = tid; s < RW * RH; s += kTX * kTY) {
+      const int sy = s / RW, sx = s - sy * RW;
+      if (sy >= kN0 && sy < kN0 + kTY && sx >= kN0 && sx < kN0 + kTX) continue;
+      int gx = x0 + sx - kN0, gy = y0 + sy - kN0;
+      T val = (T)0;
+      bool ok = true;
+      if (gx < 0 || gx >= nx) { if (px) gx = wrapi(gx, nx); else ok = false; }
+      if (gy < 0 || gy >= ny) { if (py) gy = wrapi(gy, ny); else ok = false; }
+      if (ok) val = yin[z * plane + (long long)gy * nx + gx];
+      tile[sy][sx] = val;
+    }
+    __syncthreads();
+    if (active) {
+      const T c0 = q[kN0];
+      T acc = wc * c0;
+#pragma unroll
+      for (int p = 1; p <= kN0; ++p) {
+        acc += wx[p] * (tile[ty + kN0][tx + kN0 + p] + tile[ty + kN0][tx + kN0 - p]);
+        acc += wy[p] * (tile[ty + kN0 + p][tx + kN0] + tile[ty + kN0 - p][tx + kN0]);
+        acc += wz[p] * (q[kN0 + p] + q[kN0 - p]);
+      }
+      const long long g = z * plane + (long long)y * nx + x;
+      acc += V[g] * c0;
+      T out = scale * (acc - cshift * c0);
+      if (yprev) out -= pshift * yprev[g];
+      yout[g] = out;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < 2 * kN0; ++k) q[k] = q[k + 1];
+    q[2 * kN0] = load_col(z + kN0 + 1);
+  }
+}
+
+template <typename T>
+void launch_stencil(const SubDev* d_subs, int n_sub, const Plan& plan, const T* Yin, const T* Yprev, T* Yout,
+                    const T* V, const StepCoef* coef, int step, cudaStream_t st) {
+  if (plan.total == 0) return;
+  dim3 block(kTX, kTY);
+  k_stencil<T><<<plan.total, block, 0, st>>>(d_subs, n_sub, plan.d_blk_off, Yin, Yprev, Yout, V, coef, step);
+}
+
+// ---- nonlocal projectors -------------------------------------------------------------------
+// A CTA handles one projector slot (one atom in one subdomain, all of its periodic images) and
+// 64 vectors (8 warps x 8 vectors); lanes stride over the points of each image's bounding box,
+// evaluate the four projectors on the fly, and accumulate.
+constexpr int kNlWarps = 8, kNlVec = 8;
+
+template <typename T>
+__device__ __forceinline__ void chi_at(const ProjSlot& A, const AtomImg& I, const SubDev& S, int p, T chi[4],
+                                       long long& g, bool& in) {
+  const int bx = I.box_n[0], by = I.box_n[1];
+  const int i = I.box_lo[0] + p % bx;
+  const int j = I.box_lo[1] + (p / bx) % by;
+  const int k = I.box_lo[2] + p / (bx * by);
+  const double dx = i * S.h[0] - I.R[0], dy = j * S.h[1] - I.R[1], dz = k * S.h[2] - I.R[2];
+  const double r2 = dx * dx + dy * dy + dz * dz;
+  in = r2 < A.rcut2;
+  if (!in) return;
+  const double e = exp(-r2 / (2.0 * A.w * A.w));
+  chi[0] = (T)(A.norm[0] * e);
+  chi[1] = (T)(A.norm[1] * dx * e);
+  chi[2] = (T)(A.norm[2] * dy * e);
+  chi[3] = (T)(A.norm[3] * dz * e);
+  const int gi = S.periodic[0] ? wrapi(i, S.n[0]) : i;
+  const int gj = S.periodic[1] ? wrapi(j, S.n[1]) : j;
+  const int gk = S.periodic[2] ? wrapi(k, S.n[2]) : k;
+  g = ((long long)gk * S.n[1] + gj) * S.n[0] + gi;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kNlWarps * 32)
+k_nl_project(const SubDev* __restrict__ subs, const ProjSlot* __restrict__ slots, const AtomImg* __restrict__ imgs,
+             const T* __restrict__ Y, double* __restrict__ P) {
+  const ProjSlot& A = slots[blockIdx.x];
+  const SubDev& S = subs[A.sub];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int v0 = (blockIdx.y * kNlWarps + warp) * kNlVec;
+  if (v0 >= S.ns) return;
+  const int nv = min(kNlVec, S.ns - v0);
+  T acc[4][kNlVec];
+#pragma unroll
+  for (int l = 0; l < 4; ++l)
+#pragma unroll
+    for (int v = 0; v < kNlVec; ++v) acc[l][v] = (T)0;
+  const T* yb = Y + S.off_blk + (long long)v0 * S.nd;
+  for (int im = A.img_lo; im < A.img_lo + A.img_n; ++im) {
+    const AtomImg& I = imgs[im];
+    const int npts = I.box_n[0] * I.box_n[1] * I.box_n[2];
+    for (int p = lane; p < npts; p += 32) {
+      T chi[4];
+      long long g;
+      bool in;
+      chi_at<T>(A, I, S, p, chi, g, in);
+      if (!in) continue;
+#pragma unroll
+      for (int v = 0; v < kNlVec; ++v) {
+        if (v < nv) {
+          const T y = yb[(long long)v * S.nd + g];
+#pragma unroll
+          for (int l = 0; l < 4; ++l) acc[l][v] += chi[l] * y;
+        }
+      }
+    }
+  }
+#pragma unroll
+  for (int l = 0; l < 4; ++l)
+#pragma unroll
+    for (int v = 0; v < kNlVec; ++v) {
+      T s = acc[l][v];
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+      acc[l][v] = s;
+    }
+  if (lane == 0) {
+    double* pa = P + S.off_proj + (long long)(blockIdx.x - S.slot_lo) * 4 * S.ns;
+    for (int v = 0; v < nv; ++v)
+#pragma unroll
+      for (int l = 0; l < 4; ++l) pa[l * S.ns + v0 + v] = (double)acc[l][v] * A.E[l] * S.dV;
+  }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kNlWarps * 32)
+k_nl_back(const SubDev* __restrict__ subs, const ProjSlot* __restrict__ slots, const AtomImg* __restrict__ imgs,
+          const double* __restrict__ P, T* Yout, const StepCoef* __restrict__ coef, int step) {
+  const ProjSlot& A = slots[blockIdx.x];
+  const SubDev& S = subs[A.sub];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int v0 = (blockIdx.y * kNlWarps + warp) * kNlVec;
+  if (v0 >= S.ns) return;
+  const int nv = min(kNlVec, S.ns - v0);
+  const double scale = coef[A.sub * kMaxDegree + step].scale;
+  const double* pa = P + S.off_proj + (long long)(blockIdx.x - S.slot_lo) * 4 * S.ns;
+  T q[4][kNlVec];
+#pragma unroll
+  for (int v = 0; v < kNlVec; ++v)
+#pragma unroll
+    for (int l = 0; l < 4; ++l) q[l][v] = (v < nv) ? (T)(scale * pa[l * S.ns + v0 + v]) : (T)0;
+  T* yb = Yout + S.off_blk + (long long)v0 * S.nd;
+  for (int im = A.img_lo; im < A.img_lo + A.img_n; ++im) {
+    const AtomImg& I = imgs[im];
+    const int npts = I.box_n[0] * I.box_n[1] * I.box_n[2];
+    for (int p = lane; p < npts; p += 32) {
+      T chi[4];
+      long long g;
+      bool in;
+      chi_at<T>(A, I, S, p, chi, g, in);
+      if (!in) continue;
+#pragma unroll
+      for (int v = 0; v < kNlVec; ++v) {
+        if (v < nv) {
+          const T add = chi[0] * q[0][v] + chi[1] * q[1][v] + chi[2] * q[2][v] + chi[3] * q[3][v];
+          atomicAdd(yb + (long long)v * S.nd + g, add);
+        }
+      }
+    }
+  }
+}
+
+template <typename T>
+void launch_nl_project(const SubDev* d_subs, const ProjSlot* d_slots, int n_slot, const AtomImg* d_imgs, int max_ns,
+                       const T* Y, double* P, cudaStream_t st) {
+  if (n_slot == 0) return;
+  dim3 grid(n_slot, (max_ns + kNlWarps * kNlVec - 1) / (kNlWarps * kNlVec));
+  k_nl_project<T><<<grid, kNlWarps * 32, 0, st>>>(d_subs, d_slots, d_imgs, Y, P);
+}
+
+template <typename T>
+void launch_nl_back(const SubDev* d_subs, const ProjSlot* d_slots, int n_slot, const AtomImg* d_imgs, int max_ns,
+                    const double* P, T* Yout, const StepCoef* coef, int step, cudaStream_t st) {
+  if (n_slot == 0) return;
+  dim3 grid(n_slot, (max_ns + kNlWarps * kNlVec - 1) / (kNlWarps * kNlVec));
+  k_nl_back<T><<<grid, kNlWarps * 32, 0, st>>>(d_subs, d_slots, d_imgs, P, Yout, coef, step);
+}
+
+template void launch_stencil<double>(const SubDev*, int, const Plan&, const double*, const double*, double*,
+                                     const double*, const StepCoef*, int, cudaStream_t);
+template void launch_stencil<float>(const SubDev*, int, const Plan&, const float*, const float*, float*,
+                                    const float*, const StepCoef*, int, cudaStream_t);
+template void launch_nl_project<double>(const SubDev*, const ProjSlot*, int, const AtomImg*, int, const double*,
+                                        double*, cudaStream_t);
+template void launch_nl_project<float>(const SubDev*, const ProjSlot*, int, const AtomImg*, int, const float*, double*,
+                                       cudaStream_t);
+template void launch_nl_back<double>(const SubDev*, const ProjSlot*, int, const AtomImg*, int, const double*, double*,
+                                     const StepCoef*, int, cudaStream_t);
+template void launch_nl_back<float>(const SubDev*, const ProjSlot*, int, const AtomImg*, int, const double*, float*,
+                                    const StepCoef*, int, cudaStream_t);
+
+}  // namespace xls

@@ -1,0 +1,801 @@
+// libxls C ABI: grid handle, restriction/projector set-up, CheFSI pass orchestration over all
+// subdomains (one launch per stage), Fermi level and density.  Host code only orchestrates;
+// every arithmetic step of the pass runs in the kernels of k_filter.cu, k_dense.cu, k_eig.cu
+// and k_tc.cu.
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "xls_internal.h"
+
+using namespace xls;
+
+namespace {
+
+thread_local std::string g_last_error;
+
+xls_status fail(xls_status s, const std::string& msg) {
+  g_last_error = msg;
+  return s;
+}
+
+#define XLS_CUDA(call)                                                                        \
+  do {                                                                                        \
+    cudaError_t _e = (call);                                                                  \
+    if (_e != cudaSuccess)                                                                    \
+      return fail(XLS_ECUDA, std::string(#call) + ": " + cudaGetErrorString(_e));             \
+  } while (0)
+
+#define XLS_TRY(expr)                 \
+  do {                                \
+    xls_status _s = (expr);           \
+    if (_s != XLS_OK) return _s;      \
+  } while (0)
+
+}  // namespace
+
+struct xls_grid_s {
+  int prec = XLS_FP64;
+  cudaStream_t st = nullptr;
+  int gn[3];
+  double gL[3], gh[3];
+  int n_sub = 0;
+  std::vector<SubDev> subs;     // main view (ns = N_s)
+  std::vector<SubDev> subs1;    // single-vector view (ns = 1), for the Lanczos bound and tests
+  SubDev* d_subs = nullptr;
+  SubDev* d_subs1 = nullptr;
+  Plan plan, plan1;
+  int max_ns = 0, tot_states = 0;
+  long long max_nd = 0, tot_pts = 0, tot_blk = 0, tot_ss = 0, max_core = 0;
+  size_t elem = 8;              // bytes per block element (8 FP64, 4 mixed)
+  void* blk[3] = {nullptr, nullptr, nullptr};
+  int cur = 0;                  // block holding the current orbitals
+  double* V = nullptr;
+  float* Vf = nullptr;
+  double *Ms = nullptr, *Hs = nullptr, *Lb = nullptr, *Ab = nullptr, *W = nullptr, *Y = nullptr, *R = nullptr;
+  double *lam = nullptr, *cw = nullptr, *occ = nullptr, *vecs = nullptr, *eig_scr = nullptr;
+  double* bounds = nullptr;
+  StepCoef* coef = nullptr;
+  int* status = nullptr;
+  double* out4 = nullptr;
+  double* rho = nullptr;
+  double* Vg = nullptr;
+  // projectors
+  AtomImg* d_imgs = nullptr;
+  ProjSlot* d_slots = nullptr;
+  int n_slot = 0;
+  double *P = nullptr, *P1 = nullptr;
+  // Lanczos (single-vector view, FP64)
+  double *lz_v = nullptr, *lz_vp = nullptr, *lz_f = nullptr, *lz_Hv = nullptr, *lz_a = nullptr, *lz_b = nullptr;
+  bool ham_set = false, orb_set = false, have_ritz = false;
+  size_t bytes = 0, budget = 0;
+  std::vector<void*> allocs;
+  cudaEvent_t ev[6];
+  double stage_ms[4] = {0, 0, 0, 0};
+  int last_launches = 0;
+  int launches = 0;
+  // optional per-kernel-class timing: event pairs around every launch of the pass
+  bool profiling = false;
+  std::vector<cudaEvent_t> pev;
+  std::vector<int> pcls;
+  size_t pused = 0;
+  double kms[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+  int kcnt[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+
+  template <typename P_>
+  xls_status alloc(P_** p, size_t bytes_) {
+    if (bytes_ == 0) bytes_ = 16;
+    if (budget && bytes + bytes_ > budget)
+      return fail(XLS_ENOMEM, "allocation of " + std::to_string(bytes_) + " B exceeds the HBM budget");
+    void* q = nullptr;
+    cudaError_t e = cudaMalloc(&q, bytes_);
+    if (e != cudaSuccess) return fail(XLS_ENOMEM, std::string("cudaMalloc: ") + cudaGetErrorString(e));
+    allocs.push_back(q);
+    bytes += bytes_;
+    *p = (P_*)q;
+    return XLS_OK;
+  }
+  template <typename P_>
+  void release(P_** p) {
+    if (!*p) return;
+    for (size_t i = 0; i < allocs.size(); ++i)
+      if (allocs[i] == (void*)*p) {
+        allocs.erase(allocs.begin() + i);
+        break;
+      }
+    cudaFree(*p);
+    *p = nullptr;
+  }
+};
+
+namespace {
+
+xls_status check_status(xls_grid g) {
+  int h[2] = {0, 0};
+  XLS_CUDA(cudaMemcpyAsync(h, g->status, 2 * sizeof(int), cudaMemcpyDeviceToHost, g->st));
+  XLS_CUDA(cudaStreamSynchronize(g->st));
+  if (h[0] != 0) {
+    XLS_CUDA(cudaMemsetAsync(g->status, 0, 2 * sizeof(int), g->st));
+    if (h[0] == XLS_ENOTSPD)
+      return fail(XLS_ENOTSPD, "Gram matrix M_s not positive definite in subdomain " + std::to_string(h[1]));
+    if (h[0] == XLS_ENOCONV) return fail(XLS_ENOCONV, "Fermi level not bracketed: N_e exceeds the states' capacity");
+    return fail((xls_status)h[0], "device error " + std::to_string(h[0]) + " in subdomain " + std::to_string(h[1]));
+  }
+  return XLS_OK;
+}
+
+xls_status make_plan(xls_grid g, const std::vector<SubDev>& v, Plan& plan) {
+  std::vector<int> off(v.size() + 1, 0);
+  for (size_t a = 0; a < v.size(); ++a) off[a + 1] = off[a] + stencil_blocks(v[a].n, v[a].ns);
+  plan.total = off.back();
+  XLS_TRY(g->alloc(&plan.d_blk_off, off.size() * sizeof(int)));
+  XLS_CUDA(cudaMemcpy(plan.d_blk_off, off.data(), off.size() * sizeof(int), cudaMemcpyHostToDevice));
+  return XLS_OK;
+}
+
+template <typename T>
+T* blkp(xls_grid g, int i) { return (T*)g->blk[i]; }
+
+// kernel classes of the profile
+enum { K_STENCIL = 0, K_NLPROJ = 1, K_NLBACK = 2, K_GRAM = 3, K_EIG = 4, K_ROTATE = 5, K_OTHER = 6 };
+
+struct ProfScope {
+  xls_grid g;
+  int cls;
+  bool on;
+  ProfScope(xls_grid g_, int cls_) : g(g_), cls(cls_), on(g_->profiling && g_->pused + 2 <= g_->pev.size()) {
+    if (on) cudaEventRecord(g->pev[g->pused], g->st);
+  }
+  ~ProfScope() {
+    if (!on) return;
+    cudaEventRecord(g->pev[g->pused + 1], g->st);
+    g->pcls[g->pused / 2] = cls;
+    g->pused += 2;
+  }
+};
+
+void prof_collect(xls_grid g) {
+  if (!g->profiling) return;
+  for (int c = 0; c < 8; ++c) { g->kms[c] = 0; g->kcnt[c] = 0; }
+  for (size_t i = 0; i + 1 < g->pused; i += 2) {
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, g->pev[i], g->pev[i + 1]);
+    g->kms[g->pcls[i / 2]] += ms;
+    g->kcnt[g->pcls[i / 2]] += 1;
+  }
+}
+
+// y_out = scale_step * (H - c) y_in - shift * y_prev for every subdomain of a view
+template <typename T>
+void h_step(xls_grid g, bool one, const T* yin, const T* yprev, T* yout, int step) {
+  const SubDev* ds = one ? g->d_subs1 : g->d_subs;
+  const Plan& pl = one ? g->plan1 : g->plan;
+  double* P = one ? g->P1 : g->P;
+  const int mns = one ? 1 : g->max_ns;
+  const T* V = (sizeof(T) == 8) ? (const T*)g->V : (const T*)g->Vf;
+  { ProfScope ps(g, K_NLPROJ); launch_nl_project<T>(ds, g->d_slots, g->n_slot, g->d_imgs, mns, yin, P, g->st); }
+  { ProfScope ps(g, K_STENCIL); launch_stencil<T>(ds, g->n_sub, pl, yin, yprev, yout, V, g->coef, step, g->st); }
+  { ProfScope ps(g, K_NLBACK); launch_nl_back<T>(ds, g->d_slots, g->n_slot, g->d_imgs, mns, P, yout, g->coef, step, g->st); }
+  g->launches += (g->n_slot ? 3 : 1);
+}
+
+constexpr int kUnitStep = kMaxDegree - 1;
+
+// filter the current block in place of the two spare buffers; returns the index of Psi_f
+template <typename T>
+int run_filter(xls_grid g, int m) {
+  launch_filter_coef(g->n_sub, g->bounds, m, g->coef, g->st);
+  g->launches++;
+  int ia = g->cur, ib = (g->cur + 1) % 3;
+  h_step<T>(g, false, blkp<T>(g, ia), nullptr, blkp<T>(g, ib), 1);
+  int yk = ib, yprev = ia;
+  for (int k = 2; k <= m; ++k) {
+    h_step<T>(g, false, blkp<T>(g, yk), blkp<T>(g, yprev), blkp<T>(g, yprev), k);
+    const int t = yk;
+    yk = yprev;
+    yprev = t;
+  }
+  return yk;
+}
+
+// third buffer index distinct from a and b
+int other(int a, int b) {
+  for (int i = 0; i < 3; ++i)
+    if (i != a && i != b) return i;
+  return 0;
+}
+
+template <typename T>
+void projection(xls_grid g, int f) {
+  const int hf = other(f, f == 0 ? 1 : 0);
+  h_step<T>(g, false, blkp<T>(g, f), nullptr, blkp<T>(g, hf), kUnitStep);
+  cudaMemsetAsync(g->Ms, 0, g->tot_ss * sizeof(double), g->st);
+  cudaMemsetAsync(g->Hs, 0, g->tot_ss * sizeof(double), g->st);
+  { ProfScope ps(g, K_GRAM); launch_gram<T>(g->d_subs, g->n_sub, g->max_ns, g->max_nd, blkp<T>(g, f), blkp<T>(g, hf), g->Ms, g->Hs, g->st); }
+  g->launches++;
+}
+
+void eigensolve(xls_grid g) {
+  cudaMemcpyAsync(g->Lb, g->Ms, g->tot_ss * sizeof(double), cudaMemcpyDeviceToDevice, g->st);
+  cudaMemcpyAsync(g->Ab, g->Hs, g->tot_ss * sizeof(double), cudaMemcpyDeviceToDevice, g->st);
+  { ProfScope ps(g, K_EIG);
+    launch_eig(g->d_subs, g->n_sub, g->max_ns, g->Lb, g->Ab, g->Y, g->W, g->lam, g->vecs, g->status, g->eig_scr, g->R,
+               g->st); }
+  g->launches += 7;
+}
+
+template <typename T>
+void rotation(xls_grid g, int f) {
+  const int out = other(f, f == 0 ? 1 : 0);
+  { ProfScope ps(g, K_ROTATE); launch_rotate<T>(g->d_subs, g->n_sub, g->max_ns, g->max_nd, blkp<T>(g, f), g->Y, blkp<T>(g, out), g->st); }
+  { ProfScope ps(g, K_OTHER); launch_core_weights<T>(g->d_subs, g->n_sub, g->max_ns, blkp<T>(g, out), g->cw, g->st); }
+  launch_bounds_from_ritz(g->d_subs, g->n_sub, g->lam, g->bounds, g->st);
+  g->launches += 3;
+  g->cur = out;
+}
+
+template <typename T>
+xls_status bootstrap_bounds(xls_grid g) {
+  // (a, a0) from the Ritz values of the unfiltered block; b was set by the Lanczos bound
+  projection<T>(g, g->cur);
+  eigensolve(g);
+  launch_bounds_from_ritz(g->d_subs, g->n_sub, g->lam, g->bounds, g->st);
+  g->launches++;
+  return check_status(g);
+}
+
+xls_status upload_bounds(xls_grid g, const double* bounds) {
+  XLS_CUDA(cudaMemcpyAsync(g->bounds, bounds, 3 * g->n_sub * sizeof(double), cudaMemcpyHostToDevice, g->st));
+  return XLS_OK;
+}
+
+template <typename T>
+xls_status chefsi(xls_grid g, int degree, int n_passes, const double* bounds) {
+  if (bounds) {
+    XLS_TRY(upload_bounds(g, bounds));
+  } else if (!g->have_ritz) {
+    XLS_TRY(bootstrap_bounds<T>(g));
+  }
+  for (int p = 0; p < n_passes; ++p) {
+    const bool last = (p == n_passes - 1);
+    g->launches = 0;
+    g->pused = 0;
+    if (last) cudaEventRecord(g->ev[0], g->st);
+    const int f = run_filter<T>(g, degree);
+    if (last) cudaEventRecord(g->ev[1], g->st);
+    projection<T>(g, f);
+    if (last) cudaEventRecord(g->ev[2], g->st);
+    eigensolve(g);
+    if (last) cudaEventRecord(g->ev[3], g->st);
+    rotation<T>(g, f);
+    if (last) cudaEventRecord(g->ev[4], g->st);
+  }
+  g->have_ritz = true;
+  g->last_launches = g->launches;
+  XLS_TRY(check_status(g));
+  prof_collect(g);
+  if (n_passes > 0) {
+    for (int i = 0; i < 4; ++i) {
+      float ms = 0.f;
+      cudaEventElapsedTime(&ms, g->ev[i], g->ev[i + 1]);
+      g->stage_ms[i] = ms;
+    }
+  }
+  return XLS_OK;
+}
+
+template <typename T>
+xls_status stage(xls_grid g, int which, int degree, const double* bounds) {
+  switch (which) {
+    case 1: {
+      if (bounds) XLS_TRY(upload_bounds(g, bounds));
+      else if (!g->have_ritz) XLS_TRY(bootstrap_bounds<T>(g));
+      g->cur = run_filter<T>(g, degree);
+      break;
+    }
+    case 2: projection<T>(g, g->cur); break;
+    case 3: eigensolve(g); break;
+    case 4: rotation<T>(g, g->cur); g->have_ritz = true; break;
+    default: return fail(XLS_EINVAL, "stage must be 1..4");
+  }
+  return check_status(g);
+}
+
+// Lanczos upper bound of every subdomain (10 steps, FP64, single-vector view)
+xls_status lanczos_bounds(xls_grid g) {
+  const int k = 10;
+  launch_lanczos_init(g->d_subs1, g->n_sub, g->lz_v, g->st);
+  for (int j = 0; j < k; ++j) {
+    h_step<double>(g, true, g->lz_v, nullptr, g->lz_Hv, kUnitStep);
+    launch_lanczos_step(g->d_subs1, g->n_sub, j, g->lz_Hv, g->lz_v, g->lz_vp, g->lz_f, g->lz_a, g->lz_b, g->st);
+  }
+  launch_lanczos_finish(g->n_sub, k, g->lz_a, g->lz_b, g->d_subs1, g->lz_f, g->bounds, g->st);
+  return check_status(g);
+}
+
+// periodic images of one atom that touch a subdomain (local frame of the subdomain)
+void atom_images(xls_grid g, int a, const double R[3], const xls_species& sp, int slot, std::vector<AtomImg>& out) {
+  const SubDev& S = g->subs[a];
+  std::vector<double> cand[3];
+  int lo[3][5], cnt[3][5];
+  for (int d = 0; d < 3; ++d) {
+    const double h = g->gh[d], L = g->gL[d];
+    const double Rl = R[d] - S.start[d] * h;
+    if (S.periodic[d]) {
+      double r = std::fmod(Rl, L);
+      if (r < 0) r += L;
+      cand[d].push_back(r);
+    } else {
+      for (int s = -2; s <= 2; ++s) cand[d].push_back(Rl + s * L);
+    }
+    int c = 0;
+    std::vector<double> keep;
+    for (double r : cand[d]) {
+      int b0 = (int)std::floor((r - sp.r_cut) / h), b1 = (int)std::ceil((r + sp.r_cut) / h);
+      if (!S.periodic[d]) {
+        b0 = std::max(b0, 0);
+        b1 = std::min(b1, S.n[d] - 1);
+        if (b1 < b0) continue;
+      }
+      lo[d][c] = b0;
+      cnt[d][c] = b1 - b0 + 1;
+      keep.push_back(r);
+      ++c;
+    }
+    cand[d] = keep;
+  }
+  for (size_t ix = 0; ix < cand[0].size(); ++ix)
+    for (size_t iy = 0; iy < cand[1].size(); ++iy)
+      for (size_t iz = 0; iz < cand[2].size(); ++iz) {
+        AtomImg A{};
+        const size_t ii[3] = {ix, iy, iz};
+        double dist2 = 0.0;
+        for (int d = 0; d < 3; ++d) {
+          A.R[d] = cand[d][ii[d]];
+          A.box_lo[d] = lo[d][ii[d]];
+          A.box_n[d] = cnt[d][ii[d]];
+          // distance from the sphere centre to the box (clamped), for the intersection test
+          const double h = g->gh[d];
+          const double bl = A.box_lo[d] * h, bh = (A.box_lo[d] + A.box_n[d] - 1) * h;
+          const double c = std::min(std::max(A.R[d], bl), bh);
+          dist2 += (A.R[d] - c) * (A.R[d] - c);
+        }
+        if (dist2 >= sp.r_cut * sp.r_cut) continue;
+        A.slot = slot;
+        out.push_back(A);
+      }
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* xls_last_error(void) { return g_last_error.c_str(); }
+
+xls_status xls_grid_create(const xls_cell* cell, const xls_dc* dc, int precision, size_t hbm_budget_bytes,
+                           void* cuda_stream, xls_grid* out) {
+  if (!cell || !dc || !out || dc->n_sub < 1 || !dc->core_lo || !dc->core_n || !dc->buf || !dc->n_states)
+    return fail(XLS_EINVAL, "xls_grid_create: null argument or n_sub < 1");
+  if (precision != XLS_FP64 && precision != XLS_MIXED_BF16) return fail(XLS_EINVAL, "unknown precision");
+  for (int d = 0; d < 3; ++d)
+    if (cell->n[d] < 2 * kN0 + 1 || !(cell->L[d] > 0)) return fail(XLS_EINVAL, "cell: n >= 13 and L > 0 per axis");
+  xls_grid g = new xls_grid_s();
+  g->prec = precision;
+  g->st = (cudaStream_t)cuda_stream;
+  g->budget = hbm_budget_bytes;
+  g->elem = precision == XLS_FP64 ? 8 : 4;
+  for (int d = 0; d < 3; ++d) {
+    g->gn[d] = cell->n[d];
+    g->gL[d] = cell->L[d];
+    g->gh[d] = cell->L[d] / cell->n[d];
+  }
+  g->n_sub = dc->n_sub;
+  long long covered = 0;
+  for (int a = 0; a < dc->n_sub; ++a) {
+    SubDev S{};
+    const int ns = dc->n_states[a];
+    if (ns < 1 || ns > kMaxStates) {
+      delete g;
+      return fail(XLS_EINVAL, "n_states out of range in subdomain " + std::to_string(a));
+    }
+    long long nd = 1;
+    for (int d = 0; d < 3; ++d) {
+      const int cl = dc->core_lo[3 * a + d], cn = dc->core_n[3 * a + d], b = dc->buf[3 * a + d];
+      if (cn < 1 || cn > cell->n[d] || b < 0 || cl < 0 || cl >= cell->n[d]) {
+        delete g;
+        return fail(XLS_EINVAL, "bad core/buffer in subdomain " + std::to_string(a));
+      }
+      int size = cn + 2 * b;
+      const bool per = size >= cell->n[d];
+      const int be = per ? std::min(b, (cell->n[d] - cn) / 2) : b;
+      if (per) size = cell->n[d];
+      S.n[d] = size;
+      S.periodic[d] = per ? 1 : 0;
+      S.start[d] = cl - be;
+      S.core_lo[d] = be;
+      S.core_n[d] = cn;
+      S.core_glo[d] = cl;
+      S.h[d] = g->gh[d];
+      nd *= size;
+    }
+    for (int d = 0; d < 3; ++d)
+      if (S.n[d] < 2 * kN0 + 1) {
+        delete g;
+        return fail(XLS_EINVAL, "subdomain shorter than 13 points along an axis");
+      }
+    S.ns = ns;
+    S.nd = nd;
+    S.dV = g->gh[0] * g->gh[1] * g->gh[2];
+    S.off_blk = g->tot_blk;
+    S.off_pt = g->tot_pts;
+    S.off_ss = g->tot_ss;
+    S.off_state = g->tot_states;
+    g->tot_blk += nd * ns;
+    g->tot_pts += nd;
+    g->tot_ss += (long long)ns * ns;
+    g->tot_states += ns;
+    g->max_ns = std::max(g->max_ns, ns);
+    g->max_nd = std::max(g->max_nd, nd);
+    g->max_core = std::max(g->max_core, (long long)S.core_n[0] * S.core_n[1] * S.core_n[2]);
+    covered += (long long)S.core_n[0] * S.core_n[1] * S.core_n[2];
+    g->subs.push_back(S);
+    SubDev S1 = S;
+    S1.ns = 1;
+    S1.off_blk = S.off_pt;
+    g->subs1.push_back(S1);
+  }
+  if (covered != (long long)cell->n[0] * cell->n[1] * cell->n[2]) {
+    delete g;
+    return fail(XLS_EINVAL, "cores do not tile the global grid exactly once");
+  }
+  xls_status s = XLS_OK;
+#define ALLOC(p, n)                         \
+  if ((s = g->alloc(&(p), (n))) != XLS_OK) { \
+    xls_grid_destroy(g);                    \
+    return s;                               \
+  }
+  for (int i = 0; i < 3; ++i) ALLOC(g->blk[i], g->tot_blk * g->elem);
+  ALLOC(g->V, g->tot_pts * sizeof(double));
+  ALLOC(g->Vf, g->tot_pts * sizeof(float));
+  ALLOC(g->Ms, g->tot_ss * sizeof(double));
+  ALLOC(g->Hs, g->tot_ss * sizeof(double));
+  ALLOC(g->Lb, g->tot_ss * sizeof(double));
+  ALLOC(g->Ab, g->tot_ss * sizeof(double));
+  ALLOC(g->W, g->tot_ss * sizeof(double));
+  ALLOC(g->Y, g->tot_ss * sizeof(double));
+  ALLOC(g->R, g->tot_ss * sizeof(double));
+  ALLOC(g->lam, g->tot_states * sizeof(double));
+  ALLOC(g->cw, g->tot_states * sizeof(double));
+  ALLOC(g->occ, g->tot_states * sizeof(double));
+  ALLOC(g->vecs, 8LL * g->tot_states * sizeof(double));
+  ALLOC(g->eig_scr, eig_scratch_doubles(g->n_sub, g->max_ns) * sizeof(double));
+  ALLOC(g->bounds, 3 * g->n_sub * sizeof(double));
+  ALLOC(g->coef, (size_t)g->n_sub * kMaxDegree * sizeof(StepCoef));
+  ALLOC(g->status, 2 * sizeof(int));
+  ALLOC(g->out4, 4 * sizeof(double));
+  ALLOC(g->lz_v, g->tot_pts * sizeof(double));
+  ALLOC(g->lz_vp, g->tot_pts * sizeof(double));
+  ALLOC(g->lz_f, g->tot_pts * sizeof(double));
+  ALLOC(g->lz_Hv, g->tot_pts * sizeof(double));
+  ALLOC(g->lz_a, 16 * g->n_sub * sizeof(double));
+  ALLOC(g->lz_b, 16 * g->n_sub * sizeof(double));
+  ALLOC(g->d_subs, g->n_sub * sizeof(SubDev));
+  ALLOC(g->d_subs1, g->n_sub * sizeof(SubDev));
+#undef ALLOC
+  if ((s = make_plan(g, g->subs, g->plan)) != XLS_OK || (s = make_plan(g, g->subs1, g->plan1)) != XLS_OK) {
+    xls_grid_destroy(g);
+    return s;
+  }
+  cudaMemset(g->status, 0, 2 * sizeof(int));
+  cudaMemset(g->lz_b, 0, 16 * g->n_sub * sizeof(double));
+  cudaMemset(g->cw, 0, g->tot_states * sizeof(double));
+  cudaMemset(g->lam, 0, g->tot_states * sizeof(double));
+  for (int i = 0; i < 6; ++i) cudaEventCreate(&g->ev[i]);
+  cudaError_t e = cudaMemcpy(g->d_subs, g->subs.data(), g->n_sub * sizeof(SubDev), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemcpy(g->d_subs1, g->subs1.data(), g->n_sub * sizeof(SubDev), cudaMemcpyHostToDevice);
+  if (e != cudaSuccess) {
+    xls_grid_destroy(g);
+    return fail(XLS_ECUDA, cudaGetErrorString(e));
+  }
+  *out = g;
+  return XLS_OK;
+}
+
+xls_status xls_grid_destroy(xls_grid g) {
+  if (!g) return XLS_OK;
+  if (g->st) cudaStreamSynchronize(g->st);
+  else cudaDeviceSynchronize();
+  for (void* p : g->allocs) cudaFree(p);
+  for (int i = 0; i < 6; ++i)
+    if (g->ev[i]) cudaEventDestroy(g->ev[i]);
+  for (auto& e : g->pev) cudaEventDestroy(e);
+  delete g;
+  return XLS_OK;
+}
+
+xls_status xls_hamiltonian_set(xls_grid g, const double* veff, int veff_on_device, int n_atoms, const double* pos,
+                               const int* species, int n_species, const xls_species* sp) {
+  if (!g || !veff || n_atoms < 0 || (n_atoms > 0 && (!pos || !species || !sp || n_species < 1)))
+    return fail(XLS_EINVAL, "xls_hamiltonian_set: bad arguments");
+  for (int i = 0; i < n_atoms; ++i)
+    if (species[i] < 0 || species[i] >= n_species) return fail(XLS_EINVAL, "species index out of range");
+  for (int s = 0; s < n_species; ++s)
+    for (int d = 0; d < 3; ++d)
+      if (!(sp[s].r_cut > 0) || !(sp[s].w_proj > 0) || 2 * sp[s].r_cut >= g->gL[d])
+        return fail(XLS_EINVAL, "projector cutoff must be positive and below half of every cell edge");
+  const long long ng = (long long)g->gn[0] * g->gn[1] * g->gn[2];
+  if (!g->Vg) {
+    xls_status s = g->alloc(&g->Vg, ng * sizeof(double));
+    if (s != XLS_OK) return s;
+  }
+  XLS_CUDA(cudaMemcpyAsync(g->Vg, veff, ng * sizeof(double),
+                           veff_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, g->st));
+  launch_restrict(g->d_subs, g->n_sub, g->max_nd, g->Vg, g->gn, g->V, g->Vf, g->st);
+  // projector normalisation on the global grid (one image per atom, wrapped box)
+  std::vector<double> norms(4 * (size_t)n_atoms, 1.0);
+  if (n_atoms > 0) {
+    std::vector<AtomImg> glob(n_atoms);
+    std::vector<ProjSlot> gslot(n_atoms);
+    for (int i = 0; i < n_atoms; ++i) {
+      const xls_species& q = sp[species[i]];
+      AtomImg& A = glob[i];
+      for (int d = 0; d < 3; ++d) {
+        double r = std::fmod(pos[3 * i + d], g->gL[d]);
+        if (r < 0) r += g->gL[d];
+        A.R[d] = r;
+        A.box_lo[d] = (int)std::floor((r - q.r_cut) / g->gh[d]);
+        A.box_n[d] = (int)std::ceil((r + q.r_cut) / g->gh[d]) - A.box_lo[d] + 1;
+      }
+      A.slot = i;
+      gslot[i] = ProjSlot{};
+      gslot[i].w = q.w_proj;
+      gslot[i].rcut2 = q.r_cut * q.r_cut;
+    }
+    AtomImg* dglob = nullptr;
+    ProjSlot* dgs = nullptr;
+    double* dn = nullptr;
+    XLS_CUDA(cudaMalloc(&dglob, n_atoms * sizeof(AtomImg)));
+    XLS_CUDA(cudaMalloc(&dgs, n_atoms * sizeof(ProjSlot)));
+    XLS_CUDA(cudaMalloc(&dn, 4 * (size_t)n_atoms * sizeof(double)));
+    XLS_CUDA(cudaMemcpyAsync(dglob, glob.data(), n_atoms * sizeof(AtomImg), cudaMemcpyHostToDevice, g->st));
+    XLS_CUDA(cudaMemcpyAsync(dgs, gslot.data(), n_atoms * sizeof(ProjSlot), cudaMemcpyHostToDevice, g->st));
+    launch_proj_norms(dglob, dgs, n_atoms, g->gn, g->gh, dn, g->st);
+    XLS_CUDA(cudaMemcpyAsync(norms.data(), dn, 4 * (size_t)n_atoms * sizeof(double), cudaMemcpyDeviceToHost, g->st));
+    XLS_CUDA(cudaStreamSynchronize(g->st));
+    cudaFree(dglob);
+    cudaFree(dgs);
+    cudaFree(dn);
+  }
+  // projector slots (atom x subdomain) and their periodic images
+  std::vector<AtomImg> imgs;
+  std::vector<ProjSlot> slots;
+  long long poff = 0;
+  for (int a = 0; a < g->n_sub; ++a) {
+    const size_t first = slots.size();
+    for (int i = 0; i < n_atoms; ++i) {
+      const xls_species& q = sp[species[i]];
+      const size_t before = imgs.size();
+      atom_images(g, a, pos + 3 * i, q, (int)slots.size(), imgs);
+      if (imgs.size() == before) continue;
+      ProjSlot Q{};
+      Q.sub = a;
+      Q.atom = i;
+      Q.img_lo = (int)before;
+      Q.img_n = (int)(imgs.size() - before);
+      Q.w = q.w_proj;
+      Q.rcut2 = q.r_cut * q.r_cut;
+      for (int l = 0; l < 4; ++l) Q.norm[l] = norms[4 * i + l];
+      Q.E[0] = q.E_s;
+      Q.E[1] = Q.E[2] = Q.E[3] = q.E_p;
+      slots.push_back(Q);
+    }
+    g->subs[a].slot_lo = g->subs1[a].slot_lo = (int)first;
+    g->subs[a].slot_n = g->subs1[a].slot_n = (int)(slots.size() - first);
+    g->subs[a].off_proj = poff;
+    poff += 4LL * g->subs[a].ns * g->subs[a].slot_n;
+    g->subs1[a].off_proj = 4LL * (long long)first;
+  }
+  g->release(&g->d_imgs);
+  g->release(&g->d_slots);
+  g->release(&g->P);
+  g->release(&g->P1);
+  g->n_slot = (int)slots.size();
+  xls_status s;
+  if ((s = g->alloc(&g->d_imgs, imgs.size() * sizeof(AtomImg))) != XLS_OK) return s;
+  if ((s = g->alloc(&g->d_slots, slots.size() * sizeof(ProjSlot))) != XLS_OK) return s;
+  if ((s = g->alloc(&g->P, std::max<long long>(poff, 1) * sizeof(double))) != XLS_OK) return s;
+  if ((s = g->alloc(&g->P1, std::max<size_t>(4 * slots.size(), 1) * sizeof(double))) != XLS_OK) return s;
+  if (!imgs.empty())
+    XLS_CUDA(cudaMemcpyAsync(g->d_imgs, imgs.data(), imgs.size() * sizeof(AtomImg), cudaMemcpyHostToDevice, g->st));
+  if (!slots.empty())
+    XLS_CUDA(cudaMemcpyAsync(g->d_slots, slots.data(), slots.size() * sizeof(ProjSlot), cudaMemcpyHostToDevice, g->st));
+  XLS_CUDA(cudaMemcpyAsync(g->d_subs, g->subs.data(), g->n_sub * sizeof(SubDev), cudaMemcpyHostToDevice, g->st));
+  XLS_CUDA(cudaMemcpyAsync(g->d_subs1, g->subs1.data(), g->n_sub * sizeof(SubDev), cudaMemcpyHostToDevice, g->st));
+  // unit coefficients (plain H) for every subdomain, then the Lanczos bound b
+  std::vector<double> bz(3 * g->n_sub, 1.0);
+  for (int a = 0; a < g->n_sub; ++a) { bz[3 * a] = 2.0; bz[3 * a + 1] = 1.0; bz[3 * a + 2] = 0.0; }
+  XLS_CUDA(cudaMemcpyAsync(g->bounds, bz.data(), bz.size() * sizeof(double), cudaMemcpyHostToDevice, g->st));
+  launch_filter_coef(g->n_sub, g->bounds, 1, g->coef, g->st);
+  XLS_TRY(lanczos_bounds(g));
+  g->ham_set = true;
+  g->have_ritz = false;
+  return XLS_OK;
+}
+
+xls_status xls_orbitals_set(xls_grid g, int sub, const double* psi, int on_device) {
+  if (!g || !psi || sub < 0 || sub >= g->n_sub) return fail(XLS_EINVAL, "xls_orbitals_set: bad arguments");
+  const SubDev& S = g->subs[sub];
+  const long long n = S.nd * S.ns;
+  const cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+  if (g->prec == XLS_FP64) {
+    XLS_CUDA(cudaMemcpyAsync((double*)g->blk[g->cur] + S.off_blk, psi, n * sizeof(double), kind, g->st));
+  } else {
+    // stage through the free block (as doubles) and round to FP32
+    double* tmp = (double*)g->blk[(g->cur + 1) % 3];
+    const long long cap = g->tot_blk / 2;  // doubles that fit in a float block
+    for (long long o = 0; o < n; o += cap) {
+      const long long c = std::min(cap, n - o);
+      XLS_CUDA(cudaMemcpyAsync(tmp, psi + o, c * sizeof(double), kind, g->st));
+      launch_convert_f64_f32(tmp, (float*)g->blk[g->cur] + S.off_blk + o, c, g->st);
+    }
+  }
+  XLS_CUDA(cudaStreamSynchronize(g->st));
+  g->orb_set = true;
+  g->have_ritz = false;
+  return XLS_OK;
+}
+
+xls_status xls_orbitals_random(xls_grid g, uint64_t seed) {
+  if (!g) return fail(XLS_EINVAL, "null grid");
+  if (g->prec == XLS_FP64) launch_splitmix_fill_f64((double*)g->blk[g->cur], g->tot_blk, seed, 0, g->st);
+  else launch_splitmix_fill_f32((float*)g->blk[g->cur], g->tot_blk, seed, 0, g->st);
+  XLS_CUDA(cudaGetLastError());
+  g->orb_set = true;
+  g->have_ritz = false;
+  return XLS_OK;
+}
+
+xls_status xls_orbitals_get(xls_grid g, int sub, double* psi_out, int on_device) {
+  if (!g || !psi_out || sub < 0 || sub >= g->n_sub) return fail(XLS_EINVAL, "xls_orbitals_get: bad arguments");
+  const SubDev& S = g->subs[sub];
+  const long long n = S.nd * S.ns;
+  const cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+  if (g->prec == XLS_FP64) {
+    XLS_CUDA(cudaMemcpyAsync(psi_out, (double*)g->blk[g->cur] + S.off_blk, n * sizeof(double), kind, g->st));
+  } else {
+    double* tmp = (double*)g->blk[(g->cur + 1) % 3];
+    const long long cap = g->tot_blk / 2;
+    for (long long o = 0; o < n; o += cap) {
+      const long long c = std::min(cap, n - o);
+      launch_convert_f32_f64((float*)g->blk[g->cur] + S.off_blk + o, tmp, c, g->st);
+      XLS_CUDA(cudaMemcpyAsync(psi_out + o, tmp, c * sizeof(double), kind, g->st));
+    }
+  }
+  XLS_CUDA(cudaStreamSynchronize(g->st));
+  return XLS_OK;
+}
+
+xls_status xls_chefsi_batch(xls_grid g, int degree, int n_passes, const double* bounds) {
+  if (!g || degree < 1 || degree >= kMaxDegree - 1 || n_passes < 0) return fail(XLS_EINVAL, "xls_chefsi_batch: bad arguments");
+  if (!g->ham_set || !g->orb_set) return fail(XLS_EINVAL, "xls_chefsi_batch: Hamiltonian or orbitals not set");
+  return g->prec == XLS_FP64 ? chefsi<double>(g, degree, n_passes, bounds) : chefsi<float>(g, degree, n_passes, bounds);
+}
+
+xls_status xls_chefsi_stage(xls_grid g, int which, int degree, const double* bounds) {
+  if (!g || degree < 1 || degree >= kMaxDegree - 1) return fail(XLS_EINVAL, "xls_chefsi_stage: bad arguments");
+  if (!g->ham_set || !g->orb_set) return fail(XLS_EINVAL, "xls_chefsi_stage: Hamiltonian or orbitals not set");
+  return g->prec == XLS_FP64 ? stage<double>(g, which, degree, bounds) : stage<float>(g, which, degree, bounds);
+}
+
+xls_status xls_hamiltonian_apply(xls_grid g, int sub, int k, const double* x, double* y, int on_device) {
+  if (!g || !x || !y || sub < 0 || sub >= g->n_sub || k < 1 || k > g->subs[sub].ns)
+    return fail(XLS_EINVAL, "xls_hamiltonian_apply: bad arguments");
+  if (!g->ham_set) return fail(XLS_EINVAL, "xls_hamiltonian_apply: Hamiltonian not set");
+  const SubDev& S = g->subs[sub];
+  const long long n = S.nd * k;
+  const int in = (g->cur + 1) % 3, outb = (g->cur + 2) % 3;
+  XLS_CUDA(cudaMemsetAsync(g->blk[in], 0, g->tot_blk * g->elem, g->st));
+  const cudaMemcpyKind kin = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+  const cudaMemcpyKind kout = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+  if (g->prec == XLS_FP64) {
+    XLS_CUDA(cudaMemcpyAsync((double*)g->blk[in] + S.off_blk, x, n * sizeof(double), kin, g->st));
+    h_step<double>(g, false, (double*)g->blk[in], nullptr, (double*)g->blk[outb], kUnitStep);
+    XLS_CUDA(cudaMemcpyAsync(y, (double*)g->blk[outb] + S.off_blk, n * sizeof(double), kout, g->st));
+  } else {
+    double* tmp = (double*)g->blk[g->cur];  // orbitals are clobbered on the mixed path's staging
+    (void)tmp;
+    double* dtmp = nullptr;
+    XLS_CUDA(cudaMalloc(&dtmp, n * sizeof(double)));
+    XLS_CUDA(cudaMemcpyAsync(dtmp, x, n * sizeof(double), kin, g->st));
+    launch_convert_f64_f32(dtmp, (float*)g->blk[in] + S.off_blk, n, g->st);
+    h_step<float>(g, false, (float*)g->blk[in], nullptr, (float*)g->blk[outb], kUnitStep);
+    launch_convert_f32_f64((float*)g->blk[outb] + S.off_blk, dtmp, n, g->st);
+    XLS_CUDA(cudaMemcpyAsync(y, dtmp, n * sizeof(double), kout, g->st));
+    XLS_CUDA(cudaStreamSynchronize(g->st));
+    cudaFree(dtmp);
+  }
+  XLS_CUDA(cudaStreamSynchronize(g->st));
+  return XLS_OK;
+}
+
+xls_status xls_density(xls_grid g, double n_electrons, double kT, double* mu_out, double* rho_out, int rho_on_device,
+                       double* e_band_out, double* e_entropy_out) {
+  if (!g || !(kT > 0) || !g->have_ritz) return fail(XLS_EINVAL, "xls_density: bad arguments or no pass run yet");
+  launch_fermi_occ(g->lam, g->cw, g->tot_states, n_electrons, kT, g->out4, g->occ, g->status, g->st);
+  XLS_TRY(check_status(g));
+  double h4[4];
+  XLS_CUDA(cudaMemcpy(h4, g->out4, sizeof(h4), cudaMemcpyDeviceToHost));
+  if (mu_out) *mu_out = h4[0];
+  if (e_band_out) *e_band_out = h4[1];
+  if (e_entropy_out) *e_entropy_out = h4[2];
+  if (rho_out) {
+    const long long ng = (long long)g->gn[0] * g->gn[1] * g->gn[2];
+    if (!g->rho) XLS_TRY(g->alloc(&g->rho, ng * sizeof(double)));
+    if (g->prec == XLS_FP64)
+      launch_density_occ<double>(g->d_subs, g->n_sub, g->max_core, (const double*)g->blk[g->cur], g->occ, g->gn, g->rho, g->st);
+    else
+      launch_density_occ<float>(g->d_subs, g->n_sub, g->max_core, (const float*)g->blk[g->cur], g->occ, g->gn, g->rho, g->st);
+    XLS_CUDA(cudaMemcpyAsync(rho_out, g->rho, ng * sizeof(double),
+                             rho_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, g->st));
+    XLS_CUDA(cudaStreamSynchronize(g->st));
+  }
+  return XLS_OK;
+}
+
+xls_status xls_get_eigs(xls_grid g, int sub, double* lambda_out, double* c_out) {
+  if (!g || sub < 0 || sub >= g->n_sub) return fail(XLS_EINVAL, "xls_get_eigs: bad arguments");
+  const SubDev& S = g->subs[sub];
+  XLS_CUDA(cudaStreamSynchronize(g->st));
+  if (lambda_out) XLS_CUDA(cudaMemcpy(lambda_out, g->lam + S.off_state, S.ns * sizeof(double), cudaMemcpyDeviceToHost));
+  if (c_out) XLS_CUDA(cudaMemcpy(c_out, g->cw + S.off_state, S.ns * sizeof(double), cudaMemcpyDeviceToHost));
+  return XLS_OK;
+}
+
+xls_status xls_get_subspace(xls_grid g, int sub, double* Ms_out, double* Hs_out) {
+  if (!g || sub < 0 || sub >= g->n_sub) return fail(XLS_EINVAL, "xls_get_subspace: bad arguments");
+  const SubDev& S = g->subs[sub];
+  XLS_CUDA(cudaStreamSynchronize(g->st));
+  const size_t b = (size_t)S.ns * S.ns * sizeof(double);
+  if (Ms_out) XLS_CUDA(cudaMemcpy(Ms_out, g->Ms + S.off_ss, b, cudaMemcpyDeviceToHost));
+  if (Hs_out) XLS_CUDA(cudaMemcpy(Hs_out, g->Hs + S.off_ss, b, cudaMemcpyDeviceToHost));
+  return XLS_OK;
+}
+
+xls_status xls_get_bounds(xls_grid g, double* bounds_out) {
+  if (!g || !bounds_out) return fail(XLS_EINVAL, "xls_get_bounds: bad arguments");
+  XLS_CUDA(cudaStreamSynchronize(g->st));
+  XLS_CUDA(cudaMemcpy(bounds_out, g->bounds, 3 * g->n_sub * sizeof(double), cudaMemcpyDeviceToHost));
+  return XLS_OK;
+}
+
+xls_status xls_set_profiling(xls_grid g, int on) {
+  if (!g) return fail(XLS_EINVAL, "null grid");
+  g->profiling = on != 0;
+  if (g->profiling && g->pev.empty()) {
+    g->pev.resize(4096);
+    g->pcls.resize(2048);
+    for (auto& e : g->pev) XLS_CUDA(cudaEventCreate(&e));
+  }
+  return XLS_OK;
+}
+
+xls_status xls_get_kernel_times(xls_grid g, double* ms8_out, int* count8_out) {
+  if (!g) return fail(XLS_EINVAL, "null grid");
+  for (int c = 0; c < 8; ++c) {
+    if (ms8_out) ms8_out[c] = g->kms[c];
+    if (count8_out) count8_out[c] = g->kcnt[c];
+  }
+  return XLS_OK;
+}
+
+xls_status xls_get_timings(xls_grid g, double* ms4_out, int* launches_out) {
+  if (!g) return fail(XLS_EINVAL, "null grid");
+  if (ms4_out)
+    for (int i = 0; i < 4; ++i) ms4_out[i] = g->stage_ms[i];
+  if (launches_out) *launches_out = g->last_launches;
+  return XLS_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,253 @@
+"""Thin ctypes binding of libxls (include/xls.h): the same entry points, argument marshalling only.
+
+Host arrays are numpy arrays (float64 / int32, C-contiguous); device arrays are torch CUDA
+tensors (their data_ptr is passed with the on_device flag set).  Every call raises XlsError
+with the library's message when the status is not XLS_OK.  There is no fallback: if the
+shared library is missing the import-time loader raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from ctypes import POINTER, byref, c_double, c_int, c_size_t, c_uint64, c_void_p
+
+import numpy as np
+
+LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "_lib", "libxls.so")
+
+XLS_OK, XLS_EINVAL, XLS_ENOMEM, XLS_ECUDA, XLS_ENOTSPD, XLS_ENOCONV, XLS_ETIMEOUT, XLS_ENONFINITE = range(8)
+XLS_FP64, XLS_MIXED_BF16 = 0, 1
+STATUS_NAMES = {0: "XLS_OK", 1: "XLS_EINVAL", 2: "XLS_ENOMEM", 3: "XLS_ECUDA", 4: "XLS_ENOTSPD",
+                5: "XLS_ENOCONV", 6: "XLS_ETIMEOUT", 7: "XLS_ENONFINITE"}
+
+
+class XlsError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{STATUS_NAMES.get(status, status)}: {msg}")
+        self.status = status
+
+
+class XlsCell(ctypes.Structure):
+    _fields_ = [("L", c_double * 3), ("n", c_int * 3)]
+
+
+class XlsDC(ctypes.Structure):
+    _fields_ = [("n_sub", c_int), ("core_lo", POINTER(c_int)), ("core_n", POINTER(c_int)),
+                ("buf", POINTER(c_int)), ("n_states", POINTER(c_int))]
+
+
+class XlsSpecies(ctypes.Structure):
+    _fields_ = [("Zv", c_double), ("rc_loc", c_double), ("w_proj", c_double), ("r_cut", c_double),
+                ("E_s", c_double), ("E_p", c_double)]
+
+
+_SIGS = {
+    "xls_grid_create": (c_int, [POINTER(XlsCell), POINTER(XlsDC), c_int, c_size_t, c_void_p, POINTER(c_void_p)]),
+    "xls_grid_destroy": (c_int, [c_void_p]),
+    "xls_hamiltonian_set": (c_int, [c_void_p, c_void_p, c_int, c_int, c_void_p, c_void_p, c_int,
+                                    POINTER(XlsSpecies)]),
+    "xls_orbitals_set": (c_int, [c_void_p, c_int, c_void_p, c_int]),
+    "xls_orbitals_random": (c_int, [c_void_p, c_uint64]),
+    "xls_orbitals_get": (c_int, [c_void_p, c_int, c_void_p, c_int]),
+    "xls_chefsi_batch": (c_int, [c_void_p, c_int, c_int, c_void_p]),
+    "xls_chefsi_stage": (c_int, [c_void_p, c_int, c_int, c_void_p]),
+    "xls_hamiltonian_apply": (c_int, [c_void_p, c_int, c_int, c_void_p, c_void_p, c_int]),
+    "xls_density": (c_int, [c_void_p, c_double, c_double, POINTER(c_double), c_void_p, c_int,
+                            POINTER(c_double), POINTER(c_double)]),
+    "xls_get_eigs": (c_int, [c_void_p, c_int, c_void_p, c_void_p]),
+    "xls_get_subspace": (c_int, [c_void_p, c_int, c_void_p, c_void_p]),
+    "xls_get_bounds": (c_int, [c_void_p, c_void_p]),
+    "xls_get_timings": (c_int, [c_void_p, c_void_p, POINTER(c_int)]),
+    "xls_set_profiling": (c_int, [c_void_p, c_int]),
+    "xls_get_kernel_times": (c_int, [c_void_p, c_void_p, c_void_p]),
+    "xls_last_error": (ctypes.c_char_p, []),
+}
+
+_lib = None
+
+
+def load(path: str = LIB_PATH) -> ctypes.CDLL:
+    """Load libxls.so (built by paper_2609_13115_gb300.build); raises if it is missing."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise RuntimeError(f"libxls.so not found at {path}: build it with paper_2609_13115_gb300.build.build()")
+    lib = ctypes.CDLL(path)
+    for name, (res, args) in _SIGS.items():
+        f = getattr(lib, name)
+        f.restype = res
+        f.argtypes = args
+    _lib = lib
+    return lib
+
+
+def exported_symbols() -> list:
+    return list(_SIGS)
+
+
+def _check(status: int):
+    if status != XLS_OK:
+        raise XlsError(status, load().xls_last_error().decode())
+
+
+def _ptr(a):
+    """(pointer, on_device) of a numpy array or a torch tensor; None -> (None, 0)."""
+    if a is None:
+        return None, 0
+    if isinstance(a, np.ndarray):
+        if not a.flags.c_contiguous:
+            raise ValueError("arrays must be C-contiguous")
+        return a.ctypes.data_as(c_void_p), 0
+    if hasattr(a, "data_ptr"):
+        if not a.is_contiguous():
+            raise ValueError("tensors must be contiguous")
+        return c_void_p(a.data_ptr()), 1 if a.is_cuda else 0
+    raise TypeError(f"unsupported array type {type(a)}")
+
+
+def _i32(a):
+    return np.ascontiguousarray(np.asarray(a, dtype=np.int32).ravel())
+
+
+def xls_grid_create(L, n, core_lo, core_n, buf, n_states, precision=XLS_FP64, hbm_budget_bytes=0, stream=None):
+    lib = load()
+    cell = XlsCell((c_double * 3)(*[float(x) for x in L]), (c_int * 3)(*[int(x) for x in n]))
+    arrs = [_i32(core_lo), _i32(core_n), _i32(buf), _i32(n_states)]
+    dc = XlsDC(len(arrs[3]), *[a.ctypes.data_as(POINTER(c_int)) for a in arrs])
+    h = c_void_p()
+    _check(lib.xls_grid_create(byref(cell), byref(dc), int(precision), int(hbm_budget_bytes),
+                               c_void_p(stream) if stream else None, byref(h)))
+    return h
+
+
+def xls_grid_destroy(g):
+    _check(load().xls_grid_destroy(g))
+
+
+def species_array(species) -> ctypes.Array:
+    arr = (XlsSpecies * len(species))()
+    for i, s in enumerate(species):
+        arr[i] = XlsSpecies(s.Zv, s.rc_loc, s.w_proj, s.r_cut, s.E_s, s.E_p)
+    return arr
+
+
+def xls_hamiltonian_set(g, veff, pos, species_index, species):
+    v = np.ascontiguousarray(veff, dtype=np.float64) if isinstance(veff, np.ndarray) else veff
+    vp, vdev = _ptr(v)
+    p = np.ascontiguousarray(pos, dtype=np.float64).ravel()
+    s = _i32(species_index)
+    sp = species_array(species)
+    _check(load().xls_hamiltonian_set(g, vp, vdev, len(s), p.ctypes.data_as(c_void_p), s.ctypes.data_as(c_void_p),
+                                      len(species), sp))
+
+
+def xls_orbitals_set(g, sub, psi):
+    a = np.ascontiguousarray(psi, dtype=np.float64) if isinstance(psi, np.ndarray) else psi
+    p, dev = _ptr(a)
+    _check(load().xls_orbitals_set(g, int(sub), p, dev))
+
+
+def xls_orbitals_random(g, seed):
+    _check(load().xls_orbitals_random(g, int(seed)))
+
+
+def xls_orbitals_get(g, sub, out):
+    p, dev = _ptr(out)
+    _check(load().xls_orbitals_get(g, int(sub), p, dev))
+    return out
+
+
+def xls_chefsi_batch(g, degree, n_passes, bounds=None):
+    b = None if bounds is None else np.ascontiguousarray(bounds, dtype=np.float64).ravel()
+    _check(load().xls_chefsi_batch(g, int(degree), int(n_passes), None if b is None else b.ctypes.data_as(c_void_p)))
+
+
+def xls_chefsi_stage(g, stage, degree, bounds=None):
+    b = None if bounds is None else np.ascontiguousarray(bounds, dtype=np.float64).ravel()
+    _check(load().xls_chefsi_stage(g, int(stage), int(degree), None if b is None else b.ctypes.data_as(c_void_p)))
+
+
+def xls_hamiltonian_apply(g, sub, x, y):
+    xp, dev = _ptr(x)
+    yp, dev2 = _ptr(y)
+    if dev != dev2:
+        raise ValueError("x and y must both be host or both be device arrays")
+    k = x.shape[0] if x.ndim == 2 else 1
+    _check(load().xls_hamiltonian_apply(g, int(sub), int(k), xp, yp, dev))
+    return y
+
+
+def xls_density(g, n_electrons, kT, rho_out=None):
+    mu, eb, es = c_double(), c_double(), c_double()
+    rp, dev = _ptr(rho_out)
+    _check(load().xls_density(g, float(n_electrons), float(kT), byref(mu), rp, dev, byref(eb), byref(es)))
+    return mu.value, eb.value, es.value
+
+
+def xls_get_eigs(g, sub, n_states):
+    lam = np.zeros(n_states)
+    c = np.zeros(n_states)
+    _check(load().xls_get_eigs(g, int(sub), lam.ctypes.data_as(c_void_p), c.ctypes.data_as(c_void_p)))
+    return lam, c
+
+
+def xls_get_subspace(g, sub, n_states):
+    Ms = np.zeros((n_states, n_states))
+    Hs = np.zeros((n_states, n_states))
+    _check(load().xls_get_subspace(g, int(sub), Ms.ctypes.data_as(c_void_p), Hs.ctypes.data_as(c_void_p)))
+    return Ms, Hs
+
+
+def xls_get_bounds(g, n_sub):
+    b = np.zeros(3 * n_sub)
+    _check(load().xls_get_bounds(g, b.ctypes.data_as(c_void_p)))
+    return b.reshape(n_sub, 3)
+
+
+def xls_get_timings(g):
+    ms = np.zeros(4)
+    n = c_int()
+    _check(load().xls_get_timings(g, ms.ctypes.data_as(c_void_p), byref(n)))
+    return ms, n.value
+
+
+def xls_set_profiling(g, on):
+    _check(load().xls_set_profiling(g, int(bool(on))))
+
+
+def xls_get_kernel_times(g):
+    ms = np.zeros(8)
+    cnt = np.zeros(8, dtype=np.int32)
+    _check(load().xls_get_kernel_times(g, ms.ctypes.data_as(c_void_p), cnt.ctypes.data_as(c_void_p)))
+    return ms, cnt
+
+
+class Grid:
+    """Owner of an xls_grid handle built from a synthetic workload description (any object
+    with L, n, core_lo, core_n, buf, n_states, pos, species_index, species attributes)."""
+
+    def __init__(self, w, precision=XLS_FP64, hbm_budget_bytes=0, stream=None):
+        self.w = w
+        self.precision = precision
+        self.h = xls_grid_create(w.L, w.n, w.core_lo, w.core_n, w.buf, w.n_states, precision, hbm_budget_bytes, stream)
+
+    def close(self):
+        if self.h is not None:
+            xls_grid_destroy(self.h)
+            self.h = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_hamiltonian(self, veff):
+        xls_hamiltonian_set(self.h, veff, self.w.pos, self.w.species_index, self.w.species)
