@@ -250,25 +250,35 @@ k_fermi(const double* __restrict__ lam, const double* __restrict__ c, int n, dou
     s_hi = b + 1.0;
   }
   __syncthreads();
-  auto count = [&](double mu) -> double {
-    double acc = 0.0;
-    for (int i = threadIdx.x; i < n; i += blockDim.x) acc += fermi_fn((lam[i] - mu) / kT) * c[i];
+  // N_e(mu) and dN_e/dmu in one sweep (the paper's Newton refinement, Sec. 5.A.5), safeguarded by
+  // the bracket: a Newton step outside (lo, hi) is replaced by bisection.
+  auto count2 = [&](double mu, double& dn) -> double {
+    double acc = 0.0, dacc = 0.0;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+      const double g = fermi_fn((lam[i] - mu) / kT);
+      acc += g * c[i];
+      dacc += g * (1.0 - g) * c[i];
+    }
+    dn = 2.0 * block_sum(dacc, red) / kT;
     return 2.0 * block_sum(acc, red);
   };
-  double lo = s_lo, hi = s_hi;
-  const double nlo = count(lo), nhi = count(hi);
+  double lo = s_lo, hi = s_hi, dn;
+  const double nlo = count2(lo, dn), nhi = count2(hi, dn);
   if (!(nlo <= ne && ne <= nhi)) {
     if (threadIdx.x == 0) { *status = XLS_ENOCONV; out[0] = out[1] = out[2] = out[3] = 0.0; }
     return;
   }
+  double mu_k = 0.5 * (lo + hi);
   for (int it = 0; it < 200; ++it) {
-    if (hi - lo <= 1e-14) break;
-    const double mid = 0.5 * (lo + hi);
-    if (mid == lo || mid == hi) break;
-    const double nm = count(mid);
-    if (nm < ne) lo = mid; else hi = mid;
+    const double nm = count2(mu_k, dn);
+    if (nm < ne) lo = mu_k; else hi = mu_k;
+    if (nm == ne || hi - lo <= 1e-14) break;
+    double next = (dn > 0.0) ? mu_k - (nm - ne) / dn : 0.5 * (lo + hi);
+    if (!(next > lo && next < hi)) next = 0.5 * (lo + hi);
+    if (fabs(next - mu_k) <= 1e-15 * fmax(1.0, fabs(mu_k))) { mu_k = next; break; }
+    mu_k = next;
   }
-  const double mu = 0.5 * (lo + hi);
+  const double mu = mu_k;
   double eb = 0.0, es = 0.0, nn = 0.0;
   for (int i = threadIdx.x; i < n; i += blockDim.x) {
     const double g = fermi_fn((lam[i] - mu) / kT);

@@ -16,7 +16,6 @@
 
 namespace xls {
 
-constexpr int kEigScratchThreads = 64;
 
 __device__ __forceinline__ double warp_sum(double v) {
 #pragma unroll
@@ -41,10 +40,17 @@ __device__ void set_status(int* status, int code, int sub) {
 }
 
 // ---- 1. Cholesky, left-looking by columns; warp per row for the column update -------------
+template <bool kSmem>
 __global__ void __launch_bounds__(512) k_cholesky(const SubDev* __restrict__ subs, double* Ms, int* status) {
   const SubDev& S = subs[blockIdx.x];
   const int n = S.ns;
-  double* L = Ms + S.off_ss;
+  double* Lg = Ms + S.off_ss;
+  extern __shared__ double smat[];
+  double* L = kSmem ? smat : Lg;
+  if (kSmem) {
+    for (long long q = threadIdx.x; q < (long long)n * n; q += blockDim.x) L[q] = Lg[q];
+    __syncthreads();
+  }
   __shared__ double red[32];
   __shared__ double s_piv;
   __shared__ int s_fail;
@@ -79,7 +85,7 @@ __global__ void __launch_bounds__(512) k_cholesky(const SubDev* __restrict__ sub
   // clear the strict upper triangle
   for (long long q = threadIdx.x; q < (long long)n * n; q += blockDim.x) {
     const int i = (int)(q / n), k = (int)(q % n);
-    if (k > i) L[q] = 0.0;
+    Lg[q] = (k > i) ? 0.0 : L[q];
   }
 }
 
@@ -113,16 +119,22 @@ k_trsm(const SubDev* __restrict__ subs, const double* __restrict__ Lm, const dou
 
 // ---- 3. Householder tridiagonalisation of A (lower, reflectors kept below the subdiagonal) -
 // vec layout (8n per subdomain): d[0..n), e[n..2n), tau[2n..3n), lam32[3n..4n), cluster[4n..5n)
-__global__ void __launch_bounds__(512) k_tridiag(const SubDev* __restrict__ subs, double* Am, double* vecs) {
+template <bool kSmem>
+__global__ void __launch_bounds__(512) k_tridiag(const SubDev* __restrict__ subs, double* Am, double* vecs, int max_ns) {
   const SubDev& S = subs[blockIdx.x];
   const int n = S.ns;
-  double* A = Am + S.off_ss;
+  double* Ag = Am + S.off_ss;
   double* d = vecs + 8LL * S.off_state;
   double* e = d + n;
   double* tau = d + 2 * n;
   extern __shared__ double sm[];
   double* sv = sm;          // reflector v (length <= n)
-  double* sw = sm + n;      // p, then w
+  double* sw = sm + max_ns; // p, then w
+  double* A = kSmem ? sm + 2 * max_ns : Ag;
+  if (kSmem) {
+    for (long long q = threadIdx.x; q < (long long)n * n; q += blockDim.x) A[q] = Ag[q];
+    __syncthreads();
+  }
   __shared__ double red[32];
   __shared__ double s_tau, s_K;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nwarp = blockDim.x >> 5;
@@ -197,6 +209,13 @@ __global__ void __launch_bounds__(512) k_tridiag(const SubDev* __restrict__ subs
     e[n - 1] = 0.0;
     tau[n - 1] = 0.0;
   }
+  if (kSmem) {  // reflectors (below the subdiagonal) back to global memory for the back-transformation
+    __syncthreads();
+    for (long long q = threadIdx.x; q < (long long)n * n; q += blockDim.x) {
+      const int i = (int)(q / n), k = (int)(q % n);
+      if (i > k + 1) Ag[q] = A[q];
+    }
+  }
 }
 
 // ---- 4. eigenpairs of the tridiagonal T ----------------------------------------------------
@@ -223,16 +242,16 @@ __device__ __forceinline__ double hash_unit(unsigned a, unsigned b) {
   return (double)(h & 0xFFFFFFu) * (1.0 / 16777216.0) - 0.5;
 }
 
-// y = T x (tridiagonal, FP64)
-__device__ __forceinline__ double tri_mv(const double* d, const double* e, const double* x, int n, int j) {
-  double s = d[j] * x[j];
-  if (j > 0) s += e[j - 1] * x[j - 1];
-  if (j + 1 < n) s += e[j] * x[j + 1];
-  return s;
-}
+// Eigenpairs of T.  Shifts: FP32 Sturm bisection per index.  Vectors: FP64 inverse iteration
+// with an LDL^T factorisation of T - sigma I (tiny pivots replaced by +-1e-15 |T|), one
+// thread per cluster of close eigenvalues; members of a cluster are Gram-Schmidt-orthogonalised
+// against the earlier ones at every iteration and finally Rayleigh-Ritz-rotated inside the
+// cluster (Jacobi on the k x k projected T).  Per-thread work arrays are interleaved across the
+// threads of the block (element j of thread t at [j * blockDim + t]) so that the warps' accesses
+// coalesce.
+constexpr int kTriThreads = 128;
 
-// Per-thread scratch: m_[n], U0[n], U1[n], U2[n], piv(as double)[n], x[n]  (6n doubles)
-__global__ void __launch_bounds__(kEigScratchThreads)
+__global__ void __launch_bounds__(kTriThreads)
 k_tri_eig(const SubDev* __restrict__ subs, double* vecs, double* Zm, double* scratch_all, long long scr_stride,
           double* Rm, double* lam_out) {
   const SubDev& S = subs[blockIdx.x];
@@ -240,14 +259,15 @@ k_tri_eig(const SubDev* __restrict__ subs, double* vecs, double* Zm, double* scr
   double* d = vecs + 8LL * S.off_state;
   double* e = d + n;
   double* lam32 = d + 3 * n;
-  double* cl = d + 4 * n;  // cluster start flags
   double* Z = Zm + S.off_ss;
   double* Rb = Rm + S.off_ss;
   extern __shared__ float smf[];
   float* df = smf;
   float* e2f = smf + n;
+  int* cstart = (int*)(smf + 2 * n);   // n + 1 cluster starts
   __shared__ float s_gl, s_gu, s_pivmin;
   __shared__ double s_tnorm;
+  __shared__ int s_ncl;
   for (int i = threadIdx.x; i < n; i += blockDim.x) {
     df[i] = (float)d[i];
     e2f[i] = (float)(e[i] * e[i]);
@@ -268,7 +288,6 @@ k_tri_eig(const SubDev* __restrict__ subs, double* vecs, double* Zm, double* scr
     s_pivmin = (float)fmax(1e-30, 1e-30 * emax2);
   }
   __syncthreads();
-  // FP32 bisection for every eigenvalue index
   for (int i = threadIdx.x; i < n; i += blockDim.x) {
     float lo = s_gl, hi = s_gu;
     for (int it = 0; it < 48; ++it) {
@@ -282,80 +301,82 @@ k_tri_eig(const SubDev* __restrict__ subs, double* vecs, double* Zm, double* scr
   const double tnorm = s_tnorm;
   const double ctol = 1e-4 * tnorm;
   if (threadIdx.x == 0) {
-    for (int i = 0; i < n; ++i) cl[i] = (i == 0 || lam32[i] - lam32[i - 1] > ctol) ? 1.0 : 0.0;
+    int c = 0;
+    for (int i = 0; i < n; ++i)
+      if (i == 0 || lam32[i] - lam32[i - 1] > ctol) cstart[c++] = i;
+    cstart[c] = n;
+    s_ncl = c;
   }
   __syncthreads();
-  double* scr = scratch_all + ((long long)blockIdx.x * kEigScratchThreads + threadIdx.x) * scr_stride;
-  double* mlt = scr;
-  double* U0 = scr + n;
-  double* U1 = scr + 2 * n;
-  double* U2 = scr + 3 * n;
-  double* pv = scr + 4 * n;
-  double* x = scr + 5 * n;
+  const int T = blockDim.x, t = threadIdx.x;
+  double* scr = scratch_all + (long long)blockIdx.x * scr_stride;
+  // interleaved arrays: lm (n), dinv (n), x (n)
+  auto LM = [&](int j) -> double& { return scr[(long long)j * T + t]; };
+  auto DI = [&](int j) -> double& { return scr[(long long)(n + j) * T + t]; };
+  auto X = [&](int j) -> double& { return scr[(long long)(2 * n + j) * T + t]; };
   const double tiny = 1e-15 * tnorm;
-  // clusters are handed out round-robin by their index among cluster starts
-  int cidx = -1;
-  for (int s = 0; s < n; ++s) {
-    if (cl[s] == 0.0) continue;
-    ++cidx;
-    if (cidx % (int)blockDim.x != (int)threadIdx.x) continue;
-    int t = s + 1;
-    while (t < n && cl[t] == 0.0) ++t;
-    const int k = t - s;
-    for (int mbr = s; mbr < t; ++mbr) {
-      const double sigma = lam32[mbr];
-      // LU with partial pivoting of T - sigma I
-      double r0 = d[0] - sigma, r1 = (n > 1) ? e[0] : 0.0;
-      for (int i = 0; i + 1 < n; ++i) {
-        const double n0 = e[i], n1 = d[i + 1] - sigma, n2 = (i + 2 < n) ? e[i + 1] : 0.0;
-        double P0, P1, P2, O0, O1, O2;
-        if (fabs(n0) > fabs(r0)) {
-          P0 = n0; P1 = n1; P2 = n2; O0 = r0; O1 = r1; O2 = 0.0; pv[i] = 1.0;
-        } else {
-          P0 = r0; P1 = r1; P2 = 0.0; O0 = n0; O1 = n1; O2 = n2; pv[i] = 0.0;
+  for (int c = t; c < s_ncl; c += T) {
+    const int s = cstart[c], tt = cstart[c + 1];
+    const int k = tt - s;
+    for (int mbr = s; mbr < tt; ++mbr) {
+      // a singleton refines its shift to the Rayleigh quotient after every solve (Rayleigh
+      // quotient iteration); members of a cluster keep their bisection shifts
+      double sigma = lam32[mbr];
+      for (int j = 0; j < n; ++j) X(j) = hash_unit((unsigned)mbr + 1u, (unsigned)j);
+      for (int iter = 0; iter < 3; ++iter) {
+        if (iter == 0 || k == 1) {
+          double dp = d[0] - sigma;  // LDL^T of T - sigma I
+          if (fabs(dp) < tiny) dp = dp < 0 ? -tiny : tiny;
+          DI(0) = 1.0 / dp;
+          for (int j = 1; j < n; ++j) {
+            const double l = e[j - 1] / dp;
+            LM(j - 1) = l;
+            dp = (d[j] - sigma) - l * e[j - 1];
+            if (fabs(dp) < tiny) dp = dp < 0 ? -tiny : tiny;
+            DI(j) = 1.0 / dp;
+          }
         }
-        if (fabs(P0) < tiny) P0 = (P0 < 0 ? -tiny : tiny);
-        const double mm = O0 / P0;
-        U0[i] = P0; U1[i] = P1; U2[i] = P2; mlt[i] = mm;
-        r0 = O1 - mm * P1;
-        r1 = O2 - mm * P2;
-      }
-      if (fabs(r0) < tiny) r0 = (r0 < 0 ? -tiny : tiny);
-      U0[n - 1] = r0; U1[n - 1] = 0.0; U2[n - 1] = 0.0;
-      for (int j = 0; j < n; ++j) x[j] = hash_unit((unsigned)mbr + 1u, (unsigned)j);
-      for (int iter = 0; iter < 4; ++iter) {
-        // forward: apply swaps and multipliers
-        for (int i = 0; i + 1 < n; ++i) {
-          if (pv[i] != 0.0) { const double tmp = x[i]; x[i] = x[i + 1]; x[i + 1] = tmp; }
-          x[i + 1] -= mlt[i] * x[i];
+        double y = X(0);                      // forward: L y = b (in place), then z = D^-1 y
+        X(0) = y * DI(0);
+        for (int j = 1; j < n; ++j) {
+          y = X(j) - LM(j - 1) * y;
+          X(j) = y * DI(j);
         }
-        // back substitution
-        for (int i = n - 1; i >= 0; --i) {
-          double v = x[i];
-          if (i + 1 < n) v -= U1[i] * x[i + 1];
-          if (i + 2 < n) v -= U2[i] * x[i + 2];
-          x[i] = v / U0[i];
+        double xn = X(n - 1);                 // back: L^T x = z
+        for (int j = n - 2; j >= 0; --j) {
+          xn = X(j) - LM(j) * xn;
+          X(j) = xn;
         }
-        // Gram-Schmidt against earlier members of the cluster (twice), then normalise
         for (int pass = 0; pass < 2; ++pass)
           for (int q = s; q < mbr; ++q) {
             double dot = 0.0;
-            for (int j = 0; j < n; ++j) dot += Z[(long long)j * n + q] * x[j];
-            for (int j = 0; j < n; ++j) x[j] -= dot * Z[(long long)j * n + q];
+            for (int j = 0; j < n; ++j) dot += Z[(long long)j * n + q] * X(j);
+            for (int j = 0; j < n; ++j) X(j) -= dot * Z[(long long)j * n + q];
           }
         double nrm = 0.0;
-        for (int j = 0; j < n; ++j) nrm += x[j] * x[j];
+        for (int j = 0; j < n; ++j) nrm += X(j) * X(j);
         nrm = 1.0 / sqrt(nrm);
-        for (int j = 0; j < n; ++j) x[j] *= nrm;
+        for (int j = 0; j < n; ++j) X(j) *= nrm;
+        if (k == 1) {
+          double rq = 0.0, xm = 0.0, x0 = X(0);
+          for (int j = 0; j < n; ++j) {
+            const double xp = (j + 1 < n) ? X(j + 1) : 0.0;
+            double tx = d[j] * x0 + (j + 1 < n ? e[j] * xp : 0.0);
+            if (j > 0) tx += e[j - 1] * xm;
+            rq += x0 * tx;
+            xm = x0;
+            x0 = xp;
+          }
+          sigma = rq;
+        }
       }
-      for (int j = 0; j < n; ++j) Z[(long long)j * n + mbr] = x[j];
+      for (int j = 0; j < n; ++j) Z[(long long)j * n + mbr] = X(j);
     }
-    // Rayleigh-Ritz inside the cluster: Sm = Zc^T T Zc (k x k), Jacobi, rotate
-    double* Sm = Rb + (long long)s * n;            // k*k <= k*n doubles of this cluster's slice
-    double* Rr = Sm + (long long)k * k;            // needs 2 k^2 <= k n  <=> k <= n/2 ...
+    double* Sm = Rb + (long long)s * n;
+    double* Rr = Sm + (long long)k * k;
     const bool fits = (2LL * k * k <= (long long)k * n) && k <= 64;
     if (k == 1 || !fits) {
-      for (int mbr = s; mbr < t; ++mbr) {
+      for (int mbr = s; mbr < tt; ++mbr) {
         double rq = 0.0;
         for (int j = 0; j < n; ++j) {
           double tx = d[j] * Z[(long long)j * n + mbr];
@@ -394,42 +415,40 @@ k_tri_eig(const SubDev* __restrict__ subs, double* vecs, double* Zm, double* scr
           const double apq = Sm[p * k + q];
           if (apq == 0.0) continue;
           const double theta = (Sm[q * k + q] - Sm[p * k + p]) / (2.0 * apq);
-          const double tt = copysign(1.0, theta) / (fabs(theta) + sqrt(theta * theta + 1.0));
-          const double c = 1.0 / sqrt(tt * tt + 1.0), sn = tt * c;
-          for (int r = 0; r < k; ++r) {  // columns p, q
+          const double tq = copysign(1.0, theta) / (fabs(theta) + sqrt(theta * theta + 1.0));
+          const double cs = 1.0 / sqrt(tq * tq + 1.0), sn = tq * cs;
+          for (int r = 0; r < k; ++r) {
             const double sp = Sm[r * k + p], sq = Sm[r * k + q];
-            Sm[r * k + p] = c * sp - sn * sq;
-            Sm[r * k + q] = sn * sp + c * sq;
+            Sm[r * k + p] = cs * sp - sn * sq;
+            Sm[r * k + q] = sn * sp + cs * sq;
           }
-          for (int r = 0; r < k; ++r) {  // rows p, q
+          for (int r = 0; r < k; ++r) {
             const double sp = Sm[p * k + r], sq = Sm[q * k + r];
-            Sm[p * k + r] = c * sp - sn * sq;
-            Sm[q * k + r] = sn * sp + c * sq;
+            Sm[p * k + r] = cs * sp - sn * sq;
+            Sm[q * k + r] = sn * sp + cs * sq;
           }
           for (int r = 0; r < k; ++r) {
             const double rp = Rr[r * k + p], rq = Rr[r * k + q];
-            Rr[r * k + p] = c * rp - sn * rq;
-            Rr[r * k + q] = sn * rp + c * rq;
+            Rr[r * k + p] = cs * rp - sn * rq;
+            Rr[r * k + q] = sn * rp + cs * rq;
           }
         }
     }
-    // sort ascending (selection) and rotate the cluster's vectors row by row
     int order[64];
-    const int kk = k < 64 ? k : 64;
-    for (int a = 0; a < kk; ++a) order[a] = a;
-    for (int a = 0; a < kk; ++a)
-      for (int b = a + 1; b < kk; ++b)
+    for (int a = 0; a < k; ++a) order[a] = a;
+    for (int a = 0; a < k; ++a)
+      for (int b = a + 1; b < k; ++b)
         if (Sm[order[b] * k + order[b]] < Sm[order[a] * k + order[a]]) { const int tmp = order[a]; order[a] = order[b]; order[b] = tmp; }
     for (int j = 0; j < n; ++j) {
       double row[64];
-      for (int b = 0; b < kk; ++b) {
+      for (int b = 0; b < k; ++b) {
         double acc = 0.0;
         for (int a = 0; a < k; ++a) acc += Z[(long long)j * n + s + a] * Rr[a * k + order[b]];
         row[b] = acc;
       }
-      for (int b = 0; b < kk; ++b) Z[(long long)j * n + s + b] = row[b];
+      for (int b = 0; b < k; ++b) Z[(long long)j * n + s + b] = row[b];
     }
-    for (int b = 0; b < kk; ++b) lam_out[S.off_state + s + b] = Sm[order[b] * k + order[b]];
+    for (int b = 0; b < k; ++b) lam_out[S.off_state + s + b] = Sm[order[b] * k + order[b]];
   }
 }
 
@@ -468,20 +487,42 @@ k_backtransform(const SubDev* __restrict__ subs, const double* __restrict__ Am, 
   }
 }
 
+// Dynamic shared memory for the matrix-resident variants: request exactly what a launch needs;
+// if the device refuses (static + dynamic above its opt-in limit), use the global-memory variant.
+template <typename K>
+static bool smem_ok(K kernel, size_t bytes) {
+  if (bytes <= 48 * 1024) return true;
+  cudaFuncAttributes fa;
+  if (cudaFuncGetAttributes(&fa, kernel) != cudaSuccess) return false;
+  int dev = 0, optin = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+  if (bytes + fa.sharedSizeBytes > (size_t)optin) return false;
+  if (cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return true;
+}
+
 void launch_eig(const SubDev* d_subs, int n_sub, int max_ns, double* Ms, double* Hs, double* Y, double* W, double* lam,
                 double* vecs, int* status, double* scratch, double* R, cudaStream_t st) {
-  k_cholesky<<<n_sub, 512, 0, st>>>(d_subs, Ms, status);
+  const size_t mat = (size_t)max_ns * max_ns * sizeof(double);
+  const size_t vbytes = 2 * (size_t)max_ns * sizeof(double);
+  if (smem_ok(k_cholesky<true>, mat)) k_cholesky<true><<<n_sub, 512, mat, st>>>(d_subs, Ms, status);
+  else k_cholesky<false><<<n_sub, 512, 0, st>>>(d_subs, Ms, status);
   dim3 gt((max_ns + 127) / 128, n_sub);
   k_trsm<false><<<gt, 128, 0, st>>>(d_subs, Ms, Hs, 0, W);     // W = L^-1 H_s
   k_trsm<false><<<gt, 128, 0, st>>>(d_subs, Ms, W, 1, Hs);     // A = L^-1 W^T
-  k_tridiag<<<n_sub, 512, 2 * max_ns * sizeof(double), st>>>(d_subs, Hs, vecs);
-  k_tri_eig<<<n_sub, kEigScratchThreads, 2 * max_ns * sizeof(float), st>>>(d_subs, vecs, W, scratch, 6LL * max_ns,
-                                                                            R, lam);
+  if (smem_ok(k_tridiag<true>, mat + vbytes)) k_tridiag<true><<<n_sub, 512, mat + vbytes, st>>>(d_subs, Hs, vecs, max_ns);
+  else k_tridiag<false><<<n_sub, 512, vbytes, st>>>(d_subs, Hs, vecs, max_ns);
+  k_tri_eig<<<n_sub, kTriThreads, 2 * max_ns * sizeof(float) + (max_ns + 1) * sizeof(int), st>>>(
+      d_subs, vecs, W, scratch, 3LL * max_ns * kTriThreads, R, lam);
   dim3 gb((max_ns + 31) / 32, n_sub);
   k_backtransform<<<gb, 256, (max_ns + 256) * sizeof(double), st>>>(d_subs, Hs, vecs, W);
   k_trsm<true><<<gt, 128, 0, st>>>(d_subs, Ms, W, 0, Y);       // Y = L^-T Z
 }
 
-size_t eig_scratch_doubles(int n_sub, int max_ns) { return (size_t)n_sub * kEigScratchThreads * 6 * max_ns; }
+size_t eig_scratch_doubles(int n_sub, int max_ns) { return (size_t)n_sub * kTriThreads * 3 * max_ns; }
 
 }  // namespace xls

@@ -144,37 +144,116 @@ void launch_stencil(const SubDev* d_subs, int n_sub, const Plan& plan, const T* 
 }
 
 // ---- nonlocal projectors -------------------------------------------------------------------
-// A CTA handles one projector slot (one atom in one subdomain, all of its periodic images) and
-// 64 vectors (8 warps x 8 vectors); lanes stride over the points of each image's bounding box,
-// evaluate the four projectors on the fly, and accumulate.
+// Set-up: for every projector slot (one atom in one subdomain, all of its periodic images) a
+// table of its grid points and the four chi values there, built once per Hamiltonian in FP64
+// and stored in the block's precision.  Per filter step: the projection launch
+// P[slot][l][v] = E_l dV sum_g chi_l(g) Y_v(g) (a CTA per slot and 64 vectors, a warp per 8
+// vectors, lanes over the table) and the back-projection launch Y_out[v][g] +=
+// scale sum_l chi_l(g) P[slot][l][v] (same mapping, atomic adds: a point lies in about two
+// spheres).
 constexpr int kNlWarps = 8, kNlVec = 8;
 
 template <typename T>
-__device__ __forceinline__ void chi_at(const ProjSlot& A, const AtomImg& I, const SubDev& S, int p, T chi[4],
-                                       long long& g, bool& in) {
+__device__ __forceinline__ bool chi_at(const ProjSlot& A, const AtomImg& I, const SubDev& S, int p, double chi[4],
+                                       int& g) {
   const int bx = I.box_n[0], by = I.box_n[1];
   const int i = I.box_lo[0] + p % bx;
   const int j = I.box_lo[1] + (p / bx) % by;
   const int k = I.box_lo[2] + p / (bx * by);
   const double dx = i * S.h[0] - I.R[0], dy = j * S.h[1] - I.R[1], dz = k * S.h[2] - I.R[2];
   const double r2 = dx * dx + dy * dy + dz * dz;
-  in = r2 < A.rcut2;
-  if (!in) return;
+  if (!(r2 < A.rcut2)) return false;
   const double e = exp(-r2 / (2.0 * A.w * A.w));
-  chi[0] = (T)(A.norm[0] * e);
-  chi[1] = (T)(A.norm[1] * dx * e);
-  chi[2] = (T)(A.norm[2] * dy * e);
-  chi[3] = (T)(A.norm[3] * dz * e);
+  chi[0] = A.norm[0] * e;
+  chi[1] = A.norm[1] * dx * e;
+  chi[2] = A.norm[2] * dy * e;
+  chi[3] = A.norm[3] * dz * e;
   const int gi = S.periodic[0] ? wrapi(i, S.n[0]) : i;
   const int gj = S.periodic[1] ? wrapi(j, S.n[1]) : j;
   const int gk = S.periodic[2] ? wrapi(k, S.n[2]) : k;
-  g = ((long long)gk * S.n[1] + gj) * S.n[0] + gi;
+  g = (gk * S.n[1] + gj) * S.n[0] + gi;
+  return true;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256)
+k_proj_count(const SubDev* __restrict__ subs, const ProjSlot* __restrict__ slots, const AtomImg* __restrict__ imgs,
+             int* counts) {
+  const ProjSlot& A = slots[blockIdx.x];
+  const SubDev& S = subs[A.sub];
+  int c = 0;
+  for (int im = A.img_lo; im < A.img_lo + A.img_n; ++im) {
+    const AtomImg& I = imgs[im];
+    const int npts = I.box_n[0] * I.box_n[1] * I.box_n[2];
+    for (int p = threadIdx.x; p < npts; p += blockDim.x) {
+      double chi[4];
+      int g;
+      if (chi_at<T>(A, I, S, p, chi, g)) ++c;
+    }
+  }
+  __shared__ int red[8];
+  c += __shfl_xor_sync(0xffffffffu, c, 16);
+  c += __shfl_xor_sync(0xffffffffu, c, 8);
+  c += __shfl_xor_sync(0xffffffffu, c, 4);
+  c += __shfl_xor_sync(0xffffffffu, c, 2);
+  c += __shfl_xor_sync(0xffffffffu, c, 1);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = c;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int t = 0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += red[w];
+    counts[blockIdx.x] = t;
+  }
+}
+
+// ordered compaction: chunk by chunk of blockDim points, ballot + warp prefix + block prefix
+template <typename T>
+__global__ void __launch_bounds__(256)
+k_proj_fill(const SubDev* __restrict__ subs, const ProjSlot* __restrict__ slots, const AtomImg* __restrict__ imgs,
+            int* idx, typename Vec4<T>::type* chi_out) {
+  const ProjSlot& A = slots[blockIdx.x];
+  const SubDev& S = subs[A.sub];
+  __shared__ int wsum[8];
+  __shared__ int s_base;
+  if (threadIdx.x == 0) s_base = 0;
+  __syncthreads();
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  for (int im = A.img_lo; im < A.img_lo + A.img_n; ++im) {
+    const AtomImg& I = imgs[im];
+    const int npts = I.box_n[0] * I.box_n[1] * I.box_n[2];
+    for (int p0 = 0; p0 < npts; p0 += blockDim.x) {
+      const int p = p0 + threadIdx.x;
+      double chi[4];
+      int g = 0;
+      const bool in = (p < npts) && chi_at<T>(A, I, S, p, chi, g);
+      const unsigned m = __ballot_sync(0xffffffffu, in);
+      const int before = __popc(m & ((1u << lane) - 1u));
+      if (lane == 0) wsum[warp] = __popc(m);
+      __syncthreads();
+      int off = s_base;
+      for (int w = 0; w < warp; ++w) off += wsum[w];
+      if (in) {
+        const long long e = A.pt_off + off + before;
+        idx[e] = g;
+        typename Vec4<T>::type c4;
+        c4.x = (T)chi[0]; c4.y = (T)chi[1]; c4.z = (T)chi[2]; c4.w = (T)chi[3];
+        chi_out[e] = c4;
+      }
+      __syncthreads();
+      if (threadIdx.x == 0) {
+        int t = 0;
+        for (int w = 0; w < nw; ++w) t += wsum[w];
+        s_base += t;
+      }
+      __syncthreads();
+    }
+  }
 }
 
 template <typename T>
 __global__ void __launch_bounds__(kNlWarps * 32)
-k_nl_project(const SubDev* __restrict__ subs, const ProjSlot* __restrict__ slots, const AtomImg* __restrict__ imgs,
-             const T* __restrict__ Y, double* __restrict__ P) {
+k_nl_project(const SubDev* __restrict__ subs, const ProjSlot* __restrict__ slots, const int* __restrict__ idx,
+             const typename Vec4<T>::type* __restrict__ chi, const T* __restrict__ Y, double* __restrict__ P) {
   const ProjSlot& A = slots[blockIdx.x];
   const SubDev& S = subs[A.sub];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -187,22 +266,19 @@ k_nl_project(const SubDev* __restrict__ subs, const ProjSlot* __restrict__ slots
 #pragma unroll
     for (int v = 0; v < kNlVec; ++v) acc[l][v] = (T)0;
   const T* yb = Y + S.off_blk + (long long)v0 * S.nd;
-  for (int im = A.img_lo; im < A.img_lo + A.img_n; ++im) {
-    const AtomImg& I = imgs[im];
-    const int npts = I.box_n[0] * I.box_n[1] * I.box_n[2];
-    for (int p = lane; p < npts; p += 32) {
-      T chi[4];
-      long long g;
-      bool in;
-      chi_at<T>(A, I, S, p, chi, g, in);
-      if (!in) continue;
+  const int* ix = idx + A.pt_off;
+  const typename Vec4<T>::type* cx = chi + A.pt_off;
+  for (int p = lane; p < A.pt_n; p += 32) {
+    const int g = ix[p];
+    const typename Vec4<T>::type c = cx[p];
 #pragma unroll
-      for (int v = 0; v < kNlVec; ++v) {
-        if (v < nv) {
-          const T y = yb[(long long)v * S.nd + g];
-#pragma unroll
-          for (int l = 0; l < 4; ++l) acc[l][v] += chi[l] * y;
-        }
+    for (int v = 0; v < kNlVec; ++v) {
+      if (v < nv) {
+        const T y = yb[(long long)v * S.nd + g];
+        acc[0][v] += c.x * y;
+        acc[1][v] += c.y * y;
+        acc[2][v] += c.z * y;
+        acc[3][v] += c.w * y;
       }
     }
   }
@@ -225,8 +301,9 @@ k_nl_project(const SubDev* __restrict__ subs, const ProjSlot* __restrict__ slots
 
 template <typename T>
 __global__ void __launch_bounds__(kNlWarps * 32)
-k_nl_back(const SubDev* __restrict__ subs, const ProjSlot* __restrict__ slots, const AtomImg* __restrict__ imgs,
-          const double* __restrict__ P, T* Yout, const StepCoef* __restrict__ coef, int step) {
+k_nl_back(const SubDev* __restrict__ subs, const ProjSlot* __restrict__ slots, const int* __restrict__ idx,
+          const typename Vec4<T>::type* __restrict__ chi, const double* __restrict__ P, T* Yout,
+          const StepCoef* __restrict__ coef, int step) {
   const ProjSlot& A = slots[blockIdx.x];
   const SubDev& S = subs[A.sub];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -241,53 +318,59 @@ k_nl_back(const SubDev* __restrict__ subs, const ProjSlot* __restrict__ slots, c
 #pragma unroll
     for (int l = 0; l < 4; ++l) q[l][v] = (v < nv) ? (T)(scale * pa[l * S.ns + v0 + v]) : (T)0;
   T* yb = Yout + S.off_blk + (long long)v0 * S.nd;
-  for (int im = A.img_lo; im < A.img_lo + A.img_n; ++im) {
-    const AtomImg& I = imgs[im];
-    const int npts = I.box_n[0] * I.box_n[1] * I.box_n[2];
-    for (int p = lane; p < npts; p += 32) {
-      T chi[4];
-      long long g;
-      bool in;
-      chi_at<T>(A, I, S, p, chi, g, in);
-      if (!in) continue;
+  const int* ix = idx + A.pt_off;
+  const typename Vec4<T>::type* cx = chi + A.pt_off;
+  for (int p = lane; p < A.pt_n; p += 32) {
+    const int g = ix[p];
+    const typename Vec4<T>::type c = cx[p];
 #pragma unroll
-      for (int v = 0; v < kNlVec; ++v) {
-        if (v < nv) {
-          const T add = chi[0] * q[0][v] + chi[1] * q[1][v] + chi[2] * q[2][v] + chi[3] * q[3][v];
-          atomicAdd(yb + (long long)v * S.nd + g, add);
-        }
-      }
+    for (int v = 0; v < kNlVec; ++v) {
+      if (v < nv) atomicAdd(yb + (long long)v * S.nd + g, c.x * q[0][v] + c.y * q[1][v] + c.z * q[2][v] + c.w * q[3][v]);
     }
   }
 }
 
 template <typename T>
-void launch_nl_project(const SubDev* d_subs, const ProjSlot* d_slots, int n_slot, const AtomImg* d_imgs, int max_ns,
-                       const T* Y, double* P, cudaStream_t st) {
-  if (n_slot == 0) return;
-  dim3 grid(n_slot, (max_ns + kNlWarps * kNlVec - 1) / (kNlWarps * kNlVec));
-  k_nl_project<T><<<grid, kNlWarps * 32, 0, st>>>(d_subs, d_slots, d_imgs, Y, P);
+void launch_proj_table_count(const SubDev* d_subs, const ProjSlot* d_slots, int n_slot, const AtomImg* d_imgs,
+                             int* counts, cudaStream_t st) {
+  if (n_slot) k_proj_count<T><<<n_slot, 256, 0, st>>>(d_subs, d_slots, d_imgs, counts);
+}
+template <typename T>
+void launch_proj_table_fill(const SubDev* d_subs, const ProjSlot* d_slots, int n_slot, const AtomImg* d_imgs, int* idx,
+                            typename Vec4<T>::type* chi, cudaStream_t st) {
+  if (n_slot) k_proj_fill<T><<<n_slot, 256, 0, st>>>(d_subs, d_slots, d_imgs, idx, chi);
 }
 
 template <typename T>
-void launch_nl_back(const SubDev* d_subs, const ProjSlot* d_slots, int n_slot, const AtomImg* d_imgs, int max_ns,
-                    const double* P, T* Yout, const StepCoef* coef, int step, cudaStream_t st) {
+void launch_nl_project(const SubDev* d_subs, const ProjSlot* d_slots, int n_slot, const int* idx,
+                       const typename Vec4<T>::type* chi, int max_ns, const T* Y, double* P, cudaStream_t st) {
   if (n_slot == 0) return;
   dim3 grid(n_slot, (max_ns + kNlWarps * kNlVec - 1) / (kNlWarps * kNlVec));
-  k_nl_back<T><<<grid, kNlWarps * 32, 0, st>>>(d_subs, d_slots, d_imgs, P, Yout, coef, step);
+  k_nl_project<T><<<grid, kNlWarps * 32, 0, st>>>(d_subs, d_slots, idx, chi, Y, P);
 }
+
+template <typename T>
+void launch_nl_back(const SubDev* d_subs, const ProjSlot* d_slots, int n_slot, const int* idx,
+                    const typename Vec4<T>::type* chi, int max_ns, const double* P, T* Yout, const StepCoef* coef,
+                    int step, cudaStream_t st) {
+  if (n_slot == 0) return;
+  dim3 grid(n_slot, (max_ns + kNlWarps * kNlVec - 1) / (kNlWarps * kNlVec));
+  k_nl_back<T><<<grid, kNlWarps * 32, 0, st>>>(d_subs, d_slots, idx, chi, P, Yout, coef, step);
+}
+
+#define XLS_INST_NL(T)                                                                                              \
+  template void launch_proj_table_count<T>(const SubDev*, const ProjSlot*, int, const AtomImg*, int*, cudaStream_t); \
+  template void launch_proj_table_fill<T>(const SubDev*, const ProjSlot*, int, const AtomImg*, int*,                 \
+                                          Vec4<T>::type*, cudaStream_t);                                             \
+  template void launch_nl_project<T>(const SubDev*, const ProjSlot*, int, const int*, const Vec4<T>::type*, int,     \
+                                     const T*, double*, cudaStream_t);                                               \
+  template void launch_nl_back<T>(const SubDev*, const ProjSlot*, int, const int*, const Vec4<T>::type*, int,        \
+                                  const double*, T*, const StepCoef*, int, cudaStream_t);
+XLS_INST_NL(double)
+XLS_INST_NL(float)
 
 template void launch_stencil<double>(const SubDev*, int, const Plan&, const double*, const double*, double*,
                                      const double*, const StepCoef*, int, cudaStream_t);
 template void launch_stencil<float>(const SubDev*, int, const Plan&, const float*, const float*, float*,
                                     const float*, const StepCoef*, int, cudaStream_t);
-template void launch_nl_project<double>(const SubDev*, const ProjSlot*, int, const AtomImg*, int, const double*,
-                                        double*, cudaStream_t);
-template void launch_nl_project<float>(const SubDev*, const ProjSlot*, int, const AtomImg*, int, const float*, double*,
-                                       cudaStream_t);
-template void launch_nl_back<double>(const SubDev*, const ProjSlot*, int, const AtomImg*, int, const double*, double*,
-                                     const StepCoef*, int, cudaStream_t);
-template void launch_nl_back<float>(const SubDev*, const ProjSlot*, int, const AtomImg*, int, const double*, float*,
-                                    const StepCoef*, int, cudaStream_t);
-
 }  // namespace xls

@@ -1,0 +1,477 @@
+// Tensor-core subspace contractions of the mixed path (Sec. 5.A.3 steps (2) and (4); the
+// paper's projection DGEMM/DSYRK and rotation DGEMM of Sec. 5.B.3), on 5th-generation tensor
+// cores: tcgen05.mma kind::f16 with BF16 operands and FP32 accumulators in tensor memory.
+//
+// Split-BF16 products: every FP32 operand x is written as hi + lo with hi = bf16(x) and
+// lo = bf16(x - hi); a product a b is taken as a_hi b_hi + a_hi b_lo + a_lo b_hi (the lo*lo term,
+// below 2^-16 relative, is dropped), all three accumulated in the same FP32 TMEM accumulator.
+//
+// Data flow of both kernels: eight producer warps read FP32 tiles from HBM with 16-byte loads,
+// split them and store hi and lo tiles in shared memory in the UMMA canonical 128-byte-swizzled
+// layout; after a proxy fence they arrive on the stage's "full" mbarrier.  One thread of a ninth
+// warp issues the MMAs of a stage and commits them to the stage's "empty" mbarrier, which the
+// producers wait on before refilling it (two stages).  A final commit releases the epilogue,
+// in which the producer warps read the accumulators with tcgen05.ld.
+//
+//   Gram:     D1 = Psi_f[I]^T Psi_f[J], D2 = Psi_f[I]^T (H Psi_f)[J] over a chunk of grid points,
+//             for the upper block triangle (I <= J) of 128 x 128 blocks; FP32 partial sums of the
+//             chunks go to a workspace that k_gram_reduce sums (FP64) into M_s, H_s, mirroring
+//             the off-diagonal blocks.
+//   Rotation: Psi[n][g] = sum_k Psi_f[k][g] Y[k][n] for a tile of 128 grid points, A = Psi_f
+//             (MN-major: grid points contiguous), B = Y^T (K-major, pre-split hi/lo in HBM).
+#include <cuda_bf16.h>
+
+#include "xls_internal.h"
+
+namespace xls {
+namespace tc {
+
+constexpr int kThreads = 288;      // 8 producer/epilogue warps + 1 MMA warp
+constexpr int kProducers = 256;
+constexpr int kKT = 64;            // K elements per tile (128-byte bf16 rows)
+constexpr int kStages = 2;
+constexpr long long kSpin = 1LL << 26;  // bounded mbarrier waits
+
+__device__ __forceinline__ uint32_t su32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void bar_init(uint64_t* b, uint32_t n) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(su32(b)), "r"(n) : "memory");
+}
+__device__ __forceinline__ void bar_arrive(uint64_t* b) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(su32(b)) : "memory");
+}
+__device__ __forceinline__ bool bar_try(uint64_t* b, uint32_t parity) {
+  uint32_t ok;
+  asm volatile("{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+               : "=r"(ok)
+               : "r"(su32(b)), "r"(parity)
+               : "memory");
+  return ok != 0;
+}
+__device__ __forceinline__ bool bar_wait(uint64_t* b, uint32_t parity) {
+  for (long long i = 0; i < kSpin; ++i)
+    if (bar_try(b, parity)) return true;
+  return false;
+}
+
+__device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+
+__device__ __forceinline__ void tmem_alloc(uint32_t* dst_smem, uint32_t ncols) {
+  asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(su32(dst_smem)), "r"(ncols)
+               : "memory");
+  asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+}
+__device__ __forceinline__ void tmem_dealloc(uint32_t taddr, uint32_t ncols) {
+  asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols) : "memory");
+}
+
+// D[tmem] (+)= A[smem] * B[smem]^T, M = 128, N from idesc, K = 16
+__device__ __forceinline__ void mma_bf16(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc, uint32_t idesc, int accum) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(
+          tmem_d),
+      "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accum)
+      : "memory");
+}
+__device__ __forceinline__ void mma_commit(uint64_t* bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(su32(bar))
+               : "memory");
+}
+
+// 32 lanes x 32 bit, 16 consecutive columns per thread
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float v[16]) {
+  uint32_t r[16];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];\n"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
+        "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+// Instruction descriptor, kind::f16: D = F32 (bits 4-5 = 1), A = B = BF16 (bits 7-9, 10-12 = 1),
+// A major (bit 15), B K-major (bit 16 = 0), N >> 3 at bits 17-22, M >> 4 at bits 24-28.
+__host__ __device__ constexpr uint32_t idesc_bf16(int M, int N, bool a_mn_major) {
+  return (1u << 4) | (1u << 7) | (1u << 10) | ((a_mn_major ? 1u : 0u) << 15) | ((uint32_t)(N >> 3) << 17) |
+         ((uint32_t)(M >> 4) << 24);
+}
+
+// Shared-memory matrix descriptor, 128-byte swizzle: start >> 4 (bits 0-13), leading byte
+// offset >> 4 (16-29), stride byte offset >> 4 (32-45), version 1 (46-47), layout 2 (61-63).
+__device__ __forceinline__ uint64_t sdesc(uint32_t saddr, uint32_t lbo, uint32_t sbo) {
+  return (uint64_t)((saddr >> 4) & 0x3FFF) | ((uint64_t)((lbo >> 4) & 0x3FFF) << 16) |
+         ((uint64_t)((sbo >> 4) & 0x3FFF) << 32) | (1ull << 46) | (2ull << 61);
+}
+
+// K-major 128B-swizzled tile: row r (128 bytes = 64 bf16 of K), 16-byte chunk c
+__device__ __forceinline__ uint32_t kmaj_off(int r, int c) { return (uint32_t)(r * 128 + ((c ^ (r & 7)) << 4)); }
+// MN-major 128B-swizzled tile of 128 MN x 64 K: MN group m (64 elements), K row k, chunk c of 8 MN
+// elements; K groups of 8 rows 1024 bytes apart (SBO), MN groups 8192 bytes apart (LBO)
+__device__ __forceinline__ uint32_t mnmaj_off(int m, int k, int c) {
+  return (uint32_t)(m * 8192 + (k >> 3) * 1024 + (k & 7) * 128 + ((c ^ (k & 7)) << 4));
+}
+
+__device__ __forceinline__ void split8(const float4 a, const float4 b, uint4& hi, uint4& lo) {
+  const float x[8] = {a.x, a.y, a.z, a.w, b.x, b.y, b.z, b.w};
+  uint32_t h[4], l[4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    const __nv_bfloat16 h0 = __float2bfloat16_rn(x[2 * i]), h1 = __float2bfloat16_rn(x[2 * i + 1]);
+    const __nv_bfloat16 l0 = __float2bfloat16_rn(x[2 * i] - __bfloat162float(h0));
+    const __nv_bfloat16 l1 = __float2bfloat16_rn(x[2 * i + 1] - __bfloat162float(h1));
+    h[i] = (uint32_t)__bfloat16_as_ushort(h0) | ((uint32_t)__bfloat16_as_ushort(h1) << 16);
+    l[i] = (uint32_t)__bfloat16_as_ushort(l0) | ((uint32_t)__bfloat16_as_ushort(l1) << 16);
+  }
+  hi = make_uint4(h[0], h[1], h[2], h[3]);
+  lo = make_uint4(l[0], l[1], l[2], l[3]);
+}
+
+__device__ __forceinline__ void sts128(uint32_t saddr, uint4 v) {
+  asm volatile("st.shared.v4.b32 [%0], {%1, %2, %3, %4};" ::"r"(saddr), "r"(v.x), "r"(v.y), "r"(v.z), "r"(v.w)
+               : "memory");
+}
+
+// ---------------------------------------------------------------------------------------------
+// Gram: one CTA = (subdomain, block (I, J), chunk of K tiles)
+// stage layout (bytes): A_hi 16K, A_lo 16K, B1_hi 16K, B1_lo 16K, B2_hi 16K, B2_lo 16K
+constexpr uint32_t kTile = 128 * 128;        // one 128-row x 128-byte tile
+constexpr uint32_t kGramStage = 6 * kTile;
+
+__global__ void __launch_bounds__(kThreads, 1)
+k_gram_tc(const SubDev* __restrict__ subs, const GramJob* __restrict__ jobs, const float* __restrict__ F,
+          const float* __restrict__ HF, float* __restrict__ work, int* status) {
+  extern __shared__ __align__(1024) unsigned char smem_raw[];
+  unsigned char* smem = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+  __shared__ __align__(8) uint64_t full[kStages], empty[kStages], done;
+  __shared__ uint32_t s_tmem;
+  __shared__ int s_fail;
+  const GramJob J = jobs[blockIdx.x];
+  const SubDev& S = subs[J.sub];
+  const int ns = S.ns;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int i0 = 128 * J.I, j0 = 128 * J.J;
+  const int nj = min(128, ns - j0);
+  const int nj16 = (nj + 15) & ~15;
+  const bool diag = (J.I == J.J);
+  const int nkt = J.kt1 - J.kt0;
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < kStages; ++s) {
+      bar_init(&full[s], kProducers);
+      bar_init(&empty[s], 1);
+    }
+    bar_init(&done, 1);
+    s_fail = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 8) tmem_alloc(&s_tmem, 256);
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = s_tmem;
+  const uint32_t sbase = su32(smem);
+  const float* f = F + S.off_blk;
+  const float* hf = HF + S.off_blk;
+
+  if (warp < 8) {
+    // ---------------- producers
+    const int rowsB1 = diag ? 0 : nj16;
+    const int nrows = 128 + rowsB1 + nj16;     // A rows, B1 rows, B2 rows
+    for (int it = 0; it < nkt; ++it) {
+      const int st = it % kStages;
+      if (it >= kStages && !bar_wait(&empty[st], ((it / kStages) - 1) & 1)) { atomicExch(&s_fail, 1); break; }
+      const long long k0 = (long long)(J.kt0 + it) * kKT;
+      const uint32_t stage = sbase + st * kGramStage;
+      for (int q = threadIdx.x; q < nrows * 8; q += kProducers) {
+        const int row = q >> 3, c = q & 7;
+        const float* src;
+        int grow;
+        uint32_t thi, tlo;
+        int r;
+        if (row < 128) {                       // A: rows i0 + r of Psi_f
+          r = row; grow = i0 + r; src = f; thi = stage; tlo = stage + kTile;
+        } else if (row < 128 + rowsB1) {       // B1: rows j0 + r of Psi_f
+          r = row - 128; grow = j0 + r; src = f; thi = stage + 2 * kTile; tlo = stage + 3 * kTile;
+        } else {                               // B2: rows j0 + r of H Psi_f
+          r = row - 128 - rowsB1; grow = j0 + r; src = hf; thi = stage + 4 * kTile; tlo = stage + 5 * kTile;
+        }
+        const bool valid = (row < 128) ? (grow < ns) : (r < nj);
+        float4 a = make_float4(0.f, 0.f, 0.f, 0.f), b = a;
+        const long long kk = k0 + c * 8;
+        if (valid && kk < S.nd) {
+          const float4* p = reinterpret_cast<const float4*>(src + (long long)grow * S.nd + kk);
+          a = p[0];
+          b = p[1];
+        }
+        uint4 hi, lo;
+        split8(a, b, hi, lo);
+        const uint32_t off = kmaj_off(r, c);
+        sts128(thi + off, hi);
+        sts128(tlo + off, lo);
+      }
+      fence_async_smem();
+      bar_arrive(&full[st]);
+    }
+    // ---------------- epilogue: warps 0-3 read D1 (columns 0..), warps 4-7 read D2 (columns 128..)
+    const bool ok = bar_wait(&done, 0);
+    tc_fence_after();
+    if (!ok) atomicExch(&s_fail, 1);
+    const int lg = warp & 3;
+    const int out = warp >> 2;
+    const int row = lg * 32 + lane;
+    float* w = work + (long long)blockIdx.x * 2 * 128 * 128 + (long long)out * 128 * 128 + (long long)row * 128;
+    for (int c0 = 0; c0 < nj16; c0 += 16) {
+      float v[16];
+      tmem_ld16(tmem + ((uint32_t)(lg * 32) << 16) + (uint32_t)(out * 128 + c0), v);
+      if (ok) {
+#pragma unroll
+        for (int u = 0; u < 16; u += 4) *reinterpret_cast<float4*>(w + c0 + u) = make_float4(v[u], v[u + 1], v[u + 2], v[u + 3]);
+      }
+    }
+  } else if (lane == 0) {
+    // ---------------- MMA issuer
+    const uint32_t idesc = idesc_bf16(128, nj16, false);
+    bool ok = true;
+    for (int it = 0; it < nkt; ++it) {
+      const int st = it % kStages;
+      if (!bar_wait(&full[st], (it / kStages) & 1)) { ok = false; break; }
+      tc_fence_after();
+      const uint32_t stage = sbase + st * kGramStage;
+      const uint32_t a_hi = stage, a_lo = stage + kTile;
+      const uint32_t b1_hi = diag ? a_hi : stage + 2 * kTile, b1_lo = diag ? a_lo : stage + 3 * kTile;
+      const uint32_t b2_hi = stage + 4 * kTile, b2_lo = stage + 5 * kTile;
+#pragma unroll
+      for (int ks = 0; ks < kKT / 16; ++ks) {
+        const uint32_t ko = ks * 32;           // 16 bf16 = 32 bytes along K inside the swizzle row
+        const int acc = (it > 0 || ks > 0) ? 1 : 0;
+        const uint64_t ah = sdesc(a_hi + ko, 16, 1024), al = sdesc(a_lo + ko, 16, 1024);
+        mma_bf16(tmem + 0, ah, sdesc(b1_hi + ko, 16, 1024), idesc, acc);
+        mma_bf16(tmem + 0, ah, sdesc(b1_lo + ko, 16, 1024), idesc, 1);
+        mma_bf16(tmem + 0, al, sdesc(b1_hi + ko, 16, 1024), idesc, 1);
+        mma_bf16(tmem + 128, ah, sdesc(b2_hi + ko, 16, 1024), idesc, acc);
+        mma_bf16(tmem + 128, ah, sdesc(b2_lo + ko, 16, 1024), idesc, 1);
+        mma_bf16(tmem + 128, al, sdesc(b2_hi + ko, 16, 1024), idesc, 1);
+      }
+      mma_commit(&empty[st]);
+    }
+    if (!ok) atomicExch(&s_fail, 1);
+    mma_commit(&done);
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  if (warp == 8) tmem_dealloc(tmem, 256);
+  if (threadIdx.x == 0 && s_fail) atomicCAS(status, 0, XLS_ETIMEOUT);
+}
+
+// Sum the K-chunk partials of every block into M_s, H_s (FP64) and mirror off-diagonal blocks.
+__global__ void __launch_bounds__(256)
+k_gram_reduce(const SubDev* __restrict__ subs, const GramJob* __restrict__ jobs, const int* __restrict__ grp_first,
+              const int* __restrict__ grp_n, const float* __restrict__ work, double* Ms, double* Hs) {
+  const int gi = blockIdx.y;  // group = (subdomain, block)
+  const int first = grp_first[gi], cnt = grp_n[gi];
+  const GramJob J = jobs[first];
+  const SubDev& S = subs[J.sub];
+  const int ns = S.ns;
+  const int i0 = 128 * J.I, j0 = 128 * J.J;
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < 128 * 128; e += gridDim.x * blockDim.x) {
+    const int r = e / 128, c = e % 128;
+    const int i = i0 + r, j = j0 + c;
+    if (i >= ns || j >= ns) continue;
+    double m = 0.0, h = 0.0;
+    for (int q = 0; q < cnt; ++q) {
+      const float* w = work + (long long)(first + q) * 2 * 128 * 128;
+      m += (double)w[e];
+      h += (double)w[128 * 128 + e];
+    }
+    Ms[S.off_ss + (long long)i * ns + j] = m;
+    Hs[S.off_ss + (long long)i * ns + j] = h;
+    if (J.I != J.J) {
+      Ms[S.off_ss + (long long)j * ns + i] = m;
+      Hs[S.off_ss + (long long)j * ns + i] = h;
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------------------------
+// Rotation: one CTA = (subdomain, tile of 128 grid points); K = N_s in tiles of 64
+// stage layout: A_hi 16K, A_lo 16K (MN-major), B_hi, B_lo (N rows x 128 bytes each, <= 32K each)
+constexpr uint32_t kRotStage = 2 * kTile + 2 * 256 * 128;
+
+__global__ void __launch_bounds__(kThreads, 1)
+k_rotate_tc(const SubDev* __restrict__ subs, const RotJob* __restrict__ jobs, const float* __restrict__ F,
+            const uint16_t* __restrict__ Yhi, const uint16_t* __restrict__ Ylo, int kpad_max, float* __restrict__ Out,
+            int* status) {
+  extern __shared__ __align__(1024) unsigned char smem_raw[];
+  unsigned char* smem = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+  __shared__ __align__(8) uint64_t full[kStages], empty[kStages], done;
+  __shared__ uint32_t s_tmem;
+  __shared__ int s_fail;
+  const RotJob J = jobs[blockIdx.x];
+  const SubDev& S = subs[J.sub];
+  const int ns = S.ns;
+  const int n16 = (ns + 15) & ~15;
+  const int nkt = (ns + kKT - 1) / kKT;
+  const long long g0 = (long long)J.tile * 128;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < kStages; ++s) {
+      bar_init(&full[s], kProducers);
+      bar_init(&empty[s], 1);
+    }
+    bar_init(&done, 1);
+    s_fail = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 8) tmem_alloc(&s_tmem, 256);
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = s_tmem;
+  const uint32_t sbase = su32(smem);
+  const float* f = F + S.off_blk;
+  const long long yoff = (long long)S.off_state * kpad_max;   // Y^T hi/lo of this subdomain: [n][kpad_max]
+
+  if (warp < 8) {
+    for (int it = 0; it < nkt; ++it) {
+      const int st = it % kStages;
+      if (it >= kStages && !bar_wait(&empty[st], ((it / kStages) - 1) & 1)) { atomicExch(&s_fail, 1); break; }
+      const int k0 = it * kKT;
+      const uint32_t stage = sbase + st * kRotStage;
+      // A: 64 k-rows x 128 grid points, chunks of 8 points (MN-major)
+      for (int q = threadIdx.x; q < 64 * 16; q += kProducers) {
+        const int k = q >> 4, c16 = q & 15;     // c16: chunk of 8 points within 128
+        const int kk = k0 + k;
+        const long long g = g0 + c16 * 8;
+        float4 a = make_float4(0.f, 0.f, 0.f, 0.f), b = a;
+        if (kk < ns && g < S.nd) {
+          const float4* p = reinterpret_cast<const float4*>(f + (long long)kk * S.nd + g);
+          a = p[0];
+          b = p[1];
+        }
+        uint4 hi, lo;
+        split8(a, b, hi, lo);
+        const uint32_t off = mnmaj_off(c16 >> 3, k, c16 & 7);
+        sts128(stage + off, hi);
+        sts128(stage + kTile + off, lo);
+      }
+      // B: n16 rows x 64 k of Y^T hi / lo (already split), K-major
+      for (int q = threadIdx.x; q < n16 * 8; q += kProducers) {
+        const int n = q >> 3, c = q & 7;
+        uint4 hi = make_uint4(0, 0, 0, 0), lo = hi;
+        if (n < ns) {
+          const long long e = yoff + (long long)n * kpad_max + k0 + c * 8;
+          hi = *reinterpret_cast<const uint4*>(Yhi + e);
+          lo = *reinterpret_cast<const uint4*>(Ylo + e);
+        }
+        const uint32_t off = kmaj_off(n, c);
+        sts128(stage + 2 * kTile + off, hi);
+        sts128(stage + 2 * kTile + 256 * 128 + off, lo);
+      }
+      fence_async_smem();
+      bar_arrive(&full[st]);
+    }
+    const bool ok = bar_wait(&done, 0);
+    tc_fence_after();
+    if (!ok) atomicExch(&s_fail, 1);
+    // epilogue: warp w reads lanes 32 (w & 3).., column half (w >> 2)
+    const int lg = warp & 3, half = warp >> 2;
+    const long long g = g0 + lg * 32 + lane;
+    const int nhalf = ((n16 / 16 + 1) / 2) * 16;
+    const int c_lo = half * nhalf, c_hi = min(n16, c_lo + nhalf);
+    float* o = Out + S.off_blk;
+    for (int c0 = c_lo; c0 < c_hi; c0 += 16) {
+      float v[16];
+      tmem_ld16(tmem + ((uint32_t)(lg * 32) << 16) + (uint32_t)c0, v);
+      if (ok && g < S.nd) {
+#pragma unroll
+        for (int u = 0; u < 16; ++u)
+          if (c0 + u < ns) o[(long long)(c0 + u) * S.nd + g] = v[u];
+      }
+    }
+  } else if (lane == 0) {
+    const uint32_t idesc = idesc_bf16(128, n16, true);
+    bool ok = true;
+    for (int it = 0; it < nkt; ++it) {
+      const int st = it % kStages;
+      if (!bar_wait(&full[st], (it / kStages) & 1)) { ok = false; break; }
+      tc_fence_after();
+      const uint32_t stage = sbase + st * kRotStage;
+      const uint32_t a_hi = stage, a_lo = stage + kTile;
+      const uint32_t b_hi = stage + 2 * kTile, b_lo = b_hi + 256 * 128;
+#pragma unroll
+      for (int ks = 0; ks < kKT / 16; ++ks) {
+        const int acc = (it > 0 || ks > 0) ? 1 : 0;
+        // A (MN-major): K step of 16 = two 8-row K groups = 2048 bytes; B (K-major): 32 bytes
+        const uint64_t ah = sdesc(a_hi + ks * 2048, 8192, 1024), al = sdesc(a_lo + ks * 2048, 8192, 1024);
+        const uint64_t bh = sdesc(b_hi + ks * 32, 16, 1024), bl = sdesc(b_lo + ks * 32, 16, 1024);
+        mma_bf16(tmem, ah, bh, idesc, acc);
+        mma_bf16(tmem, ah, bl, idesc, 1);
+        mma_bf16(tmem, al, bh, idesc, 1);
+      }
+      mma_commit(&empty[st]);
+    }
+    if (!ok) atomicExch(&s_fail, 1);
+    mma_commit(&done);
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  if (warp == 8) tmem_dealloc(tmem, 256);
+  if (threadIdx.x == 0 && s_fail) atomicCAS(status, 0, XLS_ETIMEOUT);
+}
+
+// Y (FP64, row-major [k][n]) -> Y^T hi/lo bf16 [n][kpad_max], zero padded
+__global__ void k_split_yt(const SubDev* __restrict__ subs, const double* __restrict__ Y, int kpad_max, uint16_t* Yhi,
+                          uint16_t* Ylo) {
+  const SubDev& S = subs[blockIdx.y];
+  const int ns = S.ns;
+  const long long yoff = (long long)S.off_state * kpad_max;
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < ns * kpad_max; e += gridDim.x * blockDim.x) {
+    const int n = e / kpad_max, k = e % kpad_max;
+    const float x = (k < ns) ? (float)Y[S.off_ss + (long long)k * ns + n] : 0.f;
+    const __nv_bfloat16 h = __float2bfloat16_rn(x);
+    const __nv_bfloat16 l = __float2bfloat16_rn(x - __bfloat162float(h));
+    Yhi[yoff + e] = __bfloat16_as_ushort(h);
+    Ylo[yoff + e] = __bfloat16_as_ushort(l);
+  }
+}
+
+}  // namespace tc
+
+size_t gram_tc_smem() { return tc::kStages * tc::kGramStage + 1024; }
+size_t rotate_tc_smem() { return tc::kStages * tc::kRotStage + 1024; }
+
+bool tc_setup() {
+  static int ok = -1;
+  if (ok < 0) {
+    ok = cudaFuncSetAttribute(tc::k_gram_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)gram_tc_smem()) ==
+                 cudaSuccess &&
+             cudaFuncSetAttribute(tc::k_rotate_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)rotate_tc_smem()) ==
+                 cudaSuccess;
+    cudaGetLastError();
+  }
+  return ok == 1;
+}
+
+void launch_gram_tc(const SubDev* d_subs, const GramPlan& gp, const float* F, const float* HF, double* Ms, double* Hs,
+                    int* status, cudaStream_t st) {
+  if (gp.n_jobs == 0) return;
+  tc::k_gram_tc<<<gp.n_jobs, tc::kThreads, gram_tc_smem(), st>>>(d_subs, gp.d_jobs, F, HF, gp.d_work, status);
+  dim3 grid(16, gp.n_groups);
+  tc::k_gram_reduce<<<grid, 256, 0, st>>>(d_subs, gp.d_jobs, gp.d_grp_first, gp.d_grp_n, gp.d_work, Ms, Hs);
+}
+
+void launch_rotate_tc(const SubDev* d_subs, int n_sub, const RotPlan& rp, const float* F, const double* Y, float* Out,
+                      int* status, cudaStream_t st) {
+  if (rp.n_jobs == 0) return;
+  dim3 gs(8, n_sub);
+  tc::k_split_yt<<<gs, 256, 0, st>>>(d_subs, Y, rp.kpad_max, rp.d_yhi, rp.d_ylo);
+  tc::k_rotate_tc<<<rp.n_jobs, tc::kThreads, rotate_tc_smem(), st>>>(d_subs, rp.d_jobs, F, rp.d_yhi, rp.d_ylo,
+                                                                     rp.kpad_max, Out, status);
+}
+
+}  // namespace xls

@@ -8,6 +8,9 @@
 #include <string>
 #include <vector>
 
+#include <cuda.h>
+#include <cstdlib>
+
 #include "xls_internal.h"
 
 using namespace xls;
@@ -62,10 +65,22 @@ struct xls_grid_s {
   double* out4 = nullptr;
   double* rho = nullptr;
   double* Vg = nullptr;
+  // TMA stencil (mixed path): classes of equal tile shape and the tensor maps of every
+  // (subdomain, block buffer, box height)
+  bool use_tma = false;
+  std::vector<TmaClass> tcls;
+  CUtensorMap* d_maps = nullptr;
+  // tensor-core GEMMs (mixed path)
+  bool use_tc = false;
+  GramPlan gplan;
+  RotPlan rplan;
   // projectors
   AtomImg* d_imgs = nullptr;
   ProjSlot* d_slots = nullptr;
   int n_slot = 0;
+  int* d_pidx = nullptr;          // projector tables: point index, chi (FP64 and, on the mixed path, FP32)
+  double4* d_chi64 = nullptr;
+  float4* d_chi32 = nullptr;
   double *P = nullptr, *P1 = nullptr;
   // Lanczos (single-vector view, FP64)
   double *lz_v = nullptr, *lz_vp = nullptr, *lz_f = nullptr, *lz_Hv = nullptr, *lz_a = nullptr, *lz_b = nullptr;
@@ -113,6 +128,8 @@ struct xls_grid_s {
 namespace {
 
 xls_status check_status(xls_grid g) {
+  const cudaError_t le = cudaGetLastError();
+  if (le != cudaSuccess) return fail(XLS_ECUDA, std::string("kernel launch: ") + cudaGetErrorString(le));
   int h[2] = {0, 0};
   XLS_CUDA(cudaMemcpyAsync(h, g->status, 2 * sizeof(int), cudaMemcpyDeviceToHost, g->st));
   XLS_CUDA(cudaStreamSynchronize(g->st));
@@ -121,6 +138,7 @@ xls_status check_status(xls_grid g) {
     if (h[0] == XLS_ENOTSPD)
       return fail(XLS_ENOTSPD, "Gram matrix M_s not positive definite in subdomain " + std::to_string(h[1]));
     if (h[0] == XLS_ENOCONV) return fail(XLS_ENOCONV, "Fermi level not bracketed: N_e exceeds the states' capacity");
+    if (h[0] == XLS_ETIMEOUT) return fail(XLS_ETIMEOUT, "a bounded device wait (TMA plane load) gave up");
     return fail((xls_status)h[0], "device error " + std::to_string(h[0]) + " in subdomain " + std::to_string(h[1]));
   }
   return XLS_OK;
@@ -137,6 +155,10 @@ xls_status make_plan(xls_grid g, const std::vector<SubDev>& v, Plan& plan) {
 
 template <typename T>
 T* blkp(xls_grid g, int i) { return (T*)g->blk[i]; }
+
+template <typename T> const typename Vec4<T>::type* chi_table(xls_grid g);
+template <> const double4* chi_table<double>(xls_grid g) { return g->d_chi64; }
+template <> const float4* chi_table<float>(xls_grid g) { return g->d_chi32; }
 
 // kernel classes of the profile
 enum { K_STENCIL = 0, K_NLPROJ = 1, K_NLBACK = 2, K_GRAM = 3, K_EIG = 4, K_ROTATE = 5, K_OTHER = 6 };
@@ -175,10 +197,32 @@ void h_step(xls_grid g, bool one, const T* yin, const T* yprev, T* yout, int ste
   double* P = one ? g->P1 : g->P;
   const int mns = one ? 1 : g->max_ns;
   const T* V = (sizeof(T) == 8) ? (const T*)g->V : (const T*)g->Vf;
-  { ProfScope ps(g, K_NLPROJ); launch_nl_project<T>(ds, g->d_slots, g->n_slot, g->d_imgs, mns, yin, P, g->st); }
+  { ProfScope ps(g, K_NLPROJ); launch_nl_project<T>(ds, g->d_slots, g->n_slot, g->d_pidx, chi_table<T>(g), mns, yin, P, g->st); }
   { ProfScope ps(g, K_STENCIL); launch_stencil<T>(ds, g->n_sub, pl, yin, yprev, yout, V, g->coef, step, g->st); }
-  { ProfScope ps(g, K_NLBACK); launch_nl_back<T>(ds, g->d_slots, g->n_slot, g->d_imgs, mns, P, yout, g->coef, step, g->st); }
+  { ProfScope ps(g, K_NLBACK); launch_nl_back<T>(ds, g->d_slots, g->n_slot, g->d_pidx, chi_table<T>(g), mns, P, yout, g->coef, step, g->st); }
   g->launches += (g->n_slot ? 3 : 1);
+}
+
+// same as h_step on the main view, with the blocks given by index (the TMA stencil addresses
+// its input through the tensor maps of that block)
+template <typename T>
+void h_step_main(xls_grid g, int bin, int bprev, int bout, int step) {
+  T* yin = (T*)g->blk[bin];
+  T* yprev = bprev >= 0 ? (T*)g->blk[bprev] : nullptr;
+  T* yout = (T*)g->blk[bout];
+  if (sizeof(T) == 4 && g->use_tma) {
+    { ProfScope ps(g, K_NLPROJ); launch_nl_project<T>(g->d_subs, g->d_slots, g->n_slot, g->d_pidx, chi_table<T>(g), g->max_ns, yin, g->P, g->st); }
+    {
+      ProfScope ps(g, K_STENCIL);
+      for (const TmaClass& c : g->tcls)
+        launch_stencil_tma(g->d_subs, c, g->d_maps, bin, (const float*)yprev, (float*)yout, g->Vf, g->coef, step,
+                           g->status, g->st);
+    }
+    { ProfScope ps(g, K_NLBACK); launch_nl_back<T>(g->d_subs, g->d_slots, g->n_slot, g->d_pidx, chi_table<T>(g), g->max_ns, g->P, yout, g->coef, step, g->st); }
+    g->launches += (g->n_slot ? 2 : 0) + (int)g->tcls.size();
+    return;
+  }
+  h_step<T>(g, false, yin, yprev, yout, step);
 }
 
 constexpr int kUnitStep = kMaxDegree - 1;
@@ -189,10 +233,10 @@ int run_filter(xls_grid g, int m) {
   launch_filter_coef(g->n_sub, g->bounds, m, g->coef, g->st);
   g->launches++;
   int ia = g->cur, ib = (g->cur + 1) % 3;
-  h_step<T>(g, false, blkp<T>(g, ia), nullptr, blkp<T>(g, ib), 1);
+  h_step_main<T>(g, ia, -1, ib, 1);
   int yk = ib, yprev = ia;
   for (int k = 2; k <= m; ++k) {
-    h_step<T>(g, false, blkp<T>(g, yk), blkp<T>(g, yprev), blkp<T>(g, yprev), k);
+    h_step_main<T>(g, yk, yprev, yprev, k);
     const int t = yk;
     yk = yprev;
     yprev = t;
@@ -210,7 +254,13 @@ int other(int a, int b) {
 template <typename T>
 void projection(xls_grid g, int f) {
   const int hf = other(f, f == 0 ? 1 : 0);
-  h_step<T>(g, false, blkp<T>(g, f), nullptr, blkp<T>(g, hf), kUnitStep);
+  h_step_main<T>(g, f, -1, hf, kUnitStep);
+  if (sizeof(T) == 4 && g->use_tc) {
+    ProfScope ps(g, K_GRAM);
+    launch_gram_tc(g->d_subs, g->gplan, (const float*)g->blk[f], (const float*)g->blk[hf], g->Ms, g->Hs, g->status, g->st);
+    g->launches += 2;
+    return;
+  }
   cudaMemsetAsync(g->Ms, 0, g->tot_ss * sizeof(double), g->st);
   cudaMemsetAsync(g->Hs, 0, g->tot_ss * sizeof(double), g->st);
   { ProfScope ps(g, K_GRAM); launch_gram<T>(g->d_subs, g->n_sub, g->max_ns, g->max_nd, blkp<T>(g, f), blkp<T>(g, hf), g->Ms, g->Hs, g->st); }
@@ -229,7 +279,14 @@ void eigensolve(xls_grid g) {
 template <typename T>
 void rotation(xls_grid g, int f) {
   const int out = other(f, f == 0 ? 1 : 0);
-  { ProfScope ps(g, K_ROTATE); launch_rotate<T>(g->d_subs, g->n_sub, g->max_ns, g->max_nd, blkp<T>(g, f), g->Y, blkp<T>(g, out), g->st); }
+  if (sizeof(T) == 4 && g->use_tc) {
+    ProfScope ps(g, K_ROTATE);
+    launch_rotate_tc(g->d_subs, g->n_sub, g->rplan, (const float*)g->blk[f], g->Y, (float*)g->blk[out], g->status, g->st);
+    g->launches += 1;
+  } else {
+    ProfScope ps(g, K_ROTATE);
+    launch_rotate<T>(g->d_subs, g->n_sub, g->max_ns, g->max_nd, blkp<T>(g, f), g->Y, blkp<T>(g, out), g->st);
+  }
   { ProfScope ps(g, K_OTHER); launch_core_weights<T>(g->d_subs, g->n_sub, g->max_ns, blkp<T>(g, out), g->cw, g->st); }
   launch_bounds_from_ritz(g->d_subs, g->n_sub, g->lam, g->bounds, g->st);
   g->launches += 3;
@@ -488,6 +545,112 @@ xls_status xls_grid_create(const xls_cell* cell, const xls_dc* dc, int precision
     xls_grid_destroy(g);
     return s;
   }
+  if (precision == XLS_MIXED_BF16) {
+    const char* env = std::getenv("XLS_STENCIL");
+    bool ok = !(env && std::string(env) == "generic");
+    for (const SubDev& S : g->subs) ok = ok && tma_eligible(S);
+    if (ok) {
+      std::vector<CUtensorMap> maps((size_t)g->n_sub * 6);
+      for (int a = 0; a < g->n_sub && ok; ++a) ok = build_tma_maps(g->subs[a], a, g->blk, (CUtensorMap_st*)&maps[(size_t)a * 6]);
+      if (ok) {
+        // classes of equal (x-points/4, rows per tile, row width)
+        std::vector<std::vector<int>> members;
+        std::vector<TmaClass> cls;
+        for (int a = 0; a < g->n_sub; ++a) {
+          const SubDev& S = g->subs[a];
+          const int nq = S.n[0] / 4, ty = tma_tile_rows(S), W = tma_row_width(S);
+          size_t k = 0;
+          for (; k < cls.size(); ++k)
+            if (cls[k].nq == nq && cls[k].TY == ty && cls[k].W == W) break;
+          if (k == cls.size()) {
+            TmaClass c;
+            c.nq = nq; c.TY = ty; c.W = W;
+            cls.push_back(c);
+            members.emplace_back();
+          }
+          members[k].push_back(a);
+        }
+        for (size_t k = 0; k < cls.size() && s == XLS_OK; ++k) {
+          std::vector<TmaJob> jobs;
+          std::vector<int> off(1, 0);
+          for (int a : members[k]) {
+            const SubDev& S = g->subs[a];
+            const int nyt = (S.n[1] + cls[k].TY - 1) / cls[k].TY;
+            jobs.push_back(TmaJob{a, nyt, cls[k].W, 0});
+            off.push_back(off.back() + nyt * S.ns);
+          }
+          cls[k].n_jobs = (int)jobs.size();
+          cls[k].total = off.back();
+          if ((s = g->alloc(&cls[k].d_jobs, jobs.size() * sizeof(TmaJob))) != XLS_OK) break;
+          if ((s = g->alloc(&cls[k].d_job_off, off.size() * sizeof(int))) != XLS_OK) break;
+          cudaMemcpy(cls[k].d_jobs, jobs.data(), jobs.size() * sizeof(TmaJob), cudaMemcpyHostToDevice);
+          cudaMemcpy(cls[k].d_job_off, off.data(), off.size() * sizeof(int), cudaMemcpyHostToDevice);
+        }
+        if (s == XLS_OK) s = g->alloc(&g->d_maps, maps.size() * sizeof(CUtensorMap));
+        if (s != XLS_OK) {
+          xls_grid_destroy(g);
+          return s;
+        }
+        cudaMemcpy(g->d_maps, maps.data(), maps.size() * sizeof(CUtensorMap), cudaMemcpyHostToDevice);
+        g->tcls = cls;
+        g->use_tma = true;
+      }
+    }
+  }
+  if (precision == XLS_MIXED_BF16) {
+    const char* env = std::getenv("XLS_GEMM");
+    bool ok = !(env && std::string(env) == "simt") && tc_setup();
+    for (const SubDev& S : g->subs) ok = ok && S.ns <= 256 && S.nd % 8 == 0;
+    if (ok) {
+      // Gram jobs: upper block triangle of every subdomain, K split so that the grid fills the GPU
+      int groups = 0;
+      for (const SubDev& S : g->subs) {
+        const int nt = (S.ns + 127) / 128;
+        groups += nt * (nt + 1) / 2;
+      }
+      const int kchunks = std::max(1, (4 * 152 + groups - 1) / groups);
+      std::vector<GramJob> jobs;
+      std::vector<int> gfirst, gn;
+      for (int a = 0; a < g->n_sub; ++a) {
+        const SubDev& S = g->subs[a];
+        const int nt = (S.ns + 127) / 128;
+        const int nkt = (int)((S.nd + 63) / 64);
+        const int kc = std::min(kchunks, nkt);
+        for (int I = 0; I < nt; ++I)
+          for (int J = I; J < nt; ++J) {
+            gfirst.push_back((int)jobs.size());
+            for (int c = 0; c < kc; ++c)
+              jobs.push_back(GramJob{a, I, J, (int)((long long)nkt * c / kc), (int)((long long)nkt * (c + 1) / kc), 0});
+            gn.push_back(kc);
+          }
+      }
+      GramPlan& gp = g->gplan;
+      gp.n_jobs = (int)jobs.size();
+      gp.n_groups = (int)gfirst.size();
+      if ((s = g->alloc(&gp.d_jobs, jobs.size() * sizeof(GramJob))) == XLS_OK &&
+          (s = g->alloc(&gp.d_grp_first, gfirst.size() * sizeof(int))) == XLS_OK &&
+          (s = g->alloc(&gp.d_grp_n, gn.size() * sizeof(int))) == XLS_OK)
+        s = g->alloc(&gp.d_work, jobs.size() * 2 * 128 * 128 * sizeof(float));
+      std::vector<RotJob> rj;
+      for (int a = 0; a < g->n_sub; ++a)
+        for (int t = 0; t < (int)((g->subs[a].nd + 127) / 128); ++t) rj.push_back(RotJob{a, t});
+      RotPlan& rp = g->rplan;
+      rp.n_jobs = (int)rj.size();
+      rp.kpad_max = ((g->max_ns + 63) / 64) * 64;
+      if (s == XLS_OK && (s = g->alloc(&rp.d_jobs, rj.size() * sizeof(RotJob))) == XLS_OK &&
+          (s = g->alloc(&rp.d_yhi, (size_t)g->tot_states * rp.kpad_max * sizeof(uint16_t))) == XLS_OK)
+        s = g->alloc(&rp.d_ylo, (size_t)g->tot_states * rp.kpad_max * sizeof(uint16_t));
+      if (s != XLS_OK) {
+        xls_grid_destroy(g);
+        return s;
+      }
+      cudaMemcpy(gp.d_jobs, jobs.data(), jobs.size() * sizeof(GramJob), cudaMemcpyHostToDevice);
+      cudaMemcpy(gp.d_grp_first, gfirst.data(), gfirst.size() * sizeof(int), cudaMemcpyHostToDevice);
+      cudaMemcpy(gp.d_grp_n, gn.data(), gn.size() * sizeof(int), cudaMemcpyHostToDevice);
+      cudaMemcpy(rp.d_jobs, rj.data(), rj.size() * sizeof(RotJob), cudaMemcpyHostToDevice);
+      g->use_tc = true;
+    }
+  }
   cudaMemset(g->status, 0, 2 * sizeof(int));
   cudaMemset(g->lz_b, 0, 16 * g->n_sub * sizeof(double));
   cudaMemset(g->cw, 0, g->tot_states * sizeof(double));
@@ -613,6 +776,33 @@ xls_status xls_hamiltonian_set(xls_grid g, const double* veff, int veff_on_devic
     XLS_CUDA(cudaMemcpyAsync(g->d_slots, slots.data(), slots.size() * sizeof(ProjSlot), cudaMemcpyHostToDevice, g->st));
   XLS_CUDA(cudaMemcpyAsync(g->d_subs, g->subs.data(), g->n_sub * sizeof(SubDev), cudaMemcpyHostToDevice, g->st));
   XLS_CUDA(cudaMemcpyAsync(g->d_subs1, g->subs1.data(), g->n_sub * sizeof(SubDev), cudaMemcpyHostToDevice, g->st));
+  // projector tables: count the points of every slot, lay the tables out, fill them
+  g->release(&g->d_pidx);
+  g->release(&g->d_chi64);
+  g->release(&g->d_chi32);
+  if (!slots.empty()) {
+    int* dcnt = nullptr;
+    XLS_CUDA(cudaMalloc(&dcnt, slots.size() * sizeof(int)));
+    launch_proj_table_count<double>(g->d_subs, g->d_slots, g->n_slot, g->d_imgs, dcnt, g->st);
+    std::vector<int> cnt(slots.size());
+    XLS_CUDA(cudaMemcpyAsync(cnt.data(), dcnt, cnt.size() * sizeof(int), cudaMemcpyDeviceToHost, g->st));
+    XLS_CUDA(cudaStreamSynchronize(g->st));
+    cudaFree(dcnt);
+    long long tot = 0;
+    for (size_t k = 0; k < slots.size(); ++k) {
+      slots[k].pt_off = tot;
+      slots[k].pt_n = cnt[k];
+      tot += cnt[k];
+    }
+    XLS_CUDA(cudaMemcpyAsync(g->d_slots, slots.data(), slots.size() * sizeof(ProjSlot), cudaMemcpyHostToDevice, g->st));
+    if ((s = g->alloc(&g->d_pidx, std::max<long long>(tot, 1) * sizeof(int))) != XLS_OK) return s;
+    if ((s = g->alloc(&g->d_chi64, std::max<long long>(tot, 1) * sizeof(double4))) != XLS_OK) return s;
+    launch_proj_table_fill<double>(g->d_subs, g->d_slots, g->n_slot, g->d_imgs, g->d_pidx, g->d_chi64, g->st);
+    if (g->prec == XLS_MIXED_BF16) {
+      if ((s = g->alloc(&g->d_chi32, std::max<long long>(tot, 1) * sizeof(float4))) != XLS_OK) return s;
+      launch_proj_table_fill<float>(g->d_subs, g->d_slots, g->n_slot, g->d_imgs, g->d_pidx, g->d_chi32, g->st);
+    }
+  }
   // unit coefficients (plain H) for every subdomain, then the Lanczos bound b
   std::vector<double> bz(3 * g->n_sub, 1.0);
   for (int a = 0; a < g->n_sub; ++a) { bz[3 * a] = 2.0; bz[3 * a + 1] = 1.0; bz[3 * a + 2] = 0.0; }
@@ -710,7 +900,7 @@ xls_status xls_hamiltonian_apply(xls_grid g, int sub, int k, const double* x, do
     XLS_CUDA(cudaMalloc(&dtmp, n * sizeof(double)));
     XLS_CUDA(cudaMemcpyAsync(dtmp, x, n * sizeof(double), kin, g->st));
     launch_convert_f64_f32(dtmp, (float*)g->blk[in] + S.off_blk, n, g->st);
-    h_step<float>(g, false, (float*)g->blk[in], nullptr, (float*)g->blk[outb], kUnitStep);
+    h_step_main<float>(g, in, -1, outb, kUnitStep);
     launch_convert_f32_f64((float*)g->blk[outb] + S.off_blk, dtmp, n, g->st);
     XLS_CUDA(cudaMemcpyAsync(y, dtmp, n * sizeof(double), kout, g->st));
     XLS_CUDA(cudaStreamSynchronize(g->st));

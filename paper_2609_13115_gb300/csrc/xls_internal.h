@@ -47,6 +47,9 @@ struct ProjSlot {
   int sub;               // owning subdomain
   int atom;              // global atom index
   int img_lo, img_n;     // range in the image array
+  long long pt_off;      // first entry of this slot's point table
+  int pt_n;              // points of the table (grid points of the subdomain inside any image's sphere)
+  int pad;
   double w, rcut2;       // projector width and squared cutoff
   double norm[4];        // grid normalisation of chi_s, chi_px, chi_py, chi_pz
   double E[4];           // KB energies E_s, E_p, E_p, E_p
@@ -58,6 +61,48 @@ struct StepCoef {
 };
 constexpr int kMaxDegree = 64;
 
+// TMA stencil: subdomains grouped in classes of equal tile shape (one launch per class).
+struct TmaJob {
+  int sub;        // subdomain
+  int n_ytiles;   // row tiles per vector
+  int W;          // staged row width (floats)
+  int pad;
+};
+struct TmaClass {
+  int nq = 0, TY = 0, W = 0;   // threads per row (x-points / 4), rows per tile, row width
+  int n_jobs = 0, total = 0;   // subdomains and CTAs of the class
+  TmaJob* d_jobs = nullptr;
+  int* d_job_off = nullptr;    // [n_jobs + 1] CTA prefix
+};
+
+// Tensor-core Gram: CTA jobs (subdomain, 128x128 block (I <= J), range of 64-point K tiles);
+// jobs of one (subdomain, block) are consecutive and form a reduction group.
+struct GramJob {
+  int sub, I, J, kt0, kt1, pad;
+};
+struct GramPlan {
+  int n_jobs = 0, n_groups = 0;
+  GramJob* d_jobs = nullptr;
+  int* d_grp_first = nullptr;
+  int* d_grp_n = nullptr;
+  float* d_work = nullptr;     // [n_jobs][2][128][128] FP32 partial sums
+};
+// Tensor-core rotation: CTA jobs (subdomain, tile of 128 grid points)
+struct RotJob {
+  int sub, tile;
+};
+struct RotPlan {
+  int n_jobs = 0, kpad_max = 0;
+  RotJob* d_jobs = nullptr;
+  uint16_t* d_yhi = nullptr;   // Y^T split into bf16 hi / lo, [states][kpad_max]
+  uint16_t* d_ylo = nullptr;
+};
+bool tc_setup();
+void launch_gram_tc(const SubDev* d_subs, const GramPlan& gp, const float* F, const float* HF, double* Ms, double* Hs,
+                    int* status, cudaStream_t st);
+void launch_rotate_tc(const SubDev* d_subs, int n_sub, const RotPlan& rp, const float* F, const double* Y, float* Out,
+                      int* status, cudaStream_t st);
+
 // Launch plan of a block-wise kernel over all subdomains of a view: prefix of CTA counts.
 struct Plan {
   int* d_blk_off = nullptr;   // [n_sub + 1]
@@ -68,13 +113,35 @@ struct Plan {
 template <typename T>
 void launch_stencil(const SubDev* d_subs, int n_sub, const Plan& plan, const T* Yin, const T* Yprev,
                     T* Yout, const T* V, const StepCoef* coef, int step, cudaStream_t st);
+// Projector tables: for every slot, its grid points (local flat index) and the four chi values
+// there, in the precision T of the block (chi of type T4: double4 / float4).
+template <typename T> struct Vec4;
+template <> struct Vec4<double> { using type = double4; };
+template <> struct Vec4<float> { using type = float4; };
 template <typename T>
-void launch_nl_project(const SubDev* d_subs, const ProjSlot* d_slots, int n_slot, const AtomImg* d_imgs, int max_ns,
-                       const T* Y, double* P, cudaStream_t st);
+void launch_proj_table_count(const SubDev* d_subs, const ProjSlot* d_slots, int n_slot, const AtomImg* d_imgs,
+                             int* counts, cudaStream_t st);
 template <typename T>
-void launch_nl_back(const SubDev* d_subs, const ProjSlot* d_slots, int n_slot, const AtomImg* d_imgs, int max_ns,
-                    const double* P, T* Yout, const StepCoef* coef, int step, cudaStream_t st);
+void launch_proj_table_fill(const SubDev* d_subs, const ProjSlot* d_slots, int n_slot, const AtomImg* d_imgs,
+                            int* idx, typename Vec4<T>::type* chi, cudaStream_t st);
+template <typename T>
+void launch_nl_project(const SubDev* d_subs, const ProjSlot* d_slots, int n_slot, const int* idx,
+                       const typename Vec4<T>::type* chi, int max_ns, const T* Y, double* P, cudaStream_t st);
+template <typename T>
+void launch_nl_back(const SubDev* d_subs, const ProjSlot* d_slots, int n_slot, const int* idx,
+                    const typename Vec4<T>::type* chi, int max_ns, const double* P, T* Yout, const StepCoef* coef,
+                    int step, cudaStream_t st);
 int stencil_blocks(const int n[3], int ns);
+}  // namespace xls
+struct CUtensorMap_st;
+namespace xls {
+bool tma_eligible(const SubDev& S);
+int tma_tile_rows(const SubDev& S);
+int tma_row_width(const SubDev& S);
+bool build_tma_maps(const SubDev& S, int sub, void* const bufs[3], struct CUtensorMap_st* out);
+void launch_stencil_tma(const SubDev* d_subs, const TmaClass& cls, const struct CUtensorMap_st* d_maps, int buf_in,
+                        const float* Yprev, float* Yout, const float* V, const StepCoef* coef, int step, int* status,
+                        cudaStream_t st);
 
 // ---- dense subspace work -------------------------------------------------------------------
 template <typename T>

@@ -180,9 +180,9 @@ def test_full_passes_fp64(wname):
     assert relerr(rho, ref.rho) < 1e-7
 
 
-@pytest.mark.parametrize("wname", ["cfg0", "dirichlet"])
+@pytest.mark.parametrize("wname", ["cfg0", "dirichlet", "dirichlet20"])
 def test_full_passes_mixed(wname):
-    w = synth.workload(0) if wname == "cfg0" else dirichlet_workload()
+    w = {"cfg0": lambda: synth.workload(0), "dirichlet": dirichlet_workload, "dirichlet20": lambda: dirichlet20_workload()}[wname]()
     V = pseudo.local_potential(w)
     ref, lam, rho, mu, eb, es = _run_both(w, V, xls.XLS_MIXED_BF16, w.n_passes)
     n_atoms = len(w.pos)
@@ -192,3 +192,73 @@ def test_full_passes_mixed(wname):
     for a in range(w.n_sub):
         occ = ref.lam[a] < ref.mu + 0.1
         np.testing.assert_allclose(lam[a][0][occ], ref.lam[a][occ], atol=1e-4)
+
+
+def dirichlet20_workload():
+    """One Si cell on a 24^3 grid cut into 8 subdomains of 20^3 (core 12, buffer 4): x-extent a
+    multiple of 4 and a ragged last row tile, the shape class of the TMA-staged stencil."""
+    w = dirichlet_workload()
+    w.buf = np.full((8, 3), 4)
+    w.name = "si8_dc8_dirichlet20"
+    return w
+
+
+@pytest.mark.parametrize("wname", ["cfg0", "dirichlet20"])
+def test_tma_stencil_matches_oracle_and_generic(wname, monkeypatch):
+    w = synth.workload(0) if wname == "cfg0" else dirichlet20_workload()
+    V = pseudo.local_potential(w)
+    subs, ops = oracle_ops(w, V)
+    xs = [synth.psi0_block(300 + a, subs[a].N, 6) for a in range(w.n_sub)]
+    outs = {}
+    for mode in ("tma", "generic"):
+        if mode == "generic":
+            monkeypatch.setenv("XLS_STENCIL", "generic")
+        else:
+            monkeypatch.delenv("XLS_STENCIL", raising=False)
+        with make_grid(w, V, xls.XLS_MIXED_BF16) as g:
+            outs[mode] = []
+            for a in range(w.n_sub):
+                y = np.zeros_like(xs[a])
+                xls.xls_hamiltonian_apply(g.h, a, xs[a], y)
+                outs[mode].append(y)
+    for a in range(w.n_sub):
+        ref = ops[a].apply(xs[a])
+        assert relerr(outs["tma"][a], ref) < 2e-6, (a, relerr(outs["tma"][a], ref))
+        assert relerr(outs["tma"][a], outs["generic"][a]) < 2e-6
+
+
+def test_eigensolver_large_block_matches_lapack():
+    """N_s = 160 (the bench's block size): Ritz values of the GPU's own M_s, H_s against the
+    oracle's Cholesky + symmetric eigensolve of the same matrices; orthonormal rotated block."""
+    w = synth.workload(0)
+    w.n_states = np.array([160])
+    V = pseudo.local_potential(w)
+    subs = dc.partition(w)
+    psi0 = synth.psi0_block(4242, subs[0].N, 160)
+    with make_grid(w, V, xls.XLS_FP64) as g:
+        xls.xls_orbitals_set(g.h, 0, psi0)
+        xls.xls_chefsi_stage(g.h, 2, 16)
+        Ms, Hs = xls.xls_get_subspace(g.h, 0, 160)
+        xls.xls_chefsi_stage(g.h, 3, 16)
+        lam, _ = xls.xls_get_eigs(g.h, 0, 160)
+        xls.xls_chefsi_stage(g.h, 4, 16)
+        Psi = xls.xls_orbitals_get(g.h, 0, np.zeros((160, subs[0].N)))
+    lam_ref, _ = chefsi.generalized_eig(0.5 * (Hs + Hs.T), Ms)
+    np.testing.assert_allclose(lam, lam_ref, atol=1e-10 * np.abs(lam_ref).max())
+    np.testing.assert_allclose(Psi @ Psi.T, np.eye(160), atol=1e-10)
+
+
+def test_eigensolver_large_block_mixed():
+    w = synth.workload(0)
+    w.n_states = np.array([160])
+    V = pseudo.local_potential(w)
+    subs = dc.partition(w)
+    psi0 = synth.psi0_block(4243, subs[0].N, 160)
+    with make_grid(w, V, xls.XLS_MIXED_BF16) as g:
+        xls.xls_orbitals_set(g.h, 0, psi0)
+        xls.xls_chefsi_batch(g.h, 16, 2)
+        lam, c = xls.xls_get_eigs(g.h, 0, 160)
+        Psi = xls.xls_orbitals_get(g.h, 0, np.zeros((160, subs[0].N)))
+    assert np.all(np.isfinite(lam)) and np.all(np.diff(lam) >= -1e-12)
+    np.testing.assert_allclose(Psi @ Psi.T, np.eye(160), atol=1e-4)
+    np.testing.assert_allclose(c, 1.0, atol=1e-4)
