@@ -268,18 +268,25 @@ k_nl_project(const SubDev* __restrict__ subs, const ProjSlot* __restrict__ slots
   const T* yb = Y + S.off_blk + (long long)v0 * S.nd;
   const int* ix = idx + A.pt_off;
   const typename Vec4<T>::type* cx = chi + A.pt_off;
-  for (int p = lane; p < A.pt_n; p += 32) {
-    const int g = ix[p];
+  for (int p = lane; p < A.pt_n; p += 64) {
+    // two points per lane per iteration: 16 independent loads in flight
+    const bool two = p + 32 < A.pt_n;
+    const int g0 = ix[p], g1 = two ? ix[p + 32] : g0;
     const typename Vec4<T>::type c = cx[p];
+    typename Vec4<T>::type d = cx[two ? p + 32 : p];
+    if (!two) { d.x = (T)0; d.y = (T)0; d.z = (T)0; d.w = (T)0; }
+    T y0[kNlVec], y1[kNlVec];
 #pragma unroll
     for (int v = 0; v < kNlVec; ++v) {
-      if (v < nv) {
-        const T y = yb[(long long)v * S.nd + g];
-        acc[0][v] += c.x * y;
-        acc[1][v] += c.y * y;
-        acc[2][v] += c.z * y;
-        acc[3][v] += c.w * y;
-      }
+      y0[v] = (v < nv) ? yb[(long long)v * S.nd + g0] : (T)0;
+      y1[v] = (v < nv) ? yb[(long long)v * S.nd + g1] : (T)0;
+    }
+#pragma unroll
+    for (int v = 0; v < kNlVec; ++v) {
+      acc[0][v] += c.x * y0[v] + d.x * y1[v];
+      acc[1][v] += c.y * y0[v] + d.y * y1[v];
+      acc[2][v] += c.z * y0[v] + d.z * y1[v];
+      acc[3][v] += c.w * y0[v] + d.w * y1[v];
     }
   }
 #pragma unroll
@@ -330,6 +337,109 @@ k_nl_back(const SubDev* __restrict__ subs, const ProjSlot* __restrict__ slots, c
   }
 }
 
+// ---- reverse tables for the back-projection (the paper's reverse CSR over grid points) -----
+// row g of subdomain a (global point index S.off_pt + g) lists (slot - S.slot_lo, chi) of every
+// slot whose sphere contains the point
+__global__ void k_rcsr_count(const SubDev* __restrict__ subs, const ProjSlot* __restrict__ slots,
+                             const int* __restrict__ idx, int* cnt) {
+  const ProjSlot& A = slots[blockIdx.x];
+  const SubDev& S = subs[A.sub];
+  for (int p = threadIdx.x; p < A.pt_n; p += blockDim.x) atomicAdd(cnt + S.off_pt + idx[A.pt_off + p], 1);
+}
+
+template <typename T>
+__global__ void k_rcsr_fill(const SubDev* __restrict__ subs, const ProjSlot* __restrict__ slots,
+                            const int* __restrict__ idx, const typename Vec4<T>::type* __restrict__ chi,
+                            const long long* __restrict__ row_ptr, int* cursor, int* rslot,
+                            typename Vec4<T>::type* rchi) {
+  const ProjSlot& A = slots[blockIdx.x];
+  const SubDev& S = subs[A.sub];
+  for (int p = threadIdx.x; p < A.pt_n; p += blockDim.x) {
+    const long long row = S.off_pt + idx[A.pt_off + p];
+    const long long e = row_ptr[row] + atomicAdd(cursor + row, 1);
+    rslot[e] = (int)blockIdx.x - S.slot_lo;
+    rchi[e] = chi[A.pt_off + p];
+  }
+}
+
+constexpr int kBackPts = 1024, kBackVec = 8;
+
+// Y_out[v][g] += scale * sum over the slots s of point g of sum_l chi_l(g) P[s][l][v]
+template <typename T>
+__global__ void __launch_bounds__(256)
+k_nl_back_csr(const SubDev* __restrict__ subs, const long long* __restrict__ row_ptr, const int* __restrict__ rslot,
+              const typename Vec4<T>::type* __restrict__ rchi, const double* __restrict__ P, T* Yout,
+              const StepCoef* __restrict__ coef, int step) {
+  using T4 = typename Vec4<T>::type;
+  extern __shared__ __align__(16) unsigned char qsm[];
+  T4* Qs = reinterpret_cast<T4*>(qsm);   // [slot][kBackVec]
+  const SubDev& S = subs[blockIdx.y];
+  const int v0 = blockIdx.z * kBackVec;
+  const long long p0 = (long long)blockIdx.x * kBackPts;
+  if (v0 >= S.ns || p0 >= S.nd || S.slot_n == 0) return;
+  const int nv = min(kBackVec, S.ns - v0);
+  const double scale = coef[blockIdx.y * kMaxDegree + step].scale;
+  for (int q = threadIdx.x; q < S.slot_n * kBackVec; q += blockDim.x) {
+    const int sl = q / kBackVec, v = q % kBackVec;
+    T4 x;
+    if (v < nv) {
+      const double* pa = P + S.off_proj + (long long)sl * 4 * S.ns + v0 + v;
+      x.x = (T)(scale * pa[0]); x.y = (T)(scale * pa[S.ns]); x.z = (T)(scale * pa[2 * S.ns]); x.w = (T)(scale * pa[3 * S.ns]);
+    } else {
+      x.x = x.y = x.z = x.w = (T)0;
+    }
+    Qs[q] = x;
+  }
+  __syncthreads();
+  T* yb = Yout + S.off_blk + (long long)v0 * S.nd;
+  for (long long g = p0 + threadIdx.x; g < min(S.nd, p0 + kBackPts); g += blockDim.x) {
+    const long long r0 = row_ptr[S.off_pt + g], r1 = row_ptr[S.off_pt + g + 1];
+    if (r0 == r1) continue;
+    T acc[kBackVec];
+#pragma unroll
+    for (int v = 0; v < kBackVec; ++v) acc[v] = (T)0;
+    for (long long e = r0; e < r1; ++e) {
+      const int sl = rslot[e];
+      const T4 c = rchi[e];
+      const T4* qq = Qs + sl * kBackVec;
+#pragma unroll
+      for (int v = 0; v < kBackVec; ++v) {
+        const T4 q = qq[v];
+        acc[v] += c.x * q.x + c.y * q.y + c.z * q.z + c.w * q.w;
+      }
+    }
+#pragma unroll
+    for (int v = 0; v < kBackVec; ++v)
+      if (v < nv) yb[(long long)v * S.nd + g] += acc[v];
+  }
+}
+
+template <typename T>
+void launch_rcsr_build(const SubDev* d_subs, const ProjSlot* d_slots, int n_slot, const int* idx,
+                       const typename Vec4<T>::type* chi, const long long* row_ptr, int* cursor, int* rslot,
+                       typename Vec4<T>::type* rchi, cudaStream_t st) {
+  if (n_slot) k_rcsr_fill<T><<<n_slot, 256, 0, st>>>(d_subs, d_slots, idx, chi, row_ptr, cursor, rslot, rchi);
+}
+void launch_rcsr_count(const SubDev* d_subs, const ProjSlot* d_slots, int n_slot, const int* idx, int* cnt,
+                       cudaStream_t st) {
+  if (n_slot) k_rcsr_count<<<n_slot, 256, 0, st>>>(d_subs, d_slots, idx, cnt);
+}
+
+template <typename T>
+void launch_nl_back_csr(const SubDev* d_subs, int n_sub, long long max_nd, int max_ns, int max_slots,
+                        const long long* row_ptr, const int* rslot, const typename Vec4<T>::type* rchi,
+                        const double* P, T* Yout, const StepCoef* coef, int step, cudaStream_t st) {
+  if (max_slots == 0) return;
+  const size_t smem = (size_t)max_slots * kBackVec * sizeof(typename Vec4<T>::type);
+  static size_t attr = 0;
+  if (smem > 48 * 1024 && smem > attr) {
+    cudaFuncSetAttribute(k_nl_back_csr<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    attr = smem;
+  }
+  dim3 grid((unsigned)((max_nd + kBackPts - 1) / kBackPts), n_sub, (max_ns + kBackVec - 1) / kBackVec);
+  k_nl_back_csr<T><<<grid, 256, smem, st>>>(d_subs, row_ptr, rslot, rchi, P, Yout, coef, step);
+}
+
 template <typename T>
 void launch_proj_table_count(const SubDev* d_subs, const ProjSlot* d_slots, int n_slot, const AtomImg* d_imgs,
                              int* counts, cudaStream_t st) {
@@ -365,7 +475,11 @@ void launch_nl_back(const SubDev* d_subs, const ProjSlot* d_slots, int n_slot, c
   template void launch_nl_project<T>(const SubDev*, const ProjSlot*, int, const int*, const Vec4<T>::type*, int,     \
                                      const T*, double*, cudaStream_t);                                               \
   template void launch_nl_back<T>(const SubDev*, const ProjSlot*, int, const int*, const Vec4<T>::type*, int,        \
-                                  const double*, T*, const StepCoef*, int, cudaStream_t);
+                                  const double*, T*, const StepCoef*, int, cudaStream_t);                            \
+  template void launch_rcsr_build<T>(const SubDev*, const ProjSlot*, int, const int*, const Vec4<T>::type*,         \
+                                     const long long*, int*, int*, Vec4<T>::type*, cudaStream_t);                    \
+  template void launch_nl_back_csr<T>(const SubDev*, int, long long, int, int, const long long*, const int*,        \
+                                      const Vec4<T>::type*, const double*, T*, const StepCoef*, int, cudaStream_t);
 XLS_INST_NL(double)
 XLS_INST_NL(float)
 

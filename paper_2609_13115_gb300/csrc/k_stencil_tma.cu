@@ -157,6 +157,19 @@ k_stencil_tma(const SubDev* __restrict__ subs, const TmaJob* __restrict__ jobs, 
   float4 q[2 * kN0 + 1];
 #pragma unroll
   for (int k = 0; k < 2 * kN0 + 1; ++k) q[k] = make_float4(0.f, 0.f, 0.f, 0.f);
+  // V and Y_prev of the next output plane are loaded one iteration ahead (their HBM latency
+  // then overlaps a plane of work)
+  const bool io = active && row_ok;
+  auto ld_v = [&](int zo_) -> float4 {
+    return (io && zo_ < nz) ? *reinterpret_cast<const float4*>(V + (long long)zo_ * plane_sz + (long long)y * nx + x4)
+                            : make_float4(0.f, 0.f, 0.f, 0.f);
+  };
+  auto ld_p = [&](int zo_) -> float4 {
+    return (io && Yprev && zo_ < nz)
+               ? *reinterpret_cast<const float4*>(Yprev + base + (long long)zo_ * plane_sz + (long long)y * nx + x4)
+               : make_float4(0.f, 0.f, 0.f, 0.f);
+  };
+  float4 v_next = ld_v(0), p_next = ld_p(0);
 
   for (int pi = 0; pi < nplanes; ++pi) {
     const int slot = pi % kSlots;
@@ -218,18 +231,17 @@ k_stencil_tma(const SubDev* __restrict__ subs, const TmaJob* __restrict__ jobs, 
         acc[3] += wz[p] * (zu.w + zd.w);
       }
       const long long g = (long long)zo * plane_sz + (long long)y * nx + x4;
-      const float4 v4 = *reinterpret_cast<const float4*>(V + g);
+      const float4 v4 = v_next, pv = p_next;
+      v_next = ld_v(zo + 1);
+      p_next = ld_p(zo + 1);
       const float vv[4] = {v4.x, v4.y, v4.z, v4.w};
       float o[4];
 #pragma unroll
       for (int r = 0; r < 4; ++r) o[r] = scale * (acc[r] + vv[r] * cv[r] - cshift * cv[r]);
-      if (Yprev) {
-        const float4 pv = *reinterpret_cast<const float4*>(Yprev + base + g);
-        o[0] -= pshift * pv.x;
-        o[1] -= pshift * pv.y;
-        o[2] -= pshift * pv.z;
-        o[3] -= pshift * pv.w;
-      }
+      o[0] -= pshift * pv.x;
+      o[1] -= pshift * pv.y;
+      o[2] -= pshift * pv.z;
+      o[3] -= pshift * pv.w;
       *reinterpret_cast<float4*>(Yout + base + g) = make_float4(o[0], o[1], o[2], o[3]);
     }
     __syncthreads();  // every thread is done with plane index pi - 6 (x/y of output zo)

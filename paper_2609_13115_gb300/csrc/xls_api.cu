@@ -81,6 +81,11 @@ struct xls_grid_s {
   int* d_pidx = nullptr;          // projector tables: point index, chi (FP64 and, on the mixed path, FP32)
   double4* d_chi64 = nullptr;
   float4* d_chi32 = nullptr;
+  long long* d_rptr = nullptr;    // reverse tables (rows = grid points of every subdomain)
+  int* d_rslot = nullptr;
+  double4* d_rchi64 = nullptr;
+  float4* d_rchi32 = nullptr;
+  int max_slots = 0;
   double *P = nullptr, *P1 = nullptr;
   // Lanczos (single-vector view, FP64)
   double *lz_v = nullptr, *lz_vp = nullptr, *lz_f = nullptr, *lz_Hv = nullptr, *lz_a = nullptr, *lz_b = nullptr;
@@ -159,6 +164,9 @@ T* blkp(xls_grid g, int i) { return (T*)g->blk[i]; }
 template <typename T> const typename Vec4<T>::type* chi_table(xls_grid g);
 template <> const double4* chi_table<double>(xls_grid g) { return g->d_chi64; }
 template <> const float4* chi_table<float>(xls_grid g) { return g->d_chi32; }
+template <typename T> const typename Vec4<T>::type* rchi_table(xls_grid g);
+template <> const double4* rchi_table<double>(xls_grid g) { return g->d_rchi64; }
+template <> const float4* rchi_table<float>(xls_grid g) { return g->d_rchi32; }
 
 // kernel classes of the profile
 enum { K_STENCIL = 0, K_NLPROJ = 1, K_NLBACK = 2, K_GRAM = 3, K_EIG = 4, K_ROTATE = 5, K_OTHER = 6 };
@@ -199,7 +207,9 @@ void h_step(xls_grid g, bool one, const T* yin, const T* yprev, T* yout, int ste
   const T* V = (sizeof(T) == 8) ? (const T*)g->V : (const T*)g->Vf;
   { ProfScope ps(g, K_NLPROJ); launch_nl_project<T>(ds, g->d_slots, g->n_slot, g->d_pidx, chi_table<T>(g), mns, yin, P, g->st); }
   { ProfScope ps(g, K_STENCIL); launch_stencil<T>(ds, g->n_sub, pl, yin, yprev, yout, V, g->coef, step, g->st); }
-  { ProfScope ps(g, K_NLBACK); launch_nl_back<T>(ds, g->d_slots, g->n_slot, g->d_pidx, chi_table<T>(g), mns, P, yout, g->coef, step, g->st); }
+  { ProfScope ps(g, K_NLBACK);
+    launch_nl_back_csr<T>(ds, g->n_sub, g->max_nd, mns, g->max_slots, g->d_rptr, g->d_rslot, rchi_table<T>(g), P, yout,
+                          g->coef, step, g->st); }
   g->launches += (g->n_slot ? 3 : 1);
 }
 
@@ -218,7 +228,9 @@ void h_step_main(xls_grid g, int bin, int bprev, int bout, int step) {
         launch_stencil_tma(g->d_subs, c, g->d_maps, bin, (const float*)yprev, (float*)yout, g->Vf, g->coef, step,
                            g->status, g->st);
     }
-    { ProfScope ps(g, K_NLBACK); launch_nl_back<T>(g->d_subs, g->d_slots, g->n_slot, g->d_pidx, chi_table<T>(g), g->max_ns, g->P, yout, g->coef, step, g->st); }
+    { ProfScope ps(g, K_NLBACK);
+      launch_nl_back_csr<T>(g->d_subs, g->n_sub, g->max_nd, g->max_ns, g->max_slots, g->d_rptr, g->d_rslot,
+                            rchi_table<T>(g), g->P, yout, g->coef, step, g->st); }
     g->launches += (g->n_slot ? 2 : 0) + (int)g->tcls.size();
     return;
   }
@@ -802,6 +814,39 @@ xls_status xls_hamiltonian_set(xls_grid g, const double* veff, int veff_on_devic
       if ((s = g->alloc(&g->d_chi32, std::max<long long>(tot, 1) * sizeof(float4))) != XLS_OK) return s;
       launch_proj_table_fill<float>(g->d_subs, g->d_slots, g->n_slot, g->d_imgs, g->d_pidx, g->d_chi32, g->st);
     }
+    // reverse tables: count per grid point, exclusive prefix (host), fill
+    g->release(&g->d_rptr);
+    g->release(&g->d_rslot);
+    g->release(&g->d_rchi64);
+    g->release(&g->d_rchi32);
+    int* dc = nullptr;
+    int* dcur = nullptr;
+    XLS_CUDA(cudaMalloc(&dc, g->tot_pts * sizeof(int)));
+    XLS_CUDA(cudaMalloc(&dcur, g->tot_pts * sizeof(int)));
+    XLS_CUDA(cudaMemsetAsync(dc, 0, g->tot_pts * sizeof(int), g->st));
+    launch_rcsr_count(g->d_subs, g->d_slots, g->n_slot, g->d_pidx, dc, g->st);
+    std::vector<int> hc(g->tot_pts);
+    XLS_CUDA(cudaMemcpyAsync(hc.data(), dc, g->tot_pts * sizeof(int), cudaMemcpyDeviceToHost, g->st));
+    XLS_CUDA(cudaStreamSynchronize(g->st));
+    std::vector<long long> rp(g->tot_pts + 1, 0);
+    for (long long q = 0; q < g->tot_pts; ++q) rp[q + 1] = rp[q] + hc[q];
+    if ((s = g->alloc(&g->d_rptr, rp.size() * sizeof(long long))) != XLS_OK) return s;
+    if ((s = g->alloc(&g->d_rslot, std::max<long long>(rp.back(), 1) * sizeof(int))) != XLS_OK) return s;
+    if ((s = g->alloc(&g->d_rchi64, std::max<long long>(rp.back(), 1) * sizeof(double4))) != XLS_OK) return s;
+    XLS_CUDA(cudaMemcpyAsync(g->d_rptr, rp.data(), rp.size() * sizeof(long long), cudaMemcpyHostToDevice, g->st));
+    XLS_CUDA(cudaMemsetAsync(dcur, 0, g->tot_pts * sizeof(int), g->st));
+    launch_rcsr_build<double>(g->d_subs, g->d_slots, g->n_slot, g->d_pidx, g->d_chi64, g->d_rptr, dcur, g->d_rslot,
+                              g->d_rchi64, g->st);
+    if (g->prec == XLS_MIXED_BF16) {
+      if ((s = g->alloc(&g->d_rchi32, std::max<long long>(rp.back(), 1) * sizeof(float4))) != XLS_OK) return s;
+      // same entry order as the FP64 table (the fill order of the atomics is not reproducible)
+      launch_convert_f64_f32((const double*)g->d_rchi64, (float*)g->d_rchi32, 4 * rp.back(), g->st);
+    }
+    XLS_CUDA(cudaStreamSynchronize(g->st));
+    cudaFree(dc);
+    cudaFree(dcur);
+    g->max_slots = 0;
+    for (const SubDev& S : g->subs) g->max_slots = std::max(g->max_slots, S.slot_n);
   }
   // unit coefficients (plain H) for every subdomain, then the Lanczos bound b
   std::vector<double> bz(3 * g->n_sub, 1.0);

@@ -127,6 +127,16 @@ void launch_proj_table_fill(const SubDev* d_subs, const ProjSlot* d_slots, int n
 template <typename T>
 void launch_nl_project(const SubDev* d_subs, const ProjSlot* d_slots, int n_slot, const int* idx,
                        const typename Vec4<T>::type* chi, int max_ns, const T* Y, double* P, cudaStream_t st);
+void launch_rcsr_count(const SubDev* d_subs, const ProjSlot* d_slots, int n_slot, const int* idx, int* cnt,
+                       cudaStream_t st);
+template <typename T>
+void launch_rcsr_build(const SubDev* d_subs, const ProjSlot* d_slots, int n_slot, const int* idx,
+                       const typename Vec4<T>::type* chi, const long long* row_ptr, int* cursor, int* rslot,
+                       typename Vec4<T>::type* rchi, cudaStream_t st);
+template <typename T>
+void launch_nl_back_csr(const SubDev* d_subs, int n_sub, long long max_nd, int max_ns, int max_slots,
+                        const long long* row_ptr, const int* rslot, const typename Vec4<T>::type* rchi,
+                        const double* P, T* Yout, const StepCoef* coef, int step, cudaStream_t st);
 template <typename T>
 void launch_nl_back(const SubDev* d_subs, const ProjSlot* d_slots, int n_slot, const int* idx,
                     const typename Vec4<T>::type* chi, int max_ns, const double* P, T* Yout, const StepCoef* coef,

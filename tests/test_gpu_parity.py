@@ -262,3 +262,38 @@ def test_eigensolver_large_block_mixed():
     assert np.all(np.isfinite(lam)) and np.all(np.diff(lam) >= -1e-12)
     np.testing.assert_allclose(Psi @ Psi.T, np.eye(160), atol=1e-4)
     np.testing.assert_allclose(c, 1.0, atol=1e-4)
+
+
+def test_tensor_core_gram_and_rotation_match_simt(monkeypatch):
+    """Split-BF16 tcgen05 Gram / rotation against the FP32 SIMT kernels on the same filtered block
+    (both on the mixed path): M_s, H_s and the rotated block agree to the split-BF16 precision."""
+    w = dirichlet20_workload()
+    V = pseudo.local_potential(w)
+    subs = dc.partition(w)
+    psi0 = _start_blocks(w, subs)
+    bounds = np.array([[70.0, 6.0, -0.4]] * w.n_sub)
+    res = {}
+    for mode in ("tc", "simt"):
+        if mode == "simt":
+            monkeypatch.setenv("XLS_GEMM", "simt")
+        else:
+            monkeypatch.delenv("XLS_GEMM", raising=False)
+        with make_grid(w, V, xls.XLS_MIXED_BF16) as g:
+            for a in range(w.n_sub):
+                xls.xls_orbitals_set(g.h, a, psi0[a])
+            xls.xls_chefsi_stage(g.h, 1, w.degree, bounds)
+            xls.xls_chefsi_stage(g.h, 2, w.degree)
+            sub = [xls.xls_get_subspace(g.h, a, int(w.n_states[a])) for a in range(w.n_sub)]
+            xls.xls_chefsi_stage(g.h, 3, w.degree)
+            xls.xls_chefsi_stage(g.h, 4, w.degree)
+            psi = [xls.xls_orbitals_get(g.h, a, np.zeros((int(w.n_states[a]), subs[a].N))) for a in range(w.n_sub)]
+            lam = [xls.xls_get_eigs(g.h, a, int(w.n_states[a]))[0] for a in range(w.n_sub)]
+        res[mode] = (sub, psi, lam)
+    for a in range(w.n_sub):
+        (Ms_t, Hs_t), (Ms_s, Hs_s) = res["tc"][0][a], res["simt"][0][a]
+        assert relerr(Ms_t, Ms_s) < 3e-5, relerr(Ms_t, Ms_s)
+        assert relerr(0.5 * (Hs_t + Hs_t.T), 0.5 * (Hs_s + Hs_s.T)) < 3e-5
+        np.testing.assert_allclose(res["tc"][2][a], res["simt"][2][a], atol=1e-4)
+        P_t, P_s = res["tc"][1][a], res["simt"][1][a]
+        # same orthonormal Ritz block up to rotations inside degenerate clusters: compare projectors
+        assert np.linalg.norm(P_t.T @ (P_t @ P_s.T) - P_s.T) < 1e-3 * np.linalg.norm(P_s)
