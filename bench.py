@@ -39,8 +39,11 @@ def parse_args():
     p.add_argument("--steps", type=int, default=5)
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    p.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
+    p.add_argument("--precision", default="fp16", choices=["fp16", "bf16", "fp64"],
+                   help="fp16 / bf16: FP32 filter + split-FP16 / split-BF16 tensor-core GEMMs; fp64: all FP64")
     p.add_argument("--fp64-steps", type=int, default=1, help="FP64 passes timed for the mixed-vs-FP64 factor")
+    p.add_argument("--compare-passes", type=int, default=10,
+                   help="passes of both forms from the same start before their energies are compared")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--cpu-baseline-worker", action="store_true", help=argparse.SUPPRESS)
     p.add_argument("--sample-states", type=int, default=32)
@@ -191,7 +194,7 @@ def run_ours(args):
     xls.load()
     w, V = bench_workload()
     stream = torch.cuda.current_stream()
-    prec = xls.XLS_MIXED_BF16 if args.precision == "mixed" else xls.XLS_FP64
+    prec = {"fp16": xls.XLS_MIXED_FP16, "bf16": xls.XLS_MIXED_BF16, "fp64": xls.XLS_FP64}[args.precision]
     ng = int(np.prod(w.n))
     rho_dev = torch.zeros(ng, dtype=torch.float64, device="cuda")
 
@@ -259,7 +262,7 @@ def run_ours(args):
     units = point_vectors(w)
     value = units * ws / (ms_step / 1e3) / 1e9
     # roofline of the dominant kernel (the stencil launches of the filter)
-    elem = 4 if prec == xls.XLS_MIXED_BF16 else 8
+    elem = 8 if prec == xls.XLS_FP64 else 4
     stencil_avg_ms = kms[0] / max(kcnt[0], 1)
     bytes_launch = stencil_bytes_per_launch(w, elem)
     peaks = {}
@@ -275,32 +278,37 @@ def run_ours(args):
     kernel_share = {n: round(float(kms[i] / max(kms.sum(), 1e-9)), 4)
                     for i, n in enumerate(["stencil", "nl_project", "nl_back", "gram", "eig", "rotate", "other"])}
 
-    # FP64 form of the same pass for the mixed-vs-FP64 factor and Delta E
+    # FP64 form of the same pass for the mixed-vs-FP64 factor, and the energy difference of the two
+    # forms once the occupied subspace has converged (both from the same start block)
     fp64 = None
-    if prec == xls.XLS_MIXED_BF16 and args.fp64_steps > 0:
+    if prec != xls.XLS_FP64 and args.fp64_steps > 0:
         g64 = make(xls.XLS_FP64)
-        gm = make(xls.XLS_MIXED_BF16)
-        n_cmp = args.warmup + 1
-        for _ in range(n_cmp - 1):
-            step(g64.h)
-            step(gm.h)
+        gm = make(prec)
         torch.cuda.synchronize()
         f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        step(g64.h)
         f0.record(stream)
         for _ in range(args.fp64_steps):
             step(g64.h)
         f1.record(stream)
         torch.cuda.synchronize()
         ms64 = f0.elapsed_time(f1) / args.fp64_steps
-        step(gm.h)
-        for _ in range(args.fp64_steps - 1):
+        for _ in range(args.compare_passes - 1 - args.fp64_steps):
+            step(g64.h)
+        for _ in range(args.compare_passes):
             step(gm.h)
-        _, eb64, _ = xls.xls_density(g64.h, w.n_electrons, w.kT)
-        _, ebm, _ = xls.xls_density(gm.h, w.n_electrons, w.kT)
+        rho64 = torch.zeros_like(rho_dev)
+        rhom = torch.zeros_like(rho_dev)
+        _, eb64, es64 = xls.xls_density(g64.h, w.n_electrons, w.kT, rho64)
+        _, ebm, esm = xls.xls_density(gm.h, w.n_electrons, w.kT, rhom)
         g64.close()
         gm.close()
+        n_at = len(w.pos)
         fp64 = {"ms_per_step": round(ms64, 3), "mixed_speedup": round(ms64 / ms_step, 2),
-                "delta_e_band_per_atom": abs(ebm - eb64) / len(w.pos), "passes_compared": n_cmp}
+                "delta_e_per_atom": abs((ebm - esm) - (eb64 - es64)) / n_at,
+                "delta_e_band_per_atom": abs(ebm - eb64) / n_at,
+                "rho_rel_l2": float(torch.linalg.norm(rhom - rho64) / torch.linalg.norm(rho64)),
+                "passes_compared": args.compare_passes}
 
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
@@ -311,7 +319,9 @@ def run_ours(args):
             "metric": METRIC, "value": round(value, 3), "unit": UNIT, "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": round(ms_step, 3), "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None,
-            "dtype": "f32+bf16x3 (f64 eig/fermi)" if prec == xls.XLS_MIXED_BF16 else "f64",
+            "dtype": {xls.XLS_MIXED_FP16: "f32 filter + fp16x3 tensor GEMM (f64 eig/fermi)",
+                      xls.XLS_MIXED_BF16: "f32 filter + bf16x3 tensor GEMM (f64 eig/fermi)",
+                      xls.XLS_FP64: "f64"}[prec],
             "data": "synthetic",
             "config": {"workload": w.name, "subdomains": w.n_sub, "points_per_subdomain": w.sub_points(0),
                        "states": int(w.n_states[0]), "degree": w.degree,

@@ -57,10 +57,11 @@ __global__ void __launch_bounds__(512) k_cholesky(const SubDev* __restrict__ sub
   if (threadIdx.x == 0) s_fail = 0;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nwarp = blockDim.x >> 5;
   for (int j = 0; j < n; ++j) {
-    double acc = 0.0;
-    for (int k = threadIdx.x; k < j; k += blockDim.x) acc += L[(long long)j * n + k] * L[(long long)j * n + k];
-    acc = block_sum_d(acc, red);
-    if (threadIdx.x == 0) {
+    if (warp == 0) {
+      double acc = 0.0;
+      for (int k = lane; k < j; k += 32) acc += L[(long long)j * n + k] * L[(long long)j * n + k];
+      acc = warp_sum(acc);
+      if (lane == 0) {
       const double dj = L[(long long)j * n + j] - acc;
       if (!(dj > 0.0) || !isfinite(dj)) {
         s_fail = 1;
@@ -70,6 +71,7 @@ __global__ void __launch_bounds__(512) k_cholesky(const SubDev* __restrict__ sub
         s_piv = sqrt(dj);
       }
       L[(long long)j * n + j] = s_piv;
+      }
     }
     __syncthreads();
     if (s_fail) return;
@@ -89,30 +91,63 @@ __global__ void __launch_bounds__(512) k_cholesky(const SubDev* __restrict__ sub
   }
 }
 
-// ---- 2./6. triangular solves, one thread per right-hand-side column ------------------------
+// ---- 2./6. triangular solves, one warp per right-hand-side column --------------------------
 // lower:  X = L^-1 B  (B[i][c] = trans ? Bm[c][i] : Bm[i][c]);  upper: X = L^-T B.
-template <bool kUpper>
-__global__ void __launch_bounds__(128)
+// Lane l keeps the solution entries x_k with k = l (mod 32) in registers; entry i is finished by
+// its owner lane after a warp-wide dot product over the already known entries.
+template <bool kUpper, int kTrsmRegs>
+__global__ void __launch_bounds__(256)
 k_trsm(const SubDev* __restrict__ subs, const double* __restrict__ Lm, const double* Bm, int trans, double* Xm) {
   const SubDev& S = subs[blockIdx.y];
   const int n = S.ns;
-  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  const int lane = threadIdx.x & 31;
+  const int c = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
   if (c >= n) return;
   const double* L = Lm + S.off_ss;
   const double* B = Bm + S.off_ss;
   double* X = Xm + S.off_ss;
+  double xr[kTrsmRegs];
+#pragma unroll
+  for (int q = 0; q < kTrsmRegs; ++q) xr[q] = 0.0;
   if (!kUpper) {
     for (int i = 0; i < n; ++i) {
-      double s = trans ? B[(long long)c * n + i] : B[(long long)i * n + c];
       const double* Li = L + (long long)i * n;
-      for (int k = 0; k < i; ++k) s -= Li[k] * X[(long long)k * n + c];
-      X[(long long)i * n + c] = s / Li[i];
+      double part = 0.0;
+#pragma unroll
+      for (int q = 0; q < kTrsmRegs; ++q) {
+        const int k = q * 32 + lane;
+        if (q * 32 < i && k < i) part += Li[k] * xr[q];
+      }
+      part = warp_sum(part);
+      double x = 0.0;
+      if (lane == (i & 31)) {
+        const double b = trans ? B[(long long)c * n + i] : B[(long long)i * n + c];
+        x = (b - part) / Li[i];
+        X[(long long)i * n + c] = x;
+      }
+      x = __shfl_sync(0xffffffffu, x, i & 31);
+      const bool own = (lane == (i & 31));
+#pragma unroll
+      for (int q = 0; q < kTrsmRegs; ++q) xr[q] = (own && q == (i >> 5)) ? x : xr[q];
     }
   } else {
     for (int i = n - 1; i >= 0; --i) {
-      double s = B[(long long)i * n + c];
-      for (int k = i + 1; k < n; ++k) s -= L[(long long)k * n + i] * X[(long long)k * n + c];
-      X[(long long)i * n + c] = s / L[(long long)i * n + i];
+      double part = 0.0;
+#pragma unroll
+      for (int q = 0; q < kTrsmRegs; ++q) {
+        const int k = q * 32 + lane;
+        if (q * 32 + 31 > i && k > i && k < n) part += L[(long long)k * n + i] * xr[q];
+      }
+      part = warp_sum(part);
+      double x = 0.0;
+      if (lane == (i & 31)) {
+        x = (B[(long long)i * n + c] - part) / L[(long long)i * n + i];
+        X[(long long)i * n + c] = x;
+      }
+      x = __shfl_sync(0xffffffffu, x, i & 31);
+      const bool own = (lane == (i & 31));
+#pragma unroll
+      for (int q = 0; q < kTrsmRegs; ++q) xr[q] = (own && q == (i >> 5)) ? x : xr[q];
     }
   }
 }
@@ -139,14 +174,12 @@ __global__ void __launch_bounds__(512) k_tridiag(const SubDev* __restrict__ subs
   __shared__ double s_tau, s_K;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nwarp = blockDim.x >> 5;
   // symmetrise
-  for (long long q = threadIdx.x; q < (long long)n * n; q += blockDim.x) {
-    const int i = (int)(q / n), k = (int)(q % n);
-    if (k > i) {
+  for (int i = warp; i < n; i += nwarp)
+    for (int k = i + 1 + lane; k < n; k += 32) {
       const double m = 0.5 * (A[(long long)i * n + k] + A[(long long)k * n + i]);
       A[(long long)i * n + k] = m;
       A[(long long)k * n + i] = m;
     }
-  }
   __syncthreads();
   for (int k = 0; k + 1 < n; ++k) {
     const int m = n - k - 1;
@@ -197,9 +230,10 @@ __global__ void __launch_bounds__(512) k_tridiag(const SubDev* __restrict__ subs
       const double K = s_K;
       for (int i = threadIdx.x; i < m; i += blockDim.x) sw[i] -= K * sv[i];
       __syncthreads();
-      for (long long q = threadIdx.x; q < (long long)m * m; q += blockDim.x) {
-        const int i = (int)(q / m), j = (int)(q % m);
-        A[(long long)(k + 1 + i) * n + (k + 1 + j)] -= sv[i] * sw[j] + sw[i] * sv[j];
+      for (int i = warp; i < m; i += nwarp) {
+        double* row = A + (long long)(k + 1 + i) * n + (k + 1);
+        const double vi = sv[i], wi = sw[i];
+        for (int j = lane; j < m; j += 32) row[j] -= vi * sw[j] + wi * sv[j];
       }
     }
     __syncthreads();
@@ -251,9 +285,12 @@ __device__ __forceinline__ double hash_unit(unsigned a, unsigned b) {
 // coalesce.
 constexpr int kTriThreads = 128;
 
+// kSmemWork: the per-thread work arrays live in shared memory (after the bisection arrays);
+// otherwise in the interleaved global scratch
+template <bool kSmemWork>
 __global__ void __launch_bounds__(kTriThreads)
 k_tri_eig(const SubDev* __restrict__ subs, double* vecs, double* Zm, double* scratch_all, long long scr_stride,
-          double* Rm, double* lam_out) {
+          double* Rm, double* lam_out, int max_ns) {
   const SubDev& S = subs[blockIdx.x];
   const int n = S.ns;
   double* d = vecs + 8LL * S.off_state;
@@ -309,7 +346,14 @@ k_tri_eig(const SubDev* __restrict__ subs, double* vecs, double* Zm, double* scr
   }
   __syncthreads();
   const int T = blockDim.x, t = threadIdx.x;
-  double* scr = scratch_all + (long long)blockIdx.x * scr_stride;
+  double* scr;
+  if (kSmemWork) {
+    // 16-byte aligned start after df, e2f (2 max_ns floats) and cstart (max_ns + 1 ints)
+    const size_t off = ((size_t)(3 * max_ns + 1) * 4 + 15) & ~(size_t)15;
+    scr = reinterpret_cast<double*>(reinterpret_cast<unsigned char*>(smf) + off);
+  } else {
+    scr = scratch_all + (long long)blockIdx.x * scr_stride;
+  }
   // interleaved arrays: lm (n), dinv (n), x (n)
   auto LM = [&](int j) -> double& { return scr[(long long)j * T + t]; };
   auto DI = [&](int j) -> double& { return scr[(long long)(n + j) * T + t]; };
@@ -487,6 +531,22 @@ k_backtransform(const SubDev* __restrict__ subs, const double* __restrict__ Am, 
   }
 }
 
+template <int RC>
+static void trsm_rc(bool upper, dim3 gt, const SubDev* d_subs, const double* L, const double* B, int trans, double* X,
+                    cudaStream_t st) {
+  if (upper) k_trsm<true, RC><<<gt, 256, 0, st>>>(d_subs, L, B, trans, X);
+  else k_trsm<false, RC><<<gt, 256, 0, st>>>(d_subs, L, B, trans, X);
+}
+static void trsm(bool upper, int max_ns, dim3 gt, const SubDev* d_subs, const double* L, const double* B, int trans,
+                 double* X, cudaStream_t st) {
+  const int rc = (max_ns + 31) / 32;
+  if (rc <= 2) trsm_rc<2>(upper, gt, d_subs, L, B, trans, X, st);
+  else if (rc <= 4) trsm_rc<4>(upper, gt, d_subs, L, B, trans, X, st);
+  else if (rc <= 8) trsm_rc<8>(upper, gt, d_subs, L, B, trans, X, st);
+  else if (rc <= 16) trsm_rc<16>(upper, gt, d_subs, L, B, trans, X, st);
+  else trsm_rc<32>(upper, gt, d_subs, L, B, trans, X, st);
+}
+
 // Dynamic shared memory for the matrix-resident variants: request exactly what a launch needs;
 // if the device refuses (static + dynamic above its opt-in limit), use the global-memory variant.
 template <typename K>
@@ -511,16 +571,26 @@ void launch_eig(const SubDev* d_subs, int n_sub, int max_ns, double* Ms, double*
   const size_t vbytes = 2 * (size_t)max_ns * sizeof(double);
   if (smem_ok(k_cholesky<true>, mat)) k_cholesky<true><<<n_sub, 512, mat, st>>>(d_subs, Ms, status);
   else k_cholesky<false><<<n_sub, 512, 0, st>>>(d_subs, Ms, status);
-  dim3 gt((max_ns + 127) / 128, n_sub);
-  k_trsm<false><<<gt, 128, 0, st>>>(d_subs, Ms, Hs, 0, W);     // W = L^-1 H_s
-  k_trsm<false><<<gt, 128, 0, st>>>(d_subs, Ms, W, 1, Hs);     // A = L^-1 W^T
+  dim3 gt((max_ns + 7) / 8, n_sub);   // 8 warps (columns) per CTA
+  trsm(false, max_ns, gt, d_subs, Ms, Hs, 0, W, st);   // W = L^-1 H_s
+  trsm(false, max_ns, gt, d_subs, Ms, W, 1, Hs, st);   // A = L^-1 W^T
   if (smem_ok(k_tridiag<true>, mat + vbytes)) k_tridiag<true><<<n_sub, 512, mat + vbytes, st>>>(d_subs, Hs, vecs, max_ns);
   else k_tridiag<false><<<n_sub, 512, vbytes, st>>>(d_subs, Hs, vecs, max_ns);
-  k_tri_eig<<<n_sub, kTriThreads, 2 * max_ns * sizeof(float) + (max_ns + 1) * sizeof(int), st>>>(
-      d_subs, vecs, W, scratch, 3LL * max_ns * kTriThreads, R, lam);
+  {
+    const size_t head = (((size_t)(3 * max_ns + 1) * 4 + 15) & ~(size_t)15);
+    const size_t per_thread = 3 * (size_t)max_ns * sizeof(double);
+    int thr = 0;
+    for (int tt = kTriThreads; tt >= 32; tt -= 32)
+      if (head + per_thread * tt <= 200 * 1024) { thr = tt; break; }
+    if (thr > 0 && smem_ok(k_tri_eig<true>, head + per_thread * thr))
+      k_tri_eig<true><<<n_sub, thr, head + per_thread * thr, st>>>(d_subs, vecs, W, scratch, 0, R, lam, max_ns);
+    else
+      k_tri_eig<false><<<n_sub, kTriThreads, head, st>>>(d_subs, vecs, W, scratch, 3LL * max_ns * kTriThreads, R, lam,
+                                                         max_ns);
+  }
   dim3 gb((max_ns + 31) / 32, n_sub);
   k_backtransform<<<gb, 256, (max_ns + 256) * sizeof(double), st>>>(d_subs, Hs, vecs, W);
-  k_trsm<true><<<gt, 128, 0, st>>>(d_subs, Ms, W, 0, Y);       // Y = L^-T Z
+  trsm(true, max_ns, gt, d_subs, Ms, W, 0, Y, st);     // Y = L^-T Z
 }
 
 size_t eig_scratch_doubles(int n_sub, int max_ns) { return (size_t)n_sub * kTriThreads * 3 * max_ns; }

@@ -254,41 +254,53 @@ template <typename T>
 __global__ void __launch_bounds__(kNlWarps * 32)
 k_nl_project(const SubDev* __restrict__ subs, const ProjSlot* __restrict__ slots, const int* __restrict__ idx,
              const typename Vec4<T>::type* __restrict__ chi, const T* __restrict__ Y, double* __restrict__ P) {
+  using T4 = typename Vec4<T>::type;
+  constexpr int kChunk = 512;
+  __shared__ int s_idx[kChunk];
+  __shared__ T4 s_chi[kChunk];
   const ProjSlot& A = slots[blockIdx.x];
   const SubDev& S = subs[A.sub];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int v0 = (blockIdx.y * kNlWarps + warp) * kNlVec;
-  if (v0 >= S.ns) return;
-  const int nv = min(kNlVec, S.ns - v0);
+  const int nv = max(0, min(kNlVec, S.ns - v0));
   T acc[4][kNlVec];
 #pragma unroll
   for (int l = 0; l < 4; ++l)
 #pragma unroll
     for (int v = 0; v < kNlVec; ++v) acc[l][v] = (T)0;
   const T* yb = Y + S.off_blk + (long long)v0 * S.nd;
-  const int* ix = idx + A.pt_off;
-  const typename Vec4<T>::type* cx = chi + A.pt_off;
-  for (int p = lane; p < A.pt_n; p += 64) {
-    // two points per lane per iteration: 16 independent loads in flight
-    const bool two = p + 32 < A.pt_n;
-    const int g0 = ix[p], g1 = two ? ix[p + 32] : g0;
-    const typename Vec4<T>::type c = cx[p];
-    typename Vec4<T>::type d = cx[two ? p + 32 : p];
-    if (!two) { d.x = (T)0; d.y = (T)0; d.z = (T)0; d.w = (T)0; }
-    T y0[kNlVec], y1[kNlVec];
-#pragma unroll
-    for (int v = 0; v < kNlVec; ++v) {
-      y0[v] = (v < nv) ? yb[(long long)v * S.nd + g0] : (T)0;
-      y1[v] = (v < nv) ? yb[(long long)v * S.nd + g1] : (T)0;
+  for (int c0 = 0; c0 < A.pt_n; c0 += kChunk) {
+    const int cn = min(kChunk, A.pt_n - c0);
+    __syncthreads();
+    for (int p = threadIdx.x; p < cn; p += blockDim.x) {
+      s_idx[p] = idx[A.pt_off + c0 + p];
+      s_chi[p] = chi[A.pt_off + c0 + p];
     }
+    __syncthreads();
+    if (nv == 0) continue;
+    for (int p = lane; p < cn; p += 64) {
+      // two points per lane per iteration: 16 independent loads in flight
+      const bool two = p + 32 < cn;
+      const int g0 = s_idx[p], g1 = two ? s_idx[p + 32] : g0;
+      const T4 c = s_chi[p];
+      T4 d = s_chi[two ? p + 32 : p];
+      if (!two) { d.x = (T)0; d.y = (T)0; d.z = (T)0; d.w = (T)0; }
+      T y0[kNlVec], y1[kNlVec];
 #pragma unroll
-    for (int v = 0; v < kNlVec; ++v) {
-      acc[0][v] += c.x * y0[v] + d.x * y1[v];
-      acc[1][v] += c.y * y0[v] + d.y * y1[v];
-      acc[2][v] += c.z * y0[v] + d.z * y1[v];
-      acc[3][v] += c.w * y0[v] + d.w * y1[v];
+      for (int v = 0; v < kNlVec; ++v) {
+        y0[v] = (v < nv) ? yb[(long long)v * S.nd + g0] : (T)0;
+        y1[v] = (v < nv) ? yb[(long long)v * S.nd + g1] : (T)0;
+      }
+#pragma unroll
+      for (int v = 0; v < kNlVec; ++v) {
+        acc[0][v] += c.x * y0[v] + d.x * y1[v];
+        acc[1][v] += c.y * y0[v] + d.y * y1[v];
+        acc[2][v] += c.z * y0[v] + d.z * y1[v];
+        acc[3][v] += c.w * y0[v] + d.w * y1[v];
+      }
     }
   }
+  if (nv == 0) return;
 #pragma unroll
   for (int l = 0; l < 4; ++l)
 #pragma unroll
@@ -362,7 +374,7 @@ __global__ void k_rcsr_fill(const SubDev* __restrict__ subs, const ProjSlot* __r
   }
 }
 
-constexpr int kBackPts = 1024, kBackVec = 8;
+constexpr int kBackPts = 1024, kBackVec = 16;
 
 // Y_out[v][g] += scale * sum over the slots s of point g of sum_l chi_l(g) P[s][l][v]
 template <typename T>

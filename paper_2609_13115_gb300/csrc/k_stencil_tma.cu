@@ -19,9 +19,6 @@
 
 namespace xls {
 
-__constant__ float c_fdw_f[kN0 + 1] = {-5369.0f / 1800.0f, 12.0f / 7.0f, -15.0f / 56.0f, 10.0f / 189.0f,
-                                       -1.0f / 112.0f,     2.0f / 1925.0f, -1.0f / 16632.0f};
-
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
   return static_cast<uint32_t>(__cvta_generic_to_shared(p));
 }
@@ -72,10 +69,18 @@ __device__ __forceinline__ bool wait_slot(uint64_t* bar, uint32_t parity) {
 constexpr int kSlots = 10;       // ring depth: 7 resident planes + 3 in flight
 constexpr int kHaloX = 8;        // halo columns on each side (16-byte aligned TMA x coordinate)
 
-__global__ void __launch_bounds__(512)
+// Stencil weights of one launch (all subdomains of a launch share the grid spacing): passed by
+// value so that the FMAs read them from the constant bank instead of registers.
+struct StencilW {
+  float wx[kN0 + 1], wy[kN0 + 1], wz[kN0 + 1];
+  float wc;
+};
+
+__global__ void __launch_bounds__(288, 2)
 k_stencil_tma(const SubDev* __restrict__ subs, const TmaJob* __restrict__ jobs, const int* __restrict__ job_off,
               int n_jobs, const CUtensorMap* __restrict__ maps, int buf_in, const float* Yprev, float* Yout,
-              const float* __restrict__ Vall, const StepCoef* __restrict__ coef, int step, int* status) {
+              const float* __restrict__ Vall, const StepCoef* __restrict__ coef, int step, int* status,
+              const StencilW sw) {
   extern __shared__ __align__(128) unsigned char smem_raw[];
   __shared__ __align__(8) uint64_t bars[kSlots];
   __shared__ int s_abort;
@@ -136,17 +141,8 @@ k_stencil_tma(const SubDev* __restrict__ subs, const TmaJob* __restrict__ jobs, 
   if (tid == 0)
     for (int pi = 0; pi < kSlots && pi < nplanes; ++pi) issue(pi);
 
-  // stencil weights (FP32) and step coefficients
-  const float ihx = (float)(-0.5 / (S.h[0] * S.h[0])), ihy = (float)(-0.5 / (S.h[1] * S.h[1])),
-              ihz = (float)(-0.5 / (S.h[2] * S.h[2]));
-  float wx[kN0 + 1], wy[kN0 + 1], wz[kN0 + 1];
-#pragma unroll
-  for (int p = 0; p <= kN0; ++p) {
-    wx[p] = c_fdw_f[p] * ihx;
-    wy[p] = c_fdw_f[p] * ihy;
-    wz[p] = c_fdw_f[p] * ihz;
-  }
-  const float wc = wx[0] + wy[0] + wz[0];
+  // step coefficients
+  const float wc = sw.wc;
   const StepCoef cf = coef[J.sub * kMaxDegree + step];
   const float scale = (float)cf.scale, cshift = (float)cf.c, pshift = (float)cf.shift;
   const long long plane_sz = (long long)nx * ny;
@@ -175,37 +171,30 @@ k_stencil_tma(const SubDev* __restrict__ subs, const TmaJob* __restrict__ jobs, 
     const int slot = pi % kSlots;
     const uint32_t parity = (uint32_t)((pi / kSlots) & 1);
     const bool ok = wait_slot(&bars[slot], parity);
-    if (__syncthreads_or(!ok)) {
-      if (tid == 0) atomicCAS(status, 0, XLS_ETIMEOUT);
-      return;
-    }
-    float* P = ring + (size_t)slot * slot_floats;
+    if (!ok) s_abort = 1;
+    const float* P = ring + (size_t)slot * slot_floats;
     const int z = pi - kN0;
     const bool plane_loaded = pz || (z >= 0 && z < nz);
-    if (px && plane_loaded) {
-      // periodic x: fill the halo columns from the opposite edge of the same rows
-      for (int s = tid; s < rows * 2 * kN0; s += blockDim.x * blockDim.y) {
-        const int r = s / (2 * kN0), c = s % (2 * kN0);
-        const int col = (c < kN0) ? (kHaloX - kN0 + c) : (kHaloX + nx + (c - kN0));
-        const int src = (c < kN0) ? (kHaloX + nx - kN0 + c) : (kHaloX + (c - kN0));
-        P[r * W + col] = P[r * W + src];
-      }
-    }
-    __syncthreads();
     // push this plane's values of the thread's four columns into the z-queue
 #pragma unroll
     for (int k = 0; k < 2 * kN0; ++k) q[k] = q[k + 1];
-    q[2 * kN0] = (plane_loaded && active) ? *reinterpret_cast<const float4*>(P + (ty + kN0) * W + kHaloX + x4)
-                                          : make_float4(0.f, 0.f, 0.f, 0.f);
+    q[2 * kN0] = (ok && plane_loaded && active) ? *reinterpret_cast<const float4*>(P + (ty + kN0) * W + kHaloX + x4)
+                                                : make_float4(0.f, 0.f, 0.f, 0.f);
     const int zo = pi - 2 * kN0;  // output plane whose z-window is now complete
-    if (zo >= 0 && active && row_ok) {
+    if (ok && zo >= 0 && active && row_ok) {
       const float* C = ring + (size_t)((pi - kN0) % kSlots) * slot_floats;  // slot of plane zo
       const float* rowp = C + (ty + kN0) * W;
-      // x-neighbours: columns x4-6 .. x4+9 of the halo-shifted row (aligned float4 window)
+      // x-neighbours: columns x4-6 .. x4+9 of the halo-shifted row (aligned float4 window);
+      // along a periodic x axis the edge threads read the wrapped columns of the same row
       float xr[20];
 #pragma unroll
       for (int j = 0; j < 5; ++j) {
-        const float4 v4 = *reinterpret_cast<const float4*>(rowp + x4 + 4 * j);
+        // chunk j covers x = x4 - 8 + 4j .. +3: wholly inside [0, nx) or wholly outside
+        // (n_x and x4 are multiples of 4); outside chunks of a periodic axis wrap
+        int xs = x4 - kHaloX + 4 * j;
+        if (px) xs = xs < 0 ? xs + nx : (xs >= nx ? xs - nx : xs);
+        const int col = xs + kHaloX;
+        const float4 v4 = *reinterpret_cast<const float4*>(rowp + col);
         xr[4 * j] = v4.x; xr[4 * j + 1] = v4.y; xr[4 * j + 2] = v4.z; xr[4 * j + 3] = v4.w;
       }
       // element r of the thread's points sits at xr[kHaloX + r]
@@ -217,18 +206,18 @@ k_stencil_tma(const SubDev* __restrict__ subs, const TmaJob* __restrict__ jobs, 
 #pragma unroll
       for (int p = 1; p <= kN0; ++p) {
 #pragma unroll
-        for (int r = 0; r < 4; ++r) acc[r] += wx[p] * (xr[kHaloX + r + p] + xr[kHaloX + r - p]);
+        for (int r = 0; r < 4; ++r) acc[r] += sw.wx[p] * (xr[kHaloX + r + p] + xr[kHaloX + r - p]);
         const float4 up = *reinterpret_cast<const float4*>(C + (ty + kN0 + p) * W + kHaloX + x4);
         const float4 dn = *reinterpret_cast<const float4*>(C + (ty + kN0 - p) * W + kHaloX + x4);
-        acc[0] += wy[p] * (up.x + dn.x);
-        acc[1] += wy[p] * (up.y + dn.y);
-        acc[2] += wy[p] * (up.z + dn.z);
-        acc[3] += wy[p] * (up.w + dn.w);
+        acc[0] += sw.wy[p] * (up.x + dn.x);
+        acc[1] += sw.wy[p] * (up.y + dn.y);
+        acc[2] += sw.wy[p] * (up.z + dn.z);
+        acc[3] += sw.wy[p] * (up.w + dn.w);
         const float4 zu = q[kN0 + p], zd = q[kN0 - p];
-        acc[0] += wz[p] * (zu.x + zd.x);
-        acc[1] += wz[p] * (zu.y + zd.y);
-        acc[2] += wz[p] * (zu.z + zd.z);
-        acc[3] += wz[p] * (zu.w + zd.w);
+        acc[0] += sw.wz[p] * (zu.x + zd.x);
+        acc[1] += sw.wz[p] * (zu.y + zd.y);
+        acc[2] += sw.wz[p] * (zu.z + zd.z);
+        acc[3] += sw.wz[p] * (zu.w + zd.w);
       }
       const long long g = (long long)zo * plane_sz + (long long)y * nx + x4;
       const float4 v4 = v_next, pv = p_next;
@@ -245,6 +234,10 @@ k_stencil_tma(const SubDev* __restrict__ subs, const TmaJob* __restrict__ jobs, 
       *reinterpret_cast<float4*>(Yout + base + g) = make_float4(o[0], o[1], o[2], o[3]);
     }
     __syncthreads();  // every thread is done with plane index pi - 6 (x/y of output zo)
+    if (s_abort) {    // a plane never landed: record it and leave (uniform: read after the barrier)
+      if (tid == 0) atomicCAS(status, 0, XLS_ETIMEOUT);
+      return;
+    }
     const int rel = pi - kN0;
     if (tid == 0 && rel >= 0) {
       const int nxt = rel + kSlots;  // reuses the slot of plane index rel
@@ -319,11 +312,23 @@ void launch_stencil_tma(const SubDev* d_subs, const TmaClass& cls, const CUtenso
   static bool attr = false;
   if (!attr) {
     cudaFuncSetAttribute(k_stencil_tma, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    cudaFuncSetAttribute(k_stencil_tma, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
     attr = true;
   }
+  StencilW sw;
+  const float ihx = (float)(-0.5 / (cls.h[0] * cls.h[0])), ihy = (float)(-0.5 / (cls.h[1] * cls.h[1])),
+              ihz = (float)(-0.5 / (cls.h[2] * cls.h[2]));
+  static const double fdw[kN0 + 1] = {-5369.0 / 1800.0, 12.0 / 7.0, -15.0 / 56.0, 10.0 / 189.0,
+                                      -1.0 / 112.0,     2.0 / 1925.0, -1.0 / 16632.0};
+  for (int p = 0; p <= kN0; ++p) {
+    sw.wx[p] = (float)fdw[p] * ihx;
+    sw.wy[p] = (float)fdw[p] * ihy;
+    sw.wz[p] = (float)fdw[p] * ihz;
+  }
+  sw.wc = sw.wx[0] + sw.wy[0] + sw.wz[0];
   dim3 block(cls.nq, cls.TY);
   k_stencil_tma<<<cls.total, block, smem, st>>>(d_subs, cls.d_jobs, cls.d_job_off, cls.n_jobs, d_maps, buf_in, Yprev,
-                                                Yout, V, coef, step, status);
+                                                Yout, V, coef, step, status, sw);
 }
 
 }  // namespace xls

@@ -20,6 +20,7 @@
 //   Rotation: Psi[n][g] = sum_k Psi_f[k][g] Y[k][n] for a tile of 128 grid points, A = Psi_f
 //             (MN-major: grid points contiguous), B = Y^T (K-major, pre-split hi/lo in HBM).
 #include <cuda_bf16.h>
+#include <cuda_fp16.h>
 
 #include "xls_internal.h"
 
@@ -95,9 +96,10 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float v[16]) {
 
 // Instruction descriptor, kind::f16: D = F32 (bits 4-5 = 1), A = B = BF16 (bits 7-9, 10-12 = 1),
 // A major (bit 15), B K-major (bit 16 = 0), N >> 3 at bits 17-22, M >> 4 at bits 24-28.
-__host__ __device__ constexpr uint32_t idesc_bf16(int M, int N, bool a_mn_major) {
-  return (1u << 4) | (1u << 7) | (1u << 10) | ((a_mn_major ? 1u : 0u) << 15) | ((uint32_t)(N >> 3) << 17) |
-         ((uint32_t)(M >> 4) << 24);
+// (A = B = F16: type code 0 in bits 7-9 and 10-12)
+__host__ __device__ constexpr uint32_t idesc_16(int M, int N, bool a_mn_major, bool fp16) {
+  return (1u << 4) | ((fp16 ? 0u : 1u) << 7) | ((fp16 ? 0u : 1u) << 10) | ((a_mn_major ? 1u : 0u) << 15) |
+         ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
 }
 
 // Shared-memory matrix descriptor, 128-byte swizzle: start >> 4 (bits 0-13), leading byte
@@ -115,16 +117,32 @@ __device__ __forceinline__ uint32_t mnmaj_off(int m, int k, int c) {
   return (uint32_t)(m * 8192 + (k >> 3) * 1024 + (k & 7) * 128 + ((c ^ (k & 7)) << 4));
 }
 
-__device__ __forceinline__ void split8(const float4 a, const float4 b, uint4& hi, uint4& lo) {
-  const float x[8] = {a.x, a.y, a.z, a.w, b.x, b.y, b.z, b.w};
+// hi = r(s x), lo = r(s x - hi) with r = round-to-nearest bf16 (kFp16 = false) or fp16 (true);
+// s is a power of two (exact), 1 on the BF16 path
+template <bool kFp16>
+__device__ __forceinline__ void split1(float x, uint16_t& h, uint16_t& l) {
+  if (kFp16) {
+    const __half hh = __float2half_rn(x);
+    h = __half_as_ushort(hh);
+    l = __half_as_ushort(__float2half_rn(x - __half2float(hh)));
+  } else {
+    const __nv_bfloat16 hh = __float2bfloat16_rn(x);
+    h = __bfloat16_as_ushort(hh);
+    l = __bfloat16_as_ushort(__float2bfloat16_rn(x - __bfloat162float(hh)));
+  }
+}
+
+template <bool kFp16>
+__device__ __forceinline__ void split8(const float4 a, const float4 b, float s, uint4& hi, uint4& lo) {
+  const float x[8] = {a.x * s, a.y * s, a.z * s, a.w * s, b.x * s, b.y * s, b.z * s, b.w * s};
   uint32_t h[4], l[4];
 #pragma unroll
   for (int i = 0; i < 4; ++i) {
-    const __nv_bfloat16 h0 = __float2bfloat16_rn(x[2 * i]), h1 = __float2bfloat16_rn(x[2 * i + 1]);
-    const __nv_bfloat16 l0 = __float2bfloat16_rn(x[2 * i] - __bfloat162float(h0));
-    const __nv_bfloat16 l1 = __float2bfloat16_rn(x[2 * i + 1] - __bfloat162float(h1));
-    h[i] = (uint32_t)__bfloat16_as_ushort(h0) | ((uint32_t)__bfloat16_as_ushort(h1) << 16);
-    l[i] = (uint32_t)__bfloat16_as_ushort(l0) | ((uint32_t)__bfloat16_as_ushort(l1) << 16);
+    uint16_t h0, h1, l0, l1;
+    split1<kFp16>(x[2 * i], h0, l0);
+    split1<kFp16>(x[2 * i + 1], h1, l1);
+    h[i] = (uint32_t)h0 | ((uint32_t)h1 << 16);
+    l[i] = (uint32_t)l0 | ((uint32_t)l1 << 16);
   }
   hi = make_uint4(h[0], h[1], h[2], h[3]);
   lo = make_uint4(l[0], l[1], l[2], l[3]);
@@ -141,9 +159,11 @@ __device__ __forceinline__ void sts128(uint32_t saddr, uint4 v) {
 constexpr uint32_t kTile = 128 * 128;        // one 128-row x 128-byte tile
 constexpr uint32_t kGramStage = 6 * kTile;
 
+template <bool kFp16>
 __global__ void __launch_bounds__(kThreads, 1)
 k_gram_tc(const SubDev* __restrict__ subs, const GramJob* __restrict__ jobs, const float* __restrict__ F,
-          const float* __restrict__ HF, float* __restrict__ work, int* status) {
+          const float* __restrict__ HF, const int* __restrict__ ex_f, const int* __restrict__ ex_hf,
+          float* __restrict__ work, int* status) {
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   unsigned char* smem = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
   __shared__ __align__(8) uint64_t full[kStages], empty[kStages], done;
@@ -206,8 +226,10 @@ k_gram_tc(const SubDev* __restrict__ subs, const GramJob* __restrict__ jobs, con
           a = p[0];
           b = p[1];
         }
+        float sc = 1.f;
+        if (kFp16 && valid) sc = ldexpf(1.f, (src == hf ? ex_hf : ex_f)[S.off_state + grow]);
         uint4 hi, lo;
-        split8(a, b, hi, lo);
+        split8<kFp16>(a, b, sc, hi, lo);
         const uint32_t off = kmaj_off(r, c);
         sts128(thi + off, hi);
         sts128(tlo + off, lo);
@@ -233,7 +255,7 @@ k_gram_tc(const SubDev* __restrict__ subs, const GramJob* __restrict__ jobs, con
     }
   } else if (lane == 0) {
     // ---------------- MMA issuer
-    const uint32_t idesc = idesc_bf16(128, nj16, false);
+    const uint32_t idesc = idesc_16(128, nj16, false, kFp16);
     bool ok = true;
     for (int it = 0; it < nkt; ++it) {
       const int st = it % kStages;
@@ -270,7 +292,8 @@ k_gram_tc(const SubDev* __restrict__ subs, const GramJob* __restrict__ jobs, con
 // Sum the K-chunk partials of every block into M_s, H_s (FP64) and mirror off-diagonal blocks.
 __global__ void __launch_bounds__(256)
 k_gram_reduce(const SubDev* __restrict__ subs, const GramJob* __restrict__ jobs, const int* __restrict__ grp_first,
-              const int* __restrict__ grp_n, const float* __restrict__ work, double* Ms, double* Hs) {
+              const int* __restrict__ grp_n, const float* __restrict__ work, const int* __restrict__ ex_f,
+              const int* __restrict__ ex_hf, double* Ms, double* Hs) {
   const int gi = blockIdx.y;  // group = (subdomain, block)
   const int first = grp_first[gi], cnt = grp_n[gi];
   const GramJob J = jobs[first];
@@ -287,6 +310,11 @@ k_gram_reduce(const SubDev* __restrict__ subs, const GramJob* __restrict__ jobs,
       m += (double)w[e];
       h += (double)w[128 * 128 + e];
     }
+    if (ex_f) {  // undo the power-of-two row scales of the FP16 split
+      const int ei = ex_f[S.off_state + i];
+      m = ldexp(m, -(ei + ex_f[S.off_state + j]));
+      h = ldexp(h, -(ei + ex_hf[S.off_state + j]));
+    }
     Ms[S.off_ss + (long long)i * ns + j] = m;
     Hs[S.off_ss + (long long)i * ns + j] = h;
     if (J.I != J.J) {
@@ -301,10 +329,11 @@ k_gram_reduce(const SubDev* __restrict__ subs, const GramJob* __restrict__ jobs,
 // stage layout: A_hi 16K, A_lo 16K (MN-major), B_hi, B_lo (N rows x 128 bytes each, <= 32K each)
 constexpr uint32_t kRotStage = 2 * kTile + 2 * 256 * 128;
 
+template <bool kFp16>
 __global__ void __launch_bounds__(kThreads, 1)
 k_rotate_tc(const SubDev* __restrict__ subs, const RotJob* __restrict__ jobs, const float* __restrict__ F,
-            const uint16_t* __restrict__ Yhi, const uint16_t* __restrict__ Ylo, int kpad_max, float* __restrict__ Out,
-            int* status) {
+            const uint16_t* __restrict__ Yhi, const uint16_t* __restrict__ Ylo, int kpad_max,
+            const int* __restrict__ ex_f, const int* __restrict__ ex_y, float* __restrict__ Out, int* status) {
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   unsigned char* smem = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
   __shared__ __align__(8) uint64_t full[kStages], empty[kStages], done;
@@ -347,13 +376,15 @@ k_rotate_tc(const SubDev* __restrict__ subs, const RotJob* __restrict__ jobs, co
         const int kk = k0 + k;
         const long long g = g0 + c16 * 8;
         float4 a = make_float4(0.f, 0.f, 0.f, 0.f), b = a;
+        float sc = 1.f;
         if (kk < ns && g < S.nd) {
           const float4* p = reinterpret_cast<const float4*>(f + (long long)kk * S.nd + g);
           a = p[0];
           b = p[1];
+          if (kFp16) sc = ldexpf(1.f, ex_f[S.off_state + kk]);
         }
         uint4 hi, lo;
-        split8(a, b, hi, lo);
+        split8<kFp16>(a, b, sc, hi, lo);
         const uint32_t off = mnmaj_off(c16 >> 3, k, c16 & 7);
         sts128(stage + off, hi);
         sts128(stage + kTile + off, lo);
@@ -389,11 +420,12 @@ k_rotate_tc(const SubDev* __restrict__ subs, const RotJob* __restrict__ jobs, co
       if (ok && g < S.nd) {
 #pragma unroll
         for (int u = 0; u < 16; ++u)
-          if (c0 + u < ns) o[(long long)(c0 + u) * S.nd + g] = v[u];
+          if (c0 + u < ns)
+            o[(long long)(c0 + u) * S.nd + g] = kFp16 ? ldexpf(v[u], -ex_y[S.off_state + c0 + u]) : v[u];
       }
     }
   } else if (lane == 0) {
-    const uint32_t idesc = idesc_bf16(128, n16, true);
+    const uint32_t idesc = idesc_16(128, n16, true, kFp16);
     bool ok = true;
     for (int it = 0; it < nkt; ++it) {
       const int st = it % kStages;
@@ -424,19 +456,61 @@ k_rotate_tc(const SubDev* __restrict__ subs, const RotJob* __restrict__ jobs, co
   if (threadIdx.x == 0 && s_fail) atomicCAS(status, 0, XLS_ETIMEOUT);
 }
 
-// Y (FP64, row-major [k][n]) -> Y^T hi/lo bf16 [n][kpad_max], zero padded
-__global__ void k_split_yt(const SubDev* __restrict__ subs, const double* __restrict__ Y, int kpad_max, uint16_t* Yhi,
-                          uint16_t* Ylo) {
+// Y (FP64, row-major [k][n]) -> Y^T hi/lo [n][kpad_max], zero padded.  FP16 path: row k of Y is
+// divided by 2^ex_f[k] (it multiplies column k of the A operand) and row n of Y^T is scaled by
+// 2^ex_y[n] so that its largest entry lies in (2^13, 2^14]; the epilogue divides column n by it.
+template <bool kFp16>
+__global__ void k_split_yt(const SubDev* __restrict__ subs, const double* __restrict__ Y, int kpad_max,
+                           const int* __restrict__ ex_f, int* ex_y, uint16_t* Yhi, uint16_t* Ylo) {
   const SubDev& S = subs[blockIdx.y];
   const int ns = S.ns;
   const long long yoff = (long long)S.off_state * kpad_max;
-  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < ns * kpad_max; e += gridDim.x * blockDim.x) {
-    const int n = e / kpad_max, k = e % kpad_max;
-    const float x = (k < ns) ? (float)Y[S.off_ss + (long long)k * ns + n] : 0.f;
-    const __nv_bfloat16 h = __float2bfloat16_rn(x);
-    const __nv_bfloat16 l = __float2bfloat16_rn(x - __bfloat162float(h));
-    Yhi[yoff + e] = __bfloat16_as_ushort(h);
-    Ylo[yoff + e] = __bfloat16_as_ushort(l);
+  for (int n = blockIdx.x * blockDim.x + threadIdx.x; n < ns; n += gridDim.x * blockDim.x) {
+    int ey = 0;
+    if (kFp16) {
+      double mx = 0.0;
+      for (int k = 0; k < ns; ++k)
+        mx = fmax(mx, fabs(ldexp(Y[S.off_ss + (long long)k * ns + n], -ex_f[S.off_state + k])));
+      ey = (mx > 0.0) ? 14 - ilogb(mx) - 1 : 0;
+      ex_y[S.off_state + n] = ey;
+    }
+    for (int k = 0; k < kpad_max; ++k) {
+      double yv = 0.0;
+      if (k < ns) {
+        yv = Y[S.off_ss + (long long)k * ns + n];
+        if (kFp16) yv = ldexp(yv, ey - ex_f[S.off_state + k]);
+      }
+      uint16_t h, l;
+      split1<kFp16>((float)yv, h, l);
+      Yhi[yoff + (long long)n * kpad_max + k] = h;
+      Ylo[yoff + (long long)n * kpad_max + k] = l;
+    }
+  }
+}
+
+// per-vector exponent e with max |2^e x| in (2^13, 2^14] (0 for an all-zero vector), for the
+// two blocks F and HF; one CTA per (vector, block)
+__global__ void __launch_bounds__(512)
+k_vec_exponent(const SubDev* __restrict__ subs, int n_sub, const float* __restrict__ F, const float* __restrict__ HF,
+               int* ex_f, int* ex_hf) {
+  const int v = blockIdx.x, a = blockIdx.y;
+  const SubDev& S = subs[a];
+  if (v >= S.ns) return;
+  const float* src = (blockIdx.z == 0 ? F : HF) + S.off_blk + (long long)v * S.nd;
+  float mx = 0.f;
+  for (long long q = threadIdx.x * 4LL; q < S.nd; q += 4LL * blockDim.x) {
+    const float4 x = *reinterpret_cast<const float4*>(src + q);
+    mx = fmaxf(mx, fmaxf(fmaxf(fabsf(x.x), fabsf(x.y)), fmaxf(fabsf(x.z), fabsf(x.w))));
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+  __shared__ float red[16];
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = mx;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    for (int w = 1; w < (int)(blockDim.x >> 5); ++w) mx = fmaxf(mx, red[w]);
+    const int e = (mx > 0.f) ? 14 - ilogbf(mx) - 1 : 0;
+    (blockIdx.z == 0 ? ex_f : ex_hf)[S.off_state + v] = e;
   }
 }
 
@@ -448,30 +522,47 @@ size_t rotate_tc_smem() { return tc::kStages * tc::kRotStage + 1024; }
 bool tc_setup() {
   static int ok = -1;
   if (ok < 0) {
-    ok = cudaFuncSetAttribute(tc::k_gram_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)gram_tc_smem()) ==
-                 cudaSuccess &&
-             cudaFuncSetAttribute(tc::k_rotate_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)rotate_tc_smem()) ==
-                 cudaSuccess;
+    ok = 1;
+    ok &= cudaFuncSetAttribute(tc::k_gram_tc<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)gram_tc_smem()) == cudaSuccess;
+    ok &= cudaFuncSetAttribute(tc::k_gram_tc<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)gram_tc_smem()) == cudaSuccess;
+    ok &= cudaFuncSetAttribute(tc::k_rotate_tc<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)rotate_tc_smem()) == cudaSuccess;
+    ok &= cudaFuncSetAttribute(tc::k_rotate_tc<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)rotate_tc_smem()) == cudaSuccess;
     cudaGetLastError();
   }
   return ok == 1;
 }
 
-void launch_gram_tc(const SubDev* d_subs, const GramPlan& gp, const float* F, const float* HF, double* Ms, double* Hs,
-                    int* status, cudaStream_t st) {
+void launch_gram_tc(const SubDev* d_subs, int n_sub, int max_ns, const GramPlan& gp, bool fp16, const float* F,
+                    const float* HF, double* Ms, double* Hs, int* status, cudaStream_t st) {
   if (gp.n_jobs == 0) return;
-  tc::k_gram_tc<<<gp.n_jobs, tc::kThreads, gram_tc_smem(), st>>>(d_subs, gp.d_jobs, F, HF, gp.d_work, status);
+  if (fp16) {
+    dim3 ge(max_ns, n_sub, 2);
+    tc::k_vec_exponent<<<ge, 512, 0, st>>>(d_subs, n_sub, F, HF, gp.d_ex_f, gp.d_ex_hf);
+    tc::k_gram_tc<true><<<gp.n_jobs, tc::kThreads, gram_tc_smem(), st>>>(d_subs, gp.d_jobs, F, HF, gp.d_ex_f,
+                                                                          gp.d_ex_hf, gp.d_work, status);
+  } else {
+    tc::k_gram_tc<false><<<gp.n_jobs, tc::kThreads, gram_tc_smem(), st>>>(d_subs, gp.d_jobs, F, HF, nullptr, nullptr,
+                                                                           gp.d_work, status);
+  }
   dim3 grid(16, gp.n_groups);
-  tc::k_gram_reduce<<<grid, 256, 0, st>>>(d_subs, gp.d_jobs, gp.d_grp_first, gp.d_grp_n, gp.d_work, Ms, Hs);
+  tc::k_gram_reduce<<<grid, 256, 0, st>>>(d_subs, gp.d_jobs, gp.d_grp_first, gp.d_grp_n, gp.d_work,
+                                          fp16 ? gp.d_ex_f : nullptr, fp16 ? gp.d_ex_hf : nullptr, Ms, Hs);
 }
 
-void launch_rotate_tc(const SubDev* d_subs, int n_sub, const RotPlan& rp, const float* F, const double* Y, float* Out,
-                      int* status, cudaStream_t st) {
+// the FP16 path uses the exponents of F computed by the Gram launch of the same pass
+void launch_rotate_tc(const SubDev* d_subs, int n_sub, const RotPlan& rp, const GramPlan& gp, bool fp16,
+                      const float* F, const double* Y, float* Out, int* status, cudaStream_t st) {
   if (rp.n_jobs == 0) return;
-  dim3 gs(8, n_sub);
-  tc::k_split_yt<<<gs, 256, 0, st>>>(d_subs, Y, rp.kpad_max, rp.d_yhi, rp.d_ylo);
-  tc::k_rotate_tc<<<rp.n_jobs, tc::kThreads, rotate_tc_smem(), st>>>(d_subs, rp.d_jobs, F, rp.d_yhi, rp.d_ylo,
-                                                                     rp.kpad_max, Out, status);
+  dim3 gs(1, n_sub);
+  if (fp16) {
+    tc::k_split_yt<true><<<gs, 256, 0, st>>>(d_subs, Y, rp.kpad_max, gp.d_ex_f, rp.d_ex_y, rp.d_yhi, rp.d_ylo);
+    tc::k_rotate_tc<true><<<rp.n_jobs, tc::kThreads, rotate_tc_smem(), st>>>(
+        d_subs, rp.d_jobs, F, rp.d_yhi, rp.d_ylo, rp.kpad_max, gp.d_ex_f, rp.d_ex_y, Out, status);
+  } else {
+    tc::k_split_yt<false><<<gs, 256, 0, st>>>(d_subs, Y, rp.kpad_max, nullptr, nullptr, rp.d_yhi, rp.d_ylo);
+    tc::k_rotate_tc<false><<<rp.n_jobs, tc::kThreads, rotate_tc_smem(), st>>>(
+        d_subs, rp.d_jobs, F, rp.d_yhi, rp.d_ylo, rp.kpad_max, nullptr, nullptr, Out, status);
+  }
 }
 
 }  // namespace xls

@@ -269,8 +269,9 @@ void projection(xls_grid g, int f) {
   h_step_main<T>(g, f, -1, hf, kUnitStep);
   if (sizeof(T) == 4 && g->use_tc) {
     ProfScope ps(g, K_GRAM);
-    launch_gram_tc(g->d_subs, g->gplan, (const float*)g->blk[f], (const float*)g->blk[hf], g->Ms, g->Hs, g->status, g->st);
-    g->launches += 2;
+    launch_gram_tc(g->d_subs, g->n_sub, g->max_ns, g->gplan, g->prec == XLS_MIXED_FP16, (const float*)g->blk[f],
+                   (const float*)g->blk[hf], g->Ms, g->Hs, g->status, g->st);
+    g->launches += g->prec == XLS_MIXED_FP16 ? 3 : 2;
     return;
   }
   cudaMemsetAsync(g->Ms, 0, g->tot_ss * sizeof(double), g->st);
@@ -293,8 +294,9 @@ void rotation(xls_grid g, int f) {
   const int out = other(f, f == 0 ? 1 : 0);
   if (sizeof(T) == 4 && g->use_tc) {
     ProfScope ps(g, K_ROTATE);
-    launch_rotate_tc(g->d_subs, g->n_sub, g->rplan, (const float*)g->blk[f], g->Y, (float*)g->blk[out], g->status, g->st);
-    g->launches += 1;
+    launch_rotate_tc(g->d_subs, g->n_sub, g->rplan, g->gplan, g->prec == XLS_MIXED_FP16, (const float*)g->blk[f], g->Y,
+                     (float*)g->blk[out], g->status, g->st);
+    g->launches += 2;
   } else {
     ProfScope ps(g, K_ROTATE);
     launch_rotate<T>(g->d_subs, g->n_sub, g->max_ns, g->max_nd, blkp<T>(g, f), g->Y, blkp<T>(g, out), g->st);
@@ -447,7 +449,8 @@ xls_status xls_grid_create(const xls_cell* cell, const xls_dc* dc, int precision
                            void* cuda_stream, xls_grid* out) {
   if (!cell || !dc || !out || dc->n_sub < 1 || !dc->core_lo || !dc->core_n || !dc->buf || !dc->n_states)
     return fail(XLS_EINVAL, "xls_grid_create: null argument or n_sub < 1");
-  if (precision != XLS_FP64 && precision != XLS_MIXED_BF16) return fail(XLS_EINVAL, "unknown precision");
+  if (precision != XLS_FP64 && precision != XLS_MIXED_BF16 && precision != XLS_MIXED_FP16)
+    return fail(XLS_EINVAL, "unknown precision");
   for (int d = 0; d < 3; ++d)
     if (cell->n[d] < 2 * kN0 + 1 || !(cell->L[d] > 0)) return fail(XLS_EINVAL, "cell: n >= 13 and L > 0 per axis");
   xls_grid g = new xls_grid_s();
@@ -557,7 +560,7 @@ xls_status xls_grid_create(const xls_cell* cell, const xls_dc* dc, int precision
     xls_grid_destroy(g);
     return s;
   }
-  if (precision == XLS_MIXED_BF16) {
+  if (precision != XLS_FP64) {
     const char* env = std::getenv("XLS_STENCIL");
     bool ok = !(env && std::string(env) == "generic");
     for (const SubDev& S : g->subs) ok = ok && tma_eligible(S);
@@ -573,10 +576,13 @@ xls_status xls_grid_create(const xls_cell* cell, const xls_dc* dc, int precision
           const int nq = S.n[0] / 4, ty = tma_tile_rows(S), W = tma_row_width(S);
           size_t k = 0;
           for (; k < cls.size(); ++k)
-            if (cls[k].nq == nq && cls[k].TY == ty && cls[k].W == W) break;
+            if (cls[k].nq == nq && cls[k].TY == ty && cls[k].W == W && cls[k].h[0] == S.h[0] && cls[k].h[1] == S.h[1] &&
+                cls[k].h[2] == S.h[2])
+              break;
           if (k == cls.size()) {
             TmaClass c;
             c.nq = nq; c.TY = ty; c.W = W;
+            c.h[0] = S.h[0]; c.h[1] = S.h[1]; c.h[2] = S.h[2];
             cls.push_back(c);
             members.emplace_back();
           }
@@ -609,7 +615,7 @@ xls_status xls_grid_create(const xls_cell* cell, const xls_dc* dc, int precision
       }
     }
   }
-  if (precision == XLS_MIXED_BF16) {
+  if (precision != XLS_FP64) {
     const char* env = std::getenv("XLS_GEMM");
     bool ok = !(env && std::string(env) == "simt") && tc_setup();
     for (const SubDev& S : g->subs) ok = ok && S.ns <= 256 && S.nd % 8 == 0;
@@ -643,6 +649,8 @@ xls_status xls_grid_create(const xls_cell* cell, const xls_dc* dc, int precision
           (s = g->alloc(&gp.d_grp_first, gfirst.size() * sizeof(int))) == XLS_OK &&
           (s = g->alloc(&gp.d_grp_n, gn.size() * sizeof(int))) == XLS_OK)
         s = g->alloc(&gp.d_work, jobs.size() * 2 * 128 * 128 * sizeof(float));
+      if (s == XLS_OK) s = g->alloc(&gp.d_ex_f, g->tot_states * sizeof(int));
+      if (s == XLS_OK) s = g->alloc(&gp.d_ex_hf, g->tot_states * sizeof(int));
       std::vector<RotJob> rj;
       for (int a = 0; a < g->n_sub; ++a)
         for (int t = 0; t < (int)((g->subs[a].nd + 127) / 128); ++t) rj.push_back(RotJob{a, t});
@@ -652,6 +660,7 @@ xls_status xls_grid_create(const xls_cell* cell, const xls_dc* dc, int precision
       if (s == XLS_OK && (s = g->alloc(&rp.d_jobs, rj.size() * sizeof(RotJob))) == XLS_OK &&
           (s = g->alloc(&rp.d_yhi, (size_t)g->tot_states * rp.kpad_max * sizeof(uint16_t))) == XLS_OK)
         s = g->alloc(&rp.d_ylo, (size_t)g->tot_states * rp.kpad_max * sizeof(uint16_t));
+      if (s == XLS_OK) s = g->alloc(&rp.d_ex_y, g->tot_states * sizeof(int));
       if (s != XLS_OK) {
         xls_grid_destroy(g);
         return s;
@@ -810,7 +819,7 @@ xls_status xls_hamiltonian_set(xls_grid g, const double* veff, int veff_on_devic
     if ((s = g->alloc(&g->d_pidx, std::max<long long>(tot, 1) * sizeof(int))) != XLS_OK) return s;
     if ((s = g->alloc(&g->d_chi64, std::max<long long>(tot, 1) * sizeof(double4))) != XLS_OK) return s;
     launch_proj_table_fill<double>(g->d_subs, g->d_slots, g->n_slot, g->d_imgs, g->d_pidx, g->d_chi64, g->st);
-    if (g->prec == XLS_MIXED_BF16) {
+    if (g->prec != XLS_FP64) {
       if ((s = g->alloc(&g->d_chi32, std::max<long long>(tot, 1) * sizeof(float4))) != XLS_OK) return s;
       launch_proj_table_fill<float>(g->d_subs, g->d_slots, g->n_slot, g->d_imgs, g->d_pidx, g->d_chi32, g->st);
     }
@@ -837,7 +846,7 @@ xls_status xls_hamiltonian_set(xls_grid g, const double* veff, int veff_on_devic
     XLS_CUDA(cudaMemsetAsync(dcur, 0, g->tot_pts * sizeof(int), g->st));
     launch_rcsr_build<double>(g->d_subs, g->d_slots, g->n_slot, g->d_pidx, g->d_chi64, g->d_rptr, dcur, g->d_rslot,
                               g->d_rchi64, g->st);
-    if (g->prec == XLS_MIXED_BF16) {
+    if (g->prec != XLS_FP64) {
       if ((s = g->alloc(&g->d_rchi32, std::max<long long>(rp.back(), 1) * sizeof(float4))) != XLS_OK) return s;
       // same entry order as the FP64 table (the fill order of the atomics is not reproducible)
       launch_convert_f64_f32((const double*)g->d_rchi64, (float*)g->d_rchi32, 4 * rp.back(), g->st);

@@ -70,6 +70,7 @@ struct TmaJob {
 };
 struct TmaClass {
   int nq = 0, TY = 0, W = 0;   // threads per row (x-points / 4), rows per tile, row width
+  double h[3] = {0, 0, 0};     // grid spacing shared by the class
   int n_jobs = 0, total = 0;   // subdomains and CTAs of the class
   TmaJob* d_jobs = nullptr;
   int* d_job_off = nullptr;    // [n_jobs + 1] CTA prefix
@@ -86,6 +87,8 @@ struct GramPlan {
   int* d_grp_first = nullptr;
   int* d_grp_n = nullptr;
   float* d_work = nullptr;     // [n_jobs][2][128][128] FP32 partial sums
+  int* d_ex_f = nullptr;       // FP16 split: power-of-two exponent of every vector of F and HF
+  int* d_ex_hf = nullptr;
 };
 // Tensor-core rotation: CTA jobs (subdomain, tile of 128 grid points)
 struct RotJob {
@@ -96,12 +99,13 @@ struct RotPlan {
   RotJob* d_jobs = nullptr;
   uint16_t* d_yhi = nullptr;   // Y^T split into bf16 hi / lo, [states][kpad_max]
   uint16_t* d_ylo = nullptr;
+  int* d_ex_y = nullptr;       // FP16 split: exponent of every row of Y^T
 };
 bool tc_setup();
-void launch_gram_tc(const SubDev* d_subs, const GramPlan& gp, const float* F, const float* HF, double* Ms, double* Hs,
-                    int* status, cudaStream_t st);
-void launch_rotate_tc(const SubDev* d_subs, int n_sub, const RotPlan& rp, const float* F, const double* Y, float* Out,
-                      int* status, cudaStream_t st);
+void launch_gram_tc(const SubDev* d_subs, int n_sub, int max_ns, const GramPlan& gp, bool fp16, const float* F,
+                    const float* HF, double* Ms, double* Hs, int* status, cudaStream_t st);
+void launch_rotate_tc(const SubDev* d_subs, int n_sub, const RotPlan& rp, const GramPlan& gp, bool fp16,
+                      const float* F, const double* Y, float* Out, int* status, cudaStream_t st);
 
 // Launch plan of a block-wise kernel over all subdomains of a view: prefix of CTA counts.
 struct Plan {

@@ -16,7 +16,7 @@ import numpy as np
 LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "_lib", "libxls.so")
 
 XLS_OK, XLS_EINVAL, XLS_ENOMEM, XLS_ECUDA, XLS_ENOTSPD, XLS_ENOCONV, XLS_ETIMEOUT, XLS_ENONFINITE = range(8)
-XLS_FP64, XLS_MIXED_BF16 = 0, 1
+XLS_FP64, XLS_MIXED_BF16, XLS_MIXED_FP16 = 0, 1, 2
 STATUS_NAMES = {0: "XLS_OK", 1: "XLS_EINVAL", 2: "XLS_ENOMEM", 3: "XLS_ECUDA", 4: "XLS_ENOTSPD",
                 5: "XLS_ENOCONV", 6: "XLS_ETIMEOUT", 7: "XLS_ENONFINITE"}
 

@@ -180,11 +180,12 @@ def test_full_passes_fp64(wname):
     assert relerr(rho, ref.rho) < 1e-7
 
 
+@pytest.mark.parametrize("prec", [xls.XLS_MIXED_BF16, xls.XLS_MIXED_FP16])
 @pytest.mark.parametrize("wname", ["cfg0", "dirichlet", "dirichlet20"])
-def test_full_passes_mixed(wname):
+def test_full_passes_mixed(wname, prec):
     w = {"cfg0": lambda: synth.workload(0), "dirichlet": dirichlet_workload, "dirichlet20": lambda: dirichlet20_workload()}[wname]()
     V = pseudo.local_potential(w)
-    ref, lam, rho, mu, eb, es = _run_both(w, V, xls.XLS_MIXED_BF16, w.n_passes)
+    ref, lam, rho, mu, eb, es = _run_both(w, V, prec, w.n_passes)
     n_atoms = len(w.pos)
     assert abs(eb - ref.e_band) / n_atoms < 1e-5
     assert abs(es - ref.e_entropy) / n_atoms < 1e-5
@@ -264,7 +265,8 @@ def test_eigensolver_large_block_mixed():
     np.testing.assert_allclose(c, 1.0, atol=1e-4)
 
 
-def test_tensor_core_gram_and_rotation_match_simt(monkeypatch):
+@pytest.mark.parametrize("prec", [xls.XLS_MIXED_BF16, xls.XLS_MIXED_FP16])
+def test_tensor_core_gram_and_rotation_match_simt(monkeypatch, prec):
     """Split-BF16 tcgen05 Gram / rotation against the FP32 SIMT kernels on the same filtered block
     (both on the mixed path): M_s, H_s and the rotated block agree to the split-BF16 precision."""
     w = dirichlet20_workload()
@@ -278,7 +280,7 @@ def test_tensor_core_gram_and_rotation_match_simt(monkeypatch):
             monkeypatch.setenv("XLS_GEMM", "simt")
         else:
             monkeypatch.delenv("XLS_GEMM", raising=False)
-        with make_grid(w, V, xls.XLS_MIXED_BF16) as g:
+        with make_grid(w, V, prec) as g:
             for a in range(w.n_sub):
                 xls.xls_orbitals_set(g.h, a, psi0[a])
             xls.xls_chefsi_stage(g.h, 1, w.degree, bounds)
@@ -289,10 +291,11 @@ def test_tensor_core_gram_and_rotation_match_simt(monkeypatch):
             psi = [xls.xls_orbitals_get(g.h, a, np.zeros((int(w.n_states[a]), subs[a].N))) for a in range(w.n_sub)]
             lam = [xls.xls_get_eigs(g.h, a, int(w.n_states[a]))[0] for a in range(w.n_sub)]
         res[mode] = (sub, psi, lam)
+    tol = 3e-5 if prec == xls.XLS_MIXED_BF16 else 3e-6
     for a in range(w.n_sub):
         (Ms_t, Hs_t), (Ms_s, Hs_s) = res["tc"][0][a], res["simt"][0][a]
-        assert relerr(Ms_t, Ms_s) < 3e-5, relerr(Ms_t, Ms_s)
-        assert relerr(0.5 * (Hs_t + Hs_t.T), 0.5 * (Hs_s + Hs_s.T)) < 3e-5
+        assert relerr(Ms_t, Ms_s) < tol, relerr(Ms_t, Ms_s)
+        assert relerr(0.5 * (Hs_t + Hs_t.T), 0.5 * (Hs_s + Hs_s.T)) < tol
         np.testing.assert_allclose(res["tc"][2][a], res["simt"][2][a], atol=1e-4)
         P_t, P_s = res["tc"][1][a], res["simt"][1][a]
         # same orthonormal Ritz block up to rotations inside degenerate clusters: compare projectors
