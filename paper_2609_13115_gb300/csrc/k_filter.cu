@@ -374,7 +374,7 @@ __global__ void k_rcsr_fill(const SubDev* __restrict__ subs, const ProjSlot* __r
   }
 }
 
-constexpr int kBackPts = 1024, kBackVec = 16;
+constexpr int kBackPts = 1024, kBackVec = 8;
 
 // Y_out[v][g] += scale * sum over the slots s of point g of sum_l chi_l(g) P[s][l][v]
 template <typename T>
