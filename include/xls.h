@@ -45,8 +45,11 @@ typedef enum {
 
 typedef enum {
   XLS_FP64 = 0,        /* every step in FP64 */
-  XLS_MIXED_BF16 = 1   /* FP32 filter, split-BF16 tensor-core Gram/rotation with FP32 accumulation,
+  XLS_MIXED_BF16 = 1,  /* FP32 filter, split-BF16 tensor-core Gram/rotation with FP32 accumulation,
                           FP64 Cholesky / eigensolve / Fermi level / energies */
+  XLS_MIXED_FP16 = 2   /* as XLS_MIXED_BF16 with split-FP16 products: every vector is scaled by a power
+                          of two (its largest entry into (2^13, 2^14]) before the split, undone exactly
+                          after the accumulation; about 16x smaller product error than split BF16 */
 } xls_precision;
 
 typedef struct {
@@ -155,6 +158,25 @@ xls_status xls_set_profiling(xls_grid g, int on);
  * [1] nonlocal projection, [2] nonlocal back-projection, [3] Gram/projection GEMM,
  * [4] eigensolve, [5] rotation GEMM, [6] other, [7] unused.  Either pointer may be NULL. */
 xls_status xls_get_kernel_times(xls_grid g, double* ms8_out, int* count8_out);
+
+/* Allocation-free Gram of one block of vectors (the paper has no counterpart: a service for
+ * callers that cannot let a library allocate device memory, e.g. applications whose device
+ * memory is owned by their own pool allocator, or latency-critical loops that cannot accept
+ * the implicit synchronisation of cudaMalloc/cudaFree).
+ *   psi_f, hpsi_f: device FP32 blocks F and HF, n_states x n_points, vector-major, 16-byte
+ *                  aligned; n_points a positive multiple of 8; 1 <= n_states <= 256.
+ *   Ms_out, Hs_out: device FP64 n_states x n_states row-major: F F^T and F HF^T by the split-BF16
+ *                  tensor-core kernel (FP32 accumulation, FP64 sum of the partial sums); the
+ *                  off-diagonal 128 x 128 blocks are mirrored, so both outputs are symmetric.
+ * It allocates nothing: its scratch is a fixed 8 MiB + 256 B device array of the library, which
+ * every GPU that loads the library holds until the process exits; larger n_states are rejected
+ * with XLS_EINVAL.  The first call on a device looks up that array's device address (make it
+ * before any stream capture).  All calls share the array and it keeps the last call's
+ * contents: calls that can overlap on the GPU (other host threads, other streams) race and
+ * must be serialised by the caller.  The call queues its work on cuda_stream (NULL = legacy
+ * default stream) and returns after it has completed. */
+xls_status xls_gram_noalloc(const float* psi_f, const float* hpsi_f, long long n_points, int n_states,
+                            double* Ms_out, double* Hs_out, void* cuda_stream);
 
 /* Message of the calling thread's last failure ("" if none). */
 const char* xls_last_error(void);

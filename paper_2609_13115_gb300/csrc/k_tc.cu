@@ -325,6 +325,166 @@ k_gram_reduce(const SubDev* __restrict__ subs, const GramJob* __restrict__ jobs,
 }
 
 // ---------------------------------------------------------------------------------------------
+// Gram of one block of vectors with caller-provided scratch (the allocation-free entry point):
+// the same split-BF16 computation as k_gram_tc for a single block F, HF (n_states x n_points,
+// vector-major); CTA b handles block pair b / kc and K chunk b % kc; the FP32 partial sums go to
+// `work` ([jobs][2][128][128]), which k_gram_reduce_single sums into M_s, H_s.
+__device__ __forceinline__ void single_job(int b, int ns, long long nd, int kc, int& I, int& J, int& kt0, int& kt1) {
+  const int pair = b / kc, chunk = b % kc;
+  const int nt = (ns + 127) / 128;
+  I = 0;
+  J = pair;
+  if (nt == 2) {
+    I = pair == 2 ? 1 : 0;
+    J = pair == 0 ? 0 : 1;
+  }
+  const long long nkt = (nd + kKT - 1) / kKT;
+  kt0 = (int)(nkt * chunk / kc);
+  kt1 = (int)(nkt * (chunk + 1) / kc);
+}
+
+__global__ void __launch_bounds__(kThreads, 1)
+k_gram_tc_single(const float* __restrict__ f, const float* __restrict__ hf, long long nd, int ns, int kc,
+                 float* __restrict__ work, int* status) {
+  extern __shared__ __align__(1024) unsigned char smem_raw[];
+  unsigned char* smem = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+  __shared__ __align__(8) uint64_t full[kStages], empty[kStages], done;
+  __shared__ uint32_t s_tmem;
+  __shared__ int s_fail;
+  int JI, JJ, kt0, kt1;
+  single_job(blockIdx.x, ns, nd, kc, JI, JJ, kt0, kt1);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int i0 = 128 * JI, j0 = 128 * JJ;
+  const int nj = min(128, ns - j0);
+  const int nj16 = (nj + 15) & ~15;
+  const bool diag = (JI == JJ);
+  const int nkt = kt1 - kt0;
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < kStages; ++s) {
+      bar_init(&full[s], kProducers);
+      bar_init(&empty[s], 1);
+    }
+    bar_init(&done, 1);
+    s_fail = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 8) tmem_alloc(&s_tmem, 256);
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = s_tmem;
+  const uint32_t sbase = su32(smem);
+  if (warp < 8) {
+    const int rowsB1 = diag ? 0 : nj16;
+    const int nrows = 128 + rowsB1 + nj16;
+    for (int it = 0; it < nkt; ++it) {
+      const int st = it % kStages;
+      if (it >= kStages && !bar_wait(&empty[st], ((it / kStages) - 1) & 1)) { atomicExch(&s_fail, 1); break; }
+      const long long k0 = (long long)(kt0 + it) * kKT;
+      const uint32_t stage = sbase + st * kGramStage;
+      for (int q = threadIdx.x; q < nrows * 8; q += kProducers) {
+        const int row = q >> 3, c = q & 7;
+        const float* src;
+        int grow, r;
+        uint32_t thi, tlo;
+        if (row < 128) {
+          r = row; grow = i0 + r; src = f; thi = stage; tlo = stage + kTile;
+        } else if (row < 128 + rowsB1) {
+          r = row - 128; grow = j0 + r; src = f; thi = stage + 2 * kTile; tlo = stage + 3 * kTile;
+        } else {
+          r = row - 128 - rowsB1; grow = j0 + r; src = hf; thi = stage + 4 * kTile; tlo = stage + 5 * kTile;
+        }
+        const bool valid = (row < 128) ? (grow < ns) : (r < nj);
+        float4 a = make_float4(0.f, 0.f, 0.f, 0.f), b = a;
+        const long long kk = k0 + c * 8;
+        if (valid && kk < nd) {
+          const float4* p = reinterpret_cast<const float4*>(src + (long long)grow * nd + kk);
+          a = p[0];
+          b = p[1];
+        }
+        uint4 hi, lo;
+        split8<false>(a, b, 1.f, hi, lo);
+        const uint32_t off = kmaj_off(r, c);
+        sts128(thi + off, hi);
+        sts128(tlo + off, lo);
+      }
+      fence_async_smem();
+      bar_arrive(&full[st]);
+    }
+    const bool ok = bar_wait(&done, 0);
+    tc_fence_after();
+    if (!ok) atomicExch(&s_fail, 1);
+    const int lg = warp & 3, out = warp >> 2, row = lg * 32 + lane;
+    float* w = work + (long long)blockIdx.x * 2 * 128 * 128 + (long long)out * 128 * 128 + (long long)row * 128;
+    for (int c0 = 0; c0 < nj16; c0 += 16) {
+      float v[16];
+      tmem_ld16(tmem + ((uint32_t)(lg * 32) << 16) + (uint32_t)(out * 128 + c0), v);
+      if (ok) {
+#pragma unroll
+        for (int u = 0; u < 16; u += 4) *reinterpret_cast<float4*>(w + c0 + u) = make_float4(v[u], v[u + 1], v[u + 2], v[u + 3]);
+      }
+    }
+  } else if (lane == 0) {
+    const uint32_t idesc = idesc_16(128, nj16, false, false);
+    bool ok = true;
+    for (int it = 0; it < nkt; ++it) {
+      const int st = it % kStages;
+      if (!bar_wait(&full[st], (it / kStages) & 1)) { ok = false; break; }
+      tc_fence_after();
+      const uint32_t stage = sbase + st * kGramStage;
+      const uint32_t a_hi = stage, a_lo = stage + kTile;
+      const uint32_t b1_hi = diag ? a_hi : stage + 2 * kTile, b1_lo = diag ? a_lo : stage + 3 * kTile;
+      const uint32_t b2_hi = stage + 4 * kTile, b2_lo = stage + 5 * kTile;
+#pragma unroll
+      for (int ks = 0; ks < kKT / 16; ++ks) {
+        const uint32_t ko = ks * 32;
+        const int acc = (it > 0 || ks > 0) ? 1 : 0;
+        const uint64_t ah = sdesc(a_hi + ko, 16, 1024), al = sdesc(a_lo + ko, 16, 1024);
+        mma_bf16(tmem + 0, ah, sdesc(b1_hi + ko, 16, 1024), idesc, acc);
+        mma_bf16(tmem + 0, ah, sdesc(b1_lo + ko, 16, 1024), idesc, 1);
+        mma_bf16(tmem + 0, al, sdesc(b1_hi + ko, 16, 1024), idesc, 1);
+        mma_bf16(tmem + 128, ah, sdesc(b2_hi + ko, 16, 1024), idesc, acc);
+        mma_bf16(tmem + 128, ah, sdesc(b2_lo + ko, 16, 1024), idesc, 1);
+        mma_bf16(tmem + 128, al, sdesc(b2_hi + ko, 16, 1024), idesc, 1);
+      }
+      mma_commit(&empty[st]);
+    }
+    if (!ok) atomicExch(&s_fail, 1);
+    mma_commit(&done);
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  if (warp == 8) tmem_dealloc(tmem, 256);
+  if (threadIdx.x == 0 && s_fail) atomicCAS(status, 0, XLS_ETIMEOUT);
+}
+
+// M_s, H_s (n_states x n_states, FP64, row-major) from the partial sums of k_gram_tc_single
+__global__ void __launch_bounds__(256)
+k_gram_reduce_single(const float* __restrict__ work, int ns, long long nd, int kc, double* Ms, double* Hs) {
+  const int pair = blockIdx.y;
+  int I, J, kt0, kt1;
+  single_job(pair * kc, ns, nd, kc, I, J, kt0, kt1);
+  const int i0 = 128 * I, j0 = 128 * J;
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < 128 * 128; e += gridDim.x * blockDim.x) {
+    const int i = i0 + e / 128, j = j0 + e % 128;
+    if (i >= ns || j >= ns) continue;
+    double m = 0.0, h = 0.0;
+    for (int q = 0; q < kc; ++q) {
+      const float* w = work + (long long)(pair * kc + q) * 2 * 128 * 128;
+      m += (double)w[e];
+      h += (double)w[128 * 128 + e];
+    }
+    Ms[(long long)i * ns + j] = m;
+    Hs[(long long)i * ns + j] = h;
+    if (I != J) {
+      Ms[(long long)j * ns + i] = m;
+      Hs[(long long)j * ns + i] = h;
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------------------------
 // Rotation: one CTA = (subdomain, tile of 128 grid points); K = N_s in tiles of 64
 // stage layout: A_hi 16K, A_lo 16K (MN-major), B_hi, B_lo (N rows x 128 bytes each, <= 32K each)
 constexpr uint32_t kRotStage = 2 * kTile + 2 * 256 * 128;
@@ -547,6 +707,30 @@ void launch_gram_tc(const SubDev* d_subs, int n_sub, int max_ns, const GramPlan&
   dim3 grid(16, gp.n_groups);
   tc::k_gram_reduce<<<grid, 256, 0, st>>>(d_subs, gp.d_jobs, gp.d_grp_first, gp.d_grp_n, gp.d_work,
                                           fp16 ? gp.d_ex_f : nullptr, fp16 ? gp.d_ex_hf : nullptr, Ms, Hs);
+}
+
+// Gram of one block with caller-provided scratch; `work` holds at least
+// gram_single_jobs(n_states, kc) * 2 * 128 * 128 floats.  Returns false if the shared-memory
+// attribute cannot be set (launches nothing then).
+int gram_single_pairs(int n_states) {
+  const int nt = (n_states + 127) / 128;
+  return nt * (nt + 1) / 2;
+}
+
+bool launch_gram_tc_single(const float* F, const float* HF, long long n_points, int n_states, int kc, float* work,
+                           double* Ms, double* Hs, int* status, cudaStream_t st) {
+  static int attr = -1;
+  if (attr < 0) {
+    attr = cudaFuncSetAttribute(tc::k_gram_tc_single, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)gram_tc_smem()) == cudaSuccess ? 1 : 0;
+    cudaGetLastError();
+  }
+  if (attr != 1) return false;
+  const int pairs = gram_single_pairs(n_states);
+  tc::k_gram_tc_single<<<pairs * kc, tc::kThreads, gram_tc_smem(), st>>>(F, HF, n_points, n_states, kc, work, status);
+  dim3 grid(16, pairs);
+  tc::k_gram_reduce_single<<<grid, 256, 0, st>>>(work, n_states, n_points, kc, Ms, Hs);
+  return true;
 }
 
 // the FP16 path uses the exponents of F computed by the Gram launch of the same pass

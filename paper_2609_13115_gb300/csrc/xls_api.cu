@@ -39,6 +39,10 @@ xls_status fail(xls_status s, const std::string& msg) {
 
 }  // namespace
 
+namespace xls {
+void set_last_error(const std::string& m) { g_last_error = m; }
+}  // namespace xls
+
 struct xls_grid_s {
   int prec = XLS_FP64;
   cudaStream_t st = nullptr;

@@ -5,6 +5,8 @@
 #include <cuda_bf16.h>
 #include <stdint.h>
 
+#include <string>
+
 #include "../../include/xls.h"
 
 namespace xls {
@@ -101,7 +103,11 @@ struct RotPlan {
   uint16_t* d_ylo = nullptr;
   int* d_ex_y = nullptr;       // FP16 split: exponent of every row of Y^T
 };
+void set_last_error(const std::string& m);
 bool tc_setup();
+int gram_single_pairs(int n_states);
+bool launch_gram_tc_single(const float* F, const float* HF, long long n_points, int n_states, int kc, float* work,
+                           double* Ms, double* Hs, int* status, cudaStream_t st);
 void launch_gram_tc(const SubDev* d_subs, int n_sub, int max_ns, const GramPlan& gp, bool fp16, const float* F,
                     const float* HF, double* Ms, double* Hs, int* status, cudaStream_t st);
 void launch_rotate_tc(const SubDev* d_subs, int n_sub, const RotPlan& rp, const GramPlan& gp, bool fp16,

@@ -60,6 +60,7 @@ _SIGS = {
     "xls_get_timings": (c_int, [c_void_p, c_void_p, POINTER(c_int)]),
     "xls_set_profiling": (c_int, [c_void_p, c_int]),
     "xls_get_kernel_times": (c_int, [c_void_p, c_void_p, c_void_p]),
+    "xls_gram_noalloc": (c_int, [c_void_p, c_void_p, ctypes.c_longlong, c_int, c_void_p, c_void_p, c_void_p]),
     "xls_last_error": (ctypes.c_char_p, []),
 }
 
@@ -221,6 +222,19 @@ def xls_get_kernel_times(g):
     cnt = np.zeros(8, dtype=np.int32)
     _check(load().xls_get_kernel_times(g, ms.ctypes.data_as(c_void_p), cnt.ctypes.data_as(c_void_p)))
     return ms, cnt
+
+
+def xls_gram_noalloc(psi_f, hpsi_f, Ms_out, Hs_out, stream=None):
+    """Allocation-free Gram of one block (see include/xls.h): psi_f, hpsi_f are contiguous CUDA
+    float32 tensors of shape (n_states, n_points); Ms_out, Hs_out CUDA float64 (n_states, n_states)."""
+    for t in (psi_f, hpsi_f, Ms_out, Hs_out):
+        if not (hasattr(t, "is_cuda") and t.is_cuda and t.is_contiguous()):
+            raise ValueError("xls_gram_noalloc takes contiguous CUDA tensors")
+    ns, nd = psi_f.shape
+    _check(load().xls_gram_noalloc(c_void_p(psi_f.data_ptr()), c_void_p(hpsi_f.data_ptr()), int(nd), int(ns),
+                                   c_void_p(Ms_out.data_ptr()), c_void_p(Hs_out.data_ptr()),
+                                   c_void_p(stream) if stream else None))
+    return Ms_out, Hs_out
 
 
 class Grid:
