@@ -32,6 +32,10 @@ constexpr int kProducers = 256;
 constexpr int kKT = 64;            // K elements per tile (128-byte bf16 rows)
 constexpr int kStages = 2;
 constexpr long long kSpin = 1LL << 26;  // bounded mbarrier waits
+// Tensor-core FP32 accumulation does not round to nearest; its error grows with the number of
+// MMAs added into one accumulator.  The Gram kernels therefore read their accumulators out every
+// kFlush K tiles (12 * kFlush MMAs) into FP32 partial sums with round-to-nearest adds.
+constexpr int kFlush = 4;
 
 __device__ __forceinline__ uint32_t su32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
@@ -166,7 +170,7 @@ k_gram_tc(const SubDev* __restrict__ subs, const GramJob* __restrict__ jobs, con
           float* __restrict__ work, int* status) {
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   unsigned char* smem = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
-  __shared__ __align__(8) uint64_t full[kStages], empty[kStages], done;
+  __shared__ __align__(8) uint64_t full[kStages], empty[kStages], acc_full[2], acc_empty[2];
   __shared__ uint32_t s_tmem;
   __shared__ int s_fail;
   const GramJob J = jobs[blockIdx.x];
@@ -183,11 +187,14 @@ k_gram_tc(const SubDev* __restrict__ subs, const GramJob* __restrict__ jobs, con
       bar_init(&full[s], kProducers);
       bar_init(&empty[s], 1);
     }
-    bar_init(&done, 1);
+    for (int b = 0; b < 2; ++b) {
+      bar_init(&acc_full[b], 1);
+      bar_init(&acc_empty[b], kProducers);
+    }
     s_fail = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
-  if (warp == 8) tmem_alloc(&s_tmem, 256);
+  if (warp == 8) tmem_alloc(&s_tmem, 512);
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
@@ -196,6 +203,34 @@ k_gram_tc(const SubDev* __restrict__ subs, const GramJob* __restrict__ jobs, con
   const float* f = F + S.off_blk;
   const float* hf = HF + S.off_blk;
 
+  // Read the accumulators of flush period p (buffer p % 2, D1 at +0, D2 at +128 columns) and add
+  // them to the CTA's FP32 partial sums with round-to-nearest adds (the first period stores).
+  const int lg = warp & 3, out_m = warp >> 2, prow = lg * 32 + lane;
+  float* wrow = work + (long long)blockIdx.x * 2 * 128 * 128 + (long long)out_m * 128 * 128 + (long long)prow * 128;
+  auto flush = [&](int p) {
+    const int b = p & 1;
+    const bool ok = bar_wait(&acc_full[b], (p >> 1) & 1);
+    tc_fence_after();
+    if (!ok) atomicExch(&s_fail, 1);
+    for (int c0 = 0; c0 < nj16; c0 += 16) {
+      float v[16];
+      tmem_ld16(tmem + ((uint32_t)(lg * 32) << 16) + (uint32_t)(b * 256 + out_m * 128 + c0), v);
+      if (ok) {
+#pragma unroll
+        for (int u = 0; u < 16; u += 4) {
+          float4* dst = reinterpret_cast<float4*>(wrow + c0 + u);
+          float4 o = make_float4(v[u], v[u + 1], v[u + 2], v[u + 3]);
+          if (p > 0) {
+            const float4 q = *dst;
+            o.x += q.x; o.y += q.y; o.z += q.z; o.w += q.w;
+          }
+          *dst = o;
+        }
+      }
+    }
+    tc_fence_before();
+    bar_arrive(&acc_empty[b]);
+  };
   if (warp < 8) {
     // ---------------- producers
     const int rowsB1 = diag ? 0 : nj16;
@@ -236,22 +271,7 @@ k_gram_tc(const SubDev* __restrict__ subs, const GramJob* __restrict__ jobs, con
       }
       fence_async_smem();
       bar_arrive(&full[st]);
-    }
-    // ---------------- epilogue: warps 0-3 read D1 (columns 0..), warps 4-7 read D2 (columns 128..)
-    const bool ok = bar_wait(&done, 0);
-    tc_fence_after();
-    if (!ok) atomicExch(&s_fail, 1);
-    const int lg = warp & 3;
-    const int out = warp >> 2;
-    const int row = lg * 32 + lane;
-    float* w = work + (long long)blockIdx.x * 2 * 128 * 128 + (long long)out * 128 * 128 + (long long)row * 128;
-    for (int c0 = 0; c0 < nj16; c0 += 16) {
-      float v[16];
-      tmem_ld16(tmem + ((uint32_t)(lg * 32) << 16) + (uint32_t)(out * 128 + c0), v);
-      if (ok) {
-#pragma unroll
-        for (int u = 0; u < 16; u += 4) *reinterpret_cast<float4*>(w + c0 + u) = make_float4(v[u], v[u + 1], v[u + 2], v[u + 3]);
-      }
+      if (it % kFlush == kFlush - 1 || it == nkt - 1) flush(it / kFlush);
     }
   } else if (lane == 0) {
     // ---------------- MMA issuer
@@ -260,7 +280,10 @@ k_gram_tc(const SubDev* __restrict__ subs, const GramJob* __restrict__ jobs, con
     for (int it = 0; it < nkt; ++it) {
       const int st = it % kStages;
       if (!bar_wait(&full[st], (it / kStages) & 1)) { ok = false; break; }
+      const int per = it / kFlush, buf = per & 1;
+      if (it % kFlush == 0 && per >= 2 && !bar_wait(&acc_empty[buf], ((per >> 1) - 1) & 1)) { ok = false; break; }
       tc_fence_after();
+      const uint32_t acc_base = tmem + (uint32_t)(buf * 256);
       const uint32_t stage = sbase + st * kGramStage;
       const uint32_t a_hi = stage, a_lo = stage + kTile;
       const uint32_t b1_hi = diag ? a_hi : stage + 2 * kTile, b1_lo = diag ? a_lo : stage + 3 * kTile;
@@ -268,24 +291,24 @@ k_gram_tc(const SubDev* __restrict__ subs, const GramJob* __restrict__ jobs, con
 #pragma unroll
       for (int ks = 0; ks < kKT / 16; ++ks) {
         const uint32_t ko = ks * 32;           // 16 bf16 = 32 bytes along K inside the swizzle row
-        const int acc = (it > 0 || ks > 0) ? 1 : 0;
+        const int acc = (it % kFlush > 0 || ks > 0) ? 1 : 0;
         const uint64_t ah = sdesc(a_hi + ko, 16, 1024), al = sdesc(a_lo + ko, 16, 1024);
-        mma_bf16(tmem + 0, ah, sdesc(b1_hi + ko, 16, 1024), idesc, acc);
-        mma_bf16(tmem + 0, ah, sdesc(b1_lo + ko, 16, 1024), idesc, 1);
-        mma_bf16(tmem + 0, al, sdesc(b1_hi + ko, 16, 1024), idesc, 1);
-        mma_bf16(tmem + 128, ah, sdesc(b2_hi + ko, 16, 1024), idesc, acc);
-        mma_bf16(tmem + 128, ah, sdesc(b2_lo + ko, 16, 1024), idesc, 1);
-        mma_bf16(tmem + 128, al, sdesc(b2_hi + ko, 16, 1024), idesc, 1);
+        mma_bf16(acc_base + 0, ah, sdesc(b1_hi + ko, 16, 1024), idesc, acc);
+        mma_bf16(acc_base + 0, ah, sdesc(b1_lo + ko, 16, 1024), idesc, 1);
+        mma_bf16(acc_base + 0, al, sdesc(b1_hi + ko, 16, 1024), idesc, 1);
+        mma_bf16(acc_base + 128, ah, sdesc(b2_hi + ko, 16, 1024), idesc, acc);
+        mma_bf16(acc_base + 128, ah, sdesc(b2_lo + ko, 16, 1024), idesc, 1);
+        mma_bf16(acc_base + 128, al, sdesc(b2_hi + ko, 16, 1024), idesc, 1);
       }
       mma_commit(&empty[st]);
+      if (it % kFlush == kFlush - 1 || it == nkt - 1) mma_commit(&acc_full[buf]);
     }
     if (!ok) atomicExch(&s_fail, 1);
-    mma_commit(&done);
   }
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
-  if (warp == 8) tmem_dealloc(tmem, 256);
+  if (warp == 8) tmem_dealloc(tmem, 512);
   if (threadIdx.x == 0 && s_fail) atomicCAS(status, 0, XLS_ETIMEOUT);
 }
 
@@ -348,7 +371,7 @@ k_gram_tc_single(const float* __restrict__ f, const float* __restrict__ hf, long
                  float* __restrict__ work, int* status) {
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   unsigned char* smem = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
-  __shared__ __align__(8) uint64_t full[kStages], empty[kStages], done;
+  __shared__ __align__(8) uint64_t full[kStages], empty[kStages], acc_full[2], acc_empty[2];
   __shared__ uint32_t s_tmem;
   __shared__ int s_fail;
   int JI, JJ, kt0, kt1;
@@ -364,16 +387,47 @@ k_gram_tc_single(const float* __restrict__ f, const float* __restrict__ hf, long
       bar_init(&full[s], kProducers);
       bar_init(&empty[s], 1);
     }
-    bar_init(&done, 1);
+    for (int b = 0; b < 2; ++b) {
+      bar_init(&acc_full[b], 1);
+      bar_init(&acc_empty[b], kProducers);
+    }
     s_fail = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
-  if (warp == 8) tmem_alloc(&s_tmem, 256);
+  if (warp == 8) tmem_alloc(&s_tmem, 512);
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
   const uint32_t tmem = s_tmem;
   const uint32_t sbase = su32(smem);
+  // Read the accumulators of flush period p (buffer p % 2, D1 at +0, D2 at +128 columns) and add
+  // them to the CTA's FP32 partial sums with round-to-nearest adds (the first period stores).
+  const int lg = warp & 3, out_m = warp >> 2, prow = lg * 32 + lane;
+  float* wrow = work + (long long)blockIdx.x * 2 * 128 * 128 + (long long)out_m * 128 * 128 + (long long)prow * 128;
+  auto flush = [&](int p) {
+    const int b = p & 1;
+    const bool ok = bar_wait(&acc_full[b], (p >> 1) & 1);
+    tc_fence_after();
+    if (!ok) atomicExch(&s_fail, 1);
+    for (int c0 = 0; c0 < nj16; c0 += 16) {
+      float v[16];
+      tmem_ld16(tmem + ((uint32_t)(lg * 32) << 16) + (uint32_t)(b * 256 + out_m * 128 + c0), v);
+      if (ok) {
+#pragma unroll
+        for (int u = 0; u < 16; u += 4) {
+          float4* dst = reinterpret_cast<float4*>(wrow + c0 + u);
+          float4 o = make_float4(v[u], v[u + 1], v[u + 2], v[u + 3]);
+          if (p > 0) {
+            const float4 q = *dst;
+            o.x += q.x; o.y += q.y; o.z += q.z; o.w += q.w;
+          }
+          *dst = o;
+        }
+      }
+    }
+    tc_fence_before();
+    bar_arrive(&acc_empty[b]);
+  };
   if (warp < 8) {
     const int rowsB1 = diag ? 0 : nj16;
     const int nrows = 128 + rowsB1 + nj16;
@@ -410,19 +464,7 @@ k_gram_tc_single(const float* __restrict__ f, const float* __restrict__ hf, long
       }
       fence_async_smem();
       bar_arrive(&full[st]);
-    }
-    const bool ok = bar_wait(&done, 0);
-    tc_fence_after();
-    if (!ok) atomicExch(&s_fail, 1);
-    const int lg = warp & 3, out = warp >> 2, row = lg * 32 + lane;
-    float* w = work + (long long)blockIdx.x * 2 * 128 * 128 + (long long)out * 128 * 128 + (long long)row * 128;
-    for (int c0 = 0; c0 < nj16; c0 += 16) {
-      float v[16];
-      tmem_ld16(tmem + ((uint32_t)(lg * 32) << 16) + (uint32_t)(out * 128 + c0), v);
-      if (ok) {
-#pragma unroll
-        for (int u = 0; u < 16; u += 4) *reinterpret_cast<float4*>(w + c0 + u) = make_float4(v[u], v[u + 1], v[u + 2], v[u + 3]);
-      }
+      if (it % kFlush == kFlush - 1 || it == nkt - 1) flush(it / kFlush);
     }
   } else if (lane == 0) {
     const uint32_t idesc = idesc_16(128, nj16, false, false);
@@ -430,7 +472,10 @@ k_gram_tc_single(const float* __restrict__ f, const float* __restrict__ hf, long
     for (int it = 0; it < nkt; ++it) {
       const int st = it % kStages;
       if (!bar_wait(&full[st], (it / kStages) & 1)) { ok = false; break; }
+      const int per = it / kFlush, buf = per & 1;
+      if (it % kFlush == 0 && per >= 2 && !bar_wait(&acc_empty[buf], ((per >> 1) - 1) & 1)) { ok = false; break; }
       tc_fence_after();
+      const uint32_t acc_base = tmem + (uint32_t)(buf * 256);
       const uint32_t stage = sbase + st * kGramStage;
       const uint32_t a_hi = stage, a_lo = stage + kTile;
       const uint32_t b1_hi = diag ? a_hi : stage + 2 * kTile, b1_lo = diag ? a_lo : stage + 3 * kTile;
@@ -438,24 +483,24 @@ k_gram_tc_single(const float* __restrict__ f, const float* __restrict__ hf, long
 #pragma unroll
       for (int ks = 0; ks < kKT / 16; ++ks) {
         const uint32_t ko = ks * 32;
-        const int acc = (it > 0 || ks > 0) ? 1 : 0;
+        const int acc = (it % kFlush > 0 || ks > 0) ? 1 : 0;
         const uint64_t ah = sdesc(a_hi + ko, 16, 1024), al = sdesc(a_lo + ko, 16, 1024);
-        mma_bf16(tmem + 0, ah, sdesc(b1_hi + ko, 16, 1024), idesc, acc);
-        mma_bf16(tmem + 0, ah, sdesc(b1_lo + ko, 16, 1024), idesc, 1);
-        mma_bf16(tmem + 0, al, sdesc(b1_hi + ko, 16, 1024), idesc, 1);
-        mma_bf16(tmem + 128, ah, sdesc(b2_hi + ko, 16, 1024), idesc, acc);
-        mma_bf16(tmem + 128, ah, sdesc(b2_lo + ko, 16, 1024), idesc, 1);
-        mma_bf16(tmem + 128, al, sdesc(b2_hi + ko, 16, 1024), idesc, 1);
+        mma_bf16(acc_base + 0, ah, sdesc(b1_hi + ko, 16, 1024), idesc, acc);
+        mma_bf16(acc_base + 0, ah, sdesc(b1_lo + ko, 16, 1024), idesc, 1);
+        mma_bf16(acc_base + 0, al, sdesc(b1_hi + ko, 16, 1024), idesc, 1);
+        mma_bf16(acc_base + 128, ah, sdesc(b2_hi + ko, 16, 1024), idesc, acc);
+        mma_bf16(acc_base + 128, ah, sdesc(b2_lo + ko, 16, 1024), idesc, 1);
+        mma_bf16(acc_base + 128, al, sdesc(b2_hi + ko, 16, 1024), idesc, 1);
       }
       mma_commit(&empty[st]);
+      if (it % kFlush == kFlush - 1 || it == nkt - 1) mma_commit(&acc_full[buf]);
     }
     if (!ok) atomicExch(&s_fail, 1);
-    mma_commit(&done);
   }
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
-  if (warp == 8) tmem_dealloc(tmem, 256);
+  if (warp == 8) tmem_dealloc(tmem, 512);
   if (threadIdx.x == 0 && s_fail) atomicCAS(status, 0, XLS_ETIMEOUT);
 }
 
@@ -734,10 +779,14 @@ bool launch_gram_tc_single(const float* F, const float* HF, long long n_points, 
 }
 
 // the FP16 path uses the exponents of F computed by the Gram launch of the same pass
-void launch_rotate_tc(const SubDev* d_subs, int n_sub, const RotPlan& rp, const GramPlan& gp, bool fp16,
-                      const float* F, const double* Y, float* Out, int* status, cudaStream_t st) {
+void launch_rotate_tc(const SubDev* d_subs, int n_sub, int max_ns, const RotPlan& rp, const GramPlan& gp, bool fp16,
+                      bool need_exponents, const float* F, const double* Y, float* Out, int* status, cudaStream_t st) {
   if (rp.n_jobs == 0) return;
   dim3 gs(1, n_sub);
+  if (fp16 && need_exponents) {   // the Gram of this pass did not run on tensor cores
+    dim3 ge(max_ns, n_sub, 1);
+    tc::k_vec_exponent<<<ge, 512, 0, st>>>(d_subs, n_sub, F, F, gp.d_ex_f, gp.d_ex_hf);
+  }
   if (fp16) {
     tc::k_split_yt<true><<<gs, 256, 0, st>>>(d_subs, Y, rp.kpad_max, gp.d_ex_f, rp.d_ex_y, rp.d_yhi, rp.d_ylo);
     tc::k_rotate_tc<true><<<rp.n_jobs, tc::kThreads, rotate_tc_smem(), st>>>(

@@ -74,8 +74,8 @@ struct xls_grid_s {
   bool use_tma = false;
   std::vector<TmaClass> tcls;
   CUtensorMap* d_maps = nullptr;
-  // tensor-core GEMMs (mixed path)
-  bool use_tc = false;
+  // tensor-core GEMMs (mixed path): Gram and rotation can be switched to SIMT independently
+  bool use_tc = false, use_tc_gram = false, use_tc_rot = false;
   GramPlan gplan;
   RotPlan rplan;
   // projectors
@@ -271,7 +271,7 @@ template <typename T>
 void projection(xls_grid g, int f) {
   const int hf = other(f, f == 0 ? 1 : 0);
   h_step_main<T>(g, f, -1, hf, kUnitStep);
-  if (sizeof(T) == 4 && g->use_tc) {
+  if (sizeof(T) == 4 && g->use_tc_gram) {
     ProfScope ps(g, K_GRAM);
     launch_gram_tc(g->d_subs, g->n_sub, g->max_ns, g->gplan, g->prec == XLS_MIXED_FP16, (const float*)g->blk[f],
                    (const float*)g->blk[hf], g->Ms, g->Hs, g->status, g->st);
@@ -296,10 +296,10 @@ void eigensolve(xls_grid g) {
 template <typename T>
 void rotation(xls_grid g, int f) {
   const int out = other(f, f == 0 ? 1 : 0);
-  if (sizeof(T) == 4 && g->use_tc) {
+  if (sizeof(T) == 4 && g->use_tc_rot) {
     ProfScope ps(g, K_ROTATE);
-    launch_rotate_tc(g->d_subs, g->n_sub, g->rplan, g->gplan, g->prec == XLS_MIXED_FP16, (const float*)g->blk[f], g->Y,
-                     (float*)g->blk[out], g->status, g->st);
+    launch_rotate_tc(g->d_subs, g->n_sub, g->max_ns, g->rplan, g->gplan, g->prec == XLS_MIXED_FP16, !g->use_tc_gram,
+                     (const float*)g->blk[f], g->Y, (float*)g->blk[out], g->status, g->st);
     g->launches += 2;
   } else {
     ProfScope ps(g, K_ROTATE);
@@ -674,6 +674,10 @@ xls_status xls_grid_create(const xls_cell* cell, const xls_dc* dc, int precision
       cudaMemcpy(gp.d_grp_n, gn.data(), gn.size() * sizeof(int), cudaMemcpyHostToDevice);
       cudaMemcpy(rp.d_jobs, rj.data(), rj.size() * sizeof(RotJob), cudaMemcpyHostToDevice);
       g->use_tc = true;
+      const char* eg = std::getenv("XLS_GEMM_GRAM");
+      const char* er = std::getenv("XLS_GEMM_ROT");
+      g->use_tc_gram = !(eg && std::string(eg) == "simt");
+      g->use_tc_rot = !(er && std::string(er) == "simt");
     }
   }
   cudaMemset(g->status, 0, 2 * sizeof(int));

@@ -110,8 +110,8 @@ bool launch_gram_tc_single(const float* F, const float* HF, long long n_points, 
                            double* Ms, double* Hs, int* status, cudaStream_t st);
 void launch_gram_tc(const SubDev* d_subs, int n_sub, int max_ns, const GramPlan& gp, bool fp16, const float* F,
                     const float* HF, double* Ms, double* Hs, int* status, cudaStream_t st);
-void launch_rotate_tc(const SubDev* d_subs, int n_sub, const RotPlan& rp, const GramPlan& gp, bool fp16,
-                      const float* F, const double* Y, float* Out, int* status, cudaStream_t st);
+void launch_rotate_tc(const SubDev* d_subs, int n_sub, int max_ns, const RotPlan& rp, const GramPlan& gp, bool fp16,
+                      bool need_exponents, const float* F, const double* Y, float* Out, int* status, cudaStream_t st);
 
 // Launch plan of a block-wise kernel over all subdomains of a view: prefix of CTA counts.
 struct Plan {
