@@ -285,26 +285,22 @@ __device__ __forceinline__ double hash_unit(unsigned a, unsigned b) {
 // coalesce.
 constexpr int kTriThreads = 128;
 
-// kSmemWork: the per-thread work arrays live in shared memory (after the bisection arrays);
-// otherwise in the interleaved global scratch
-template <bool kSmemWork>
-__global__ void __launch_bounds__(kTriThreads)
-k_tri_eig(const SubDev* __restrict__ subs, double* vecs, double* Zm, double* scratch_all, long long scr_stride,
-          double* Rm, double* lam_out, int max_ns) {
+// (a) shifts: FP32 Sturm bisection for every eigenvalue index; clusters of close eigenvalues.
+// vecs per subdomain: d [0,n), e [n,2n), tau [2n,3n), lam32 [3n,4n), cluster starts [4n,5n] (as doubles),
+// [5n+1] cluster count, [5n+2] |T| estimate.
+__global__ void __launch_bounds__(128)
+k_tri_bisect(const SubDev* __restrict__ subs, double* vecs) {
   const SubDev& S = subs[blockIdx.x];
   const int n = S.ns;
   double* d = vecs + 8LL * S.off_state;
   double* e = d + n;
   double* lam32 = d + 3 * n;
-  double* Z = Zm + S.off_ss;
-  double* Rb = Rm + S.off_ss;
+  double* cst = d + 4 * n;
   extern __shared__ float smf[];
   float* df = smf;
   float* e2f = smf + n;
-  int* cstart = (int*)(smf + 2 * n);   // n + 1 cluster starts
   __shared__ float s_gl, s_gu, s_pivmin;
   __shared__ double s_tnorm;
-  __shared__ int s_ncl;
   for (int i = threadIdx.x; i < n; i += blockDim.x) {
     df[i] = (float)d[i];
     e2f[i] = (float)(e[i] * e[i]);
@@ -335,32 +331,49 @@ k_tri_eig(const SubDev* __restrict__ subs, double* vecs, double* Zm, double* scr
     lam32[i] = 0.5 * ((double)lo + (double)hi);
   }
   __syncthreads();
-  const double tnorm = s_tnorm;
-  const double ctol = 1e-4 * tnorm;
   if (threadIdx.x == 0) {
+    const double ctol = 1e-4 * s_tnorm;
     int c = 0;
     for (int i = 0; i < n; ++i)
-      if (i == 0 || lam32[i] - lam32[i - 1] > ctol) cstart[c++] = i;
-    cstart[c] = n;
-    s_ncl = c;
+      if (i == 0 || lam32[i] - lam32[i - 1] > ctol) cst[c++] = (double)i;
+    cst[c] = (double)n;
+    d[5 * n + 1] = (double)c;
+    d[5 * n + 2] = s_tnorm;
   }
-  __syncthreads();
+}
+
+// (b) vectors: CTA (subdomain, group) handles the clusters c = group * blockDim + t (stride
+// gridDim.y * blockDim).  kSmemWork: per-thread work arrays in shared memory, else in the
+// interleaved global scratch.
+template <bool kSmemWork>
+__global__ void __launch_bounds__(kTriThreads)
+k_tri_eig(const SubDev* __restrict__ subs, double* vecs, double* Zm, double* scratch_all, long long scr_stride,
+          double* Rm, double* lam_out, int max_ns) {
+  const SubDev& S = subs[blockIdx.x];
+  const int n = S.ns;
+  double* d = vecs + 8LL * S.off_state;
+  double* e = d + n;
+  double* lam32 = d + 3 * n;
+  const double* cst = d + 4 * n;
+  double* Z = Zm + S.off_ss;
+  double* Rb = Rm + S.off_ss;
+  extern __shared__ __align__(16) unsigned char smraw[];
+  const int ncl = (int)d[5 * n + 1];
+  const double tnorm = d[5 * n + 2];
   const int T = blockDim.x, t = threadIdx.x;
   double* scr;
   if (kSmemWork) {
-    // 16-byte aligned start after df, e2f (2 max_ns floats) and cstart (max_ns + 1 ints)
-    const size_t off = ((size_t)(3 * max_ns + 1) * 4 + 15) & ~(size_t)15;
-    scr = reinterpret_cast<double*>(reinterpret_cast<unsigned char*>(smf) + off);
+    scr = reinterpret_cast<double*>(smraw);
   } else {
-    scr = scratch_all + (long long)blockIdx.x * scr_stride;
+    scr = scratch_all + ((long long)blockIdx.x * gridDim.y + blockIdx.y) * scr_stride;
   }
   // interleaved arrays: lm (n), dinv (n), x (n)
   auto LM = [&](int j) -> double& { return scr[(long long)j * T + t]; };
   auto DI = [&](int j) -> double& { return scr[(long long)(n + j) * T + t]; };
   auto X = [&](int j) -> double& { return scr[(long long)(2 * n + j) * T + t]; };
   const double tiny = 1e-15 * tnorm;
-  for (int c = t; c < s_ncl; c += T) {
-    const int s = cstart[c], tt = cstart[c + 1];
+  for (int c = blockIdx.y * T + t; c < ncl; c += gridDim.y * T) {
+    const int s = (int)cst[c], tt = (int)cst[c + 1];
     const int k = tt - s;
     for (int mbr = s; mbr < tt; ++mbr) {
       // a singleton refines its shift to the Rayleigh quotient after every solve (Rayleigh
@@ -566,27 +579,34 @@ static bool smem_ok(K kernel, size_t bytes) {
 }
 
 void launch_eig(const SubDev* d_subs, int n_sub, int max_ns, double* Ms, double* Hs, double* Y, double* W, double* lam,
-                double* vecs, int* status, double* scratch, double* R, cudaStream_t st) {
+                double* vecs, int* status, double* scratch, double* R, bool cluster, cudaStream_t st) {
   const size_t mat = (size_t)max_ns * max_ns * sizeof(double);
   const size_t vbytes = 2 * (size_t)max_ns * sizeof(double);
-  if (smem_ok(k_cholesky<true>, mat)) k_cholesky<true><<<n_sub, 512, mat, st>>>(d_subs, Ms, status);
+  // Cholesky and tridiagonalisation on a cluster of CTAs per subdomain; one CTA per subdomain
+  // where the cluster variant cannot be launched, or when the caller asks for it
+  if (cluster && launch_cholesky_cluster(d_subs, n_sub, max_ns, Ms, status, st)) {
+  } else if (smem_ok(k_cholesky<true>, mat)) k_cholesky<true><<<n_sub, 512, mat, st>>>(d_subs, Ms, status);
   else k_cholesky<false><<<n_sub, 512, 0, st>>>(d_subs, Ms, status);
   dim3 gt((max_ns + 7) / 8, n_sub);   // 8 warps (columns) per CTA
   trsm(false, max_ns, gt, d_subs, Ms, Hs, 0, W, st);   // W = L^-1 H_s
   trsm(false, max_ns, gt, d_subs, Ms, W, 1, Hs, st);   // A = L^-1 W^T
-  if (smem_ok(k_tridiag<true>, mat + vbytes)) k_tridiag<true><<<n_sub, 512, mat + vbytes, st>>>(d_subs, Hs, vecs, max_ns);
+  if (cluster && launch_tridiag_cluster(d_subs, n_sub, max_ns, Hs, vecs, st)) {
+  } else if (smem_ok(k_tridiag<true>, mat + vbytes)) k_tridiag<true><<<n_sub, 512, mat + vbytes, st>>>(d_subs, Hs, vecs, max_ns);
   else k_tridiag<false><<<n_sub, 512, vbytes, st>>>(d_subs, Hs, vecs, max_ns);
+  k_tri_bisect<<<n_sub, 128, 2 * max_ns * sizeof(float), st>>>(d_subs, vecs);
   {
-    const size_t head = (((size_t)(3 * max_ns + 1) * 4 + 15) & ~(size_t)15);
+    // vector stage: 32 threads per CTA with shared-memory work arrays where they fit, one CTA per
+    // 32 clusters of a subdomain; else 128 threads per CTA on the global scratch
     const size_t per_thread = 3 * (size_t)max_ns * sizeof(double);
-    int thr = 0;
-    for (int tt = kTriThreads; tt >= 32; tt -= 32)
-      if (head + per_thread * tt <= 200 * 1024) { thr = tt; break; }
-    if (thr > 0 && smem_ok(k_tri_eig<true>, head + per_thread * thr))
-      k_tri_eig<true><<<n_sub, thr, head + per_thread * thr, st>>>(d_subs, vecs, W, scratch, 0, R, lam, max_ns);
-    else
-      k_tri_eig<false><<<n_sub, kTriThreads, head, st>>>(d_subs, vecs, W, scratch, 3LL * max_ns * kTriThreads, R, lam,
-                                                         max_ns);
+    const int groups = (max_ns + 31) / 32;
+    if (per_thread * 32 <= 200 * 1024 && smem_ok(k_tri_eig<true>, per_thread * 32)) {
+      dim3 gv(n_sub, groups);
+      k_tri_eig<true><<<gv, 32, per_thread * 32, st>>>(d_subs, vecs, W, scratch, 0, R, lam, max_ns);
+    } else {
+      dim3 gv(n_sub, 1);
+      k_tri_eig<false><<<gv, kTriThreads, 0, st>>>(d_subs, vecs, W, scratch, 3LL * max_ns * kTriThreads, R, lam,
+                                                   max_ns);
+    }
   }
   dim3 gb((max_ns + 31) / 32, n_sub);
   k_backtransform<<<gb, 256, (max_ns + 256) * sizeof(double), st>>>(d_subs, Hs, vecs, W);

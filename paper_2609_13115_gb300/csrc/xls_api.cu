@@ -76,6 +76,7 @@ struct xls_grid_s {
   CUtensorMap* d_maps = nullptr;
   // tensor-core GEMMs (mixed path): Gram and rotation can be switched to SIMT independently
   bool use_tc = false, use_tc_gram = false, use_tc_rot = false;
+  bool eig_cluster = true;  // Cholesky / tridiagonalisation on CTA clusters (XLS_EIG=single: one CTA)
   GramPlan gplan;
   RotPlan rplan;
   // projectors
@@ -289,8 +290,8 @@ void eigensolve(xls_grid g) {
   cudaMemcpyAsync(g->Ab, g->Hs, g->tot_ss * sizeof(double), cudaMemcpyDeviceToDevice, g->st);
   { ProfScope ps(g, K_EIG);
     launch_eig(g->d_subs, g->n_sub, g->max_ns, g->Lb, g->Ab, g->Y, g->W, g->lam, g->vecs, g->status, g->eig_scr, g->R,
-               g->st); }
-  g->launches += 7;
+               g->eig_cluster, g->st); }
+  g->launches += 8;
 }
 
 template <typename T>
@@ -618,6 +619,10 @@ xls_status xls_grid_create(const xls_cell* cell, const xls_dc* dc, int precision
         g->use_tma = true;
       }
     }
+  }
+  {
+    const char* env = std::getenv("XLS_EIG");
+    g->eig_cluster = !(env && std::string(env) == "single");
   }
   if (precision != XLS_FP64) {
     const char* env = std::getenv("XLS_GEMM");

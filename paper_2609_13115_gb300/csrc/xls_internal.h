@@ -181,8 +181,10 @@ void launch_fermi_occ(const double* lam, const double* c, int n_tot, double n_e,
 // ---- eigensolver (FP64) --------------------------------------------------------------------
 // L (in: M_s, out: Cholesky factor), A (in: H_s, out: reflectors), W (workspace/Z), Y (out),
 // R (cluster workspace), all n x n per subdomain; lam (out); vecs 8n per subdomain.
+bool launch_cholesky_cluster(const SubDev* d_subs, int n_sub, int max_ns, double* Ms, int* status, cudaStream_t st);
+bool launch_tridiag_cluster(const SubDev* d_subs, int n_sub, int max_ns, double* A, double* vecs, cudaStream_t st);
 void launch_eig(const SubDev* d_subs, int n_sub, int max_ns, double* L, double* A, double* Y, double* W, double* lam,
-                double* vecs, int* status, double* scratch, double* R, cudaStream_t st);
+                double* vecs, int* status, double* scratch, double* R, bool cluster, cudaStream_t st);
 size_t eig_scratch_doubles(int n_sub, int max_ns);
 
 // ---- small kernels -------------------------------------------------------------------------

@@ -228,9 +228,15 @@ def test_tma_stencil_matches_oracle_and_generic(wname, monkeypatch):
         assert relerr(outs["tma"][a], outs["generic"][a]) < 2e-6
 
 
-def test_eigensolver_large_block_matches_lapack():
+@pytest.mark.parametrize("eig_mode", ["cluster", "single"])
+def test_eigensolver_large_block_matches_lapack(eig_mode, monkeypatch):
     """N_s = 160 (the bench's block size): Ritz values of the GPU's own M_s, H_s against the
-    oracle's Cholesky + symmetric eigensolve of the same matrices; orthonormal rotated block."""
+    oracle's Cholesky + symmetric eigensolve of the same matrices; orthonormal rotated block.
+    Both the cluster-distributed and the one-CTA Cholesky / tridiagonalisation."""
+    if eig_mode == "single":
+        monkeypatch.setenv("XLS_EIG", "single")
+    else:
+        monkeypatch.delenv("XLS_EIG", raising=False)
     w = synth.workload(0)
     w.n_states = np.array([160])
     V = pseudo.local_potential(w)
