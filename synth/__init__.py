@@ -234,3 +234,23 @@ def veff_erf_wells(w: Workload, r_trunc: float = 8.0) -> np.ndarray:
         v = np.where(r < r_trunc, v, 0.0)
         V[np.ix_(idx[2], idx[1], idx[0])] += v
     return V - V.mean()
+
+
+def mlp_init(seed: int, layers=((32, 64), (64, 64), (64, 64), (64, 1))) -> np.ndarray:
+    """Flat parameters of the learned-start MLP (W row = input, then bias, per layer): weights
+    uniform in +-sqrt(6 / (fan_in + fan_out)) from the SplitMix64 stream, biases zero."""
+    out, off = [], 0
+    for i, o in layers:
+        a = math.sqrt(6.0 / (i + o))
+        out.append(2.0 * a * uniform_pm_half(seed, i * o, off))
+        off += i * o
+        out.append(np.zeros(o))
+    return np.concatenate(out)
+
+
+def two_species(w: Workload, substitute: list) -> Workload:
+    """Copy of w with the atoms `substitute` turned into the second species."""
+    idx = np.array(w.species_index).copy()
+    idx[list(substitute)] = 1
+    return Workload(w.name + "_2sp", w.L, w.n, w.pos, idx, [w.species[0], SPECIES_B], w.core_lo, w.core_n, w.buf,
+                    w.n_states, w.degree, w.n_passes, w.psi_seed, w.kT)
