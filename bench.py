@@ -210,11 +210,11 @@ def run_ours(args):
         xls.xls_chefsi_batch(gh, w.degree, 1)
         return xls.xls_density(gh, w.n_electrons, w.kT, rho_dev)
 
-    for _ in range(args.warmup):
+    # passes replay CUDA graphs (one per orbital block holding the input; the warm-up captures
+    # all three)
+    xls.xls_set_graphs(g.h, 1)
+    for _ in range(max(args.warmup, 3)):
         step(g.h)
-    xls.xls_set_profiling(g.h, 1)
-    kms = np.zeros(8)
-    kcnt = np.zeros(8)
     sampler = ClockSampler(local)
     sampler.start()
     barrier(ws)
@@ -223,9 +223,6 @@ def run_ours(args):
     e0.record(stream)
     for _ in range(args.steps):
         step(g.h)
-        ms, cnt = xls.xls_get_kernel_times(g.h)
-        kms += ms
-        kcnt += cnt
     e1.record(stream)
     torch.cuda.synchronize()
     barrier(ws)
@@ -233,8 +230,18 @@ def run_ours(args):
     ms_step = e0.elapsed_time(e1) / args.steps
     ms_step = allreduce_max(ms_step, ws)
     _, launches_pass = xls.xls_get_timings(g.h)
-    stage_ms, _ = xls.xls_get_timings(g.h)
     mu, eb_mixed, _ = xls.xls_density(g.h, w.n_electrons, w.kT)
+    # per-kernel-class times and the stage split from two further passes launched directly with
+    # CUDA events around every launch (outside the timed region)
+    xls.xls_set_profiling(g.h, 1)
+    kms = np.zeros(8)
+    kcnt = np.zeros(8)
+    for _ in range(2):
+        step(g.h)
+        ms, cnt = xls.xls_get_kernel_times(g.h)
+        kms += ms
+        kcnt += cnt
+    stage_ms, _ = xls.xls_get_timings(g.h)
     xls.xls_set_profiling(g.h, 0)
 
     # end to end through the C ABI with host buffers: H2D of every start block from pinned host

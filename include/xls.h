@@ -31,6 +31,7 @@ extern "C" {
 #endif
 
 typedef struct xls_grid_s* xls_grid;
+typedef struct xls_mlp_s* xls_mlp;   /* learned-start model: owns its device parameters */
 
 typedef enum {
   XLS_OK = 0,
@@ -75,9 +76,11 @@ typedef struct {
 } xls_species;
 
 /* Create a grid handle: validates the partition, allocates the blocks of every subdomain in
- * the requested precision and the subspace workspaces.  hbm_budget_bytes (0 = no limit) caps
- * the device memory the handle may allocate (XLS_ENOMEM beyond it).  cuda_stream may be NULL
- * (legacy default stream).  Sec. 5.A.2 (partition), Sec. 5.B (data kept resident in HBM). */
+ * the requested precision and the subspace workspaces.  hbm_budget_bytes (0 = no limit): when
+ * the estimated device footprint of all subdomains exceeds it, the grid runs in waves of
+ * consecutive subdomains whose footprint fits (see xls_get_waves); XLS_ENOMEM if one subdomain
+ * alone exceeds it.  cuda_stream may be NULL (legacy default stream).  Sec. 5.A.2 (partition),
+ * Sec. 5.B (data kept resident in HBM). */
 xls_status xls_grid_create(const xls_cell* cell, const xls_dc* dc, int precision,
                            size_t hbm_budget_bytes, void* cuda_stream, xls_grid* out);
 
@@ -153,6 +156,95 @@ xls_status xls_get_timings(xls_grid g, double* ms4_out, int* launches_out);
  * the grid's stream (a few microseconds of overhead per launch).  Library-specific: the
  * paper has no counterpart; it feeds roofline measurements. */
 xls_status xls_set_profiling(xls_grid g, int on);
+
+/* Parameters of the self-consistent-field iteration (Sec. 5.A.4, Sec. 5.B.3 SCF): electron count
+ * n_electrons, smearing kT (Ha), filter degree and CheFSI passes per SCF step, mixing weight beta,
+ * Kerker constant kappa (1/bohr), Pulay history (1..8) and Pulay period (a Pulay extrapolation
+ * every pulay_period-th step, preconditioned linear mixing otherwise).  Requires
+ * xls_hamiltonian_set (the atoms give the pseudocharge; the projectors stay fixed across steps)
+ * and resets the mixing history.  Device memory for the global-grid fields and the history
+ * (3 * history + 16 arrays of the global grid, FP64) is taken on the first call.
+ * Errors: XLS_EINVAL (bad values, no Hamiltonian), XLS_ENOMEM. */
+xls_status xls_scf_setup(xls_grid g, double n_electrons, double kT, int degree, int n_passes, double beta,
+                         double kappa, int history, int pulay_period);
+
+/* One SCF step (Sec. 5.A.4; Eq. poisson): from the input density rho_inout (global grid,
+ * [n_z][n_y][n_x] FP64, host pointer, or device pointer with rho_on_device = 1):
+ *   phi:   -Delta_h phi = 4 pi (rho + b) on the periodic grid, zero mean (conjugate gradients to
+ *          a relative residual of 1e-13), b the Gaussian pseudocharge of the atoms renormalised to
+ *          -sum Z with its mean removed;
+ *   V_eff = phi + v_xc[rho] (LDA: Slater exchange, Perdew-Zunger 1981 correlation), restricted to
+ *          every subdomain; new Lanczos upper bounds; n_passes CheFSI passes;
+ *   mu, rho_out, E_band, E_entropy as xls_density;
+ *   energy = E_band + E_xc[rho] - sum v_xc rho dV + 1/2 sum (b - rho) phi dV - E_self - E_entropy
+ *          (input density; E_self = 1/2 sum_I Z_I^2 sqrt(2/pi) / r_c,I);
+ *   residual = ||rho_out - rho||_2 / ||rho_out||_2;
+ *   rho_inout <- periodic Pulay mix of (rho, rho_out) with preconditioner
+ *          P = -Delta_h (-Delta_h + kappa^2)^-1 (solved by conjugate gradients).
+ * Outputs may be NULL.  Errors: XLS_EINVAL (no setup, no orbitals), XLS_ENOCONV (Fermi level or
+ * conjugate gradients), XLS_ENONFINITE, XLS_ENOTSPD, XLS_ECUDA. */
+xls_status xls_scf_step(xls_grid g, double* rho_inout, int rho_on_device, double* residual_out, double* energy_out,
+                        double* mu_out);
+
+/* Waves of the grid (Sec. 5.B.3: subdomains processed in batches that fit the node): 1 when every
+ * subdomain is resident at once, else the number of waves of consecutive subdomains admitted by
+ * the HBM budget given to xls_grid_create; first_sub_out (optional, n_sub entries suffice)
+ * receives each wave's first subdomain.  In wave mode the orbitals of all subdomains live in a
+ * pinned host store in the device format (FP32 on the mixed path, FP64 otherwise);
+ * xls_chefsi_batch runs the waves in turn (per wave: a partial grid, the projector tables and
+ * Lanczos bounds of its subdomains, orbitals up, passes, orbitals, Ritz values, weights and
+ * bounds back), xls_density finds mu from all Ritz values and weights on the device and forms
+ * rho in a second sweep over the stored orbitals.  xls_chefsi_stage, xls_hamiltonian_apply,
+ * xls_get_subspace, profiling and the SCF calls return XLS_EINVAL in wave mode.
+ * Library-specific: the paper batches subdomains per MPI rank instead. */
+xls_status xls_get_waves(xls_grid g, int* n_waves_out, int* first_sub_out);
+
+/* ---- learned SCF start (Sec. 5.A.4, SCF initialisation: superposed atomic densities plus a
+ * learned, material-specific correction).  The paper names the idea, not the model; this library
+ * fixes: per grid point 2 species x 16 radial descriptors
+ *   d_{s,k}(x) = sum_{I in s} exp(-(r_I - r_k)^2 / (2 * 0.25^2)) f_c(r_I), r_k = k * 6/15 bohr,
+ *   f_c(r) = (cos(pi r / 6) + 1) / 2 for r < 6 bohr, minimum-image r_I;
+ * a 32 -> 64 -> 64 -> 64 -> 1 MLP with tanh hidden layers and a linear output; parameters as
+ * W1 (32 x 64, row = input), b1 (64), W2 (64 x 64), b2, W3 (64 x 64), b3, w4 (64), b4 (1):
+ * 10497 values. */
+
+/* Model from host parameters (FP64 in, FP32 master copy on the device; Adam moments zero).
+ * cuda_stream may be NULL.  Errors: XLS_EINVAL (n_params != 10497), XLS_ENOMEM. */
+xls_status xls_mlp_create(const double* params, int n_params, void* cuda_stream, xls_mlp* out);
+xls_status xls_mlp_destroy(xls_mlp m);
+/* Current parameters (10497 values, FP32 master copy widened). */
+xls_status xls_mlp_get_params(xls_mlp m, double* params_out);
+/* Inference with BF16 operands (inputs, weights, hidden activations rounded to BF16) and FP32
+ * accumulation: y[p] = MLP(X[p]), X row-major [n][32] FP32.  Host or device arrays
+ * (on_device = 1: both X and y on the device).  Work arrays grow to n points. */
+xls_status xls_mlp_infer(xls_mlp m, const float* X, long long n, float* y_out, int on_device);
+/* FP32 training quantities: loss = mean_p (MLP(X[p]) - y[p])^2 and its gradient (10497 values,
+ * host; may be NULL).  Backpropagation per point, weight gradients as fixed-order batch sums. */
+xls_status xls_mlp_loss_grad(xls_mlp m, const float* X, const float* y, long long n, double* loss_out,
+                             double* grad_out, int on_device);
+/* One Adam step (beta1 0.9, beta2 0.999, eps 1e-8, learning rate lr) on the loss above; loss_out
+ * receives the loss before the step. */
+xls_status xls_mlp_train_step(xls_mlp m, const float* X, const float* y, long long n, double lr, double* loss_out,
+                              int on_device);
+/* Descriptors of the grid's atoms (from xls_hamiltonian_set; species indices 0 and 1) at every
+ * global grid point, [n_z n_y n_x][32] FP32 (x fastest), host or device output. */
+xls_status xls_descriptors(xls_grid g, float* X_out, int on_device);
+/* Start density rho_0 = max(rho_SAD + MLP(d), 0) renormalised to sum rho dV = n_electrons, with
+ * rho_SAD the superposed normalised Gaussians of Z_v electrons and width r_c (the species' local
+ * radius), itself renormalised to n_electrons; m = NULL gives rho_SAD alone (the fallback).
+ * Global grid FP64 [n_z][n_y][n_x], host or device. */
+xls_status xls_learned_start(xls_grid g, xls_mlp m, double n_electrons, double* rho_out, int on_device);
+
+/* Turn on (1) or off (0) CUDA-graph replay of the CheFSI pass (Sec. 5.A.3 steps (1)-(4) as one
+ * graph: filter, projection, eigensolve, rotation).  With graphs on, xls_chefsi_batch captures a
+ * pass the first time it meets a given (orbital block, degree) and replays the graph afterwards;
+ * the captured kernels read the filter bounds, coefficients and orbitals from device memory, so
+ * replays follow every change of those.  xls_hamiltonian_set and turning graphs off drop the
+ * captured graphs (after synchronising the grid's stream).  While profiling is on, passes are
+ * launched directly.  A grid created on the legacy default stream captures on a private stream
+ * and replays on the legacy stream.  Library-specific: the paper has no counterpart.
+ * Errors: XLS_EINVAL (null grid), XLS_ECUDA (capture or instantiation failed). */
+xls_status xls_set_graphs(xls_grid g, int on);
 
 /* Device time (ms) and launch count per kernel class in the last profiled pass: [0] stencil,
  * [1] nonlocal projection, [2] nonlocal back-projection, [3] Gram/projection GEMM,

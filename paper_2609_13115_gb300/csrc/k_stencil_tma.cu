@@ -3,21 +3,20 @@
 //
 //   Y_out = scale * (-1/2 Delta_h Y_in + V Y_in - c Y_in) - shift * Y_prev
 //
-// A CTA owns a tile of TY full-width rows of one vector of one subdomain and marches along z.
-// Each xy-plane of the tile, with 6 halo rows above and below and 8 halo columns left and right,
-// is brought into a ring of shared-memory slots by TMA (cp.async.bulk.tensor, three boxes: top
-// halo rows, interior rows, bottom halo rows; out-of-range boxes are zero-filled, which is the
-// Dirichlet boundary; periodic axes wrap the box coordinates instead).  A thread computes four
-// consecutive x-points of one row: the x- and y-neighbours come from the plane slot with 128-bit
-// shared loads, the z-neighbours from a register queue of 13 planes fed from the same slots.
-// The nonlocal projector terms are added by the projection / back-projection launches around
-// this one.
+// Every operand reaches shared memory by TMA (cp.async.bulk.tensor): the Y_in planes with their
+// halo, and the rows of V and Y_prev.  A producer warp keeps a ring of plane slots filled; the
+// consumer warps never meet at a block-wide barrier.  The z-direction is a register-resident
+// scatter into thirteen plane accumulators, so a plane leaves shared memory as soon as it has
+// been read once.  The nonlocal projector terms are added by the projection / back-projection
+// launches around this one.
 #include <cuda.h>
 #include <cudaTypedefs.h>
 
 #include "xls_internal.h"
 
 namespace xls {
+
+constexpr uint32_t kSuspendNs = 100000;   // suspend-time hint of the barrier waits (100 us)
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
   return static_cast<uint32_t>(__cvta_generic_to_shared(p));
@@ -35,12 +34,14 @@ __device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
   asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
 }
 
+// try_wait with a suspend-time hint: the thread sleeps until the phase completes or the hint
+// (in ns) elapses, instead of spinning on the barrier word
 __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
   uint32_t ok;
   asm volatile(
-      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n selp.u32 %0, 1, 0, p;\n}\n"
       : "=r"(ok)
-      : "r"(smem_u32(bar)), "r"(parity)
+      : "r"(smem_u32(bar)), "r"(parity), "r"(kSuspendNs)
       : "memory");
   return ok != 0;
 }
@@ -54,37 +55,57 @@ __device__ __forceinline__ void tma_load_4d(void* dst, const CUtensorMap* map, u
       : "memory");
 }
 
+__device__ __forceinline__ void tma_load_3d(void* dst, const CUtensorMap* map, uint64_t* bar, int x, int y, int z) {
+  asm volatile(
+      "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], "
+      "[%5];" ::"r"(smem_u32(dst)),
+      "l"(map), "r"(x), "r"(y), "r"(z), "r"(smem_u32(bar))
+      : "memory");
+}
+
 __device__ __forceinline__ int wrapt(int i, int n) {
   i %= n;
   return i < 0 ? i + n : i;
 }
 
-// Bounded wait on a TMA landing: on expiry the status word gets XLS_ETIMEOUT (never a trap).
-__device__ __forceinline__ bool wait_slot(uint64_t* bar, uint32_t parity) {
-  for (long long it = 0; it < (1LL << 28); ++it)
-    if (mbar_try_wait(bar, parity)) return true;
-  return false;
-}
+constexpr int kNS = 5;              // ring slots: planes in flight + the one being read
+constexpr int kHaloX = 8;           // halo columns on each side (16-byte aligned TMA x coordinate)
+constexpr int kQ = 2 * kN0 + 1;     // output planes accumulating at any time
+constexpr int kMaxThreads = 320;    // consumer threads (<= 288) + one producer warp
 
-constexpr int kSlots = 10;       // ring depth: 7 resident planes + 3 in flight
-constexpr int kHaloX = 8;        // halo columns on each side (16-byte aligned TMA x coordinate)
-
-// Stencil weights of one launch (all subdomains of a launch share the grid spacing): passed by
-// value so that the FMAs read them from the constant bank instead of registers.
+// Stencil weights of one launch (all subdomains of a launch share the grid spacing), passed by
+// value so that the FMAs read them from the constant bank.
 struct StencilW {
   float wx[kN0 + 1], wy[kN0 + 1], wz[kN0 + 1];
   float wc;
 };
 
-__global__ void __launch_bounds__(288, 2)
+// Bounded waits (iteration limit; on expiry the caller records XLS_ETIMEOUT, never a trap).
+constexpr int kSpin = 20000;   // x kSuspendNs: a wait gives up after about two seconds
+__device__ __forceinline__ bool wait_full(uint64_t* bar, uint32_t parity) {
+  for (int it = 0; it < kSpin; ++it)
+    if (mbar_try_wait(bar, parity)) return true;
+  return false;
+}
+
+// One CTA: TY full-width rows of one vector of one subdomain, marching along z.  A producer
+// warp streams, for every plane z_t, three boxes of Y_in (6 halo rows above, TY rows, 6 halo
+// rows below, 8 halo columns each side; out-of-range boxes zero-filled = Dirichlet, periodic
+// axes wrap the coordinates) plus the TY rows of V at z_t and of Y_prev at z_t - 6 into a ring
+// of kNS slots (full/empty mbarriers, no block-wide barrier).  A consumer thread owns four
+// consecutive x-points of one row: when plane z_t lands it adds the plane's x/y-stencil, centre
+// and potential terms into the accumulator of z_t and scatters w_z[p] * Y(z_t) into the
+// accumulators of z_t +- p; the output plane z_t - 6 is then complete and is written out.
+// Thirteen accumulators live in registers (the loop is unrolled by 13 so their indices are
+// static).
+template <int kW>
+__global__ void __launch_bounds__(kMaxThreads, 2)
 k_stencil_tma(const SubDev* __restrict__ subs, const TmaJob* __restrict__ jobs, const int* __restrict__ job_off,
-              int n_jobs, const CUtensorMap* __restrict__ maps, int buf_in, const float* Yprev, float* Yout,
-              const float* __restrict__ Vall, const StepCoef* __restrict__ coef, int step, int* status,
-              const StencilW sw) {
+              int n_jobs, const CUtensorMap* __restrict__ maps, int buf_in, int buf_prev, float* Yout,
+              const StepCoef* __restrict__ coef, int step, int* status, const StencilW sw) {
   extern __shared__ __align__(128) unsigned char smem_raw[];
-  __shared__ __align__(8) uint64_t bars[kSlots];
-  __shared__ int s_abort;
-  // locate the job (class-uniform launch: all jobs share W and TY)
+  __shared__ __align__(8) uint64_t full[kNS], empty[kNS];
+  __shared__ volatile int s_abort;
   const int b = blockIdx.x;
   int lo = 0, hi = n_jobs;
   while (hi - lo > 1) {
@@ -97,154 +118,185 @@ k_stencil_tma(const SubDev* __restrict__ subs, const TmaJob* __restrict__ jobs, 
   const int nyt = J.n_ytiles;
   const int vec = local / nyt, yt = local % nyt;
   const int nx = S.n[0], ny = S.n[1], nz = S.n[2];
-  const int TY = blockDim.y, W = J.W;
+  const int TY = J.TY, W = J.W, nq = nx >> 2;
+  const int n_cons = blockDim.x - 32;
   const int y0 = yt * TY;
   const int rows = TY + 2 * kN0;
+  const int off_yp = rows * W;
+  const int aux = ((TY * nx + 31) / 32) * 32;
+  const int off_v = off_yp + aux;
+  const int slot_floats = off_v + aux;
   float* ring = reinterpret_cast<float*>(smem_raw);
-  const int slot_floats = rows * W;
-  const CUtensorMap* map_tb = maps + (size_t)(J.sub * 3 + buf_in) * 2;   // 6-row boxes
-  const CUtensorMap* map_in = map_tb + 1;                                // TY-row boxes
-  const int tx = threadIdx.x, ty = threadIdx.y;
-  const int tid = ty * blockDim.x + tx;
-  const int x4 = 4 * tx;                 // first of this thread's four x-points
-  const int y = y0 + ty;
-  const bool row_ok = (y < ny);
   const bool px = S.periodic[0], py = S.periodic[1], pz = S.periodic[2];
-  const int nplanes = nz + 2 * kN0;      // planes -6 .. nz+5
-  const uint32_t slot_bytes = (uint32_t)slot_floats * 4u;
-  const int ytop = py ? wrapt(y0 - kN0, ny) : y0 - kN0;
-  const int ybot = py ? wrapt(y0 + TY, ny) : y0 + TY;
-
-  auto issue = [&](int pi) {  // plane index pi (z = pi - 6) into slot pi % kSlots
-    const int z = pi - kN0;
-    uint64_t* bar = &bars[pi % kSlots];
-    const bool in_range = pz || (z >= 0 && z < nz);
-    if (!in_range) {
-      mbar_arrive(bar);
-      return;
-    }
-    const int zz = pz ? wrapt(z, nz) : z;
-    float* dst = ring + (size_t)(pi % kSlots) * slot_floats;
-    mbar_expect_tx(bar, slot_bytes);
-    tma_load_4d(dst, map_tb, bar, -kHaloX, ytop, zz, vec);
-    tma_load_4d(dst + kN0 * W, map_in, bar, -kHaloX, y0, zz, vec);
-    tma_load_4d(dst + (kN0 + TY) * W, map_tb, bar, -kHaloX, ybot, zz, vec);
-  };
+  const int zbase = pz ? -kN0 : 0;
+  const int n_iter = nz + kN0 - zbase;  // arrivals z_t = zbase .. nz + 5
+  const bool has_prev = buf_prev >= 0;
+  const int tid = threadIdx.x;
+  const int n_cons_warps = n_cons >> 5;
 
   if (tid == 0) {
     s_abort = 0;
-    for (int s = 0; s < kSlots; ++s) mbar_init(&bars[s], 1);
+    for (int s = 0; s < kNS; ++s) {
+      mbar_init(&full[s], 1);
+      mbar_init(&empty[s], n_cons_warps);
+    }
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
   }
   __syncthreads();
-  if (tid == 0)
-    for (int pi = 0; pi < kSlots && pi < nplanes; ++pi) issue(pi);
 
-  // step coefficients
-  const float wc = sw.wc;
+  if (tid >= n_cons) {
+    // ---- producer warp ------------------------------------------------------------------
+    if (tid != n_cons) return;
+    const CUtensorMap* mb = maps + (size_t)J.sub * kMapsPerSub;
+    const CUtensorMap* m_halo = mb + buf_in * 3;
+    const CUtensorMap* m_in = m_halo + 1;
+    const CUtensorMap* m_prev = has_prev ? mb + buf_prev * 3 + 2 : nullptr;
+    const CUtensorMap* m_v = mb + 9;
+    const int ytop = py ? wrapt(y0 - kN0, ny) : y0 - kN0;
+    const int ybot = py ? wrapt(y0 + TY, ny) : y0 + TY;
+    const uint32_t in_bytes = (uint32_t)(rows * W) * 4u, aux_bytes = (uint32_t)(TY * nx) * 4u;
+    int issued = 0;
+    for (int it = 0; it < n_iter; ++it) {
+      const int slot = it % kNS;
+      if (it >= kNS) {
+        const uint32_t par = (uint32_t)(((it / kNS) - 1) & 1);
+        bool ok = false;
+        for (int k = 0; k < kSpin && !ok; ++k) {
+          ok = mbar_try_wait(&empty[slot], par);
+          if (!ok && s_abort) break;
+        }
+        if (!ok) {
+          if (atomicCAS(status, 0, XLS_ETIMEOUT) == 0) status[1] = J.sub;
+          s_abort = 1;
+          break;
+        }
+      }
+      const int zt = zbase + it;
+      const bool real = pz || zt < nz;
+      const int zo = zt - kN0;
+      const bool yp = has_prev && zo >= 0;
+      const uint32_t bytes = (real ? in_bytes + aux_bytes : 0u) + (yp ? aux_bytes : 0u);
+      uint64_t* bar = &full[slot];
+      float* dst = ring + (size_t)slot * slot_floats;
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      if (bytes == 0) {
+        mbar_arrive(bar);
+      } else {
+        mbar_expect_tx(bar, bytes);
+        if (real) {
+          const int zz = pz ? wrapt(zt, nz) : zt;
+          tma_load_4d(dst, m_halo, bar, -kHaloX, ytop, zz, vec);
+          tma_load_4d(dst + kN0 * W, m_in, bar, -kHaloX, y0, zz, vec);
+          tma_load_4d(dst + (kN0 + TY) * W, m_halo, bar, -kHaloX, ybot, zz, vec);
+          tma_load_3d(dst + off_v, m_v, bar, 0, y0, zz);
+        }
+        if (yp) tma_load_4d(dst + off_yp, m_prev, bar, 0, y0, zo, vec);
+      }
+      ++issued;
+    }
+    // no copy may still be landing when the CTA exits
+    for (int it = issued - kNS < 0 ? 0 : issued - kNS; it < issued; ++it)
+      wait_full(&full[it % kNS], (uint32_t)((it / kNS) & 1));
+    return;
+  }
+
+  // ---- consumers ----------------------------------------------------------------------------
+  const int lane = tid & 31;
+  const bool active = tid < nq * TY;
+  const int tx = active ? tid % nq : 0, ty = active ? tid / nq : 0;
+  const int x4 = 4 * tx;
+  const int y = y0 + ty;
+  const bool store_ok = active && y < ny;
   const StepCoef cf = coef[J.sub * kMaxDegree + step];
   const float scale = (float)cf.scale, cshift = (float)cf.c, pshift = (float)cf.shift;
-  const long long plane_sz = (long long)nx * ny;
-  const long long base = S.off_blk + (long long)vec * S.nd;
-  const float* V = Vall + S.off_pt;
-  const bool active = (x4 < nx);
+  const int plane_sz = nx * ny;
+  float* outp = Yout + S.off_blk + (long long)vec * S.nd + (long long)y * nx + x4;   // advances one plane per output
+  const int rc = (ty + kN0) * W + kHaloX + x4;   // this thread's centre in an input slot
+  const int ra = ty * nx + x4;                    // ... and in the V / Y_prev boxes
+  // x-neighbour chunks q = 0..4 cover columns x4 - 8 + 4q .. +3 (wholly inside [0, n_x) or wholly
+  // outside, as n_x and x4 are multiples of 4); along a periodic x axis the outside chunks read
+  // the wrapped columns of the same row: offsets of chunks 0, 1 (left) and 3, 4 (right)
+  const int wl0 = (px && x4 < 8) ? nx : 0, wl1 = (px && x4 < 4) ? nx : 0;
+  const int wr3 = (px && x4 + 4 >= nx) ? -nx : 0, wr4 = (px && x4 + 8 >= nx) ? -nx : 0;
+  const int Wr = kW ? kW : W;   // row pitch of a slot (compile-time where specialised)
 
-  float4 q[2 * kN0 + 1];
+  float acc[kQ][4];
 #pragma unroll
-  for (int k = 0; k < 2 * kN0 + 1; ++k) q[k] = make_float4(0.f, 0.f, 0.f, 0.f);
-  // V and Y_prev of the next output plane are loaded one iteration ahead (their HBM latency
-  // then overlaps a plane of work)
-  const bool io = active && row_ok;
-  auto ld_v = [&](int zo_) -> float4 {
-    return (io && zo_ < nz) ? *reinterpret_cast<const float4*>(V + (long long)zo_ * plane_sz + (long long)y * nx + x4)
-                            : make_float4(0.f, 0.f, 0.f, 0.f);
-  };
-  auto ld_p = [&](int zo_) -> float4 {
-    return (io && Yprev && zo_ < nz)
-               ? *reinterpret_cast<const float4*>(Yprev + base + (long long)zo_ * plane_sz + (long long)y * nx + x4)
-               : make_float4(0.f, 0.f, 0.f, 0.f);
-  };
-  float4 v_next = ld_v(0), p_next = ld_p(0);
+  for (int k = 0; k < kQ; ++k) acc[k][0] = acc[k][1] = acc[k][2] = acc[k][3] = 0.f;
 
-  for (int pi = 0; pi < nplanes; ++pi) {
-    const int slot = pi % kSlots;
-    const uint32_t parity = (uint32_t)((pi / kSlots) & 1);
-    const bool ok = wait_slot(&bars[slot], parity);
-    if (!ok) s_abort = 1;
-    const float* P = ring + (size_t)slot * slot_floats;
-    const int z = pi - kN0;
-    const bool plane_loaded = pz || (z >= 0 && z < nz);
-    // push this plane's values of the thread's four columns into the z-queue
+  int slot = 0;
+  uint32_t par = 0;
+  const float* P = ring;
+  for (int k0 = 0; k0 < n_iter; k0 += kQ) {
 #pragma unroll
-    for (int k = 0; k < 2 * kN0; ++k) q[k] = q[k + 1];
-    q[2 * kN0] = (ok && plane_loaded && active) ? *reinterpret_cast<const float4*>(P + (ty + kN0) * W + kHaloX + x4)
-                                                : make_float4(0.f, 0.f, 0.f, 0.f);
-    const int zo = pi - 2 * kN0;  // output plane whose z-window is now complete
-    if (ok && zo >= 0 && active && row_ok) {
-      const float* C = ring + (size_t)((pi - kN0) % kSlots) * slot_floats;  // slot of plane zo
-      const float* rowp = C + (ty + kN0) * W;
-      // x-neighbours: columns x4-6 .. x4+9 of the halo-shifted row (aligned float4 window);
-      // along a periodic x axis the edge threads read the wrapped columns of the same row
-      float xr[20];
-#pragma unroll
-      for (int j = 0; j < 5; ++j) {
-        // chunk j covers x = x4 - 8 + 4j .. +3: wholly inside [0, nx) or wholly outside
-        // (n_x and x4 are multiples of 4); outside chunks of a periodic axis wrap
-        int xs = x4 - kHaloX + 4 * j;
-        if (px) xs = xs < 0 ? xs + nx : (xs >= nx ? xs - nx : xs);
-        const int col = xs + kHaloX;
-        const float4 v4 = *reinterpret_cast<const float4*>(rowp + col);
-        xr[4 * j] = v4.x; xr[4 * j + 1] = v4.y; xr[4 * j + 2] = v4.z; xr[4 * j + 3] = v4.w;
+    for (int j = 0; j < kQ; ++j) {
+      const int it = k0 + j;
+      if (it >= n_iter) break;
+      if (!wait_full(&full[slot], par)) {
+        if (atomicCAS(status, 0, XLS_ETIMEOUT) == 0) status[1] = J.sub;
+        s_abort = 1;
+        return;
       }
-      // element r of the thread's points sits at xr[kHaloX + r]
-      float acc[4];
-      const float4 c4 = q[kN0];
-      const float cv[4] = {c4.x, c4.y, c4.z, c4.w};
+      const int zt = zbase + it;
+      const int zo = zt - kN0;
+      float4 yp = make_float4(0.f, 0.f, 0.f, 0.f);
+      if ((pz || zt < nz) && active) {
+        const float* C = P + rc;
+        float xr[20];
 #pragma unroll
-      for (int r = 0; r < 4; ++r) acc[r] = wc * cv[r];
+        for (int q = 0; q < 5; ++q) {
+          const int wo = q == 0 ? wl0 : (q == 1 ? wl1 : (q == 3 ? wr3 : (q == 4 ? wr4 : 0)));
+          const float4 v4 = *reinterpret_cast<const float4*>(C + (4 * q - kHaloX) + wo);
+          xr[4 * q] = v4.x; xr[4 * q + 1] = v4.y; xr[4 * q + 2] = v4.z; xr[4 * q + 3] = v4.w;
+        }
+        const float4 v = *reinterpret_cast<const float4*>(P + off_v + ra);
+          const float c[4] = {xr[8], xr[9], xr[10], xr[11]};
+          const float vv[4] = {v.x, v.y, v.z, v.w};
+          float t[4];
 #pragma unroll
-      for (int p = 1; p <= kN0; ++p) {
+          for (int r = 0; r < 4; ++r) t[r] = fmaf(vv[r] - cshift, c[r], sw.wc * c[r]);
 #pragma unroll
-        for (int r = 0; r < 4; ++r) acc[r] += sw.wx[p] * (xr[kHaloX + r + p] + xr[kHaloX + r - p]);
-        const float4 up = *reinterpret_cast<const float4*>(C + (ty + kN0 + p) * W + kHaloX + x4);
-        const float4 dn = *reinterpret_cast<const float4*>(C + (ty + kN0 - p) * W + kHaloX + x4);
-        acc[0] += sw.wy[p] * (up.x + dn.x);
-        acc[1] += sw.wy[p] * (up.y + dn.y);
-        acc[2] += sw.wy[p] * (up.z + dn.z);
-        acc[3] += sw.wy[p] * (up.w + dn.w);
-        const float4 zu = q[kN0 + p], zd = q[kN0 - p];
-        acc[0] += sw.wz[p] * (zu.x + zd.x);
-        acc[1] += sw.wz[p] * (zu.y + zd.y);
-        acc[2] += sw.wz[p] * (zu.z + zd.z);
-        acc[3] += sw.wz[p] * (zu.w + zd.w);
+          for (int p = 1; p <= kN0; ++p) {
+#pragma unroll
+            for (int r = 0; r < 4; ++r) t[r] += sw.wx[p] * (xr[8 + r + p] + xr[8 + r - p]);
+            const float4 up = *reinterpret_cast<const float4*>(C + p * Wr);
+            const float4 dn = *reinterpret_cast<const float4*>(C - p * Wr);
+            t[0] += sw.wy[p] * (up.x + dn.x);
+            t[1] += sw.wy[p] * (up.y + dn.y);
+            t[2] += sw.wy[p] * (up.z + dn.z);
+            t[3] += sw.wy[p] * (up.w + dn.w);
+          }
+#pragma unroll
+          for (int r = 0; r < 4; ++r) acc[j][r] += t[r];
+#pragma unroll
+          for (int p = 1; p <= kN0; ++p) {
+            const int u = (j + p) % kQ, d = (j + kQ - p) % kQ;
+#pragma unroll
+            for (int r = 0; r < 4; ++r) {
+              acc[u][r] = fmaf(sw.wz[p], c[r], acc[u][r]);
+              acc[d][r] = fmaf(sw.wz[p], c[r], acc[d][r]);
+            }
+          }
       }
-      const long long g = (long long)zo * plane_sz + (long long)y * nx + x4;
-      const float4 v4 = v_next, pv = p_next;
-      v_next = ld_v(zo + 1);
-      p_next = ld_p(zo + 1);
-      const float vv[4] = {v4.x, v4.y, v4.z, v4.w};
-      float o[4];
-#pragma unroll
-      for (int r = 0; r < 4; ++r) o[r] = scale * (acc[r] + vv[r] * cv[r] - cshift * cv[r]);
-      o[0] -= pshift * pv.x;
-      o[1] -= pshift * pv.y;
-      o[2] -= pshift * pv.z;
-      o[3] -= pshift * pv.w;
-      *reinterpret_cast<float4*>(Yout + base + g) = make_float4(o[0], o[1], o[2], o[3]);
-    }
-    __syncthreads();  // every thread is done with plane index pi - 6 (x/y of output zo)
-    if (s_abort) {    // a plane never landed: record it and leave (uniform: read after the barrier)
-      if (tid == 0) atomicCAS(status, 0, XLS_ETIMEOUT);
-      return;
-    }
-    const int rel = pi - kN0;
-    if (tid == 0 && rel >= 0) {
-      const int nxt = rel + kSlots;  // reuses the slot of plane index rel
-      if (nxt < nplanes) {
-        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-        issue(nxt);
+      if (has_prev && zo >= 0 && active) yp = *reinterpret_cast<const float4*>(P + off_yp + ra);
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&empty[slot]);
+      if (++slot == kNS) {
+        slot = 0;
+        par ^= 1u;
+        P = ring;
+      } else {
+        P += slot_floats;
       }
+      // output plane z_t - 6 is complete
+      const int f = (j + kQ - kN0) % kQ;
+      if (zo >= 0 && store_ok) {
+        *reinterpret_cast<float4*>(outp) =
+            make_float4(fmaf(-pshift, yp.x, scale * acc[f][0]), fmaf(-pshift, yp.y, scale * acc[f][1]),
+                        fmaf(-pshift, yp.z, scale * acc[f][2]), fmaf(-pshift, yp.w, scale * acc[f][3]));
+      }
+      if (zo >= 0) outp += plane_sz;
+      acc[f][0] = acc[f][1] = acc[f][2] = acc[f][3] = 0.f;
     }
   }
 }
@@ -263,58 +315,77 @@ static PFN_cuTensorMapEncodeTiled_v12000 get_encode() {
 }
 
 int tma_tile_rows(const SubDev& S) {
-  // rows per tile: 16, or a divisor of n_y along a periodic y axis (the wrapped halo boxes
-  // then start exactly at the tile edges)
-  if (!S.periodic[1]) return 16;
-  for (int ty : {16, 12, 8, 24, 6})
-    if (S.n[1] % ty == 0) return ty;
+  // rows per tile: the largest candidate with at most 288 consumer threads (x-points / 4 per
+  // row) that, along a periodic y axis, divides n_y (the wrapped halo boxes then start exactly
+  // at the tile edges)
+  const int nq = S.n[0] / 4;
+  for (int ty : {24, 16, 12, 8, 6})
+    if (nq * ty <= kMaxThreads - 32 && (!S.periodic[1] || S.n[1] % ty == 0)) return ty;
   return 0;
-}
-
-bool tma_eligible(const SubDev& S) {
-  const int W = ((S.n[0] + 2 * kHaloX + 31) / 32) * 32;
-  const int ty = tma_tile_rows(S);
-  if (S.n[0] % 4 != 0 || W > 256 || ty == 0 || S.n[0] / 4 * ty > 1024) return false;
-  const size_t smem = (size_t)kSlots * (ty + 2 * kN0) * W * 4;
-  return smem <= 200 * 1024;
 }
 
 int tma_row_width(const SubDev& S) { return ((S.n[0] + 2 * kHaloX + 31) / 32) * 32; }
 
-// out[buf * 2 + {0: 6-row box, 1: TY-row box}] for one subdomain; the device array holds the
-// maps of subdomain `sub` at [(sub * 3 + buf) * 2 + k]
-bool build_tma_maps(const SubDev& S, int sub, void* const bufs[3], CUtensorMap* out) {
-  (void)sub;
+size_t tma_smem_bytes(int TY, int W, int nx) {
+  const size_t aux = ((size_t)(TY * nx) + 31) / 32 * 32;
+  return (size_t)kNS * ((size_t)(TY + 2 * kN0) * W + 2 * aux) * 4;
+}
+
+bool tma_eligible(const SubDev& S) {
+  const int W = tma_row_width(S);
+  const int ty = tma_tile_rows(S);
+  if (S.n[0] % 4 != 0 || W > 256 || ty == 0) return false;
+  return tma_smem_bytes(ty, W, S.n[0]) <= 200 * 1024;
+}
+
+// Maps of one subdomain, kMapsPerSub of them: for each of the three blocks, [halo box (6 rows x
+// W), interior box (TY rows x W), auxiliary box (TY rows x n_x)], then the potential's box
+// (TY rows x n_x of the FP32 V).
+bool build_tma_maps(const SubDev& S, const float* Vf, void* const bufs[3], CUtensorMap* out) {
   auto enc = get_encode();
   if (!enc) return false;
   const int W = tma_row_width(S), TY = tma_tile_rows(S);
+  cuuint32_t estr[4] = {1, 1, 1, 1};
   for (int bi = 0; bi < 3; ++bi) {
     const float* basep = (const float*)bufs[bi] + S.off_blk;
     cuuint64_t dims[4] = {(cuuint64_t)S.n[0], (cuuint64_t)S.n[1], (cuuint64_t)S.n[2], (cuuint64_t)S.ns};
     cuuint64_t strides[3] = {(cuuint64_t)S.n[0] * 4, (cuuint64_t)S.n[0] * S.n[1] * 4, (cuuint64_t)S.nd * 4};
-    cuuint32_t estr[4] = {1, 1, 1, 1};
-    for (int k = 0; k < 2; ++k) {
-      cuuint32_t box[4] = {(cuuint32_t)W, (cuuint32_t)(k == 0 ? kN0 : TY), 1, 1};
-      CUresult r = enc(&out[(size_t)bi * 2 + k], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, (void*)basep, dims,
+    for (int k = 0; k < 3; ++k) {
+      cuuint32_t box[4] = {(cuuint32_t)(k == 2 ? S.n[0] : W), (cuuint32_t)(k == 0 ? kN0 : TY), 1, 1};
+      CUresult r = enc(&out[(size_t)bi * 3 + k], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, (void*)basep, dims,
                        strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
                        CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
       if (r != CUDA_SUCCESS) return false;
     }
   }
-  return true;
+  cuuint64_t dims[3] = {(cuuint64_t)S.n[0], (cuuint64_t)S.n[1], (cuuint64_t)S.n[2]};
+  cuuint64_t strides[2] = {(cuuint64_t)S.n[0] * 4, (cuuint64_t)S.n[0] * S.n[1] * 4};
+  cuuint32_t box[3] = {(cuuint32_t)S.n[0], (cuuint32_t)TY, 1};
+  CUresult r = enc(&out[9], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, (void*)(Vf + S.off_pt), dims, strides, box, estr,
+                   CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                   CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS;
+}
+
+template <int kW>
+static void launch_variant(const TmaClass& cls, size_t smem, const SubDev* d_subs, const CUtensorMap* d_maps,
+                           int buf_in, int buf_prev, float* Yout, const StepCoef* coef, int step, int* status,
+                           const StencilW& sw, cudaStream_t st) {
+  static bool attr = false;
+  if (!attr) {
+    cudaFuncSetAttribute(k_stencil_tma<kW>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    cudaFuncSetAttribute(k_stencil_tma<kW>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+    attr = true;
+  }
+  const int threads = ((cls.nq * cls.TY + 31) / 32) * 32 + 32;
+  k_stencil_tma<kW><<<cls.total, threads, smem, st>>>(d_subs, cls.d_jobs, cls.d_job_off, cls.n_jobs, d_maps, buf_in,
+                                                      buf_prev, Yout, coef, step, status, sw);
 }
 
 void launch_stencil_tma(const SubDev* d_subs, const TmaClass& cls, const CUtensorMap* d_maps, int buf_in,
-                        const float* Yprev, float* Yout, const float* V, const StepCoef* coef, int step, int* status,
-                        cudaStream_t st) {
+                        int buf_prev, float* Yout, const StepCoef* coef, int step, int* status, cudaStream_t st) {
   if (cls.total == 0) return;
-  const size_t smem = (size_t)kSlots * (cls.TY + 2 * kN0) * cls.W * 4;
-  static bool attr = false;
-  if (!attr) {
-    cudaFuncSetAttribute(k_stencil_tma, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-    cudaFuncSetAttribute(k_stencil_tma, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
-    attr = true;
-  }
+  const size_t smem = tma_smem_bytes(cls.TY, cls.W, cls.nq * 4);
   StencilW sw;
   const float ihx = (float)(-0.5 / (cls.h[0] * cls.h[0])), ihy = (float)(-0.5 / (cls.h[1] * cls.h[1])),
               ihz = (float)(-0.5 / (cls.h[2] * cls.h[2]));
@@ -326,9 +397,12 @@ void launch_stencil_tma(const SubDev* d_subs, const TmaClass& cls, const CUtenso
     sw.wz[p] = (float)fdw[p] * ihz;
   }
   sw.wc = sw.wx[0] + sw.wy[0] + sw.wz[0];
-  dim3 block(cls.nq, cls.TY);
-  k_stencil_tma<<<cls.total, block, smem, st>>>(d_subs, cls.d_jobs, cls.d_job_off, cls.n_jobs, d_maps, buf_in, Yprev,
-                                                Yout, V, coef, step, status, sw);
+  // row pitches of the common subdomain widths as compile-time constants (immediate offsets)
+  switch (cls.W) {
+    case 64: launch_variant<64>(cls, smem, d_subs, d_maps, buf_in, buf_prev, Yout, coef, step, status, sw, st); break;
+    case 96: launch_variant<96>(cls, smem, d_subs, d_maps, buf_in, buf_prev, Yout, coef, step, status, sw, st); break;
+    default: launch_variant<0>(cls, smem, d_subs, d_maps, buf_in, buf_prev, Yout, coef, step, status, sw, st);
+  }
 }
 
 }  // namespace xls

@@ -69,6 +69,43 @@ struct xls_grid_s {
   double* out4 = nullptr;
   double* rho = nullptr;
   double* Vg = nullptr;
+  // wave mode (HBM budget below the whole footprint): waves of consecutive subdomains run on
+  // partial grids; the orbitals of every subdomain live in a pinned host store (device format)
+  bool wave = false;
+  xls_cell cell{};
+  std::vector<std::pair<int, int>> waves;   // (first subdomain, count)
+  std::vector<int> dc_core_lo, dc_core_n, dc_buf, dc_ns;
+  void* store = nullptr;
+  std::vector<double> host_bounds;
+  double wave_stage_ms[4] = {0, 0, 0, 0};
+  // geometry of the last xls_hamiltonian_set (for the pseudocharge of the SCF step)
+  std::vector<double> atom_pos;
+  std::vector<int> atom_sp;
+  std::vector<xls_species> species;
+  // learned start: descriptors, correction, SAD and their atom tables
+  float* ls_X = nullptr;
+  float* ls_y = nullptr;
+  float4* ls_atoms = nullptr;
+  double *ls_sad = nullptr, *ls_g1 = nullptr, *ls_pos = nullptr, *ls_rc = nullptr, *ls_amp = nullptr;
+  double *ls_partial = nullptr, *ls_s = nullptr;
+  int ls_na = -1;
+  // SCF (global periodic grid)
+  struct Scf {
+    bool ready = false, pc_ready = false;
+    double ne = 0, kT = 0, beta = 0.3, kappa = 0.5;
+    int degree = 20, passes = 1, hist = 7, period = 2, k = 0;
+    SubDev gs{};
+    SubDev* d_gs = nullptr;
+    Plan plan;
+    StepCoef* d_coef = nullptr;
+    double *b = nullptr, *phi = nullptr, *eps = nullptr, *vxc = nullptr, *rho_in = nullptr, *rho_out = nullptr;
+    double *zero = nullptr, *r = nullptr, *p = nullptr, *q = nullptr, *tmp = nullptr, *f = nullptr, *pf = nullptr;
+    double *x_prev = nullptr, *f_prev = nullptr, *pf_prev = nullptr, *dX = nullptr, *dF = nullptr, *dPF = nullptr;
+    double *partial = nullptr, *pulay_partial = nullptr, *scal = nullptr, *gamma = nullptr, *g1 = nullptr;
+    double *d_pos = nullptr, *d_rc = nullptr, *d_amp = nullptr;
+    double e_self = 0, z_total = 0;
+    int cg_iters = 0;
+  } scf;
   // TMA stencil (mixed path): classes of equal tile shape and the tensor maps of every
   // (subdomain, block buffer, box height)
   bool use_tma = false;
@@ -103,6 +140,18 @@ struct xls_grid_s {
   int launches = 0;
   // optional per-kernel-class timing: event pairs around every launch of the pass
   bool profiling = false;
+  // CUDA graphs of one pass, keyed by (block holding Psi, degree); replayed by xls_chefsi_batch
+  struct PassGraph {
+    int cur, degree, cur_after, launches;
+    cudaGraphExec_t exec;
+  };
+  bool use_graphs = false;
+  std::vector<PassGraph> graphs;
+  cudaStream_t cap_st = nullptr;  // capture stream when the caller's stream is the legacy stream
+  void drop_graphs() {
+    for (auto& pg : graphs) cudaGraphExecDestroy(pg.exec);
+    graphs.clear();
+  }
   std::vector<cudaEvent_t> pev;
   std::vector<int> pcls;
   size_t pused = 0;
@@ -230,8 +279,7 @@ void h_step_main(xls_grid g, int bin, int bprev, int bout, int step) {
     {
       ProfScope ps(g, K_STENCIL);
       for (const TmaClass& c : g->tcls)
-        launch_stencil_tma(g->d_subs, c, g->d_maps, bin, (const float*)yprev, (float*)yout, g->Vf, g->coef, step,
-                           g->status, g->st);
+        launch_stencil_tma(g->d_subs, c, g->d_maps, bin, bprev, (float*)yout, g->coef, step, g->status, g->st);
     }
     { ProfScope ps(g, K_NLBACK);
       launch_nl_back_csr<T>(g->d_subs, g->n_sub, g->max_nd, g->max_ns, g->max_slots, g->d_rptr, g->d_rslot,
@@ -327,6 +375,69 @@ xls_status upload_bounds(xls_grid g, const double* bounds) {
   return XLS_OK;
 }
 
+// stage events of a pass: external event-record nodes while a graph is being captured
+void stage_event(xls_grid g, int i) {
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  cudaStreamIsCapturing(g->st, &cs);
+  if (cs == cudaStreamCaptureStatusActive) cudaEventRecordWithFlags(g->ev[i], g->st, cudaEventRecordExternal);
+  else cudaEventRecord(g->ev[i], g->st);
+}
+
+// one CheFSI pass (filter, projection, eigensolve, rotation) on the grid's stream
+template <typename T>
+void one_pass(xls_grid g, int degree, bool timed) {
+  g->launches = 0;
+  g->pused = 0;
+  if (timed) stage_event(g, 0);
+  const int f = run_filter<T>(g, degree);
+  if (timed) stage_event(g, 1);
+  projection<T>(g, f);
+  if (timed) stage_event(g, 2);
+  eigensolve(g);
+  if (timed) stage_event(g, 3);
+  rotation<T>(g, f);
+  if (timed) stage_event(g, 4);
+}
+
+// the pass as a CUDA graph: captured on first use for this (block, degree), replayed after
+template <typename T>
+xls_status graph_pass(xls_grid g, int degree) {
+  for (auto& pg : g->graphs)
+    if (pg.cur == g->cur && pg.degree == degree) {
+      XLS_CUDA(cudaGraphLaunch(pg.exec, g->st));
+      g->cur = pg.cur_after;
+      g->launches = pg.launches;
+      return XLS_OK;
+    }
+  const int cur0 = g->cur;
+  cudaStream_t user = g->st;
+  if (!user) {  // the legacy stream cannot be captured: capture on a private stream
+    if (!g->cap_st) XLS_CUDA(cudaStreamCreateWithFlags(&g->cap_st, cudaStreamNonBlocking));
+    g->st = g->cap_st;
+  }
+  cudaGraph_t graph = nullptr;
+  cudaError_t e = cudaStreamBeginCapture(g->st, cudaStreamCaptureModeRelaxed);
+  if (e == cudaSuccess) {
+    one_pass<T>(g, degree, true);
+    e = cudaStreamEndCapture(g->st, &graph);
+  }
+  g->st = user;
+  if (e != cudaSuccess) {
+    g->cur = cur0;
+    return fail(XLS_ECUDA, std::string("pass graph capture: ") + cudaGetErrorString(e));
+  }
+  cudaGraphExec_t exec = nullptr;
+  e = cudaGraphInstantiate(&exec, graph, 0);
+  cudaGraphDestroy(graph);
+  if (e != cudaSuccess) {
+    g->cur = cur0;
+    return fail(XLS_ECUDA, std::string("pass graph instantiation: ") + cudaGetErrorString(e));
+  }
+  g->graphs.push_back({cur0, degree, g->cur, g->launches, exec});
+  XLS_CUDA(cudaGraphLaunch(exec, g->st));
+  return XLS_OK;
+}
+
 template <typename T>
 xls_status chefsi(xls_grid g, int degree, int n_passes, const double* bounds) {
   if (bounds) {
@@ -335,18 +446,8 @@ xls_status chefsi(xls_grid g, int degree, int n_passes, const double* bounds) {
     XLS_TRY(bootstrap_bounds<T>(g));
   }
   for (int p = 0; p < n_passes; ++p) {
-    const bool last = (p == n_passes - 1);
-    g->launches = 0;
-    g->pused = 0;
-    if (last) cudaEventRecord(g->ev[0], g->st);
-    const int f = run_filter<T>(g, degree);
-    if (last) cudaEventRecord(g->ev[1], g->st);
-    projection<T>(g, f);
-    if (last) cudaEventRecord(g->ev[2], g->st);
-    eigensolve(g);
-    if (last) cudaEventRecord(g->ev[3], g->st);
-    rotation<T>(g, f);
-    if (last) cudaEventRecord(g->ev[4], g->st);
+    if (g->use_graphs && !g->profiling) XLS_TRY(graph_pass<T>(g, degree));
+    else one_pass<T>(g, degree, p == n_passes - 1);
   }
   g->have_ritz = true;
   g->last_launches = g->launches;
@@ -446,18 +547,145 @@ void atom_images(xls_grid g, int a, const double R[3], const xls_species& sp, in
 
 }  // namespace
 
+// ---- SCF step on the global periodic grid ------------------------------------------------------
+xls_status scf_alloc(xls_grid g) {
+  auto& S = g->scf;
+  const long long n = (long long)g->gn[0] * g->gn[1] * g->gn[2];
+  SubDev& G = S.gs;
+  G = SubDev{};
+  for (int d = 0; d < 3; ++d) {
+    G.n[d] = g->gn[d];
+    G.periodic[d] = 1;
+    G.core_n[d] = g->gn[d];
+    G.h[d] = g->gh[d];
+  }
+  G.ns = 1;
+  G.nd = n;
+  G.dV = g->gh[0] * g->gh[1] * g->gh[2];
+  XLS_TRY(g->alloc(&S.d_gs, sizeof(SubDev)));
+  XLS_CUDA(cudaMemcpy(S.d_gs, &G, sizeof(SubDev), cudaMemcpyHostToDevice));
+  XLS_TRY(make_plan(g, std::vector<SubDev>{G}, S.plan));
+  XLS_TRY(g->alloc(&S.d_coef, kMaxDegree * sizeof(StepCoef)));
+  double** bufs[] = {&S.b, &S.phi, &S.eps, &S.vxc, &S.rho_in, &S.rho_out, &S.zero, &S.r, &S.p,
+                     &S.q, &S.tmp, &S.f, &S.pf, &S.x_prev, &S.f_prev, &S.pf_prev};
+  for (double** b : bufs) XLS_TRY(g->alloc(b, n * sizeof(double)));
+  XLS_CUDA(cudaMemsetAsync(S.zero, 0, n * sizeof(double), g->st));
+  XLS_CUDA(cudaMemsetAsync(S.phi, 0, n * sizeof(double), g->st));
+  XLS_TRY(g->alloc(&S.dX, (size_t)S.hist * n * sizeof(double)));
+  XLS_TRY(g->alloc(&S.dF, (size_t)S.hist * n * sizeof(double)));
+  XLS_TRY(g->alloc(&S.dPF, (size_t)S.hist * n * sizeof(double)));
+  XLS_TRY(g->alloc(&S.partial, kRedPartials * sizeof(double)));
+  XLS_TRY(g->alloc(&S.pulay_partial, pulay_partial_doubles() * sizeof(double)));
+  XLS_TRY(g->alloc(&S.scal, 16 * sizeof(double)));
+  XLS_TRY(g->alloc(&S.gamma, 16 * sizeof(double)));
+  return XLS_OK;
+}
+
+// the stencil's step coefficients on the global grid: step 0: -Delta_h, step 1: -Delta_h + kappa^2
+xls_status scf_coefficients(xls_grid g) {
+  std::vector<StepCoef> c(kMaxDegree, StepCoef{0, 0, 0, 0});
+  c[0] = StepCoef{2.0, 0.0, 0.0, 0.0};
+  c[1] = StepCoef{2.0, -0.5 * g->scf.kappa * g->scf.kappa, 0.0, 0.0};
+  XLS_CUDA(cudaMemcpy(g->scf.d_coef, c.data(), c.size() * sizeof(StepCoef), cudaMemcpyHostToDevice));
+  return XLS_OK;
+}
+
+void scf_apply(xls_grid g, int which, const double* x, double* y) {
+  launch_stencil<double>(g->scf.d_gs, 1, g->scf.plan, x, nullptr, y, g->scf.zero, g->scf.d_coef, which, g->st);
+}
+
+// conjugate gradients for A x = rhs (A = -Delta_h (which 0, rhs of zero mean) or -Delta_h + kappa^2
+// (which 1)), x holds the start and receives the solution; stops at
+// ||r||^2 <= tol^2 max(||rhs||^2, ref_sq) (ref_sq: the scale of the terms that formed rhs, for
+// right-hand sides that cancel to rounding)
+xls_status scf_cg(xls_grid g, int which, const double* rhs, double* x, double tol, int max_iter, double ref_sq = 0.0) {
+  auto& S = g->scf;
+  const long long n = S.gs.nd;
+  double* s = S.scal;  // s[0] r.r, s[1] p.Ap, s[2] new r.r, s[3] rhs.rhs
+  scf_apply(g, which, x, S.q);
+  launch_axpbypcz(n, 1.0, rhs, 0.0, S.r, -1.0, S.q, g->st);
+  XLS_CUDA(cudaMemcpyAsync(S.p, S.r, n * sizeof(double), cudaMemcpyDeviceToDevice, g->st));
+  {
+    const double* xs[2] = {S.r, rhs};
+    const double* ys[2] = {S.r, rhs};
+    launch_dots(n, xs, ys, 2, S.partial, s + 4, 1.0, g->st);   // s[4] = r.r, s[5] = rhs.rhs
+    XLS_CUDA(cudaMemcpyAsync(s, s + 4, sizeof(double), cudaMemcpyDeviceToDevice, g->st));
+    XLS_CUDA(cudaMemcpyAsync(s + 3, s + 5, sizeof(double), cudaMemcpyDeviceToDevice, g->st));
+  }
+  double h[4];
+  XLS_CUDA(cudaMemcpyAsync(h, s, 4 * sizeof(double), cudaMemcpyDeviceToHost, g->st));
+  XLS_CUDA(cudaStreamSynchronize(g->st));
+  const double stop = tol * tol * std::max(h[3], ref_sq);
+  if (h[0] <= stop) return XLS_OK;
+  for (int it = 1; it <= max_iter; ++it) {
+    scf_apply(g, which, S.p, S.q);
+    const double* xs[1] = {S.p};
+    const double* ys[1] = {S.q};
+    launch_dots(n, xs, ys, 1, S.partial, s + 1, 1.0, g->st);
+    launch_cg_xr(n, s, x, S.r, S.p, S.q, S.partial, g->st);
+    launch_cg_p(n, s, S.r, S.p, g->st);
+    S.cg_iters++;
+    if (it % 16 == 0 || it == max_iter) {
+      XLS_CUDA(cudaMemcpyAsync(h, s, sizeof(double), cudaMemcpyDeviceToHost, g->st));
+      XLS_CUDA(cudaStreamSynchronize(g->st));
+      if (!std::isfinite(h[0])) return fail(XLS_ENONFINITE, "SCF: conjugate gradients produced a non-finite residual");
+      if (h[0] <= stop) return XLS_OK;
+    }
+  }
+  return fail(XLS_ENOCONV, "SCF: conjugate gradients did not reach the tolerance");
+}
+
+// P f = -Delta_h (-Delta_h + kappa^2)^-1 f
+xls_status scf_kerker(xls_grid g, const double* f, double* out) {
+  auto& S = g->scf;
+  XLS_CUDA(cudaMemsetAsync(S.tmp, 0, S.gs.nd * sizeof(double), g->st));
+  XLS_TRY(scf_cg(g, 1, f, S.tmp, 1e-13, 4000));
+  scf_apply(g, 0, S.tmp, out);
+  return XLS_OK;
+}
+
+xls_status scf_pseudocharge(xls_grid g) {
+  auto& S = g->scf;
+  const int na = (int)g->atom_sp.size();
+  if (na == 0) return fail(XLS_EINVAL, "SCF: the Hamiltonian has no atoms");
+  std::vector<double> rc(na), amp(na);
+  S.z_total = 0.0;
+  S.e_self = 0.0;
+  for (int i = 0; i < na; ++i) {
+    const xls_species& q = g->species[g->atom_sp[i]];
+    rc[i] = q.rc_loc;
+    amp[i] = -q.Zv * std::pow(M_PI, -1.5) / (q.rc_loc * q.rc_loc * q.rc_loc);
+    S.z_total += q.Zv;
+    S.e_self += 0.5 * q.Zv * q.Zv * std::sqrt(2.0 / M_PI) / q.rc_loc;   // 1/2 int b_I V_I
+  }
+  if (!S.d_pos) {
+    XLS_TRY(g->alloc(&S.d_pos, 3 * (size_t)na * sizeof(double)));
+    XLS_TRY(g->alloc(&S.d_rc, (size_t)na * sizeof(double)));
+    XLS_TRY(g->alloc(&S.d_amp, (size_t)na * sizeof(double)));
+    XLS_TRY(g->alloc(&S.g1, (size_t)na * (g->gn[0] + g->gn[1] + g->gn[2]) * sizeof(double)));
+  }
+  XLS_CUDA(cudaMemcpy(S.d_pos, g->atom_pos.data(), 3 * (size_t)na * sizeof(double), cudaMemcpyHostToDevice));
+  XLS_CUDA(cudaMemcpy(S.d_rc, rc.data(), na * sizeof(double), cudaMemcpyHostToDevice));
+  XLS_CUDA(cudaMemcpy(S.d_amp, amp.data(), na * sizeof(double), cudaMemcpyHostToDevice));
+  launch_pseudocharge(na, S.d_pos, S.d_rc, S.d_amp, g->gn, g->gh, g->gL, S.g1, S.b, S.z_total, S.partial, S.scal,
+                      g->st);
+  S.pc_ready = true;
+  return XLS_OK;
+}
+
 extern "C" {
 
 const char* xls_last_error(void) { return g_last_error.c_str(); }
 
-xls_status xls_grid_create(const xls_cell* cell, const xls_dc* dc, int precision, size_t hbm_budget_bytes,
-                           void* cuda_stream, xls_grid* out) {
-  if (!cell || !dc || !out || dc->n_sub < 1 || !dc->core_lo || !dc->core_n || !dc->buf || !dc->n_states)
-    return fail(XLS_EINVAL, "xls_grid_create: null argument or n_sub < 1");
-  if (precision != XLS_FP64 && precision != XLS_MIXED_BF16 && precision != XLS_MIXED_FP16)
-    return fail(XLS_EINVAL, "unknown precision");
-  for (int d = 0; d < 3; ++d)
-    if (cell->n[d] < 2 * kN0 + 1 || !(cell->L[d] > 0)) return fail(XLS_EINVAL, "cell: n >= 13 and L > 0 per axis");
+}  // extern "C"
+
+namespace {
+
+// The grid of a set of subdomains.  `partial` grids (one wave of a wave-mode grid) need not tile
+// the global grid; `wave` grids keep only the per-state arrays on the device (the orbitals stay
+// in a host store and the waves run on partial grids).
+xls_status create_grid(const xls_cell* cell, const xls_dc* dc, int precision, size_t hbm_budget_bytes,
+                       void* cuda_stream, xls_grid* out, bool partial, bool wave, bool dry = false) {
   xls_grid g = new xls_grid_s();
   g->prec = precision;
   g->st = (cudaStream_t)cuda_stream;
@@ -523,15 +751,51 @@ xls_status xls_grid_create(const xls_cell* cell, const xls_dc* dc, int precision
     S1.off_blk = S.off_pt;
     g->subs1.push_back(S1);
   }
-  if (covered != (long long)cell->n[0] * cell->n[1] * cell->n[2]) {
+  if (!partial && covered != (long long)cell->n[0] * cell->n[1] * cell->n[2]) {
     delete g;
     return fail(XLS_EINVAL, "cores do not tile the global grid exactly once");
+  }
+  g->cell = *cell;
+  if (dry) {  // descriptors only
+    *out = g;
+    return XLS_OK;
   }
   xls_status s = XLS_OK;
 #define ALLOC(p, n)                         \
   if ((s = g->alloc(&(p), (n))) != XLS_OK) { \
     xls_grid_destroy(g);                    \
     return s;                               \
+  }
+  if (wave) {
+    g->wave = true;
+    ALLOC(g->lam, g->tot_states * sizeof(double));
+    ALLOC(g->cw, g->tot_states * sizeof(double));
+    ALLOC(g->occ, g->tot_states * sizeof(double));
+    ALLOC(g->status, 2 * sizeof(int));
+    ALLOC(g->out4, 4 * sizeof(double));
+    ALLOC(g->d_subs, g->n_sub * sizeof(SubDev));
+    {  // descriptors of a subdomain staged alone in blk[0] (the density sweep)
+      std::vector<SubDev> staged = g->subs;
+      for (SubDev& S : staged) S.off_blk = 0;
+      cudaMemcpy(g->d_subs, staged.data(), staged.size() * sizeof(SubDev), cudaMemcpyHostToDevice);
+    }
+    long long max_blk = 0;
+    for (const SubDev& S : g->subs) max_blk = std::max(max_blk, S.nd * S.ns);
+    ALLOC(g->blk[0], max_blk * std::max<size_t>(g->elem, 8));   // staging block of one subdomain
+    cudaMemset(g->status, 0, 2 * sizeof(int));
+    cudaMemset(g->lam, 0, g->tot_states * sizeof(double));
+    cudaMemset(g->cw, 0, g->tot_states * sizeof(double));
+    for (int i = 0; i < 6; ++i) cudaEventCreate(&g->ev[i]);
+    if (cudaMallocHost(&g->store, g->tot_blk * g->elem) != cudaSuccess) {
+      cudaGetLastError();
+      g->store = nullptr;
+      xls_grid_destroy(g);
+      return fail(XLS_ENOMEM, "wave mode: pinned host store for the orbitals could not be allocated");
+    }
+    std::memset(g->store, 0, g->tot_blk * g->elem);
+    g->host_bounds.assign(3 * (size_t)g->n_sub, 0.0);
+    *out = g;
+    return XLS_OK;
   }
   for (int i = 0; i < 3; ++i) ALLOC(g->blk[i], g->tot_blk * g->elem);
   ALLOC(g->V, g->tot_pts * sizeof(double));
@@ -570,8 +834,9 @@ xls_status xls_grid_create(const xls_cell* cell, const xls_dc* dc, int precision
     bool ok = !(env && std::string(env) == "generic");
     for (const SubDev& S : g->subs) ok = ok && tma_eligible(S);
     if (ok) {
-      std::vector<CUtensorMap> maps((size_t)g->n_sub * 6);
-      for (int a = 0; a < g->n_sub && ok; ++a) ok = build_tma_maps(g->subs[a], a, g->blk, (CUtensorMap_st*)&maps[(size_t)a * 6]);
+      std::vector<CUtensorMap> maps((size_t)g->n_sub * kMapsPerSub);
+      for (int a = 0; a < g->n_sub && ok; ++a)
+        ok = build_tma_maps(g->subs[a], g->Vf, g->blk, (CUtensorMap_st*)&maps[(size_t)a * kMapsPerSub]);
       if (ok) {
         // classes of equal (x-points/4, rows per tile, row width)
         std::vector<std::vector<int>> members;
@@ -599,7 +864,7 @@ xls_status xls_grid_create(const xls_cell* cell, const xls_dc* dc, int precision
           for (int a : members[k]) {
             const SubDev& S = g->subs[a];
             const int nyt = (S.n[1] + cls[k].TY - 1) / cls[k].TY;
-            jobs.push_back(TmaJob{a, nyt, cls[k].W, 0});
+            jobs.push_back(TmaJob{a, nyt, cls[k].W, cls[k].TY});
             off.push_back(off.back() + nyt * S.ns);
           }
           cls[k].n_jobs = (int)jobs.size();
@@ -700,6 +965,226 @@ xls_status xls_grid_create(const xls_cell* cell, const xls_dc* dc, int precision
   return XLS_OK;
 }
 
+// device bytes of one subdomain on a grid (blocks, potential, subspace matrices, per-state
+// arrays, Lanczos vectors, projector tables estimated at four supports per point)
+size_t sub_footprint(const SubDev& S, size_t elem) {
+  const size_t nd = (size_t)S.nd, ns = (size_t)S.ns;
+  return 3 * nd * ns * elem + nd * 12 + 7 * ns * ns * 8 + 11 * ns * 8 + 4 * nd * 8 + nd * 4 * 104 + nd * 8;
+}
+
+
+// ---- wave mode ---------------------------------------------------------------------------------
+// copy between the current block of grid g (subdomain `sub`) and host memory, device format
+xls_status raw_orbitals(xls_grid g, int sub, void* host, bool upload) {
+  const SubDev& S = g->subs[sub];
+  char* dev = (char*)g->blk[g->cur] + (size_t)S.off_blk * g->elem;
+  const size_t bytes = (size_t)S.nd * S.ns * g->elem;
+  if (upload) XLS_CUDA(cudaMemcpyAsync(dev, host, bytes, cudaMemcpyHostToDevice, g->st));
+  else XLS_CUDA(cudaMemcpyAsync(host, dev, bytes, cudaMemcpyDeviceToHost, g->st));
+  return XLS_OK;
+}
+
+char* store_ptr(xls_grid g, int sub) { return (char*)g->store + (size_t)g->subs[sub].off_blk * g->elem; }
+
+// the partial grid of wave w with the Hamiltonian of the wave-mode grid
+xls_status wave_worker(xls_grid g, int w, xls_grid* out) {
+  const int first = g->waves[w].first, cnt = g->waves[w].second;
+  xls_dc dc{cnt, &g->dc_core_lo[3 * (size_t)first], &g->dc_core_n[3 * (size_t)first], &g->dc_buf[3 * (size_t)first],
+            &g->dc_ns[first]};
+  XLS_TRY(create_grid(&g->cell, &dc, g->prec, 0, g->st, out, true, false));
+  const int na = (int)g->atom_sp.size();
+  const xls_status s = xls_hamiltonian_set(*out, g->Vg, 1, na, na ? g->atom_pos.data() : nullptr,
+                                           na ? g->atom_sp.data() : nullptr, (int)g->species.size(),
+                                           g->species.empty() ? nullptr : g->species.data());
+  if (s != XLS_OK) {
+    xls_grid_destroy(*out);
+    *out = nullptr;
+  }
+  return s;
+}
+
+xls_status wave_hamiltonian_set(xls_grid g, const double* veff, int veff_on_device, int n_atoms, const double* pos,
+                                const int* species, int n_species, const xls_species* sp) {
+  const long long ng = (long long)g->gn[0] * g->gn[1] * g->gn[2];
+  if (!g->Vg) XLS_TRY(g->alloc(&g->Vg, ng * sizeof(double)));
+  XLS_CUDA(cudaMemcpyAsync(g->Vg, veff, ng * sizeof(double),
+                           veff_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, g->st));
+  XLS_CUDA(cudaStreamSynchronize(g->st));
+  g->atom_pos.assign(pos, pos + 3 * (size_t)n_atoms);
+  g->atom_sp.assign(species, species + n_atoms);
+  g->species.assign(sp, sp + n_species);
+  g->ham_set = true;
+  g->have_ritz = false;
+  return XLS_OK;
+}
+
+xls_status wave_orbitals_set(xls_grid g, int sub, const double* psi, int on_device) {
+  const SubDev& S = g->subs[sub];
+  const size_t n = (size_t)S.nd * S.ns;
+  std::vector<double> tmp;
+  const double* src = psi;
+  if (on_device) {
+    tmp.resize(n);
+    XLS_CUDA(cudaMemcpy(tmp.data(), psi, n * sizeof(double), cudaMemcpyDeviceToHost));
+    src = tmp.data();
+  }
+  if (g->prec == XLS_FP64) {
+    std::memcpy(store_ptr(g, sub), src, n * sizeof(double));
+  } else {
+    float* dst = (float*)store_ptr(g, sub);
+    for (size_t i = 0; i < n; ++i) dst[i] = (float)src[i];   // the rounding of the FP32 block
+  }
+  g->orb_set = true;
+  g->have_ritz = false;
+  return XLS_OK;
+}
+
+xls_status wave_orbitals_get(xls_grid g, int sub, double* out, int on_device) {
+  const SubDev& S = g->subs[sub];
+  const size_t n = (size_t)S.nd * S.ns;
+  std::vector<double> tmp;
+  if (on_device) tmp.resize(n);
+  double* dst = on_device ? tmp.data() : out;
+  if (g->prec == XLS_FP64) {
+    std::memcpy(dst, store_ptr(g, sub), n * sizeof(double));
+  } else {
+    const float* src = (const float*)store_ptr(g, sub);
+    for (size_t i = 0; i < n; ++i) dst[i] = src[i];
+  }
+  if (on_device) XLS_CUDA(cudaMemcpy(out, tmp.data(), n * sizeof(double), cudaMemcpyHostToDevice));
+  return XLS_OK;
+}
+
+xls_status wave_orbitals_random(xls_grid g, uint64_t seed) {
+  for (int a = 0; a < g->n_sub; ++a) {
+    const SubDev& S = g->subs[a];
+    const long long n = S.nd * S.ns;
+    if (g->prec == XLS_FP64) launch_splitmix_fill_f64((double*)g->blk[0], n, seed, S.off_blk, g->st);
+    else launch_splitmix_fill_f32((float*)g->blk[0], n, seed, S.off_blk, g->st);
+    XLS_CUDA(cudaMemcpyAsync(store_ptr(g, a), g->blk[0], (size_t)n * g->elem, cudaMemcpyDeviceToHost, g->st));
+  }
+  XLS_CUDA(cudaStreamSynchronize(g->st));
+  g->orb_set = true;
+  g->have_ritz = false;
+  return XLS_OK;
+}
+
+// every wave in turn: partial grid, orbitals up, passes, orbitals / Ritz values / weights /
+// bounds back, partial grid released
+xls_status wave_chefsi(xls_grid g, int degree, int n_passes, const double* bounds) {
+  for (double& t : g->wave_stage_ms) t = 0.0;
+  int launches = 0;
+  for (size_t w = 0; w < g->waves.size(); ++w) {
+    const int first = g->waves[w].first, cnt = g->waves[w].second;
+    xls_grid k = nullptr;
+    XLS_TRY(wave_worker(g, (int)w, &k));
+    xls_status s = XLS_OK;
+    for (int j = 0; j < cnt && s == XLS_OK; ++j) s = raw_orbitals(k, j, store_ptr(g, first + j), true);
+    k->orb_set = true;
+    const double* bw = bounds ? bounds + 3 * (size_t)first
+                              : (g->have_ritz ? g->host_bounds.data() + 3 * (size_t)first : nullptr);
+    if (s == XLS_OK) s = xls_chefsi_batch(k, degree, n_passes, bw);
+    if (s == XLS_OK) {
+      const SubDev& S0 = g->subs[first];
+      cudaMemcpyAsync(g->lam + S0.off_state, k->lam, k->tot_states * sizeof(double), cudaMemcpyDeviceToDevice, g->st);
+      cudaMemcpyAsync(g->cw + S0.off_state, k->cw, k->tot_states * sizeof(double), cudaMemcpyDeviceToDevice, g->st);
+      s = xls_get_bounds(k, g->host_bounds.data() + 3 * (size_t)first);
+    }
+    for (int j = 0; j < cnt && s == XLS_OK; ++j) s = raw_orbitals(k, j, store_ptr(g, first + j), false);
+    if (s == XLS_OK && cudaStreamSynchronize(g->st) != cudaSuccess) s = fail(XLS_ECUDA, "wave: synchronisation failed");
+    if (s == XLS_OK) {
+      for (int i = 0; i < 4; ++i) g->wave_stage_ms[i] += k->stage_ms[i];
+      launches += k->last_launches;
+    }
+    xls_grid_destroy(k);
+    if (s != XLS_OK) return s;
+  }
+  g->last_launches = launches;
+  g->have_ritz = true;
+  return XLS_OK;
+}
+
+xls_status wave_density(xls_grid g, double n_electrons, double kT, double* mu_out, double* rho_out, int rho_on_device,
+                        double* e_band_out, double* e_entropy_out) {
+  launch_fermi_occ(g->lam, g->cw, g->tot_states, n_electrons, kT, g->out4, g->occ, g->status, g->st);
+  XLS_TRY(check_status(g));
+  double h4[4];
+  XLS_CUDA(cudaMemcpy(h4, g->out4, sizeof(h4), cudaMemcpyDeviceToHost));
+  if (mu_out) *mu_out = h4[0];
+  if (e_band_out) *e_band_out = h4[1];
+  if (e_entropy_out) *e_entropy_out = h4[2];
+  if (!rho_out) return XLS_OK;
+  const long long ng = (long long)g->gn[0] * g->gn[1] * g->gn[2];
+  if (!g->rho) XLS_TRY(g->alloc(&g->rho, ng * sizeof(double)));
+  // second sweep: every subdomain's block staged alone; its core points of rho written
+  for (int a = 0; a < g->n_sub; ++a) {
+    const SubDev& S = g->subs[a];
+    const long long core = (long long)S.core_n[0] * S.core_n[1] * S.core_n[2];
+    XLS_CUDA(cudaMemcpyAsync(g->blk[0], store_ptr(g, a), (size_t)S.nd * S.ns * g->elem, cudaMemcpyHostToDevice, g->st));
+    if (g->prec == XLS_FP64)
+      launch_density_occ<double>(g->d_subs + a, 1, core, (const double*)g->blk[0], g->occ, g->gn, g->rho, g->st);
+    else
+      launch_density_occ<float>(g->d_subs + a, 1, core, (const float*)g->blk[0], g->occ, g->gn, g->rho, g->st);
+  }
+  XLS_CUDA(cudaMemcpyAsync(rho_out, g->rho, ng * sizeof(double),
+                           rho_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, g->st));
+  XLS_CUDA(cudaStreamSynchronize(g->st));
+  return XLS_OK;
+}
+
+xls_status not_in_wave_mode(const char* what) {
+  return fail(XLS_EINVAL, std::string(what) + ": not available on a grid running in waves (HBM budget below its footprint)");
+}
+
+}  // namespace
+
+extern "C" {
+
+xls_status xls_grid_create(const xls_cell* cell, const xls_dc* dc, int precision, size_t hbm_budget_bytes,
+                           void* cuda_stream, xls_grid* out) {
+  if (!cell || !dc || !out || dc->n_sub < 1 || !dc->core_lo || !dc->core_n || !dc->buf || !dc->n_states)
+    return fail(XLS_EINVAL, "xls_grid_create: null argument or n_sub < 1");
+  if (precision != XLS_FP64 && precision != XLS_MIXED_BF16 && precision != XLS_MIXED_FP16)
+    return fail(XLS_EINVAL, "unknown precision");
+  for (int d = 0; d < 3; ++d)
+    if (cell->n[d] < 2 * kN0 + 1 || !(cell->L[d] > 0)) return fail(XLS_EINVAL, "cell: n >= 13 and L > 0 per axis");
+  if (hbm_budget_bytes == 0) return create_grid(cell, dc, precision, 0, cuda_stream, out, false, false);
+  // HBM budget: everything at once if it fits, else waves of consecutive subdomains
+  xls_grid probe = nullptr;
+  XLS_TRY(create_grid(cell, dc, precision, 0, cuda_stream, &probe, false, false, true));
+  const size_t elem = precision == XLS_FP64 ? 8 : 4;
+  size_t total = 1 << 26, run = 0;
+  std::vector<std::pair<int, int>> waves;
+  int first = 0;
+  const size_t fixed = (size_t)1 << 26;  // per-grid plans, events and small tables
+  for (int a = 0; a < probe->n_sub; ++a) {
+    const size_t f = sub_footprint(probe->subs[a], elem);
+    total += f;
+    if (f + fixed > hbm_budget_bytes) {
+      delete probe;
+      return fail(XLS_ENOMEM, "HBM budget below the footprint of subdomain " + std::to_string(a));
+    }
+    if (run + f + fixed > hbm_budget_bytes) {
+      waves.push_back({first, a - first});
+      first = a;
+      run = 0;
+    }
+    run += f;
+  }
+  waves.push_back({first, probe->n_sub - first});
+  delete probe;   // descriptors only: nothing allocated
+  if (total <= hbm_budget_bytes) return create_grid(cell, dc, precision, hbm_budget_bytes, cuda_stream, out, false, false);
+  xls_grid g = nullptr;
+  XLS_TRY(create_grid(cell, dc, precision, hbm_budget_bytes, cuda_stream, &g, false, true));
+  g->waves = waves;
+  g->dc_core_lo.assign(dc->core_lo, dc->core_lo + 3 * (size_t)dc->n_sub);
+  g->dc_core_n.assign(dc->core_n, dc->core_n + 3 * (size_t)dc->n_sub);
+  g->dc_buf.assign(dc->buf, dc->buf + 3 * (size_t)dc->n_sub);
+  g->dc_ns.assign(dc->n_states, dc->n_states + dc->n_sub);
+  *out = g;
+  return XLS_OK;
+}
+
 xls_status xls_grid_destroy(xls_grid g) {
   if (!g) return XLS_OK;
   if (g->st) cudaStreamSynchronize(g->st);
@@ -708,6 +1193,9 @@ xls_status xls_grid_destroy(xls_grid g) {
   for (int i = 0; i < 6; ++i)
     if (g->ev[i]) cudaEventDestroy(g->ev[i]);
   for (auto& e : g->pev) cudaEventDestroy(e);
+  g->drop_graphs();
+  if (g->cap_st) cudaStreamDestroy(g->cap_st);
+  if (g->store) cudaFreeHost(g->store);
   delete g;
   return XLS_OK;
 }
@@ -718,15 +1206,24 @@ xls_status xls_hamiltonian_set(xls_grid g, const double* veff, int veff_on_devic
     return fail(XLS_EINVAL, "xls_hamiltonian_set: bad arguments");
   for (int i = 0; i < n_atoms; ++i)
     if (species[i] < 0 || species[i] >= n_species) return fail(XLS_EINVAL, "species index out of range");
+  if (!g->graphs.empty()) {  // captured passes hold the previous operator's tables
+    XLS_CUDA(cudaStreamSynchronize(g->st));
+    g->drop_graphs();
+  }
   for (int s = 0; s < n_species; ++s)
     for (int d = 0; d < 3; ++d)
       if (!(sp[s].r_cut > 0) || !(sp[s].w_proj > 0) || 2 * sp[s].r_cut >= g->gL[d])
         return fail(XLS_EINVAL, "projector cutoff must be positive and below half of every cell edge");
+  if (g->wave) return wave_hamiltonian_set(g, veff, veff_on_device, n_atoms, pos, species, n_species, sp);
   const long long ng = (long long)g->gn[0] * g->gn[1] * g->gn[2];
   if (!g->Vg) {
     xls_status s = g->alloc(&g->Vg, ng * sizeof(double));
     if (s != XLS_OK) return s;
   }
+  g->atom_pos.assign(pos, pos + 3 * (size_t)n_atoms);
+  g->atom_sp.assign(species, species + n_atoms);
+  g->species.assign(sp, sp + n_species);
+  g->scf.pc_ready = false;
   XLS_CUDA(cudaMemcpyAsync(g->Vg, veff, ng * sizeof(double),
                            veff_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, g->st));
   launch_restrict(g->d_subs, g->n_sub, g->max_nd, g->Vg, g->gn, g->V, g->Vf, g->st);
@@ -883,6 +1380,7 @@ xls_status xls_hamiltonian_set(xls_grid g, const double* veff, int veff_on_devic
 
 xls_status xls_orbitals_set(xls_grid g, int sub, const double* psi, int on_device) {
   if (!g || !psi || sub < 0 || sub >= g->n_sub) return fail(XLS_EINVAL, "xls_orbitals_set: bad arguments");
+  if (g->wave) return wave_orbitals_set(g, sub, psi, on_device);
   const SubDev& S = g->subs[sub];
   const long long n = S.nd * S.ns;
   const cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
@@ -906,6 +1404,7 @@ xls_status xls_orbitals_set(xls_grid g, int sub, const double* psi, int on_devic
 
 xls_status xls_orbitals_random(xls_grid g, uint64_t seed) {
   if (!g) return fail(XLS_EINVAL, "null grid");
+  if (g->wave) return wave_orbitals_random(g, seed);
   if (g->prec == XLS_FP64) launch_splitmix_fill_f64((double*)g->blk[g->cur], g->tot_blk, seed, 0, g->st);
   else launch_splitmix_fill_f32((float*)g->blk[g->cur], g->tot_blk, seed, 0, g->st);
   XLS_CUDA(cudaGetLastError());
@@ -916,6 +1415,7 @@ xls_status xls_orbitals_random(xls_grid g, uint64_t seed) {
 
 xls_status xls_orbitals_get(xls_grid g, int sub, double* psi_out, int on_device) {
   if (!g || !psi_out || sub < 0 || sub >= g->n_sub) return fail(XLS_EINVAL, "xls_orbitals_get: bad arguments");
+  if (g->wave) return wave_orbitals_get(g, sub, psi_out, on_device);
   const SubDev& S = g->subs[sub];
   const long long n = S.nd * S.ns;
   const cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
@@ -937,11 +1437,13 @@ xls_status xls_orbitals_get(xls_grid g, int sub, double* psi_out, int on_device)
 xls_status xls_chefsi_batch(xls_grid g, int degree, int n_passes, const double* bounds) {
   if (!g || degree < 1 || degree >= kMaxDegree - 1 || n_passes < 0) return fail(XLS_EINVAL, "xls_chefsi_batch: bad arguments");
   if (!g->ham_set || !g->orb_set) return fail(XLS_EINVAL, "xls_chefsi_batch: Hamiltonian or orbitals not set");
+  if (g->wave) return wave_chefsi(g, degree, n_passes, bounds);
   return g->prec == XLS_FP64 ? chefsi<double>(g, degree, n_passes, bounds) : chefsi<float>(g, degree, n_passes, bounds);
 }
 
 xls_status xls_chefsi_stage(xls_grid g, int which, int degree, const double* bounds) {
   if (!g || degree < 1 || degree >= kMaxDegree - 1) return fail(XLS_EINVAL, "xls_chefsi_stage: bad arguments");
+  if (g->wave) return not_in_wave_mode("xls_chefsi_stage");
   if (!g->ham_set || !g->orb_set) return fail(XLS_EINVAL, "xls_chefsi_stage: Hamiltonian or orbitals not set");
   return g->prec == XLS_FP64 ? stage<double>(g, which, degree, bounds) : stage<float>(g, which, degree, bounds);
 }
@@ -949,6 +1451,7 @@ xls_status xls_chefsi_stage(xls_grid g, int which, int degree, const double* bou
 xls_status xls_hamiltonian_apply(xls_grid g, int sub, int k, const double* x, double* y, int on_device) {
   if (!g || !x || !y || sub < 0 || sub >= g->n_sub || k < 1 || k > g->subs[sub].ns)
     return fail(XLS_EINVAL, "xls_hamiltonian_apply: bad arguments");
+  if (g->wave) return not_in_wave_mode("xls_hamiltonian_apply");
   if (!g->ham_set) return fail(XLS_EINVAL, "xls_hamiltonian_apply: Hamiltonian not set");
   const SubDev& S = g->subs[sub];
   const long long n = S.nd * k;
@@ -980,6 +1483,7 @@ xls_status xls_hamiltonian_apply(xls_grid g, int sub, int k, const double* x, do
 xls_status xls_density(xls_grid g, double n_electrons, double kT, double* mu_out, double* rho_out, int rho_on_device,
                        double* e_band_out, double* e_entropy_out) {
   if (!g || !(kT > 0) || !g->have_ritz) return fail(XLS_EINVAL, "xls_density: bad arguments or no pass run yet");
+  if (g->wave) return wave_density(g, n_electrons, kT, mu_out, rho_out, rho_on_device, e_band_out, e_entropy_out);
   launch_fermi_occ(g->lam, g->cw, g->tot_states, n_electrons, kT, g->out4, g->occ, g->status, g->st);
   XLS_TRY(check_status(g));
   double h4[4];
@@ -1012,6 +1516,7 @@ xls_status xls_get_eigs(xls_grid g, int sub, double* lambda_out, double* c_out) 
 
 xls_status xls_get_subspace(xls_grid g, int sub, double* Ms_out, double* Hs_out) {
   if (!g || sub < 0 || sub >= g->n_sub) return fail(XLS_EINVAL, "xls_get_subspace: bad arguments");
+  if (g->wave) return not_in_wave_mode("xls_get_subspace");
   const SubDev& S = g->subs[sub];
   XLS_CUDA(cudaStreamSynchronize(g->st));
   const size_t b = (size_t)S.ns * S.ns * sizeof(double);
@@ -1022,6 +1527,10 @@ xls_status xls_get_subspace(xls_grid g, int sub, double* Ms_out, double* Hs_out)
 
 xls_status xls_get_bounds(xls_grid g, double* bounds_out) {
   if (!g || !bounds_out) return fail(XLS_EINVAL, "xls_get_bounds: bad arguments");
+  if (g->wave) {
+    std::memcpy(bounds_out, g->host_bounds.data(), 3 * (size_t)g->n_sub * sizeof(double));
+    return XLS_OK;
+  }
   XLS_CUDA(cudaStreamSynchronize(g->st));
   XLS_CUDA(cudaMemcpy(bounds_out, g->bounds, 3 * g->n_sub * sizeof(double), cudaMemcpyDeviceToHost));
   return XLS_OK;
@@ -1029,12 +1538,227 @@ xls_status xls_get_bounds(xls_grid g, double* bounds_out) {
 
 xls_status xls_set_profiling(xls_grid g, int on) {
   if (!g) return fail(XLS_EINVAL, "null grid");
+  if (g->wave && on) return not_in_wave_mode("xls_set_profiling");
   g->profiling = on != 0;
   if (g->profiling && g->pev.empty()) {
     g->pev.resize(4096);
     g->pcls.resize(2048);
     for (auto& e : g->pev) XLS_CUDA(cudaEventCreate(&e));
   }
+  return XLS_OK;
+}
+
+xls_status xls_scf_setup(xls_grid g, double n_electrons, double kT, int degree, int n_passes, double beta,
+                         double kappa, int history, int pulay_period) {
+  if (!g || !(n_electrons > 0) || !(kT > 0) || degree < 1 || degree >= kMaxDegree || n_passes < 1 || !(beta > 0) ||
+      !(kappa > 0) || history < 1 || history > 8 || pulay_period < 1)
+    return fail(XLS_EINVAL, "xls_scf_setup: bad arguments");
+  if (g->wave) return not_in_wave_mode("xls_scf_setup");
+  if (!g->ham_set) return fail(XLS_EINVAL, "xls_scf_setup: call xls_hamiltonian_set first (atoms and projectors)");
+  auto& S = g->scf;
+  const bool need_alloc = !S.d_gs || history > S.hist;
+  S.ne = n_electrons;
+  S.kT = kT;
+  S.degree = degree;
+  S.passes = n_passes;
+  S.beta = beta;
+  S.kappa = kappa;
+  S.period = pulay_period;
+  S.k = 0;
+  if (need_alloc) {
+    if (S.d_gs && history > S.hist) return fail(XLS_EINVAL, "xls_scf_setup: history cannot grow after the first setup");
+    S.hist = history;
+    XLS_TRY(scf_alloc(g));
+  }
+  S.hist = history;
+  XLS_TRY(scf_coefficients(g));
+  S.ready = true;
+  return XLS_OK;
+}
+
+xls_status xls_scf_step(xls_grid g, double* rho_inout, int rho_on_device, double* residual_out, double* energy_out,
+                        double* mu_out) {
+  if (!g || !rho_inout) return fail(XLS_EINVAL, "xls_scf_step: bad arguments");
+  if (g->wave) return not_in_wave_mode("xls_scf_step");
+  auto& S = g->scf;
+  if (!S.ready) return fail(XLS_EINVAL, "xls_scf_step: call xls_scf_setup first");
+  if (!g->orb_set) return fail(XLS_EINVAL, "xls_scf_step: orbitals not set");
+  const long long n = S.gs.nd;
+  const double dV = S.gs.dV;
+  cudaStream_t st = g->st;
+  if (!S.pc_ready) XLS_TRY(scf_pseudocharge(g));
+  XLS_CUDA(cudaMemcpyAsync(S.rho_in, rho_inout, n * sizeof(double),
+                           rho_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, st));
+  // 1. electrostatics: -Delta_h phi = 4 pi (rho + b), zero mean (warm start from the last phi)
+  launch_axpbypcz(n, 4.0 * M_PI, S.rho_in, 0.0, S.f, 4.0 * M_PI, S.b, st);
+  launch_sum(n, S.f, S.partial, S.scal + 8, st);
+  launch_sub_mean(n, S.scal + 8, S.f, st);
+  double ref_sq = 0.0;   // ||4 pi rho||^2: the scale of the cancelling terms
+  {
+    const double* xs[1] = {S.rho_in};
+    launch_dots(n, xs, xs, 1, S.partial, S.scal + 8, 16.0 * M_PI * M_PI, st);
+    XLS_CUDA(cudaMemcpyAsync(&ref_sq, S.scal + 8, sizeof(double), cudaMemcpyDeviceToHost, st));
+    XLS_CUDA(cudaStreamSynchronize(st));
+  }
+  XLS_TRY(scf_cg(g, 0, S.f, S.phi, 1e-13, 6000, ref_sq));
+  launch_sum(n, S.phi, S.partial, S.scal + 8, st);
+  launch_sub_mean(n, S.scal + 8, S.phi, st);
+  // 2. exchange-correlation and V_eff = phi + v_xc, restricted to the subdomains
+  launch_lda(n, S.rho_in, S.eps, S.vxc, st);
+  if (!g->Vg) XLS_TRY(g->alloc(&g->Vg, n * sizeof(double)));
+  launch_axpbypcz(n, 1.0, S.phi, 0.0, g->Vg, 1.0, S.vxc, st);
+  launch_restrict(g->d_subs, g->n_sub, g->max_nd, g->Vg, g->gn, g->V, g->Vf, st);
+  // 3. new upper bounds (Lanczos) and the CheFSI passes
+  XLS_TRY(lanczos_bounds(g));
+  if (g->prec == XLS_FP64) XLS_TRY(chefsi<double>(g, S.degree, S.passes, nullptr));
+  else XLS_TRY(chefsi<float>(g, S.degree, S.passes, nullptr));
+  // 4. Fermi level, output density, band and entropy energies
+  double mu = 0, e_band = 0, e_ent = 0;
+  XLS_TRY(xls_density(g, S.ne, S.kT, &mu, S.rho_out, 1, &e_band, &e_ent));
+  // 5. energy at the input density and the residual
+  double sums[4], rr[2];
+  {
+    const double* xs[4] = {S.rho_in, S.vxc, S.b, S.rho_in};
+    const double* ys[4] = {S.eps, S.rho_in, S.phi, S.phi};
+    launch_dots(n, xs, ys, 4, S.partial, S.scal + 8, 1.0, st);
+    XLS_CUDA(cudaMemcpyAsync(sums, S.scal + 8, 4 * sizeof(double), cudaMemcpyDeviceToHost, st));
+  }
+  launch_axpbypcz(n, 1.0, S.rho_out, 0.0, S.f, -1.0, S.rho_in, st);   // f = rho_out - rho_in
+  {
+    const double* xs[2] = {S.f, S.rho_out};
+    const double* ys[2] = {S.f, S.rho_out};
+    launch_dots(n, xs, ys, 2, S.partial, S.scal + 12, 1.0, st);
+    XLS_CUDA(cudaMemcpyAsync(rr, S.scal + 12, 2 * sizeof(double), cudaMemcpyDeviceToHost, st));
+  }
+  XLS_CUDA(cudaStreamSynchronize(st));
+  const double energy = e_band + dV * (sums[0] - sums[1] + 0.5 * (sums[2] - sums[3])) - S.e_self - e_ent;
+  const double residual = std::sqrt(rr[0] / rr[1]);
+  // 6. periodic Pulay mixing with the Kerker preconditioner: x_next = x + beta P f
+  //    [- sum_i gamma_i (dX_i + beta dPF_i) on every period-th step]
+  XLS_TRY(scf_kerker(g, S.f, S.pf));
+  if (S.k > 0) {
+    const int slot = (S.k - 1) % S.hist;
+    launch_axpbypcz(n, 1.0, S.rho_in, 0.0, S.dX + (size_t)slot * n, -1.0, S.x_prev, st);
+    launch_axpbypcz(n, 1.0, S.f, 0.0, S.dF + (size_t)slot * n, -1.0, S.f_prev, st);
+    launch_axpbypcz(n, 1.0, S.pf, 0.0, S.dPF + (size_t)slot * n, -1.0, S.pf_prev, st);
+  }
+  XLS_CUDA(cudaMemcpyAsync(S.x_prev, S.rho_in, n * sizeof(double), cudaMemcpyDeviceToDevice, st));
+  XLS_CUDA(cudaMemcpyAsync(S.f_prev, S.f, n * sizeof(double), cudaMemcpyDeviceToDevice, st));
+  XLS_CUDA(cudaMemcpyAsync(S.pf_prev, S.pf, n * sizeof(double), cudaMemcpyDeviceToDevice, st));
+  launch_axpbypcz(n, 1.0, S.rho_in, 0.0, S.tmp, S.beta, S.pf, st);     // tmp = x + beta P f
+  const int nh = std::min(S.k, S.hist);
+  if ((S.k + 1) % S.period == 0 && nh > 0)
+    launch_pulay(n, nh, S.dF, S.dX, S.dPF, S.f, S.beta, S.pulay_partial, S.gamma, S.tmp, st);
+  S.k++;
+  XLS_CUDA(cudaMemcpyAsync(rho_inout, S.tmp, n * sizeof(double),
+                           rho_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, st));
+  XLS_CUDA(cudaStreamSynchronize(st));
+  if (residual_out) *residual_out = residual;
+  if (energy_out) *energy_out = energy;
+  if (mu_out) *mu_out = mu;
+  return XLS_OK;
+}
+
+// atom tables of the learned start for the grid's current atoms
+xls_status ls_tables(xls_grid g) {
+  const int na = (int)g->atom_sp.size();
+  if (na == 0) return fail(XLS_EINVAL, "learned start: the Hamiltonian has no atoms");
+  for (int s : g->atom_sp)
+    if (s > 1) return fail(XLS_EINVAL, "learned start: the descriptors cover two species (indices 0 and 1)");
+  if (g->ls_na != na) {
+    if (g->ls_na >= 0) return fail(XLS_EINVAL, "learned start: the atom count changed since the first call");
+    const long long ng = (long long)g->gn[0] * g->gn[1] * g->gn[2];
+    XLS_TRY(g->alloc(&g->ls_atoms, na * sizeof(float4)));
+    XLS_TRY(g->alloc(&g->ls_pos, 3 * (size_t)na * sizeof(double)));
+    XLS_TRY(g->alloc(&g->ls_rc, na * sizeof(double)));
+    XLS_TRY(g->alloc(&g->ls_amp, na * sizeof(double)));
+    XLS_TRY(g->alloc(&g->ls_g1, (size_t)na * (g->gn[0] + g->gn[1] + g->gn[2]) * sizeof(double)));
+    XLS_TRY(g->alloc(&g->ls_sad, ng * sizeof(double)));
+    XLS_TRY(g->alloc(&g->ls_partial, kRedPartials * sizeof(double)));
+    XLS_TRY(g->alloc(&g->ls_s, 4 * sizeof(double)));
+    g->ls_na = na;
+  }
+  std::vector<float4> at(na);
+  std::vector<double> rc(na), amp(na);
+  for (int i = 0; i < na; ++i) {
+    const xls_species& q = g->species[g->atom_sp[i]];
+    double r[3];
+    for (int d = 0; d < 3; ++d) {
+      r[d] = std::fmod(g->atom_pos[3 * i + d], g->gL[d]);
+      if (r[d] < 0) r[d] += g->gL[d];
+    }
+    at[i] = make_float4((float)r[0], (float)r[1], (float)r[2], (float)g->atom_sp[i]);
+    rc[i] = q.rc_loc;
+    amp[i] = q.Zv * std::pow(M_PI, -1.5) / (q.rc_loc * q.rc_loc * q.rc_loc);
+  }
+  XLS_CUDA(cudaMemcpy(g->ls_atoms, at.data(), na * sizeof(float4), cudaMemcpyHostToDevice));
+  XLS_CUDA(cudaMemcpy(g->ls_pos, g->atom_pos.data(), 3 * (size_t)na * sizeof(double), cudaMemcpyHostToDevice));
+  XLS_CUDA(cudaMemcpy(g->ls_rc, rc.data(), na * sizeof(double), cudaMemcpyHostToDevice));
+  XLS_CUDA(cudaMemcpy(g->ls_amp, amp.data(), na * sizeof(double), cudaMemcpyHostToDevice));
+  return XLS_OK;
+}
+
+xls_status xls_descriptors(xls_grid g, float* X_out, int on_device) {
+  if (!g || !X_out) return fail(XLS_EINVAL, "xls_descriptors: bad arguments");
+  if (!g->ham_set) return fail(XLS_EINVAL, "xls_descriptors: call xls_hamiltonian_set first (atoms)");
+  XLS_TRY(ls_tables(g));
+  const long long ng = (long long)g->gn[0] * g->gn[1] * g->gn[2];
+  if (!g->ls_X) XLS_TRY(g->alloc(&g->ls_X, (size_t)ng * 32 * sizeof(float)));
+  launch_descriptors(ng, g->gn, g->gh, g->gL, g->ls_atoms, g->ls_na, 2, g->ls_X, g->st);
+  XLS_CUDA(cudaGetLastError());
+  XLS_CUDA(cudaMemcpyAsync(X_out, g->ls_X, (size_t)ng * 32 * sizeof(float),
+                           on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, g->st));
+  XLS_CUDA(cudaStreamSynchronize(g->st));
+  return XLS_OK;
+}
+
+xls_status xls_learned_start(xls_grid g, xls_mlp m, double n_electrons, double* rho_out, int on_device) {
+  if (!g || !rho_out || !(n_electrons > 0)) return fail(XLS_EINVAL, "xls_learned_start: bad arguments");
+  if (!g->ham_set) return fail(XLS_EINVAL, "xls_learned_start: call xls_hamiltonian_set first (atoms)");
+  XLS_TRY(ls_tables(g));
+  const long long ng = (long long)g->gn[0] * g->gn[1] * g->gn[2];
+  cudaStream_t st = g->st;
+  launch_gaussian_density(g->ls_na, g->ls_pos, g->ls_rc, g->ls_amp, g->gn, g->gh, g->gL, g->ls_g1, g->ls_sad,
+                          n_electrons, g->ls_partial, g->ls_s, st);
+  double* out = g->ls_sad;
+  if (m) {
+    if (!g->ls_X) XLS_TRY(g->alloc(&g->ls_X, (size_t)ng * 32 * sizeof(float)));
+    if (!g->ls_y) XLS_TRY(g->alloc(&g->ls_y, (size_t)ng * sizeof(float)));
+    if (!g->rho) XLS_TRY(g->alloc(&g->rho, ng * sizeof(double)));
+    launch_descriptors(ng, g->gn, g->gh, g->gL, g->ls_atoms, g->ls_na, 2, g->ls_X, st);
+    if (m->st != st) XLS_CUDA(cudaStreamSynchronize(m->st));   // the model's pending updates
+    launch_mlp_infer(ng, m->theta, g->ls_X, g->ls_y, st);
+    launch_add_clamp(ng, g->ls_sad, g->ls_y, g->rho, st);
+    launch_sum(ng, g->rho, g->ls_partial, g->ls_s, st);
+    launch_rescale(ng, g->ls_s, n_electrons / (g->gh[0] * g->gh[1] * g->gh[2]), g->rho, st);
+    out = g->rho;
+  }
+  XLS_CUDA(cudaGetLastError());
+  XLS_CUDA(cudaMemcpyAsync(rho_out, out, ng * sizeof(double), on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
+                           st));
+  XLS_CUDA(cudaStreamSynchronize(st));
+  return XLS_OK;
+}
+
+xls_status xls_get_waves(xls_grid g, int* n_waves_out, int* first_sub_out) {
+  if (!g || !n_waves_out) return fail(XLS_EINVAL, "xls_get_waves: bad arguments");
+  *n_waves_out = g->wave ? (int)g->waves.size() : 1;
+  if (first_sub_out) {
+    if (g->wave)
+      for (size_t w = 0; w < g->waves.size(); ++w) first_sub_out[w] = g->waves[w].first;
+    else
+      first_sub_out[0] = 0;
+  }
+  return XLS_OK;
+}
+
+xls_status xls_set_graphs(xls_grid g, int on) {
+  if (!g) return fail(XLS_EINVAL, "null grid");
+  if (!on && !g->graphs.empty()) {
+    XLS_CUDA(cudaStreamSynchronize(g->st));
+    g->drop_graphs();
+  }
+  g->use_graphs = on != 0;
   return XLS_OK;
 }
 
@@ -1049,6 +1773,12 @@ xls_status xls_get_kernel_times(xls_grid g, double* ms8_out, int* count8_out) {
 
 xls_status xls_get_timings(xls_grid g, double* ms4_out, int* launches_out) {
   if (!g) return fail(XLS_EINVAL, "null grid");
+  if (g->wave) {
+    if (ms4_out)
+      for (int i = 0; i < 4; ++i) ms4_out[i] = g->wave_stage_ms[i];
+    if (launches_out) *launches_out = g->last_launches;
+    return XLS_OK;
+  }
   if (ms4_out)
     for (int i = 0; i < 4; ++i) ms4_out[i] = g->stage_ms[i];
   if (launches_out) *launches_out = g->last_launches;

@@ -68,8 +68,9 @@ struct TmaJob {
   int sub;        // subdomain
   int n_ytiles;   // row tiles per vector
   int W;          // staged row width (floats)
-  int pad;
+  int TY;         // rows per tile
 };
+constexpr int kMapsPerSub = 10;  // TMA stencil tensor maps per subdomain (3 per block + V)
 struct TmaClass {
   int nq = 0, TY = 0, W = 0;   // threads per row (x-points / 4), rows per tile, row width
   double h[3] = {0, 0, 0};     // grid spacing shared by the class
@@ -158,10 +159,9 @@ namespace xls {
 bool tma_eligible(const SubDev& S);
 int tma_tile_rows(const SubDev& S);
 int tma_row_width(const SubDev& S);
-bool build_tma_maps(const SubDev& S, int sub, void* const bufs[3], struct CUtensorMap_st* out);
+bool build_tma_maps(const SubDev& S, const float* Vf, void* const bufs[3], struct CUtensorMap_st* out);
 void launch_stencil_tma(const SubDev* d_subs, const TmaClass& cls, const struct CUtensorMap_st* d_maps, int buf_in,
-                        const float* Yprev, float* Yout, const float* V, const StepCoef* coef, int step, int* status,
-                        cudaStream_t st);
+                        int buf_prev, float* Yout, const StepCoef* coef, int step, int* status, cudaStream_t st);
 
 // ---- dense subspace work -------------------------------------------------------------------
 template <typename T>
@@ -183,6 +183,53 @@ void launch_fermi_occ(const double* lam, const double* c, int n_tot, double n_e,
 // R (cluster workspace), all n x n per subdomain; lam (out); vecs 8n per subdomain.
 bool launch_cholesky_cluster(const SubDev* d_subs, int n_sub, int max_ns, double* Ms, int* status, cudaStream_t st);
 bool launch_tridiag_cluster(const SubDev* d_subs, int n_sub, int max_ns, double* A, double* vecs, cudaStream_t st);
+// ---- learned start ---------------------------------------------------------------------------
+}  // namespace xls
+// model handle: FP32 master parameters, Adam moments and the training work arrays
+struct xls_mlp_s {
+  cudaStream_t st = nullptr;
+  int n_params = 0;
+  float *theta = nullptr, *m = nullptr, *v = nullptr, *grad = nullptr;
+  int t = 0;                              // Adam steps taken
+  long long cap = 0;                      // points the work arrays hold
+  float *A = nullptr, *D = nullptr, *e = nullptr, *wpartial = nullptr, *X = nullptr, *y = nullptr, *yp = nullptr;
+  double *loss_partial = nullptr, *loss = nullptr;
+};
+namespace xls {
+xls_status mlp_reserve(xls_mlp_s* m, long long n);
+int mlp_param_count();
+size_t mlp_wpartial_floats();
+void launch_descriptors(long long n, const int gn[3], const double gh[3], const double gL[3], const float4* atoms,
+                        int n_atoms, int n_species, float* X, cudaStream_t st);
+void launch_mlp_infer(long long n, const float* theta, const float* X, float* y, cudaStream_t st);
+void launch_mlp_grad(long long n, const float* theta, const float* X, const float* yt, float* A, float* D, float* e,
+                     double* loss_partial, float* wpartial, float* grad, double* loss_out, cudaStream_t st);
+void launch_adam(int n, float* theta, float* m, float* v, const float* g, float lr, int t, cudaStream_t st);
+void launch_add_clamp(long long n, const double* sad, const float* corr, double* rho, cudaStream_t st);
+
+// ---- SCF on the global grid -----------------------------------------------------------------
+void launch_dots(long long n, const double* const* x, const double* const* y, int nq, double* partial, double* out,
+                 double scale, cudaStream_t st);
+void launch_sum(long long n, const double* x, double* partial, double* out, cudaStream_t st);
+void launch_axpbypcz(long long n, double a, const double* x, double b, double* y, double c, const double* z,
+                     cudaStream_t st);
+void launch_sub_mean(long long n, const double* sum, double* y, cudaStream_t st);
+void launch_cg_xr(long long n, const double* s, double* x, double* r, const double* p, const double* q,
+                  double* partial, cudaStream_t st);
+void launch_cg_p(long long n, double* s, const double* r, double* p, cudaStream_t st);
+void launch_lda(long long n, const double* rho, double* eps, double* vxc, cudaStream_t st);
+void launch_pseudocharge(int n_atoms, const double* d_pos, const double* d_rc, const double* d_amp, const int gn[3],
+                         const double gh[3], const double gL[3], double* g1, double* b, double z_total, double* partial,
+                         double* s4, cudaStream_t st);
+size_t pulay_partial_doubles();
+void launch_gaussian_density(int n_atoms, const double* d_pos, const double* d_rc, const double* d_amp, const int gn[3],
+                             const double gh[3], const double gL[3], double* g1, double* out, double total,
+                             double* partial, double* s4, cudaStream_t st);
+void launch_rescale(long long n, const double* sum, double target, double* y, cudaStream_t st);
+void launch_pulay(long long n, int m, const double* dF, const double* dX, const double* dPF, const double* f, double beta,
+                  double* partial, double* gamma, double* x, cudaStream_t st);
+constexpr int kRedPartials = 296 * 4;  // doubles of a reduction's partial-sum buffer
+
 void launch_eig(const SubDev* d_subs, int n_sub, int max_ns, double* L, double* A, double* Y, double* W, double* lam,
                 double* vecs, int* status, double* scratch, double* R, bool cluster, cudaStream_t st);
 size_t eig_scratch_doubles(int n_sub, int max_ns);

@@ -59,6 +59,18 @@ _SIGS = {
     "xls_get_bounds": (c_int, [c_void_p, c_void_p]),
     "xls_get_timings": (c_int, [c_void_p, c_void_p, POINTER(c_int)]),
     "xls_set_profiling": (c_int, [c_void_p, c_int]),
+    "xls_set_graphs": (c_int, [c_void_p, c_int]),
+    "xls_get_waves": (c_int, [c_void_p, POINTER(c_int), c_void_p]),
+    "xls_mlp_create": (c_int, [c_void_p, c_int, c_void_p, POINTER(c_void_p)]),
+    "xls_mlp_destroy": (c_int, [c_void_p]),
+    "xls_mlp_get_params": (c_int, [c_void_p, c_void_p]),
+    "xls_mlp_infer": (c_int, [c_void_p, c_void_p, ctypes.c_longlong, c_void_p, c_int]),
+    "xls_mlp_loss_grad": (c_int, [c_void_p, c_void_p, c_void_p, ctypes.c_longlong, POINTER(c_double), c_void_p, c_int]),
+    "xls_mlp_train_step": (c_int, [c_void_p, c_void_p, c_void_p, ctypes.c_longlong, c_double, POINTER(c_double), c_int]),
+    "xls_descriptors": (c_int, [c_void_p, c_void_p, c_int]),
+    "xls_learned_start": (c_int, [c_void_p, c_void_p, c_double, c_void_p, c_int]),
+    "xls_scf_setup": (c_int, [c_void_p, c_double, c_double, c_int, c_int, c_double, c_double, c_int, c_int]),
+    "xls_scf_step": (c_int, [c_void_p, c_void_p, c_int, POINTER(c_double), POINTER(c_double), POINTER(c_double)]),
     "xls_get_kernel_times": (c_int, [c_void_p, c_void_p, c_void_p]),
     "xls_gram_noalloc": (c_int, [c_void_p, c_void_p, ctypes.c_longlong, c_int, c_void_p, c_void_p, c_void_p]),
     "xls_last_error": (ctypes.c_char_p, []),
@@ -215,6 +227,97 @@ def xls_get_timings(g):
 
 def xls_set_profiling(g, on):
     _check(load().xls_set_profiling(g, int(bool(on))))
+
+
+def xls_get_waves(g, n_sub):
+    """(number of waves, first subdomain of each wave)."""
+    n = c_int()
+    first = np.zeros(max(1, n_sub), dtype=np.int32)
+    _check(load().xls_get_waves(g, byref(n), first.ctypes.data_as(c_void_p)))
+    return n.value, first[:n.value].tolist()
+
+
+N_MLP_PARAMS = 10497
+
+
+def _f32(a):
+    a = np.ascontiguousarray(a, dtype=np.float32)
+    return a, a.ctypes.data_as(c_void_p)
+
+
+def xls_mlp_create(params, stream=None):
+    p = np.ascontiguousarray(params, dtype=np.float64)
+    h = c_void_p()
+    _check(load().xls_mlp_create(p.ctypes.data_as(c_void_p), int(p.size), c_void_p(stream) if stream else None,
+                                 byref(h)))
+    return h
+
+
+def xls_mlp_destroy(m):
+    _check(load().xls_mlp_destroy(m))
+
+
+def xls_mlp_get_params(m):
+    out = np.zeros(N_MLP_PARAMS)
+    _check(load().xls_mlp_get_params(m, out.ctypes.data_as(c_void_p)))
+    return out
+
+
+def xls_mlp_infer(m, X):
+    X, px = _f32(X)
+    y = np.zeros(X.shape[0], dtype=np.float32)
+    _check(load().xls_mlp_infer(m, px, X.shape[0], y.ctypes.data_as(c_void_p), 0))
+    return y
+
+
+def xls_mlp_loss_grad(m, X, y):
+    X, px = _f32(X)
+    y, py = _f32(y)
+    loss = c_double()
+    grad = np.zeros(N_MLP_PARAMS)
+    _check(load().xls_mlp_loss_grad(m, px, py, X.shape[0], byref(loss), grad.ctypes.data_as(c_void_p), 0))
+    return loss.value, grad
+
+
+def xls_mlp_train_step(m, X, y, lr):
+    X, px = _f32(X)
+    y, py = _f32(y)
+    loss = c_double()
+    _check(load().xls_mlp_train_step(m, px, py, X.shape[0], float(lr), byref(loss), 0))
+    return loss.value
+
+
+def xls_descriptors(g, n_points):
+    X = np.zeros((n_points, 32), dtype=np.float32)
+    _check(load().xls_descriptors(g, X.ctypes.data_as(c_void_p), 0))
+    return X
+
+
+def xls_learned_start(g, m, n_electrons, n_points):
+    rho = np.zeros(n_points)
+    _check(load().xls_learned_start(g, m, float(n_electrons), rho.ctypes.data_as(c_void_p), 0))
+    return rho
+
+
+def xls_set_graphs(g, on):
+    _check(load().xls_set_graphs(g, int(bool(on))))
+
+
+def xls_scf_setup(g, n_electrons, kT, degree, n_passes=1, beta=0.3, kappa=0.5, history=7, pulay_period=2):
+    _check(load().xls_scf_setup(g, float(n_electrons), float(kT), int(degree), int(n_passes), float(beta),
+                                float(kappa), int(history), int(pulay_period)))
+
+
+def xls_scf_step(g, rho):
+    """One SCF step; rho (global grid, float64: a contiguous numpy array or a CUDA tensor) is
+    replaced by the mixed next input density.  Returns (residual, energy, mu)."""
+    res, en, mu = c_double(), c_double(), c_double()
+    if hasattr(rho, "data_ptr"):
+        _check(load().xls_scf_step(g, c_void_p(rho.data_ptr()), 1, byref(res), byref(en), byref(mu)))
+    else:
+        assert rho.dtype == np.float64 and rho.flags.c_contiguous
+        _check(load().xls_scf_step(g, rho.ctypes.data_as(c_void_p), 0, byref(res), byref(en), byref(mu)))
+    return res.value, en.value, mu.value
 
 
 def xls_get_kernel_times(g):

@@ -306,3 +306,216 @@ def test_tensor_core_gram_and_rotation_match_simt(monkeypatch, prec):
         P_t, P_s = res["tc"][1][a], res["simt"][1][a]
         # same orthonormal Ritz block up to rotations inside degenerate clusters: compare projectors
         assert np.linalg.norm(P_t.T @ (P_t @ P_s.T) - P_s.T) < 1e-3 * np.linalg.norm(P_s)
+
+
+@pytest.mark.parametrize("prec", [xls.XLS_FP64, xls.XLS_MIXED_BF16])
+@pytest.mark.parametrize("on_torch_stream", [False, True])
+def test_graph_replay_matches_direct_launches(prec, on_torch_stream):
+    """Passes replayed from captured CUDA graphs (seven passes: every orbital block holds the
+    input at least twice, so all three graphs are captured and replayed) give the same Ritz values
+    and density as directly launched passes, on the legacy stream and on a side stream.  Orbitals
+    inside degenerate clusters are not unique (summation orders differ between the two grids'
+    tables), so the unique quantities are compared."""
+    import torch
+    w = dirichlet20_workload()
+    V = pseudo.local_potential(w)
+    subs = dc.partition(w)
+    psi0 = _start_blocks(w, subs)
+    res = {}
+    for mode in ("direct", "graph"):
+        st = torch.cuda.Stream() if on_torch_stream else None
+        g = xls.Grid(w, prec, stream=st.cuda_stream if st is not None else None)
+        try:
+            g.set_hamiltonian(V)
+            for a in range(w.n_sub):
+                xls.xls_orbitals_set(g.h, a, psi0[a])
+            xls.xls_set_graphs(g.h, mode == "graph")
+            for _ in range(5):
+                xls.xls_chefsi_batch(g.h, w.degree, 1)
+            xls.xls_chefsi_batch(g.h, w.degree, 2)
+            lam = [xls.xls_get_eigs(g.h, a, int(w.n_states[a]))[0] for a in range(w.n_sub)]
+            rho = np.zeros(int(np.prod(w.n)))
+            mu, eb, es = xls.xls_density(g.h, w.n_electrons, w.kT, rho)
+            psi = [xls.xls_orbitals_get(g.h, a, np.zeros((int(w.n_states[a]), subs[a].N))) for a in range(w.n_sub)]
+        finally:
+            g.close()
+        res[mode] = (lam, rho, mu, eb, psi)
+    tol = 1e-9 if prec == xls.XLS_FP64 else 1e-5
+    for a in range(w.n_sub):
+        np.testing.assert_allclose(res["graph"][0][a], res["direct"][0][a], rtol=0, atol=tol)
+        P = res["graph"][4][a]
+        np.testing.assert_allclose(P @ P.T, np.eye(P.shape[0]), atol=1e-9 if prec == xls.XLS_FP64 else 1e-4)
+    assert relerr(res["graph"][1], res["direct"][1]) < (1e-9 if prec == xls.XLS_FP64 else 1e-5)
+    assert abs(res["graph"][2] - res["direct"][2]) < tol
+
+
+def _scf_start(w):
+    """Start density: the neutralising Gaussian clouds of the pseudocharge (sum = N_e dV^-1)."""
+    b = pseudo.pseudocharge(w)
+    n_pts = int(np.prod(w.n))
+    dV = float(np.prod(w.h))
+    return w.n_electrons / (n_pts * dV) - b
+
+
+@pytest.mark.parametrize("prec", [xls.XLS_FP64, xls.XLS_MIXED_BF16])
+def test_scf_steps_match_oracle(prec):
+    """SCF steps (Poisson, LDA, Lanczos bound, one CheFSI pass, Fermi level, density, energy,
+    residual, periodic Pulay + Kerker mixing) against the oracle's steps from the same start
+    density and blocks: three steps on the FP64 path (to FP64 rounding), seven on the mixed path,
+    whose energy bar (1e-5 Ha/atom) applies once the subspace has converged past the random
+    start."""
+    from oracle import scf
+    w = synth.workload(0)
+    V0 = pseudo.local_potential(w)
+    subs = dc.partition(w)
+    psi0 = [synth.psi0_block(w.psi_seed + a, subs[a].N, int(w.n_states[a])) for a in range(w.n_sub)]
+    rho0 = _scf_start(w)
+    st = scf.start(w, rho0, psi0)
+    n_steps = 3 if prec == xls.XLS_FP64 else 7
+    ref = [scf.step(w, st) for _ in range(n_steps)]
+    rho_ref = st.rho
+    g = make_grid(w, V0, prec)
+    try:
+        for a in range(w.n_sub):
+            xls.xls_orbitals_set(g.h, a, psi0[a])
+        xls.xls_scf_setup(g.h, w.n_electrons, w.kT, w.degree)
+        rho = np.ascontiguousarray(rho0.astype(np.float64))
+        out = [xls.xls_scf_step(g.h, rho) for _ in range(n_steps)]
+    finally:
+        g.close()
+    n_at = len(w.pos)
+    for k, ((r_o, e_o, mu_o, _), (r_g, e_g, mu_g)) in enumerate(zip(ref, out)):
+        if prec == xls.XLS_FP64:
+            assert abs(e_g - e_o) < 1e-8 * n_at, (k, e_g, e_o)
+            assert abs(mu_g - mu_o) < 1e-8, (k, mu_g, mu_o)
+            assert abs(r_g - r_o) < 1e-6 * r_o, (k, r_g, r_o)
+        else:
+            bar = 1e-5 if k >= n_steps - 2 else 1e-4
+            assert abs(e_g - e_o) < bar * n_at, (k, e_g, e_o)
+            assert abs(r_g - r_o) < 1e-2 * r_o + 1e-5, (k, r_g, r_o)
+    tol = 1e-7 if prec == xls.XLS_FP64 else 1e-4
+    assert np.linalg.norm(rho - rho_ref) / np.linalg.norm(rho_ref) < tol
+
+
+@pytest.mark.parametrize("prec", [xls.XLS_FP64, xls.XLS_MIXED_BF16])
+def test_waves_match_resident_grid(prec):
+    """An HBM budget below the footprint runs the subdomains in waves (orbitals in the host
+    store): Ritz values, weights, mu, rho and bounds equal those of the all-resident grid; the
+    oracle pins the FP64 eigenvalues of the first subdomain."""
+    w = dirichlet20_workload()
+    V = pseudo.local_potential(w)
+    subs = dc.partition(w)
+    psi0 = _start_blocks(w, subs)
+    res = {}
+    for mode, budget in (("resident", 0), ("waves", 90 << 20)):
+        g = xls.Grid(w, prec, hbm_budget_bytes=budget)
+        try:
+            n_waves, first = xls.xls_get_waves(g.h, w.n_sub)
+            if mode == "waves":
+                assert n_waves >= 2, n_waves
+                assert first[0] == 0 and all(b > a for a, b in zip(first, first[1:]))
+            else:
+                assert n_waves == 1
+            g.set_hamiltonian(V)
+            for a in range(w.n_sub):
+                xls.xls_orbitals_set(g.h, a, psi0[a])
+            xls.xls_chefsi_batch(g.h, w.degree, 2)
+            xls.xls_chefsi_batch(g.h, w.degree, 1)
+            lam = [xls.xls_get_eigs(g.h, a, int(w.n_states[a])) for a in range(w.n_sub)]
+            rho = np.zeros(int(np.prod(w.n)))
+            mu, eb, es = xls.xls_density(g.h, w.n_electrons, w.kT, rho)
+            bnd = xls.xls_get_bounds(g.h, w.n_sub)
+            P0 = xls.xls_orbitals_get(g.h, 0, np.zeros((int(w.n_states[0]), subs[0].N)))
+        finally:
+            g.close()
+        res[mode] = (lam, rho, mu, eb, bnd, P0)
+    tol = 1e-9 if prec == xls.XLS_FP64 else 2e-5
+    for a in range(w.n_sub):
+        np.testing.assert_allclose(res["waves"][0][a][0], res["resident"][0][a][0], rtol=0, atol=tol)
+        np.testing.assert_allclose(res["waves"][0][a][1], res["resident"][0][a][1], rtol=0, atol=10 * tol)
+    assert abs(res["waves"][2] - res["resident"][2]) < tol
+    assert relerr(res["waves"][1], res["resident"][1]) < 10 * tol
+    np.testing.assert_allclose(res["waves"][4], res["resident"][4], rtol=tol, atol=tol)
+    P = res["waves"][5]
+    np.testing.assert_allclose(P @ P.T, np.eye(P.shape[0]), atol=1e-9 if prec == xls.XLS_FP64 else 1e-4)
+
+
+def _two_species_cell():
+    return synth.two_species(synth.workload(0), [0, 5])
+
+
+def test_descriptors_match_oracle():
+    from oracle import learned
+    w = _two_species_cell()
+    V = pseudo.local_potential(w)
+    with make_grid(w, V, xls.XLS_FP64) as g:
+        X = xls.xls_descriptors(g.h, int(np.prod(w.n)))
+    ref = learned.descriptors(w)
+    assert np.abs(X - ref).max() < 2e-5 * max(1.0, np.abs(ref).max())
+    assert np.all(X[:, :16].sum(axis=1) > 0) and (X[:, 16:].sum(axis=1) > 0).mean() > 0.5   # both species seen
+
+
+def test_mlp_loss_gradient_and_training_match_oracle():
+    """FP32 backpropagation against the oracle's FP64 gradient (itself pinned by finite
+    differences), then five Adam steps on both sides."""
+    from oracle import learned
+    rng = np.random.default_rng(8)
+    X = rng.standard_normal((3000, 32)).astype(np.float32) * 0.5
+    y = (rng.standard_normal(3000) * 0.2).astype(np.float32)
+    theta = synth.mlp_init(31)
+    m = xls.xls_mlp_create(theta)
+    try:
+        loss, grad = xls.xls_mlp_loss_grad(m, X, y)
+        loss_ref, grad_ref = learned.loss_and_grad(theta, X.astype(np.float64), y.astype(np.float64))
+        assert abs(loss - loss_ref) < 1e-5 * loss_ref
+        assert np.linalg.norm(grad - grad_ref) < 1e-4 * np.linalg.norm(grad_ref)
+        opt = learned.Adam(learned.N_PARAMS, lr=1e-3)
+        th = theta.copy()
+        for _ in range(5):
+            l_gpu = xls.xls_mlp_train_step(m, X, y, 1e-3)
+            l_ref, g_ref = learned.loss_and_grad(th, X.astype(np.float64), y.astype(np.float64))
+            th = opt.step(th, g_ref)
+            assert abs(l_gpu - l_ref) < 1e-4 * l_ref
+        got = xls.xls_mlp_get_params(m)
+        assert np.linalg.norm(got - th) < 1e-4 * np.linalg.norm(th - theta) + 1e-6 * np.linalg.norm(theta)
+    finally:
+        xls.xls_mlp_destroy(m)
+
+
+def test_mlp_bf16_inference_matches_oracle():
+    """BF16 operands with FP32 accumulation against the oracle's BF16-rounded inference (exact
+    accumulation): equal to FP32 rounding except where the two sides' tanh values round to
+    different BF16 neighbours, a one-ulp change of one activation."""
+    from oracle import learned
+    w = _two_species_cell()
+    X = learned.descriptors(w).astype(np.float32)
+    theta = synth.mlp_init(12)
+    m = xls.xls_mlp_create(theta)
+    try:
+        y = xls.xls_mlp_infer(m, X)
+    finally:
+        xls.xls_mlp_destroy(m)
+    ref = learned.forward_bf16(theta, X.astype(np.float64))
+    d = np.abs(y - ref)
+    assert np.median(d) < 1e-5
+    assert np.mean(d > 1e-4) < 0.02
+    assert d.max() < 2e-2
+
+
+def test_learned_start_matches_oracle():
+    from oracle import learned
+    w = _two_species_cell()
+    V = pseudo.local_potential(w)
+    n_pts = int(np.prod(w.n))
+    theta = synth.mlp_init(5) * 0.1
+    m = xls.xls_mlp_create(theta)
+    try:
+        with make_grid(w, V, xls.XLS_FP64) as g:
+            sad = xls.xls_learned_start(g.h, None, w.n_electrons, n_pts)
+            rho = xls.xls_learned_start(g.h, m, w.n_electrons, n_pts)
+    finally:
+        xls.xls_mlp_destroy(m)
+    assert relerr(sad, learned.sad_density(w).ravel()) < 1e-12
+    ref = learned.learned_start(w, theta).ravel()
+    assert relerr(rho, ref) < 1e-4
+    assert rho.min() >= 0.0 and abs(rho.sum() * np.prod(w.h) - w.n_electrons) < 1e-9
