@@ -375,6 +375,7 @@ __global__ void k_rcsr_fill(const SubDev* __restrict__ subs, const ProjSlot* __r
 }
 
 constexpr int kBackPts = 1024, kBackVec = 8;
+constexpr int kBackRow = kBackVec + 1;   // padded slot row of Q (consecutive slots in different bank groups)
 
 // Y_out[v][g] += scale * sum over the slots s of point g of sum_l chi_l(g) P[s][l][v]
 template <typename T>
@@ -384,7 +385,7 @@ k_nl_back_csr(const SubDev* __restrict__ subs, const long long* __restrict__ row
               const StepCoef* __restrict__ coef, int step) {
   using T4 = typename Vec4<T>::type;
   extern __shared__ __align__(16) unsigned char qsm[];
-  T4* Qs = reinterpret_cast<T4*>(qsm);   // [slot][kBackVec]
+  T4* Qs = reinterpret_cast<T4*>(qsm);   // [slot][kBackRow]
   const SubDev& S = subs[blockIdx.y];
   const int v0 = blockIdx.z * kBackVec;
   const long long p0 = (long long)blockIdx.x * kBackPts;
@@ -400,7 +401,7 @@ k_nl_back_csr(const SubDev* __restrict__ subs, const long long* __restrict__ row
     } else {
       x.x = x.y = x.z = x.w = (T)0;
     }
-    Qs[q] = x;
+    Qs[sl * kBackRow + v] = x;
   }
   __syncthreads();
   T* yb = Yout + S.off_blk + (long long)v0 * S.nd;
@@ -413,7 +414,7 @@ k_nl_back_csr(const SubDev* __restrict__ subs, const long long* __restrict__ row
     for (long long e = r0; e < r1; ++e) {
       const int sl = rslot[e];
       const T4 c = rchi[e];
-      const T4* qq = Qs + sl * kBackVec;
+      const T4* qq = Qs + sl * kBackRow;
 #pragma unroll
       for (int v = 0; v < kBackVec; ++v) {
         const T4 q = qq[v];
@@ -442,7 +443,7 @@ void launch_nl_back_csr(const SubDev* d_subs, int n_sub, long long max_nd, int m
                         const long long* row_ptr, const int* rslot, const typename Vec4<T>::type* rchi,
                         const double* P, T* Yout, const StepCoef* coef, int step, cudaStream_t st) {
   if (max_slots == 0) return;
-  const size_t smem = (size_t)max_slots * kBackVec * sizeof(typename Vec4<T>::type);
+  const size_t smem = (size_t)max_slots * kBackRow * sizeof(typename Vec4<T>::type);
   static size_t attr = 0;
   if (smem > 48 * 1024 && smem > attr) {
     cudaFuncSetAttribute(k_nl_back_csr<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);

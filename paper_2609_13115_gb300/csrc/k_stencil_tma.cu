@@ -179,7 +179,13 @@ k_stencil_tma(const SubDev* __restrict__ subs, const TmaJob* __restrict__ jobs, 
       uint64_t* bar = &full[slot];
       float* dst = ring + (size_t)slot * slot_floats;
       asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-      if (bytes == 0) {
+      // every box destination must be 128-byte aligned (the host sizes the slots so); a slot that
+      // is not is recorded and left unloaded instead of issuing the copy
+      const uint32_t a0 = smem_u32(dst);
+      const bool aligned = ((a0 | (a0 + kN0 * W * 4) | (a0 + (kN0 + TY) * W * 4) | (a0 + off_yp * 4) |
+                             (a0 + off_v * 4)) & 127u) == 0;
+      if (!aligned && atomicCAS(status, 0, XLS_EINVAL) == 0) status[1] = J.sub;
+      if (bytes == 0 || !aligned) {
         mbar_arrive(bar);
       } else {
         mbar_expect_tx(bar, bytes);
@@ -324,7 +330,59 @@ int tma_tile_rows(const SubDev& S) {
   return 0;
 }
 
-int tma_row_width(const SubDev& S) { return ((S.n[0] + 2 * kHaloX + 31) / 32) * 32; }
+// Shared-memory wavefronts of one plane's y-neighbour loads (16-byte loads of consecutive rows
+// at pitch W, nq threads per row, TY rows) by the four 8-lane phases of every warp: a phase
+// needs as many wavefronts as the most 16-byte chunks it puts into one bank group.
+static long long smem_wavefronts(int W, int nq, int TY) {
+  const int n = nq * TY;
+  long long waves = 0;
+  for (int w0 = 0; w0 < n; w0 += 32)
+    for (int ph = 0; ph < 4; ++ph) {
+      int per_bank[8] = {0, 0, 0, 0, 0, 0, 0, 0};   // 16-byte bank groups of a 128-byte line
+      int addr[8];
+      int k = 0;
+      for (int l = 0; l < 8; ++l) {
+        const int t = w0 + ph * 8 + l;
+        if (t >= n) break;
+        const int word = (t / nq) * W + kHaloX + 4 * (t % nq);
+        bool dup = false;
+        for (int j = 0; j < k; ++j) dup = dup || addr[j] == word;
+        if (dup) continue;
+        addr[k++] = word;
+        per_bank[(word / 4) % 8]++;
+      }
+      int m = 0;
+      for (int b = 0; b < 8; ++b) m = per_bank[b] > m ? per_bank[b] : m;
+      waves += m;
+    }
+  return waves;
+}
+
+// Row pitch of a plane slot: at least n_x + 16 (8 halo columns each side) and a multiple of 16
+// floats, so that with an even tile height every TMA box lands on a 128-byte aligned shared-memory
+// address (6 W, (6 + TY) W and (12 + TY) W floats are multiples of 32); among the pitches up to
+// 32 floats wider, the one whose y-loads need the fewest shared-memory wavefronts (columns beyond
+// the halo are out of range for the TMA box and cost no memory traffic).
+int tma_row_width(const SubDev& S) {
+  const int nq = S.n[0] / 4;
+  int ty = 0;
+  for (int t : {24, 16, 12, 8, 6})
+    if (nq * t <= kMaxThreads - 32 && (!S.periodic[1] || S.n[1] % t == 0)) {
+      ty = t;
+      break;
+    }
+  const int w0 = ((S.n[0] + 2 * kHaloX + 15) / 16) * 16;
+  int best = w0;
+  long long best_w = -1;
+  for (int W = w0; W <= w0 + 32 && W <= 256; W += 16) {
+    const long long f = ty ? smem_wavefronts(W, nq, ty) : 0;
+    if (best_w < 0 || f < best_w) {
+      best_w = f;
+      best = W;
+    }
+  }
+  return best;
+}
 
 size_t tma_smem_bytes(int TY, int W, int nx) {
   const size_t aux = ((size_t)(TY * nx) + 31) / 32 * 32;
@@ -335,6 +393,8 @@ bool tma_eligible(const SubDev& S) {
   const int W = tma_row_width(S);
   const int ty = tma_tile_rows(S);
   if (S.n[0] % 4 != 0 || W > 256 || ty == 0) return false;
+  // every box destination 128-byte aligned: 6 W, (6 + TY) W, (12 + TY) W floats multiples of 32
+  if ((6 * W) % 32 || ((6 + ty) * W) % 32 || ((12 + ty) * W) % 32) return false;
   return tma_smem_bytes(ty, W, S.n[0]) <= 200 * 1024;
 }
 
@@ -399,8 +459,8 @@ void launch_stencil_tma(const SubDev* d_subs, const TmaClass& cls, const CUtenso
   sw.wc = sw.wx[0] + sw.wy[0] + sw.wz[0];
   // row pitches of the common subdomain widths as compile-time constants (immediate offsets)
   switch (cls.W) {
-    case 64: launch_variant<64>(cls, smem, d_subs, d_maps, buf_in, buf_prev, Yout, coef, step, status, sw, st); break;
-    case 96: launch_variant<96>(cls, smem, d_subs, d_maps, buf_in, buf_prev, Yout, coef, step, status, sw, st); break;
+    case 80: launch_variant<80>(cls, smem, d_subs, d_maps, buf_in, buf_prev, Yout, coef, step, status, sw, st); break;
+    case 112: launch_variant<112>(cls, smem, d_subs, d_maps, buf_in, buf_prev, Yout, coef, step, status, sw, st); break;
     default: launch_variant<0>(cls, smem, d_subs, d_maps, buf_in, buf_prev, Yout, coef, step, status, sw, st);
   }
 }
