@@ -147,10 +147,9 @@ void launch_stencil(const SubDev* d_subs, int n_sub, const Plan& plan, const T* 
 // Set-up: for every projector slot (one atom in one subdomain, all of its periodic images) a
 // table of its grid points and the four chi values there, built once per Hamiltonian in FP64
 // and stored in the block's precision.  Per filter step: the projection launch
-// P[slot][l][v] = E_l dV sum_g chi_l(g) Y_v(g) (a CTA per slot and 64 vectors, a warp per 8
-// vectors, lanes over the table) and the back-projection launch Y_out[v][g] +=
-// scale sum_l chi_l(g) P[slot][l][v] (same mapping, atomic adds: a point lies in about two
-// spheres).
+// P[slot][l][v] = E_l dV sum_g chi_l(g) Y_v(g) (k_nl_project) and the back-projection launch
+// Y_out[v][g] += scale sum_l chi_l(g) P[slot][l][v] over the reverse table rows (k_nl_back_csr,
+// no atomics; k_nl_back is the atomic per-slot variant kept for reference runs).
 constexpr int kNlWarps = 8, kNlVec = 8;
 
 template <typename T>
@@ -250,71 +249,76 @@ k_proj_fill(const SubDev* __restrict__ subs, const ProjSlot* __restrict__ slots,
   }
 }
 
+// Projection P[slot][l][v] = E_l dV sum_g chi_l(g) Y_v(g).  A CTA takes one slot and a group of
+// kPV = 16 vectors; the grid runs group-major, so that the CTAs resident at any time read the
+// same 16-vector slice of every subdomain's block (a few tens of MB: it stays in L2 and each Y
+// element, shared by the about two spheres that contain its point, comes from DRAM once).  Warp w
+// takes vectors 8 (w & 1) .. +7 and every fourth 32-point chunk of the table from chunk w >> 1;
+// a lane two points at a time (16 loads in flight); lanes and warps are reduced at the end.
+constexpr int kPV = 16;
+
 template <typename T>
-__global__ void __launch_bounds__(kNlWarps * 32)
-k_nl_project(const SubDev* __restrict__ subs, const ProjSlot* __restrict__ slots, const int* __restrict__ idx,
-             const typename Vec4<T>::type* __restrict__ chi, const T* __restrict__ Y, double* __restrict__ P) {
+__global__ void __launch_bounds__(256)
+k_nl_project(const SubDev* __restrict__ subs, const ProjSlot* __restrict__ slots, int n_slot,
+             const int* __restrict__ idx, const typename Vec4<T>::type* __restrict__ chi, const T* __restrict__ Y,
+             double* __restrict__ P) {
   using T4 = typename Vec4<T>::type;
-  constexpr int kChunk = 512;
-  __shared__ int s_idx[kChunk];
-  __shared__ T4 s_chi[kChunk];
-  const ProjSlot& A = slots[blockIdx.x];
+  __shared__ T red[4][kPV * 4];
+  const int slot = blockIdx.x % n_slot, grp = blockIdx.x / n_slot;
+  const ProjSlot& A = slots[slot];
   const SubDev& S = subs[A.sub];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int v0 = (blockIdx.y * kNlWarps + warp) * kNlVec;
-  const int nv = max(0, min(kNlVec, S.ns - v0));
-  T acc[4][kNlVec];
+  const int vh = warp & 1, ph = warp >> 1;
+  const int v0 = grp * kPV + vh * 8;
+  const int nv = max(0, min(8, S.ns - v0));
+  if (grp * kPV >= S.ns) return;   // uniform per CTA
+  T acc[4][8];
 #pragma unroll
   for (int l = 0; l < 4; ++l)
 #pragma unroll
-    for (int v = 0; v < kNlVec; ++v) acc[l][v] = (T)0;
+    for (int v = 0; v < 8; ++v) acc[l][v] = (T)0;
   const T* yb = Y + S.off_blk + (long long)v0 * S.nd;
-  for (int c0 = 0; c0 < A.pt_n; c0 += kChunk) {
-    const int cn = min(kChunk, A.pt_n - c0);
-    __syncthreads();
-    for (int p = threadIdx.x; p < cn; p += blockDim.x) {
-      s_idx[p] = idx[A.pt_off + c0 + p];
-      s_chi[p] = chi[A.pt_off + c0 + p];
-    }
-    __syncthreads();
-    if (nv == 0) continue;
-    for (int p = lane; p < cn; p += 64) {
-      // two points per lane per iteration: 16 independent loads in flight
-      const bool two = p + 32 < cn;
-      const int g0 = s_idx[p], g1 = two ? s_idx[p + 32] : g0;
-      const T4 c = s_chi[p];
-      T4 d = s_chi[two ? p + 32 : p];
+  const int* ib = idx + A.pt_off;
+  const T4* cb = chi + A.pt_off;
+  if (nv > 0)
+    for (int p = ph * 32 + lane; p < A.pt_n; p += 256) {
+      const bool two = p + 128 < A.pt_n;
+      const int g0 = ib[p], g1 = two ? ib[p + 128] : g0;
+      const T4 c = cb[p];
+      T4 d = cb[two ? p + 128 : p];
       if (!two) { d.x = (T)0; d.y = (T)0; d.z = (T)0; d.w = (T)0; }
-      T y0[kNlVec], y1[kNlVec];
+      T y0[8], y1[8];
 #pragma unroll
-      for (int v = 0; v < kNlVec; ++v) {
+      for (int v = 0; v < 8; ++v) {
         y0[v] = (v < nv) ? yb[(long long)v * S.nd + g0] : (T)0;
         y1[v] = (v < nv) ? yb[(long long)v * S.nd + g1] : (T)0;
       }
 #pragma unroll
-      for (int v = 0; v < kNlVec; ++v) {
+      for (int v = 0; v < 8; ++v) {
         acc[0][v] += c.x * y0[v] + d.x * y1[v];
         acc[1][v] += c.y * y0[v] + d.y * y1[v];
         acc[2][v] += c.z * y0[v] + d.z * y1[v];
         acc[3][v] += c.w * y0[v] + d.w * y1[v];
       }
     }
-  }
-  if (nv == 0) return;
 #pragma unroll
   for (int l = 0; l < 4; ++l)
 #pragma unroll
-    for (int v = 0; v < kNlVec; ++v) {
+    for (int v = 0; v < 8; ++v) {
       T s = acc[l][v];
 #pragma unroll
       for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-      acc[l][v] = s;
+      if (lane == 0) red[ph][vh * 32 + l * 8 + v] = s;
     }
-  if (lane == 0) {
-    double* pa = P + S.off_proj + (long long)(blockIdx.x - S.slot_lo) * 4 * S.ns;
-    for (int v = 0; v < nv; ++v)
-#pragma unroll
-      for (int l = 0; l < 4; ++l) pa[l * S.ns + v0 + v] = (double)acc[l][v] * A.E[l] * S.dV;
+  __syncthreads();
+  if (threadIdx.x < kPV * 4) {
+    const int h = threadIdx.x / 32, l = (threadIdx.x / 8) % 4, v = threadIdx.x % 8;
+    const int vg = grp * kPV + h * 8 + v;
+    if (vg < S.ns) {
+      const T s = red[0][threadIdx.x] + red[1][threadIdx.x] + red[2][threadIdx.x] + red[3][threadIdx.x];
+      double* pa = P + S.off_proj + (long long)(slot - S.slot_lo) * 4 * S.ns;
+      pa[l * S.ns + vg] = (double)s * A.E[l] * S.dV;
+    }
   }
 }
 
@@ -405,25 +409,45 @@ k_nl_back_csr(const SubDev* __restrict__ subs, const long long* __restrict__ row
   }
   __syncthreads();
   T* yb = Yout + S.off_blk + (long long)v0 * S.nd;
-  for (long long g = p0 + threadIdx.x; g < min(S.nd, p0 + kBackPts); g += blockDim.x) {
-    const long long r0 = row_ptr[S.off_pt + g], r1 = row_ptr[S.off_pt + g + 1];
-    if (r0 == r1) continue;
-    T acc[kBackVec];
+  const long long end = min(S.nd, p0 + kBackPts);
+  // two points per thread per iteration; the read half of the read-modify-write is issued before
+  // the table rows are walked, so that both latencies overlap
+  for (long long g = p0 + threadIdx.x; g < end; g += 2 * blockDim.x) {
+    const long long gB = g + blockDim.x;
+    const bool hasB = gB < end;
+    const long long rA0 = row_ptr[S.off_pt + g], rA1 = row_ptr[S.off_pt + g + 1];
+    const long long rB0 = hasB ? row_ptr[S.off_pt + gB] : 0, rB1 = hasB ? row_ptr[S.off_pt + gB + 1] : 0;
+    T yA[kBackVec], yB[kBackVec];
 #pragma unroll
-    for (int v = 0; v < kBackVec; ++v) acc[v] = (T)0;
-    for (long long e = r0; e < r1; ++e) {
+    for (int v = 0; v < kBackVec; ++v) {
+      yA[v] = (v < nv && rA1 > rA0) ? yb[(long long)v * S.nd + g] : (T)0;
+      yB[v] = (v < nv && rB1 > rB0) ? yb[(long long)v * S.nd + gB] : (T)0;
+    }
+    for (long long e = rA0; e < rA1; ++e) {
       const int sl = rslot[e];
       const T4 c = rchi[e];
       const T4* qq = Qs + sl * kBackRow;
 #pragma unroll
       for (int v = 0; v < kBackVec; ++v) {
         const T4 q = qq[v];
-        acc[v] += c.x * q.x + c.y * q.y + c.z * q.z + c.w * q.w;
+        yA[v] += c.x * q.x + c.y * q.y + c.z * q.z + c.w * q.w;
+      }
+    }
+    for (long long e = rB0; e < rB1; ++e) {
+      const int sl = rslot[e];
+      const T4 c = rchi[e];
+      const T4* qq = Qs + sl * kBackRow;
+#pragma unroll
+      for (int v = 0; v < kBackVec; ++v) {
+        const T4 q = qq[v];
+        yB[v] += c.x * q.x + c.y * q.y + c.z * q.z + c.w * q.w;
       }
     }
 #pragma unroll
-    for (int v = 0; v < kBackVec; ++v)
-      if (v < nv) yb[(long long)v * S.nd + g] += acc[v];
+    for (int v = 0; v < kBackVec; ++v) {
+      if (v < nv && rA1 > rA0) yb[(long long)v * S.nd + g] = yA[v];
+      if (v < nv && rB1 > rB0) yb[(long long)v * S.nd + gB] = yB[v];
+    }
   }
 }
 
@@ -468,8 +492,8 @@ template <typename T>
 void launch_nl_project(const SubDev* d_subs, const ProjSlot* d_slots, int n_slot, const int* idx,
                        const typename Vec4<T>::type* chi, int max_ns, const T* Y, double* P, cudaStream_t st) {
   if (n_slot == 0) return;
-  dim3 grid(n_slot, (max_ns + kNlWarps * kNlVec - 1) / (kNlWarps * kNlVec));
-  k_nl_project<T><<<grid, kNlWarps * 32, 0, st>>>(d_subs, d_slots, idx, chi, Y, P);
+  const int groups = (max_ns + kPV - 1) / kPV;
+  k_nl_project<T><<<n_slot * groups, 256, 0, st>>>(d_subs, d_slots, n_slot, idx, chi, Y, P);
 }
 
 template <typename T>
