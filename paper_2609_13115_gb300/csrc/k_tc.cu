@@ -36,6 +36,7 @@ constexpr long long kSpin = 1LL << 26;  // bounded mbarrier waits
 // MMAs added into one accumulator.  The Gram kernels therefore read their accumulators out every
 // kFlush K tiles (12 * kFlush MMAs) into FP32 partial sums with round-to-nearest adds.
 constexpr int kFlush = 4;
+constexpr int kFlushGram = 8;   // flush period of the batched Gram (k_gram_tc): 96 MMAs per accumulator
 
 __device__ __forceinline__ uint32_t su32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
@@ -97,6 +98,20 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float v[16]) {
 #pragma unroll
   for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
 }
+
+// 32 lanes x 32 bit, 32 consecutive columns per thread (no wait: the caller issues
+// tcgen05.wait::ld after overlapping other loads)
+__device__ __forceinline__ void tmem_ld32_nowait(uint32_t taddr, uint32_t r[32]) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+      "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];\n"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
+        "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]),
+        "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]),
+        "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+      : "r"(taddr));
+}
+__device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
 
 // Instruction descriptor, kind::f16: D = F32 (bits 4-5 = 1), A = B = BF16 (bits 7-9, 10-12 = 1),
 // A major (bit 15), B K-major (bit 16 = 0), N >> 3 at bits 17-22, M >> 4 at bits 24-28.
@@ -212,19 +227,26 @@ k_gram_tc(const SubDev* __restrict__ subs, const GramJob* __restrict__ jobs, con
     const bool ok = bar_wait(&acc_full[b], (p >> 1) & 1);
     tc_fence_after();
     if (!ok) atomicExch(&s_fail, 1);
-    for (int c0 = 0; c0 < nj16; c0 += 16) {
-      float v[16];
-      tmem_ld16(tmem + ((uint32_t)(lg * 32) << 16) + (uint32_t)(b * 256 + out_m * 128 + c0), v);
+    for (int c0 = 0; c0 < nj16; c0 += 32) {
+      // the previous partial sums are loaded while the accumulator columns come out of TMEM
+      float4 q[8];
+      if (ok && p > 0)
+#pragma unroll
+        for (int u = 0; u < 8; ++u)
+          q[u] = (c0 + 4 * u < nj16) ? *reinterpret_cast<const float4*>(wrow + c0 + 4 * u) : make_float4(0.f, 0.f, 0.f, 0.f);
+      uint32_t r[32];
+      tmem_ld32_nowait(tmem + ((uint32_t)(lg * 32) << 16) + (uint32_t)(b * 256 + out_m * 128 + c0), r);
+      tmem_wait_ld();
       if (ok) {
 #pragma unroll
-        for (int u = 0; u < 16; u += 4) {
-          float4* dst = reinterpret_cast<float4*>(wrow + c0 + u);
-          float4 o = make_float4(v[u], v[u + 1], v[u + 2], v[u + 3]);
+        for (int u = 0; u < 8; ++u) {
+          if (c0 + 4 * u >= nj16) break;
+          float4 o = make_float4(__uint_as_float(r[4 * u]), __uint_as_float(r[4 * u + 1]), __uint_as_float(r[4 * u + 2]),
+                                 __uint_as_float(r[4 * u + 3]));
           if (p > 0) {
-            const float4 q = *dst;
-            o.x += q.x; o.y += q.y; o.z += q.z; o.w += q.w;
+            o.x += q[u].x; o.y += q[u].y; o.z += q[u].z; o.w += q[u].w;
           }
-          *dst = o;
+          *reinterpret_cast<float4*>(wrow + c0 + 4 * u) = o;
         }
       }
     }
@@ -240,38 +262,49 @@ k_gram_tc(const SubDev* __restrict__ subs, const GramJob* __restrict__ jobs, con
       if (it >= kStages && !bar_wait(&empty[st], ((it / kStages) - 1) & 1)) { atomicExch(&s_fail, 1); break; }
       const long long k0 = (long long)(J.kt0 + it) * kKT;
       const uint32_t stage = sbase + st * kGramStage;
-      for (int q = threadIdx.x; q < nrows * 8; q += kProducers) {
+      // up to 12 items (row, 8-element chunk) per thread: all global loads of the tile are issued
+      // before any is split and stored, so that their latencies overlap
+      constexpr int kItems = 12;
+      float4 a[kItems], b[kItems];
+#pragma unroll
+      for (int u = 0; u < kItems; ++u) {
+        const int q = threadIdx.x + u * kProducers;
+        a[u] = make_float4(0.f, 0.f, 0.f, 0.f);
+        b[u] = a[u];
+        if (q >= nrows * 8) continue;
         const int row = q >> 3, c = q & 7;
-        const float* src;
-        int grow;
-        uint32_t thi, tlo;
-        int r;
-        if (row < 128) {                       // A: rows i0 + r of Psi_f
-          r = row; grow = i0 + r; src = f; thi = stage; tlo = stage + kTile;
-        } else if (row < 128 + rowsB1) {       // B1: rows j0 + r of Psi_f
-          r = row - 128; grow = j0 + r; src = f; thi = stage + 2 * kTile; tlo = stage + 3 * kTile;
-        } else {                               // B2: rows j0 + r of H Psi_f
-          r = row - 128 - rowsB1; grow = j0 + r; src = hf; thi = stage + 4 * kTile; tlo = stage + 5 * kTile;
-        }
-        const bool valid = (row < 128) ? (grow < ns) : (r < nj);
-        float4 a = make_float4(0.f, 0.f, 0.f, 0.f), b = a;
+        const bool isA = row < 128, isB1 = !isA && row < 128 + rowsB1;
+        const int r = isA ? row : (isB1 ? row - 128 : row - 128 - rowsB1);
+        const int grow = isA ? i0 + r : j0 + r;
+        const bool valid = isA ? (grow < ns) : (r < nj);
         const long long kk = k0 + c * 8;
         if (valid && kk < S.nd) {
-          const float4* p = reinterpret_cast<const float4*>(src + (long long)grow * S.nd + kk);
-          a = p[0];
-          b = p[1];
+          const float4* p = reinterpret_cast<const float4*>((isA || isB1 ? f : hf) + (long long)grow * S.nd + kk);
+          a[u] = p[0];
+          b[u] = p[1];
         }
+      }
+#pragma unroll
+      for (int u = 0; u < kItems; ++u) {
+        const int q = threadIdx.x + u * kProducers;
+        if (q >= nrows * 8) continue;
+        const int row = q >> 3, c = q & 7;
+        const bool isA = row < 128, isB1 = !isA && row < 128 + rowsB1;
+        const int r = isA ? row : (isB1 ? row - 128 : row - 128 - rowsB1);
+        const int grow = isA ? i0 + r : j0 + r;
+        const bool valid = isA ? (grow < ns) : (r < nj);
+        const uint32_t thi = isA ? stage : (isB1 ? stage + 2 * kTile : stage + 4 * kTile);
         float sc = 1.f;
-        if (kFp16 && valid) sc = ldexpf(1.f, (src == hf ? ex_hf : ex_f)[S.off_state + grow]);
+        if (kFp16 && valid) sc = ldexpf(1.f, (isA || isB1 ? ex_f : ex_hf)[S.off_state + grow]);
         uint4 hi, lo;
-        split8<kFp16>(a, b, sc, hi, lo);
+        split8<kFp16>(a[u], b[u], sc, hi, lo);
         const uint32_t off = kmaj_off(r, c);
         sts128(thi + off, hi);
-        sts128(tlo + off, lo);
+        sts128(thi + kTile + off, lo);
       }
       fence_async_smem();
       bar_arrive(&full[st]);
-      if (it % kFlush == kFlush - 1 || it == nkt - 1) flush(it / kFlush);
+      if (it % kFlushGram == kFlushGram - 1 || it == nkt - 1) flush(it / kFlushGram);
     }
   } else if (lane == 0) {
     // ---------------- MMA issuer
@@ -280,8 +313,8 @@ k_gram_tc(const SubDev* __restrict__ subs, const GramJob* __restrict__ jobs, con
     for (int it = 0; it < nkt; ++it) {
       const int st = it % kStages;
       if (!bar_wait(&full[st], (it / kStages) & 1)) { ok = false; break; }
-      const int per = it / kFlush, buf = per & 1;
-      if (it % kFlush == 0 && per >= 2 && !bar_wait(&acc_empty[buf], ((per >> 1) - 1) & 1)) { ok = false; break; }
+      const int per = it / kFlushGram, buf = per & 1;
+      if (it % kFlushGram == 0 && per >= 2 && !bar_wait(&acc_empty[buf], ((per >> 1) - 1) & 1)) { ok = false; break; }
       tc_fence_after();
       const uint32_t acc_base = tmem + (uint32_t)(buf * 256);
       const uint32_t stage = sbase + st * kGramStage;
@@ -291,7 +324,7 @@ k_gram_tc(const SubDev* __restrict__ subs, const GramJob* __restrict__ jobs, con
 #pragma unroll
       for (int ks = 0; ks < kKT / 16; ++ks) {
         const uint32_t ko = ks * 32;           // 16 bf16 = 32 bytes along K inside the swizzle row
-        const int acc = (it % kFlush > 0 || ks > 0) ? 1 : 0;
+        const int acc = (it % kFlushGram > 0 || ks > 0) ? 1 : 0;
         const uint64_t ah = sdesc(a_hi + ko, 16, 1024), al = sdesc(a_lo + ko, 16, 1024);
         mma_bf16(acc_base + 0, ah, sdesc(b1_hi + ko, 16, 1024), idesc, acc);
         mma_bf16(acc_base + 0, ah, sdesc(b1_lo + ko, 16, 1024), idesc, 1);
@@ -301,7 +334,7 @@ k_gram_tc(const SubDev* __restrict__ subs, const GramJob* __restrict__ jobs, con
         mma_bf16(acc_base + 128, al, sdesc(b2_hi + ko, 16, 1024), idesc, 1);
       }
       mma_commit(&empty[st]);
-      if (it % kFlush == kFlush - 1 || it == nkt - 1) mma_commit(&acc_full[buf]);
+      if (it % kFlushGram == kFlushGram - 1 || it == nkt - 1) mma_commit(&acc_full[buf]);
     }
     if (!ok) atomicExch(&s_fail, 1);
   }
@@ -575,37 +608,58 @@ k_rotate_tc(const SubDev* __restrict__ subs, const RotJob* __restrict__ jobs, co
       if (it >= kStages && !bar_wait(&empty[st], ((it / kStages) - 1) & 1)) { atomicExch(&s_fail, 1); break; }
       const int k0 = it * kKT;
       const uint32_t stage = sbase + st * kRotStage;
-      // A: 64 k-rows x 128 grid points, chunks of 8 points (MN-major)
-      for (int q = threadIdx.x; q < 64 * 16; q += kProducers) {
+      // A: 64 k-rows x 128 grid points, chunks of 8 points (MN-major), 4 items per thread; B:
+      // n16 rows x 64 k of Y^T hi / lo (already split), K-major, up to 8 items per thread.  All
+      // global loads of the tile are issued before the stores, so that their latencies overlap.
+      float4 a[4], b[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const int q = threadIdx.x + u * kProducers;
         const int k = q >> 4, c16 = q & 15;     // c16: chunk of 8 points within 128
         const int kk = k0 + k;
         const long long g = g0 + c16 * 8;
-        float4 a = make_float4(0.f, 0.f, 0.f, 0.f), b = a;
-        float sc = 1.f;
+        a[u] = make_float4(0.f, 0.f, 0.f, 0.f);
+        b[u] = a[u];
         if (kk < ns && g < S.nd) {
           const float4* p = reinterpret_cast<const float4*>(f + (long long)kk * S.nd + g);
-          a = p[0];
-          b = p[1];
-          if (kFp16) sc = ldexpf(1.f, ex_f[S.off_state + kk]);
+          a[u] = p[0];
+          b[u] = p[1];
         }
+      }
+      uint4 yh[8], yl[8];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) {
+        const int q = threadIdx.x + u * kProducers;
+        const int n = q >> 3, c = q & 7;
+        yh[u] = make_uint4(0, 0, 0, 0);
+        yl[u] = yh[u];
+        if (q < n16 * 8 && n < ns) {
+          const long long e = yoff + (long long)n * kpad_max + k0 + c * 8;
+          yh[u] = *reinterpret_cast<const uint4*>(Yhi + e);
+          yl[u] = *reinterpret_cast<const uint4*>(Ylo + e);
+        }
+      }
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const int q = threadIdx.x + u * kProducers;
+        const int k = q >> 4, c16 = q & 15;
+        const int kk = k0 + k;
+        float sc = 1.f;
+        if (kFp16 && kk < ns) sc = ldexpf(1.f, ex_f[S.off_state + kk]);
         uint4 hi, lo;
-        split8<kFp16>(a, b, sc, hi, lo);
+        split8<kFp16>(a[u], b[u], sc, hi, lo);
         const uint32_t off = mnmaj_off(c16 >> 3, k, c16 & 7);
         sts128(stage + off, hi);
         sts128(stage + kTile + off, lo);
       }
-      // B: n16 rows x 64 k of Y^T hi / lo (already split), K-major
-      for (int q = threadIdx.x; q < n16 * 8; q += kProducers) {
+#pragma unroll
+      for (int u = 0; u < 8; ++u) {
+        const int q = threadIdx.x + u * kProducers;
+        if (q >= n16 * 8) continue;
         const int n = q >> 3, c = q & 7;
-        uint4 hi = make_uint4(0, 0, 0, 0), lo = hi;
-        if (n < ns) {
-          const long long e = yoff + (long long)n * kpad_max + k0 + c * 8;
-          hi = *reinterpret_cast<const uint4*>(Yhi + e);
-          lo = *reinterpret_cast<const uint4*>(Ylo + e);
-        }
         const uint32_t off = kmaj_off(n, c);
-        sts128(stage + 2 * kTile + off, hi);
-        sts128(stage + 2 * kTile + 256 * 128 + off, lo);
+        sts128(stage + 2 * kTile + off, yh[u]);
+        sts128(stage + 2 * kTile + 256 * 128 + off, yl[u]);
       }
       fence_async_smem();
       bar_arrive(&full[st]);
