@@ -199,7 +199,7 @@ k_gram_tc(const SubDev* __restrict__ subs, const GramJob* __restrict__ jobs, con
   const int nkt = J.kt1 - J.kt0;
   if (threadIdx.x == 0) {
     for (int s = 0; s < kStages; ++s) {
-      bar_init(&full[s], kProducers);
+      bar_init(&full[s], kProducers / 2);   // one producer group per stage
       bar_init(&empty[s], 1);
     }
     for (int b = 0; b < 2; ++b) {
@@ -222,18 +222,14 @@ k_gram_tc(const SubDev* __restrict__ subs, const GramJob* __restrict__ jobs, con
   // them to the CTA's FP32 partial sums with round-to-nearest adds (the first period stores).
   const int lg = warp & 3, out_m = warp >> 2, prow = lg * 32 + lane;
   float* wrow = work + (long long)blockIdx.x * 2 * 128 * 128 + (long long)out_m * 128 * 128 + (long long)prow * 128;
+  // The first period stores, later periods add with fire-and-forget vector reductions in L2
+  // (round-to-nearest FP32 adds, in program order per address: one thread owns each row).
   auto flush = [&](int p) {
     const int b = p & 1;
     const bool ok = bar_wait(&acc_full[b], (p >> 1) & 1);
     tc_fence_after();
     if (!ok) atomicExch(&s_fail, 1);
     for (int c0 = 0; c0 < nj16; c0 += 32) {
-      // the previous partial sums are loaded while the accumulator columns come out of TMEM
-      float4 q[8];
-      if (ok && p > 0)
-#pragma unroll
-        for (int u = 0; u < 8; ++u)
-          q[u] = (c0 + 4 * u < nj16) ? *reinterpret_cast<const float4*>(wrow + c0 + 4 * u) : make_float4(0.f, 0.f, 0.f, 0.f);
       uint32_t r[32];
       tmem_ld32_nowait(tmem + ((uint32_t)(lg * 32) << 16) + (uint32_t)(b * 256 + out_m * 128 + c0), r);
       tmem_wait_ld();
@@ -241,12 +237,11 @@ k_gram_tc(const SubDev* __restrict__ subs, const GramJob* __restrict__ jobs, con
 #pragma unroll
         for (int u = 0; u < 8; ++u) {
           if (c0 + 4 * u >= nj16) break;
-          float4 o = make_float4(__uint_as_float(r[4 * u]), __uint_as_float(r[4 * u + 1]), __uint_as_float(r[4 * u + 2]),
-                                 __uint_as_float(r[4 * u + 3]));
-          if (p > 0) {
-            o.x += q[u].x; o.y += q[u].y; o.z += q[u].z; o.w += q[u].w;
-          }
-          *reinterpret_cast<float4*>(wrow + c0 + 4 * u) = o;
+          const float4 o = make_float4(__uint_as_float(r[4 * u]), __uint_as_float(r[4 * u + 1]),
+                                       __uint_as_float(r[4 * u + 2]), __uint_as_float(r[4 * u + 3]));
+          float4* dst = reinterpret_cast<float4*>(wrow + c0 + 4 * u);
+          if (p == 0) *dst = o;
+          else atomicAdd(dst, o);
         }
       }
     }
@@ -254,57 +249,66 @@ k_gram_tc(const SubDev* __restrict__ subs, const GramJob* __restrict__ jobs, con
     bar_arrive(&acc_empty[b]);
   };
   if (warp < 8) {
-    // ---------------- producers
+    // ---------------- producers: two groups of four warps, group g fills stage g with the K tiles
+    // it = g (mod 2), so that two tiles are in flight; both groups flush every period (group 0 the
+    // D1 accumulator rows, group 1 the D2 rows)
+    const int grp = warp >> 2, gt = threadIdx.x & 127;
     const int rowsB1 = diag ? 0 : nj16;
     const int nrows = 128 + rowsB1 + nj16;     // A rows, B1 rows, B2 rows
-    for (int it = 0; it < nkt; ++it) {
-      const int st = it % kStages;
-      if (it >= kStages && !bar_wait(&empty[st], ((it / kStages) - 1) & 1)) { atomicExch(&s_fail, 1); break; }
-      const long long k0 = (long long)(J.kt0 + it) * kKT;
-      const uint32_t stage = sbase + st * kGramStage;
-      // up to 12 items (row, 8-element chunk) per thread: all global loads of the tile are issued
-      // before any is split and stored, so that their latencies overlap
-      constexpr int kItems = 12;
-      float4 a[kItems], b[kItems];
+    bool go = true;
+    for (int p = 0; p * kFlushGram < nkt; ++p) {
+      const int t_end = min((p + 1) * kFlushGram, nkt);
+      for (int it = p * kFlushGram + grp; go && it < t_end; it += 2) {
+        if (it >= 2 && !bar_wait(&empty[grp], ((it >> 1) - 1) & 1)) { atomicExch(&s_fail, 1); go = false; break; }
+        const long long k0 = (long long)(J.kt0 + it) * kKT;
+        const uint32_t stage = sbase + grp * kGramStage;
+        // rounds of 8 items (row, 8-element chunk) per thread: the global loads of a round are
+        // issued before any item is split and stored, so that their latencies overlap
+        constexpr int kItems = 8;
+        for (int q0 = 0; q0 < nrows * 8; q0 += 128 * kItems) {
+          float4 a[kItems], b[kItems];
 #pragma unroll
-      for (int u = 0; u < kItems; ++u) {
-        const int q = threadIdx.x + u * kProducers;
-        a[u] = make_float4(0.f, 0.f, 0.f, 0.f);
-        b[u] = a[u];
-        if (q >= nrows * 8) continue;
-        const int row = q >> 3, c = q & 7;
-        const bool isA = row < 128, isB1 = !isA && row < 128 + rowsB1;
-        const int r = isA ? row : (isB1 ? row - 128 : row - 128 - rowsB1);
-        const int grow = isA ? i0 + r : j0 + r;
-        const bool valid = isA ? (grow < ns) : (r < nj);
-        const long long kk = k0 + c * 8;
-        if (valid && kk < S.nd) {
-          const float4* p = reinterpret_cast<const float4*>((isA || isB1 ? f : hf) + (long long)grow * S.nd + kk);
-          a[u] = p[0];
-          b[u] = p[1];
+          for (int u = 0; u < kItems; ++u) {
+            const int q = q0 + gt + u * 128;
+            a[u] = make_float4(0.f, 0.f, 0.f, 0.f);
+            b[u] = a[u];
+            if (q >= nrows * 8) continue;
+            const int row = q >> 3, c = q & 7;
+            const bool isA = row < 128, isB1 = !isA && row < 128 + rowsB1;
+            const int r = isA ? row : (isB1 ? row - 128 : row - 128 - rowsB1);
+            const int grow = isA ? i0 + r : j0 + r;
+            const bool valid = isA ? (grow < ns) : (r < nj);
+            const long long kk = k0 + c * 8;
+            if (valid && kk < S.nd) {
+              const float4* src = reinterpret_cast<const float4*>((isA || isB1 ? f : hf) + (long long)grow * S.nd + kk);
+              a[u] = src[0];
+              b[u] = src[1];
+            }
+          }
+#pragma unroll
+          for (int u = 0; u < kItems; ++u) {
+            const int q = q0 + gt + u * 128;
+            if (q >= nrows * 8) continue;
+            const int row = q >> 3, c = q & 7;
+            const bool isA = row < 128, isB1 = !isA && row < 128 + rowsB1;
+            const int r = isA ? row : (isB1 ? row - 128 : row - 128 - rowsB1);
+            const int grow = isA ? i0 + r : j0 + r;
+            const bool valid = isA ? (grow < ns) : (r < nj);
+            const uint32_t thi = isA ? stage : (isB1 ? stage + 2 * kTile : stage + 4 * kTile);
+            float sc = 1.f;
+            if (kFp16 && valid) sc = ldexpf(1.f, (isA || isB1 ? ex_f : ex_hf)[S.off_state + grow]);
+            uint4 hi, lo;
+            split8<kFp16>(a[u], b[u], sc, hi, lo);
+            const uint32_t off = kmaj_off(r, c);
+            sts128(thi + off, hi);
+            sts128(thi + kTile + off, lo);
+          }
         }
+        fence_async_smem();
+        bar_arrive(&full[grp]);
       }
-#pragma unroll
-      for (int u = 0; u < kItems; ++u) {
-        const int q = threadIdx.x + u * kProducers;
-        if (q >= nrows * 8) continue;
-        const int row = q >> 3, c = q & 7;
-        const bool isA = row < 128, isB1 = !isA && row < 128 + rowsB1;
-        const int r = isA ? row : (isB1 ? row - 128 : row - 128 - rowsB1);
-        const int grow = isA ? i0 + r : j0 + r;
-        const bool valid = isA ? (grow < ns) : (r < nj);
-        const uint32_t thi = isA ? stage : (isB1 ? stage + 2 * kTile : stage + 4 * kTile);
-        float sc = 1.f;
-        if (kFp16 && valid) sc = ldexpf(1.f, (isA || isB1 ? ex_f : ex_hf)[S.off_state + grow]);
-        uint4 hi, lo;
-        split8<kFp16>(a[u], b[u], sc, hi, lo);
-        const uint32_t off = kmaj_off(r, c);
-        sts128(thi + off, hi);
-        sts128(thi + kTile + off, lo);
-      }
-      fence_async_smem();
-      bar_arrive(&full[st]);
-      if (it % kFlushGram == kFlushGram - 1 || it == nkt - 1) flush(it / kFlushGram);
+      if (!go) break;
+      flush(p);
     }
   } else if (lane == 0) {
     // ---------------- MMA issuer
