@@ -288,7 +288,7 @@ constexpr int kTriThreads = 128;
 // (a) shifts: FP32 Sturm bisection for every eigenvalue index; clusters of close eigenvalues.
 // vecs per subdomain: d [0,n), e [n,2n), tau [2n,3n), lam32 [3n,4n), cluster starts [4n,5n] (as doubles),
 // [5n+1] cluster count, [5n+2] |T| estimate.
-__global__ void __launch_bounds__(128)
+__global__ void __launch_bounds__(1024)
 k_tri_bisect(const SubDev* __restrict__ subs, double* vecs) {
   const SubDev& S = subs[blockIdx.x];
   const int n = S.ns;
@@ -321,14 +321,29 @@ k_tri_bisect(const SubDev* __restrict__ subs, double* vecs) {
     s_pivmin = (float)fmax(1e-30, 1e-30 * emax2);
   }
   __syncthreads();
-  for (int i = threadIdx.x; i < n; i += blockDim.x) {
+  // multisection: four threads per eigenvalue index evaluate the counts at the three quarter
+  // points of its interval (and one spare), the interval shrinks to the quarter where the count
+  // passes the index (two bits per round)
+  const int sub = threadIdx.x & 3;
+  const unsigned gmask = 0xFu << (threadIdx.x & 28);   // the four lanes of this group
+  const int groups = blockDim.x >> 2;
+  for (int i = threadIdx.x >> 2; i < n; i += groups) {  // uniform inside a group
     float lo = s_gl, hi = s_gu;
-    for (int it = 0; it < 48; ++it) {
-      const float mid = 0.5f * (lo + hi);
-      if (mid == lo || mid == hi) break;
-      if (sturm_count_f(df, e2f, n, mid, s_pivmin) > i) hi = mid; else lo = mid;
+    for (int it = 0; it < 26; ++it) {
+      const float w = hi - lo;
+      const float pt = lo + 0.25f * (float)(sub + 1) * w;      // sub = 3: the upper end (count known)
+      const int cnt = sub < 3 ? sturm_count_f(df, e2f, n, pt, s_pivmin) : 0x7fffffff;
+      // first quarter point whose count exceeds i
+      const int c1 = __shfl_sync(gmask, cnt, 0, 4), c2 = __shfl_sync(gmask, cnt, 1, 4),
+                c3 = __shfl_sync(gmask, cnt, 2, 4);
+      const int q = c1 > i ? 0 : (c2 > i ? 1 : (c3 > i ? 2 : 3));
+      const float nlo = q == 0 ? lo : lo + 0.25f * (float)q * w;
+      const float nhi = q == 3 ? hi : lo + 0.25f * (float)(q + 1) * w;
+      if (!(nlo > lo || nhi < hi) || nlo >= nhi) break;   // no longer divisible in FP32 (uniform per group)
+      lo = nlo;
+      hi = nhi;
     }
-    lam32[i] = 0.5 * ((double)lo + (double)hi);
+    if (sub == 0) lam32[i] = 0.5 * ((double)lo + (double)hi);
   }
   __syncthreads();
   if (threadIdx.x == 0) {
@@ -544,6 +559,75 @@ k_backtransform(const SubDev* __restrict__ subs, const double* __restrict__ Am, 
   }
 }
 
+// ---- 2./6. blocked triangular solves: CTA = (8 right-hand-side columns, subdomain) ----------
+// lower: X = L^-1 B (B[i][c] = trans ? Bm[c][i] : Bm[i][c]); upper: X = L^-T B.  The 8 columns
+// live in shared memory; rows are taken in blocks of 32: one warp solves the block's diagonal
+// part (4 lanes per column split the dot product), then all warps subtract the block's
+// contribution from the remaining rows.  FP64 throughput, not latency, bounds it; the per-column
+// kernel above (warp per column) remains for reference runs with XLS_EIG=single.
+constexpr int kTrsmCols = 8, kTrsmRB = 32;
+
+template <bool kUpper>
+__global__ void __launch_bounds__(256)
+k_trsm_blk(const SubDev* __restrict__ subs, const double* __restrict__ Lm, const double* Bm, int trans, double* Xm) {
+  const SubDev& S = subs[blockIdx.y];
+  const int n = S.ns;
+  const int c0 = blockIdx.x * kTrsmCols;
+  if (c0 >= n) return;
+  const int nc = min(kTrsmCols, n - c0);
+  const double* L = Lm + S.off_ss;
+  const double* B = Bm + S.off_ss;
+  double* X = Xm + S.off_ss;
+  extern __shared__ double xs[];   // [n][kTrsmCols]
+  for (int q = threadIdx.x; q < n * kTrsmCols; q += blockDim.x) {
+    const int i = q / kTrsmCols, c = q % kTrsmCols;
+    xs[q] = c < nc ? (trans ? B[(long long)(c0 + c) * n + i] : B[(long long)i * n + c0 + c]) : 0.0;
+  }
+  __syncthreads();
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int nblk = (n + kTrsmRB - 1) / kTrsmRB;
+  for (int bb = 0; bb < nblk; ++bb) {
+    // rows of this block: lower from the top, upper from the bottom
+    const int r0 = kUpper ? max(0, n - (bb + 1) * kTrsmRB) : bb * kTrsmRB;
+    const int r1 = kUpper ? n - bb * kTrsmRB : min(n, r0 + kTrsmRB);
+    if (warp == 0) {
+      const int c = lane >> 2, part = lane & 3;   // 8 columns x 4 partial sums
+      for (int t = 0; t < r1 - r0; ++t) {
+        const int i = kUpper ? r1 - 1 - t : r0 + t;
+        double acc = 0.0;
+        if (!kUpper) {
+          for (int k = r0 + part; k < i; k += 4) acc += L[(long long)i * n + k] * xs[k * kTrsmCols + c];
+        } else {
+          for (int k = i + 1 + part; k < r1; k += 4) acc += L[(long long)k * n + i] * xs[k * kTrsmCols + c];
+        }
+        acc += __shfl_xor_sync(0xffffffffu, acc, 1);
+        acc += __shfl_xor_sync(0xffffffffu, acc, 2);
+        if (part == 0) xs[i * kTrsmCols + c] = (xs[i * kTrsmCols + c] - acc) / L[(long long)i * n + i];
+        __syncwarp();
+      }
+    }
+    __syncthreads();
+    // remaining rows: lower r1..n-1, upper 0..r0-1
+    const int u0 = kUpper ? 0 : r1, u1 = kUpper ? r0 : n;
+    for (int q = threadIdx.x; q < (u1 - u0) * kTrsmCols; q += blockDim.x) {
+      const int i = u0 + q / kTrsmCols, c = q % kTrsmCols;
+      double acc = 0.0;
+      if (!kUpper) {
+        const double* Li = L + (long long)i * n;
+        for (int k = r0; k < r1; ++k) acc += Li[k] * xs[k * kTrsmCols + c];
+      } else {
+        for (int k = r0; k < r1; ++k) acc += L[(long long)k * n + i] * xs[k * kTrsmCols + c];
+      }
+      xs[i * kTrsmCols + c] -= acc;
+    }
+    __syncthreads();
+  }
+  for (int q = threadIdx.x; q < n * kTrsmCols; q += blockDim.x) {
+    const int i = q / kTrsmCols, c = q % kTrsmCols;
+    if (c < nc) X[(long long)i * n + c0 + c] = xs[q];
+  }
+}
+
 template <int RC>
 static void trsm_rc(bool upper, dim3 gt, const SubDev* d_subs, const double* L, const double* B, int trans, double* X,
                     cudaStream_t st) {
@@ -551,7 +635,18 @@ static void trsm_rc(bool upper, dim3 gt, const SubDev* d_subs, const double* L, 
   else k_trsm<false, RC><<<gt, 256, 0, st>>>(d_subs, L, B, trans, X);
 }
 static void trsm(bool upper, int max_ns, dim3 gt, const SubDev* d_subs, const double* L, const double* B, int trans,
-                 double* X, cudaStream_t st) {
+                 double* X, cudaStream_t st, bool blocked = true) {
+  if (blocked) {
+    dim3 g((max_ns + kTrsmCols - 1) / kTrsmCols, gt.y);
+    const size_t smem = (size_t)max_ns * kTrsmCols * sizeof(double);
+    if (smem > 48 * 1024) {
+      cudaFuncSetAttribute(k_trsm_blk<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      cudaFuncSetAttribute(k_trsm_blk<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    }
+    if (upper) k_trsm_blk<true><<<g, 256, smem, st>>>(d_subs, L, B, trans, X);
+    else k_trsm_blk<false><<<g, 256, smem, st>>>(d_subs, L, B, trans, X);
+    return;
+  }
   const int rc = (max_ns + 31) / 32;
   if (rc <= 2) trsm_rc<2>(upper, gt, d_subs, L, B, trans, X, st);
   else if (rc <= 4) trsm_rc<4>(upper, gt, d_subs, L, B, trans, X, st);
@@ -588,12 +683,13 @@ void launch_eig(const SubDev* d_subs, int n_sub, int max_ns, double* Ms, double*
   } else if (smem_ok(k_cholesky<true>, mat)) k_cholesky<true><<<n_sub, 512, mat, st>>>(d_subs, Ms, status);
   else k_cholesky<false><<<n_sub, 512, 0, st>>>(d_subs, Ms, status);
   dim3 gt((max_ns + 7) / 8, n_sub);   // 8 warps (columns) per CTA
-  trsm(false, max_ns, gt, d_subs, Ms, Hs, 0, W, st);   // W = L^-1 H_s
-  trsm(false, max_ns, gt, d_subs, Ms, W, 1, Hs, st);   // A = L^-1 W^T
+  trsm(false, max_ns, gt, d_subs, Ms, Hs, 0, W, st, cluster);   // W = L^-1 H_s
+  trsm(false, max_ns, gt, d_subs, Ms, W, 1, Hs, st, cluster);   // A = L^-1 W^T
   if (cluster && launch_tridiag_cluster(d_subs, n_sub, max_ns, Hs, vecs, st)) {
   } else if (smem_ok(k_tridiag<true>, mat + vbytes)) k_tridiag<true><<<n_sub, 512, mat + vbytes, st>>>(d_subs, Hs, vecs, max_ns);
   else k_tridiag<false><<<n_sub, 512, vbytes, st>>>(d_subs, Hs, vecs, max_ns);
-  k_tri_bisect<<<n_sub, 128, 2 * max_ns * sizeof(float), st>>>(d_subs, vecs);
+  k_tri_bisect<<<n_sub, std::min(1024, ((4 * max_ns + 31) / 32) * 32), 2 * max_ns * sizeof(float), st>>>(d_subs,
+                                                                                                      vecs);
   {
     // vector stage: 32 threads per CTA with shared-memory work arrays where they fit, one CTA per
     // 32 clusters of a subdomain; else 128 threads per CTA on the global scratch
@@ -610,7 +706,7 @@ void launch_eig(const SubDev* d_subs, int n_sub, int max_ns, double* Ms, double*
   }
   dim3 gb((max_ns + 31) / 32, n_sub);
   k_backtransform<<<gb, 256, (max_ns + 256) * sizeof(double), st>>>(d_subs, Hs, vecs, W);
-  trsm(true, max_ns, gt, d_subs, Ms, W, 0, Y, st);     // Y = L^-T Z
+  trsm(true, max_ns, gt, d_subs, Ms, W, 0, Y, st, cluster);     // Y = L^-T Z
 }
 
 size_t eig_scratch_doubles(int n_sub, int max_ns) { return (size_t)n_sub * kTriThreads * 3 * max_ns; }
