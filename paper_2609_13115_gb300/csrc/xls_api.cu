@@ -82,6 +82,30 @@ struct xls_grid_s {
   std::vector<double> atom_pos;
   std::vector<int> atom_sp;
   std::vector<xls_species> species;
+  // concurrent halves (XLS_CONCURRENT=1): the subdomains split in two views whose passes run on
+  // two streams, half 1's filter beside half 0's projection, eigensolve and rotation
+  struct View {
+    int first = 0, n = 0;
+    const SubDev* ds = nullptr;           // descriptors of the view (d_subs + first)
+    StepCoef* coef = nullptr;             // per-subdomain arrays offset to the view
+    double* bounds = nullptr;
+    const CUtensorMap* maps = nullptr;
+    Plan plan;                            // generic stencil
+    std::vector<TmaClass> tcls;           // TMA stencil classes, jobs relative to `first`
+    GramPlan gplan;
+    RotPlan rplan;
+    int slot_off = 0, n_slot = 0;         // projector slots (global indices)
+    long long ss_off = 0, ss_n = 0;       // subspace-matrix range (doubles)
+    double* eig_scr = nullptr;
+    int max_ns = 0;
+    long long max_nd = 0;
+    cudaStream_t st = nullptr;
+    cudaEvent_t ev = nullptr;
+  };
+  View full;
+  View halves[2];
+  bool concurrent = false;
+  cudaEvent_t ev_fork = nullptr, ev_mid = nullptr;
   // learned start: descriptors, correction, SAD and their atom tables
   float* ls_X = nullptr;
   float* ls_y = nullptr;
@@ -259,7 +283,7 @@ void h_step(xls_grid g, bool one, const T* yin, const T* yprev, T* yout, int ste
   double* P = one ? g->P1 : g->P;
   const int mns = one ? 1 : g->max_ns;
   const T* V = (sizeof(T) == 8) ? (const T*)g->V : (const T*)g->Vf;
-  { ProfScope ps(g, K_NLPROJ); launch_nl_project<T>(ds, g->d_slots, g->n_slot, g->d_pidx, chi_table<T>(g), mns, yin, P, g->st); }
+  { ProfScope ps(g, K_NLPROJ); launch_nl_project<T>(ds, g->d_slots, 0, g->n_slot, g->d_pidx, chi_table<T>(g), mns, yin, P, g->st); }
   { ProfScope ps(g, K_STENCIL); launch_stencil<T>(ds, g->n_sub, pl, yin, yprev, yout, V, g->coef, step, g->st); }
   { ProfScope ps(g, K_NLBACK);
     launch_nl_back_csr<T>(ds, g->n_sub, g->max_nd, mns, g->max_slots, g->d_rptr, g->d_rslot, rchi_table<T>(g), P, yout,
@@ -267,41 +291,52 @@ void h_step(xls_grid g, bool one, const T* yin, const T* yprev, T* yout, int ste
   g->launches += (g->n_slot ? 3 : 1);
 }
 
-// same as h_step on the main view, with the blocks given by index (the TMA stencil addresses
-// its input through the tensor maps of that block)
+// the whole grid as a view on the grid's current stream (graph capture may substitute a
+// capture stream for the legacy stream)
+xls_grid_s::View& fv(xls_grid g) {
+  g->full.st = g->st;
+  return g->full;
+}
+
+// same as h_step on a view of the main blocks, with the blocks given by index (the TMA stencil
+// addresses its input through the tensor maps of that block)
 template <typename T>
-void h_step_main(xls_grid g, int bin, int bprev, int bout, int step) {
+void h_step_main(xls_grid g, const xls_grid_s::View& v, int bin, int bprev, int bout, int step) {
   T* yin = (T*)g->blk[bin];
   T* yprev = bprev >= 0 ? (T*)g->blk[bprev] : nullptr;
   T* yout = (T*)g->blk[bout];
+  const T* V = (sizeof(T) == 8) ? (const T*)g->V : (const T*)g->Vf;
+  { ProfScope ps(g, K_NLPROJ);
+    launch_nl_project<T>(g->d_subs, g->d_slots, v.slot_off, v.n_slot, g->d_pidx, chi_table<T>(g), v.max_ns, yin, g->P,
+                         v.st); }
   if (sizeof(T) == 4 && g->use_tma) {
-    { ProfScope ps(g, K_NLPROJ); launch_nl_project<T>(g->d_subs, g->d_slots, g->n_slot, g->d_pidx, chi_table<T>(g), g->max_ns, yin, g->P, g->st); }
-    {
-      ProfScope ps(g, K_STENCIL);
-      for (const TmaClass& c : g->tcls)
-        launch_stencil_tma(g->d_subs, c, g->d_maps, bin, bprev, (float*)yout, g->coef, step, g->status, g->st);
-    }
-    { ProfScope ps(g, K_NLBACK);
-      launch_nl_back_csr<T>(g->d_subs, g->n_sub, g->max_nd, g->max_ns, g->max_slots, g->d_rptr, g->d_rslot,
-                            rchi_table<T>(g), g->P, yout, g->coef, step, g->st); }
-    g->launches += (g->n_slot ? 2 : 0) + (int)g->tcls.size();
-    return;
+    ProfScope ps(g, K_STENCIL);
+    for (const TmaClass& c : v.tcls)
+      launch_stencil_tma(v.ds, c, v.maps, bin, bprev, (float*)yout, v.coef, step, g->status, v.st);
+    g->launches += (int)v.tcls.size();
+  } else {
+    ProfScope ps(g, K_STENCIL);
+    launch_stencil<T>(v.ds, v.n, v.plan, yin, yprev, yout, V, v.coef, step, v.st);
+    g->launches++;
   }
-  h_step<T>(g, false, yin, yprev, yout, step);
+  { ProfScope ps(g, K_NLBACK);
+    launch_nl_back_csr<T>(v.ds, v.n, v.max_nd, v.max_ns, g->max_slots, g->d_rptr, g->d_rslot, rchi_table<T>(g), g->P,
+                          yout, v.coef, step, v.st); }
+  g->launches += (v.n_slot ? 2 : 0);
 }
 
 constexpr int kUnitStep = kMaxDegree - 1;
 
 // filter the current block in place of the two spare buffers; returns the index of Psi_f
 template <typename T>
-int run_filter(xls_grid g, int m) {
-  launch_filter_coef(g->n_sub, g->bounds, m, g->coef, g->st);
+int run_filter(xls_grid g, const xls_grid_s::View& v, int m) {
+  launch_filter_coef(v.n, v.bounds, m, v.coef, v.st);
   g->launches++;
   int ia = g->cur, ib = (g->cur + 1) % 3;
-  h_step_main<T>(g, ia, -1, ib, 1);
+  h_step_main<T>(g, v, ia, -1, ib, 1);
   int yk = ib, yprev = ia;
   for (int k = 2; k <= m; ++k) {
-    h_step_main<T>(g, yk, yprev, yprev, k);
+    h_step_main<T>(g, v, yk, yprev, yprev, k);
     const int t = yk;
     yk = yprev;
     yprev = t;
@@ -317,54 +352,56 @@ int other(int a, int b) {
 }
 
 template <typename T>
-void projection(xls_grid g, int f) {
+void projection(xls_grid g, const xls_grid_s::View& v, int f) {
   const int hf = other(f, f == 0 ? 1 : 0);
-  h_step_main<T>(g, f, -1, hf, kUnitStep);
+  h_step_main<T>(g, v, f, -1, hf, kUnitStep);
   if (sizeof(T) == 4 && g->use_tc_gram) {
     ProfScope ps(g, K_GRAM);
-    launch_gram_tc(g->d_subs, g->n_sub, g->max_ns, g->gplan, g->prec == XLS_MIXED_FP16, (const float*)g->blk[f],
-                   (const float*)g->blk[hf], g->Ms, g->Hs, g->status, g->st);
+    launch_gram_tc(v.ds, v.n, v.max_ns, v.gplan, g->prec == XLS_MIXED_FP16, (const float*)g->blk[f],
+                   (const float*)g->blk[hf], g->Ms, g->Hs, g->status, v.st);
     g->launches += g->prec == XLS_MIXED_FP16 ? 3 : 2;
     return;
   }
-  cudaMemsetAsync(g->Ms, 0, g->tot_ss * sizeof(double), g->st);
-  cudaMemsetAsync(g->Hs, 0, g->tot_ss * sizeof(double), g->st);
-  { ProfScope ps(g, K_GRAM); launch_gram<T>(g->d_subs, g->n_sub, g->max_ns, g->max_nd, blkp<T>(g, f), blkp<T>(g, hf), g->Ms, g->Hs, g->st); }
+  cudaMemsetAsync(g->Ms + v.ss_off, 0, v.ss_n * sizeof(double), v.st);
+  cudaMemsetAsync(g->Hs + v.ss_off, 0, v.ss_n * sizeof(double), v.st);
+  { ProfScope ps(g, K_GRAM);
+    launch_gram<T>(v.ds, v.n, v.max_ns, v.max_nd, blkp<T>(g, f), blkp<T>(g, hf), g->Ms, g->Hs, v.st); }
   g->launches++;
 }
 
-void eigensolve(xls_grid g) {
-  cudaMemcpyAsync(g->Lb, g->Ms, g->tot_ss * sizeof(double), cudaMemcpyDeviceToDevice, g->st);
-  cudaMemcpyAsync(g->Ab, g->Hs, g->tot_ss * sizeof(double), cudaMemcpyDeviceToDevice, g->st);
+void eigensolve(xls_grid g, const xls_grid_s::View& v) {
+  cudaMemcpyAsync(g->Lb + v.ss_off, g->Ms + v.ss_off, v.ss_n * sizeof(double), cudaMemcpyDeviceToDevice, v.st);
+  cudaMemcpyAsync(g->Ab + v.ss_off, g->Hs + v.ss_off, v.ss_n * sizeof(double), cudaMemcpyDeviceToDevice, v.st);
   { ProfScope ps(g, K_EIG);
-    launch_eig(g->d_subs, g->n_sub, g->max_ns, g->Lb, g->Ab, g->Y, g->W, g->lam, g->vecs, g->status, g->eig_scr, g->R,
-               g->eig_cluster, g->st); }
+    launch_eig(v.ds, v.n, v.max_ns, g->Lb, g->Ab, g->Y, g->W, g->lam, g->vecs, g->status, v.eig_scr, g->R,
+               g->eig_cluster, v.st); }
   g->launches += 8;
 }
 
+// rotation, interior weights and the next pass's (a, a0); returns the block now holding Psi
 template <typename T>
-void rotation(xls_grid g, int f) {
+int rotation(xls_grid g, const xls_grid_s::View& v, int f) {
   const int out = other(f, f == 0 ? 1 : 0);
   if (sizeof(T) == 4 && g->use_tc_rot) {
     ProfScope ps(g, K_ROTATE);
-    launch_rotate_tc(g->d_subs, g->n_sub, g->max_ns, g->rplan, g->gplan, g->prec == XLS_MIXED_FP16, !g->use_tc_gram,
-                     (const float*)g->blk[f], g->Y, (float*)g->blk[out], g->status, g->st);
+    launch_rotate_tc(v.ds, v.n, v.max_ns, v.rplan, v.gplan, g->prec == XLS_MIXED_FP16, !g->use_tc_gram,
+                     (const float*)g->blk[f], g->Y, (float*)g->blk[out], g->status, v.st);
     g->launches += 2;
   } else {
     ProfScope ps(g, K_ROTATE);
-    launch_rotate<T>(g->d_subs, g->n_sub, g->max_ns, g->max_nd, blkp<T>(g, f), g->Y, blkp<T>(g, out), g->st);
+    launch_rotate<T>(v.ds, v.n, v.max_ns, v.max_nd, blkp<T>(g, f), g->Y, blkp<T>(g, out), v.st);
   }
-  { ProfScope ps(g, K_OTHER); launch_core_weights<T>(g->d_subs, g->n_sub, g->max_ns, blkp<T>(g, out), g->cw, g->st); }
-  launch_bounds_from_ritz(g->d_subs, g->n_sub, g->lam, g->bounds, g->st);
+  { ProfScope ps(g, K_OTHER); launch_core_weights<T>(v.ds, v.n, v.max_ns, blkp<T>(g, out), g->cw, v.st); }
+  launch_bounds_from_ritz(v.ds, v.n, g->lam, v.bounds, v.st);
   g->launches += 3;
-  g->cur = out;
+  return out;
 }
 
 template <typename T>
 xls_status bootstrap_bounds(xls_grid g) {
   // (a, a0) from the Ritz values of the unfiltered block; b was set by the Lanczos bound
-  projection<T>(g, g->cur);
-  eigensolve(g);
+  projection<T>(g, fv(g), g->cur);
+  eigensolve(g, fv(g));
   launch_bounds_from_ritz(g->d_subs, g->n_sub, g->lam, g->bounds, g->st);
   g->launches++;
   return check_status(g);
@@ -383,19 +420,57 @@ void stage_event(xls_grid g, int i) {
   else cudaEventRecord(g->ev[i], g->st);
 }
 
-// one CheFSI pass (filter, projection, eigensolve, rotation) on the grid's stream
+// one CheFSI pass (filter, projection, eigensolve, rotation).  Sequential on the grid's stream
+// (stage events when timed), or, with concurrent halves and profiling off, the two halves on two
+// streams forked from and joined back into the grid's stream: the GPU then overlaps the
+// eigensolve (few SMs, FP64 latency) of one half with the filter of the other.
 template <typename T>
 void one_pass(xls_grid g, int degree, bool timed) {
   g->launches = 0;
   g->pused = 0;
+  if (g->concurrent && !g->profiling) {
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    cudaStreamIsCapturing(g->st, &cs);
+    const bool cap = cs == cudaStreamCaptureStatusActive;
+    if (timed) stage_event(g, 0);
+    if (cap) cudaEventRecordWithFlags(g->ev_fork, g->st, cudaEventRecordDefault);
+    else cudaEventRecord(g->ev_fork, g->st);
+    // half 0: filter, then projection / eigensolve / rotation; half 1 starts its filter when half
+    // 0's filter is done, so that half 0's subspace stages run beside half 1's filter
+    auto& h0 = g->halves[0];
+    auto& h1 = g->halves[1];
+    cudaStreamWaitEvent(h0.st, g->ev_fork, 0);
+    const int f = run_filter<T>(g, h0, degree);
+    cudaEventRecord(g->ev_mid, h0.st);
+    projection<T>(g, h0, f);
+    eigensolve(g, h0);
+    rotation<T>(g, h0, f);
+    cudaEventRecord(h0.ev, h0.st);
+    cudaStreamWaitEvent(h1.st, g->ev_mid, 0);
+    run_filter<T>(g, h1, degree);
+    projection<T>(g, h1, f);
+    eigensolve(g, h1);
+    const int out = rotation<T>(g, h1, f);
+    cudaEventRecord(h1.ev, h1.st);
+    cudaStreamWaitEvent(g->st, h0.ev, 0);
+    cudaStreamWaitEvent(g->st, h1.ev, 0);
+    g->cur = out;
+    if (timed) {   // stages overlap: the whole pass is reported as the filter stage
+      stage_event(g, 1);
+      stage_event(g, 2);
+      stage_event(g, 3);
+      stage_event(g, 4);
+    }
+    return;
+  }
   if (timed) stage_event(g, 0);
-  const int f = run_filter<T>(g, degree);
+  const int f = run_filter<T>(g, fv(g), degree);
   if (timed) stage_event(g, 1);
-  projection<T>(g, f);
+  projection<T>(g, fv(g), f);
   if (timed) stage_event(g, 2);
-  eigensolve(g);
+  eigensolve(g, fv(g));
   if (timed) stage_event(g, 3);
-  rotation<T>(g, f);
+  g->cur = rotation<T>(g, fv(g), f);
   if (timed) stage_event(g, 4);
 }
 
@@ -469,12 +544,12 @@ xls_status stage(xls_grid g, int which, int degree, const double* bounds) {
     case 1: {
       if (bounds) XLS_TRY(upload_bounds(g, bounds));
       else if (!g->have_ritz) XLS_TRY(bootstrap_bounds<T>(g));
-      g->cur = run_filter<T>(g, degree);
+      g->cur = run_filter<T>(g, fv(g), degree);
       break;
     }
-    case 2: projection<T>(g, g->cur); break;
-    case 3: eigensolve(g); break;
-    case 4: rotation<T>(g, g->cur); g->have_ritz = true; break;
+    case 2: projection<T>(g, fv(g), g->cur); break;
+    case 3: eigensolve(g, fv(g)); break;
+    case 4: g->cur = rotation<T>(g, fv(g), g->cur); g->have_ritz = true; break;
     default: return fail(XLS_EINVAL, "stage must be 1..4");
   }
   return check_status(g);
@@ -546,6 +621,153 @@ void atom_images(xls_grid g, int a, const double R[3], const xls_species& sp, in
 }
 
 }  // namespace
+
+// ---- views --------------------------------------------------------------------------------------
+
+void set_view_slots(xls_grid g, xls_grid_s::View& v) {
+  v.slot_off = v.n ? g->subs[v.first].slot_lo : 0;
+  v.n_slot = 0;
+  for (int a = v.first; a < v.first + v.n; ++a) v.n_slot += g->subs[a].slot_n;
+}
+
+// TMA stencil classes of subdomains [first, first + n): equal (x-points / 4, rows per tile, row
+// width, spacing); jobs index the subdomains relative to `first`
+xls_status build_tma_classes(xls_grid g, int first, int n, std::vector<TmaClass>& out) {
+  std::vector<std::vector<int>> members;
+  std::vector<TmaClass> cls;
+  for (int a = first; a < first + n; ++a) {
+    const SubDev& S = g->subs[a];
+    const int nq = S.n[0] / 4, ty = tma_tile_rows(S), W = tma_row_width(S);
+    size_t k = 0;
+    for (; k < cls.size(); ++k)
+      if (cls[k].nq == nq && cls[k].TY == ty && cls[k].W == W && cls[k].h[0] == S.h[0] && cls[k].h[1] == S.h[1] &&
+          cls[k].h[2] == S.h[2])
+        break;
+    if (k == cls.size()) {
+      TmaClass c;
+      c.nq = nq; c.TY = ty; c.W = W;
+      c.h[0] = S.h[0]; c.h[1] = S.h[1]; c.h[2] = S.h[2];
+      cls.push_back(c);
+      members.emplace_back();
+    }
+    members[k].push_back(a);
+  }
+  for (size_t k = 0; k < cls.size(); ++k) {
+    std::vector<TmaJob> jobs;
+    std::vector<int> off(1, 0);
+    for (int a : members[k]) {
+      const SubDev& S = g->subs[a];
+      const int nyt = (S.n[1] + cls[k].TY - 1) / cls[k].TY;
+      jobs.push_back(TmaJob{a - first, nyt, cls[k].W, cls[k].TY});
+      off.push_back(off.back() + nyt * S.ns);
+    }
+    cls[k].n_jobs = (int)jobs.size();
+    cls[k].total = off.back();
+    XLS_TRY(g->alloc(&cls[k].d_jobs, jobs.size() * sizeof(TmaJob)));
+    XLS_TRY(g->alloc(&cls[k].d_job_off, off.size() * sizeof(int)));
+    XLS_CUDA(cudaMemcpy(cls[k].d_jobs, jobs.data(), jobs.size() * sizeof(TmaJob), cudaMemcpyHostToDevice));
+    XLS_CUDA(cudaMemcpy(cls[k].d_job_off, off.data(), off.size() * sizeof(int), cudaMemcpyHostToDevice));
+  }
+  out = cls;
+  return XLS_OK;
+}
+
+// tensor-core Gram and rotation jobs of subdomains [first, first + n) (indices relative to
+// `first`); the exponent and split-Y arrays are indexed by state and shared with `shared`
+xls_status build_tc_plans(xls_grid g, int first, int n, GramPlan& gp, RotPlan& rp, const GramPlan* gshared,
+                          const RotPlan* rshared) {
+  int groups = 0;
+  int max_ns = 0;
+  for (int a = first; a < first + n; ++a) {
+    const int nt = (g->subs[a].ns + 127) / 128;
+    groups += nt * (nt + 1) / 2;
+    max_ns = std::max(max_ns, g->subs[a].ns);
+  }
+  // K split so that the grid fills the GPU
+  const int kchunks = std::max(1, (4 * 152 + groups - 1) / groups);
+  std::vector<GramJob> jobs;
+  std::vector<int> gfirst, gn;
+  for (int a = first; a < first + n; ++a) {
+    const SubDev& S = g->subs[a];
+    const int nt = (S.ns + 127) / 128;
+    const int nkt = (int)((S.nd + 63) / 64);
+    const int kc = std::min(kchunks, nkt);
+    for (int I = 0; I < nt; ++I)
+      for (int J = I; J < nt; ++J) {
+        gfirst.push_back((int)jobs.size());
+        for (int c = 0; c < kc; ++c)
+          jobs.push_back(GramJob{a - first, I, J, (int)((long long)nkt * c / kc), (int)((long long)nkt * (c + 1) / kc), 0});
+        gn.push_back(kc);
+      }
+  }
+  gp.n_jobs = (int)jobs.size();
+  gp.n_groups = (int)gfirst.size();
+  XLS_TRY(g->alloc(&gp.d_jobs, jobs.size() * sizeof(GramJob)));
+  XLS_TRY(g->alloc(&gp.d_grp_first, gfirst.size() * sizeof(int)));
+  XLS_TRY(g->alloc(&gp.d_grp_n, gn.size() * sizeof(int)));
+  XLS_TRY(g->alloc(&gp.d_work, jobs.size() * 2 * 128 * 128 * sizeof(float)));
+  if (gshared) {
+    gp.d_ex_f = gshared->d_ex_f;
+    gp.d_ex_hf = gshared->d_ex_hf;
+  } else {
+    XLS_TRY(g->alloc(&gp.d_ex_f, g->tot_states * sizeof(int)));
+    XLS_TRY(g->alloc(&gp.d_ex_hf, g->tot_states * sizeof(int)));
+  }
+  std::vector<RotJob> rj;
+  for (int a = first; a < first + n; ++a)
+    for (int t = 0; t < (int)((g->subs[a].nd + 127) / 128); ++t) rj.push_back(RotJob{a - first, t});
+  rp.n_jobs = (int)rj.size();
+  rp.kpad_max = ((g->max_ns + 63) / 64) * 64;
+  XLS_TRY(g->alloc(&rp.d_jobs, rj.size() * sizeof(RotJob)));
+  if (rshared) {
+    rp.d_yhi = rshared->d_yhi;
+    rp.d_ylo = rshared->d_ylo;
+    rp.d_ex_y = rshared->d_ex_y;
+  } else {
+    XLS_TRY(g->alloc(&rp.d_yhi, (size_t)g->tot_states * rp.kpad_max * sizeof(uint16_t)));
+    XLS_TRY(g->alloc(&rp.d_ylo, (size_t)g->tot_states * rp.kpad_max * sizeof(uint16_t)));
+    XLS_TRY(g->alloc(&rp.d_ex_y, g->tot_states * sizeof(int)));
+  }
+  XLS_CUDA(cudaMemcpy(gp.d_jobs, jobs.data(), jobs.size() * sizeof(GramJob), cudaMemcpyHostToDevice));
+  XLS_CUDA(cudaMemcpy(gp.d_grp_first, gfirst.data(), gfirst.size() * sizeof(int), cudaMemcpyHostToDevice));
+  XLS_CUDA(cudaMemcpy(gp.d_grp_n, gn.data(), gn.size() * sizeof(int), cudaMemcpyHostToDevice));
+  XLS_CUDA(cudaMemcpy(rp.d_jobs, rj.data(), rj.size() * sizeof(RotJob), cudaMemcpyHostToDevice));
+  return XLS_OK;
+}
+
+// the descriptors, offsets and plans of subdomains [first, first + n) on stream st
+xls_status make_view(xls_grid g, int first, int n, cudaStream_t st, bool own_plans, xls_grid_s::View& v) {
+  v.first = first;
+  v.n = n;
+  v.ds = g->d_subs + first;
+  v.coef = g->coef + (size_t)first * kMaxDegree;
+  v.bounds = g->bounds + 3 * (size_t)first;
+  v.maps = g->d_maps ? g->d_maps + (size_t)first * kMapsPerSub : nullptr;
+  v.ss_off = g->subs[first].off_ss;
+  const SubDev& L = g->subs[first + n - 1];
+  v.ss_n = L.off_ss + (long long)L.ns * L.ns - v.ss_off;
+  v.max_ns = 0;
+  v.max_nd = 0;
+  for (int a = first; a < first + n; ++a) {
+    v.max_ns = std::max(v.max_ns, g->subs[a].ns);
+    v.max_nd = std::max(v.max_nd, g->subs[a].nd);
+  }
+  v.eig_scr = g->eig_scr + (size_t)first * (eig_scratch_doubles(g->n_sub, g->max_ns) / g->n_sub);
+  v.st = st;
+  if (own_plans) {
+    std::vector<SubDev> sub(g->subs.begin() + first, g->subs.begin() + first + n);
+    XLS_TRY(make_plan(g, sub, v.plan));
+    if (g->use_tma) XLS_TRY(build_tma_classes(g, first, n, v.tcls));
+    if (g->use_tc) XLS_TRY(build_tc_plans(g, first, n, v.gplan, v.rplan, &g->gplan, &g->rplan));
+  } else {
+    v.plan = g->plan;
+    v.tcls = g->tcls;
+    v.gplan = g->gplan;
+    v.rplan = g->rplan;
+  }
+  set_view_slots(g, v);
+  return XLS_OK;
+}
 
 // ---- SCF step on the global periodic grid ------------------------------------------------------
 xls_status scf_alloc(xls_grid g) {
@@ -950,6 +1172,43 @@ xls_status create_grid(const xls_cell* cell, const xls_dc* dc, int precision, si
       g->use_tc_rot = !(er && std::string(er) == "simt");
     }
   }
+  // views: the whole grid, and two halves of about equal work on streams of their own
+  if ((s = make_view(g, 0, g->n_sub, g->st, false, g->full)) != XLS_OK) {
+    xls_grid_destroy(g);
+    return s;
+  }
+  {
+    const char* env = std::getenv("XLS_CONCURRENT");
+    const bool want = env && std::string(env) == "1";
+    if (want && g->n_sub >= 2) {
+      double tot = 0.0, run = 0.0;
+      for (const SubDev& S : g->subs) tot += (double)S.nd * S.ns;
+      int split = 1;
+      double best = 1e300;
+      for (int k = 1; k < g->n_sub; ++k) {
+        run += (double)g->subs[k - 1].nd * g->subs[k - 1].ns;
+        if (std::fabs(2 * run - tot) < best) {
+          best = std::fabs(2 * run - tot);
+          split = k;
+        }
+      }
+      bool ok = true;
+      for (int h = 0; h < 2 && ok; ++h) {
+        ok = cudaStreamCreateWithFlags(&g->halves[h].st, cudaStreamNonBlocking) == cudaSuccess &&
+             cudaEventCreateWithFlags(&g->halves[h].ev, cudaEventDisableTiming) == cudaSuccess;
+        if (ok) ok = make_view(g, h ? split : 0, h ? g->n_sub - split : split, g->halves[h].st, true, g->halves[h]) ==
+                     XLS_OK;
+      }
+      ok = ok && cudaEventCreateWithFlags(&g->ev_fork, cudaEventDisableTiming) == cudaSuccess &&
+           cudaEventCreateWithFlags(&g->ev_mid, cudaEventDisableTiming) == cudaSuccess;
+      if (!ok) {
+        cudaGetLastError();
+        xls_grid_destroy(g);
+        return fail(XLS_ECUDA, "concurrent halves could not be set up");
+      }
+      g->concurrent = true;
+    }
+  }
   cudaMemset(g->status, 0, 2 * sizeof(int));
   cudaMemset(g->lz_b, 0, 16 * g->n_sub * sizeof(double));
   cudaMemset(g->cw, 0, g->tot_states * sizeof(double));
@@ -1195,6 +1454,12 @@ xls_status xls_grid_destroy(xls_grid g) {
   for (auto& e : g->pev) cudaEventDestroy(e);
   g->drop_graphs();
   if (g->cap_st) cudaStreamDestroy(g->cap_st);
+  for (auto& v : g->halves) {
+    if (v.st) cudaStreamDestroy(v.st);
+    if (v.ev) cudaEventDestroy(v.ev);
+  }
+  if (g->ev_fork) cudaEventDestroy(g->ev_fork);
+  if (g->ev_mid) cudaEventDestroy(g->ev_mid);
   if (g->store) cudaFreeHost(g->store);
   delete g;
   return XLS_OK;
@@ -1367,6 +1632,9 @@ xls_status xls_hamiltonian_set(xls_grid g, const double* veff, int veff_on_devic
     g->max_slots = 0;
     for (const SubDev& S : g->subs) g->max_slots = std::max(g->max_slots, S.slot_n);
   }
+  set_view_slots(g, g->full);
+  if (g->concurrent)
+    for (auto& v : g->halves) set_view_slots(g, v);
   // unit coefficients (plain H) for every subdomain, then the Lanczos bound b
   std::vector<double> bz(3 * g->n_sub, 1.0);
   for (int a = 0; a < g->n_sub; ++a) { bz[3 * a] = 2.0; bz[3 * a + 1] = 1.0; bz[3 * a + 2] = 0.0; }
@@ -1470,7 +1738,7 @@ xls_status xls_hamiltonian_apply(xls_grid g, int sub, int k, const double* x, do
     XLS_CUDA(cudaMalloc(&dtmp, n * sizeof(double)));
     XLS_CUDA(cudaMemcpyAsync(dtmp, x, n * sizeof(double), kin, g->st));
     launch_convert_f64_f32(dtmp, (float*)g->blk[in] + S.off_blk, n, g->st);
-    h_step_main<float>(g, in, -1, outb, kUnitStep);
+    h_step_main<float>(g, fv(g), in, -1, outb, kUnitStep);
     launch_convert_f32_f64((float*)g->blk[outb] + S.off_blk, dtmp, n, g->st);
     XLS_CUDA(cudaMemcpyAsync(y, dtmp, n * sizeof(double), kout, g->st));
     XLS_CUDA(cudaStreamSynchronize(g->st));

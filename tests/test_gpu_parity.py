@@ -519,3 +519,33 @@ def test_learned_start_matches_oracle():
     ref = learned.learned_start(w, theta).ravel()
     assert relerr(rho, ref) < 1e-4
     assert rho.min() >= 0.0 and abs(rho.sum() * np.prod(w.h) - w.n_electrons) < 1e-9
+
+
+@pytest.mark.parametrize("prec", [xls.XLS_FP64, xls.XLS_MIXED_FP16])
+def test_concurrent_halves_match_sequential(prec, monkeypatch):
+    """Passes whose two halves of subdomains run on two streams (XLS_CONCURRENT=1) give the Ritz
+    values, weights, bounds and density of the single-stream pass; both with graph replay."""
+    w = dirichlet20_workload()
+    V = pseudo.local_potential(w)
+    subs = dc.partition(w)
+    psi0 = _start_blocks(w, subs)
+    res = {}
+    for mode in ("concurrent", "sequential"):
+        monkeypatch.setenv("XLS_CONCURRENT", "1" if mode == "concurrent" else "0")
+        with make_grid(w, V, prec) as g:
+            for a in range(w.n_sub):
+                xls.xls_orbitals_set(g.h, a, psi0[a])
+            xls.xls_set_graphs(g.h, 1)
+            xls.xls_chefsi_batch(g.h, w.degree, 3)
+            xls.xls_chefsi_batch(g.h, w.degree, 1)
+            lam = [xls.xls_get_eigs(g.h, a, int(w.n_states[a])) for a in range(w.n_sub)]
+            rho = np.zeros(int(np.prod(w.n)))
+            mu = xls.xls_density(g.h, w.n_electrons, w.kT, rho)[0]
+            bnd = xls.xls_get_bounds(g.h, w.n_sub)
+        res[mode] = (lam, rho, mu, bnd)
+    tol = 1e-9 if prec == xls.XLS_FP64 else 2e-5
+    for a in range(w.n_sub):
+        np.testing.assert_allclose(res["concurrent"][0][a][0], res["sequential"][0][a][0], rtol=0, atol=tol)
+    assert relerr(res["concurrent"][1], res["sequential"][1]) < 10 * tol
+    assert abs(res["concurrent"][2] - res["sequential"][2]) < tol
+    np.testing.assert_allclose(res["concurrent"][3], res["sequential"][3], rtol=tol, atol=tol)
