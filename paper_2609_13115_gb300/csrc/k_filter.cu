@@ -250,25 +250,27 @@ k_proj_fill(const SubDev* __restrict__ subs, const ProjSlot* __restrict__ slots,
 }
 
 // Projection P[slot][l][v] = E_l dV sum_g chi_l(g) Y_v(g).  A CTA takes one slot and a group of
-// kPV = 16 vectors; the grid runs group-major, so that the CTAs resident at any time read the
-// same 16-vector slice of every subdomain's block (a few tens of MB: it stays in L2 and each Y
-// element, shared by the about two spheres that contain its point, comes from DRAM once).  Warp w
-// takes vectors 8 (w & 1) .. +7 and every fourth 32-point chunk of the table from chunk w >> 1;
-// a lane two points at a time (16 loads in flight); lanes and warps are reduced at the end.
-constexpr int kPV = 16;
+// kPV = 8 vectors; the grid runs group-major, so that the CTAs resident at any time read the
+// same 8-vector slice of every subdomain's block (tens of MB: it stays in L2 and each Y element,
+// shared by the about two spheres that contain its point, comes from DRAM about once).  Warp w
+// takes vectors 8 (w % kVH) .. +7 and every kPH-th 32-point chunk of the table from chunk
+// w / kVH; a lane two points at a time (16 loads in flight); lanes and warps are reduced at the
+// end.
+constexpr int kPV = 8;
+constexpr int kVH = kPV / 8, kPH = 8 / kVH;   // vector halves and point phases of the 8 warps
 
 template <typename T>
 __global__ void __launch_bounds__(256)
-k_nl_project(const SubDev* __restrict__ subs, const ProjSlot* __restrict__ slots, int n_slot,
+k_nl_project(const SubDev* __restrict__ subs, const ProjSlot* __restrict__ slots, int slot_off, int n_slot,
              const int* __restrict__ idx, const typename Vec4<T>::type* __restrict__ chi, const T* __restrict__ Y,
              double* __restrict__ P) {
   using T4 = typename Vec4<T>::type;
-  __shared__ T red[4][kPV * 4];
-  const int slot = blockIdx.x % n_slot, grp = blockIdx.x / n_slot;
+  __shared__ T red[kPH][kPV * 4];
+  const int slot = slot_off + (int)(blockIdx.x % n_slot), grp = blockIdx.x / n_slot;
   const ProjSlot& A = slots[slot];
   const SubDev& S = subs[A.sub];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int vh = warp & 1, ph = warp >> 1;
+  const int vh = warp % kVH, ph = warp / kVH;
   const int v0 = grp * kPV + vh * 8;
   const int nv = max(0, min(8, S.ns - v0));
   if (grp * kPV >= S.ns) return;   // uniform per CTA
@@ -281,11 +283,11 @@ k_nl_project(const SubDev* __restrict__ subs, const ProjSlot* __restrict__ slots
   const int* ib = idx + A.pt_off;
   const T4* cb = chi + A.pt_off;
   if (nv > 0)
-    for (int p = ph * 32 + lane; p < A.pt_n; p += 256) {
-      const bool two = p + 128 < A.pt_n;
-      const int g0 = ib[p], g1 = two ? ib[p + 128] : g0;
+    for (int p = ph * 32 + lane; p < A.pt_n; p += 64 * kPH) {
+      const bool two = p + 32 * kPH < A.pt_n;
+      const int g0 = ib[p], g1 = two ? ib[p + 32 * kPH] : g0;
       const T4 c = cb[p];
-      T4 d = cb[two ? p + 128 : p];
+      T4 d = cb[two ? p + 32 * kPH : p];
       if (!two) { d.x = (T)0; d.y = (T)0; d.z = (T)0; d.w = (T)0; }
       T y0[8], y1[8];
 #pragma unroll
@@ -315,7 +317,9 @@ k_nl_project(const SubDev* __restrict__ subs, const ProjSlot* __restrict__ slots
     const int h = threadIdx.x / 32, l = (threadIdx.x / 8) % 4, v = threadIdx.x % 8;
     const int vg = grp * kPV + h * 8 + v;
     if (vg < S.ns) {
-      const T s = red[0][threadIdx.x] + red[1][threadIdx.x] + red[2][threadIdx.x] + red[3][threadIdx.x];
+      T s = (T)0;
+#pragma unroll
+      for (int q = 0; q < kPH; ++q) s += red[q][threadIdx.x];
       double* pa = P + S.off_proj + (long long)(slot - S.slot_lo) * 4 * S.ns;
       pa[l * S.ns + vg] = (double)s * A.E[l] * S.dV;
     }
@@ -489,11 +493,11 @@ void launch_proj_table_fill(const SubDev* d_subs, const ProjSlot* d_slots, int n
 }
 
 template <typename T>
-void launch_nl_project(const SubDev* d_subs, const ProjSlot* d_slots, int n_slot, const int* idx,
+void launch_nl_project(const SubDev* d_subs, const ProjSlot* d_slots, int slot_off, int n_slot, const int* idx,
                        const typename Vec4<T>::type* chi, int max_ns, const T* Y, double* P, cudaStream_t st) {
   if (n_slot == 0) return;
   const int groups = (max_ns + kPV - 1) / kPV;
-  k_nl_project<T><<<n_slot * groups, 256, 0, st>>>(d_subs, d_slots, n_slot, idx, chi, Y, P);
+  k_nl_project<T><<<n_slot * groups, 256, 0, st>>>(d_subs, d_slots, slot_off, n_slot, idx, chi, Y, P);
 }
 
 template <typename T>
@@ -509,8 +513,8 @@ void launch_nl_back(const SubDev* d_subs, const ProjSlot* d_slots, int n_slot, c
   template void launch_proj_table_count<T>(const SubDev*, const ProjSlot*, int, const AtomImg*, int*, cudaStream_t); \
   template void launch_proj_table_fill<T>(const SubDev*, const ProjSlot*, int, const AtomImg*, int*,                 \
                                           Vec4<T>::type*, cudaStream_t);                                             \
-  template void launch_nl_project<T>(const SubDev*, const ProjSlot*, int, const int*, const Vec4<T>::type*, int,     \
-                                     const T*, double*, cudaStream_t);                                               \
+  template void launch_nl_project<T>(const SubDev*, const ProjSlot*, int, int, const int*, const Vec4<T>::type*,     \
+                                     int, const T*, double*, cudaStream_t);                                          \
   template void launch_nl_back<T>(const SubDev*, const ProjSlot*, int, const int*, const Vec4<T>::type*, int,        \
                                   const double*, T*, const StepCoef*, int, cudaStream_t);                            \
   template void launch_rcsr_build<T>(const SubDev*, const ProjSlot*, int, const int*, const Vec4<T>::type*,         \
