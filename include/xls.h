@@ -186,6 +186,21 @@ xls_status xls_scf_setup(xls_grid g, double n_electrons, double kT, int degree, 
 xls_status xls_scf_step(xls_grid g, double* rho_inout, int rho_on_device, double* residual_out, double* energy_out,
                         double* mu_out);
 
+/* ---- Fermi level across grids (Sec. 5.A.5, "Chemical potential": a histogram of the eigenvalues
+ * narrows the bracket, then Newton steps on N_e(mu) with dN_e/dmu, each needing only global sums of
+ * two scalars).  These calls give one grid's contribution; the host combines the contributions of
+ * the grids of all ranks (for instance by an allreduce) and steers the iteration.  Library-
+ * specific split of xls_density, which does the whole solve on one grid. */
+/* out4 = [2 sum c g((lambda - mu)/kT), 2 sum c g (1 - g) / kT, min lambda, max lambda] over the
+ * grid's states (FP64; g the Fermi-Dirac function). */
+xls_status xls_fermi_partial(xls_grid g, double mu, double kT, double* out4);
+/* hist_out[b] = 2 sum of the weights c over the states with lambda in bin b of n_bins equal bins
+ * of [lo, hi) (states below lo in bin 0, at or above hi in the last bin); n_bins <= 4096. */
+xls_status xls_fermi_histogram(xls_grid g, double lo, double hi, int n_bins, double* hist_out);
+/* Occupations at the given mu; rho on the grid's core points ([n_z][n_y][n_x] FP64, the other
+ * points 0; may be NULL); e3_out = [E_band, E_entropy, N_e] of the grid's states (may be NULL). */
+xls_status xls_density_at(xls_grid g, double mu, double kT, double* rho_out, int rho_on_device, double* e3_out);
+
 /* Waves of the grid (Sec. 5.B.3: subdomains processed in batches that fit the node): 1 when every
  * subdomain is resident at once, else the number of waves of consecutive subdomains admitted by
  * the HBM budget given to xls_grid_create; first_sub_out (optional, n_sub entries suffice)

@@ -23,6 +23,19 @@ __device__ __forceinline__ T block_sum(T v, T* red) {
   return s;
 }
 
+__device__ __forceinline__ double block_sum_max(double v, double* red) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31, nw = (blockDim.x + 31) >> 5;
+  __syncthreads();
+  if (l == 0) red[w] = v;
+  __syncthreads();
+  double s = -1e300;
+  for (int i = 0; i < nw; ++i) s = fmax(s, red[i]);
+  __syncthreads();
+  return s;
+}
+
 // ---- projection: M_s = F F^T, H_s = F HF^T over the grid (Sec. 5.A.3 step (2)) -------------
 // Blocks: (subdomain, 32x32 output tile, K-chunk of the grid); FP64 atomics combine K-chunks.
 constexpr int kGT = 32, kGK = 32, kGChunk = 4096;
@@ -303,6 +316,86 @@ k_fermi(const double* __restrict__ lam, const double* __restrict__ c, int n, dou
 void launch_fermi_occ(const double* lam, const double* c, int n_tot, double n_e, double kT, double* out4, double* occ,
                       int* status, cudaStream_t st) {
   k_fermi<<<1, 1024, 0, st>>>(lam, c, n_tot, n_e, kT, out4, occ, status);
+}
+
+// ---- partial sums of this grid's states for a Fermi level found across ranks (Sec. 5.A.5:
+// histogram of the eigenvalues, then Newton on N_e(mu) with dN_e/dmu) -------------------------
+// out: [0] 2 sum c g, [1] 2 sum c g (1 - g) / kT, [2] min lambda, [3] max lambda
+__global__ void __launch_bounds__(1024)
+k_fermi_partial(const double* __restrict__ lam, const double* __restrict__ c, int n, double mu, double kT, double* out) {
+  __shared__ double red[32];
+  double acc = 0.0, dacc = 0.0, lmin = 1e300, lmax = -1e300;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) {
+    const double g = fermi_fn((lam[i] - mu) / kT);
+    acc += g * c[i];
+    dacc += g * (1.0 - g) * c[i];
+    lmin = fmin(lmin, lam[i]);
+    lmax = fmax(lmax, lam[i]);
+  }
+  acc = block_sum(acc, red);
+  dacc = block_sum(dacc, red);
+  lmin = -block_sum_max(-lmin, red);
+  lmax = block_sum_max(lmax, red);
+  if (threadIdx.x == 0) {
+    out[0] = 2.0 * acc;
+    out[1] = 2.0 * dacc / kT;
+    out[2] = lmin;
+    out[3] = lmax;
+  }
+}
+
+// hist[b] = 2 sum of c over the states with lambda in bin b of [lo, hi) (nb bins; below lo
+// counted in bin 0, at or above hi in bin nb - 1)
+__global__ void __launch_bounds__(1024)
+k_fermi_hist(const double* __restrict__ lam, const double* __restrict__ c, int n, double lo, double hi, int nb,
+             double* hist) {
+  extern __shared__ double sh[];
+  for (int b = threadIdx.x; b < nb; b += blockDim.x) sh[b] = 0.0;
+  __syncthreads();
+  for (int i = threadIdx.x; i < n; i += blockDim.x) {
+    int b = (int)floor((lam[i] - lo) / (hi - lo) * nb);
+    b = b < 0 ? 0 : (b >= nb ? nb - 1 : b);
+    atomicAdd(&sh[b], 2.0 * c[i]);
+  }
+  __syncthreads();
+  for (int b = threadIdx.x; b < nb; b += blockDim.x) hist[b] = sh[b];
+}
+
+// occupations at a given mu and the partial energies: out [0] E_band, [1] E_entropy, [2] N_e
+__global__ void __launch_bounds__(1024)
+k_occ_at(const double* __restrict__ lam, const double* __restrict__ c, int n, double mu, double kT, double* occ,
+         double* out) {
+  __shared__ double red[32];
+  double eb = 0.0, es = 0.0, nn = 0.0;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) {
+    const double g = fermi_fn((lam[i] - mu) / kT);
+    occ[i] = g;
+    eb += g * c[i] * lam[i];
+    const double q = 1.0 - g;
+    es += c[i] * ((g > 0 ? g * log(g) : 0.0) + (q > 0 ? q * log(q) : 0.0));
+    nn += g * c[i];
+  }
+  eb = block_sum(eb, red);
+  es = block_sum(es, red);
+  nn = block_sum(nn, red);
+  if (threadIdx.x == 0) {
+    out[0] = 2.0 * eb;
+    out[1] = -2.0 * kT * es;
+    out[2] = 2.0 * nn;
+  }
+}
+
+void launch_fermi_partial(const double* lam, const double* c, int n, double mu, double kT, double* out,
+                          cudaStream_t st) {
+  k_fermi_partial<<<1, 1024, 0, st>>>(lam, c, n, mu, kT, out);
+}
+void launch_fermi_hist(const double* lam, const double* c, int n, double lo, double hi, int nb, double* hist,
+                       cudaStream_t st) {
+  k_fermi_hist<<<1, 1024, nb * sizeof(double), st>>>(lam, c, n, lo, hi, nb, hist);
+}
+void launch_occ_at(const double* lam, const double* c, int n, double mu, double kT, double* occ, double* out,
+                   cudaStream_t st) {
+  k_occ_at<<<1, 1024, 0, st>>>(lam, c, n, mu, kT, occ, out);
 }
 
 // ---- filter coefficients of the scaled recurrence (Zhou et al. 2006) ----------------------

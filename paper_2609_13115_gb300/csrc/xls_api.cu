@@ -2008,6 +2008,54 @@ xls_status xls_learned_start(xls_grid g, xls_mlp m, double n_electrons, double* 
   return XLS_OK;
 }
 
+xls_status xls_fermi_partial(xls_grid g, double mu, double kT, double* out4) {
+  if (!g || !out4 || !(kT > 0) || !g->have_ritz) return fail(XLS_EINVAL, "xls_fermi_partial: bad arguments or no pass run yet");
+  launch_fermi_partial(g->lam, g->cw, g->tot_states, mu, kT, g->out4, g->st);
+  XLS_CUDA(cudaGetLastError());
+  XLS_CUDA(cudaMemcpyAsync(out4, g->out4, 4 * sizeof(double), cudaMemcpyDeviceToHost, g->st));
+  XLS_CUDA(cudaStreamSynchronize(g->st));
+  return XLS_OK;
+}
+
+xls_status xls_fermi_histogram(xls_grid g, double lo, double hi, int n_bins, double* hist_out) {
+  if (!g || !hist_out || !(hi > lo) || n_bins < 1 || n_bins > 4096 || !g->have_ritz)
+    return fail(XLS_EINVAL, "xls_fermi_histogram: bad arguments or no pass run yet");
+  double* d = nullptr;
+  XLS_CUDA(cudaMallocAsync(&d, n_bins * sizeof(double), g->st));
+  launch_fermi_hist(g->lam, g->cw, g->tot_states, lo, hi, n_bins, d, g->st);
+  XLS_CUDA(cudaGetLastError());
+  XLS_CUDA(cudaMemcpyAsync(hist_out, d, n_bins * sizeof(double), cudaMemcpyDeviceToHost, g->st));
+  XLS_CUDA(cudaFreeAsync(d, g->st));
+  XLS_CUDA(cudaStreamSynchronize(g->st));
+  return XLS_OK;
+}
+
+xls_status xls_density_at(xls_grid g, double mu, double kT, double* rho_out, int rho_on_device, double* e3_out) {
+  if (!g || !(kT > 0) || !g->have_ritz) return fail(XLS_EINVAL, "xls_density_at: bad arguments or no pass run yet");
+  if (g->wave) return not_in_wave_mode("xls_density_at");
+  launch_occ_at(g->lam, g->cw, g->tot_states, mu, kT, g->occ, g->out4, g->st);
+  double h[3];
+  XLS_CUDA(cudaMemcpyAsync(h, g->out4, 3 * sizeof(double), cudaMemcpyDeviceToHost, g->st));
+  if (rho_out) {
+    const long long ng = (long long)g->gn[0] * g->gn[1] * g->gn[2];
+    if (!g->rho) XLS_TRY(g->alloc(&g->rho, ng * sizeof(double)));
+    XLS_CUDA(cudaMemsetAsync(g->rho, 0, ng * sizeof(double), g->st));
+    if (g->prec == XLS_FP64)
+      launch_density_occ<double>(g->d_subs, g->n_sub, g->max_core, (const double*)g->blk[g->cur], g->occ, g->gn, g->rho, g->st);
+    else
+      launch_density_occ<float>(g->d_subs, g->n_sub, g->max_core, (const float*)g->blk[g->cur], g->occ, g->gn, g->rho, g->st);
+    XLS_CUDA(cudaMemcpyAsync(rho_out, g->rho, ng * sizeof(double),
+                             rho_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, g->st));
+  }
+  XLS_CUDA(cudaStreamSynchronize(g->st));
+  if (e3_out) {
+    e3_out[0] = h[0];
+    e3_out[1] = h[1];
+    e3_out[2] = h[2];
+  }
+  return XLS_OK;
+}
+
 xls_status xls_get_waves(xls_grid g, int* n_waves_out, int* first_sub_out) {
   if (!g || !n_waves_out) return fail(XLS_EINVAL, "xls_get_waves: bad arguments");
   *n_waves_out = g->wave ? (int)g->waves.size() : 1;

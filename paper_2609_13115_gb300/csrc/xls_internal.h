@@ -235,6 +235,12 @@ void launch_eig(const SubDev* d_subs, int n_sub, int max_ns, double* L, double* 
 size_t eig_scratch_doubles(int n_sub, int max_ns);
 
 // ---- small kernels -------------------------------------------------------------------------
+void launch_fermi_partial(const double* lam, const double* c, int n, double mu, double kT, double* out,
+                          cudaStream_t st);
+void launch_fermi_hist(const double* lam, const double* c, int n, double lo, double hi, int nb, double* hist,
+                       cudaStream_t st);
+void launch_occ_at(const double* lam, const double* c, int n, double mu, double kT, double* occ, double* out,
+                   cudaStream_t st);
 void launch_filter_coef(int n_sub, const double* bounds, int degree, StepCoef* coef, cudaStream_t st);
 void launch_bounds_from_ritz(const SubDev* d_subs, int n_sub, const double* lam, double* bounds, cudaStream_t st);
 void launch_restrict(const SubDev* d_subs, int n_sub, long long max_nd, const double* Vg, const int gn[3],

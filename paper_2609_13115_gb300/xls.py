@@ -61,6 +61,9 @@ _SIGS = {
     "xls_set_profiling": (c_int, [c_void_p, c_int]),
     "xls_set_graphs": (c_int, [c_void_p, c_int]),
     "xls_get_waves": (c_int, [c_void_p, POINTER(c_int), c_void_p]),
+    "xls_fermi_partial": (c_int, [c_void_p, c_double, c_double, c_void_p]),
+    "xls_fermi_histogram": (c_int, [c_void_p, c_double, c_double, c_int, c_void_p]),
+    "xls_density_at": (c_int, [c_void_p, c_double, c_double, c_void_p, c_int, c_void_p]),
     "xls_mlp_create": (c_int, [c_void_p, c_int, c_void_p, POINTER(c_void_p)]),
     "xls_mlp_destroy": (c_int, [c_void_p]),
     "xls_mlp_get_params": (c_int, [c_void_p, c_void_p]),
@@ -227,6 +230,26 @@ def xls_get_timings(g):
 
 def xls_set_profiling(g, on):
     _check(load().xls_set_profiling(g, int(bool(on))))
+
+
+def xls_fermi_partial(g, mu, kT):
+    out = np.zeros(4)
+    _check(load().xls_fermi_partial(g, float(mu), float(kT), out.ctypes.data_as(c_void_p)))
+    return out
+
+
+def xls_fermi_histogram(g, lo, hi, n_bins):
+    out = np.zeros(int(n_bins))
+    _check(load().xls_fermi_histogram(g, float(lo), float(hi), int(n_bins), out.ctypes.data_as(c_void_p)))
+    return out
+
+
+def xls_density_at(g, mu, kT, rho=None):
+    """Occupations at mu; fills rho (numpy, global grid) when given; returns [E_band, E_entropy, N_e]."""
+    e3 = np.zeros(3)
+    p = rho.ctypes.data_as(c_void_p) if rho is not None else None
+    _check(load().xls_density_at(g, float(mu), float(kT), p, 0, e3.ctypes.data_as(c_void_p)))
+    return e3
 
 
 def xls_get_waves(g, n_sub):

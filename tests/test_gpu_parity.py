@@ -549,3 +549,64 @@ def test_concurrent_halves_match_sequential(prec, monkeypatch):
     assert relerr(res["concurrent"][1], res["sequential"][1]) < 10 * tol
     assert abs(res["concurrent"][2] - res["sequential"][2]) < tol
     np.testing.assert_allclose(res["concurrent"][3], res["sequential"][3], rtol=tol, atol=tol)
+
+
+def test_fermi_partials_and_density_at_match_single_grid_solve():
+    """The per-grid sums of the distributed Fermi-level scheme (xls_fermi_partial / histogram),
+    driven by the host-side histogram + Newton iteration on one rank, give the Fermi level of the
+    single-grid solve; the density and energies at that mu equal xls_density's."""
+    from oracle import fermi
+    from paper_2609_13115_gb300 import dist as xd
+    w = dirichlet20_workload()
+    V = pseudo.local_potential(w)
+    subs = dc.partition(w)
+    psi0 = _start_blocks(w, subs)
+    with make_grid(w, V, xls.XLS_FP64) as g:
+        for a in range(w.n_sub):
+            xls.xls_orbitals_set(g.h, a, psi0[a])
+        xls.xls_chefsi_batch(g.h, w.degree, 3)
+        rho = np.zeros(int(np.prod(w.n)))
+        mu, eb, es = xls.xls_density(g.h, w.n_electrons, w.kT, rho)
+        lam = np.concatenate([xls.xls_get_eigs(g.h, a, int(w.n_states[a]))[0] for a in range(w.n_sub)])
+        c = np.concatenate([xls.xls_get_eigs(g.h, a, int(w.n_states[a]))[1] for a in range(w.n_sub)])
+        part = xls.xls_fermi_partial(g.h, mu, w.kT)
+        assert abs(part[0] - fermi.electron_count(mu, lam, c, w.kT)) < 1e-10
+        assert part[2] == lam.min() and part[3] == lam.max()
+        h = xls.xls_fermi_histogram(g.h, lam.min() - 1, lam.max() + 1, 64)
+        assert abs(h.sum() - 2 * c.sum()) < 1e-10
+        mu_d, _ = xd.grid_fermi_level(g.h, w.n_electrons, w.kT)
+        assert abs(mu_d - mu) < 1e-11
+        rho2 = np.zeros_like(rho)
+        e3 = xls.xls_density_at(g.h, mu_d, w.kT, rho2)
+    assert relerr(rho2, rho) < 1e-11
+    assert abs(e3[0] - eb) < 1e-9 and abs(e3[1] - es) < 1e-9 and abs(e3[2] - w.n_electrons) < 1e-9
+
+
+def test_bench_workload_full_size_sampled_parity():
+    """The bench workload at full size (8 subdomains of 48^3, 160 states, degree 20) in the launch
+    configuration the bench times: the FP64 degree-20 filter over all subdomains from the
+    SplitMix64 start with explicit bounds, a sample of subdomain 0's filtered vectors against the
+    oracle's filter (a fixed polynomial in H acting on each vector alone, so FP64 agreement is to
+    rounding); and the
+    mixed path's H application on two vectors of subdomain 5 against the oracle operator."""
+    w = synth.workload(1)
+    V = synth.veff_erf_wells(w)
+    subs = dc.partition(w)
+    norms = pseudo.projector_norms(w)
+    bounds = np.array([[70.0, 1.0, -1.0]] * w.n_sub)
+    ns0 = int(w.n_states[0])
+    with make_grid(w, V, xls.XLS_FP64) as g:
+        xls.xls_orbitals_random(g.h, w.psi_seed)
+        xls.xls_chefsi_stage(g.h, 1, w.degree, bounds)
+        F0 = xls.xls_orbitals_get(g.h, 0, np.zeros((ns0, subs[0].N)))
+    H0 = dc.subdomain_operator(w, subs[0], V, norms)
+    psi0 = synth.psi0_block(w.psi_seed, subs[0].N, ns0, synth.psi0_offsets(w)[0])
+    sample = [0, 37, 80, 123, 159]   # the filter acts on every vector alone: a sample of columns
+    F_ref = chefsi.chebyshev_filter(H0, psi0[sample], w.degree, 1.0, 70.0, -1.0)
+    assert relerr(F0[sample], F_ref) < 1e-10
+    H5 = dc.subdomain_operator(w, subs[5], V, norms)
+    x = synth.psi0_block(77, subs[5].N, 2)
+    with make_grid(w, V, xls.XLS_MIXED_FP16) as g:
+        y = np.zeros_like(x)
+        xls.xls_hamiltonian_apply(g.h, 5, x, y)
+    assert relerr(y, H5.apply(x)) < 2e-6
