@@ -255,6 +255,13 @@ def run_ours(args):
         kcnt += cnt
     stage_ms, _ = xls.xls_get_timings(g.h)
     xls.xls_set_profiling(g.h, 0)
+    # density stage: Fermi level, occupations and rho on the device (CUDA events around the call)
+    d0, d1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    d0.record(stream)
+    xls.xls_density(g.h, w.n_electrons, w.kT, rho_dev)
+    d1.record(stream)
+    torch.cuda.synchronize()
+    density_ms = d0.elapsed_time(d1)
 
     # end to end through the C ABI with host buffers: H2D of every start block from pinned host
     # memory, the pass, Fermi level and the density read back to the host
@@ -347,7 +354,8 @@ def run_ours(args):
                        "states": int(w.n_states[0]), "degree": w.degree,
                        "l2": "inputs larger than L2 (each orbital block 566 MB)",
                        "parallelism": f"replicas x{ws}" if ws > 1 else "single GPU"},
-            "stage_ms": {k: round(float(v), 3) for k, v in zip(["filter", "projection", "eig", "rotation"], stage_ms)},
+            "stage_ms": dict({k: round(float(v), 3) for k, v in zip(["filter", "projection", "eig", "rotation"], stage_ms)},
+                             density=round(density_ms, 3)),
             "kernel_share": kernel_share,
             "roofline": roofline,
             "cpu_baseline": cpu,
