@@ -34,6 +34,19 @@ def dirichlet_workload():
                           n_states=np.full(8, 16), degree=10, n_passes=3, psi_seed=55)
 
 
+def uneven_workload():
+    """The 24^3 cell in 8 subdomains of uneven size and state count (the mixed shape of the
+    512-subdomain workload): per subdomain a seeded buffer of 2, 4 or 6 points per side (16^3,
+    20^3 or 24^3, the last periodic) and 16, 20 or 24 states."""
+    w = dirichlet_workload()
+    pick = synth.seeded_permutation(1002, 24)[:8] % 3
+    bufs = np.array([2, 4, 6])[pick]
+    w.buf = np.repeat(bufs[:, None], 3, axis=1)
+    w.n_states = np.array([16, 20, 24])[pick]
+    w.name = "si8_dc8_uneven"
+    return w
+
+
 def make_grid(w, V, precision):
     g = xls.Grid(w, precision)
     g.set_hamiltonian(V)
@@ -166,9 +179,9 @@ def _run_both(w, V, precision, n_passes):
     return ref, lam, rho.reshape(ref.rho.shape), mu, eb, es
 
 
-@pytest.mark.parametrize("wname", ["cfg0", "dirichlet"])
+@pytest.mark.parametrize("wname", ["cfg0", "dirichlet", "uneven"])
 def test_full_passes_fp64(wname):
-    w = synth.workload(0) if wname == "cfg0" else dirichlet_workload()
+    w = {"cfg0": lambda: synth.workload(0), "dirichlet": dirichlet_workload, "uneven": uneven_workload}[wname]()
     V = pseudo.local_potential(w)
     ref, lam, rho, mu, eb, es = _run_both(w, V, xls.XLS_FP64, w.n_passes)
     for a in range(w.n_sub):
@@ -181,9 +194,10 @@ def test_full_passes_fp64(wname):
 
 
 @pytest.mark.parametrize("prec", [xls.XLS_MIXED_BF16, xls.XLS_MIXED_FP16])
-@pytest.mark.parametrize("wname", ["cfg0", "dirichlet", "dirichlet20"])
+@pytest.mark.parametrize("wname", ["cfg0", "dirichlet", "dirichlet20", "uneven"])
 def test_full_passes_mixed(wname, prec):
-    w = {"cfg0": lambda: synth.workload(0), "dirichlet": dirichlet_workload, "dirichlet20": lambda: dirichlet20_workload()}[wname]()
+    w = {"cfg0": lambda: synth.workload(0), "dirichlet": dirichlet_workload, "dirichlet20": lambda: dirichlet20_workload(),
+         "uneven": uneven_workload}[wname]()
     V = pseudo.local_potential(w)
     ref, lam, rho, mu, eb, es = _run_both(w, V, prec, w.n_passes)
     n_atoms = len(w.pos)
