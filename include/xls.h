@@ -186,6 +186,23 @@ xls_status xls_scf_setup(xls_grid g, double n_electrons, double kT, int degree, 
 xls_status xls_scf_step(xls_grid g, double* rho_inout, int rho_on_device, double* residual_out, double* energy_out,
                         double* mu_out);
 
+/* FP16 warm-start storage of one subdomain's current orbitals (Sec. 5.B.3: orbitals kept in FP16
+ * between SCF steps): vector v is stored as half(psi_v * 2^e_v), with the power of two e_v
+ * (exp_out[v]) placing max |psi_v| 2^e_v in [2^13, 2^14); half_out holds n_states x N_d
+ * IEEE binary16 values (vector-major, x fastest), host memory.  Relative error per element
+ * <= 2^-11 of the vector's largest entry.  Loading converts back into the grid's block
+ * (FP32 or FP64) and keeps the filter bounds of the last pass (a warm start).  Library-
+ * specific layout; not available in wave mode.  Errors: XLS_EINVAL, XLS_ECUDA. */
+xls_status xls_orbitals_store_fp16(xls_grid g, int sub, uint16_t* half_out, int* exp_out);
+xls_status xls_orbitals_load_fp16(xls_grid g, int sub, const uint16_t* half_in, const int* exp_in);
+
+/* Self-test of the failure path every bounded device wait of the library takes: a kernel waits
+ * on a shared-memory barrier that nothing completes, gives up after spin_limit tries
+ * (1..2^20; each try returns after a short hardware-defined time) and records XLS_ETIMEOUT, which
+ * this call returns.  No fault, no trap; the context stays usable.  Library-specific: the paper
+ * has no counterpart.  Errors: XLS_EINVAL, XLS_ECUDA. */
+xls_status xls_selftest_wait(int spin_limit, void* cuda_stream);
+
 /* ---- Fermi level across grids (Sec. 5.A.5, "Chemical potential": a histogram of the eigenvalues
  * narrows the bracket, then Newton steps on N_e(mu) with dN_e/dmu, each needing only global sums of
  * two scalars).  These calls give one grid's contribution; the host combines the contributions of

@@ -1,5 +1,7 @@
 // Subspace contractions on SIMT cores (FP64 path), interior weights, Fermi level, density,
 // and the small set-up kernels (restriction, projector norms, Lanczos bound, random start).
+#include <cuda_fp16.h>
+
 #include "xls_internal.h"
 
 namespace xls {
@@ -316,6 +318,79 @@ k_fermi(const double* __restrict__ lam, const double* __restrict__ c, int n, dou
 void launch_fermi_occ(const double* lam, const double* c, int n_tot, double n_e, double kT, double* out4, double* occ,
                       int* status, cudaStream_t st) {
   k_fermi<<<1, 1024, 0, st>>>(lam, c, n_tot, n_e, kT, out4, occ, status);
+}
+
+// ---- FP16 orbital storage (warm start between SCF steps): vector v stored as
+// half(psi_v * 2^e_v) with e_v such that max |psi_v| 2^e_v lies in [2^13, 2^14) -------------------
+template <typename T>
+__global__ void __launch_bounds__(256) k_vec_exp14(const T* __restrict__ X, long long nd, int* ex) {
+  __shared__ float red[8];
+  const T* x = X + (long long)blockIdx.x * nd;
+  float m = 0.f;
+  for (long long i = threadIdx.x; i < nd; i += blockDim.x) m = fmaxf(m, fabsf((float)x[i]));
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = m;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    float t = 0.f;
+    for (int i = 0; i < (int)(blockDim.x >> 5); ++i) t = fmaxf(t, red[i]);
+    int k = 0;
+    frexpf(t, &k);                       // 2^(k-1) <= t < 2^k
+    ex[blockIdx.x] = t > 0.f ? 14 - k : 0;
+  }
+}
+
+template <typename T>
+__global__ void k_to_half(const T* __restrict__ X, long long nd, int ns, const int* __restrict__ ex, __half* out) {
+  const long long n = nd * ns;
+  for (long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x; q < n; q += (long long)gridDim.x * blockDim.x)
+    out[q] = __float2half_rn((float)ldexp((double)X[q], ex[q / nd]));
+}
+
+template <typename T>
+__global__ void k_from_half(const __half* __restrict__ in, long long nd, int ns, const int* __restrict__ ex, T* X) {
+  const long long n = nd * ns;
+  for (long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x; q < n; q += (long long)gridDim.x * blockDim.x)
+    X[q] = (T)ldexp((double)__half2float(in[q]), -ex[q / nd]);
+}
+
+template <typename T>
+void launch_store_half(const T* X, long long nd, int ns, int* ex, void* out, cudaStream_t st) {
+  k_vec_exp14<T><<<ns, 256, 0, st>>>(X, nd, ex);
+  k_to_half<T><<<592, 256, 0, st>>>(X, nd, ns, ex, (__half*)out);
+}
+template <typename T>
+void launch_load_half(const void* in, long long nd, int ns, const int* ex, T* X, cudaStream_t st) {
+  k_from_half<T><<<592, 256, 0, st>>>((const __half*)in, nd, ns, ex, X);
+}
+template void launch_store_half<float>(const float*, long long, int, int*, void*, cudaStream_t);
+template void launch_store_half<double>(const double*, long long, int, int*, void*, cudaStream_t);
+template void launch_load_half<float>(const void*, long long, int, const int*, float*, cudaStream_t);
+template void launch_load_half<double>(const void*, long long, int, const int*, double*, cudaStream_t);
+
+// ---- bounded-wait self-test: an mbarrier that nothing completes, waited on with an iteration
+// limit; the wait gives up and records XLS_ETIMEOUT (the path every bounded wait of the library
+// takes when its copy or peer never arrives) ------------------------------------------------------
+__global__ void k_wait_selftest(int spin_limit, int* status) {
+  __shared__ __align__(8) uint64_t bar;
+  const uint32_t a = (uint32_t)__cvta_generic_to_shared(&bar);
+  if (threadIdx.x == 0) asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(a), "r"(1) : "memory");
+  __syncthreads();
+  bool done = false;
+  for (int i = 0; i < spin_limit && !done; ++i) {
+    uint32_t ok;
+    asm volatile("{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+                 : "=r"(ok)
+                 : "r"(a), "r"(0u)
+                 : "memory");
+    done = ok != 0;
+  }
+  if (!done && threadIdx.x == 0) atomicCAS(status, 0, XLS_ETIMEOUT);
+}
+
+void launch_wait_selftest(int spin_limit, int* status, cudaStream_t st) {
+  k_wait_selftest<<<1, 32, 0, st>>>(spin_limit, status);
 }
 
 // ---- partial sums of this grid's states for a Fermi level found across ranks (Sec. 5.A.5:

@@ -2008,6 +2008,68 @@ xls_status xls_learned_start(xls_grid g, xls_mlp m, double n_electrons, double* 
   return XLS_OK;
 }
 
+xls_status xls_orbitals_store_fp16(xls_grid g, int sub, uint16_t* half_out, int* exp_out) {
+  if (!g || !half_out || !exp_out || sub < 0 || sub >= g->n_sub) return fail(XLS_EINVAL, "xls_orbitals_store_fp16: bad arguments");
+  if (g->wave) return not_in_wave_mode("xls_orbitals_store_fp16");
+  const SubDev& S = g->subs[sub];
+  const size_t n = (size_t)S.nd * S.ns;
+  void* dh = nullptr;
+  int* de = nullptr;
+  XLS_CUDA(cudaMallocAsync(&dh, n * 2, g->st));
+  XLS_CUDA(cudaMallocAsync((void**)&de, S.ns * sizeof(int), g->st));
+  if (g->prec == XLS_FP64) launch_store_half<double>((const double*)g->blk[g->cur] + S.off_blk, S.nd, S.ns, de, dh, g->st);
+  else launch_store_half<float>((const float*)g->blk[g->cur] + S.off_blk, S.nd, S.ns, de, dh, g->st);
+  cudaError_t e = cudaGetLastError();
+  if (e == cudaSuccess) e = cudaMemcpyAsync(half_out, dh, n * 2, cudaMemcpyDeviceToHost, g->st);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(exp_out, de, S.ns * sizeof(int), cudaMemcpyDeviceToHost, g->st);
+  cudaFreeAsync(dh, g->st);
+  cudaFreeAsync(de, g->st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(g->st);
+  if (e != cudaSuccess) return fail(XLS_ECUDA, cudaGetErrorString(e));
+  return XLS_OK;
+}
+
+xls_status xls_orbitals_load_fp16(xls_grid g, int sub, const uint16_t* half_in, const int* exp_in) {
+  if (!g || !half_in || !exp_in || sub < 0 || sub >= g->n_sub) return fail(XLS_EINVAL, "xls_orbitals_load_fp16: bad arguments");
+  if (g->wave) return not_in_wave_mode("xls_orbitals_load_fp16");
+  const SubDev& S = g->subs[sub];
+  const size_t n = (size_t)S.nd * S.ns;
+  void* dh = nullptr;
+  int* de = nullptr;
+  XLS_CUDA(cudaMallocAsync(&dh, n * 2, g->st));
+  XLS_CUDA(cudaMallocAsync((void**)&de, S.ns * sizeof(int), g->st));
+  cudaError_t e = cudaMemcpyAsync(dh, half_in, n * 2, cudaMemcpyHostToDevice, g->st);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(de, exp_in, S.ns * sizeof(int), cudaMemcpyHostToDevice, g->st);
+  if (e == cudaSuccess) {
+    if (g->prec == XLS_FP64) launch_load_half<double>(dh, S.nd, S.ns, de, (double*)g->blk[g->cur] + S.off_blk, g->st);
+    else launch_load_half<float>(dh, S.nd, S.ns, de, (float*)g->blk[g->cur] + S.off_blk, g->st);
+    e = cudaGetLastError();
+  }
+  cudaFreeAsync(dh, g->st);
+  cudaFreeAsync(de, g->st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(g->st);
+  if (e != cudaSuccess) return fail(XLS_ECUDA, cudaGetErrorString(e));
+  g->orb_set = true;
+  return XLS_OK;
+}
+
+xls_status xls_selftest_wait(int spin_limit, void* cuda_stream) {
+  if (spin_limit < 1 || spin_limit > (1 << 20)) return fail(XLS_EINVAL, "xls_selftest_wait: spin_limit in 1..2^20");
+  cudaStream_t st = (cudaStream_t)cuda_stream;
+  int* d = nullptr;
+  XLS_CUDA(cudaMalloc(&d, sizeof(int)));
+  XLS_CUDA(cudaMemsetAsync(d, 0, sizeof(int), st));
+  launch_wait_selftest(spin_limit, d, st);
+  int h = 0;
+  cudaError_t e = cudaGetLastError();
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&h, d, sizeof(int), cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  cudaFree(d);
+  if (e != cudaSuccess) return fail(XLS_ECUDA, cudaGetErrorString(e));
+  if (h == XLS_ETIMEOUT) return fail(XLS_ETIMEOUT, "bounded device wait gave up (self-test)");
+  return XLS_OK;
+}
+
 xls_status xls_fermi_partial(xls_grid g, double mu, double kT, double* out4) {
   if (!g || !out4 || !(kT > 0) || !g->have_ritz) return fail(XLS_EINVAL, "xls_fermi_partial: bad arguments or no pass run yet");
   launch_fermi_partial(g->lam, g->cw, g->tot_states, mu, kT, g->out4, g->st);

@@ -235,6 +235,11 @@ void launch_eig(const SubDev* d_subs, int n_sub, int max_ns, double* L, double* 
 size_t eig_scratch_doubles(int n_sub, int max_ns);
 
 // ---- small kernels -------------------------------------------------------------------------
+void launch_wait_selftest(int spin_limit, int* status, cudaStream_t st);
+template <typename T>
+void launch_store_half(const T* X, long long nd, int ns, int* ex, void* out, cudaStream_t st);
+template <typename T>
+void launch_load_half(const void* in, long long nd, int ns, const int* ex, T* X, cudaStream_t st);
 void launch_fermi_partial(const double* lam, const double* c, int n, double mu, double kT, double* out,
                           cudaStream_t st);
 void launch_fermi_hist(const double* lam, const double* c, int n, double lo, double hi, int nb, double* hist,

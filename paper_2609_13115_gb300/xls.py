@@ -62,6 +62,9 @@ _SIGS = {
     "xls_set_graphs": (c_int, [c_void_p, c_int]),
     "xls_get_waves": (c_int, [c_void_p, POINTER(c_int), c_void_p]),
     "xls_fermi_partial": (c_int, [c_void_p, c_double, c_double, c_void_p]),
+    "xls_selftest_wait": (c_int, [c_int, c_void_p]),
+    "xls_orbitals_store_fp16": (c_int, [c_void_p, c_int, c_void_p, c_void_p]),
+    "xls_orbitals_load_fp16": (c_int, [c_void_p, c_int, c_void_p, c_void_p]),
     "xls_fermi_histogram": (c_int, [c_void_p, c_double, c_double, c_int, c_void_p]),
     "xls_density_at": (c_int, [c_void_p, c_double, c_double, c_void_p, c_int, c_void_p]),
     "xls_mlp_create": (c_int, [c_void_p, c_int, c_void_p, POINTER(c_void_p)]),
@@ -230,6 +233,24 @@ def xls_get_timings(g):
 
 def xls_set_profiling(g, on):
     _check(load().xls_set_profiling(g, int(bool(on))))
+
+
+def xls_orbitals_store_fp16(g, sub, n_states, n_points):
+    """(half values as uint16 array (n_states, n_points), exponents (n_states,))."""
+    h = np.zeros((int(n_states), int(n_points)), dtype=np.uint16)
+    e = np.zeros(int(n_states), dtype=np.int32)
+    _check(load().xls_orbitals_store_fp16(g, int(sub), h.ctypes.data_as(c_void_p), e.ctypes.data_as(c_void_p)))
+    return h, e
+
+
+def xls_orbitals_load_fp16(g, sub, h, e):
+    h = np.ascontiguousarray(h, dtype=np.uint16)
+    e = np.ascontiguousarray(e, dtype=np.int32)
+    _check(load().xls_orbitals_load_fp16(g, int(sub), h.ctypes.data_as(c_void_p), e.ctypes.data_as(c_void_p)))
+
+
+def xls_selftest_wait(spin_limit=64, stream=None):
+    _check(load().xls_selftest_wait(int(spin_limit), c_void_p(stream) if stream else None))
 
 
 def xls_fermi_partial(g, mu, kT):

@@ -624,3 +624,68 @@ def test_bench_workload_full_size_sampled_parity():
         y = np.zeros_like(x)
         xls.xls_hamiltonian_apply(g.h, 5, x, y)
     assert relerr(y, H5.apply(x)) < 2e-6
+
+
+def test_failure_paths_return_status_codes():
+    """Failures made on the host come back as status codes, with the context still usable: a
+    bounded device wait that nothing completes (XLS_ETIMEOUT), a rank-deficient start block
+    (a zero vector: the Gram matrix is singular, XLS_ENOTSPD naming the subdomain), more
+    electrons than the states hold (XLS_ENOCONV)."""
+    with pytest.raises(xls.XlsError) as ei:
+        xls.xls_selftest_wait(64)
+    assert ei.value.status == xls.XLS_ETIMEOUT
+    w = dirichlet_workload()
+    V = pseudo.local_potential(w)
+    subs = dc.partition(w)
+    psi0 = _start_blocks(w, subs)
+    psi0[3][5] = 0.0
+    with make_grid(w, V, xls.XLS_FP64) as g:
+        for a in range(w.n_sub):
+            xls.xls_orbitals_set(g.h, a, psi0[a])
+        with pytest.raises(xls.XlsError) as ei:
+            xls.xls_chefsi_batch(g.h, w.degree, 1)
+        assert ei.value.status == xls.XLS_ENOTSPD and "subdomain 3" in str(ei.value)
+    psi0 = _start_blocks(w, subs)
+    with make_grid(w, V, xls.XLS_FP64) as g:
+        for a in range(w.n_sub):
+            xls.xls_orbitals_set(g.h, a, psi0[a])
+        xls.xls_chefsi_batch(g.h, w.degree, 1)
+        with pytest.raises(xls.XlsError) as ei:
+            xls.xls_density(g.h, 1e4, w.kT)
+        assert ei.value.status == xls.XLS_ENOCONV
+        xls.xls_chefsi_batch(g.h, w.degree, 1)          # the grid still works
+        assert np.all(np.isfinite(xls.xls_get_eigs(g.h, 0, int(w.n_states[0]))[0]))
+
+
+@pytest.mark.parametrize("prec", [xls.XLS_FP64, xls.XLS_MIXED_FP16])
+def test_fp16_warm_start_storage(prec):
+    """FP16 storage of the orbitals between passes: the stored halves decode (IEEE binary16 times
+    2^-e) to the orbitals within 2^-11 of each vector's largest entry, and a pass from the
+    reloaded orbitals gives the occupied Ritz values of a pass from the unrounded ones to 1e-6 Ha."""
+    w = dirichlet20_workload()
+    V = pseudo.local_potential(w)
+    subs = dc.partition(w)
+    psi0 = _start_blocks(w, subs)
+    lam = {}
+    for mode in ("plain", "fp16"):
+        with make_grid(w, V, prec) as g:
+            for a in range(w.n_sub):
+                xls.xls_orbitals_set(g.h, a, psi0[a])
+            xls.xls_chefsi_batch(g.h, w.degree, 3)
+            if mode == "fp16":
+                for a in range(w.n_sub):
+                    ns = int(w.n_states[a])
+                    P = xls.xls_orbitals_get(g.h, a, np.zeros((ns, subs[a].N)))
+                    h, e = xls.xls_orbitals_store_fp16(g.h, a, ns, subs[a].N)
+                    dec = h.view(np.float16).astype(np.float64) * np.ldexp(1.0, -e.astype(np.int64))[:, None]
+                    bound = np.ldexp(1.0, -11) * np.abs(P).max(axis=1)
+                    assert np.all(np.abs(dec - P).max(axis=1) <= bound * (1 + 1e-12)), a
+                    assert np.all((np.abs(P).max(axis=1) * np.ldexp(1.0, e.astype(np.int64)) >= 2 ** 13)
+                                  & (np.abs(P).max(axis=1) * np.ldexp(1.0, e.astype(np.int64)) < 2 ** 14))
+                    xls.xls_orbitals_load_fp16(g.h, a, h, e)
+            xls.xls_chefsi_batch(g.h, w.degree, 1)
+            lam[mode] = [xls.xls_get_eigs(g.h, a, int(w.n_states[a]))[0] for a in range(w.n_sub)]
+            mu = xls.xls_density(g.h, w.n_electrons, w.kT)[0]
+    for a in range(w.n_sub):
+        occ = lam["plain"][a] < mu + 0.1
+        np.testing.assert_allclose(lam["fp16"][a][occ], lam["plain"][a][occ], rtol=0, atol=1e-6)
