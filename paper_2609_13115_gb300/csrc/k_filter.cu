@@ -382,7 +382,7 @@ __global__ void k_rcsr_fill(const SubDev* __restrict__ subs, const ProjSlot* __r
   }
 }
 
-constexpr int kBackPts = 1024, kBackVec = 8;
+constexpr int kBackPts = 2048, kBackVec = 8;
 constexpr int kBackRow = kBackVec + 1;   // padded slot row of Q (consecutive slots in different bank groups)
 
 // Y_out[v][g] += scale * sum over the slots s of point g of sum_l chi_l(g) P[s][l][v]
