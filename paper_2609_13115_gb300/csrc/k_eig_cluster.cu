@@ -223,6 +223,156 @@ k_tridiag_cl(const SubDev* __restrict__ subs, double* Am, double* vecs) {
   cl.sync();
 }
 
+// ---- Householder tridiagonalisation with one cluster barrier per column ----------------------
+// Every CTA keeps the full reflector v, the full update vector w and the pivot row, and updates
+// only its own rows.  Per column k: each CTA forms the partial column sums q_r = A_own^T v of its
+// rows (A symmetric, so these are the rows' contributions to p = tau A v) and pushes them, with
+// the owner also pushing row k+1 (still before this column's update), into every CTA; after the
+// single barrier every CTA adds the partials (p), forms K and w, updates its own rows, applies the
+// same update to the pushed row k+1 -- which is column k+1 below the diagonal, by symmetry -- and
+// derives the next reflector from it redundantly, so no further exchange is needed.  Buffers
+// alternate with the column parity: a CTA can be at most one column ahead of another.
+// shared memory: own rows [nloc][n], partials [2][CL][n], pivot rows [2][n], v, w, p [3][n]
+__global__ void __launch_bounds__(256)
+k_tridiag_cl1(const SubDev* __restrict__ subs, double* Am, double* vecs) {
+  cg::cluster_group cl = cg::this_cluster();
+  const int CL = (int)cl.num_blocks(), rank = (int)cl.block_rank();
+  const int a = blockIdx.x / CL;
+  const SubDev& S = subs[a];
+  const int n = S.ns;
+  const int nloc = (n + CL - 1) / CL;
+  double* Ag = Am + S.off_ss;
+  double* d = vecs + 8LL * S.off_state;
+  double* e = d + n;
+  double* tau = d + 2 * n;
+  extern __shared__ __align__(16) double tsm[];
+  double* Ar = tsm;
+  double* qb = Ar + (size_t)nloc * n;          // [2][CL][n]
+  double* rb = qb + 2 * (size_t)CL * n;        // [2][n]
+  double* vf = rb + 2 * (size_t)n;
+  double* wf = vf + n;
+  double* pf = wf + n;
+  __shared__ double red[8];
+  __shared__ double s_sc[4];                   // tau, K, scale of the reflector
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+  for (int r = 0; r < nloc; ++r) {
+    const int i = r * CL + rank;
+    if (i >= n) break;
+    for (int j = threadIdx.x; j < n; j += blockDim.x)
+      Ar[(size_t)r * n + j] = 0.5 * (Ag[(size_t)i * n + j] + Ag[(size_t)j * n + i]);
+  }
+  __syncthreads();
+  // row 0 to every CTA, then the first reflector (from column 0 = row 0)
+  if (rank == 0)
+    for (int q = 0; q < CL; ++q) {
+      double* dst = cl.map_shared_rank(rb, q);
+      for (int j = threadIdx.x; j < n; j += blockDim.x) dst[j] = Ar[j];
+    }
+  cl.sync();
+  // reflector of column k from the pivot row buffer `row` (entries j > k): v, tau; d[k], e[k]
+  auto reflector = [&](int k, const double* row) {
+    double acc = 0.0;
+    for (int j = k + 2 + threadIdx.x; j < n; j += blockDim.x) acc += row[j] * row[j];
+    const double xn2 = bsum(acc, red);
+    const double alpha = row[k + 1];
+    double beta, t, scal;
+    if (xn2 == 0.0) {
+      t = 0.0; beta = alpha; scal = 0.0;
+    } else {
+      beta = -copysign(sqrt(alpha * alpha + xn2), alpha);
+      t = (beta - alpha) / beta;
+      scal = 1.0 / (alpha - beta);
+    }
+    for (int j = threadIdx.x; j < n; j += blockDim.x) vf[j] = j <= k ? 0.0 : (j == k + 1 ? 1.0 : row[j] * scal);
+    if (threadIdx.x == 0) {
+      s_sc[0] = t;
+      if (rank == 0) {
+        d[k] = row[k];
+        e[k] = beta;
+        tau[k] = t;
+      }
+    }
+    __syncthreads();
+  };
+  if (n >= 2) reflector(0, rb);
+  for (int k = 0; k + 1 < n; ++k) {
+    const int par = k & 1;
+    const double t = s_sc[0];
+    // own reflector entries into the owned rows (column k, below the subdiagonal)
+    for (int r = threadIdx.x; r < nloc; r += blockDim.x) {
+      const int i = r * CL + rank;
+      if (i >= k + 2 && i < n) Ar[(size_t)r * n + k] = vf[i];
+    }
+    // partial column sums of the own rows: q_j = sum_{i own, i > k} A_ij v_i, j > k
+    double* qmine = qb + ((size_t)par * CL + rank) * n;
+    for (int j = k + 1 + threadIdx.x; j < n; j += blockDim.x) {
+      double acc = 0.0;
+      for (int r = 0; r < nloc; ++r) {
+        const int i = r * CL + rank;
+        if (i > k && i < n) acc += Ar[(size_t)r * n + j] * vf[i];
+      }
+      for (int q = 0; q < CL; ++q) cl.map_shared_rank(qmine, q)[j] = acc;
+    }
+    // the owner of row k+1 pushes it (before this column's update) for the next reflector
+    if ((k + 1) % CL == rank) {
+      const double* src = Ar + (size_t)((k + 1) / CL) * n;
+      for (int q = 0; q < CL; ++q) {
+        double* dst = cl.map_shared_rank(rb + (size_t)(1 - par) * n, q);
+        for (int j = k + 1 + threadIdx.x; j < n; j += blockDim.x) dst[j] = src[j];
+      }
+    }
+    cl.sync();
+    // p = tau sum_r q_r, K = tau p.v / 2, w = p - K v (all j > k, in every CTA)
+    double pv = 0.0;
+    for (int j = k + 1 + threadIdx.x; j < n; j += blockDim.x) {
+      double s = 0.0;
+      for (int q = 0; q < CL; ++q) s += qb[((size_t)par * CL + q) * n + j];
+      s *= t;
+      pf[j] = s;
+      pv += s * vf[j];
+    }
+    pv = bsum(pv, red);
+    const double K = 0.5 * t * pv;
+    for (int j = k + 1 + threadIdx.x; j < n; j += blockDim.x) wf[j] = pf[j] - K * vf[j];
+    __syncthreads();
+    if (t != 0.0) {
+      // own rows: A_ij -= v_i w_j + w_i v_j (i, j > k)
+      for (int r = warp; r < nloc; r += nw) {
+        const int i = r * CL + rank;
+        if (i <= k || i >= n) continue;
+        double* row = Ar + (size_t)r * n;
+        const double vi = vf[i], wi = wf[i];
+        for (int j = k + 1 + lane; j < n; j += 32) row[j] -= vi * wf[j] + wi * vf[j];
+      }
+      // the pushed row k+1, updated the same way (every CTA)
+      double* row1 = rb + (size_t)(1 - par) * n;
+      const double v1 = vf[k + 1], w1 = wf[k + 1];
+      for (int j = k + 1 + threadIdx.x; j < n; j += blockDim.x) row1[j] -= v1 * wf[j] + w1 * vf[j];
+    }
+    __syncthreads();
+    if (k + 2 < n) {
+      reflector(k + 1, rb + (size_t)(1 - par) * n);
+    } else if (threadIdx.x == 0 && rank == 0) {   // last diagonal entries
+      const double* row1 = rb + (size_t)(1 - par) * n;
+      d[k + 1] = row1[k + 1];
+      e[k + 1] = 0.0;
+      tau[k + 1] = 0.0;
+    }
+  }
+  if (n == 1 && threadIdx.x == 0 && rank == 0) {
+    d[0] = Ar[0];
+    e[0] = 0.0;
+    tau[0] = 0.0;
+  }
+  // reflectors back to global memory for the back-transformation
+  for (int r = 0; r < nloc; ++r) {
+    const int i = r * CL + rank;
+    if (i >= n) break;
+    for (int j = threadIdx.x; j + 1 < i; j += blockDim.x) Ag[(size_t)i * n + j] = Ar[(size_t)r * n + j];
+  }
+  cl.sync();
+}
+
 // cluster size and shared memory per CTA for an n x n matrix (0: not possible)
 static int pick_cluster(int n, size_t extra_per_cta, size_t& smem) {
   for (int CL : {8, 16}) {
@@ -277,9 +427,15 @@ bool launch_cholesky_cluster(const SubDev* d_subs, int n_sub, int max_ns, double
 
 bool launch_tridiag_cluster(const SubDev* d_subs, int n_sub, int max_ns, double* A, double* vecs, cudaStream_t st) {
   size_t smem = 0;
-  const int CL = pick_cluster(max_ns, (2 * (size_t)max_ns + 4) * sizeof(double), smem);
-  if (!CL) return false;
-  return launch_cluster(k_tridiag_cl, n_sub, CL, smem, st, d_subs, A, vecs, true);
+  // one barrier per column: partials [2][8][n], pivot rows [2][n], v, w, p
+  const int CL = pick_cluster(max_ns, (2 * 16 + 2 + 3) * (size_t)max_ns * sizeof(double), smem);
+  if (CL) {
+    const size_t exact = ((size_t)(max_ns + CL - 1) / CL * max_ns + (2 * (size_t)CL + 5) * max_ns) * sizeof(double);
+    if (launch_cluster(k_tridiag_cl1, n_sub, CL, exact, st, d_subs, A, vecs, true)) return true;
+  }
+  const int CL4 = pick_cluster(max_ns, (2 * (size_t)max_ns + 4) * sizeof(double), smem);
+  if (!CL4) return false;
+  return launch_cluster(k_tridiag_cl, n_sub, CL4, smem, st, d_subs, A, vecs, true);
 }
 
 }  // namespace xls
