@@ -12,6 +12,8 @@
 #include <cuda.h>
 #include <cudaTypedefs.h>
 
+#include <cstring>
+
 #include "xls_internal.h"
 
 namespace xls {
@@ -73,11 +75,41 @@ constexpr int kHaloX = 8;           // halo columns on each side (16-byte aligne
 constexpr int kQ = 2 * kN0 + 1;     // output planes accumulating at any time
 constexpr int kMaxThreads = 320;    // consumer threads (<= 288) + one producer warp
 
+// Two FP32 values in one 64-bit register (low half = first value), the operand type of the
+// packed f32x2 instructions of sm_100 and later: one instruction does the arithmetic of two
+// x-points.
+using f2 = unsigned long long;
+__device__ __forceinline__ f2 add2(f2 a, f2 b) {
+  f2 d;
+  asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+  return d;
+}
+__device__ __forceinline__ f2 mul2(f2 a, f2 b) {
+  f2 d;
+  asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+  return d;
+}
+__device__ __forceinline__ f2 fma2(f2 a, f2 b, f2 c) {
+  f2 d;
+  asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+  return d;
+}
+__device__ __forceinline__ f2 pack2(float lo, float hi) {
+  f2 d;
+  asm("mov.b64 %0, {%1, %2};" : "=l"(d) : "f"(lo), "f"(hi));
+  return d;
+}
+__device__ __forceinline__ void unpack2(f2 a, float& lo, float& hi) {
+  asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(a));
+}
+
 // Stencil weights of one launch (all subdomains of a launch share the grid spacing), passed by
-// value so that the FMAs read them from the constant bank.
+// value so that the FMAs read them from the constant bank: each packed weight holds the same
+// value in both halves; wxs are the scalar x-weights of the odd offsets.
 struct StencilW {
-  float wx[kN0 + 1], wy[kN0 + 1], wz[kN0 + 1];
-  float wc;
+  f2 wx[kN0 + 1], wy[kN0 + 1], wz[kN0 + 1];
+  f2 wc;
+  float wxs[kN0 + 1];
 };
 
 // Bounded waits (iteration limit; on expiry the caller records XLS_ETIMEOUT, never a trap).
@@ -97,7 +129,10 @@ __device__ __forceinline__ bool wait_full(uint64_t* bar, uint32_t parity) {
 // and potential terms into the accumulator of z_t and scatters w_z[p] * Y(z_t) into the
 // accumulators of z_t +- p; the output plane z_t - 6 is then complete and is written out.
 // Thirteen accumulators live in registers (the loop is unrolled by 13 so their indices are
-// static).
+// static), two x-points per 64-bit register, and the arithmetic runs on packed f32x2
+// instructions (the odd x-offsets, whose partner pairs straddle register pairs, on scalars).
+// Along a periodic z axis the six wrapped planes at either end contribute only their
+// z-neighbour terms: of those planes only the TY centre rows are loaded.
 template <int kW>
 __global__ void __launch_bounds__(kMaxThreads, 2)
 k_stencil_tma(const SubDev* __restrict__ subs, const TmaJob* __restrict__ jobs, const int* __restrict__ job_off,
@@ -155,6 +190,7 @@ k_stencil_tma(const SubDev* __restrict__ subs, const TmaJob* __restrict__ jobs, 
     const int ytop = py ? wrapt(y0 - kN0, ny) : y0 - kN0;
     const int ybot = py ? wrapt(y0 + TY, ny) : y0 + TY;
     const uint32_t in_bytes = (uint32_t)(rows * W) * 4u, aux_bytes = (uint32_t)(TY * nx) * 4u;
+    const uint32_t ctr_bytes = (uint32_t)(TY * W) * 4u;
     int issued = 0;
     for (int it = 0; it < n_iter; ++it) {
       const int slot = it % kNS;
@@ -173,9 +209,13 @@ k_stencil_tma(const SubDev* __restrict__ subs, const TmaJob* __restrict__ jobs, 
       }
       const int zt = zbase + it;
       const bool real = pz || zt < nz;
+      // planes outside [0, n_z) (periodic z only) feed the z-neighbours of the edge planes: their
+      // centre rows are all that is read of them
+      const bool interior = zt >= 0 && zt < nz;
       const int zo = zt - kN0;
       const bool yp = has_prev && zo >= 0;
-      const uint32_t bytes = (real ? in_bytes + aux_bytes : 0u) + (yp ? aux_bytes : 0u);
+      const uint32_t bytes =
+          (real ? (interior ? in_bytes + aux_bytes : ctr_bytes) : 0u) + (yp ? aux_bytes : 0u);
       uint64_t* bar = &full[slot];
       float* dst = ring + (size_t)slot * slot_floats;
       asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
@@ -191,10 +231,12 @@ k_stencil_tma(const SubDev* __restrict__ subs, const TmaJob* __restrict__ jobs, 
         mbar_expect_tx(bar, bytes);
         if (real) {
           const int zz = pz ? wrapt(zt, nz) : zt;
-          tma_load_4d(dst, m_halo, bar, -kHaloX, ytop, zz, vec);
           tma_load_4d(dst + kN0 * W, m_in, bar, -kHaloX, y0, zz, vec);
-          tma_load_4d(dst + (kN0 + TY) * W, m_halo, bar, -kHaloX, ybot, zz, vec);
-          tma_load_3d(dst + off_v, m_v, bar, 0, y0, zz);
+          if (interior) {
+            tma_load_4d(dst, m_halo, bar, -kHaloX, ytop, zz, vec);
+            tma_load_4d(dst + (kN0 + TY) * W, m_halo, bar, -kHaloX, ybot, zz, vec);
+            tma_load_3d(dst + off_v, m_v, bar, 0, y0, zz);
+          }
         }
         if (yp) tma_load_4d(dst + off_yp, m_prev, bar, 0, y0, zo, vec);
       }
@@ -215,20 +257,23 @@ k_stencil_tma(const SubDev* __restrict__ subs, const TmaJob* __restrict__ jobs, 
   const bool store_ok = active && y < ny;
   const StepCoef cf = coef[J.sub * kMaxDegree + step];
   const float scale = (float)cf.scale, cshift = (float)cf.c, pshift = (float)cf.shift;
+  const f2 scale2 = pack2(scale, scale), ncs2 = pack2(-cshift, -cshift), nps2 = pack2(-pshift, -pshift);
   const int plane_sz = nx * ny;
   float* outp = Yout + S.off_blk + (long long)vec * S.nd + (long long)y * nx + x4;   // advances one plane per output
   const int rc = (ty + kN0) * W + kHaloX + x4;   // this thread's centre in an input slot
   const int ra = ty * nx + x4;                    // ... and in the V / Y_prev boxes
-  // x-neighbour chunks q = 0..4 cover columns x4 - 8 + 4q .. +3 (wholly inside [0, n_x) or wholly
+  // x-neighbour chunks of four columns x4 - 8 + 4q .. +3 (wholly inside [0, n_x) or wholly
   // outside, as n_x and x4 are multiples of 4); along a periodic x axis the outside chunks read
-  // the wrapped columns of the same row: offsets of chunks 0, 1 (left) and 3, 4 (right)
+  // the wrapped columns of the same row: offsets of chunks 0, 1 (left) and 3, 4 (right).  Of
+  // chunks 0 and 4 only the pair next to the centre is within reach of the 6-point stencil.
   const int wl0 = (px && x4 < 8) ? nx : 0, wl1 = (px && x4 < 4) ? nx : 0;
   const int wr3 = (px && x4 + 4 >= nx) ? -nx : 0, wr4 = (px && x4 + 8 >= nx) ? -nx : 0;
   const int Wr = kW ? kW : W;   // row pitch of a slot (compile-time where specialised)
 
-  float acc[kQ][4];
+  // accumulators of the 13 output planes in flight, x-points (x4, x4+1) and (x4+2, x4+3)
+  f2 acc[kQ][2];
 #pragma unroll
-  for (int k = 0; k < kQ; ++k) acc[k][0] = acc[k][1] = acc[k][2] = acc[k][3] = 0.f;
+  for (int k = 0; k < kQ; ++k) acc[k][0] = acc[k][1] = 0ull;
 
   int slot = 0;
   uint32_t par = 0;
@@ -245,46 +290,73 @@ k_stencil_tma(const SubDev* __restrict__ subs, const TmaJob* __restrict__ jobs, 
       }
       const int zt = zbase + it;
       const int zo = zt - kN0;
-      float4 yp = make_float4(0.f, 0.f, 0.f, 0.f);
+      ulonglong2 yp = make_ulonglong2(0ull, 0ull);
       if ((pz || zt < nz) && active) {
         const float* C = P + rc;
-        float xr[20];
+        f2 c01, c23;
+        if (zt >= 0 && zt < nz) {
+          // row of the plane: packed pairs x[k], k = 2..17 relative to x4 - 8 (centre at 8..11)
+          const f2 x2 = *reinterpret_cast<const f2*>(C - 6 + wl0);
+          const ulonglong2 x4v = *reinterpret_cast<const ulonglong2*>(C - 4 + wl1);
+          const ulonglong2 x8v = *reinterpret_cast<const ulonglong2*>(C);
+          const ulonglong2 x12v = *reinterpret_cast<const ulonglong2*>(C + 4 + wr3);
+          const f2 x16 = *reinterpret_cast<const f2*>(C + 8 + wr4);
+          const ulonglong2 vp = *reinterpret_cast<const ulonglong2*>(P + off_v + ra);
+          c01 = x8v.x;
+          c23 = x8v.y;
+          // centre and potential: (V - c) y + w_c y
+          f2 t01 = fma2(add2(vp.x, ncs2), c01, mul2(sw.wc, c01));
+          f2 t23 = fma2(add2(vp.y, ncs2), c23, mul2(sw.wc, c23));
+          // even x-offsets: both partners of a pair are aligned pairs
+          t01 = fma2(sw.wx[2], add2(x8v.y, x4v.y), t01);
+          t23 = fma2(sw.wx[2], add2(x12v.x, x8v.x), t23);
+          t01 = fma2(sw.wx[4], add2(x12v.x, x4v.x), t01);
+          t23 = fma2(sw.wx[4], add2(x12v.y, x4v.y), t23);
+          t01 = fma2(sw.wx[6], add2(x12v.y, x2), t01);
+          t23 = fma2(sw.wx[6], add2(x16, x4v.x), t23);
+          // odd x-offsets on scalars
+          float x[20];
+          unpack2(x2, x[2], x[3]);
+          unpack2(x4v.x, x[4], x[5]);
+          unpack2(x4v.y, x[6], x[7]);
+          unpack2(x8v.x, x[8], x[9]);
+          unpack2(x8v.y, x[10], x[11]);
+          unpack2(x12v.x, x[12], x[13]);
+          unpack2(x12v.y, x[14], x[15]);
+          unpack2(x16, x[16], x[17]);
+          float o[4];
 #pragma unroll
-        for (int q = 0; q < 5; ++q) {
-          const int wo = q == 0 ? wl0 : (q == 1 ? wl1 : (q == 3 ? wr3 : (q == 4 ? wr4 : 0)));
-          const float4 v4 = *reinterpret_cast<const float4*>(C + (4 * q - kHaloX) + wo);
-          xr[4 * q] = v4.x; xr[4 * q + 1] = v4.y; xr[4 * q + 2] = v4.z; xr[4 * q + 3] = v4.w;
+          for (int r = 0; r < 4; ++r) o[r] = sw.wxs[1] * (x[9 + r] + x[7 + r]);
+#pragma unroll
+          for (int p = 3; p <= kN0; p += 2)
+#pragma unroll
+            for (int r = 0; r < 4; ++r) o[r] = fmaf(sw.wxs[p], x[8 + r + p] + x[8 + r - p], o[r]);
+          // y-neighbours
+#pragma unroll
+          for (int p = 1; p <= kN0; ++p) {
+            const ulonglong2 up = *reinterpret_cast<const ulonglong2*>(C + p * Wr);
+            const ulonglong2 dn = *reinterpret_cast<const ulonglong2*>(C - p * Wr);
+            t01 = fma2(sw.wy[p], add2(up.x, dn.x), t01);
+            t23 = fma2(sw.wy[p], add2(up.y, dn.y), t23);
+          }
+          acc[j][0] = add2(acc[j][0], add2(t01, pack2(o[0], o[1])));
+          acc[j][1] = add2(acc[j][1], add2(t23, pack2(o[2], o[3])));
+        } else {
+          // a plane beyond the z-ends (periodic z): only its z-neighbour contributions count
+          const ulonglong2 cv = *reinterpret_cast<const ulonglong2*>(C);
+          c01 = cv.x;
+          c23 = cv.y;
         }
-        const float4 v = *reinterpret_cast<const float4*>(P + off_v + ra);
-          const float c[4] = {xr[8], xr[9], xr[10], xr[11]};
-          const float vv[4] = {v.x, v.y, v.z, v.w};
-          float t[4];
 #pragma unroll
-          for (int r = 0; r < 4; ++r) t[r] = fmaf(vv[r] - cshift, c[r], sw.wc * c[r]);
-#pragma unroll
-          for (int p = 1; p <= kN0; ++p) {
-#pragma unroll
-            for (int r = 0; r < 4; ++r) t[r] += sw.wx[p] * (xr[8 + r + p] + xr[8 + r - p]);
-            const float4 up = *reinterpret_cast<const float4*>(C + p * Wr);
-            const float4 dn = *reinterpret_cast<const float4*>(C - p * Wr);
-            t[0] += sw.wy[p] * (up.x + dn.x);
-            t[1] += sw.wy[p] * (up.y + dn.y);
-            t[2] += sw.wy[p] * (up.z + dn.z);
-            t[3] += sw.wy[p] * (up.w + dn.w);
-          }
-#pragma unroll
-          for (int r = 0; r < 4; ++r) acc[j][r] += t[r];
-#pragma unroll
-          for (int p = 1; p <= kN0; ++p) {
-            const int u = (j + p) % kQ, d = (j + kQ - p) % kQ;
-#pragma unroll
-            for (int r = 0; r < 4; ++r) {
-              acc[u][r] = fmaf(sw.wz[p], c[r], acc[u][r]);
-              acc[d][r] = fmaf(sw.wz[p], c[r], acc[d][r]);
-            }
-          }
+        for (int p = 1; p <= kN0; ++p) {
+          const int u = (j + p) % kQ, d = (j + kQ - p) % kQ;
+          acc[u][0] = fma2(sw.wz[p], c01, acc[u][0]);
+          acc[u][1] = fma2(sw.wz[p], c23, acc[u][1]);
+          acc[d][0] = fma2(sw.wz[p], c01, acc[d][0]);
+          acc[d][1] = fma2(sw.wz[p], c23, acc[d][1]);
+        }
       }
-      if (has_prev && zo >= 0 && active) yp = *reinterpret_cast<const float4*>(P + off_yp + ra);
+      if (has_prev && zo >= 0 && active) yp = *reinterpret_cast<const ulonglong2*>(P + off_yp + ra);
       __syncwarp();
       if (lane == 0) mbar_arrive(&empty[slot]);
       if (++slot == kNS) {
@@ -296,13 +368,11 @@ k_stencil_tma(const SubDev* __restrict__ subs, const TmaJob* __restrict__ jobs, 
       }
       // output plane z_t - 6 is complete
       const int f = (j + kQ - kN0) % kQ;
-      if (zo >= 0 && store_ok) {
-        *reinterpret_cast<float4*>(outp) =
-            make_float4(fmaf(-pshift, yp.x, scale * acc[f][0]), fmaf(-pshift, yp.y, scale * acc[f][1]),
-                        fmaf(-pshift, yp.z, scale * acc[f][2]), fmaf(-pshift, yp.w, scale * acc[f][3]));
-      }
+      if (zo >= 0 && store_ok)
+        *reinterpret_cast<ulonglong2*>(outp) =
+            make_ulonglong2(fma2(nps2, yp.x, mul2(scale2, acc[f][0])), fma2(nps2, yp.y, mul2(scale2, acc[f][1])));
       if (zo >= 0) outp += plane_sz;
-      acc[f][0] = acc[f][1] = acc[f][2] = acc[f][3] = 0.f;
+      acc[f][0] = acc[f][1] = 0ull;
     }
   }
 }
@@ -451,12 +521,18 @@ void launch_stencil_tma(const SubDev* d_subs, const TmaClass& cls, const CUtenso
               ihz = (float)(-0.5 / (cls.h[2] * cls.h[2]));
   static const double fdw[kN0 + 1] = {-5369.0 / 1800.0, 12.0 / 7.0, -15.0 / 56.0, 10.0 / 189.0,
                                       -1.0 / 112.0,     2.0 / 1925.0, -1.0 / 16632.0};
+  auto both = [](float v) {
+    uint32_t u;
+    memcpy(&u, &v, 4);
+    return ((f2)u << 32) | u;
+  };
   for (int p = 0; p <= kN0; ++p) {
-    sw.wx[p] = (float)fdw[p] * ihx;
-    sw.wy[p] = (float)fdw[p] * ihy;
-    sw.wz[p] = (float)fdw[p] * ihz;
+    sw.wxs[p] = (float)fdw[p] * ihx;
+    sw.wx[p] = both(sw.wxs[p]);
+    sw.wy[p] = both((float)fdw[p] * ihy);
+    sw.wz[p] = both((float)fdw[p] * ihz);
   }
-  sw.wc = sw.wx[0] + sw.wy[0] + sw.wz[0];
+  sw.wc = both((float)fdw[0] * ihx + (float)fdw[0] * ihy + (float)fdw[0] * ihz);
   // row pitches of the common subdomain widths as compile-time constants (immediate offsets)
   switch (cls.W) {
     case 80: launch_variant<80>(cls, smem, d_subs, d_maps, buf_in, buf_prev, Yout, coef, step, status, sw, st); break;
