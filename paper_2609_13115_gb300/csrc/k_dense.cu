@@ -1,5 +1,7 @@
 // Subspace contractions on SIMT cores (FP64 path), interior weights, Fermi level, density,
 // and the small set-up kernels (restriction, projector norms, Lanczos bound, random start).
+#include <cooperative_groups.h>
+#include <cstdlib>
 #include <cuda_fp16.h>
 
 #include "xls_internal.h"
@@ -315,8 +317,164 @@ k_fermi(const double* __restrict__ lam, const double* __restrict__ c, int n, dou
   }
 }
 
+// The same Fermi level on a cluster of kFermiCL CTAs, so that the FP64 Fermi-function sums of
+// every iteration run on kFermiCL SMs.  Every CTA sums its share of the states and pushes its
+// partial sums into a slot of every CTA's shared memory (distributed shared memory); after one
+// cluster barrier every CTA adds the slots in the same order and takes the same decision.  The
+// bracket comes from a histogram of 2 c_n over the eigenvalue range (no exponentials): the bin
+// where the cumulative count crosses N_e, widened by 40 kT on both sides (where the Fermi
+// function has reached e^-40), holds the root whenever N_e changes inside it; Newton steps on
+// N_e(mu), kept inside the bracket, then take a few iterations instead of dozens of bisections.
+namespace cg = cooperative_groups;
+constexpr int kFermiCL = 8, kFermiBins = 256;
+
+__global__ void __launch_bounds__(256)
+k_fermi_cl(const double* __restrict__ lam, const double* __restrict__ c, int n, double ne, double kT, double* out,
+           double* occ, int* status) {
+  cg::cluster_group cl = cg::this_cluster();
+  const int CL = (int)cl.num_blocks(), rank = (int)cl.block_rank();
+  __shared__ double red[32];
+  __shared__ double part[2][kFermiCL][4];         // partial sums of every CTA, alternate buffers
+  __shared__ double hist[kFermiCL][kFermiBins];   // histogram of every CTA
+  __shared__ double hloc[kFermiBins];
+  __shared__ double s_cum[kFermiBins];
+  const int t = threadIdx.x;
+  const int i0 = rank * blockDim.x + t, stride = CL * blockDim.x;
+  int buf = 0;
+  // all-gather of four scalars; returns after the cluster barrier
+  auto gather = [&](double a0, double a1, double a2, double a3) {
+    if (t < CL) {
+      double* dst = cl.map_shared_rank(&part[buf][rank][0], t);
+      dst[0] = a0; dst[1] = a1; dst[2] = a2; dst[3] = a3;
+    }
+    cl.sync();
+  };
+  auto total = [&](int k) {
+    double s = 0.0;
+    for (int q = 0; q < CL; ++q) s += part[buf][q][k];
+    return s;
+  };
+  double lmin = 1e300, lmax = -1e300;
+  for (int i = i0; i < n; i += stride) {
+    lmin = fmin(lmin, lam[i]);
+    lmax = fmax(lmax, lam[i]);
+  }
+  lmax = block_sum_max(lmax, red);
+  lmin = -block_sum_max(-lmin, red);
+  gather(lmin, lmax, 0.0, 0.0);
+  double lo = 1e300, hi = -1e300;
+  for (int q = 0; q < CL; ++q) {
+    lo = fmin(lo, part[buf][q][0]);
+    hi = fmax(hi, part[buf][q][1]);
+  }
+  lo -= 1.0;
+  hi += 1.0;
+  buf ^= 1;
+  // histogram bracket
+  const double w = (hi - lo) / kFermiBins;
+  for (int b = t; b < kFermiBins; b += blockDim.x) hloc[b] = 0.0;
+  __syncthreads();
+  for (int i = i0; i < n; i += stride) {
+    const int b = min(kFermiBins - 1, max(0, (int)((lam[i] - lo) / w)));
+    atomicAdd(&hloc[b], 2.0 * c[i]);
+  }
+  __syncthreads();
+  for (int b = t; b < kFermiBins; b += blockDim.x)
+    for (int q = 0; q < CL; ++q) cl.map_shared_rank(&hist[rank][0], q)[b] = hloc[b];
+  cl.sync();
+  if (t == 0) {
+    double run = 0.0;
+    for (int b = 0; b < kFermiBins; ++b) {
+      for (int q = 0; q < CL; ++q) run += hist[q][b];
+      s_cum[b] = run;
+    }
+  }
+  __syncthreads();
+  int bstar = kFermiBins - 1;
+  for (int b = 0; b < kFermiBins; ++b)
+    if (s_cum[b] >= ne) { bstar = b; break; }
+  auto count2 = [&](double mu, double& dn) -> double {
+    double acc = 0.0, dacc = 0.0;
+    for (int i = i0; i < n; i += stride) {
+      const double g = fermi_fn((lam[i] - mu) / kT);
+      acc += g * c[i];
+      dacc += g * (1.0 - g) * c[i];
+    }
+    acc = block_sum(acc, red);
+    dacc = block_sum(dacc, red);
+    gather(acc, dacc, 0.0, 0.0);
+    const double nm = 2.0 * total(0);
+    dn = 2.0 * total(1) / kT;
+    buf ^= 1;
+    return nm;
+  };
+  double dn;
+  double blo = fmax(lo, lo + fmax(bstar - 1, 0) * w - 40.0 * kT);
+  double bhi = fmin(hi, lo + fmin(bstar + 2, kFermiBins) * w + 40.0 * kT);
+  double nlo = count2(blo, dn), nhi = count2(bhi, dn);
+  if (!(nlo <= ne && ne <= nhi)) {
+    blo = lo;
+    bhi = hi;
+    nlo = count2(blo, dn);
+    nhi = count2(bhi, dn);
+    if (!(nlo <= ne && ne <= nhi)) {
+      if (rank == 0 && t == 0) { *status = XLS_ENOCONV; out[0] = out[1] = out[2] = out[3] = 0.0; }
+      return;
+    }
+  }
+  lo = blo;
+  hi = bhi;
+  double mu_k = 0.5 * (lo + hi);
+  for (int it = 0; it < 200; ++it) {
+    const double nm = count2(mu_k, dn);
+    if (nm < ne) lo = mu_k; else hi = mu_k;
+    if (nm == ne || hi - lo <= 1e-14) break;
+    double next = (dn > 0.0) ? mu_k - (nm - ne) / dn : 0.5 * (lo + hi);
+    if (!(next > lo && next < hi)) next = 0.5 * (lo + hi);
+    if (fabs(next - mu_k) <= 1e-15 * fmax(1.0, fabs(mu_k))) { mu_k = next; break; }
+    mu_k = next;
+  }
+  const double mu = mu_k;
+  double eb = 0.0, es = 0.0, nn = 0.0;
+  for (int i = i0; i < n; i += stride) {
+    const double g = fermi_fn((lam[i] - mu) / kT);
+    occ[i] = g;
+    eb += g * c[i] * lam[i];
+    const double q = 1.0 - g;
+    const double sl = (g > 0 ? g * log(g) : 0.0) + (q > 0 ? q * log(q) : 0.0);
+    es += c[i] * sl;
+    nn += g * c[i];
+  }
+  eb = block_sum(eb, red);
+  es = block_sum(es, red);
+  nn = block_sum(nn, red);
+  gather(eb, es, nn, 0.0);
+  if (rank == 0 && t == 0) {
+    out[0] = mu;
+    out[1] = 2.0 * total(0);
+    out[2] = -2.0 * kT * total(1);
+    out[3] = 2.0 * total(2);
+  }
+}
+
 void launch_fermi_occ(const double* lam, const double* c, int n_tot, double n_e, double kT, double* out4, double* occ,
                       int* status, cudaStream_t st) {
+  if (!std::getenv("XLS_FERMI_SINGLE")) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(kFermiCL);
+    cfg.blockDim = dim3(256);
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = kFermiCL;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    if (cudaLaunchKernelEx(&cfg, k_fermi_cl, lam, c, n_tot, n_e, kT, out4, occ, status) == cudaSuccess) return;
+    cudaGetLastError();
+  }
   k_fermi<<<1, 1024, 0, st>>>(lam, c, n_tot, n_e, kT, out4, occ, status);
 }
 

@@ -295,7 +295,6 @@ k_tri_bisect(const SubDev* __restrict__ subs, double* vecs) {
   double* d = vecs + 8LL * S.off_state;
   double* e = d + n;
   double* lam32 = d + 3 * n;
-  double* cst = d + 4 * n;
   extern __shared__ float smf[];
   float* df = smf;
   float* e2f = smf + n;
@@ -327,7 +326,7 @@ k_tri_bisect(const SubDev* __restrict__ subs, double* vecs) {
   const int sub = threadIdx.x & 3;
   const unsigned gmask = 0xFu << (threadIdx.x & 28);   // the four lanes of this group
   const int groups = blockDim.x >> 2;
-  for (int i = threadIdx.x >> 2; i < n; i += groups) {  // uniform inside a group
+  for (int i = blockIdx.y * groups + (threadIdx.x >> 2); i < n; i += groups * gridDim.y) {  // uniform inside a group
     float lo = s_gl, hi = s_gu;
     for (int it = 0; it < 26; ++it) {
       const float w = hi - lo;
@@ -345,15 +344,24 @@ k_tri_bisect(const SubDev* __restrict__ subs, double* vecs) {
     }
     if (sub == 0) lam32[i] = 0.5 * ((double)lo + (double)hi);
   }
-  __syncthreads();
+  if (blockIdx.y == 0 && threadIdx.x == 0) d[5 * n + 2] = s_tnorm;
+}
+
+// clusters of the bisection estimates (after all of them are in): runs of eigenvalues closer than
+// 1e-4 ||T|| are one cluster, solved together by one thread of the vector stage
+__global__ void k_tri_clusters(const SubDev* __restrict__ subs, double* vecs) {
+  const SubDev& S = subs[blockIdx.x];
+  const int n = S.ns;
+  double* d = vecs + 8LL * S.off_state;
+  const double* lam32 = d + 3 * n;
+  double* cst = d + 4 * n;
   if (threadIdx.x == 0) {
-    const double ctol = 1e-4 * s_tnorm;
+    const double ctol = 1e-4 * d[5 * n + 2];
     int c = 0;
     for (int i = 0; i < n; ++i)
       if (i == 0 || lam32[i] - lam32[i - 1] > ctol) cst[c++] = (double)i;
     cst[c] = (double)n;
     d[5 * n + 1] = (double)c;
-    d[5 * n + 2] = s_tnorm;
   }
 }
 
@@ -559,12 +567,72 @@ k_backtransform(const SubDev* __restrict__ subs, const double* __restrict__ Am, 
   }
 }
 
+// Same back-transformation with everything it touches in shared memory and one warp per column:
+// a CTA takes 8 columns of Z (8 warps), stages all n - 1 reflectors (the strict lower triangle
+// of the reduced matrix, packed by columns) and tau, and each warp applies the reflectors to its
+// column with lane-strided rows and a shuffle reduction, without block barriers.  Global memory
+// is read once at the start and Z written once at the end; the n / 8 CTAs per subdomain spread
+// the FP64 work over the SMs.
+constexpr int kBtCols = 8;
+
+__host__ __device__ inline long long bt_col_off(int k, int n) { return (long long)k * (n - 1) - (long long)k * (k - 1) / 2; }
+
+size_t backtransform_sm_bytes(int n) {
+  return ((size_t)kBtCols * n + (size_t)n * (n - 1) / 2 + (size_t)n) * sizeof(double);
+}
+
+__global__ void __launch_bounds__(kBtCols * 32)
+k_backtransform_sm(const SubDev* __restrict__ subs, const double* __restrict__ Am, const double* __restrict__ vecs,
+                   double* Zm) {
+  const SubDev& S = subs[blockIdx.y];
+  const int n = S.ns;
+  const int c0 = blockIdx.x * kBtCols;
+  if (c0 >= n) return;
+  const double* A = Am + S.off_ss;
+  const double* tau = vecs + 8LL * S.off_state + 2 * n;
+  double* Z = Zm + S.off_ss;
+  extern __shared__ double sm[];
+  double* Zs = sm;                                        // [kBtCols][n]
+  double* Vs = Zs + (size_t)kBtCols * n;                  // reflector k: entries i = k+1 .. n-1
+  double* ts = Vs + (long long)n * (n - 1) / 2;           // tau
+  for (int q = threadIdx.x; q < n * kBtCols; q += blockDim.x) {
+    const int i = q / kBtCols, cc = q % kBtCols;
+    Zs[cc * n + i] = (c0 + cc < n) ? Z[(long long)i * n + c0 + cc] : 0.0;
+  }
+  for (long long q = threadIdx.x; q < (long long)n * n; q += blockDim.x) {
+    const int i = (int)(q / n), k = (int)(q - (long long)i * n);
+    if (i > k) Vs[bt_col_off(k, n) + (i - k - 1)] = (i == k + 1) ? 1.0 : A[q];
+  }
+  for (int k = threadIdx.x; k < n; k += blockDim.x) ts[k] = tau[k];
+  __syncthreads();
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  double* z = Zs + warp * n;
+  for (int k = n - 2; k >= 0; --k) {
+    const double t = ts[k];
+    if (t == 0.0) continue;
+    const long long vo = bt_col_off(k, n) - (k + 1);   // entry i > k of reflector k at Vs[vo + i]
+    double acc = 0.0;
+    for (int i = k + 1 + lane; i < n; i += 32) acc += Vs[vo + i] * z[i];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    const double td = t * acc;
+    for (int i = k + 1 + lane; i < n; i += 32) z[i] -= td * Vs[vo + i];
+    __syncwarp();
+  }
+  __syncthreads();
+  for (int q = threadIdx.x; q < n * kBtCols; q += blockDim.x) {
+    const int i = q / kBtCols, cc = q % kBtCols;
+    if (c0 + cc < n) Z[(long long)i * n + c0 + cc] = Zs[cc * n + i];
+  }
+}
+
 // ---- 2./6. blocked triangular solves: CTA = (8 right-hand-side columns, subdomain) ----------
 // lower: X = L^-1 B (B[i][c] = trans ? Bm[c][i] : Bm[i][c]); upper: X = L^-T B.  The 8 columns
-// live in shared memory; rows are taken in blocks of 32: one warp solves the block's diagonal
-// part (4 lanes per column split the dot product), then all warps subtract the block's
-// contribution from the remaining rows.  FP64 throughput, not latency, bounds it; the per-column
-// kernel above (warp per column) remains for reference runs with XLS_EIG=single.
+// live in shared memory; rows are taken in blocks of 32: the block's diagonal part of L is staged
+// in shared memory with the reciprocals of its diagonal, one warp solves it (4 lanes per column
+// split the dot product; the 32 dependent rows then wait on shared memory only), and all warps
+// subtract the block's contribution from the remaining rows.  The per-column kernel above (warp
+// per column) remains for reference runs with XLS_EIG=single.
 constexpr int kTrsmCols = 8, kTrsmRB = 32;
 
 template <bool kUpper>
@@ -578,31 +646,43 @@ k_trsm_blk(const SubDev* __restrict__ subs, const double* __restrict__ Lm, const
   const double* L = Lm + S.off_ss;
   const double* B = Bm + S.off_ss;
   double* X = Xm + S.off_ss;
-  extern __shared__ double xs[];   // [n][kTrsmCols]
+  extern __shared__ double xs[];   // [n][kTrsmCols], then the diagonal block of L
+  double* Ld = xs + (size_t)n * kTrsmCols;        // [kTrsmRB][kTrsmRB + 1]: (row, col) of the block
+  double* dinv = Ld + kTrsmRB * (kTrsmRB + 1);    // reciprocals of its diagonal
   for (int q = threadIdx.x; q < n * kTrsmCols; q += blockDim.x) {
     const int i = q / kTrsmCols, c = q % kTrsmCols;
     xs[q] = c < nc ? (trans ? B[(long long)(c0 + c) * n + i] : B[(long long)i * n + c0 + c]) : 0.0;
   }
-  __syncthreads();
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int nblk = (n + kTrsmRB - 1) / kTrsmRB;
   for (int bb = 0; bb < nblk; ++bb) {
     // rows of this block: lower from the top, upper from the bottom
     const int r0 = kUpper ? max(0, n - (bb + 1) * kTrsmRB) : bb * kTrsmRB;
     const int r1 = kUpper ? n - bb * kTrsmRB : min(n, r0 + kTrsmRB);
+    const int m = r1 - r0;
+    // the block's part of L in shared memory (all threads, coalesced), so that the sequential
+    // diagonal solve below waits on shared memory only
+    for (int q = threadIdx.x; q < m * m; q += blockDim.x) {
+      const int a = q / m, b = q % m;
+      Ld[a * (kTrsmRB + 1) + b] = L[(long long)(r0 + a) * n + r0 + b];
+    }
+    __syncthreads();
+    if (threadIdx.x < m) dinv[threadIdx.x] = 1.0 / Ld[threadIdx.x * (kTrsmRB + 2)];
+    __syncthreads();
     if (warp == 0) {
       const int c = lane >> 2, part = lane & 3;   // 8 columns x 4 partial sums
-      for (int t = 0; t < r1 - r0; ++t) {
-        const int i = kUpper ? r1 - 1 - t : r0 + t;
+      for (int t = 0; t < m; ++t) {
+        const int il = kUpper ? m - 1 - t : t;    // row within the block
         double acc = 0.0;
         if (!kUpper) {
-          for (int k = r0 + part; k < i; k += 4) acc += L[(long long)i * n + k] * xs[k * kTrsmCols + c];
+          for (int k = part; k < il; k += 4) acc += Ld[il * (kTrsmRB + 1) + k] * xs[(r0 + k) * kTrsmCols + c];
         } else {
-          for (int k = i + 1 + part; k < r1; k += 4) acc += L[(long long)k * n + i] * xs[k * kTrsmCols + c];
+          for (int k = il + 1 + part; k < m; k += 4) acc += Ld[k * (kTrsmRB + 1) + il] * xs[(r0 + k) * kTrsmCols + c];
         }
         acc += __shfl_xor_sync(0xffffffffu, acc, 1);
         acc += __shfl_xor_sync(0xffffffffu, acc, 2);
-        if (part == 0) xs[i * kTrsmCols + c] = (xs[i * kTrsmCols + c] - acc) / L[(long long)i * n + i];
+        const int i = r0 + il;
+        if (part == 0) xs[i * kTrsmCols + c] = (xs[i * kTrsmCols + c] - acc) * dinv[il];
         __syncwarp();
       }
     }
@@ -638,7 +718,7 @@ static void trsm(bool upper, int max_ns, dim3 gt, const SubDev* d_subs, const do
                  double* X, cudaStream_t st, bool blocked = true) {
   if (blocked) {
     dim3 g((max_ns + kTrsmCols - 1) / kTrsmCols, gt.y);
-    const size_t smem = (size_t)max_ns * kTrsmCols * sizeof(double);
+    const size_t smem = ((size_t)max_ns * kTrsmCols + kTrsmRB * (kTrsmRB + 1) + kTrsmRB) * sizeof(double);
     if (smem > 48 * 1024) {
       cudaFuncSetAttribute(k_trsm_blk<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
       cudaFuncSetAttribute(k_trsm_blk<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -688,16 +768,20 @@ void launch_eig(const SubDev* d_subs, int n_sub, int max_ns, double* Ms, double*
   if (cluster && launch_tridiag_cluster(d_subs, n_sub, max_ns, Hs, vecs, st)) {
   } else if (smem_ok(k_tridiag<true>, mat + vbytes)) k_tridiag<true><<<n_sub, 512, mat + vbytes, st>>>(d_subs, Hs, vecs, max_ns);
   else k_tridiag<false><<<n_sub, 512, vbytes, st>>>(d_subs, Hs, vecs, max_ns);
-  k_tri_bisect<<<n_sub, std::min(1024, ((4 * max_ns + 31) / 32) * 32), 2 * max_ns * sizeof(float), st>>>(d_subs,
-                                                                                                      vecs);
+  // 32 eigenvalue indices (128 threads) per CTA, spread over the SMs
+  k_tri_bisect<<<dim3(n_sub, (max_ns + 31) / 32), 128, 2 * max_ns * sizeof(float), st>>>(d_subs, vecs);
+  k_tri_clusters<<<n_sub, 32, 0, st>>>(d_subs, vecs);
   {
     // vector stage: 32 threads per CTA with shared-memory work arrays where they fit, one CTA per
-    // 32 clusters of a subdomain; else 128 threads per CTA on the global scratch
+    // 32 clusters of a subdomain; else 128 threads per CTA on the global scratch (8 threads per
+    // CTA, spreading the clusters over more SMs, measured no faster: the longest cluster's
+    // dependent FP64 chain sets the time)
+    constexpr int kVecThreads = 32;
     const size_t per_thread = 3 * (size_t)max_ns * sizeof(double);
-    const int groups = (max_ns + 31) / 32;
-    if (per_thread * 32 <= 200 * 1024 && smem_ok(k_tri_eig<true>, per_thread * 32)) {
+    const int groups = (max_ns + kVecThreads - 1) / kVecThreads;
+    if (per_thread * kVecThreads <= 200 * 1024 && smem_ok(k_tri_eig<true>, per_thread * kVecThreads)) {
       dim3 gv(n_sub, groups);
-      k_tri_eig<true><<<gv, 32, per_thread * 32, st>>>(d_subs, vecs, W, scratch, 0, R, lam, max_ns);
+      k_tri_eig<true><<<gv, kVecThreads, per_thread * kVecThreads, st>>>(d_subs, vecs, W, scratch, 0, R, lam, max_ns);
     } else {
       dim3 gv(n_sub, 1);
       k_tri_eig<false><<<gv, kTriThreads, 0, st>>>(d_subs, vecs, W, scratch, 3LL * max_ns * kTriThreads, R, lam,
@@ -705,7 +789,12 @@ void launch_eig(const SubDev* d_subs, int n_sub, int max_ns, double* Ms, double*
     }
   }
   dim3 gb((max_ns + 31) / 32, n_sub);
-  k_backtransform<<<gb, 256, (max_ns + 256) * sizeof(double), st>>>(d_subs, Hs, vecs, W);
+  const size_t bt_smem = backtransform_sm_bytes(max_ns);
+  if (bt_smem <= 200 * 1024 && smem_ok(k_backtransform_sm, bt_smem))
+    k_backtransform_sm<<<dim3((max_ns + kBtCols - 1) / kBtCols, n_sub), kBtCols * 32, bt_smem, st>>>(d_subs, Hs, vecs,
+                                                                                                   W);
+  else
+    k_backtransform<<<gb, 256, (max_ns + 256) * sizeof(double), st>>>(d_subs, Hs, vecs, W);
   trsm(true, max_ns, gt, d_subs, Ms, W, 0, Y, st, cluster);     // Y = L^-T Z
 }
 

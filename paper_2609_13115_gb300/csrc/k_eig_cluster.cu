@@ -406,6 +406,13 @@ static bool launch_cluster(K kernel, int n_sub, int CL, size_t smem, cudaStream_
   attr[0].val.clusterDim.z = 1;
   cfg.attrs = attr;
   cfg.numAttrs = 1;
+  // ask the occupancy calculator before launching: a refused launch inside a stream capture would
+  // end the capture
+  int active = 0;
+  if (cudaOccupancyMaxActiveClusters(&active, (const void*)kernel, &cfg) != cudaSuccess || active < 1) {
+    cudaGetLastError();
+    return false;
+  }
   cudaError_t err;
   if (tridiag)
     err = cudaLaunchKernelEx(&cfg, (void (*)(const SubDev*, double*, double*))kernel, subs, m, (double*)third);
@@ -418,20 +425,22 @@ static bool launch_cluster(K kernel, int n_sub, int CL, size_t smem, cudaStream_
   return true;
 }
 
+// Both factorisations run on 8-CTA clusters (16, a non-portable size, only where 8 does not fit:
+// measured at N_s = 160, the extra barrier latency of 16 CTAs outweighs their extra FP64 pipes).
 bool launch_cholesky_cluster(const SubDev* d_subs, int n_sub, int max_ns, double* Ms, int* status, cudaStream_t st) {
-  size_t smem = 0;
-  const int CL = pick_cluster(max_ns, 2 * (size_t)(max_ns + 1) * sizeof(double), smem);
-  if (!CL) return false;
-  return launch_cluster(k_cholesky_cl, n_sub, CL, smem, st, d_subs, Ms, status, false);
+  for (int CL : {8, 16}) {
+    const size_t smem = ((size_t)(max_ns + CL - 1) / CL * max_ns + 2 * (size_t)(max_ns + 1)) * sizeof(double);
+    if (smem <= 200 * 1024 && launch_cluster(k_cholesky_cl, n_sub, CL, smem, st, d_subs, Ms, status, false)) return true;
+  }
+  return false;
 }
 
 bool launch_tridiag_cluster(const SubDev* d_subs, int n_sub, int max_ns, double* A, double* vecs, cudaStream_t st) {
   size_t smem = 0;
   // one barrier per column: partials [2][8][n], pivot rows [2][n], v, w, p
-  const int CL = pick_cluster(max_ns, (2 * 16 + 2 + 3) * (size_t)max_ns * sizeof(double), smem);
-  if (CL) {
+  for (int CL : {8, 16}) {
     const size_t exact = ((size_t)(max_ns + CL - 1) / CL * max_ns + (2 * (size_t)CL + 5) * max_ns) * sizeof(double);
-    if (launch_cluster(k_tridiag_cl1, n_sub, CL, exact, st, d_subs, A, vecs, true)) return true;
+    if (exact <= 200 * 1024 && launch_cluster(k_tridiag_cl1, n_sub, CL, exact, st, d_subs, A, vecs, true)) return true;
   }
   const int CL4 = pick_cluster(max_ns, (2 * (size_t)max_ns + 4) * sizeof(double), smem);
   if (!CL4) return false;

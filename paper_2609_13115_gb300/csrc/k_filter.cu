@@ -254,8 +254,8 @@ k_proj_fill(const SubDev* __restrict__ subs, const ProjSlot* __restrict__ slots,
 // same 8-vector slice of every subdomain's block (tens of MB: it stays in L2 and each Y element,
 // shared by the about two spheres that contain its point, comes from DRAM about once).  Warp w
 // takes vectors 8 (w % kVH) .. +7 and every kPH-th 32-point chunk of the table from chunk
-// w / kVH; a lane two points at a time (16 loads in flight); lanes and warps are reduced at the
-// end.
+// w / kVH; a lane two points at a time (16 loads in flight); lanes (transpose reduction) and
+// warps are reduced at the end.
 constexpr int kPV = 8;
 constexpr int kVH = kPV / 8, kPH = 8 / kVH;   // vector halves and point phases of the 8 warps
 
@@ -303,15 +303,20 @@ k_nl_project(const SubDev* __restrict__ subs, const ProjSlot* __restrict__ slots
         acc[3][v] += c.w * y0[v] + d.w * y1[v];
       }
     }
+  // transpose reduction over the lanes: after five halving steps lane q = l * 8 + v holds the
+  // warp's sum of acc[l][v] (31 exchanges instead of 32 x 5)
+  T* a = &acc[0][0];
 #pragma unroll
-  for (int l = 0; l < 4; ++l)
+  for (int h = 16; h >= 1; h >>= 1) {
+    const bool up = (lane & h) != 0;
 #pragma unroll
-    for (int v = 0; v < 8; ++v) {
-      T s = acc[l][v];
-#pragma unroll
-      for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-      if (lane == 0) red[ph][vh * 32 + l * 8 + v] = s;
+    for (int q = 0; q < h; ++q) {
+      const T send = up ? a[q] : a[q + h];
+      const T keep = up ? a[q + h] : a[q];
+      a[q] = keep + __shfl_xor_sync(0xffffffffu, send, h);
     }
+  }
+  red[ph][vh * 32 + lane] = a[0];
   __syncthreads();
   if (threadIdx.x < kPV * 4) {
     const int h = threadIdx.x / 32, l = (threadIdx.x / 8) % 4, v = threadIdx.x % 8;

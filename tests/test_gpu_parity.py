@@ -242,6 +242,32 @@ def test_tma_stencil_matches_oracle_and_generic(wname, monkeypatch):
         assert relerr(outs["tma"][a], outs["generic"][a]) < 2e-6
 
 
+def test_fermi_cluster_matches_single_cta(monkeypatch):
+    """The Fermi level on a CTA cluster (histogram bracket + Newton) and on one CTA (bisection +
+    Newton) agree, and both match the oracle's."""
+    w = synth.workload(0)
+    V = pseudo.local_potential(w)
+    subs = dc.partition(w)
+    psi0 = _start_blocks(w, subs)
+    ref = dc.run(w, V, psi0, n_passes=1)
+    res = {}
+    for mode in ("cluster", "single"):
+        if mode == "single":
+            monkeypatch.setenv("XLS_FERMI_SINGLE", "1")
+        else:
+            monkeypatch.delenv("XLS_FERMI_SINGLE", raising=False)
+        with make_grid(w, V, xls.XLS_FP64) as g:
+            for a in range(w.n_sub):
+                xls.xls_orbitals_set(g.h, a, psi0[a])
+            xls.xls_chefsi_batch(g.h, w.degree, 1)
+            res[mode] = xls.xls_density(g.h, w.n_electrons, w.kT)
+    for mode in res:
+        mu, eb, es = res[mode]
+        assert abs(mu - ref.mu) < 1e-8, mode
+        assert abs(eb - ref.e_band) < 1e-8 * len(w.pos), mode
+    assert abs(res["cluster"][0] - res["single"][0]) < 1e-12
+
+
 @pytest.mark.parametrize("eig_mode", ["cluster", "single"])
 def test_eigensolver_large_block_matches_lapack(eig_mode, monkeypatch):
     """N_s = 160 (the bench's block size): Ritz values of the GPU's own M_s, H_s against the
