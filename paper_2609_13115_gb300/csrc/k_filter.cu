@@ -282,10 +282,20 @@ k_nl_project(const SubDev* __restrict__ subs, const ProjSlot* __restrict__ slots
   const T* yb = Y + S.off_blk + (long long)v0 * S.nd;
   const int* ib = idx + A.pt_off;
   const T4* cb = chi + A.pt_off;
+  // the point indices of the next iteration are fetched one iteration ahead, so that only the Y
+  // gathers (not the table loads before them) wait on memory
+  const int pfirst = ph * 32 + lane;
+  int ng0 = pfirst < A.pt_n ? ib[pfirst] : 0;
+  int ng1 = pfirst + 32 * kPH < A.pt_n ? ib[pfirst + 32 * kPH] : 0;
   if (nv > 0)
-    for (int p = ph * 32 + lane; p < A.pt_n; p += 64 * kPH) {
+    for (int p = pfirst; p < A.pt_n; p += 64 * kPH) {
       const bool two = p + 32 * kPH < A.pt_n;
-      const int g0 = ib[p], g1 = two ? ib[p + 32 * kPH] : g0;
+      const int g0 = ng0, g1 = two ? ng1 : g0;
+      const int pn = p + 64 * kPH;
+      if (pn < A.pt_n) {
+        ng0 = ib[pn];
+        ng1 = pn + 32 * kPH < A.pt_n ? ib[pn + 32 * kPH] : 0;
+      }
       const T4 c = cb[p];
       T4 d = cb[two ? p + 32 * kPH : p];
       if (!two) { d.x = (T)0; d.y = (T)0; d.z = (T)0; d.w = (T)0; }
@@ -419,8 +429,10 @@ k_nl_back_csr(const SubDev* __restrict__ subs, const long long* __restrict__ row
   __syncthreads();
   T* yb = Yout + S.off_blk + (long long)v0 * S.nd;
   const long long end = min(S.nd, p0 + kBackPts);
-  // two points per thread per iteration; the read half of the read-modify-write is issued before
-  // the table rows are walked, so that both latencies overlap
+  // two points per thread per iteration; the sum over the table rows is formed in registers and
+  // added to Y_out with fire-and-forget reductions (red.global.add): the read-modify-write happens
+  // in L2, no load of Y sits on the thread's critical path, and each element receives exactly one
+  // addition (deterministic)
   for (long long g = p0 + threadIdx.x; g < end; g += 2 * blockDim.x) {
     const long long gB = g + blockDim.x;
     const bool hasB = gB < end;
@@ -428,10 +440,7 @@ k_nl_back_csr(const SubDev* __restrict__ subs, const long long* __restrict__ row
     const long long rB0 = hasB ? row_ptr[S.off_pt + gB] : 0, rB1 = hasB ? row_ptr[S.off_pt + gB + 1] : 0;
     T yA[kBackVec], yB[kBackVec];
 #pragma unroll
-    for (int v = 0; v < kBackVec; ++v) {
-      yA[v] = (v < nv && rA1 > rA0) ? yb[(long long)v * S.nd + g] : (T)0;
-      yB[v] = (v < nv && rB1 > rB0) ? yb[(long long)v * S.nd + gB] : (T)0;
-    }
+    for (int v = 0; v < kBackVec; ++v) yA[v] = yB[v] = (T)0;
     for (long long e = rA0; e < rA1; ++e) {
       const int sl = rslot[e];
       const T4 c = rchi[e];
@@ -454,8 +463,8 @@ k_nl_back_csr(const SubDev* __restrict__ subs, const long long* __restrict__ row
     }
 #pragma unroll
     for (int v = 0; v < kBackVec; ++v) {
-      if (v < nv && rA1 > rA0) yb[(long long)v * S.nd + g] = yA[v];
-      if (v < nv && rB1 > rB0) yb[(long long)v * S.nd + gB] = yB[v];
+      if (v < nv && rA1 > rA0) atomicAdd(yb + (long long)v * S.nd + g, yA[v]);
+      if (v < nv && rB1 > rB0) atomicAdd(yb + (long long)v * S.nd + gB, yB[v]);
     }
   }
 }
