@@ -259,19 +259,21 @@ k_gram_tc(const SubDev* __restrict__ subs, const GramJob* __restrict__ jobs, con
     for (int p = 0; p * kFlushGram < nkt; ++p) {
       const int t_end = min((p + 1) * kFlushGram, nkt);
       for (int it = p * kFlushGram + grp; go && it < t_end; it += 2) {
-        if (it >= 2 && !bar_wait(&empty[grp], ((it >> 1) - 1) & 1)) { atomicExch(&s_fail, 1); go = false; break; }
         const long long k0 = (long long)(J.kt0 + it) * kKT;
         const uint32_t stage = sbase + grp * kGramStage;
-        // rounds of 8 items (row, 8-element chunk) per thread: the global loads of a round are
-        // issued before any item is split and stored, so that their latencies overlap
+        // rounds of 8 items (row, 8-element chunk) per thread: the global loads of a round (and the
+        // rows' scale exponents) are issued before any item is split and stored, so that their
+        // latencies overlap; the wait for the stage to be free comes after the first round's loads
         constexpr int kItems = 8;
         for (int q0 = 0; q0 < nrows * 8; q0 += 128 * kItems) {
           float4 a[kItems], b[kItems];
+          int ex[kItems];
 #pragma unroll
           for (int u = 0; u < kItems; ++u) {
             const int q = q0 + gt + u * 128;
             a[u] = make_float4(0.f, 0.f, 0.f, 0.f);
             b[u] = a[u];
+            ex[u] = 0;
             if (q >= nrows * 8) continue;
             const int row = q >> 3, c = q & 7;
             const bool isA = row < 128, isB1 = !isA && row < 128 + rowsB1;
@@ -284,6 +286,12 @@ k_gram_tc(const SubDev* __restrict__ subs, const GramJob* __restrict__ jobs, con
               a[u] = src[0];
               b[u] = src[1];
             }
+            if (kFp16 && valid) ex[u] = (isA || isB1 ? ex_f : ex_hf)[S.off_state + grow];
+          }
+          if (q0 == 0 && it >= 2 && !bar_wait(&empty[grp], ((it >> 1) - 1) & 1)) {
+            atomicExch(&s_fail, 1);
+            go = false;
+            break;
           }
 #pragma unroll
           for (int u = 0; u < kItems; ++u) {
@@ -292,11 +300,8 @@ k_gram_tc(const SubDev* __restrict__ subs, const GramJob* __restrict__ jobs, con
             const int row = q >> 3, c = q & 7;
             const bool isA = row < 128, isB1 = !isA && row < 128 + rowsB1;
             const int r = isA ? row : (isB1 ? row - 128 : row - 128 - rowsB1);
-            const int grow = isA ? i0 + r : j0 + r;
-            const bool valid = isA ? (grow < ns) : (r < nj);
             const uint32_t thi = isA ? stage : (isB1 ? stage + 2 * kTile : stage + 4 * kTile);
-            float sc = 1.f;
-            if (kFp16 && valid) sc = ldexpf(1.f, (isA || isB1 ? ex_f : ex_hf)[S.off_state + grow]);
+            const float sc = kFp16 ? ldexpf(1.f, ex[u]) : 1.f;
             uint4 hi, lo;
             split8<kFp16>(a[u], b[u], sc, hi, lo);
             const uint32_t off = kmaj_off(r, c);
@@ -304,6 +309,7 @@ k_gram_tc(const SubDev* __restrict__ subs, const GramJob* __restrict__ jobs, con
             sts128(thi + kTile + off, lo);
           }
         }
+        if (!go) break;
         fence_async_smem();
         bar_arrive(&full[grp]);
       }
@@ -609,13 +615,14 @@ k_rotate_tc(const SubDev* __restrict__ subs, const RotJob* __restrict__ jobs, co
   if (warp < 8) {
     for (int it = 0; it < nkt; ++it) {
       const int st = it % kStages;
-      if (it >= kStages && !bar_wait(&empty[st], ((it / kStages) - 1) & 1)) { atomicExch(&s_fail, 1); break; }
       const int k0 = it * kKT;
       const uint32_t stage = sbase + st * kRotStage;
       // A: 64 k-rows x 128 grid points, chunks of 8 points (MN-major), 4 items per thread; B:
       // n16 rows x 64 k of Y^T hi / lo (already split), K-major, up to 8 items per thread.  All
-      // global loads of the tile are issued before the stores, so that their latencies overlap.
+      // global loads of the tile (and the rows' scale exponents) are issued before the stores, so
+      // that their latencies overlap, and before the wait for the stage to be free.
       float4 a[4], b[4];
+      int ex[4];
 #pragma unroll
       for (int u = 0; u < 4; ++u) {
         const int q = threadIdx.x + u * kProducers;
@@ -624,11 +631,13 @@ k_rotate_tc(const SubDev* __restrict__ subs, const RotJob* __restrict__ jobs, co
         const long long g = g0 + c16 * 8;
         a[u] = make_float4(0.f, 0.f, 0.f, 0.f);
         b[u] = a[u];
+        ex[u] = 0;
         if (kk < ns && g < S.nd) {
           const float4* p = reinterpret_cast<const float4*>(f + (long long)kk * S.nd + g);
           a[u] = p[0];
           b[u] = p[1];
         }
+        if (kFp16 && kk < ns) ex[u] = ex_f[S.off_state + kk];
       }
       uint4 yh[8], yl[8];
 #pragma unroll
@@ -643,13 +652,12 @@ k_rotate_tc(const SubDev* __restrict__ subs, const RotJob* __restrict__ jobs, co
           yl[u] = *reinterpret_cast<const uint4*>(Ylo + e);
         }
       }
+      if (it >= kStages && !bar_wait(&empty[st], ((it / kStages) - 1) & 1)) { atomicExch(&s_fail, 1); break; }
 #pragma unroll
       for (int u = 0; u < 4; ++u) {
         const int q = threadIdx.x + u * kProducers;
         const int k = q >> 4, c16 = q & 15;
-        const int kk = k0 + k;
-        float sc = 1.f;
-        if (kFp16 && kk < ns) sc = ldexpf(1.f, ex_f[S.off_state + kk]);
+        const float sc = kFp16 ? ldexpf(1.f, ex[u]) : 1.f;
         uint4 hi, lo;
         split8<kFp16>(a[u], b[u], sc, hi, lo);
         const uint32_t off = mnmaj_off(c16 >> 3, k, c16 & 7);
@@ -722,32 +730,41 @@ k_rotate_tc(const SubDev* __restrict__ subs, const RotJob* __restrict__ jobs, co
 // Y (FP64, row-major [k][n]) -> Y^T hi/lo [n][kpad_max], zero padded.  FP16 path: row k of Y is
 // divided by 2^ex_f[k] (it multiplies column k of the A operand) and row n of Y^T is scaled by
 // 2^ex_y[n] so that its largest entry lies in (2^13, 2^14]; the epilogue divides column n by it.
+// One CTA per column n of one subdomain: the column's scaled maximum (FP16 path) by a block
+// reduction, then one element per thread, so that no thread runs a loop over the whole column.
 template <bool kFp16>
-__global__ void k_split_yt(const SubDev* __restrict__ subs, const double* __restrict__ Y, int kpad_max,
-                           const int* __restrict__ ex_f, int* ex_y, uint16_t* Yhi, uint16_t* Ylo) {
+__global__ void __launch_bounds__(128)
+k_split_yt(const SubDev* __restrict__ subs, const double* __restrict__ Y, int kpad_max,
+           const int* __restrict__ ex_f, int* ex_y, uint16_t* Yhi, uint16_t* Ylo) {
   const SubDev& S = subs[blockIdx.y];
   const int ns = S.ns;
+  const int n = blockIdx.x;
+  if (n >= ns) return;
   const long long yoff = (long long)S.off_state * kpad_max;
-  for (int n = blockIdx.x * blockDim.x + threadIdx.x; n < ns; n += gridDim.x * blockDim.x) {
-    int ey = 0;
-    if (kFp16) {
-      double mx = 0.0;
-      for (int k = 0; k < ns; ++k)
-        mx = fmax(mx, fabs(ldexp(Y[S.off_ss + (long long)k * ns + n], -ex_f[S.off_state + k])));
-      ey = (mx > 0.0) ? 14 - ilogb(mx) - 1 : 0;
-      ex_y[S.off_state + n] = ey;
+  __shared__ double red[4];
+  int ey = 0;
+  if (kFp16) {
+    double mx = 0.0;
+    for (int k = threadIdx.x; k < ns; k += blockDim.x)
+      mx = fmax(mx, fabs(ldexp(Y[S.off_ss + (long long)k * ns + n], -ex_f[S.off_state + k])));
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = mx;
+    __syncthreads();
+    mx = fmax(fmax(red[0], red[1]), fmax(red[2], red[3]));
+    ey = (mx > 0.0) ? 14 - ilogb(mx) - 1 : 0;
+    if (threadIdx.x == 0) ex_y[S.off_state + n] = ey;
+  }
+  for (int k = threadIdx.x; k < kpad_max; k += blockDim.x) {
+    double yv = 0.0;
+    if (k < ns) {
+      yv = Y[S.off_ss + (long long)k * ns + n];
+      if (kFp16) yv = ldexp(yv, ey - ex_f[S.off_state + k]);
     }
-    for (int k = 0; k < kpad_max; ++k) {
-      double yv = 0.0;
-      if (k < ns) {
-        yv = Y[S.off_ss + (long long)k * ns + n];
-        if (kFp16) yv = ldexp(yv, ey - ex_f[S.off_state + k]);
-      }
-      uint16_t h, l;
-      split1<kFp16>((float)yv, h, l);
-      Yhi[yoff + (long long)n * kpad_max + k] = h;
-      Ylo[yoff + (long long)n * kpad_max + k] = l;
-    }
+    uint16_t h, l;
+    split1<kFp16>((float)yv, h, l);
+    Yhi[yoff + (long long)n * kpad_max + k] = h;
+    Ylo[yoff + (long long)n * kpad_max + k] = l;
   }
 }
 
@@ -840,17 +857,17 @@ bool launch_gram_tc_single(const float* F, const float* HF, long long n_points, 
 void launch_rotate_tc(const SubDev* d_subs, int n_sub, int max_ns, const RotPlan& rp, const GramPlan& gp, bool fp16,
                       bool need_exponents, const float* F, const double* Y, float* Out, int* status, cudaStream_t st) {
   if (rp.n_jobs == 0) return;
-  dim3 gs(1, n_sub);
+  dim3 gs(max_ns, n_sub);
   if (fp16 && need_exponents) {   // the Gram of this pass did not run on tensor cores
     dim3 ge(max_ns, n_sub, 1);
     tc::k_vec_exponent<<<ge, 512, 0, st>>>(d_subs, n_sub, F, F, gp.d_ex_f, gp.d_ex_hf);
   }
   if (fp16) {
-    tc::k_split_yt<true><<<gs, 256, 0, st>>>(d_subs, Y, rp.kpad_max, gp.d_ex_f, rp.d_ex_y, rp.d_yhi, rp.d_ylo);
+    tc::k_split_yt<true><<<gs, 128, 0, st>>>(d_subs, Y, rp.kpad_max, gp.d_ex_f, rp.d_ex_y, rp.d_yhi, rp.d_ylo);
     tc::k_rotate_tc<true><<<rp.n_jobs, tc::kThreads, rotate_tc_smem(), st>>>(
         d_subs, rp.d_jobs, F, rp.d_yhi, rp.d_ylo, rp.kpad_max, gp.d_ex_f, rp.d_ex_y, Out, status);
   } else {
-    tc::k_split_yt<false><<<gs, 256, 0, st>>>(d_subs, Y, rp.kpad_max, nullptr, nullptr, rp.d_yhi, rp.d_ylo);
+    tc::k_split_yt<false><<<gs, 128, 0, st>>>(d_subs, Y, rp.kpad_max, nullptr, nullptr, rp.d_yhi, rp.d_ylo);
     tc::k_rotate_tc<false><<<rp.n_jobs, tc::kThreads, rotate_tc_smem(), st>>>(
         d_subs, rp.d_jobs, F, rp.d_yhi, rp.d_ylo, rp.kpad_max, nullptr, nullptr, Out, status);
   }
