@@ -409,7 +409,7 @@ k_tri_eig(const SubDev* __restrict__ subs, double* vecs, double* Zm, double* scr
           if (fabs(dp) < tiny) dp = dp < 0 ? -tiny : tiny;
           DI(0) = 1.0 / dp;
           for (int j = 1; j < n; ++j) {
-            const double l = e[j - 1] / dp;
+            const double l = e[j - 1] * DI(j - 1);   // e / dp through the reciprocal already formed
             LM(j - 1) = l;
             dp = (d[j] - sigma) - l * e[j - 1];
             if (fabs(dp) < tiny) dp = dp < 0 ? -tiny : tiny;
