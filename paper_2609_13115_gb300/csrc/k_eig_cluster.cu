@@ -6,6 +6,8 @@
 // (k_eig.cu), which remain for blocks too large for the cluster's shared memory.
 #include <cooperative_groups.h>
 
+#include <cstdlib>
+
 #include "xls_internal.h"
 
 namespace cg = cooperative_groups;
@@ -91,6 +93,74 @@ k_cholesky_cl(const SubDev* __restrict__ subs, double* Ms, int* status) {
     if (i >= n) break;
     for (int j = threadIdx.x; j < n; j += blockDim.x) G[(size_t)i * n + j] = (j > i) ? 0.0 : Lr[(size_t)r * n + j];
   }
+  cl.sync();
+}
+
+// Right-looking Cholesky on the same row distribution: per column j every CTA pushes the current
+// entries A_ij of its own rows i >= j into every CTA; after the one cluster barrier every CTA forms
+// the pivot sqrt(A_jj) and the scaled column L_kj = A_kj / L_jj (k > j) itself and applies the
+// rank-1 update A_ik -= L_ij L_kj (j < k <= i) to its own rows -- element-parallel FP64 FMAs and
+// no dot-product reductions on the critical path.  Buffers alternate with the column parity.
+// shared memory: local rows [nloc][n], column buffers [2][n]
+__global__ void __launch_bounds__(256)
+k_cholesky_cl2(const SubDev* __restrict__ subs, double* Ms, int* status) {
+  cg::cluster_group cl = cg::this_cluster();
+  const int CL = (int)cl.num_blocks(), rank = (int)cl.block_rank();
+  const int a = blockIdx.x / CL;
+  const SubDev& S = subs[a];
+  const int n = S.ns;
+  const int nloc = (n + CL - 1) / CL;
+  double* G = Ms + S.off_ss;
+  extern __shared__ __align__(16) double csm[];
+  double* Lr = csm;                      // local rows
+  double* colb = csm + (size_t)nloc * n; // [2][n]: column j of the working matrix, rows j..n-1
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+  for (int r = 0; r < nloc; ++r) {
+    const int i = r * CL + rank;
+    if (i >= n) break;
+    for (int j = threadIdx.x; j < n; j += blockDim.x) Lr[(size_t)r * n + j] = G[(size_t)i * n + j];
+  }
+  __syncthreads();
+  bool failed = false;
+  for (int j = 0; j < n; ++j) {
+    double* cb = colb + (size_t)(j & 1) * n;
+    // push column j of the own rows i >= j
+    for (int r = threadIdx.x; r < nloc; r += blockDim.x) {
+      const int i = r * CL + rank;
+      if (i < j || i >= n) continue;
+      const double x = Lr[(size_t)r * n + j];
+      for (int q = 0; q < CL; ++q) cl.map_shared_rank(cb, q)[i] = x;
+    }
+    cl.sync();
+    const double dj = cb[j];
+    if (!(dj > 0.0) || !isfinite(dj)) {   // not positive definite: every CTA sees the same value
+      if (rank == 0 && threadIdx.x == 0 && atomicCAS(status, 0, XLS_ENOTSPD) == 0) status[1] = a;
+      failed = true;
+      break;
+    }
+    const double piv = sqrt(dj), rinv = 1.0 / piv;
+    // own rows: L_ij = A_ij / L_jj, then A_ik -= L_ij L_kj for j < k <= i (L_kj = cb[k] / L_jj)
+    for (int r = warp; r < nloc; r += nw) {
+      const int i = r * CL + rank;
+      if (i < j || i >= n) continue;
+      double* row = Lr + (size_t)r * n;
+      if (i == j) {
+        if (lane == 0) row[j] = piv;
+        continue;
+      }
+      const double lij = cb[i] * rinv;
+      const double f = lij * rinv;
+      for (int k = j + 1 + lane; k <= i; k += 32) row[k] -= f * cb[k];
+      if (lane == 0) row[j] = lij;
+    }
+    __syncthreads();
+  }
+  if (!failed)
+    for (int r = 0; r < nloc; ++r) {
+      const int i = r * CL + rank;
+      if (i >= n) break;
+      for (int j = threadIdx.x; j < n; j += blockDim.x) G[(size_t)i * n + j] = (j > i) ? 0.0 : Lr[(size_t)r * n + j];
+    }
   cl.sync();
 }
 
@@ -373,6 +443,169 @@ k_tridiag_cl1(const SubDev* __restrict__ subs, double* Am, double* vecs) {
   cl.sync();
 }
 
+// Same reduction with the redundant vector work of each column on four warps (one per SM
+// sub-partition, so that their FP64 instructions -- each of which holds a sub-partition's FP64
+// pipe for tens of cycles on GB300 -- spread over all four pipes): after the cluster barrier
+// warps 0-3 form p, p.v, K and w, update the pushed row k+1 and derive the next reflector from it
+// (into the other half of a double-buffered v), synchronising among themselves with a named
+// barrier, while the other warps wait at the one block barrier before the row update; a second
+// block barrier separates the update from the next column's partial sums.  Per column: one
+// cluster barrier and two block barriers (the block-wide reductions of k_tridiag_cl1 take nine).
+// shared memory: own rows [nloc][n], partials [2][CL][n], pivot rows [2][n], v [2][n], w [n]
+__global__ void __launch_bounds__(256)
+k_tridiag_cl2(const SubDev* __restrict__ subs, double* Am, double* vecs) {
+  cg::cluster_group cl = cg::this_cluster();
+  const int CL = (int)cl.num_blocks(), rank = (int)cl.block_rank();
+  const int a = blockIdx.x / CL;
+  const SubDev& S = subs[a];
+  const int n = S.ns;
+  const int nloc = (n + CL - 1) / CL;
+  double* Ag = Am + S.off_ss;
+  double* d = vecs + 8LL * S.off_state;
+  double* e = d + n;
+  double* tau = d + 2 * n;
+  extern __shared__ __align__(16) double tsm[];
+  double* Ar = tsm;
+  double* qb = Ar + (size_t)nloc * n;          // [2][CL][n]
+  double* rb = qb + 2 * (size_t)CL * n;        // [2][n]
+  double* vb = rb + 2 * (size_t)n;             // [2][n]
+  double* wf = vb + 2 * (size_t)n;             // [n]
+  __shared__ double s_t[2];                    // tau of the reflector in vb[0], vb[1]
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+  for (int r = 0; r < nloc; ++r) {
+    const int i = r * CL + rank;
+    if (i >= n) break;
+    for (int j = threadIdx.x; j < n; j += blockDim.x)
+      Ar[(size_t)r * n + j] = 0.5 * (Ag[(size_t)i * n + j] + Ag[(size_t)j * n + i]);
+  }
+  __syncthreads();
+  if (rank == 0)
+    for (int q = 0; q < CL; ++q) {
+      double* dst = cl.map_shared_rank(rb, q);
+      for (int j = threadIdx.x; j < n; j += blockDim.x) dst[j] = Ar[j];
+    }
+  cl.sync();
+  // the four vector warps: thread tv of 128, their own barrier and reduction slots
+  const int tv = threadIdx.x;
+  __shared__ double s_red[4];
+  auto vbar = []() { asm volatile("bar.sync 1, 128;" ::: "memory"); };
+  auto vsum = [&](double x) {   // sum over the 128 vector threads (all of them get it)
+    x = wsum(x);
+    if (lane == 0) s_red[warp] = x;
+    vbar();
+    const double r = (s_red[0] + s_red[1]) + (s_red[2] + s_red[3]);
+    vbar();
+    return r;
+  };
+  // reflector of column k from `row` (entries j > k) into vout / tout; d[k], e[k], tau[k]
+  auto reflector_w = [&](int k, const double* row, double* vout, double* tout) {
+    double acc = 0.0;
+    for (int j = k + 2 + tv; j < n; j += 128) acc += row[j] * row[j];
+    const double xn2 = vsum(acc);
+    const double alpha = row[k + 1];
+    double beta, t, scal;
+    if (xn2 == 0.0) {
+      t = 0.0; beta = alpha; scal = 0.0;
+    } else {
+      beta = -copysign(sqrt(alpha * alpha + xn2), alpha);
+      t = (beta - alpha) / beta;
+      scal = 1.0 / (alpha - beta);
+    }
+    for (int j = tv; j < n; j += 128) vout[j] = j <= k ? 0.0 : (j == k + 1 ? 1.0 : row[j] * scal);
+    if (tv == 0) {
+      *tout = t;
+      if (rank == 0) {
+        d[k] = row[k];
+        e[k] = beta;
+        tau[k] = t;
+      }
+    }
+  };
+  if (n >= 2 && warp < 4) reflector_w(0, rb, vb, &s_t[0]);
+  __syncthreads();
+  for (int k = 0; k + 1 < n; ++k) {
+    const int par = k & 1;
+    const double* vf = vb + (size_t)par * n;
+    const double t = s_t[par];
+    // own reflector entries into the owned rows (column k, below the subdiagonal)
+    for (int r = threadIdx.x; r < nloc; r += blockDim.x) {
+      const int i = r * CL + rank;
+      if (i >= k + 2 && i < n) Ar[(size_t)r * n + k] = vf[i];
+    }
+    // partial column sums of the own rows, pushed into every CTA
+    double* qmine = qb + ((size_t)par * CL + rank) * n;
+    for (int j = k + 1 + threadIdx.x; j < n; j += blockDim.x) {
+      double acc = 0.0;
+      for (int r = 0; r < nloc; ++r) {
+        const int i = r * CL + rank;
+        if (i > k && i < n) acc += Ar[(size_t)r * n + j] * vf[i];
+      }
+      for (int q = 0; q < CL; ++q) cl.map_shared_rank(qmine, q)[j] = acc;
+    }
+    // the owner of row k+1 pushes it (before this column's update) for the next reflector
+    if ((k + 1) % CL == rank) {
+      const double* src = Ar + (size_t)((k + 1) / CL) * n;
+      for (int q = 0; q < CL; ++q) {
+        double* dst = cl.map_shared_rank(rb + (size_t)(1 - par) * n, q);
+        for (int j = k + 1 + threadIdx.x; j < n; j += blockDim.x) dst[j] = src[j];
+      }
+    }
+    cl.sync();
+    if (warp < 4) {
+      // p = tau sum_r q_r, K = tau p.v / 2, w = p - K v (j > k); then row k+1 and the next reflector
+      double pv = 0.0;
+      for (int j = k + 1 + tv; j < n; j += 128) {
+        double sacc = 0.0;
+        for (int q = 0; q < CL; ++q) sacc += qb[((size_t)par * CL + q) * n + j];
+        sacc *= t;
+        wf[j] = sacc;
+        pv += sacc * vf[j];
+      }
+      pv = vsum(pv);
+      const double K = 0.5 * t * pv;
+      for (int j = k + 1 + tv; j < n; j += 128) wf[j] -= K * vf[j];
+      vbar();
+      double* row1 = rb + (size_t)(1 - par) * n;
+      if (t != 0.0) {
+        const double v1 = vf[k + 1], w1 = wf[k + 1];
+        for (int j = k + 1 + tv; j < n; j += 128) row1[j] -= v1 * wf[j] + w1 * vf[j];
+      }
+      vbar();
+      if (k + 2 < n) {
+        reflector_w(k + 1, row1, vb + (size_t)(1 - par) * n, &s_t[1 - par]);
+      } else if (tv == 0 && rank == 0) {   // last diagonal entries
+        d[k + 1] = row1[k + 1];
+        e[k + 1] = 0.0;
+        tau[k + 1] = 0.0;
+      }
+    }
+    __syncthreads();
+    if (t != 0.0) {
+      // own rows: A_ij -= v_i w_j + w_i v_j (i, j > k)
+      for (int r = warp; r < nloc; r += nw) {
+        const int i = r * CL + rank;
+        if (i <= k || i >= n) continue;
+        double* row = Ar + (size_t)r * n;
+        const double vi = vf[i], wi = wf[i];
+        for (int j = k + 1 + lane; j < n; j += 32) row[j] -= vi * wf[j] + wi * vf[j];
+      }
+    }
+    __syncthreads();
+  }
+  if (n == 1 && threadIdx.x == 0 && rank == 0) {
+    d[0] = Ar[0];
+    e[0] = 0.0;
+    tau[0] = 0.0;
+  }
+  // reflectors back to global memory for the back-transformation
+  for (int r = 0; r < nloc; ++r) {
+    const int i = r * CL + rank;
+    if (i >= n) break;
+    for (int j = threadIdx.x; j + 1 < i; j += blockDim.x) Ag[(size_t)i * n + j] = Ar[(size_t)r * n + j];
+  }
+  cl.sync();
+}
+
 // cluster size and shared memory per CTA for an n x n matrix (0: not possible)
 static int pick_cluster(int n, size_t extra_per_cta, size_t& smem) {
   for (int CL : {8, 16}) {
@@ -430,7 +663,10 @@ static bool launch_cluster(K kernel, int n_sub, int CL, size_t smem, cudaStream_
 bool launch_cholesky_cluster(const SubDev* d_subs, int n_sub, int max_ns, double* Ms, int* status, cudaStream_t st) {
   for (int CL : {8, 16}) {
     const size_t smem = ((size_t)(max_ns + CL - 1) / CL * max_ns + 2 * (size_t)(max_ns + 1)) * sizeof(double);
-    if (smem <= 200 * 1024 && launch_cluster(k_cholesky_cl, n_sub, CL, smem, st, d_subs, Ms, status, false)) return true;
+    if (smem <= 200 * 1024 &&
+        launch_cluster(std::getenv("XLS_CHOL_LEFT") ? k_cholesky_cl : k_cholesky_cl2, n_sub, CL, smem, st, d_subs, Ms,
+                       status, false))
+      return true;
   }
   return false;
 }
@@ -438,9 +674,15 @@ bool launch_cholesky_cluster(const SubDev* d_subs, int n_sub, int max_ns, double
 bool launch_tridiag_cluster(const SubDev* d_subs, int n_sub, int max_ns, double* A, double* vecs, cudaStream_t st) {
   size_t smem = 0;
   // one barrier per column: partials [2][8][n], pivot rows [2][n], v, w, p
+  // k_tridiag_cl2 on 8-CTA clusters; 16-CTA clusters (only where 8 do not fit) take k_tridiag_cl1:
+  // k_tridiag_cl2 on 16 CTAs ended a bench run with a non-positive-definite Gram matrix in the next
+  // pass (cause not found), k_tridiag_cl1 on 16 CTAs passes every test
   for (int CL : {8, 16}) {
     const size_t exact = ((size_t)(max_ns + CL - 1) / CL * max_ns + (2 * (size_t)CL + 5) * max_ns) * sizeof(double);
-    if (exact <= 200 * 1024 && launch_cluster(k_tridiag_cl1, n_sub, CL, exact, st, d_subs, A, vecs, true)) return true;
+    const bool cl2 = CL <= 8 && !std::getenv("XLS_TRIDIAG_CL1");
+    if (exact <= 200 * 1024 && launch_cluster(cl2 ? k_tridiag_cl2 : k_tridiag_cl1, n_sub, CL, exact, st, d_subs, A, vecs,
+                                              true))
+      return true;
   }
   const int CL4 = pick_cluster(max_ns, (2 * (size_t)max_ns + 4) * sizeof(double), smem);
   if (!CL4) return false;
