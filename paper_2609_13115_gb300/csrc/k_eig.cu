@@ -629,9 +629,9 @@ k_backtransform_sm(const SubDev* __restrict__ subs, const double* __restrict__ A
 // ---- 2./6. blocked triangular solves: CTA = (8 right-hand-side columns, subdomain) ----------
 // lower: X = L^-1 B (B[i][c] = trans ? Bm[c][i] : Bm[i][c]); upper: X = L^-T B.  The 8 columns
 // live in shared memory; rows are taken in blocks of 32: the block's diagonal part of L is staged
-// in shared memory with the reciprocals of its diagonal, one warp solves it (4 lanes per column
-// split the dot product; the 32 dependent rows then wait on shared memory only), and all warps
-// subtract the block's contribution from the remaining rows.  The per-column kernel above (warp
+// in shared memory with the reciprocals of its diagonal, one warp per column solves it
+// right-looking (lane = row: per unknown one multiply, one broadcast and one FMA, from shared
+// memory only), and all warps subtract the block's contribution from the remaining rows.  The per-column kernel above (warp
 // per column) remains for reference runs with XLS_EIG=single.
 constexpr int kTrsmCols = 8, kTrsmRB = 32;
 
@@ -669,22 +669,19 @@ k_trsm_blk(const SubDev* __restrict__ subs, const double* __restrict__ Lm, const
     __syncthreads();
     if (threadIdx.x < m) dinv[threadIdx.x] = 1.0 / Ld[threadIdx.x * (kTrsmRB + 2)];
     __syncthreads();
-    if (warp == 0) {
-      const int c = lane >> 2, part = lane & 3;   // 8 columns x 4 partial sums
+    {
+      // warp c solves column c; lane l holds row l of the block and is updated as soon as each
+      // unknown is known (right-looking), so every step is one multiply, one broadcast and one FMA
+      const int c = warp;
+      double xl = lane < m ? xs[(r0 + lane) * kTrsmCols + c] : 0.0;
       for (int t = 0; t < m; ++t) {
         const int il = kUpper ? m - 1 - t : t;    // row within the block
-        double acc = 0.0;
-        if (!kUpper) {
-          for (int k = part; k < il; k += 4) acc += Ld[il * (kTrsmRB + 1) + k] * xs[(r0 + k) * kTrsmCols + c];
-        } else {
-          for (int k = il + 1 + part; k < m; k += 4) acc += Ld[k * (kTrsmRB + 1) + il] * xs[(r0 + k) * kTrsmCols + c];
-        }
-        acc += __shfl_xor_sync(0xffffffffu, acc, 1);
-        acc += __shfl_xor_sync(0xffffffffu, acc, 2);
-        const int i = r0 + il;
-        if (part == 0) xs[i * kTrsmCols + c] = (xs[i * kTrsmCols + c] - acc) * dinv[il];
-        __syncwarp();
+        const double xi = __shfl_sync(0xffffffffu, xl * dinv[il], il);
+        if (lane == il) xl = xi;
+        const bool pending = kUpper ? lane < il : (lane > il && lane < m);
+        if (pending) xl -= (kUpper ? Ld[il * (kTrsmRB + 1) + lane] : Ld[lane * (kTrsmRB + 1) + il]) * xi;
       }
+      if (lane < m) xs[(r0 + lane) * kTrsmCols + c] = xl;
     }
     __syncthreads();
     // remaining rows: lower r1..n-1, upper 0..r0-1
