@@ -5,7 +5,7 @@
 //   Y_out = scale * (H Y_in - c Y_in) - shift * Y_prev,
 //   H Y = -1/2 Delta_h Y + V Y + sum_I sum_l chi_Il P_Il,   P_Il = E_l dV <chi_Il, Y>.
 // The local part is one launch (k_stencil); the nonlocal part is a projection launch before it
-// (k_nl_project, P from Y_in) and a back-projection launch after it (k_nl_back, adds
+// (k_nl_project, P from Y_in) and a back-projection launch after it (k_nl_back_csr, adds
 // scale * chi P into Y_out).  All subdomains of a step share each launch.
 #include "xls_internal.h"
 
@@ -148,8 +148,9 @@ void launch_stencil(const SubDev* d_subs, int n_sub, const Plan& plan, const T* 
 // table of its grid points and the four chi values there, built once per Hamiltonian in FP64
 // and stored in the block's precision.  Per filter step: the projection launch
 // P[slot][l][v] = E_l dV sum_g chi_l(g) Y_v(g) (k_nl_project) and the back-projection launch
-// Y_out[v][g] += scale sum_l chi_l(g) P[slot][l][v] over the reverse table rows (k_nl_back_csr,
-// no atomics; k_nl_back is the atomic per-slot variant kept for reference runs).
+// Y_out[v][g] += scale sum_l chi_l(g) P[slot][l][v] over the reverse table rows (k_nl_back_csr:
+// each element receives one reduction, the sum of its row; k_nl_back is the per-slot variant with
+// one atomic per table entry, kept for reference runs).
 constexpr int kNlWarps = 8, kNlVec = 8;
 
 template <typename T>
