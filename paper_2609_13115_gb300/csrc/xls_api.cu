@@ -106,6 +106,9 @@ struct xls_grid_s {
   View halves[2];
   bool concurrent = false;
   cudaEvent_t ev_fork = nullptr, ev_mid = nullptr;
+  // side stream of the FP32 filter steps: the projection of a step runs beside its stencil
+  cudaStream_t side_st = nullptr;
+  cudaEvent_t ev_side_in = nullptr, ev_side_out = nullptr;
   // learned start: descriptors, correction, SAD and their atom tables
   float* ls_X = nullptr;
   float* ls_y = nullptr;
@@ -306,9 +309,18 @@ void h_step_main(xls_grid g, const xls_grid_s::View& v, int bin, int bprev, int 
   T* yprev = bprev >= 0 ? (T*)g->blk[bprev] : nullptr;
   T* yout = (T*)g->blk[bout];
   const T* V = (sizeof(T) == 8) ? (const T*)g->V : (const T*)g->Vf;
+  // the projection reads Y_in and writes P, the stencil reads Y_in, Y_prev and writes Y_out: with
+  // the side stream (FP32 blocks, one view, no per-launch profiling) the two run side by side and
+  // the back-projection waits for both
+  const bool side = g->side_st && sizeof(T) == 4 && !g->concurrent && !g->profiling;
+  if (side) {
+    cudaEventRecord(g->ev_side_in, v.st);
+    cudaStreamWaitEvent(g->side_st, g->ev_side_in, 0);
+  }
   { ProfScope ps(g, K_NLPROJ);
     launch_nl_project<T>(g->d_subs, g->d_slots, v.slot_off, v.n_slot, g->d_pidx, chi_table<T>(g), v.max_ns, yin, g->P,
-                         v.st); }
+                         side ? g->side_st : v.st); }
+  if (side) cudaEventRecord(g->ev_side_out, g->side_st);
   if (sizeof(T) == 4 && g->use_tma) {
     ProfScope ps(g, K_STENCIL);
     for (const TmaClass& c : v.tcls)
@@ -319,6 +331,7 @@ void h_step_main(xls_grid g, const xls_grid_s::View& v, int bin, int bprev, int 
     launch_stencil<T>(v.ds, v.n, v.plan, yin, yprev, yout, V, v.coef, step, v.st);
     g->launches++;
   }
+  if (side) cudaStreamWaitEvent(v.st, g->ev_side_out, 0);
   { ProfScope ps(g, K_NLBACK);
     launch_nl_back_csr<T>(v.ds, v.n, v.max_nd, v.max_ns, g->max_slots, g->d_rptr, g->d_rslot, rchi_table<T>(g), g->P,
                           yout, v.coef, step, v.st); }
@@ -1209,6 +1222,19 @@ xls_status create_grid(const xls_cell* cell, const xls_dc* dc, int precision, si
       g->concurrent = true;
     }
   }
+  {
+    const char* env = std::getenv("XLS_PROJ_SIDE");
+    if (!(env && env[0] == '0') && !dry) {
+      const bool ok = cudaStreamCreateWithFlags(&g->side_st, cudaStreamNonBlocking) == cudaSuccess &&
+                      cudaEventCreateWithFlags(&g->ev_side_in, cudaEventDisableTiming) == cudaSuccess &&
+                      cudaEventCreateWithFlags(&g->ev_side_out, cudaEventDisableTiming) == cudaSuccess;
+      if (!ok) {   // without the side stream the steps stay sequential
+        cudaGetLastError();
+        if (g->side_st) cudaStreamDestroy(g->side_st);
+        g->side_st = nullptr;
+      }
+    }
+  }
   cudaMemset(g->status, 0, 2 * sizeof(int));
   cudaMemset(g->lz_b, 0, 16 * g->n_sub * sizeof(double));
   cudaMemset(g->cw, 0, g->tot_states * sizeof(double));
@@ -1460,6 +1486,9 @@ xls_status xls_grid_destroy(xls_grid g) {
   }
   if (g->ev_fork) cudaEventDestroy(g->ev_fork);
   if (g->ev_mid) cudaEventDestroy(g->ev_mid);
+  if (g->side_st) cudaStreamDestroy(g->side_st);
+  if (g->ev_side_in) cudaEventDestroy(g->ev_side_in);
+  if (g->ev_side_out) cudaEventDestroy(g->ev_side_out);
   if (g->store) cudaFreeHost(g->store);
   delete g;
   return XLS_OK;
