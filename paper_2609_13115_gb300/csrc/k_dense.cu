@@ -181,16 +181,20 @@ __global__ void __launch_bounds__(256) k_core_weights(const SubDev* __restrict__
   if (v >= S.ns) return;
   const T* p = Psi + S.off_blk + (long long)v * S.nd;
   const int cx = S.core_n[0], cy = S.core_n[1], cz = S.core_n[2];
-  const long long ncore = (long long)cx * cy * cz;
-  double acc = 0.0;
-  for (long long q = threadIdx.x; q < ncore; q += blockDim.x) {
-    const int i = (int)(q % cx), j = (int)((q / cx) % cy), k = (int)(q / ((long long)cx * cy));
-    const long long g = ((long long)(S.core_lo[2] + k) * S.n[1] + (S.core_lo[1] + j)) * S.n[0] + (S.core_lo[0] + i);
-    const double x = (double)p[g];
-    acc += x * x;
+  // core rows (j, k) by warps, points of a row by lanes; each thread's partial sum in the block's
+  // precision (a few dozen terms), the block sum in FP64
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+  T part = (T)0;
+  for (int r = warp; r < cy * cz; r += nw) {
+    const int j = r % cy, k = r / cy;
+    const T* row = p + ((long long)(S.core_lo[2] + k) * S.n[1] + (S.core_lo[1] + j)) * S.n[0] + S.core_lo[0];
+    for (int i = lane; i < cx; i += 32) {
+      const T x = row[i];
+      part += x * x;
+    }
   }
   __shared__ double red[32];
-  acc = block_sum(acc, red);
+  const double acc = block_sum((double)part, red);
   if (threadIdx.x == 0) c[S.off_state + v] = acc;
 }
 
@@ -210,15 +214,18 @@ k_density(const SubDev* __restrict__ subs, const T* __restrict__ Psi, const doub
   const long long ncore = (long long)cx * cy * cz;
   const long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (q >= ncore) return;
-  const int i = (int)(q % cx), j = (int)((q / cx) % cy), k = (int)(q / ((long long)cx * cy));
+  const int qi = (int)q;   // a subdomain core has fewer than 2^31 points
+  const int i = qi % cx, j = (qi / cx) % cy, k = qi / (cx * cy);
   const long long g = ((long long)(S.core_lo[2] + k) * S.n[1] + (S.core_lo[1] + j)) * S.n[0] + (S.core_lo[0] + i);
   const T* p = Psi + S.off_blk + g;
   const double* o = occ + S.off_state;
-  double acc = 0.0;
+  // sum over the states in the block's precision (FP32 blocks: FP32 FMAs, relative error ~1e-7)
+  T acc_t = (T)0;
   for (int v = 0; v < S.ns; ++v) {
-    const double x = (double)p[(long long)v * S.nd];
-    acc += o[v] * x * x;
+    const T x = p[(long long)v * S.nd];
+    acc_t += (T)o[v] * x * x;
   }
+  const double acc = (double)acc_t;
   const long long G = ((long long)(S.core_glo[2] + k) * gny + (S.core_glo[1] + j)) * gnx + (S.core_glo[0] + i);
   rho[G] = 2.0 * acc / S.dV;
 }
@@ -382,17 +389,30 @@ k_fermi_cl(const double* __restrict__ lam, const double* __restrict__ c, int n, 
   for (int b = t; b < kFermiBins; b += blockDim.x)
     for (int q = 0; q < CL; ++q) cl.map_shared_rank(&hist[rank][0], q)[b] = hloc[b];
   cl.sync();
-  if (t == 0) {
-    double run = 0.0;
-    for (int b = 0; b < kFermiBins; ++b) {
-      for (int q = 0; q < CL; ++q) run += hist[q][b];
-      s_cum[b] = run;
+  // cumulative counts by a block-wide scan (one bin per thread; blockDim == kFermiBins), then the
+  // first bin whose cumulative count reaches N_e
+  __shared__ double s_wsum[kFermiBins / 32];
+  __shared__ int s_bstar;
+  {
+    double tb = 0.0;
+    for (int q = 0; q < CL; ++q) tb += hist[q][t];
+    const int l = t & 31, w = t >> 5;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const double y = __shfl_up_sync(0xffffffffu, tb, o);
+      if (l >= o) tb += y;
     }
+    if (l == 31) s_wsum[w] = tb;
+    if (t == 0) s_bstar = kFermiBins - 1;
+    __syncthreads();
+    double base = 0.0;
+    for (int q = 0; q < w; ++q) base += s_wsum[q];
+    s_cum[t] = base + tb;
+    __syncthreads();
+    if (s_cum[t] >= ne && (t == 0 || s_cum[t - 1] < ne)) s_bstar = t;
+    __syncthreads();
   }
-  __syncthreads();
-  int bstar = kFermiBins - 1;
-  for (int b = 0; b < kFermiBins; ++b)
-    if (s_cum[b] >= ne) { bstar = b; break; }
+  const int bstar = s_bstar;
   auto count2 = [&](double mu, double& dn) -> double {
     double acc = 0.0, dacc = 0.0;
     for (int i = i0; i < n; i += stride) {

@@ -305,13 +305,36 @@ k_tri_bisect(const SubDev* __restrict__ subs, double* vecs) {
     e2f[i] = (float)(e[i] * e[i]);
   }
   __syncthreads();
-  if (threadIdx.x == 0) {
+  // Gershgorin bounds: per-thread extrema over a strided share of the rows, then warp shuffles
+  // and one pass over the warps' results (no serial loop over n on one thread)
+  __shared__ double s_ext[3][32];
+  {
     double gl = 1e300, gu = -1e300, emax2 = 0.0;
-    for (int i = 0; i < n; ++i) {
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {
       const double r = (i > 0 ? fabs(e[i - 1]) : 0.0) + (i + 1 < n ? fabs(e[i]) : 0.0);
       gl = fmin(gl, d[i] - r);
       gu = fmax(gu, d[i] + r);
       if (i + 1 < n) emax2 = fmax(emax2, e[i] * e[i]);
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      gl = fmin(gl, __shfl_xor_sync(0xffffffffu, gl, o));
+      gu = fmax(gu, __shfl_xor_sync(0xffffffffu, gu, o));
+      emax2 = fmax(emax2, __shfl_xor_sync(0xffffffffu, emax2, o));
+    }
+    if ((threadIdx.x & 31) == 0) {
+      s_ext[0][threadIdx.x >> 5] = gl;
+      s_ext[1][threadIdx.x >> 5] = gu;
+      s_ext[2][threadIdx.x >> 5] = emax2;
+    }
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double gl = 1e300, gu = -1e300, emax2 = 0.0;
+    for (int w = 0; w < (int)((blockDim.x + 31) >> 5); ++w) {
+      gl = fmin(gl, s_ext[0][w]);
+      gu = fmax(gu, s_ext[1][w]);
+      emax2 = fmax(emax2, s_ext[2][w]);
     }
     const double tn = fmax(fabs(gl), fabs(gu));
     s_tnorm = tn > 0 ? tn : 1.0;
