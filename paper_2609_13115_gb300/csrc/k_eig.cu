@@ -378,13 +378,22 @@ __global__ void k_tri_clusters(const SubDev* __restrict__ subs, double* vecs) {
   double* d = vecs + 8LL * S.off_state;
   const double* lam32 = d + 3 * n;
   double* cst = d + 4 * n;
-  if (threadIdx.x == 0) {
+  // one warp: 32 indices at a time, the cluster starts compacted by ballot and prefix count
+  if (threadIdx.x < 32) {
+    const int lane = threadIdx.x;
     const double ctol = 1e-4 * d[5 * n + 2];
     int c = 0;
-    for (int i = 0; i < n; ++i)
-      if (i == 0 || lam32[i] - lam32[i - 1] > ctol) cst[c++] = (double)i;
-    cst[c] = (double)n;
-    d[5 * n + 1] = (double)c;
+    for (int i0 = 0; i0 < n; i0 += 32) {
+      const int i = i0 + lane;
+      const bool start = i < n && (i == 0 || lam32[i] - lam32[i - 1] > ctol);
+      const unsigned m = __ballot_sync(0xffffffffu, start);
+      if (start) cst[c + __popc(m & ((1u << lane) - 1u))] = (double)i;
+      c += __popc(m);
+    }
+    if (lane == 0) {
+      cst[c] = (double)n;
+      d[5 * n + 1] = (double)c;
+    }
   }
 }
 

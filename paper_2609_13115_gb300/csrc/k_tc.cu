@@ -370,12 +370,19 @@ k_gram_reduce(const SubDev* __restrict__ subs, const GramJob* __restrict__ jobs,
     const int r = e / 128, c = e % 128;
     const int i = i0 + r, j = j0 + c;
     if (i >= ns || j >= ns) continue;
-    double m = 0.0, h = 0.0;
+    // compensated FP32 sums of the K-chunk partials (FP32 adds: the FP64 pipe is a few percent of
+    // the FP32 one); the sum and its running error are combined in FP64
+    float ms = 0.f, mc = 0.f, hs = 0.f, hc = 0.f;
     for (int q = 0; q < cnt; ++q) {
       const float* w = work + (long long)(first + q) * 2 * 128 * 128;
-      m += (double)w[e];
-      h += (double)w[128 * 128 + e];
+      const float ym = w[e] - mc, yh = w[128 * 128 + e] - hc;
+      const float tm = ms + ym, th = hs + yh;
+      mc = (tm - ms) - ym;
+      hc = (th - hs) - yh;
+      ms = tm;
+      hs = th;
     }
+    double m = (double)ms - (double)mc, h = (double)hs - (double)hc;
     if (ex_f) {  // undo the power-of-two row scales of the FP16 split
       const int ei = ex_f[S.off_state + i];
       m = ldexp(m, -(ei + ex_f[S.off_state + j]));
