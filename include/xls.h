@@ -142,6 +142,13 @@ xls_status xls_density(xls_grid g, double n_electrons, double kT, double* mu_out
 /* Read back lambda (ascending) and c of subdomain `sub` (N_s doubles each; either may be NULL). */
 xls_status xls_get_eigs(xls_grid g, int sub, double* lambda_out, double* c_out);
 
+/* Density of states (Eq. dos, Sec. 5.A.4 "Postprocessing"): D(E) = 2 sum_alpha sum_n c_n
+ * delta(E - lambda_n) over the Ritz values and interior weights of every subdomain from the last
+ * pass, the delta function broadened to a normalised Gaussian of width `width` (Ha, > 0).
+ * energies: n_energies host doubles (Ha); dos_out: n_energies host doubles (states per Ha).
+ * Synchronous on the grid's stream.  XLS_EINVAL for a non-positive width or missing arrays. */
+xls_status xls_dos(xls_grid g, const double* energies, int n_energies, double width, double* dos_out);
+
 /* Read back M_s and H_s (N_s x N_s, row-major) of subdomain `sub` from the last projection. */
 xls_status xls_get_subspace(xls_grid g, int sub, double* Ms_out, double* Hs_out);
 

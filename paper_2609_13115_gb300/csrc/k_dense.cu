@@ -498,6 +498,38 @@ void launch_fermi_occ(const double* lam, const double* c, int n_tot, double n_e,
   k_fermi<<<1, 1024, 0, st>>>(lam, c, n_tot, n_e, kT, out4, occ, status);
 }
 
+// ---- density of states, Eq. dos: D(E) = 2 sum_alpha sum_n c_n delta(E - lambda_n), the delta
+// function broadened to a normalised Gaussian of width w.  One thread per energy point; the
+// Ritz values and weights are staged through shared memory in chunks.
+__global__ void __launch_bounds__(256)
+k_dos(const double* __restrict__ lam, const double* __restrict__ c, int n, const double* __restrict__ energies,
+      int n_e, double w, double* out) {
+  __shared__ double sl[256], sc[256];
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const double e = i < n_e ? energies[i] : 0.0;
+  const double inv2w2 = 0.5 / (w * w), norm = 1.0 / (w * sqrt(2.0 * 3.14159265358979323846));
+  double acc = 0.0;
+  for (int q0 = 0; q0 < n; q0 += 256) {
+    const int q = q0 + threadIdx.x;
+    sl[threadIdx.x] = q < n ? lam[q] : 0.0;
+    sc[threadIdx.x] = q < n ? c[q] : 0.0;
+    __syncthreads();
+    const int m = min(256, n - q0);
+    for (int k = 0; k < m; ++k) {
+      const double d = e - sl[k];
+      acc += sc[k] * exp(-d * d * inv2w2);
+    }
+    __syncthreads();
+  }
+  if (i < n_e) out[i] = 2.0 * norm * acc;
+}
+
+void launch_dos(const double* lam, const double* c, int n, const double* energies, int n_e, double w, double* out,
+                cudaStream_t st) {
+  if (n_e <= 0) return;
+  k_dos<<<(n_e + 255) / 256, 256, 0, st>>>(lam, c, n, energies, n_e, w, out);
+}
+
 // ---- FP16 orbital storage (warm start between SCF steps): vector v stored as
 // half(psi_v * 2^e_v) with e_v such that max |psi_v| 2^e_v lies in [2^13, 2^14) -------------------
 template <typename T>

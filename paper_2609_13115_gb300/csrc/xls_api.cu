@@ -1811,6 +1811,28 @@ xls_status xls_get_eigs(xls_grid g, int sub, double* lambda_out, double* c_out) 
   return XLS_OK;
 }
 
+xls_status xls_dos(xls_grid g, const double* energies, int n_energies, double width, double* dos_out) {
+  if (!g || n_energies < 0 || (n_energies > 0 && (!energies || !dos_out)) || !(width > 0))
+    return fail(XLS_EINVAL, "xls_dos: bad arguments");
+  if (n_energies == 0) return XLS_OK;
+  double* d = nullptr;
+  if (cudaMalloc(&d, 2 * (size_t)n_energies * sizeof(double)) != cudaSuccess) {
+    cudaGetLastError();
+    return fail(XLS_ENOMEM, "xls_dos: device allocation failed");
+  }
+  cudaError_t e = cudaMemcpyAsync(d, energies, (size_t)n_energies * sizeof(double), cudaMemcpyHostToDevice, g->st);
+  if (e == cudaSuccess) {
+    launch_dos(g->lam, g->cw, (int)g->tot_states, d, n_energies, width, d + n_energies, g->st);
+    e = cudaGetLastError();
+  }
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(dos_out, d + n_energies, (size_t)n_energies * sizeof(double), cudaMemcpyDeviceToHost, g->st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(g->st);
+  cudaFree(d);
+  if (e != cudaSuccess) return fail(XLS_ECUDA, std::string("xls_dos: ") + cudaGetErrorString(e));
+  return XLS_OK;
+}
+
 xls_status xls_get_subspace(xls_grid g, int sub, double* Ms_out, double* Hs_out) {
   if (!g || sub < 0 || sub >= g->n_sub) return fail(XLS_EINVAL, "xls_get_subspace: bad arguments");
   if (g->wave) return not_in_wave_mode("xls_get_subspace");

@@ -175,6 +175,8 @@ void launch_core_weights(const SubDev* d_subs, int n_sub, int max_ns, const T* P
 template <typename T>
 void launch_density_occ(const SubDev* d_subs, int n_sub, long long max_core, const T* Psi, const double* occ,
                         const int gn[3], double* rho, cudaStream_t st);
+void launch_dos(const double* lam, const double* c, int n, const double* energies, int n_e, double w, double* out,
+                cudaStream_t st);
 void launch_fermi_occ(const double* lam, const double* c, int n_tot, double n_e, double kT, double* out4, double* occ,
                       int* status, cudaStream_t st);
 

@@ -56,6 +56,7 @@ _SIGS = {
                             POINTER(c_double), POINTER(c_double)]),
     "xls_get_eigs": (c_int, [c_void_p, c_int, c_void_p, c_void_p]),
     "xls_get_subspace": (c_int, [c_void_p, c_int, c_void_p, c_void_p]),
+    "xls_dos": (c_int, [c_void_p, c_void_p, c_int, c_double, c_void_p]),
     "xls_get_bounds": (c_int, [c_void_p, c_void_p]),
     "xls_get_timings": (c_int, [c_void_p, c_void_p, POINTER(c_int)]),
     "xls_set_profiling": (c_int, [c_void_p, c_int]),
@@ -209,6 +210,14 @@ def xls_get_eigs(g, sub, n_states):
     c = np.zeros(n_states)
     _check(load().xls_get_eigs(g, int(sub), lam.ctypes.data_as(c_void_p), c.ctypes.data_as(c_void_p)))
     return lam, c
+
+
+def xls_dos(g, energies, width):
+    """Gaussian-broadened density of states (Eq. dos) at the given energies (Ha)."""
+    e = np.ascontiguousarray(energies, dtype=np.float64).ravel()
+    out = np.zeros_like(e)
+    _check(load().xls_dos(g, e.ctypes.data_as(c_void_p), int(e.size), float(width), out.ctypes.data_as(c_void_p)))
+    return out
 
 
 def xls_get_subspace(g, sub, n_states):

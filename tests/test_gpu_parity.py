@@ -242,6 +242,30 @@ def test_tma_stencil_matches_oracle_and_generic(wname, monkeypatch):
         assert relerr(outs["tma"][a], outs["generic"][a]) < 2e-6
 
 
+def test_dos_matches_oracle():
+    """Eq. dos on the device from the pass's Ritz values and weights equals the oracle's DOS of the
+    same values, and integrates to 2 sum c (the electron capacity of the interior states)."""
+    from oracle import fermi
+    w = synth.workload(0)
+    V = pseudo.local_potential(w)
+    subs = dc.partition(w)
+    psi0 = _start_blocks(w, subs)
+    with make_grid(w, V, xls.XLS_FP64) as g:
+        for a in range(w.n_sub):
+            xls.xls_orbitals_set(g.h, a, psi0[a])
+        xls.xls_chefsi_batch(g.h, w.degree, 1)
+        lc = [xls.xls_get_eigs(g.h, a, int(w.n_states[a])) for a in range(w.n_sub)]
+        E = np.linspace(-1.5, 1.5, 3001)
+        d = xls.xls_dos(g.h, E, 0.02)
+        with pytest.raises(xls.XlsError):
+            xls.xls_dos(g.h, E, 0.0)
+    lam = np.concatenate([x[0] for x in lc])
+    c = np.concatenate([x[1] for x in lc])
+    ref = fermi.dos(lam, c, E, 0.02)
+    np.testing.assert_allclose(d, ref, rtol=1e-10, atol=1e-10 * ref.max())
+    np.testing.assert_allclose(np.sum(0.5 * (d[1:] + d[:-1]) * np.diff(E)), 2.0 * c.sum(), rtol=1e-6)
+
+
 def test_fermi_cluster_matches_single_cta(monkeypatch):
     """The Fermi level on a CTA cluster (histogram bracket + Newton) and on one CTA (bisection +
     Newton) agree, and both match the oracle's."""
