@@ -193,6 +193,12 @@ xls_status xls_scf_setup(xls_grid g, double n_electrons, double kT, int degree, 
 xls_status xls_scf_step(xls_grid g, double* rho_inout, int rho_on_device, double* residual_out, double* energy_out,
                         double* mu_out);
 
+/* Conjugate-gradient iterations spent by the SCF steps so far (Poisson and Kerker solves).  The
+ * solves are preconditioned by one FP32 multigrid V-cycle of the 7-point operator per iteration
+ * (Sec. 5.B "Poisson solver": FP64 CG, FP32 V-cycle); with the environment variable
+ * XLS_SCF_PLAIN_CG=1 set when the SCF state is first set up they are plain CG. */
+xls_status xls_scf_cg_iterations(xls_grid g, long long* iterations_out);
+
 /* FP16 warm-start storage of one subdomain's current orbitals (Sec. 5.B.3: orbitals kept in FP16
  * between SCF steps): vector v is stored as half(psi_v * 2^e_v), with the power of two e_v
  * (exp_out[v]) placing max |psi_v| 2^e_v in [2^13, 2^14); half_out holds n_states x N_d

@@ -132,6 +132,10 @@ struct xls_grid_s {
     double *d_pos = nullptr, *d_rc = nullptr, *d_amp = nullptr;
     double e_self = 0, z_total = 0;
     int cg_iters = 0;
+    // multigrid-preconditioned CG (XLS_SCF_PLAIN_CG=1: plain CG)
+    bool pcg = true;
+    double *z = nullptr, *r_old = nullptr;
+    float* mg = nullptr;
   } scf;
   // TMA stencil (mixed path): classes of equal tile shape and the tensor maps of every
   // (subdomain, block buffer, box height)
@@ -813,7 +817,26 @@ xls_status scf_alloc(xls_grid g) {
   XLS_TRY(g->alloc(&S.pulay_partial, pulay_partial_doubles() * sizeof(double)));
   XLS_TRY(g->alloc(&S.scal, 16 * sizeof(double)));
   XLS_TRY(g->alloc(&S.gamma, 16 * sizeof(double)));
+  const char* env = std::getenv("XLS_SCF_PLAIN_CG");
+  S.pcg = !(env && env[0] == '1');
+  if (S.pcg) {
+    XLS_TRY(g->alloc(&S.z, n * sizeof(double)));
+    XLS_TRY(g->alloc(&S.r_old, n * sizeof(double)));
+    XLS_TRY(g->alloc(&S.mg, mg_floats(g->gn) * sizeof(float)));
+  }
   return XLS_OK;
+}
+
+// z = M r: one FP32 V-cycle of the 7-point operator (+ kappa^2 for which 1); the Poisson case
+// keeps z at zero mean (the periodic operator's null space)
+void scf_precondition(xls_grid g, int which, const double* r, double* z) {
+  auto& S = g->scf;
+  const long long n = S.gs.nd;
+  launch_mg_vcycle(g->gn, g->gh, which == 1 ? S.kappa * S.kappa : 0.0, r, z, S.mg, g->st);
+  if (which == 0) {
+    launch_sum(n, z, S.partial, S.scal + 6, g->st);
+    launch_sub_mean(n, S.scal + 6, z, g->st);
+  }
 }
 
 // the stencil's step coefficients on the global grid: step 0: -Delta_h, step 1: -Delta_h + kappa^2
@@ -833,7 +856,10 @@ void scf_apply(xls_grid g, int which, const double* x, double* y) {
 // (which 1)), x holds the start and receives the solution; stops at
 // ||r||^2 <= tol^2 max(||rhs||^2, ref_sq) (ref_sq: the scale of the terms that formed rhs, for
 // right-hand sides that cancel to rounding)
+xls_status scf_pcg(xls_grid g, int which, const double* rhs, double* x, double tol, int max_iter, double ref_sq);
+
 xls_status scf_cg(xls_grid g, int which, const double* rhs, double* x, double tol, int max_iter, double ref_sq = 0.0) {
+  if (g->scf.pcg) return scf_pcg(g, which, rhs, x, tol, max_iter, ref_sq);
   auto& S = g->scf;
   const long long n = S.gs.nd;
   double* s = S.scal;  // s[0] r.r, s[1] p.Ap, s[2] new r.r, s[3] rhs.rhs
@@ -865,6 +891,54 @@ xls_status scf_cg(xls_grid g, int which, const double* rhs, double* x, double to
       XLS_CUDA(cudaStreamSynchronize(g->st));
       if (!std::isfinite(h[0])) return fail(XLS_ENONFINITE, "SCF: conjugate gradients produced a non-finite residual");
       if (h[0] <= stop) return XLS_OK;
+    }
+  }
+  return fail(XLS_ENOCONV, "SCF: conjugate gradients did not reach the tolerance");
+}
+
+// The same solve by flexible preconditioned CG (Polak-Ribiere beta, robust to the FP32 rounding of
+// the preconditioner), the preconditioner one multigrid V-cycle; same stopping rule on ||r||^2.
+// s[0] r.z, s[1] p.Ap, s[2] r.r, s[3] rhs.rhs, s[4] new r.z, s[5] r_old.z, s[6] scratch sum
+xls_status scf_pcg(xls_grid g, int which, const double* rhs, double* x, double tol, int max_iter, double ref_sq) {
+  auto& S = g->scf;
+  const long long n = S.gs.nd;
+  double* s = S.scal;
+  scf_apply(g, which, x, S.q);
+  launch_axpbypcz(n, 1.0, rhs, 0.0, S.r, -1.0, S.q, g->st);
+  scf_precondition(g, which, S.r, S.z);
+  XLS_CUDA(cudaMemcpyAsync(S.p, S.z, n * sizeof(double), cudaMemcpyDeviceToDevice, g->st));
+  {
+    const double* xs[3] = {S.r, S.r, rhs};
+    const double* ys[3] = {S.z, S.r, rhs};
+    launch_dots(n, xs, ys, 3, S.partial, s + 8, 1.0, g->st);   // s[8] r.z, s[9] r.r, s[10] rhs.rhs
+    XLS_CUDA(cudaMemcpyAsync(s, s + 8, sizeof(double), cudaMemcpyDeviceToDevice, g->st));
+    XLS_CUDA(cudaMemcpyAsync(s + 2, s + 9, 2 * sizeof(double), cudaMemcpyDeviceToDevice, g->st));
+  }
+  double h[4];
+  XLS_CUDA(cudaMemcpyAsync(h, s, 4 * sizeof(double), cudaMemcpyDeviceToHost, g->st));
+  XLS_CUDA(cudaStreamSynchronize(g->st));
+  const double stop = tol * tol * std::max(h[3], ref_sq);
+  if (h[2] <= stop) return XLS_OK;
+  for (int it = 1; it <= max_iter; ++it) {
+    scf_apply(g, which, S.p, S.q);
+    const double* xs[1] = {S.p};
+    const double* ys[1] = {S.q};
+    launch_dots(n, xs, ys, 1, S.partial, s + 1, 1.0, g->st);
+    XLS_CUDA(cudaMemcpyAsync(S.r_old, S.r, n * sizeof(double), cudaMemcpyDeviceToDevice, g->st));
+    launch_cg_xr(n, s, x, S.r, S.p, S.q, S.partial, g->st);   // x += a p, r -= a q, s[2] = r.r
+    scf_precondition(g, which, S.r, S.z);
+    {
+      const double* xz[2] = {S.r, S.r_old};
+      const double* yz[2] = {S.z, S.z};
+      launch_dots(n, xz, yz, 2, S.partial, s + 4, 1.0, g->st);
+    }
+    launch_pcg_p(n, s, S.z, S.p, g->st);
+    S.cg_iters++;
+    if (it % 4 == 0 || it == max_iter) {
+      XLS_CUDA(cudaMemcpyAsync(h, s, 3 * sizeof(double), cudaMemcpyDeviceToHost, g->st));
+      XLS_CUDA(cudaStreamSynchronize(g->st));
+      if (!std::isfinite(h[2])) return fail(XLS_ENONFINITE, "SCF: conjugate gradients produced a non-finite residual");
+      if (h[2] <= stop) return XLS_OK;
     }
   }
   return fail(XLS_ENOCONV, "SCF: conjugate gradients did not reach the tolerance");
@@ -1808,6 +1882,12 @@ xls_status xls_get_eigs(xls_grid g, int sub, double* lambda_out, double* c_out) 
   XLS_CUDA(cudaStreamSynchronize(g->st));
   if (lambda_out) XLS_CUDA(cudaMemcpy(lambda_out, g->lam + S.off_state, S.ns * sizeof(double), cudaMemcpyDeviceToHost));
   if (c_out) XLS_CUDA(cudaMemcpy(c_out, g->cw + S.off_state, S.ns * sizeof(double), cudaMemcpyDeviceToHost));
+  return XLS_OK;
+}
+
+xls_status xls_scf_cg_iterations(xls_grid g, long long* iterations_out) {
+  if (!g || !iterations_out) return fail(XLS_EINVAL, "xls_scf_cg_iterations: bad arguments");
+  *iterations_out = g->scf.cg_iters;
   return XLS_OK;
 }
 

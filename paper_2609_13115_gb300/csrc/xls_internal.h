@@ -2,6 +2,8 @@
 #pragma once
 
 #include <cuda_runtime.h>
+
+#include <algorithm>
 #include <cuda_bf16.h>
 #include <stdint.h>
 
@@ -219,6 +221,11 @@ void launch_sub_mean(long long n, const double* sum, double* y, cudaStream_t st)
 void launch_cg_xr(long long n, const double* s, double* x, double* r, const double* p, const double* q,
                   double* partial, cudaStream_t st);
 void launch_cg_p(long long n, double* s, const double* r, double* p, cudaStream_t st);
+int mg_level_count(const int n[3]);
+size_t mg_floats(const int n[3]);
+void launch_mg_vcycle(const int n[3], const double h[3], double sigma, const double* r, double* z, float* work,
+                      cudaStream_t st);
+void launch_pcg_p(long long n, double* s, const double* z, double* p, cudaStream_t st);
 void launch_lda(long long n, const double* rho, double* eps, double* vxc, cudaStream_t st);
 void launch_pseudocharge(int n_atoms, const double* d_pos, const double* d_rc, const double* d_amp, const int gn[3],
                          const double gh[3], const double gL[3], double* g1, double* b, double z_total, double* partial,

@@ -255,12 +255,12 @@ def test_dos_matches_oracle():
             xls.xls_orbitals_set(g.h, a, psi0[a])
         xls.xls_chefsi_batch(g.h, w.degree, 1)
         lc = [xls.xls_get_eigs(g.h, a, int(w.n_states[a])) for a in range(w.n_sub)]
-        E = np.linspace(-1.5, 1.5, 3001)
+        lam = np.concatenate([x[0] for x in lc])
+        c = np.concatenate([x[1] for x in lc])
+        E = np.linspace(lam.min() - 0.3, lam.max() + 0.3, 6001)   # the whole spectrum +- 15 widths
         d = xls.xls_dos(g.h, E, 0.02)
         with pytest.raises(xls.XlsError):
             xls.xls_dos(g.h, E, 0.0)
-    lam = np.concatenate([x[0] for x in lc])
-    c = np.concatenate([x[1] for x in lc])
     ref = fermi.dos(lam, c, E, 0.02)
     np.testing.assert_allclose(d, ref, rtol=1e-10, atol=1e-10 * ref.max())
     np.testing.assert_allclose(np.sum(0.5 * (d[1:] + d[:-1]) * np.diff(E)), 2.0 * c.sum(), rtol=1e-6)
@@ -459,6 +459,40 @@ def test_scf_steps_match_oracle(prec):
             assert abs(r_g - r_o) < 1e-2 * r_o + 1e-5, (k, r_g, r_o)
     tol = 1e-7 if prec == xls.XLS_FP64 else 1e-4
     assert np.linalg.norm(rho - rho_ref) / np.linalg.norm(rho_ref) < tol
+
+
+def test_scf_multigrid_pcg_matches_plain_cg(monkeypatch):
+    """The SCF steps with multigrid-preconditioned CG (default) and with plain CG give the same
+    energies, Fermi levels and densities (both solve to the same tolerance), the preconditioned
+    solves in far fewer iterations."""
+    w = synth.workload(0)
+    V0 = pseudo.local_potential(w)
+    subs = dc.partition(w)
+    psi0 = [synth.psi0_block(w.psi_seed + a, subs[a].N, int(w.n_states[a])) for a in range(w.n_sub)]
+    rho0 = _scf_start(w)
+    res = {}
+    for mode in ("pcg", "cg"):
+        if mode == "cg":
+            monkeypatch.setenv("XLS_SCF_PLAIN_CG", "1")
+        else:
+            monkeypatch.delenv("XLS_SCF_PLAIN_CG", raising=False)
+        g = make_grid(w, V0, xls.XLS_FP64)
+        try:
+            for a in range(w.n_sub):
+                xls.xls_orbitals_set(g.h, a, psi0[a])
+            xls.xls_scf_setup(g.h, w.n_electrons, w.kT, w.degree)
+            rho = np.ascontiguousarray(rho0.astype(np.float64))
+            out = [xls.xls_scf_step(g.h, rho) for _ in range(2)]
+            res[mode] = (out, rho.copy(), xls.xls_scf_cg_iterations(g.h))
+        finally:
+            g.close()
+    (o_p, r_p, it_p), (o_c, r_c, it_c) = res["pcg"], res["cg"]
+    for (rp, ep, mp), (rc, ec, mc) in zip(o_p, o_c):
+        assert abs(ep - ec) < 1e-9 * len(w.pos)
+        assert abs(mp - mc) < 1e-9
+        assert abs(rp - rc) < 1e-6 * rc
+    assert np.linalg.norm(r_p - r_c) / np.linalg.norm(r_c) < 1e-9
+    assert it_p * 3 < it_c, (it_p, it_c)
 
 
 @pytest.mark.parametrize("prec", [xls.XLS_FP64, xls.XLS_MIXED_BF16])
