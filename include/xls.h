@@ -239,8 +239,10 @@ xls_status xls_density_at(xls_grid g, double mu, double kT, double* rho_out, int
  * xls_chefsi_batch runs the waves in turn (per wave: a partial grid, the projector tables and
  * Lanczos bounds of its subdomains, orbitals up, passes, orbitals, Ritz values, weights and
  * bounds back), xls_density finds mu from all Ritz values and weights on the device and forms
- * rho in a second sweep over the stored orbitals.  xls_chefsi_stage, xls_hamiltonian_apply,
- * xls_get_subspace, profiling and the SCF calls return XLS_EINVAL in wave mode.
+ * rho in a second sweep over the stored orbitals; xls_scf_step solves the global-grid parts as
+ * on a resident grid and runs the passes in waves (each wave's partial grid restricts the new
+ * V_eff and takes its own Lanczos upper bound).  xls_chefsi_stage, xls_hamiltonian_apply,
+ * xls_get_subspace and profiling return XLS_EINVAL in wave mode.
  * Library-specific: the paper batches subdomains per MPI rank instead. */
 xls_status xls_get_waves(xls_grid g, int* n_waves_out, int* first_sub_out);
 

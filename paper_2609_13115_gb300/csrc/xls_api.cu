@@ -1430,7 +1430,10 @@ xls_status wave_orbitals_random(xls_grid g, uint64_t seed) {
 
 // every wave in turn: partial grid, orbitals up, passes, orbitals / Ritz values / weights /
 // bounds back, partial grid released
-xls_status wave_chefsi(xls_grid g, int degree, int n_passes, const double* bounds) {
+// fresh_b: the potential changed since the last pass (an SCF step): the upper bound b of every
+// subdomain is the worker's new Lanczos bound, a and a0 stay those of the last pass's Ritz values
+// (what the resident grid's SCF step does with its Lanczos bounds)
+xls_status wave_chefsi(xls_grid g, int degree, int n_passes, const double* bounds, bool fresh_b = false) {
   for (double& t : g->wave_stage_ms) t = 0.0;
   int launches = 0;
   for (size_t w = 0; w < g->waves.size(); ++w) {
@@ -1442,6 +1445,14 @@ xls_status wave_chefsi(xls_grid g, int degree, int n_passes, const double* bound
     k->orb_set = true;
     const double* bw = bounds ? bounds + 3 * (size_t)first
                               : (g->have_ritz ? g->host_bounds.data() + 3 * (size_t)first : nullptr);
+    std::vector<double> mixed;
+    if (s == XLS_OK && fresh_b && bw) {
+      mixed.assign(bw, bw + 3 * (size_t)cnt);
+      std::vector<double> wb(3 * (size_t)cnt);
+      s = xls_get_bounds(k, wb.data());
+      for (int j = 0; j < cnt; ++j) mixed[3 * (size_t)j] = wb[3 * (size_t)j];
+      bw = mixed.data();
+    }
     if (s == XLS_OK) s = xls_chefsi_batch(k, degree, n_passes, bw);
     if (s == XLS_OK) {
       const SubDev& S0 = g->subs[first];
@@ -1952,7 +1963,6 @@ xls_status xls_scf_setup(xls_grid g, double n_electrons, double kT, int degree, 
   if (!g || !(n_electrons > 0) || !(kT > 0) || degree < 1 || degree >= kMaxDegree || n_passes < 1 || !(beta > 0) ||
       !(kappa > 0) || history < 1 || history > 8 || pulay_period < 1)
     return fail(XLS_EINVAL, "xls_scf_setup: bad arguments");
-  if (g->wave) return not_in_wave_mode("xls_scf_setup");
   if (!g->ham_set) return fail(XLS_EINVAL, "xls_scf_setup: call xls_hamiltonian_set first (atoms and projectors)");
   auto& S = g->scf;
   const bool need_alloc = !S.d_gs || history > S.hist;
@@ -1978,7 +1988,6 @@ xls_status xls_scf_setup(xls_grid g, double n_electrons, double kT, int degree, 
 xls_status xls_scf_step(xls_grid g, double* rho_inout, int rho_on_device, double* residual_out, double* energy_out,
                         double* mu_out) {
   if (!g || !rho_inout) return fail(XLS_EINVAL, "xls_scf_step: bad arguments");
-  if (g->wave) return not_in_wave_mode("xls_scf_step");
   auto& S = g->scf;
   if (!S.ready) return fail(XLS_EINVAL, "xls_scf_step: call xls_scf_setup first");
   if (!g->orb_set) return fail(XLS_EINVAL, "xls_scf_step: orbitals not set");
@@ -2006,11 +2015,18 @@ xls_status xls_scf_step(xls_grid g, double* rho_inout, int rho_on_device, double
   launch_lda(n, S.rho_in, S.eps, S.vxc, st);
   if (!g->Vg) XLS_TRY(g->alloc(&g->Vg, n * sizeof(double)));
   launch_axpbypcz(n, 1.0, S.phi, 0.0, g->Vg, 1.0, S.vxc, st);
-  launch_restrict(g->d_subs, g->n_sub, g->max_nd, g->Vg, g->gn, g->V, g->Vf, st);
-  // 3. new upper bounds (Lanczos) and the CheFSI passes
-  XLS_TRY(lanczos_bounds(g));
-  if (g->prec == XLS_FP64) XLS_TRY(chefsi<double>(g, S.degree, S.passes, nullptr));
-  else XLS_TRY(chefsi<float>(g, S.degree, S.passes, nullptr));
+  if (g->wave) {
+    // 3'. in waves: every wave's worker grid restricts V_eff from the global grid, takes its new
+    // Lanczos bounds and runs the passes with its orbitals staged from the host store
+    XLS_CUDA(cudaStreamSynchronize(st));
+    XLS_TRY(wave_chefsi(g, S.degree, S.passes, nullptr, true));
+  } else {
+    launch_restrict(g->d_subs, g->n_sub, g->max_nd, g->Vg, g->gn, g->V, g->Vf, st);
+    // 3. new upper bounds (Lanczos) and the CheFSI passes
+    XLS_TRY(lanczos_bounds(g));
+    if (g->prec == XLS_FP64) XLS_TRY(chefsi<double>(g, S.degree, S.passes, nullptr));
+    else XLS_TRY(chefsi<float>(g, S.degree, S.passes, nullptr));
+  }
   // 4. Fermi level, output density, band and entropy energies
   double mu = 0, e_band = 0, e_ent = 0;
   XLS_TRY(xls_density(g, S.ne, S.kT, &mu, S.rho_out, 1, &e_band, &e_ent));

@@ -495,6 +495,37 @@ def test_scf_multigrid_pcg_matches_plain_cg(monkeypatch):
     assert it_p * 3 < it_c, (it_p, it_c)
 
 
+def test_scf_in_waves_matches_resident_grid():
+    """SCF steps on a grid running in waves (HBM budget below the footprint: every wave's worker
+    restricts the new V_eff, takes its Lanczos bound and runs the pass from the host store) equal
+    those of the all-resident grid."""
+    w = dirichlet20_workload()
+    V0 = pseudo.local_potential(w)
+    subs = dc.partition(w)
+    psi0 = [synth.psi0_block(w.psi_seed + a, subs[a].N, int(w.n_states[a])) for a in range(w.n_sub)]
+    rho0 = _scf_start(w)
+    res = {}
+    for mode, budget in (("resident", 0), ("waves", 90 << 20)):
+        g = xls.Grid(w, xls.XLS_FP64, hbm_budget_bytes=budget)
+        try:
+            n_waves, _ = xls.xls_get_waves(g.h, w.n_sub)
+            assert (n_waves >= 2) == (mode == "waves"), n_waves
+            g.set_hamiltonian(V0)
+            for a in range(w.n_sub):
+                xls.xls_orbitals_set(g.h, a, psi0[a])
+            xls.xls_scf_setup(g.h, w.n_electrons, w.kT, w.degree)
+            rho = np.ascontiguousarray(rho0.astype(np.float64))
+            out = [xls.xls_scf_step(g.h, rho) for _ in range(2)]
+            res[mode] = (out, rho.copy())
+        finally:
+            g.close()
+    for (rw, ew, mw), (rr, er, mr) in zip(res["waves"][0], res["resident"][0]):
+        assert abs(ew - er) < 1e-9 * len(w.pos), (ew, er)
+        assert abs(mw - mr) < 1e-9, (mw, mr)
+        assert abs(rw - rr) < 1e-7 * rr, (rw, rr)
+    assert relerr(res["waves"][1], res["resident"][1]) < 1e-9
+
+
 @pytest.mark.parametrize("prec", [xls.XLS_FP64, xls.XLS_MIXED_BF16])
 def test_waves_match_resident_grid(prec):
     """An HBM budget below the footprint runs the subdomains in waves (orbitals in the host
