@@ -246,6 +246,14 @@ xls_status xls_density_at(xls_grid g, double mu, double kT, double* rho_out, int
  * Library-specific: the paper batches subdomains per MPI rank instead. */
 xls_status xls_get_waves(xls_grid g, int* n_waves_out, int* first_sub_out);
 
+/* Wave mode only: keep the host store of the orbitals in FP16 (on != 0) or in the compute
+ * precision (on == 0).  FP16: every vector v of a subdomain is stored as half(psi_v 2^e_v) with
+ * the power of two e_v putting max |psi_v| 2^e_v into [2^13, 2^14) (the FP16 warm-start storage of
+ * Sec. 5.B.3), half the FP32 store; conversions run on the device when a wave's orbitals go up or
+ * come back.  Orbitals already stored are converted.  XLS_EINVAL on a resident grid, XLS_ENOMEM
+ * if the new pinned store cannot be allocated. */
+xls_status xls_wave_store_fp16(xls_grid g, int on);
+
 /* ---- learned SCF start (Sec. 5.A.4, SCF initialisation: superposed atomic densities plus a
  * learned, material-specific correction).  The paper names the idea, not the model; this library
  * fixes: per grid point 2 species x 16 radial descriptors

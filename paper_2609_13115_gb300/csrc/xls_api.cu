@@ -76,6 +76,12 @@ struct xls_grid_s {
   std::vector<std::pair<int, int>> waves;   // (first subdomain, count)
   std::vector<int> dc_core_lo, dc_core_n, dc_buf, dc_ns;
   void* store = nullptr;
+  // FP16 store (xls_wave_store_fp16): half(psi_v 2^e_v) per value, the exponents per state on the
+  // host, converted on the device through a half staging block and an exponent array
+  bool store16 = false;
+  std::vector<int> store_ex;
+  void* stage16 = nullptr;
+  int* stage_ex = nullptr;
   std::vector<double> host_bounds;
   double wave_stage_ms[4] = {0, 0, 0, 0};
   // geometry of the last xls_hamiltonian_set (for the pseudocharge of the SCF step)
@@ -1333,17 +1339,45 @@ size_t sub_footprint(const SubDev& S, size_t elem) {
 
 
 // ---- wave mode ---------------------------------------------------------------------------------
-// copy between the current block of grid g (subdomain `sub`) and host memory, device format
-xls_status raw_orbitals(xls_grid g, int sub, void* host, bool upload) {
+size_t store_elem(xls_grid g) { return g->store16 ? 2 : g->elem; }
+char* store_ptr(xls_grid g, int sub) { return (char*)g->store + (size_t)g->subs[sub].off_blk * store_elem(g); }
+
+// the stored block of subdomain `sub` into device memory `dev` in the compute precision of the
+// wave grid g (the store's format: a plain copy, or halves + exponents converted on the device)
+xls_status store_to_device(xls_grid g, int sub, void* dev, cudaStream_t st) {
   const SubDev& S = g->subs[sub];
-  char* dev = (char*)g->blk[g->cur] + (size_t)S.off_blk * g->elem;
-  const size_t bytes = (size_t)S.nd * S.ns * g->elem;
-  if (upload) XLS_CUDA(cudaMemcpyAsync(dev, host, bytes, cudaMemcpyHostToDevice, g->st));
-  else XLS_CUDA(cudaMemcpyAsync(host, dev, bytes, cudaMemcpyDeviceToHost, g->st));
+  const size_t n = (size_t)S.nd * S.ns;
+  if (!g->store16) {
+    XLS_CUDA(cudaMemcpyAsync(dev, store_ptr(g, sub), n * g->elem, cudaMemcpyHostToDevice, st));
+    return XLS_OK;
+  }
+  XLS_CUDA(cudaMemcpyAsync(g->stage16, store_ptr(g, sub), n * 2, cudaMemcpyHostToDevice, st));
+  XLS_CUDA(cudaMemcpyAsync(g->stage_ex, g->store_ex.data() + S.off_state, S.ns * sizeof(int), cudaMemcpyHostToDevice,
+                           st));
+  if (g->prec == XLS_FP64) launch_load_half<double>(g->stage16, S.nd, S.ns, g->stage_ex, (double*)dev, st);
+  else launch_load_half<float>(g->stage16, S.nd, S.ns, g->stage_ex, (float*)dev, st);
+  XLS_CUDA(cudaGetLastError());
   return XLS_OK;
 }
 
-char* store_ptr(xls_grid g, int sub) { return (char*)g->store + (size_t)g->subs[sub].off_blk * g->elem; }
+// device block `dev` (compute precision) of subdomain `sub` into the store; synchronous for the
+// FP16 store (its exponents land in a host vector)
+xls_status device_to_store(xls_grid g, int sub, const void* dev, cudaStream_t st) {
+  const SubDev& S = g->subs[sub];
+  const size_t n = (size_t)S.nd * S.ns;
+  if (!g->store16) {
+    XLS_CUDA(cudaMemcpyAsync(store_ptr(g, sub), dev, n * g->elem, cudaMemcpyDeviceToHost, st));
+    return XLS_OK;
+  }
+  if (g->prec == XLS_FP64) launch_store_half<double>((const double*)dev, S.nd, S.ns, g->stage_ex, g->stage16, st);
+  else launch_store_half<float>((const float*)dev, S.nd, S.ns, g->stage_ex, g->stage16, st);
+  XLS_CUDA(cudaGetLastError());
+  XLS_CUDA(cudaMemcpyAsync(store_ptr(g, sub), g->stage16, n * 2, cudaMemcpyDeviceToHost, st));
+  XLS_CUDA(cudaMemcpyAsync(g->store_ex.data() + S.off_state, g->stage_ex, S.ns * sizeof(int), cudaMemcpyDeviceToHost,
+                           st));
+  XLS_CUDA(cudaStreamSynchronize(st));
+  return XLS_OK;
+}
 
 // the partial grid of wave w with the Hamiltonian of the wave-mode grid
 xls_status wave_worker(xls_grid g, int w, xls_grid* out) {
@@ -1387,7 +1421,15 @@ xls_status wave_orbitals_set(xls_grid g, int sub, const double* psi, int on_devi
     XLS_CUDA(cudaMemcpy(tmp.data(), psi, n * sizeof(double), cudaMemcpyDeviceToHost));
     src = tmp.data();
   }
-  if (g->prec == XLS_FP64) {
+  if (g->store16) {   // FP64 up, halves + exponents back
+    XLS_CUDA(cudaMemcpyAsync(g->blk[0], src, n * sizeof(double), cudaMemcpyHostToDevice, g->st));
+    launch_store_half<double>((const double*)g->blk[0], S.nd, S.ns, g->stage_ex, g->stage16, g->st);
+    XLS_CUDA(cudaGetLastError());
+    XLS_CUDA(cudaMemcpyAsync(store_ptr(g, sub), g->stage16, n * 2, cudaMemcpyDeviceToHost, g->st));
+    XLS_CUDA(cudaMemcpyAsync(g->store_ex.data() + S.off_state, g->stage_ex, S.ns * sizeof(int), cudaMemcpyDeviceToHost,
+                             g->st));
+    XLS_CUDA(cudaStreamSynchronize(g->st));
+  } else if (g->prec == XLS_FP64) {
     std::memcpy(store_ptr(g, sub), src, n * sizeof(double));
   } else {
     float* dst = (float*)store_ptr(g, sub);
@@ -1404,7 +1446,15 @@ xls_status wave_orbitals_get(xls_grid g, int sub, double* out, int on_device) {
   std::vector<double> tmp;
   if (on_device) tmp.resize(n);
   double* dst = on_device ? tmp.data() : out;
-  if (g->prec == XLS_FP64) {
+  if (g->store16) {   // halves + exponents up, FP64 back
+    XLS_CUDA(cudaMemcpyAsync(g->stage16, store_ptr(g, sub), n * 2, cudaMemcpyHostToDevice, g->st));
+    XLS_CUDA(cudaMemcpyAsync(g->stage_ex, g->store_ex.data() + S.off_state, S.ns * sizeof(int), cudaMemcpyHostToDevice,
+                             g->st));
+    launch_load_half<double>(g->stage16, S.nd, S.ns, g->stage_ex, (double*)g->blk[0], g->st);
+    XLS_CUDA(cudaGetLastError());
+    XLS_CUDA(cudaMemcpyAsync(dst, g->blk[0], n * sizeof(double), cudaMemcpyDeviceToHost, g->st));
+    XLS_CUDA(cudaStreamSynchronize(g->st));
+  } else if (g->prec == XLS_FP64) {
     std::memcpy(dst, store_ptr(g, sub), n * sizeof(double));
   } else {
     const float* src = (const float*)store_ptr(g, sub);
@@ -1420,7 +1470,7 @@ xls_status wave_orbitals_random(xls_grid g, uint64_t seed) {
     const long long n = S.nd * S.ns;
     if (g->prec == XLS_FP64) launch_splitmix_fill_f64((double*)g->blk[0], n, seed, S.off_blk, g->st);
     else launch_splitmix_fill_f32((float*)g->blk[0], n, seed, S.off_blk, g->st);
-    XLS_CUDA(cudaMemcpyAsync(store_ptr(g, a), g->blk[0], (size_t)n * g->elem, cudaMemcpyDeviceToHost, g->st));
+    XLS_TRY(device_to_store(g, a, g->blk[0], g->st));
   }
   XLS_CUDA(cudaStreamSynchronize(g->st));
   g->orb_set = true;
@@ -1441,7 +1491,8 @@ xls_status wave_chefsi(xls_grid g, int degree, int n_passes, const double* bound
     xls_grid k = nullptr;
     XLS_TRY(wave_worker(g, (int)w, &k));
     xls_status s = XLS_OK;
-    for (int j = 0; j < cnt && s == XLS_OK; ++j) s = raw_orbitals(k, j, store_ptr(g, first + j), true);
+    for (int j = 0; j < cnt && s == XLS_OK; ++j)
+      s = store_to_device(g, first + j, (char*)k->blk[k->cur] + (size_t)k->subs[j].off_blk * k->elem, g->st);
     k->orb_set = true;
     const double* bw = bounds ? bounds + 3 * (size_t)first
                               : (g->have_ritz ? g->host_bounds.data() + 3 * (size_t)first : nullptr);
@@ -1460,7 +1511,8 @@ xls_status wave_chefsi(xls_grid g, int degree, int n_passes, const double* bound
       cudaMemcpyAsync(g->cw + S0.off_state, k->cw, k->tot_states * sizeof(double), cudaMemcpyDeviceToDevice, g->st);
       s = xls_get_bounds(k, g->host_bounds.data() + 3 * (size_t)first);
     }
-    for (int j = 0; j < cnt && s == XLS_OK; ++j) s = raw_orbitals(k, j, store_ptr(g, first + j), false);
+    for (int j = 0; j < cnt && s == XLS_OK; ++j)
+      s = device_to_store(g, first + j, (const char*)k->blk[k->cur] + (size_t)k->subs[j].off_blk * k->elem, g->st);
     if (s == XLS_OK && cudaStreamSynchronize(g->st) != cudaSuccess) s = fail(XLS_ECUDA, "wave: synchronisation failed");
     if (s == XLS_OK) {
       for (int i = 0; i < 4; ++i) g->wave_stage_ms[i] += k->stage_ms[i];
@@ -1490,7 +1542,7 @@ xls_status wave_density(xls_grid g, double n_electrons, double kT, double* mu_ou
   for (int a = 0; a < g->n_sub; ++a) {
     const SubDev& S = g->subs[a];
     const long long core = (long long)S.core_n[0] * S.core_n[1] * S.core_n[2];
-    XLS_CUDA(cudaMemcpyAsync(g->blk[0], store_ptr(g, a), (size_t)S.nd * S.ns * g->elem, cudaMemcpyHostToDevice, g->st));
+    XLS_TRY(store_to_device(g, a, g->blk[0], g->st));
     if (g->prec == XLS_FP64)
       launch_density_occ<double>(g->d_subs + a, 1, core, (const double*)g->blk[0], g->occ, g->gn, g->rho, g->st);
     else
@@ -1575,6 +1627,8 @@ xls_status xls_grid_destroy(xls_grid g) {
   if (g->ev_side_in) cudaEventDestroy(g->ev_side_in);
   if (g->ev_side_out) cudaEventDestroy(g->ev_side_out);
   if (g->store) cudaFreeHost(g->store);
+  if (g->stage16) cudaFree(g->stage16);
+  if (g->stage_ex) cudaFree(g->stage_ex);
   delete g;
   return XLS_OK;
 }
@@ -1893,6 +1947,50 @@ xls_status xls_get_eigs(xls_grid g, int sub, double* lambda_out, double* c_out) 
   XLS_CUDA(cudaStreamSynchronize(g->st));
   if (lambda_out) XLS_CUDA(cudaMemcpy(lambda_out, g->lam + S.off_state, S.ns * sizeof(double), cudaMemcpyDeviceToHost));
   if (c_out) XLS_CUDA(cudaMemcpy(c_out, g->cw + S.off_state, S.ns * sizeof(double), cudaMemcpyDeviceToHost));
+  return XLS_OK;
+}
+
+xls_status xls_wave_store_fp16(xls_grid g, int on) {
+  if (!g) return fail(XLS_EINVAL, "xls_wave_store_fp16: bad arguments");
+  if (!g->wave) return fail(XLS_EINVAL, "xls_wave_store_fp16: the grid is not running in waves");
+  if ((on != 0) == g->store16) return XLS_OK;
+  long long max_blk = 0;
+  int max_ns = 0;
+  for (const SubDev& S : g->subs) {
+    max_blk = std::max(max_blk, S.nd * S.ns);
+    max_ns = std::max(max_ns, S.ns);
+  }
+  if (!g->stage16) {
+    if (cudaMalloc(&g->stage16, (size_t)max_blk * 2) != cudaSuccess ||
+        cudaMalloc((void**)&g->stage_ex, (size_t)max_ns * sizeof(int)) != cudaSuccess) {
+      cudaGetLastError();
+      return fail(XLS_ENOMEM, "xls_wave_store_fp16: device staging could not be allocated");
+    }
+  }
+  // new store; the orbitals held so far move over through the device
+  const bool to16 = on != 0;
+  const size_t new_elem = to16 ? 2 : g->elem;
+  void* ns_ = nullptr;
+  if (cudaMallocHost(&ns_, (size_t)g->tot_blk * new_elem) != cudaSuccess) {
+    cudaGetLastError();
+    return fail(XLS_ENOMEM, "xls_wave_store_fp16: pinned host store could not be allocated");
+  }
+  std::memset(ns_, 0, (size_t)g->tot_blk * new_elem);
+  void* old = g->store;
+  const bool was16 = g->store16;
+  if (to16) g->store_ex.assign((size_t)g->tot_states, 0);
+  for (int a = 0; a < g->n_sub && g->orb_set; ++a) {
+    g->store = old;
+    g->store16 = was16;
+    XLS_TRY(store_to_device(g, a, g->blk[0], g->st));
+    g->store = ns_;
+    g->store16 = to16;
+    XLS_TRY(device_to_store(g, a, g->blk[0], g->st));
+  }
+  XLS_CUDA(cudaStreamSynchronize(g->st));
+  g->store = ns_;
+  g->store16 = to16;
+  cudaFreeHost(old);
   return XLS_OK;
 }
 

@@ -58,6 +58,7 @@ _SIGS = {
     "xls_get_subspace": (c_int, [c_void_p, c_int, c_void_p, c_void_p]),
     "xls_dos": (c_int, [c_void_p, c_void_p, c_int, c_double, c_void_p]),
     "xls_scf_cg_iterations": (c_int, [c_void_p, c_void_p]),
+    "xls_wave_store_fp16": (c_int, [c_void_p, c_int]),
     "xls_get_bounds": (c_int, [c_void_p, c_void_p]),
     "xls_get_timings": (c_int, [c_void_p, c_void_p, POINTER(c_int)]),
     "xls_set_profiling": (c_int, [c_void_p, c_int]),
@@ -211,6 +212,10 @@ def xls_get_eigs(g, sub, n_states):
     c = np.zeros(n_states)
     _check(load().xls_get_eigs(g, int(sub), lam.ctypes.data_as(c_void_p), c.ctypes.data_as(c_void_p)))
     return lam, c
+
+
+def xls_wave_store_fp16(g, on=True):
+    _check(load().xls_wave_store_fp16(g, 1 if on else 0))
 
 
 def xls_scf_cg_iterations(g):

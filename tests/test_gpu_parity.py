@@ -526,6 +526,48 @@ def test_scf_in_waves_matches_resident_grid():
     assert relerr(res["waves"][1], res["resident"][1]) < 1e-9
 
 
+@pytest.mark.parametrize("prec", [xls.XLS_FP64, xls.XLS_MIXED_FP16])
+def test_waves_fp16_store(prec):
+    """Waves with the orbitals kept in FP16 in the host store (switched before and after they are
+    set): passes, mu and rho stay within the FP16 storage error of the all-resident grid, and the
+    orbitals read back are orthonormal to that error."""
+    w = dirichlet20_workload()
+    V = pseudo.local_potential(w)
+    subs = dc.partition(w)
+    psi0 = _start_blocks(w, subs)
+    res = {}
+    for mode, budget in (("resident", 0), ("waves16", 90 << 20), ("waves16_late", 90 << 20)):
+        g = xls.Grid(w, prec, hbm_budget_bytes=budget)
+        try:
+            g.set_hamiltonian(V)
+            if mode == "waves16":
+                xls.xls_wave_store_fp16(g.h, True)
+            for a in range(w.n_sub):
+                xls.xls_orbitals_set(g.h, a, psi0[a])
+            xls.xls_chefsi_batch(g.h, w.degree, 2)
+            if mode == "waves16_late":
+                xls.xls_wave_store_fp16(g.h, True)   # converts the stored orbitals
+            xls.xls_chefsi_batch(g.h, w.degree, 1)
+            lam = [xls.xls_get_eigs(g.h, a, int(w.n_states[a]))[0] for a in range(w.n_sub)]
+            rho = np.zeros(int(np.prod(w.n)))
+            mu, eb, es = xls.xls_density(g.h, w.n_electrons, w.kT, rho)
+            P0 = xls.xls_orbitals_get(g.h, 0, np.zeros((int(w.n_states[0]), subs[0].N)))
+            if mode == "resident":
+                with pytest.raises(xls.XlsError):
+                    xls.xls_wave_store_fp16(g.h, True)
+        finally:
+            g.close()
+        res[mode] = (lam, rho, mu, P0)
+    for mode in ("waves16", "waves16_late"):
+        for a in range(w.n_sub):
+            occ = res["resident"][0][a] < res["resident"][2] + 0.1
+            np.testing.assert_allclose(res[mode][0][a][occ], res["resident"][0][a][occ], atol=1e-4)
+        assert abs(res[mode][2] - res["resident"][2]) < 1e-4
+        assert relerr(res[mode][1], res["resident"][1]) < 1e-3
+        P = res[mode][3]
+        np.testing.assert_allclose(P @ P.T, np.eye(P.shape[0]), atol=2e-3)
+
+
 @pytest.mark.parametrize("prec", [xls.XLS_FP64, xls.XLS_MIXED_BF16])
 def test_waves_match_resident_grid(prec):
     """An HBM budget below the footprint runs the subdomains in waves (orbitals in the host
