@@ -4,10 +4,11 @@
 //   1. M_s = L L^T                   k_cholesky      one CTA per subdomain
 //   2. W = L^-1 H_s, A = L^-1 W^T    k_trsm_lower x2 column-parallel CTAs
 //   3. A = Q T Q^T (Householder)     k_tridiag       one CTA per subdomain
-//   4. T = Z_T diag(lambda) Z_T^T    k_tri_eig       FP32 Sturm bisection for shifts, FP64
-//                                                    inverse iteration + Gram-Schmidt per
-//                                                    cluster, FP64 Rayleigh-Ritz (Jacobi) inside
-//                                                    each cluster of close eigenvalues
+//   4. T = Z_T diag(lambda) Z_T^T    k_tri_eig       FP32 Sturm bisection for shifts, inverse
+//                                                    iteration + Gram-Schmidt per cluster (two
+//                                                    FP32 iterations, a final FP64 one), FP64
+//                                                    Rayleigh-Ritz (Jacobi) inside each cluster
+//                                                    of close eigenvalues
 //   5. Z = Q Z_T                     k_backtransform column-parallel CTAs
 //   6. Y = L^-T Z                    k_trsm_upper    column-parallel CTAs
 //
@@ -434,9 +435,92 @@ k_tri_eig(const SubDev* __restrict__ subs, double* vecs, double* Zm, double* scr
       // a singleton refines its shift to the Rayleigh quotient after every solve (Rayleigh
       // quotient iteration); members of a cluster keep their bisection shifts
       double sigma = lam32[mbr];
-      for (int j = 0; j < n; ++j) X(j) = hash_unit((unsigned)mbr + 1u, (unsigned)j);
-      for (int iter = 0; iter < 3; ++iter) {
-        if (iter == 0 || k == 1) {
+      bool ok32;
+      // the first two iterations in FP32 (their dependent chains run at FP32 latency; the vector
+      // they give is good to FP32 rounding), the third in FP64 from that vector, with an FP64
+      // Rayleigh-quotient shift for singletons: the FP64 result of three FP64 iterations
+      {
+        float* fs = reinterpret_cast<float*>(scr);   // FP32 arrays in the space of lm / dinv
+        auto LMf = [&](int jj) -> float& { return fs[(long long)jj * T + t]; };
+        auto DIf = [&](int jj) -> float& { return fs[(long long)(n + jj) * T + t]; };
+        auto Xf = [&](int jj) -> float& { return fs[(long long)(2 * n + jj) * T + t]; };
+        const float tiny_f = (float)fmax(1e-7 * tnorm, 1e-30);   // FP32 rounding level of the shift
+        float sig_f = (float)sigma;
+        ok32 = true;
+        for (int jj = 0; jj < n; ++jj) Xf(jj) = (float)hash_unit((unsigned)mbr + 1u, (unsigned)jj);
+        for (int iter = 0; iter < 2; ++iter) {
+          if (iter == 0 || k == 1) {
+            float dp = (float)d[0] - sig_f;
+            if (fabsf(dp) < tiny_f) dp = dp < 0.f ? -tiny_f : tiny_f;
+            DIf(0) = 1.f / dp;
+            for (int jj = 1; jj < n; ++jj) {
+              const float ej = (float)e[jj - 1];
+              const float l = ej * DIf(jj - 1);
+              LMf(jj - 1) = l;
+              dp = ((float)d[jj] - sig_f) - l * ej;
+              if (fabsf(dp) < tiny_f) dp = dp < 0.f ? -tiny_f : tiny_f;
+              DIf(jj) = 1.f / dp;
+            }
+          }
+          float yv = Xf(0);
+          Xf(0) = yv * DIf(0);
+          for (int jj = 1; jj < n; ++jj) {
+            yv = Xf(jj) - LMf(jj - 1) * yv;
+            Xf(jj) = yv * DIf(jj);
+          }
+          float xn = Xf(n - 1);
+          for (int jj = n - 2; jj >= 0; --jj) {
+            xn = Xf(jj) - LMf(jj) * xn;
+            Xf(jj) = xn;
+          }
+          for (int pass = 0; pass < 2; ++pass)
+            for (int q = s; q < mbr; ++q) {
+              float dot = 0.f;
+              for (int jj = 0; jj < n; ++jj) dot += (float)Z[(long long)jj * n + q] * Xf(jj);
+              for (int jj = 0; jj < n; ++jj) Xf(jj) -= dot * (float)Z[(long long)jj * n + q];
+            }
+          float nrm = 0.f;
+          for (int jj = 0; jj < n; ++jj) nrm += Xf(jj) * Xf(jj);
+          if (!(nrm > 0.f) || isinf(nrm)) {   // FP32 range exceeded: redo the member in FP64
+            ok32 = false;
+            break;
+          }
+          nrm = rsqrtf(nrm);
+          for (int jj = 0; jj < n; ++jj) Xf(jj) *= nrm;
+          if (k == 1) {
+            float rq = 0.f, xm = 0.f, x0 = Xf(0);
+            for (int jj = 0; jj < n; ++jj) {
+              const float xp = (jj + 1 < n) ? Xf(jj + 1) : 0.f;
+              float tx = (float)d[jj] * x0 + (jj + 1 < n ? (float)e[jj] * xp : 0.f);
+              if (jj > 0) tx += (float)e[jj - 1] * xm;
+              rq += x0 * tx;
+              xm = x0;
+              x0 = xp;
+            }
+            sig_f = rq;
+          }
+        }
+        for (int jj = 0; jj < n; ++jj) X(jj) = (double)Xf(jj);
+      }
+      int it0 = 2;
+      if (!ok32) {
+        for (int j = 0; j < n; ++j) X(j) = hash_unit((unsigned)mbr + 1u, (unsigned)j);
+        it0 = 0;
+      } else if (k == 1) {   // FP64 Rayleigh quotient of the FP32 vector (error quadratic in the vector's)
+        double rq = 0.0, xx = 0.0, xm = 0.0, x0 = X(0);
+        for (int jj = 0; jj < n; ++jj) {
+          const double xp = (jj + 1 < n) ? X(jj + 1) : 0.0;
+          double tx = d[jj] * x0 + (jj + 1 < n ? e[jj] * xp : 0.0);
+          if (jj > 0) tx += e[jj - 1] * xm;
+          rq += x0 * tx;
+          xx += x0 * x0;
+          xm = x0;
+          x0 = xp;
+        }
+        sigma = rq / xx;
+      }
+      for (int iter = it0; iter < 3; ++iter) {
+        if (iter == it0 || k == 1) {
           double dp = d[0] - sigma;  // LDL^T of T - sigma I
           if (fabs(dp) < tiny) dp = dp < 0 ? -tiny : tiny;
           DI(0) = 1.0 / dp;
@@ -469,7 +553,7 @@ k_tri_eig(const SubDev* __restrict__ subs, double* vecs, double* Zm, double* scr
         for (int j = 0; j < n; ++j) nrm += X(j) * X(j);
         nrm = 1.0 / sqrt(nrm);
         for (int j = 0; j < n; ++j) X(j) *= nrm;
-        if (k == 1) {
+        if (k == 1 && iter < 2) {
           double rq = 0.0, xm = 0.0, x0 = X(0);
           for (int j = 0; j < n; ++j) {
             const double xp = (j + 1 < n) ? X(j + 1) : 0.0;
