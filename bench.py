@@ -268,20 +268,24 @@ def run_ours(args):
     # bounds the previous pass left (read back with the density, passed in with the blocks, so
     # that the pass needs no Rayleigh-Ritz step of the unfiltered blocks), Fermi level and the
     # density read back to the host
-    host_in = [torch.empty((int(w.n_states[a]), w.sub_points(a)), dtype=torch.float64).pin_memory()
+    # (in the grid's own precision: FP32 blocks for the mixed paths, FP64 for the FP64 path)
+    f32 = prec != xls.XLS_FP64
+    hdt = torch.float32 if f32 else torch.float64
+    host_in = [torch.empty((int(w.n_states[a]), w.sub_points(a)), dtype=hdt).pin_memory()
                for a in range(w.n_sub)]
+    set_block = xls.xls_orbitals_set_f32 if f32 else xls.xls_orbitals_set
     for a in range(w.n_sub):
-        xls.xls_orbitals_get(g.h, a, host_in[a].numpy())
+        (xls.xls_orbitals_get_f32 if f32 else xls.xls_orbitals_get)(g.h, a, host_in[a].numpy())
     rho_host = torch.empty(ng, dtype=torch.float64).pin_memory()
     bounds = xls.xls_get_bounds(g.h, w.n_sub)
-    h2d = sum(t.numel() * 8 for t in host_in) + bounds.size * 8
+    h2d = sum(t.numel() * t.element_size() for t in host_in) + bounds.size * 8
     d2h = ng * 8 + 3 * 8 + bounds.size * 8
     torch.cuda.synchronize()
     e2e_times = []
     for it in range(max(2, args.steps // 2) + 1):
         t0 = time.perf_counter()
         for a in range(w.n_sub):
-            xls.xls_orbitals_set(g.h, a, host_in[a].numpy())
+            set_block(g.h, a, host_in[a].numpy())
         xls.xls_chefsi_batch(g.h, w.degree, 1, bounds)
         xls.xls_density(g.h, w.n_electrons, w.kT, rho_host.numpy())
         bounds = xls.xls_get_bounds(g.h, w.n_sub)

@@ -101,6 +101,15 @@ xls_status xls_hamiltonian_set(xls_grid g, const double* veff, int veff_on_devic
  * orbital storage (rounded to FP32 on the mixed path). */
 xls_status xls_orbitals_set(xls_grid g, int sub, const double* psi, int on_device);
 
+/* FP32 forms of xls_orbitals_set / xls_orbitals_get (N_s x N_d floats, vector-major, host or
+ * device): on the mixed paths the block is the grid's own FP32 storage, copied without
+ * conversion (half the bytes of the FP64 forms); on the FP64 path it is widened to (set) or
+ * rounded from (get) FP64 on the device.  Library-specific: the paper keeps FP64 orbitals.
+ * Errors: XLS_EINVAL for bad arguments and in wave mode (whose host store the FP64 forms fill),
+ * XLS_ECUDA. */
+xls_status xls_orbitals_set_f32(xls_grid g, int sub, const float* psi, int on_device);
+xls_status xls_orbitals_get_f32(xls_grid g, int sub, float* psi_out, int on_device);
+
 /* Fill every subdomain's start block with U[-0.5, 0.5) from SplitMix64 (Steele et al. 2014):
  * value k of the concatenated blocks (subdomains in order, each vector-major) is the top 53
  * bits of output k of the stream of `seed`, times 2^-53, minus 0.5. */

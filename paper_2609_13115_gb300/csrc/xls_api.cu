@@ -1870,6 +1870,43 @@ xls_status xls_orbitals_get(xls_grid g, int sub, double* psi_out, int on_device)
   return XLS_OK;
 }
 
+xls_status xls_orbitals_set_f32(xls_grid g, int sub, const float* psi, int on_device) {
+  if (!g || !psi || sub < 0 || sub >= g->n_sub) return fail(XLS_EINVAL, "xls_orbitals_set_f32: bad arguments");
+  if (g->wave) return fail(XLS_EINVAL, "xls_orbitals_set_f32: not in wave mode (xls_orbitals_set takes doubles)");
+  const SubDev& S = g->subs[sub];
+  const long long n = S.nd * S.ns;
+  const cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+  if (g->prec != XLS_FP64) {
+    XLS_CUDA(cudaMemcpyAsync((float*)g->blk[g->cur] + S.off_blk, psi, n * sizeof(float), kind, g->st));
+  } else {
+    // stage through the free block (n floats fit in a block of doubles) and widen to FP64
+    float* tmp = (float*)g->blk[(g->cur + 1) % 3];
+    XLS_CUDA(cudaMemcpyAsync(tmp, psi, n * sizeof(float), kind, g->st));
+    launch_convert_f32_f64(tmp, (double*)g->blk[g->cur] + S.off_blk, n, g->st);
+  }
+  XLS_CUDA(cudaStreamSynchronize(g->st));
+  g->orb_set = true;
+  g->have_ritz = false;
+  return XLS_OK;
+}
+
+xls_status xls_orbitals_get_f32(xls_grid g, int sub, float* psi_out, int on_device) {
+  if (!g || !psi_out || sub < 0 || sub >= g->n_sub) return fail(XLS_EINVAL, "xls_orbitals_get_f32: bad arguments");
+  if (g->wave) return fail(XLS_EINVAL, "xls_orbitals_get_f32: not in wave mode (xls_orbitals_get gives doubles)");
+  const SubDev& S = g->subs[sub];
+  const long long n = S.nd * S.ns;
+  const cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+  if (g->prec != XLS_FP64) {
+    XLS_CUDA(cudaMemcpyAsync(psi_out, (float*)g->blk[g->cur] + S.off_blk, n * sizeof(float), kind, g->st));
+  } else {
+    float* tmp = (float*)g->blk[(g->cur + 1) % 3];
+    launch_convert_f64_f32((double*)g->blk[g->cur] + S.off_blk, tmp, n, g->st);
+    XLS_CUDA(cudaMemcpyAsync(psi_out, tmp, n * sizeof(float), kind, g->st));
+  }
+  XLS_CUDA(cudaStreamSynchronize(g->st));
+  return XLS_OK;
+}
+
 xls_status xls_chefsi_batch(xls_grid g, int degree, int n_passes, const double* bounds) {
   if (!g || degree < 1 || degree >= kMaxDegree - 1 || n_passes < 0) return fail(XLS_EINVAL, "xls_chefsi_batch: bad arguments");
   if (!g->ham_set || !g->orb_set) return fail(XLS_EINVAL, "xls_chefsi_batch: Hamiltonian or orbitals not set");

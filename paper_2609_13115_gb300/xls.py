@@ -49,6 +49,8 @@ _SIGS = {
     "xls_orbitals_set": (c_int, [c_void_p, c_int, c_void_p, c_int]),
     "xls_orbitals_random": (c_int, [c_void_p, c_uint64]),
     "xls_orbitals_get": (c_int, [c_void_p, c_int, c_void_p, c_int]),
+    "xls_orbitals_set_f32": (c_int, [c_void_p, c_int, c_void_p, c_int]),
+    "xls_orbitals_get_f32": (c_int, [c_void_p, c_int, c_void_p, c_int]),
     "xls_chefsi_batch": (c_int, [c_void_p, c_int, c_int, c_void_p]),
     "xls_chefsi_stage": (c_int, [c_void_p, c_int, c_int, c_void_p]),
     "xls_hamiltonian_apply": (c_int, [c_void_p, c_int, c_int, c_void_p, c_void_p, c_int]),
@@ -168,6 +170,26 @@ def xls_orbitals_set(g, sub, psi):
     a = np.ascontiguousarray(psi, dtype=np.float64) if isinstance(psi, np.ndarray) else psi
     p, dev = _ptr(a)
     _check(load().xls_orbitals_set(g, int(sub), p, dev))
+
+
+def _require_f32(a):
+    dt = a.dtype if isinstance(a, np.ndarray) else getattr(a, "dtype", None)
+    if str(dt) not in ("float32", "torch.float32"):
+        raise TypeError(f"FP32 orbital arrays must be float32, got {dt}")
+
+
+def xls_orbitals_set_f32(g, sub, psi):
+    a = np.ascontiguousarray(psi, dtype=np.float32) if isinstance(psi, np.ndarray) else psi
+    _require_f32(a)
+    p, dev = _ptr(a)
+    _check(load().xls_orbitals_set_f32(g, int(sub), p, dev))
+
+
+def xls_orbitals_get_f32(g, sub, out):
+    _require_f32(out)
+    p, dev = _ptr(out)
+    _check(load().xls_orbitals_get_f32(g, int(sub), p, dev))
+    return out
 
 
 def xls_orbitals_random(g, seed):

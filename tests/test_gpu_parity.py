@@ -109,6 +109,34 @@ def _start_blocks(w, subs):
     return [synth.psi0_block(w.psi_seed, s.N, int(w.n_states[a]), offs[a]) for a, s in enumerate(subs)]
 
 
+@pytest.mark.parametrize("prec", [xls.XLS_FP64, xls.XLS_MIXED_FP16])
+def test_orbitals_fp32_entry_points(prec):
+    """Blocks set and read as FP32: the round trip is exact (the mixed grid stores FP32; the FP64
+    grid widens exactly), the FP64 read of an FP32-set block is the widened block, and a pass from
+    it gives the Ritz values of a pass from the same values set through the FP64 entry point."""
+    w = synth.workload(0)
+    V = pseudo.local_potential(w)
+    n, ns = w.sub_points(0), int(w.n_states[0])
+    psi = synth.psi0_block(w.psi_seed, n, ns).astype(np.float32)
+    lam = {}
+    for entry in ("f32", "f64"):
+        with make_grid(w, V, prec) as g:
+            if entry == "f32":
+                xls.xls_orbitals_set_f32(g.h, 0, psi)
+                back32 = xls.xls_orbitals_get_f32(g.h, 0, np.empty_like(psi))
+                back64 = xls.xls_orbitals_get(g.h, 0, np.empty(psi.shape))
+                assert np.array_equal(back32, psi)
+                assert np.array_equal(back64, psi.astype(np.float64))
+                with pytest.raises(TypeError):
+                    xls.xls_orbitals_get_f32(g.h, 0, np.empty(psi.shape))
+            else:
+                xls.xls_orbitals_set(g.h, 0, psi.astype(np.float64))
+            xls.xls_chefsi_batch(g.h, w.degree, 2)
+            lam[entry] = xls.xls_get_eigs(g.h, 0, ns)[0]
+    tol = 1e-10 if prec == xls.XLS_FP64 else 1e-5
+    np.testing.assert_allclose(lam["f32"], lam["f64"], rtol=0, atol=tol)
+
+
 def test_random_start_matches_host_generator():
     w = dirichlet_workload()
     V = pseudo.local_potential(w)
