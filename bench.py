@@ -228,6 +228,11 @@ def run_ours(args):
     xls.xls_set_graphs(g.h, 1)
     for _ in range(max(args.warmup, 3)):
         step(g.h)
+    # the library's autotuner picks the eigensolver cluster size and the Gram K split on this
+    # workload (outside the timed region); the passes after it recapture their graphs
+    tune = xls.xls_autotune(g.h, 5)
+    for _ in range(2):
+        step(g.h)
     sampler = ClockSampler(local)
     sampler.start()
     barrier(ws)
@@ -324,6 +329,8 @@ def run_ours(args):
         torch.cuda.synchronize()
         f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         step(g64.h)
+        xls.xls_autotune(g64.h, 2)
+        step(g64.h)
         f0.record(stream)
         for _ in range(args.fp64_steps):
             step(g64.h)
@@ -363,7 +370,8 @@ def run_ours(args):
             "config": {"workload": w.name, "subdomains": w.n_sub, "points_per_subdomain": w.sub_points(0),
                        "states": int(w.n_states[0]), "degree": w.degree,
                        "l2": "inputs larger than L2 (each orbital block 566 MB)",
-                       "parallelism": f"replicas x{ws}" if ws > 1 else "single GPU"},
+                       "parallelism": f"replicas x{ws}" if ws > 1 else "single GPU",
+                       "autotuned": {"eig_cluster_ctas": tune[0], "gram_ctas_per_sm": tune[1]}},
             "stage_ms": dict({k: round(float(v), 3) for k, v in zip(["filter", "projection", "eig", "rotation"], stage_ms)},
                              density=round(density_ms, 3)),
             "kernel_share": kernel_share,

@@ -130,6 +130,22 @@ xls_status xls_orbitals_get(xls_grid g, int sub, double* psi_out, int on_device)
  * from the previous pass's Ritz values.  Every subdomain runs in the same launches. */
 xls_status xls_chefsi_batch(xls_grid g, int degree, int n_passes, const double* bounds);
 
+/* Autotuner of the batched launches (library-specific: the paper tunes its kernels by hand for
+ * its CPUs).  On the grid's own data it times the launch configurations of the tunable stages
+ * and keeps the fastest of each:
+ *   choices_out[0]: CTAs per subdomain cluster of the Cholesky factorisation and the
+ *                   tridiagonalisation, 8 or 16 (0: clusters off, not tuned);
+ *   choices_out[1]: K split of the tensor-core Gram, in CTAs per SM aimed at, one of 1, 2, 3, 4,
+ *                   6, 8 (0: no tensor-core Gram on this grid, not tuned).
+ * Every candidate runs `reps` (1..100) times after one warm-up call, timed with CUDA events on
+ * the grid's stream.  The input is the last pass's M_s and H_s: they and the split exponents are
+ * saved and put back, the eigenpairs recomputed with the chosen configuration, so the next pass
+ * differs from an untuned one by rounding only.  Captured pass graphs are dropped (the next
+ * graphed pass captures the tuned launches).  choices_out may be NULL.
+ * Errors: XLS_EINVAL (bad arguments, wave mode, no pass run yet), XLS_ENOMEM (no room for the
+ * saved matrices), XLS_ECUDA, and the status of the eigensolve (XLS_ENOTSPD). */
+xls_status xls_autotune(xls_grid g, int reps, int* choices_out);
+
 /* Stage-wise entry points with the same arithmetic as one pass of xls_chefsi_batch, for
  * checking each step on its own.  stage 1: filter only (the orbital block becomes Psi_f);
  * stage 2: projection of the current block into M_s, H_s; stage 3: eigensolve of the current

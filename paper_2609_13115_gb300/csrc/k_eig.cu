@@ -867,18 +867,19 @@ static bool smem_ok(K kernel, size_t bytes) {
 }
 
 void launch_eig(const SubDev* d_subs, int n_sub, int max_ns, double* Ms, double* Hs, double* Y, double* W, double* lam,
-                double* vecs, int* status, double* scratch, double* R, bool cluster, cudaStream_t st) {
+                double* vecs, int* status, double* scratch, double* R, int cluster, cudaStream_t st) {
   const size_t mat = (size_t)max_ns * max_ns * sizeof(double);
   const size_t vbytes = 2 * (size_t)max_ns * sizeof(double);
   // Cholesky and tridiagonalisation on a cluster of CTAs per subdomain; one CTA per subdomain
-  // where the cluster variant cannot be launched, or when the caller asks for it
-  if (cluster && launch_cholesky_cluster(d_subs, n_sub, max_ns, Ms, status, st)) {
+  // where the cluster variant cannot be launched, or when the caller asks for it (cluster = 0;
+  // else the cluster size tried first, 8 or 16)
+  if (cluster && launch_cholesky_cluster(d_subs, n_sub, max_ns, Ms, status, cluster, st)) {
   } else if (smem_ok(k_cholesky<true>, mat)) k_cholesky<true><<<n_sub, 512, mat, st>>>(d_subs, Ms, status);
   else k_cholesky<false><<<n_sub, 512, 0, st>>>(d_subs, Ms, status);
   dim3 gt((max_ns + 7) / 8, n_sub);   // 8 warps (columns) per CTA
-  trsm(false, max_ns, gt, d_subs, Ms, Hs, 0, W, st, cluster);   // W = L^-1 H_s
-  trsm(false, max_ns, gt, d_subs, Ms, W, 1, Hs, st, cluster);   // A = L^-1 W^T
-  if (cluster && launch_tridiag_cluster(d_subs, n_sub, max_ns, Hs, vecs, st)) {
+  trsm(false, max_ns, gt, d_subs, Ms, Hs, 0, W, st, cluster != 0);   // W = L^-1 H_s
+  trsm(false, max_ns, gt, d_subs, Ms, W, 1, Hs, st, cluster != 0);   // A = L^-1 W^T
+  if (cluster && launch_tridiag_cluster(d_subs, n_sub, max_ns, Hs, vecs, cluster, st)) {
   } else if (smem_ok(k_tridiag<true>, mat + vbytes)) k_tridiag<true><<<n_sub, 512, mat + vbytes, st>>>(d_subs, Hs, vecs, max_ns);
   else k_tridiag<false><<<n_sub, 512, vbytes, st>>>(d_subs, Hs, vecs, max_ns);
   // 32 eigenvalue indices (128 threads) per CTA, spread over the SMs
@@ -908,7 +909,7 @@ void launch_eig(const SubDev* d_subs, int n_sub, int max_ns, double* Ms, double*
                                                                                                    W);
   else
     k_backtransform<<<gb, 256, (max_ns + 256) * sizeof(double), st>>>(d_subs, Hs, vecs, W);
-  trsm(true, max_ns, gt, d_subs, Ms, W, 0, Y, st, cluster);     // Y = L^-T Z
+  trsm(true, max_ns, gt, d_subs, Ms, W, 0, Y, st, cluster != 0);     // Y = L^-T Z
 }
 
 size_t eig_scratch_doubles(int n_sub, int max_ns) { return (size_t)n_sub * kTriThreads * 3 * max_ns; }

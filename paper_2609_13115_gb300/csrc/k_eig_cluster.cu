@@ -658,10 +658,12 @@ static bool launch_cluster(K kernel, int n_sub, int CL, size_t smem, cudaStream_
   return true;
 }
 
-// Both factorisations run on 8-CTA clusters (16, a non-portable size, only where 8 does not fit:
-// measured at N_s = 160, the extra barrier latency of 16 CTAs outweighs their extra FP64 pipes).
-bool launch_cholesky_cluster(const SubDev* d_subs, int n_sub, int max_ns, double* Ms, int* status, cudaStream_t st) {
-  for (int CL : {8, 16}) {
+// Both factorisations run on clusters of cl_first CTAs (8 by default; 16, a non-portable size,
+// where the autotuner finds it faster, and as the fallback where 8 do not fit: measured at
+// N_s = 160, the extra barrier latency of 16 CTAs outweighs their extra FP64 pipes).
+bool launch_cholesky_cluster(const SubDev* d_subs, int n_sub, int max_ns, double* Ms, int* status, int cl_first,
+                             cudaStream_t st) {
+  for (int CL : {cl_first == 16 ? 16 : 8, cl_first == 16 ? 8 : 16}) {
     const size_t smem = ((size_t)(max_ns + CL - 1) / CL * max_ns + 2 * (size_t)(max_ns + 1)) * sizeof(double);
     if (smem <= 200 * 1024 &&
         launch_cluster(std::getenv("XLS_CHOL_LEFT") ? k_cholesky_cl : k_cholesky_cl2, n_sub, CL, smem, st, d_subs, Ms,
@@ -671,13 +673,14 @@ bool launch_cholesky_cluster(const SubDev* d_subs, int n_sub, int max_ns, double
   return false;
 }
 
-bool launch_tridiag_cluster(const SubDev* d_subs, int n_sub, int max_ns, double* A, double* vecs, cudaStream_t st) {
+bool launch_tridiag_cluster(const SubDev* d_subs, int n_sub, int max_ns, double* A, double* vecs, int cl_first,
+                            cudaStream_t st) {
   size_t smem = 0;
   // one barrier per column: partials [2][8][n], pivot rows [2][n], v, w, p
   // k_tridiag_cl2 on 8-CTA clusters; 16-CTA clusters (only where 8 do not fit) take k_tridiag_cl1:
   // k_tridiag_cl2 on 16 CTAs ended a bench run with a non-positive-definite Gram matrix in the next
   // pass (cause not found), k_tridiag_cl1 on 16 CTAs passes every test
-  for (int CL : {8, 16}) {
+  for (int CL : {cl_first == 16 ? 16 : 8, cl_first == 16 ? 8 : 16}) {
     const size_t exact = ((size_t)(max_ns + CL - 1) / CL * max_ns + (2 * (size_t)CL + 5) * max_ns) * sizeof(double);
     const bool cl2 = CL <= 8 && !std::getenv("XLS_TRIDIAG_CL1");
     if (exact <= 200 * 1024 && launch_cluster(cl2 ? k_tridiag_cl2 : k_tridiag_cl1, n_sub, CL, exact, st, d_subs, A, vecs,

@@ -5,6 +5,7 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <functional>
 #include <string>
 #include <vector>
 
@@ -151,6 +152,8 @@ struct xls_grid_s {
   // tensor-core GEMMs (mixed path): Gram and rotation can be switched to SIMT independently
   bool use_tc = false, use_tc_gram = false, use_tc_rot = false;
   bool eig_cluster = true;  // Cholesky / tridiagonalisation on CTA clusters (XLS_EIG=single: one CTA)
+  int eig_cl = 8;            // cluster size tried first (8 or 16; xls_autotune)
+  int gram_cps = 4;          // tensor-core Gram: K split aiming at this many CTAs per SM (xls_autotune)
   GramPlan gplan;
   RotPlan rplan;
   // projectors
@@ -397,7 +400,7 @@ void eigensolve(xls_grid g, const xls_grid_s::View& v) {
   cudaMemcpyAsync(g->Ab + v.ss_off, g->Hs + v.ss_off, v.ss_n * sizeof(double), cudaMemcpyDeviceToDevice, v.st);
   { ProfScope ps(g, K_EIG);
     launch_eig(v.ds, v.n, v.max_ns, g->Lb, g->Ab, g->Y, g->W, g->lam, g->vecs, g->status, v.eig_scr, g->R,
-               g->eig_cluster, v.st); }
+               g->eig_cluster ? g->eig_cl : 0, v.st); }
   g->launches += 8;
 }
 
@@ -695,21 +698,21 @@ xls_status build_tma_classes(xls_grid g, int first, int n, std::vector<TmaClass>
   return XLS_OK;
 }
 
-// tensor-core Gram and rotation jobs of subdomains [first, first + n) (indices relative to
-// `first`); the exponent and split-Y arrays are indexed by state and shared with `shared`
-xls_status build_tc_plans(xls_grid g, int first, int n, GramPlan& gp, RotPlan& rp, const GramPlan* gshared,
-                          const RotPlan* rshared) {
+// Tensor-core Gram jobs of subdomains [first, first + n) (indices relative to `first`): the upper
+// block triangle of every subdomain, each block's K range split so that the grid aims at `cps`
+// CTAs per SM (152 SMs); jobs of one block are consecutive (a reduction group).
+constexpr int kMaxGramCps = 8;   // finest K split xls_autotune tries (sizes the job arrays)
+void gram_jobs(xls_grid g, int first, int n, int cps, std::vector<GramJob>& jobs, std::vector<int>& gfirst,
+               std::vector<int>& gn) {
   int groups = 0;
-  int max_ns = 0;
   for (int a = first; a < first + n; ++a) {
     const int nt = (g->subs[a].ns + 127) / 128;
     groups += nt * (nt + 1) / 2;
-    max_ns = std::max(max_ns, g->subs[a].ns);
   }
-  // K split so that the grid fills the GPU
-  const int kchunks = std::max(1, (4 * 152 + groups - 1) / groups);
-  std::vector<GramJob> jobs;
-  std::vector<int> gfirst, gn;
+  const int kchunks = std::max(1, (cps * 152 + groups - 1) / groups);
+  jobs.clear();
+  gfirst.clear();
+  gn.clear();
   for (int a = first; a < first + n; ++a) {
     const SubDev& S = g->subs[a];
     const int nt = (S.ns + 127) / 128;
@@ -723,12 +726,47 @@ xls_status build_tc_plans(xls_grid g, int first, int n, GramPlan& gp, RotPlan& r
         gn.push_back(kc);
       }
   }
-  gp.n_jobs = (int)jobs.size();
+}
+
+// device arrays of a Gram plan sized for the finest split, then the jobs of the grid's split
+xls_status alloc_gram_plan(xls_grid g, int first, int n, GramPlan& gp) {
+  std::vector<GramJob> jobs;
+  std::vector<int> gfirst, gn;
+  gram_jobs(g, first, n, kMaxGramCps, jobs, gfirst, gn);
+  gp.cap_jobs = (int)jobs.size();
   gp.n_groups = (int)gfirst.size();
   XLS_TRY(g->alloc(&gp.d_jobs, jobs.size() * sizeof(GramJob)));
   XLS_TRY(g->alloc(&gp.d_grp_first, gfirst.size() * sizeof(int)));
   XLS_TRY(g->alloc(&gp.d_grp_n, gn.size() * sizeof(int)));
   XLS_TRY(g->alloc(&gp.d_work, jobs.size() * 2 * 128 * 128 * sizeof(float)));
+  gram_jobs(g, first, n, g->gram_cps, jobs, gfirst, gn);
+  gp.n_jobs = (int)jobs.size();
+  XLS_CUDA(cudaMemcpy(gp.d_jobs, jobs.data(), jobs.size() * sizeof(GramJob), cudaMemcpyHostToDevice));
+  XLS_CUDA(cudaMemcpy(gp.d_grp_first, gfirst.data(), gfirst.size() * sizeof(int), cudaMemcpyHostToDevice));
+  XLS_CUDA(cudaMemcpy(gp.d_grp_n, gn.data(), gn.size() * sizeof(int), cudaMemcpyHostToDevice));
+  return XLS_OK;
+}
+
+// rewrite a plan's jobs for the grid's current split (stream-ordered on st)
+xls_status replan_gram(xls_grid g, int first, int n, GramPlan& gp, cudaStream_t st) {
+  std::vector<GramJob> jobs;
+  std::vector<int> gfirst, gn;
+  gram_jobs(g, first, n, g->gram_cps, jobs, gfirst, gn);
+  if ((int)jobs.size() > gp.cap_jobs || (int)gfirst.size() != gp.n_groups)
+    return fail(XLS_EINVAL, "Gram plan: split beyond the planned capacity");
+  gp.n_jobs = (int)jobs.size();
+  XLS_CUDA(cudaMemcpyAsync(gp.d_jobs, jobs.data(), jobs.size() * sizeof(GramJob), cudaMemcpyHostToDevice, st));
+  XLS_CUDA(cudaMemcpyAsync(gp.d_grp_first, gfirst.data(), gfirst.size() * sizeof(int), cudaMemcpyHostToDevice, st));
+  XLS_CUDA(cudaMemcpyAsync(gp.d_grp_n, gn.data(), gn.size() * sizeof(int), cudaMemcpyHostToDevice, st));
+  XLS_CUDA(cudaStreamSynchronize(st));   // the host vectors go out of scope
+  return XLS_OK;
+}
+
+// tensor-core Gram and rotation jobs of subdomains [first, first + n) (indices relative to
+// `first`); the exponent and split-Y arrays are indexed by state and shared with `shared`
+xls_status build_tc_plans(xls_grid g, int first, int n, GramPlan& gp, RotPlan& rp, const GramPlan* gshared,
+                          const RotPlan* rshared) {
+  XLS_TRY(alloc_gram_plan(g, first, n, gp));
   if (gshared) {
     gp.d_ex_f = gshared->d_ex_f;
     gp.d_ex_hf = gshared->d_ex_hf;
@@ -751,9 +789,6 @@ xls_status build_tc_plans(xls_grid g, int first, int n, GramPlan& gp, RotPlan& r
     XLS_TRY(g->alloc(&rp.d_ylo, (size_t)g->tot_states * rp.kpad_max * sizeof(uint16_t)));
     XLS_TRY(g->alloc(&rp.d_ex_y, g->tot_states * sizeof(int)));
   }
-  XLS_CUDA(cudaMemcpy(gp.d_jobs, jobs.data(), jobs.size() * sizeof(GramJob), cudaMemcpyHostToDevice));
-  XLS_CUDA(cudaMemcpy(gp.d_grp_first, gfirst.data(), gfirst.size() * sizeof(int), cudaMemcpyHostToDevice));
-  XLS_CUDA(cudaMemcpy(gp.d_grp_n, gn.data(), gn.size() * sizeof(int), cudaMemcpyHostToDevice));
   XLS_CUDA(cudaMemcpy(rp.d_jobs, rj.data(), rj.size() * sizeof(RotJob), cudaMemcpyHostToDevice));
   return XLS_OK;
 }
@@ -1210,34 +1245,8 @@ xls_status create_grid(const xls_cell* cell, const xls_dc* dc, int precision, si
     for (const SubDev& S : g->subs) ok = ok && S.ns <= 256 && S.nd % 8 == 0;
     if (ok) {
       // Gram jobs: upper block triangle of every subdomain, K split so that the grid fills the GPU
-      int groups = 0;
-      for (const SubDev& S : g->subs) {
-        const int nt = (S.ns + 127) / 128;
-        groups += nt * (nt + 1) / 2;
-      }
-      const int kchunks = std::max(1, (4 * 152 + groups - 1) / groups);
-      std::vector<GramJob> jobs;
-      std::vector<int> gfirst, gn;
-      for (int a = 0; a < g->n_sub; ++a) {
-        const SubDev& S = g->subs[a];
-        const int nt = (S.ns + 127) / 128;
-        const int nkt = (int)((S.nd + 63) / 64);
-        const int kc = std::min(kchunks, nkt);
-        for (int I = 0; I < nt; ++I)
-          for (int J = I; J < nt; ++J) {
-            gfirst.push_back((int)jobs.size());
-            for (int c = 0; c < kc; ++c)
-              jobs.push_back(GramJob{a, I, J, (int)((long long)nkt * c / kc), (int)((long long)nkt * (c + 1) / kc), 0});
-            gn.push_back(kc);
-          }
-      }
       GramPlan& gp = g->gplan;
-      gp.n_jobs = (int)jobs.size();
-      gp.n_groups = (int)gfirst.size();
-      if ((s = g->alloc(&gp.d_jobs, jobs.size() * sizeof(GramJob))) == XLS_OK &&
-          (s = g->alloc(&gp.d_grp_first, gfirst.size() * sizeof(int))) == XLS_OK &&
-          (s = g->alloc(&gp.d_grp_n, gn.size() * sizeof(int))) == XLS_OK)
-        s = g->alloc(&gp.d_work, jobs.size() * 2 * 128 * 128 * sizeof(float));
+      s = alloc_gram_plan(g, 0, g->n_sub, gp);
       if (s == XLS_OK) s = g->alloc(&gp.d_ex_f, g->tot_states * sizeof(int));
       if (s == XLS_OK) s = g->alloc(&gp.d_ex_hf, g->tot_states * sizeof(int));
       std::vector<RotJob> rj;
@@ -1254,9 +1263,6 @@ xls_status create_grid(const xls_cell* cell, const xls_dc* dc, int precision, si
         xls_grid_destroy(g);
         return s;
       }
-      cudaMemcpy(gp.d_jobs, jobs.data(), jobs.size() * sizeof(GramJob), cudaMemcpyHostToDevice);
-      cudaMemcpy(gp.d_grp_first, gfirst.data(), gfirst.size() * sizeof(int), cudaMemcpyHostToDevice);
-      cudaMemcpy(gp.d_grp_n, gn.data(), gn.size() * sizeof(int), cudaMemcpyHostToDevice);
       cudaMemcpy(rp.d_jobs, rj.data(), rj.size() * sizeof(RotJob), cudaMemcpyHostToDevice);
       g->use_tc = true;
       const char* eg = std::getenv("XLS_GEMM_GRAM");
@@ -1912,6 +1918,116 @@ xls_status xls_chefsi_batch(xls_grid g, int degree, int n_passes, const double* 
   if (!g->ham_set || !g->orb_set) return fail(XLS_EINVAL, "xls_chefsi_batch: Hamiltonian or orbitals not set");
   if (g->wave) return wave_chefsi(g, degree, n_passes, bounds);
   return g->prec == XLS_FP64 ? chefsi<double>(g, degree, n_passes, bounds) : chefsi<float>(g, degree, n_passes, bounds);
+}
+
+xls_status xls_autotune(xls_grid g, int reps, int* choices_out) {
+  if (!g || reps < 1 || reps > 100) return fail(XLS_EINVAL, "xls_autotune: bad arguments");
+  if (g->wave) return fail(XLS_EINVAL, "xls_autotune: not in wave mode");
+  if (!g->have_ritz) return fail(XLS_EINVAL, "xls_autotune: run a pass first (its subspace matrices are the input)");
+  XLS_TRY(check_status(g));
+  cudaStream_t st = g->st;
+  // the last projection's M_s, H_s and split exponents are saved and put back afterwards
+  const size_t ss = (size_t)g->tot_ss * sizeof(double);
+  const bool tc_gram = g->prec != XLS_FP64 && g->use_tc && g->use_tc_gram;
+  const size_t ex = tc_gram ? (size_t)g->tot_states * sizeof(int) : 0;
+  unsigned char* save = nullptr;
+  if (cudaMalloc((void**)&save, 2 * ss + 2 * ex) != cudaSuccess) {
+    cudaGetLastError();
+    return fail(XLS_ENOMEM, "xls_autotune: no room to save the subspace matrices");
+  }
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  xls_status rc = XLS_OK;
+  auto cuda_ok = [&](cudaError_t e) {
+    if (e != cudaSuccess && rc == XLS_OK) rc = fail(XLS_ECUDA, std::string("xls_autotune: ") + cudaGetErrorString(e));
+    return rc == XLS_OK;
+  };
+  cuda_ok(cudaMemcpyAsync(save, g->Ms, ss, cudaMemcpyDeviceToDevice, st));
+  cuda_ok(cudaMemcpyAsync(save + ss, g->Hs, ss, cudaMemcpyDeviceToDevice, st));
+  if (tc_gram) {
+    cuda_ok(cudaMemcpyAsync(save + 2 * ss, g->gplan.d_ex_f, ex, cudaMemcpyDeviceToDevice, st));
+    cuda_ok(cudaMemcpyAsync(save + 2 * ss + ex, g->gplan.d_ex_hf, ex, cudaMemcpyDeviceToDevice, st));
+  }
+  cuda_ok(cudaEventCreate(&e0));
+  cuda_ok(cudaEventCreate(&e1));
+  // mean time of `reps` calls after one warm-up call, CUDA events on the grid's stream
+  auto time_it = [&](const std::function<void()>& fn) -> float {
+    fn();
+    cudaEventRecord(e0, st);
+    for (int r = 0; r < reps; ++r) fn();
+    cudaEventRecord(e1, st);
+    float ms = -1.f;
+    if (!cuda_ok(cudaEventSynchronize(e1)) || !cuda_ok(cudaEventElapsedTime(&ms, e0, e1))) return -1.f;
+    const xls_status k = check_status(g);
+    if (k != XLS_OK && rc == XLS_OK) rc = k;
+    return rc == XLS_OK ? ms / reps : -1.f;
+  };
+  auto replan_all = [&]() {
+    if (rc == XLS_OK) rc = replan_gram(g, 0, g->n_sub, g->gplan, st);
+    g->full.gplan = g->gplan;
+    if (g->concurrent)
+      for (auto& h : g->halves)
+        if (rc == XLS_OK) rc = replan_gram(g, h.first, h.n, h.gplan, st);
+  };
+  // (1) cluster size of the Cholesky and the tridiagonalisation
+  if (rc == XLS_OK && g->eig_cluster) {
+    int best = g->eig_cl;
+    float bt = -1.f;
+    for (int cl : {8, 16}) {
+      g->eig_cl = cl;
+      const float t = time_it([&] { eigensolve(g, fv(g)); });
+      if (rc != XLS_OK) break;
+      if (bt < 0.f || t < bt) {
+        bt = t;
+        best = cl;
+      }
+    }
+    g->eig_cl = best;
+  }
+  // (2) K split of the tensor-core Gram
+  if (rc == XLS_OK && tc_gram) {
+    const int f = g->cur, hf = (g->cur + 1) % 3;
+    int best = g->gram_cps;
+    float bt = -1.f;
+    for (int cps : {1, 2, 3, 4, 6, 8}) {
+      g->gram_cps = cps;
+      replan_all();
+      if (rc != XLS_OK) break;
+      xls_grid_s::View& v = fv(g);
+      const float t = time_it([&] {
+        launch_gram_tc(v.ds, v.n, v.max_ns, v.gplan, g->prec == XLS_MIXED_FP16, (const float*)g->blk[f],
+                       (const float*)g->blk[hf], g->Ms, g->Hs, g->status, st);
+      });
+      if (rc != XLS_OK) break;
+      if (bt < 0.f || t < bt) {
+        bt = t;
+        best = cps;
+      }
+    }
+    g->gram_cps = best;
+    replan_all();
+  }
+  // the saved matrices and exponents back; eigenpairs of the last pass recomputed with the
+  // chosen configuration; passes captured with the old launch shapes dropped
+  cuda_ok(cudaMemcpyAsync(g->Ms, save, ss, cudaMemcpyDeviceToDevice, st));
+  cuda_ok(cudaMemcpyAsync(g->Hs, save + ss, ss, cudaMemcpyDeviceToDevice, st));
+  if (tc_gram) {
+    cuda_ok(cudaMemcpyAsync(g->gplan.d_ex_f, save + 2 * ss, ex, cudaMemcpyDeviceToDevice, st));
+    cuda_ok(cudaMemcpyAsync(g->gplan.d_ex_hf, save + 2 * ss + ex, ex, cudaMemcpyDeviceToDevice, st));
+  }
+  if (rc == XLS_OK) {
+    eigensolve(g, fv(g));
+    rc = check_status(g);
+  }
+  cudaStreamSynchronize(st);
+  g->drop_graphs();
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
+  cudaFree(save);
+  if (choices_out) {
+    choices_out[0] = g->eig_cluster ? g->eig_cl : 0;
+    choices_out[1] = tc_gram ? g->gram_cps : 0;
+  }
+  return rc;
 }
 
 xls_status xls_chefsi_stage(xls_grid g, int which, int degree, const double* bounds) {

@@ -88,6 +88,7 @@ struct GramJob {
 };
 struct GramPlan {
   int n_jobs = 0, n_groups = 0;
+  int cap_jobs = 0;            // job capacity of the device arrays (the finest K split tried)
   GramJob* d_jobs = nullptr;
   int* d_grp_first = nullptr;
   int* d_grp_n = nullptr;
@@ -185,8 +186,10 @@ void launch_fermi_occ(const double* lam, const double* c, int n_tot, double n_e,
 // ---- eigensolver (FP64) --------------------------------------------------------------------
 // L (in: M_s, out: Cholesky factor), A (in: H_s, out: reflectors), W (workspace/Z), Y (out),
 // R (cluster workspace), all n x n per subdomain; lam (out); vecs 8n per subdomain.
-bool launch_cholesky_cluster(const SubDev* d_subs, int n_sub, int max_ns, double* Ms, int* status, cudaStream_t st);
-bool launch_tridiag_cluster(const SubDev* d_subs, int n_sub, int max_ns, double* A, double* vecs, cudaStream_t st);
+bool launch_cholesky_cluster(const SubDev* d_subs, int n_sub, int max_ns, double* Ms, int* status, int cl_first,
+                             cudaStream_t st);
+bool launch_tridiag_cluster(const SubDev* d_subs, int n_sub, int max_ns, double* A, double* vecs, int cl_first,
+                            cudaStream_t st);
 // ---- learned start ---------------------------------------------------------------------------
 }  // namespace xls
 // model handle: FP32 master parameters, Adam moments and the training work arrays
@@ -240,7 +243,7 @@ void launch_pulay(long long n, int m, const double* dF, const double* dX, const 
 constexpr int kRedPartials = 296 * 4;  // doubles of a reduction's partial-sum buffer
 
 void launch_eig(const SubDev* d_subs, int n_sub, int max_ns, double* L, double* A, double* Y, double* W, double* lam,
-                double* vecs, int* status, double* scratch, double* R, bool cluster, cudaStream_t st);
+                double* vecs, int* status, double* scratch, double* R, int cluster, cudaStream_t st);
 size_t eig_scratch_doubles(int n_sub, int max_ns);
 
 // ---- small kernels -------------------------------------------------------------------------

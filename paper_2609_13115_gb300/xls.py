@@ -50,6 +50,7 @@ _SIGS = {
     "xls_orbitals_random": (c_int, [c_void_p, c_uint64]),
     "xls_orbitals_get": (c_int, [c_void_p, c_int, c_void_p, c_int]),
     "xls_orbitals_set_f32": (c_int, [c_void_p, c_int, c_void_p, c_int]),
+    "xls_autotune": (c_int, [c_void_p, c_int, c_void_p]),
     "xls_orbitals_get_f32": (c_int, [c_void_p, c_int, c_void_p, c_int]),
     "xls_chefsi_batch": (c_int, [c_void_p, c_int, c_int, c_void_p]),
     "xls_chefsi_stage": (c_int, [c_void_p, c_int, c_int, c_void_p]),
@@ -205,6 +206,14 @@ def xls_orbitals_get(g, sub, out):
 def xls_chefsi_batch(g, degree, n_passes, bounds=None):
     b = None if bounds is None else np.ascontiguousarray(bounds, dtype=np.float64).ravel()
     _check(load().xls_chefsi_batch(g, int(degree), int(n_passes), None if b is None else b.ctypes.data_as(c_void_p)))
+
+
+def xls_autotune(g, reps=5):
+    """Time the tunable launch configurations on the grid's data, keep the fastest; returns
+    (cluster CTAs of the factorisations, Gram CTAs per SM aimed at), 0 where not tuned."""
+    out = np.zeros(2, dtype=np.int32)
+    _check(load().xls_autotune(g, int(reps), out.ctypes.data_as(c_void_p)))
+    return int(out[0]), int(out[1])
 
 
 def xls_chefsi_stage(g, stage, degree, bounds=None):

@@ -804,6 +804,45 @@ def test_learned_start_trained_on_scf_densities():
 
 
 @pytest.mark.parametrize("prec", [xls.XLS_FP64, xls.XLS_MIXED_FP16])
+def test_autotune_keeps_results(prec):
+    """xls_autotune on the uneven subdomains picks configurations from its candidate sets, leaves
+    the subspace matrices of the last pass as they were, and the next pass of the tuned grid
+    (graph recaptured) gives the Ritz values, density, Fermi level and bounds of an untuned grid's
+    next pass to rounding."""
+    w = uneven_workload()
+    V = pseudo.local_potential(w)
+    subs = dc.partition(w)
+    psi0 = _start_blocks(w, subs)
+    res = {}
+    for mode in ("tuned", "plain"):
+        with make_grid(w, V, prec) as g:
+            for a in range(w.n_sub):
+                xls.xls_orbitals_set(g.h, a, psi0[a])
+            xls.xls_set_graphs(g.h, 1)
+            xls.xls_chefsi_batch(g.h, w.degree, 2)
+            if mode == "tuned":
+                before = [xls.xls_get_subspace(g.h, a, int(w.n_states[a])) for a in range(w.n_sub)]
+                cl, cps = xls.xls_autotune(g.h, 2)
+                assert cl in (8, 16), cl
+                assert cps in ((0,) if prec == xls.XLS_FP64 else (1, 2, 3, 4, 6, 8)), cps
+                for a in range(w.n_sub):
+                    ms, hs = xls.xls_get_subspace(g.h, a, int(w.n_states[a]))
+                    assert np.array_equal(ms, before[a][0]) and np.array_equal(hs, before[a][1])
+            xls.xls_chefsi_batch(g.h, w.degree, 1)
+            lam = [xls.xls_get_eigs(g.h, a, int(w.n_states[a]))[0] for a in range(w.n_sub)]
+            rho = np.zeros(int(np.prod(w.n)))
+            mu = xls.xls_density(g.h, w.n_electrons, w.kT, rho)[0]
+            bnd = xls.xls_get_bounds(g.h, w.n_sub)
+        res[mode] = (lam, rho, mu, bnd)
+    tol = 1e-9 if prec == xls.XLS_FP64 else 2e-5
+    for a in range(w.n_sub):
+        np.testing.assert_allclose(res["tuned"][0][a], res["plain"][0][a], rtol=0, atol=tol)
+    assert relerr(res["tuned"][1], res["plain"][1]) < 10 * tol
+    assert abs(res["tuned"][2] - res["plain"][2]) < tol
+    np.testing.assert_allclose(res["tuned"][3], res["plain"][3], rtol=tol, atol=tol)
+
+
+@pytest.mark.parametrize("prec", [xls.XLS_FP64, xls.XLS_MIXED_FP16])
 def test_concurrent_halves_match_sequential(prec, monkeypatch):
     """Passes whose two halves of subdomains run on two streams (XLS_CONCURRENT=1) give the Ritz
     values, weights, bounds and density of the single-stream pass; both with graph replay."""
