@@ -580,7 +580,9 @@ k_gram_reduce_single(const float* __restrict__ work, int ns, long long nd, int k
 }
 
 // ---------------------------------------------------------------------------------------------
-// Rotation: one CTA = (subdomain, tile of 128 grid points); K = N_s in tiles of 64
+// Rotation: one CTA = (subdomain, tile of 128 grid points, up to 256 output states from n0); K = N_s
+// in tiles of 64 (more than 256 states: one CTA per 256-state slice of the output, each reading the
+// tile of Psi_f again)
 // stage layout: A_hi 16K, A_lo 16K (MN-major), B_hi, B_lo (N rows x 128 bytes each, <= 32K each)
 constexpr uint32_t kRotStage = 2 * kTile + 2 * 256 * 128;
 
@@ -597,7 +599,8 @@ k_rotate_tc(const SubDev* __restrict__ subs, const RotJob* __restrict__ jobs, co
   const RotJob J = jobs[blockIdx.x];
   const SubDev& S = subs[J.sub];
   const int ns = S.ns;
-  const int n16 = (ns + 15) & ~15;
+  const int n0 = J.n0, nloc = min(256, ns - n0);   // output states n0 .. n0 + nloc - 1
+  const int n16 = (nloc + 15) & ~15;
   const int nkt = (ns + kKT - 1) / kKT;
   const long long g0 = (long long)J.tile * 128;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -653,8 +656,8 @@ k_rotate_tc(const SubDev* __restrict__ subs, const RotJob* __restrict__ jobs, co
         const int n = q >> 3, c = q & 7;
         yh[u] = make_uint4(0, 0, 0, 0);
         yl[u] = yh[u];
-        if (q < n16 * 8 && n < ns) {
-          const long long e = yoff + (long long)n * kpad_max + k0 + c * 8;
+        if (q < n16 * 8 && n < nloc) {
+          const long long e = yoff + (long long)(n0 + n) * kpad_max + k0 + c * 8;
           yh[u] = *reinterpret_cast<const uint4*>(Yhi + e);
           yl[u] = *reinterpret_cast<const uint4*>(Ylo + e);
         }
@@ -698,8 +701,8 @@ k_rotate_tc(const SubDev* __restrict__ subs, const RotJob* __restrict__ jobs, co
       if (ok && g < S.nd) {
 #pragma unroll
         for (int u = 0; u < 16; ++u)
-          if (c0 + u < ns)
-            o[(long long)(c0 + u) * S.nd + g] = kFp16 ? ldexpf(v[u], -ex_y[S.off_state + c0 + u]) : v[u];
+          if (c0 + u < nloc)
+            o[(long long)(n0 + c0 + u) * S.nd + g] = kFp16 ? ldexpf(v[u], -ex_y[S.off_state + n0 + c0 + u]) : v[u];
       }
     }
   } else if (lane == 0) {

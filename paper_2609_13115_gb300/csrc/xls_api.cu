@@ -776,7 +776,8 @@ xls_status build_tc_plans(xls_grid g, int first, int n, GramPlan& gp, RotPlan& r
   }
   std::vector<RotJob> rj;
   for (int a = first; a < first + n; ++a)
-    for (int t = 0; t < (int)((g->subs[a].nd + 127) / 128); ++t) rj.push_back(RotJob{a - first, t});
+    for (int t = 0; t < (int)((g->subs[a].nd + 127) / 128); ++t)
+      for (int n0 = 0; n0 < g->subs[a].ns; n0 += 256) rj.push_back(RotJob{a - first, t, n0});
   rp.n_jobs = (int)rj.size();
   rp.kpad_max = ((g->max_ns + 63) / 64) * 64;
   XLS_TRY(g->alloc(&rp.d_jobs, rj.size() * sizeof(RotJob)));
@@ -1242,7 +1243,7 @@ xls_status create_grid(const xls_cell* cell, const xls_dc* dc, int precision, si
   if (precision != XLS_FP64) {
     const char* env = std::getenv("XLS_GEMM");
     bool ok = !(env && std::string(env) == "simt") && tc_setup();
-    for (const SubDev& S : g->subs) ok = ok && S.ns <= 256 && S.nd % 8 == 0;
+    for (const SubDev& S : g->subs) ok = ok && S.ns <= 2048 && S.nd % 8 == 0;
     if (ok) {
       // Gram jobs: upper block triangle of every subdomain, K split so that the grid fills the GPU
       GramPlan& gp = g->gplan;
@@ -1251,7 +1252,8 @@ xls_status create_grid(const xls_cell* cell, const xls_dc* dc, int precision, si
       if (s == XLS_OK) s = g->alloc(&gp.d_ex_hf, g->tot_states * sizeof(int));
       std::vector<RotJob> rj;
       for (int a = 0; a < g->n_sub; ++a)
-        for (int t = 0; t < (int)((g->subs[a].nd + 127) / 128); ++t) rj.push_back(RotJob{a, t});
+        for (int t = 0; t < (int)((g->subs[a].nd + 127) / 128); ++t)
+          for (int n0 = 0; n0 < g->subs[a].ns; n0 += 256) rj.push_back(RotJob{a, t, n0});
       RotPlan& rp = g->rplan;
       rp.n_jobs = (int)rj.size();
       rp.kpad_max = ((g->max_ns + 63) / 64) * 64;

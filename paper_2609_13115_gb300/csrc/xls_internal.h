@@ -96,9 +96,10 @@ struct GramPlan {
   int* d_ex_f = nullptr;       // FP16 split: power-of-two exponent of every vector of F and HF
   int* d_ex_hf = nullptr;
 };
-// Tensor-core rotation: CTA jobs (subdomain, tile of 128 grid points)
+// Tensor-core rotation: CTA jobs (subdomain, tile of 128 grid points, first of up to 256 output
+// states)
 struct RotJob {
-  int sub, tile;
+  int sub, tile, n0;
 };
 struct RotPlan {
   int n_jobs = 0, kpad_max = 0;

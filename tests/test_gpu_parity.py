@@ -400,6 +400,44 @@ def test_tensor_core_gram_and_rotation_match_simt(monkeypatch, prec):
         assert np.linalg.norm(P_t.T @ (P_t @ P_s.T) - P_s.T) < 1e-3 * np.linalg.norm(P_s)
 
 
+def test_tensor_core_path_beyond_256_states(monkeypatch):
+    """272 states on the 8-atom cell: the Gram runs over 3 x 3 blocks of 128 and the rotation over
+    two output slices (256 + 16 states) per tile; M_s, H_s, Ritz values and the rotated block
+    agree with the FP32 SIMT kernels, and the eigensolver (shared-memory limits exceeded: global
+    work arrays for the inverse iteration and the back-transformation) matches LAPACK's
+    generalised eigenvalues of the M_s, H_s it was given."""
+    import scipy.linalg
+    w = synth.workload(0)
+    w.n_states = np.array([272])
+    V = pseudo.local_potential(w)
+    subs = dc.partition(w)
+    psi0 = _start_blocks(w, subs)
+    bounds = np.array([[70.0, 8.0, -0.4]])
+    res = {}
+    for mode in ("tc", "simt"):
+        if mode == "simt":
+            monkeypatch.setenv("XLS_GEMM", "simt")
+        else:
+            monkeypatch.delenv("XLS_GEMM", raising=False)
+        with make_grid(w, V, xls.XLS_MIXED_FP16) as g:
+            xls.xls_orbitals_set(g.h, 0, psi0[0])
+            xls.xls_chefsi_stage(g.h, 1, w.degree, bounds)
+            xls.xls_chefsi_stage(g.h, 2, w.degree)
+            Ms, Hs = xls.xls_get_subspace(g.h, 0, 272)
+            xls.xls_chefsi_stage(g.h, 3, w.degree)
+            xls.xls_chefsi_stage(g.h, 4, w.degree)
+            psi = xls.xls_orbitals_get(g.h, 0, np.zeros((272, subs[0].N)))
+            lam = xls.xls_get_eigs(g.h, 0, 272)[0]
+        res[mode] = (Ms, Hs, psi, lam)
+        ref = scipy.linalg.eigh(0.5 * (Hs + Hs.T), 0.5 * (Ms + Ms.T), eigvals_only=True)
+        np.testing.assert_allclose(lam, ref, rtol=0, atol=1e-8 * max(1.0, np.abs(ref).max()))
+    (Ms_t, Hs_t, P_t, lam_t), (Ms_s, Hs_s, P_s, lam_s) = res["tc"], res["simt"]
+    assert relerr(Ms_t, Ms_s) < 3e-6, relerr(Ms_t, Ms_s)
+    assert relerr(0.5 * (Hs_t + Hs_t.T), 0.5 * (Hs_s + Hs_s.T)) < 3e-6
+    np.testing.assert_allclose(lam_t, lam_s, atol=1e-4)
+    assert np.linalg.norm(P_t.T @ (P_t @ P_s.T) - P_s.T) < 1e-3 * np.linalg.norm(P_s)
+
+
 @pytest.mark.parametrize("prec", [xls.XLS_FP64, xls.XLS_MIXED_BF16])
 @pytest.mark.parametrize("on_torch_stream", [False, True])
 def test_graph_replay_matches_direct_launches(prec, on_torch_stream):
