@@ -147,10 +147,12 @@ def effective_potential(w, rho: np.ndarray, b: np.ndarray):
     return phi + vxc, phi, eps, vxc
 
 
-def step(w, st: SCFState, n_passes: int = 1):
+def step(w, st: SCFState, n_passes: int = 1, n_electrons: float | None = None):
     """One SCF step: V_eff[rho_in]; per subdomain the Lanczos bound b of the new operator and
     n_passes CheFSI passes (a, a0 from the previous Ritz values); mu, rho_out, energies; the
-    residual; mixing.  Returns (residual, energy, mu, rho_out) and advances the state."""
+    residual; mixing.  n_electrons defaults to the cell's valence count (another count leaves
+    the cell charged against the neutralising background of the G = 0 convention).  Returns
+    (residual, energy, mu, rho_out) and advances the state."""
     dV = float(np.prod(w.h))
     V, phi, eps, vxc = effective_potential(w, st.rho, st.b)
     subs = dc.partition(w)
@@ -165,7 +167,8 @@ def step(w, st: SCFState, n_passes: int = 1):
         lam.append(la)
         Psi.append(P)
         c.append(dc.interior_weights(P, s))
-    mu, rho_out, e_band, e_ent = dc.assemble(w, subs, lam, c, Psi, w.kT, w.n_electrons)
+    ne = w.n_electrons if n_electrons is None else float(n_electrons)
+    mu, rho_out, e_band, e_ent = dc.assemble(w, subs, lam, c, Psi, w.kT, ne)
     rho_in = st.rho
     e_xc = float((rho_in * eps).sum() * dV)
     energy = (e_band + e_xc - float((vxc * rho_in).sum() * dV) + 0.5 * float(((st.b - rho_in) * phi).sum() * dV)

@@ -849,13 +849,13 @@ int gram_single_pairs(int n_states) {
 
 bool launch_gram_tc_single(const float* F, const float* HF, long long n_points, int n_states, int kc, float* work,
                            double* Ms, double* Hs, int* status, cudaStream_t st) {
-  static int attr = -1;
-  if (attr < 0) {
-    attr = cudaFuncSetAttribute(tc::k_gram_tc_single, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                (int)gram_tc_smem()) == cudaSuccess ? 1 : 0;
+  // the attribute belongs to the current device: set it on every call (cheap, and no shared
+  // state between threads or devices)
+  if (cudaFuncSetAttribute(tc::k_gram_tc_single, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)gram_tc_smem()) !=
+      cudaSuccess) {
     cudaGetLastError();
+    return false;
   }
-  if (attr != 1) return false;
   const int pairs = gram_single_pairs(n_states);
   tc::k_gram_tc_single<<<pairs * kc, tc::kThreads, gram_tc_smem(), st>>>(F, HF, n_points, n_states, kc, work, status);
   dim3 grid(16, pairs);

@@ -57,6 +57,11 @@ extern "C" xls_status xls_gram_noalloc(const float* psi_f, const float* hpsi_f, 
     }
     base = g_scratch_ptr[dev];
   }
+  // an error left pending by earlier, unrelated work would otherwise be reported as this call's
+  e = cudaGetLastError();
+  if (e != cudaSuccess)
+    return err(XLS_ECUDA, std::string("xls_gram_noalloc: a CUDA error was pending before the call: ") +
+                              cudaGetErrorString(e));
   cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
   int* status = reinterpret_cast<int*>(base);
   float* work = base + kStatusFloats;

@@ -426,10 +426,24 @@ def xls_get_kernel_times(g):
 def xls_gram_noalloc(psi_f, hpsi_f, Ms_out, Hs_out, stream=None):
     """Allocation-free Gram of one block (see include/xls.h): psi_f, hpsi_f are contiguous CUDA
     float32 tensors of shape (n_states, n_points); Ms_out, Hs_out CUDA float64 (n_states, n_states)."""
+    import torch
     for t in (psi_f, hpsi_f, Ms_out, Hs_out):
-        if not (hasattr(t, "is_cuda") and t.is_cuda and t.is_contiguous()):
+        if not (isinstance(t, torch.Tensor) and t.is_cuda and t.is_contiguous()):
             raise ValueError("xls_gram_noalloc takes contiguous CUDA tensors")
+    if psi_f.dtype != torch.float32 or hpsi_f.dtype != torch.float32:
+        raise TypeError("xls_gram_noalloc: psi_f and hpsi_f must be float32")
+    if Ms_out.dtype != torch.float64 or Hs_out.dtype != torch.float64:
+        raise TypeError("xls_gram_noalloc: Ms_out and Hs_out must be float64")
+    if psi_f.dim() != 2 or tuple(hpsi_f.shape) != tuple(psi_f.shape):
+        raise ValueError("xls_gram_noalloc: psi_f and hpsi_f must both be (n_states, n_points)")
     ns, nd = psi_f.shape
+    if tuple(Ms_out.shape) != (ns, ns) or tuple(Hs_out.shape) != (ns, ns):
+        raise ValueError(f"xls_gram_noalloc: Ms_out and Hs_out must be ({ns}, {ns})")
+    dev = torch.cuda.current_device()
+    if any(t.device.index != dev for t in (psi_f, hpsi_f, Ms_out, Hs_out)):
+        raise ValueError("xls_gram_noalloc: every tensor must be on the current CUDA device")
+    if stream is None:   # ordered after the torch work that produced the inputs
+        stream = torch.cuda.current_stream().cuda_stream
     _check(load().xls_gram_noalloc(c_void_p(psi_f.data_ptr()), c_void_p(hpsi_f.data_ptr()), int(nd), int(ns),
                                    c_void_p(Ms_out.data_ptr()), c_void_p(Hs_out.data_ptr()),
                                    c_void_p(stream) if stream else None))

@@ -3,6 +3,7 @@ continuity and the potential as the derivative of the energy density; the ion se
 against numerical quadrature; the Kerker preconditioner against the real-space FD operator;
 Pulay mixing against its exactness on linear fixed-point maps."""
 import math
+import os
 
 import numpy as np
 import pytest
@@ -15,26 +16,84 @@ def rho_of_rs(rs):
     return 3.0 / (4.0 * math.pi * np.asarray(rs, dtype=np.float64) ** 3)
 
 
-def test_slater_exchange_closed_form():
-    """eps_x = -(3/(4 pi)) (9 pi / 4)^(1/3) / r_s for the uniform gas (the textbook form in r_s)."""
-    rs = np.array([0.3, 0.9, 1.0, 2.0, 5.0, 12.0])
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden", "lda_limits.txt")
+
+
+def golden_limits():
+    """name -> (value, kind, tolerance) from tests/golden/lda_limits.txt."""
+    out = {}
+    for line in open(GOLDEN):
+        line = line.split("#")[0].strip()
+        if not line:
+            continue
+        name, rest = line.split(":")
+        val, kind, tol = rest.split()
+        out[name.strip()] = (float(val), kind, float(tol))
+    return out
+
+
+def check_golden(name, got):
+    val, kind, tol = golden_limits()[name]
+    bound = tol * abs(val) if kind == "rel" else tol
+    assert abs(got - val) <= bound, f"{name}: {got} vs {val} (tolerance {bound})"
+
+
+SLATER = (3.0 / (4.0 * math.pi)) * (9.0 * math.pi / 4.0) ** (1.0 / 3.0)   # 0.458165...
+
+
+def eps_c(rs):
+    """Correlation energy per electron of the oracle's LDA: eps_xc minus the exchange closed form."""
+    rs = np.asarray(rs, dtype=np.float64)
     eps, _ = scf.lda_pz81(rho_of_rs(rs))
-    ec = np.where(rs >= 1.0, scf.PZ_GAMMA / (1.0 + scf.PZ_BETA1 * np.sqrt(rs) + scf.PZ_BETA2 * rs),
-                  scf.PZ_A * np.log(rs) + scf.PZ_B + scf.PZ_C * rs * np.log(rs) + scf.PZ_D * rs)
-    ex = eps - ec
-    np.testing.assert_allclose(ex * rs, -(3.0 / (4.0 * math.pi)) * (9.0 * math.pi / 4.0) ** (1.0 / 3.0), rtol=1e-13)
+    return eps + SLATER / rs
+
+
+def test_slater_exchange_high_density_limit():
+    """r_s eps_xc -> -(3/(4 pi)) (9 pi / 4)^(1/3) as r_s -> 0, where the logarithmic correlation
+    energy is negligible against the 1/r_s exchange: pins the exchange without the correlation."""
+    rs = np.array([1e-10, 1e-9, 1e-8])
+    eps, _ = scf.lda_pz81(rho_of_rs(rs))
+    np.testing.assert_allclose(eps * rs, -SLATER, rtol=1e-7)
     # known value of the exchange constant, 0.458165...
-    assert abs((3.0 / (4.0 * math.pi)) * (9.0 * math.pi / 4.0) ** (1.0 / 3.0) - 0.4581652932831429) < 1e-15
+    assert abs(SLATER - 0.4581652932831429) < 1e-15
 
 
-def test_pz81_correlation_joins_at_rs_one():
-    """The two branches of the Perdew-Zunger fit meet at r_s = 1 (value to 1e-4 Ha, the fit's
-    own matching accuracy) and the potential has no jump larger than that either."""
-    lo, hi = rho_of_rs(1.0 - 1e-9), rho_of_rs(1.0 + 1e-9)
-    e_lo, v_lo = scf.lda_pz81(np.array([lo]))
-    e_hi, v_hi = scf.lda_pz81(np.array([hi]))
-    assert abs(e_lo[0] - e_hi[0]) < 1e-4
-    assert abs(v_lo[0] - v_hi[0]) < 2e-3
+def test_pz81_high_density_expansion():
+    """Slope of eps_c against ln r_s at r_s -> 0 is the exact (1 - ln 2)/pi^2; the constant term
+    is Gell-Mann and Brueckner's (both from the oracle's function values, not its constants)."""
+    r1, r2 = 1e-7, 1e-6
+    e1, e2 = eps_c([r1, r2])
+    slope = (e2 - e1) / (math.log(r2) - math.log(r1))
+    check_golden("hd_log_coefficient", slope)
+    assert abs(slope - (1.0 - math.log(2.0)) / math.pi ** 2) < 1e-3 * slope
+    check_golden("hd_constant", e1 - slope * math.log(r1))
+
+
+def test_pz81_correlation_joins_smoothly_at_rs_one():
+    """The two branches of the Perdew-Zunger fit meet at r_s = 1 in value and in slope (C and D
+    are defined by that), within the precision of the printed constants; a wrong C or D by 1e-3
+    breaks one of the two."""
+    e_lo, e_hi = eps_c([1.0 - 1e-12, 1.0 + 1e-12])
+    check_golden("join_value", e_hi - e_lo)
+    d = 1e-6
+    lo = eps_c([1.0 - 2 * d, 1.0 - d])        # one-sided slopes inside each branch
+    hi = eps_c([1.0 + d, 1.0 + 2 * d])
+    check_golden("join_slope", (hi[1] - hi[0]) / d - (lo[1] - lo[0]) / d)
+    # and the potential has no jump larger than the slope mismatch allows
+    _, v_lo = scf.lda_pz81(np.array([rho_of_rs(1.0 - 1e-9)]))
+    _, v_hi = scf.lda_pz81(np.array([rho_of_rs(1.0 + 1e-9)]))
+    assert abs(v_lo[0] - v_hi[0]) < 1e-4
+
+
+def test_pz81_low_density_wigner_limit():
+    """r_s eps_c = L + C r_s^-1/2 + O(1/r_s) at r_s -> infinity, against the Wigner-crystal
+    energy minus exchange."""
+    r1, r2 = 1e8, 4e8
+    y1, y2 = eps_c([r1, r2]) * np.array([r1, r2])
+    C = (y1 - y2) / (r1 ** -0.5 - r2 ** -0.5)
+    L = y1 - C * r1 ** -0.5
+    check_golden("ld_inverse_rs", L)
+    check_golden("ld_inverse_rs_three_halves", C)
 
 
 @pytest.mark.parametrize("rs", [0.2, 0.6, 0.95, 1.05, 2.0, 4.0, 10.0])
@@ -112,3 +171,45 @@ def test_periodic_pulay_alternates_linear_and_extrapolated_steps():
     np.testing.assert_allclose(x1, x0 + 0.3 * (A @ x0 + c - x0), rtol=1e-14)
     x2 = m.step(x1, A @ x1 + c)          # k = 1: extrapolated
     assert np.linalg.norm(x2 - (x1 + 0.3 * (A @ x1 + c - x1))) > 1e-6
+
+
+def _si2_cell():
+    """Two displaced Si atoms in a cubic 8.55 bohr cell (20^3 points, h = 0.4275 bohr), 10 states."""
+    a = 8.55
+    pos = np.array([[0.3, 0.2, 0.1], [2.1375 + 0.3, 2.1375 + 0.1, 2.1375 - 0.2]])
+    return synth.Workload("si2_20cube", (a, a, a), (20, 20, 20), pos, np.zeros(2, int), [synth.SI],
+                          core_lo=np.zeros((1, 3), int), core_n=np.full((1, 3), 20), buf=np.zeros((1, 3), int),
+                          n_states=np.array([10]), degree=16, n_passes=1, psi_seed=1000)
+
+
+def _converged_scf(w, n_electrons, tol=1e-10, max_steps=80):
+    """(free energy, mu) of the oracle's SCF run to a density residual below tol."""
+    from oracle import dc
+    b = pseudo.pseudocharge(w)
+    n_pts = int(np.prod(w.n))
+    dV = float(np.prod(w.h))
+    rho0 = (w.n_electrons / (n_pts * dV) - b) * (n_electrons / w.n_electrons)
+    sub = dc.partition(w)[0]
+    st = scf.start(w, rho0, [synth.psi0_block(w.psi_seed, sub.N, int(w.n_states[0]))])
+    for k in range(max_steps):
+        res, energy, mu, _ = scf.step(w, st, n_passes=2 if k == 0 else 1, n_electrons=n_electrons)
+        if res < tol:
+            return energy, mu
+    raise AssertionError(f"SCF did not reach {tol} (last residual {res:.2e})")
+
+
+@pytest.mark.slow
+def test_scf_energy_derivative_is_chemical_potential():
+    """Janak's theorem for the Mermin free energy: at self-consistency dF/dN = mu.  The SCF
+    energy assembly (E_band + E_xc - sum v_xc rho + 1/2 sum (b - rho) phi - E_self - E_entropy)
+    is pinned by F(N + d) - F(N - d) = integral of mu dN (Simpson's rule over three converged
+    runs) on a cell with a partly filled level (7 electrons, 8 valence), where mu(N) is smooth.
+    A flipped entropy or Hartree sign, or a dropped -sum v_xc rho term, moves the difference by
+    more than 1e-3 Ha; the pin holds to 1e-8."""
+    w = _si2_cell()
+    N, d = 7.0, 0.1
+    F_m, mu_m = _converged_scf(w, N - d)
+    _, mu_0 = _converged_scf(w, N)
+    F_p, mu_p = _converged_scf(w, N + d)
+    assert abs((F_p - F_m) - d / 3.0 * (mu_m + 4.0 * mu_0 + mu_p)) < 1e-7
+    assert abs(F_p - F_m) > 1e-3          # a non-trivial energy change

@@ -1,4 +1,5 @@
-"""The allocation-free Gram entry point (xls_gram_noalloc) against the library's regular Gram.
+"""The allocation-free Gram entry point (xls_gram_noalloc) against the library's regular Gram
+and against the oracle's projection (Sec. 5.A.3 step (2)) of the same block.
 
 Callers that cannot let a library allocate device memory (applications whose device memory
 belongs to their own pool allocator, latency-critical loops that cannot take cudaMalloc's
@@ -12,7 +13,7 @@ import numpy as np
 import pytest
 
 import synth
-from oracle import dc, pseudo
+from oracle import chefsi, dc, pseudo
 from paper_2609_13115_gb300 import xls
 
 pytestmark = pytest.mark.gpu
@@ -70,3 +71,53 @@ def test_gram_noalloc_rejects_oversized_block():
     with pytest.raises(xls.XlsError) as e:
         xls.xls_gram_noalloc(F, F, M, M)
     assert e.value.status == xls.XLS_EINVAL
+
+
+class _DiagonalOperator:
+    """H = diag(d): H Psi_f scales every grid value, so F (H F)^T is symmetric like the pass's."""
+
+    def __init__(self, d):
+        self.d = d
+        self.N = d.size
+
+    def apply(self, X):
+        return X * self.d[None, :]
+
+
+@pytest.mark.parametrize("n_states", [200, 256])
+def test_gram_noalloc_two_blocks_ragged_tail_matches_oracle(n_states):
+    """Two 128-state blocks (three block pairs, 21 K chunks of uneven length) and a ragged last
+    K tile (n_points = 64 m + 8), against the oracle's FP64 projection of the same FP32 block;
+    two calls in a row (the second on a shorter block) share the fixed scratch."""
+    import torch
+    xls.load()
+    n_points = 64 * 300 + 8
+    F = synth.uniform_pm_half(4242 + n_states, n_states * n_points).reshape(n_states, n_points)
+    F = F.astype(np.float32).astype(np.float64)               # the FP32 block both sides see
+    d = (1.0 + synth.uniform_pm_half(77, n_points)).astype(np.float32).astype(np.float64)
+    H = _DiagonalOperator(d)
+    HF = H.apply(F).astype(np.float32).astype(np.float64)
+    Ms_o, Hs_o = chefsi.projection(H, F)     # FP64 (the FP32 rounding of HF is far below the bound)
+    Ft = torch.tensor(F, dtype=torch.float32, device="cuda")
+    HFt = torch.tensor(HF, dtype=torch.float32, device="cuda")
+    for rows in (n_states, n_states - 72):                    # second call: one block + a partial one
+        Ms = torch.full((rows, rows), float("nan"), dtype=torch.float64, device="cuda")
+        Hs = torch.full_like(Ms, float("nan"))
+        xls.xls_gram_noalloc(Ft[:rows].contiguous(), HFt[:rows].contiguous(), Ms, Hs)
+        torch.cuda.synchronize()
+        # split-BF16 products (about 16 significant bits per operand) summed in FP32 partial sums
+        assert _relerr(Ms.cpu().numpy(), Ms_o[:rows, :rows]) < 2e-5
+        assert _relerr(Hs.cpu().numpy(), Hs_o[:rows, :rows]) < 2e-5
+
+
+def test_gram_noalloc_checks_tensor_arguments():
+    import torch
+    xls.load()
+    F = torch.zeros((16, 64), dtype=torch.float32, device="cuda")
+    M = torch.zeros((16, 16), dtype=torch.float64, device="cuda")
+    with pytest.raises(TypeError):
+        xls.xls_gram_noalloc(F, F, M.float(), M)
+    with pytest.raises(ValueError):
+        xls.xls_gram_noalloc(F, F[:8].contiguous(), M, M)
+    with pytest.raises(ValueError):
+        xls.xls_gram_noalloc(F, F, M[:8, :8].contiguous(), M)
