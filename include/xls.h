@@ -177,6 +177,11 @@ xls_status xls_dos(xls_grid g, const double* energies, int n_energies, double wi
 /* Read back M_s and H_s (N_s x N_s, row-major) of subdomain `sub` from the last projection. */
 xls_status xls_get_subspace(xls_grid g, int sub, double* Ms_out, double* Hs_out);
 
+/* Read back the N_s x N_s rotation Y of subdomain `sub` from the last generalised eigensolve
+ * (row-major; the rotated block is psi_n = sum_k Y[k][n] psi_f,k, Sec. 5.A.3 step (4): Psi = Psi_f Y).
+ * Test/readback helper; XLS_EINVAL in wave mode. */
+xls_status xls_get_rotation(xls_grid g, int sub, double* Y_out);
+
 /* Read back the (b, a, a0) filter bounds the next pass will use, [3*n_sub]. */
 xls_status xls_get_bounds(xls_grid g, double* bounds_out);
 

@@ -2188,6 +2188,15 @@ xls_status xls_get_subspace(xls_grid g, int sub, double* Ms_out, double* Hs_out)
   return XLS_OK;
 }
 
+xls_status xls_get_rotation(xls_grid g, int sub, double* Y_out) {
+  if (!g || !Y_out || sub < 0 || sub >= g->n_sub) return fail(XLS_EINVAL, "xls_get_rotation: bad arguments");
+  if (g->wave) return not_in_wave_mode("xls_get_rotation");
+  const SubDev& S = g->subs[sub];
+  XLS_CUDA(cudaStreamSynchronize(g->st));
+  XLS_CUDA(cudaMemcpy(Y_out, g->Y + S.off_ss, (size_t)S.ns * S.ns * sizeof(double), cudaMemcpyDeviceToHost));
+  return XLS_OK;
+}
+
 xls_status xls_get_bounds(xls_grid g, double* bounds_out) {
   if (!g || !bounds_out) return fail(XLS_EINVAL, "xls_get_bounds: bad arguments");
   if (g->wave) {

@@ -59,6 +59,7 @@ _SIGS = {
                             POINTER(c_double), POINTER(c_double)]),
     "xls_get_eigs": (c_int, [c_void_p, c_int, c_void_p, c_void_p]),
     "xls_get_subspace": (c_int, [c_void_p, c_int, c_void_p, c_void_p]),
+    "xls_get_rotation": (c_int, [c_void_p, c_int, c_void_p]),
     "xls_dos": (c_int, [c_void_p, c_void_p, c_int, c_double, c_void_p]),
     "xls_scf_cg_iterations": (c_int, [c_void_p, c_void_p]),
     "xls_wave_store_fp16": (c_int, [c_void_p, c_int]),
@@ -268,6 +269,12 @@ def xls_get_subspace(g, sub, n_states):
     Hs = np.zeros((n_states, n_states))
     _check(load().xls_get_subspace(g, int(sub), Ms.ctypes.data_as(c_void_p), Hs.ctypes.data_as(c_void_p)))
     return Ms, Hs
+
+
+def xls_get_rotation(g, sub, n_states):
+    Y = np.zeros((n_states, n_states))
+    _check(load().xls_get_rotation(g, int(sub), Y.ctypes.data_as(c_void_p)))
+    return Y
 
 
 def xls_get_bounds(g, n_sub):

@@ -1,0 +1,192 @@
+"""Parity with the FP64 oracle at the sizes the benchmark runs (the 64-atom cell: 8 periodic
+subdomains of 48^3, 160 states, degree 20), in the launch configuration the benchmark times
+(all eight subdomains in the same launches).
+
+* Tensor-core Gram and rotation (Sec. 5.A.3 steps (2) and (4)) at 160 and 272 states: M_s and
+  H_s against the oracle's projection of the same filtered block, the rotated block against the
+  oracle's product of that block with the library's own Y, the Ritz values against LAPACK.
+* One full pass of subdomain 0 with all 160 vectors against the oracle's pass (FP64: Ritz
+  values to 1e-8 Ha; mixed: occupied Ritz values), and the interior weights and core density of
+  that subdomain at the library's Fermi level.
+* Ten passes of the mixed path against ten of the FP64 path from the same start (the FP64 path
+  being pinned to the oracle by the one-pass comparison): energy per atom to 1e-5 Ha, density to
+  1e-4 relative L2.
+* Two SCF steps of the eight-subdomain Dirichlet cell against the oracle's SCF steps.
+
+The tolerances of the split products: each operand is carried as hi + lo 16-bit halves, and the
+dropped lo*lo term bounds the error of a product at 2^-16 (BF16) or 2^-22 (FP16, with per-vector
+power-of-two scaling) of |a||b|; FP32 accumulation in tensor memory adds a few units of 2^-24 per
+flush.  The Gram bounds below are relative (Frobenius) errors, the rotation bound is elementwise
+relative to sum_k |Y_kn| |psi_f,k(g)|.
+"""
+import numpy as np
+import pytest
+import scipy.linalg
+
+import synth
+from oracle import chefsi, dc, fermi, pseudo, scf
+from paper_2609_13115_gb300 import xls
+
+pytestmark = pytest.mark.gpu
+
+GRAM_TOL = {xls.XLS_MIXED_BF16: 3e-5, xls.XLS_MIXED_FP16: 3e-6}
+ROT_TOL = {xls.XLS_MIXED_BF16: 6e-5, xls.XLS_MIXED_FP16: 6e-6}
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    import os
+    from paper_2609_13115_gb300 import build
+    if not os.path.exists(xls.LIB_PATH):
+        build.build()
+    xls.load()
+
+
+@pytest.fixture(scope="module")
+def bench():
+    """The benchmark's workload, its stand-in potential and the oracle's operator of subdomains
+    0 and 5."""
+    w = synth.workload(1)
+    V = synth.veff_erf_wells(w)
+    subs = dc.partition(w)
+    norms = pseudo.projector_norms(w)
+    ops = {a: dc.subdomain_operator(w, subs[a], V, norms) for a in (0, 5)}
+    return w, V, subs, ops
+
+
+def relerr(a, b):
+    return float(np.linalg.norm(a - b) / np.linalg.norm(b))
+
+
+def make_grid(w, V, precision):
+    g = xls.Grid(w, precision)
+    g.set_hamiltonian(V)
+    return g
+
+
+@pytest.mark.parametrize("n_states", [160, 272])
+@pytest.mark.parametrize("prec", [xls.XLS_MIXED_FP16, xls.XLS_MIXED_BF16])
+def test_tensor_core_gram_and_rotation_at_bench_size(bench, prec, n_states):
+    w0, V, subs, ops = bench
+    w = synth.workload(1)
+    w.n_states = np.full(w.n_sub, n_states)
+    bounds = np.array([[70.0, 1.0, -1.0]] * w.n_sub)
+    with make_grid(w, V, prec) as g:
+        xls.xls_orbitals_random(g.h, w.psi_seed)
+        xls.xls_chefsi_stage(g.h, 1, w.degree, bounds)          # filter: the block becomes Psi_f
+        F = {a: xls.xls_orbitals_get(g.h, a, np.zeros((n_states, subs[a].N))) for a in ops}
+        xls.xls_chefsi_stage(g.h, 2, w.degree)                  # Gram: M_s, H_s
+        MH = {a: xls.xls_get_subspace(g.h, a, n_states) for a in ops}
+        xls.xls_chefsi_stage(g.h, 3, w.degree)                  # eigensolve: Y, lambda
+        Y = {a: xls.xls_get_rotation(g.h, a, n_states) for a in ops}
+        lam = {a: xls.xls_get_eigs(g.h, a, n_states)[0] for a in ops}
+        xls.xls_chefsi_stage(g.h, 4, w.degree)                  # rotation: Psi = Psi_f Y
+        P = {a: xls.xls_orbitals_get(g.h, a, np.zeros((n_states, subs[a].N))) for a in ops}
+    for a, H in ops.items():
+        Ms_o, Hs_o = chefsi.projection(H, F[a])
+        Ms, Hs = MH[a]
+        assert relerr(Ms, Ms_o) < GRAM_TOL[prec], (a, relerr(Ms, Ms_o))
+        assert relerr(0.5 * (Hs + Hs.T), Hs_o) < GRAM_TOL[prec], (a, relerr(0.5 * (Hs + Hs.T), Hs_o))
+        ref = scipy.linalg.eigh(0.5 * (Hs + Hs.T), 0.5 * (Ms + Ms.T), eigvals_only=True)
+        np.testing.assert_allclose(lam[a], ref, rtol=0, atol=1e-8 * max(1.0, np.abs(ref).max()))
+        P_o = chefsi.rotate(F[a], Y[a])
+        scale = np.abs(Y[a]).T @ np.abs(F[a])
+        err = float(np.max(np.abs(P[a] - P_o) / scale))
+        assert err < ROT_TOL[prec], (a, err)
+
+
+def _start(w, subs):
+    offs = synth.psi0_offsets(w)
+    return [synth.psi0_block(w.psi_seed, subs[a].N, int(w.n_states[a]), offs[a]) for a in range(w.n_sub)]
+
+
+def _core_density(w, s, P, lam, mu):
+    dV = float(np.prod(w.h))
+    return fermi.point_density(P[:, dc.core_local_indices(s)], fermi.occupations(lam, mu, w.kT), dV)
+
+
+@pytest.mark.parametrize("prec", [xls.XLS_FP64, xls.XLS_MIXED_FP16])
+def test_full_pass_of_bench_subdomain_matches_oracle(bench, prec):
+    """One pass (Lanczos bound, Rayleigh-Ritz of the start block for (a, a0), filter, projection,
+    eigensolve, rotation, interior weights) of subdomain 0 with all 160 vectors from the
+    SplitMix64 start, on the full eight-subdomain grid; then the Fermi level of all subdomains on
+    the GPU and subdomain 0's interior weights and core density at that level."""
+    w, V, subs, ops = bench
+    ns = int(w.n_states[0])
+    with make_grid(w, V, prec) as g:
+        xls.xls_orbitals_random(g.h, w.psi_seed)
+        xls.xls_chefsi_batch(g.h, w.degree, 1)
+        lam_g, c_g = xls.xls_get_eigs(g.h, 0, ns)
+        rho = np.zeros(int(np.prod(w.n)))
+        mu, _, _ = xls.xls_density(g.h, w.n_electrons, w.kT, rho)
+    ref = dc.run(w, V, [_start(w, subs)[0]], n_passes=1, subdomains=[0])
+    lam_o, P_o = ref.lam[0], ref.Psi[0]
+    if prec == xls.XLS_FP64:
+        np.testing.assert_allclose(lam_g, lam_o, rtol=0, atol=1e-8)
+    else:
+        occ = lam_o < mu + 0.1
+        np.testing.assert_allclose(lam_g[occ], lam_o[occ], rtol=0, atol=1e-4)
+    # weights summed over clusters of (near-)degenerate levels, and the core density at the
+    # library's mu (a global quantity of all eight subdomains)
+    c_o = dc.interior_weights(P_o, subs[0])
+    tol_c = 1e-7 if prec == xls.XLS_FP64 else 1e-4
+    occ = lam_o < mu + 0.1
+    assert abs(np.sum(c_g[occ]) - np.sum(c_o[occ])) < tol_c * np.sum(c_o[occ])
+    rho_o = _core_density(w, subs[0], P_o, lam_o, mu)
+    rho_g = rho[dc.core_global_indices(subs[0], np.asarray(w.n))]
+    assert relerr(rho_g, rho_o) < (1e-7 if prec == xls.XLS_FP64 else 1e-4)
+
+
+def test_mixed_matches_fp64_after_ten_passes_at_bench_size(bench):
+    """The benchmark's energy comparison with the FP64 side pinned: ten passes of the split-FP16
+    path and of the FP64 path from the same SplitMix64 start; band energy minus entropy term per
+    atom to 1e-5 Ha and the density to 1e-4 relative L2."""
+    w, V, subs, ops = bench
+    out = {}
+    for prec in (xls.XLS_FP64, xls.XLS_MIXED_FP16):
+        with make_grid(w, V, prec) as g:
+            xls.xls_orbitals_random(g.h, w.psi_seed)
+            xls.xls_chefsi_batch(g.h, w.degree, 10)
+            rho = np.zeros(int(np.prod(w.n)))
+            mu, eb, es = xls.xls_density(g.h, w.n_electrons, w.kT, rho)
+        out[prec] = (mu, eb - es, rho)
+    n_at = len(w.pos)
+    (mu64, e64, r64), (mum, em, rm) = out[xls.XLS_FP64], out[xls.XLS_MIXED_FP16]
+    assert abs(em - e64) / n_at < 1e-5
+    assert relerr(rm, r64) < 1e-4
+    assert abs(mum - mu64) < 1e-4
+
+
+def _dirichlet_cell():
+    """The 8-atom cell cut into eight 18^3 subdomains with Dirichlet buffers of 3 points, 16 states."""
+    w = synth.workload(0)
+    cores = np.array([(i, j, k) for k in (0, 12) for j in (0, 12) for i in (0, 12)])
+    return synth.Workload("si8_dc8_dirichlet", w.L, w.n, synth.displace(w.pos, 0.05, 77, w.L), w.species_index,
+                          w.species, core_lo=cores, core_n=np.full((8, 3), 12), buf=np.full((8, 3), 3),
+                          n_states=np.full(8, 16), degree=10, n_passes=3, psi_seed=55)
+
+
+def test_dc_scf_steps_match_oracle():
+    """Three SCF steps of the divide-and-conquer solver (eight Dirichlet subdomains: restriction
+    of every new V_eff, per-subdomain Lanczos bounds and passes, the Fermi level over all
+    subdomains, each core's density from its own subdomain, Pulay + Kerker mixing) against the
+    oracle's steps from the same start density and blocks, FP64."""
+    w = _dirichlet_cell()
+    subs = dc.partition(w)
+    psi0 = [synth.psi0_block(w.psi_seed + a, subs[a].N, int(w.n_states[a])) for a in range(w.n_sub)]
+    b = pseudo.pseudocharge(w)
+    rho0 = w.n_electrons / (int(np.prod(w.n)) * float(np.prod(w.h))) - b
+    st = scf.start(w, rho0, psi0)
+    ref = [scf.step(w, st) for _ in range(3)]
+    with make_grid(w, pseudo.local_potential(w), xls.XLS_FP64) as g:
+        for a in range(w.n_sub):
+            xls.xls_orbitals_set(g.h, a, psi0[a])
+        xls.xls_scf_setup(g.h, w.n_electrons, w.kT, w.degree)
+        rho = np.ascontiguousarray(rho0.astype(np.float64))
+        out = [xls.xls_scf_step(g.h, rho) for _ in range(3)]
+    n_at = len(w.pos)
+    for k, ((r_o, e_o, mu_o, _), (r_g, e_g, mu_g)) in enumerate(zip(ref, out)):
+        assert abs(e_g - e_o) < 1e-8 * n_at, (k, e_g, e_o)
+        assert abs(mu_g - mu_o) < 1e-8, (k, mu_g, mu_o)
+        assert abs(r_g - r_o) < 1e-6 * r_o, (k, r_g, r_o)
+    assert relerr(rho, st.rho) < 1e-7
