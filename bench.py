@@ -1,16 +1,21 @@
 #!/usr/bin/env python
 """Benchmark of the divide-and-conquer CheFSI pass on GB300.
 
-Workload (default): 64-atom Si (2x2x2 conventional cells, seeded displacements sigma = 0.05 bohr),
-global 48^3 grid (h = 0.4275 bohr), 8 subdomains with 1-cell cores and 0.5-cell buffers (48^3
-points each, periodic because the buffer covers the cell), 160 states per subdomain (the state
-count that holds the subdomain's electrons, 1.2 x N_e/2 rounded up to 16), Chebyshev degree 20.
-V_eff is the seeded stand-in potential of `synth` (erf-Coulomb wells).  One step = one full
-CheFSI pass over all subdomains (filter, projection, eigensolve, rotation, interior weights)
-followed by the Fermi level, energies and the density on the global grid.
+Workload (default, `--workload si13824`): the precision-at-scale cell, 13,824 Si atoms (12^3
+conventional cells, seeded displacements sigma = 0.1 bohr), global 288^3 grid (h = 0.4275 bohr),
+1,728 subdomains of 72^3 points (1-cell core, 1-cell Dirichlet buffer), 528 states per subdomain
+(the count that holds a subdomain's electrons, 1.2 x N_e/2 rounded up to 16; `--states literal`
+runs 240), Chebyshev degree 20, V_eff the seeded stand-in potential of `synth`.  The subdomains do
+not fit in HBM together: the grid runs in waves of equal size in carry mode (one worker of W
+subdomain slots re-targeted to each wave, every wave starting from the subspace the previous wave
+left; the core rows of every subdomain's orbitals kept on the device for the density).  One step =
+one wave: restriction, projector tables and Lanczos bound of its subdomains, one CheFSI pass
+(filter, projection, eigensolve, rotation, interior weights), core rows out; every completed
+cycle of waves adds the Fermi level, energies and the density on the global grid.
+`--workload si64` runs the 64-atom cell (8 resident subdomains of 48^3, 160 states) instead.
 
-metric: CheFSI throughput in Gpt.vec/s = sum_alpha m N_d N_s / (pass time), one point-vector
-being one Hamiltonian application (+ recurrence) to one grid value of one vector.
+metric: CheFSI throughput in Gpt.vec/s = sum_alpha m N_d N_s / time, one point-vector being one
+Hamiltonian application (+ recurrence) to one grid value of one vector.
 """
 from __future__ import annotations
 
@@ -48,6 +53,15 @@ def parse_args():
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--cpu-baseline-worker", action="store_true", help=argparse.SUPPRESS)
     p.add_argument("--sample-states", type=int, default=32)
+    p.add_argument("--workload", default="si13824", choices=["si13824", "si64"])
+    p.add_argument("--states", default="consistent", choices=["consistent", "literal"],
+                   help="si13824: 528 states per subdomain (consistent) or 240 (literal count, timing only)")
+    p.add_argument("--budget-gb", type=float, default=250.0, help="si13824: HBM budget of the wave grid")
+    p.add_argument("--fp64-cycles", type=int, default=3,
+                   help="si13824: carry cycles of the FP64 and mixed forms on the 512-atom crystal of the same "
+                        "subdomain geometry (mixed-vs-FP64 factor and energy difference); 0 skips")
+    p.add_argument("--sample-vectors", type=int, default=16, help="si13824: vectors per oracle sample pass")
+    p.add_argument("--ncell", type=int, default=12, help="si13824: crystal edge in cells (12; smaller for a quick run)")
     return p.parse_args()
 
 
@@ -200,7 +214,7 @@ def stencil_bytes_per_launch(w, elem: int) -> float:
     return tot
 
 
-def run_ours(args):
+def run_si64(args):
     import torch
     from paper_2609_13115_gb300 import xls
     ws, rank, local = dist_setup()
@@ -390,6 +404,377 @@ def run_ours(args):
         dist.destroy_process_group()
 
 
+# ---------------------------------------------------------------------------------------------
+# The 13,824-atom cell: oracle samples on the host cores
+# ---------------------------------------------------------------------------------------------
+def si13824_workload(states: str, ncell: int = 12):
+    import synth
+    return synth.workload(3, consistent=(states == "consistent"), ncell=ncell)
+
+
+def _near_atoms(w, start, size, margin):
+    """Indices (in order) of the atoms within `margin` of the subdomain box (minimum image)."""
+    h = w.h
+    L = np.asarray(w.L, dtype=np.float64)
+    lo = np.asarray(start) * h
+    hi = (np.asarray(start) + np.asarray(size) - 1) * h
+    c = 0.5 * (lo + hi)
+    half = 0.5 * (hi - lo) + margin
+    d = w.pos - c
+    d -= L * np.round(d / L)
+    return np.nonzero(np.all(np.abs(d) <= half, axis=1))[0]
+
+
+def _oracle_sample(args):
+    """One host process: the oracle's CheFSI pass (Lanczos bound, Rayleigh-Ritz of the start
+    block, filter, projection, eigensolve, rotation, interior weights) on subdomain `sub` of the
+    13,824-atom cell with the first n_vec start vectors.  The subdomain operator is the oracle's
+    own, built from the atoms near the subdomain (the others have no projector support in it);
+    each of those atoms' projector normalisation is the oracle's, evaluated on one conventional
+    cell that carries the atom at its position modulo the cell (the same grid displacements
+    within r_cut as on the 288^3 grid).  Returns (point-vectors, seconds of the pass)."""
+    v_path, states, ncell, sub, n_vec = args
+    import synth
+    from oracle import chefsi, dc, pseudo
+    w = si13824_workload(states, ncell)
+    V = np.load(v_path, mmap_mode="r")
+    s = dc.partition(w)[sub]
+    near = _near_atoms(w, s.start, s.size, max(sp.r_cut for sp in w.species) + 1.0)
+    a = synth.SI_LATTICE_BOHR
+    cell = synth.Workload("norms", (a, a, a), (synth.POINTS_PER_CELL,) * 3, np.mod(w.pos[near], a),
+                          w.species_index[near], w.species, core_lo=np.zeros((1, 3), int),
+                          core_n=np.full((1, 3), synth.POINTS_PER_CELL), buf=np.zeros((1, 3), int),
+                          n_states=np.array([1]), degree=1, n_passes=1, psi_seed=0)
+    norms = pseudo.projector_norms(cell)
+    local = synth.Workload("near", w.L, w.n, w.pos[near], w.species_index[near], w.species, w.core_lo, w.core_n,
+                           w.buf, w.n_states, w.degree, w.n_passes, w.psi_seed)
+    H = dc.subdomain_operator(local, s, V, norms)
+    psi = synth.psi0_block(w.psi_seed, s.N, n_vec, synth.psi0_offsets(w)[sub])
+    t0 = time.perf_counter()
+    b = chefsi.lanczos_upper_bound(H, synth.lanczos_start(H.N))
+    lam = chefsi.ritz_values(H, psi)
+    lam, psi = chefsi.chefsi_pass(H, psi, w.degree, a=float(lam[-1]), b=b, a0=float(lam[0]))
+    dc.interior_weights(psi, s)
+    return float(H.N) * n_vec * w.degree, time.perf_counter() - t0
+
+
+class OraclePool:
+    """Host processes (spawned, one BLAS thread each) that run oracle samples side by side."""
+
+    def __init__(self, states: str, ncell: int, V: np.ndarray, processes: int):
+        import concurrent.futures as cf
+        import multiprocessing as mp
+        self.dir = tempfile.mkdtemp(prefix="xls_oracle_")
+        self.v_path = os.path.join(self.dir, "veff.npy")
+        np.save(self.v_path, V)
+        self.states = states
+        self.ncell = ncell
+        for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS", "BLIS_NUM_THREADS"):
+            os.environ[k] = "1"
+        self.n = processes
+        self.ex = cf.ProcessPoolExecutor(processes, mp_context=mp.get_context("spawn"))
+
+    def run(self, subs, n_vec):
+        """(total point-vectors, wall seconds, per-sample seconds) of one sample per subdomain."""
+        t0 = time.perf_counter()
+        out = list(self.ex.map(_oracle_sample, [(self.v_path, self.states, self.ncell, int(a), n_vec) for a in subs]))
+        return sum(u for u, _ in out), time.perf_counter() - t0, [t for _, t in out]
+
+    def close(self):
+        import shutil
+        self.ex.shutdown()
+        shutil.rmtree(self.dir, ignore_errors=True)
+
+
+def si13824_cpu_baseline(w, V, states, ncell, n_vec) -> dict:
+    """The oracle on the host cores: one subdomain alone (one thread), then one subdomain per core
+    side by side; the rate of the latter is the line's value, and the oracle's full pass of the
+    cell is extrapolated from it."""
+    cores = os.cpu_count() or 1
+    pool = OraclePool(states, ncell, V, cores)
+    try:
+        u1, _, t1 = pool.run([0], n_vec)
+        subs = np.linspace(0, w.n_sub - 1, cores).astype(int)
+        uN, wall, _ = pool.run(subs, n_vec)
+    finally:
+        pool.close()
+    full = point_vectors(w)
+    rate = uN / wall / 1e9
+    return {"value": round(rate, 6), "unit": UNIT, "cores": cores, "kind": "oracle",
+            "single_thread_value": round(u1 / t1[0] / 1e9, 6),
+            "sample": f"{n_vec} of {int(w.n_states[0])} start vectors of one 72^3 subdomain per process, one full "
+                      f"pass each (Lanczos bound, Rayleigh-Ritz, degree-{w.degree} filter, projection, eigensolve, "
+                      f"rotation), FP64 numpy, one BLAS thread per process; {cores} subdomains side by side took "
+                      f"{wall:.1f} s, one alone {t1[0]:.1f} s",
+            "extrapolated_full_pass_s": round(full / (rate * 1e9), 1)}
+
+
+# ---------------------------------------------------------------------------------------------
+# The 13,824-atom cell on the GPU (carry waves)
+# ---------------------------------------------------------------------------------------------
+def run_si13824(args):
+    import torch
+    ws, rank, local = dist_setup()
+    w = si13824_workload(args.states, args.ncell)
+    import synth
+    V = synth.veff_erf_wells(w)
+    from paper_2609_13115_gb300 import xls
+    xls.load()
+    stream = torch.cuda.current_stream()
+    prec = {"fp16": xls.XLS_MIXED_FP16, "bf16": xls.XLS_MIXED_BF16, "fp64": xls.XLS_FP64}[args.precision]
+    ng = int(np.prod(w.n))
+    rho_dev = torch.zeros(ng, dtype=torch.float64, device="cuda")
+    budget = int(args.budget_gb * 1e9)
+    g = xls.Grid(w, prec, hbm_budget_bytes=budget, stream=stream.cuda_stream)
+    g.set_hamiltonian(V)
+    xls.xls_wave_carry(g.h, -1)
+    n_waves, firsts = xls.xls_get_waves(g.h, w.n_sub)
+    W = w.n_sub // n_waves
+    xls.xls_orbitals_random(g.h, w.psi_seed)
+    ns = int(w.n_states[0])
+    nd = w.sub_points(0)
+    units_wave = float(W) * nd * ns * w.degree
+    state = {"k": 0, "launches": 0, "densities": 0}
+
+    def step():
+        k = state["k"] % n_waves
+        xls.xls_chefsi_wave(g.h, k, w.degree, 1)
+        state["launches"] += xls.xls_get_timings(g.h)[1]
+        if k == n_waves - 1:   # a cycle is complete: Fermi level, energies, density (on the device)
+            xls.xls_density(g.h, w.n_electrons, w.kT, rho_dev)
+            state["densities"] += 1
+        state["k"] += 1
+
+    # warm-up: the first wave bootstraps (a, a0) by a Rayleigh-Ritz step of the random block; the
+    # autotuner then picks the eigensolver cluster size and the Gram K split on the worker
+    for _ in range(max(args.warmup, 3)):
+        step()
+    tune = xls.xls_autotune(g.h, 3)
+    step()
+    sampler = ClockSampler(local)
+    sampler.start()
+    barrier(ws)
+    torch.cuda.synchronize()
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps + 1)]
+    state["launches"] = 0
+    state["densities"] = 0
+    k_first = state["k"]
+    ev[0].record(stream)
+    for i in range(args.steps):
+        step()
+        ev[i + 1].record(stream)
+    torch.cuda.synchronize()
+    barrier(ws)
+    clocks = sampler.stop()
+    step_ms = [ev[i].elapsed_time(ev[i + 1]) for i in range(args.steps)]
+    ms_total = ev[0].elapsed_time(ev[args.steps])
+    ms_total = allreduce_max(ms_total, ws)
+    ms_step = ms_total / args.steps
+    launches = state["launches"] + 3 * state["densities"]
+    # one full pass over the cell: the last n_waves consecutive steps ending with a density, if
+    # the timed steps hold a whole cycle (else the mean wave time times the wave count)
+    pass_ms = None
+    for end in range(args.steps - 1, n_waves - 2, -1):
+        if (k_first + end) % n_waves == n_waves - 1:
+            pass_ms = sum(step_ms[end - n_waves + 1:end + 1])
+            break
+    # complete the cycle (outside the timed region) and time the density stage alone
+    while state["k"] % n_waves != 0:
+        step()
+    d0, d1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    d0.record(stream)
+    mu, eb, es = xls.xls_density(g.h, w.n_electrons, w.kT, rho_dev)
+    d1.record(stream)
+    torch.cuda.synchronize()
+    density_ms = d0.elapsed_time(d1)
+    if pass_ms is None:
+        pass_ms = float(np.mean(step_ms)) * n_waves + density_ms
+    # per-kernel times and the stage split of one wave with CUDA events around every launch
+    xls.xls_set_profiling(g.h, 1)
+    step()
+    kms, kcnt = xls.xls_get_kernel_times(g.h)
+    stage_ms, _ = xls.xls_get_timings(g.h)
+    xls.xls_set_profiling(g.h, 0)
+
+    # end to end through the C ABI with host buffers: every step the wave's Ritz values and weights
+    # come back to the host; a cycle starts with V_eff going up from pinned host memory and ends
+    # with the density coming back
+    v_host = torch.from_numpy(np.ascontiguousarray(V, dtype=np.float64)).pin_memory()
+    rho_host = torch.empty(ng, dtype=torch.float64).pin_memory()
+    lam_host = np.zeros(ns)
+    c_host = np.zeros(ns)
+    while state["k"] % n_waves != 0:
+        step()
+    e2e_steps = max(3, args.steps // 4)
+    h2d = d2h = 0
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for i in range(e2e_steps):
+        k = state["k"] % n_waves
+        if k == 0:
+            xls.xls_hamiltonian_set(g.h, v_host.numpy(), w.pos, w.species_index, w.species)
+            h2d += v_host.numel() * 8 + w.pos.size * 8
+        xls.xls_chefsi_wave(g.h, k, w.degree, 1)
+        for a in range(firsts[k], firsts[k] + W):
+            xls.xls_get_eigs_into(g.h, a, lam_host, c_host)
+        d2h += W * ns * 16
+        if k == n_waves - 1:
+            xls.xls_density(g.h, w.n_electrons, w.kT, rho_host.numpy())
+            d2h += ng * 8 + 24
+        state["k"] += 1
+    e2e_s = allreduce_max((time.perf_counter() - t0) / e2e_steps, ws)
+    g.close()
+    del rho_dev
+
+    value = units_wave * ws / (ms_step / 1e3) / 1e9
+    elem = 8 if prec == xls.XLS_FP64 else 4
+    peaks = {}
+    pk_path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(pk_path):
+        peaks = json.load(open(pk_path))
+    peak = peaks.get("hbm_gbs", 6800.0)
+    stencil_avg_ms = kms[0] / max(kcnt[0], 1)
+    bytes_launch = float(W) * (3.0 * elem * nd * ns + elem * nd)
+    achieved = bytes_launch / (stencil_avg_ms / 1e3) / 1e9
+    roofline = {"bound": "hbm", "kernel": "k_stencil_tma" if prec != xls.XLS_FP64 else "k_stencil",
+                "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s", "frac": round(achieved / peak, 4),
+                "traffic": stencil_traffic_13824() if prec != xls.XLS_FP64 else None,
+                "peak_source": "measured" if "hbm_gbs" in peaks else "fallback",
+                "bytes_per_launch": bytes_launch, "avg_launch_ms": round(stencil_avg_ms, 4)}
+    kernel_share = {n: round(float(kms[i] / max(kms.sum(), 1e-9)), 4)
+                    for i, n in enumerate(["stencil", "nl_project", "nl_back", "gram", "eig", "rotate", "other"])}
+
+    fp64 = None
+    if args.fp64_cycles > 0 and prec != xls.XLS_FP64:
+        fp64 = si13824_precision(args, prec)
+
+    cpu = None
+    if rank == 0 and not args.no_cpu_baseline:
+        cpu = si13824_cpu_baseline(w, V, args.states, args.ncell, args.sample_vectors)
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": round(value, 3), "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": round(ms_step, 3), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None,
+            "dtype": {xls.XLS_MIXED_FP16: "f32 filter + fp16x3 tensor GEMM (f64 eig/fermi)",
+                      xls.XLS_MIXED_BF16: "f32 filter + bf16x3 tensor GEMM (f64 eig/fermi)",
+                      xls.XLS_FP64: "f64"}[prec],
+            "data": "synthetic",
+            "config": {"workload": w.name, "atoms": len(w.pos), "subdomains": w.n_sub, "points_per_subdomain": nd,
+                       "states": ns, "degree": w.degree, "waves": n_waves, "subdomains_per_wave": W,
+                       "step": "one wave of subdomains (restriction, tables, Lanczos bound, one CheFSI pass, core "
+                               "rows); Fermi level + density at each completed cycle",
+                       "l2": "inputs larger than L2 (each subdomain's orbital block "
+                             f"{nd * ns * elem / 1e6:.0f} MB)",
+                       "parallelism": f"replicas x{ws}" if ws > 1 else "single GPU",
+                       "autotuned": {"eig_cluster_ctas": tune[0], "gram_ctas_per_sm": tune[1]}},
+            "pass_ms": round(pass_ms, 1),
+            "stage_ms_per_wave": dict({k: round(float(v), 3) for k, v in
+                                       zip(["filter", "projection", "eig", "rotation"], stage_ms)},
+                                      density_per_cycle=round(density_ms, 3)),
+            "kernel_share": kernel_share,
+            "roofline": roofline,
+            "cpu_baseline": cpu,
+            "e2e": {"value": round(units_wave * ws / e2e_s / 1e9, 3), "unit": UNIT,
+                    "h2d_bytes_per_step": int(h2d / e2e_steps), "d2h_bytes_per_step": int(d2h / e2e_steps)},
+            "gpu_launches": int(launches),
+            "clocks": clocks,
+            "fp64": fp64,
+            "mu": mu, "e_band_per_atom": eb / len(w.pos),
+        }
+        print(json.dumps(line))
+    if ws > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+def si13824_precision(args, prec) -> dict:
+    """Mixed against FP64 on the 512-atom crystal (4^3 cells) cut like the 13,824-atom cell
+    (64 subdomains of 72^3 with Dirichlet buffers, the same states): both forms run the same carry
+    schedule from the same start (waves of 8); the last cycle is timed for the mixed-vs-FP64
+    factor; band energy minus entropy term per atom and the density are compared after the
+    cycles."""
+    import torch
+    import synth
+    from paper_2609_13115_gb300 import xls
+    w = synth.workload(3, consistent=(args.states == "consistent"), ncell=4)
+    V = synth.veff_erf_wells(w)
+    stream = torch.cuda.current_stream()
+    out = {}
+    for p in (xls.XLS_FP64, prec):
+        # a budget below the 64 subdomains' footprint in either precision: waves of 8
+        g = xls.Grid(w, p, hbm_budget_bytes=int(100e9), stream=stream.cuda_stream)
+        g.set_hamiltonian(V)
+        xls.xls_wave_carry(g.h, 8)
+        xls.xls_orbitals_random(g.h, w.psi_seed)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        for c in range(args.fp64_cycles):
+            if c == args.fp64_cycles - 1:
+                e0.record(stream)
+            xls.xls_chefsi_batch(g.h, w.degree, 1)
+        e1.record(stream)
+        rho = torch.zeros(int(np.prod(w.n)), dtype=torch.float64, device="cuda")
+        mu, eb, es = xls.xls_density(g.h, w.n_electrons, w.kT, rho)
+        torch.cuda.synchronize()
+        out[p] = (e0.elapsed_time(e1), mu, eb - es, rho)
+        g.close()
+    (t64, mu64, e64, r64), (tm, mum, em, rm) = out[xls.XLS_FP64], out[prec]
+    n_at = len(w.pos)
+    return {"workload": w.name, "cycles": args.fp64_cycles, "ms_per_cycle_fp64": round(t64, 1),
+            "ms_per_cycle_mixed": round(tm, 1), "mixed_speedup": round(t64 / tm, 2),
+            "delta_e_per_atom": abs(em - e64) / n_at,
+            "rho_rel_l2": float(torch.linalg.norm(rm - r64) / torch.linalg.norm(r64)),
+            "mu_fp64": mu64, "mu_mixed": mum}
+
+
+# DRAM bytes (read + write) of one FP32 stencil launch over a wave of 72 subdomains of 72^3 with
+# 528 states, measured by ncu for the kernel source whose SHA-256 starts with the key
+STENCIL_TRAFFIC_13824 = {}
+
+
+def stencil_traffic_13824():
+    import hashlib
+    src = os.path.join(ROOT, "paper_2609_13115_gb300", "csrc", "k_stencil_tma.cu")
+    h = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+    return STENCIL_TRAFFIC_13824.get(h)
+
+
+def run_reference_si13824(args):
+    """The oracle as it stands on the host cores: each step one pass per core, side by side, each
+    on a different 72^3 subdomain with a few start vectors."""
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    import synth
+    w = si13824_workload(args.states, args.ncell)
+    V = synth.veff_erf_wells(w)
+    cores = os.cpu_count() or 1
+    n_vec = 2
+    pool = OraclePool(args.states, args.ncell, V, cores)
+    rates, secs = [], []
+    try:
+        for it in range(args.warmup + args.steps):
+            subs = (np.arange(cores) * 7 + it * cores) % w.n_sub
+            u, wall, _ = pool.run(subs, n_vec)
+            if it >= args.warmup:
+                rates.append(u / wall / 1e9)
+                secs.append(wall)
+    finally:
+        pool.close()
+    value = float(np.mean(rates))
+    line = {"impl": "reference", "metric": METRIC, "value": round(value, 6), "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(float(np.mean(secs)) * 1e3, 1),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": w.name, "atoms": len(w.pos), "subdomains": w.n_sub,
+                       "points_per_subdomain": w.sub_points(0), "states": int(w.n_states[0]), "degree": w.degree},
+            "cpu_baseline": {"kind": "oracle", "cores": cores, "value": round(value, 6), "unit": UNIT,
+                             "sample": f"per step {cores} processes side by side, each one full pass of a different "
+                                       f"72^3 subdomain with {n_vec} of {int(w.n_states[0])} start vectors"},
+            "e2e": {"value": round(value, 6), "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+
+
 def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
@@ -420,9 +805,14 @@ def main():
         print(json.dumps(cpu_sample_pass(args.sample_states)))
         return
     if args.impl == "reference":
-        run_reference(args)
+        if args.workload == "si13824":
+            run_reference_si13824(args)
+        else:
+            run_reference(args)
+    elif args.workload == "si13824":
+        run_si13824(args)
     else:
-        run_ours(args)
+        run_si64(args)
 
 
 if __name__ == "__main__":

@@ -141,8 +141,9 @@ xls_status xls_chefsi_batch(xls_grid g, int degree, int n_passes, const double* 
  * the grid's stream.  The input is the last pass's M_s and H_s: they and the split exponents are
  * saved and put back, the eigenpairs recomputed with the chosen configuration, so the next pass
  * differs from an untuned one by rounding only.  Captured pass graphs are dropped (the next
- * graphed pass captures the tuned launches).  choices_out may be NULL.
- * Errors: XLS_EINVAL (bad arguments, wave mode, no pass run yet), XLS_ENOMEM (no room for the
+ * graphed pass captures the tuned launches).  In wave carry mode it tunes the worker on the last
+ * wave it ran (the choices hold for every wave: all have the same shapes).  choices_out may be NULL.
+ * Errors: XLS_EINVAL (bad arguments, store-mode waves, no pass run yet), XLS_ENOMEM (no room for the
  * saved matrices), XLS_ECUDA, and the status of the eigensolve (XLS_ENOTSPD). */
 xls_status xls_autotune(xls_grid g, int reps, int* choices_out);
 
@@ -190,8 +191,9 @@ xls_status xls_get_bounds(xls_grid g, double* bounds_out);
 xls_status xls_get_timings(xls_grid g, double* ms4_out, int* launches_out);
 
 /* Turn on (1) or off (0) per-kernel timing: CUDA events around every launch of each pass on
- * the grid's stream (a few microseconds of overhead per launch).  Library-specific: the
- * paper has no counterpart; it feeds roofline measurements. */
+ * the grid's stream (a few microseconds of overhead per launch).  In wave carry mode it times the
+ * worker's passes (xls_get_kernel_times then reads the last wave's); in store mode XLS_EINVAL.
+ * Library-specific: the paper has no counterpart; it feeds roofline measurements. */
 xls_status xls_set_profiling(xls_grid g, int on);
 
 /* Parameters of the self-consistent-field iteration (Sec. 5.A.4, Sec. 5.B.3 SCF): electron count
@@ -275,6 +277,38 @@ xls_status xls_density_at(xls_grid g, double mu, double kT, double* rho_out, int
  * xls_get_subspace and profiling return XLS_EINVAL in wave mode.
  * Library-specific: the paper batches subdomains per MPI rank instead. */
 xls_status xls_get_waves(xls_grid g, int* n_waves_out, int* first_sub_out);
+
+/* Wave mode only: carry mode with `slots` subdomains per wave (slots > 0: that many, a divisor of
+ * the subdomain count; slots < 0: the largest divisor whose worker and core store fit the HBM
+ * budget given at creation) or store mode (slots == 0, the default).  In carry mode the
+ * grid keeps no copy of the orbitals between waves: one worker grid of W subdomain slots is
+ * allocated once and re-targeted to each wave in turn (its descriptors moved, V_eff restricted,
+ * projector tables rebuilt and the Lanczos bound taken for the wave's subdomains), and every
+ * wave's passes start from the rotated block the previous wave left in the worker -- the restart
+ * of a crystal's subdomains from a neighbouring subdomain's subspace, for subdomains too many for
+ * the host to keep (the 1,728 subdomains of 72^3 points with 528 states of a 13,824-atom cell
+ * would need 1.4 TB of FP32 orbitals).  xls_orbitals_random draws the first wave's start block
+ * (the first pass then takes (a, a0) from a Rayleigh-Ritz step of it); later waves take a and a0
+ * from the subdomain's own last pass, or from the slot's last pass on the first cycle.  After
+ * each wave the core rows of every subdomain's orbitals go to a device store (core points x
+ * N_s values per subdomain, the compute precision), from which xls_density forms rho after the
+ * Fermi level of all subdomains.  Every subdomain must have the shape of subdomain 0 (points,
+ * boundaries, core box, states); the waves become equal.  Switching the mode or the slot count
+ * drops the orbitals (xls_orbitals_random again).  xls_orbitals_set and xls_orbitals_get return
+ * XLS_EINVAL in carry mode.  Errors: XLS_EINVAL (not a wave grid, unequal shapes, a slot count
+ * that does not divide the subdomain count), XLS_ENOMEM (the slots and the core store exceed the
+ * budget).  Sec. 5.A.5
+ * "Parallel CheFSI" (subdomains processed independently); the restart between waves is
+ * library-specific. */
+xls_status xls_wave_carry(xls_grid g, int slots);
+
+/* Wave mode only: the passes of one wave (waves numbered as xls_get_waves lists them): in store
+ * mode the wave's orbitals go up from the host store and come back; in carry mode the worker is
+ * re-targeted to the wave and starts from the block the previous call left.  Ritz values,
+ * weights and bounds of the wave's subdomains are kept; xls_density needs every wave to have run
+ * since the last xls_hamiltonian_set.  bounds: optional [3*n_sub] (b, a, a0) of every subdomain
+ * (only the wave's entries are read).  Library-specific (a unit of work sized to the HBM budget). */
+xls_status xls_chefsi_wave(xls_grid g, int wave, int degree, int n_passes, const double* bounds);
 
 /* Wave mode only: keep the host store of the orbitals in FP16 (on != 0) or in the compute
  * precision (on == 0).  FP16: every vector v of a subdomain is stored as half(psi_v 2^e_v) with

@@ -2,6 +2,7 @@
 // subdomains (one launch per stage), Fermi level and density.  Host code only orchestrates;
 // every arithmetic step of the pass runs in the kernels of k_filter.cu, k_dense.cu, k_eig.cu
 // and k_tc.cu.
+#include <algorithm>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -85,6 +86,15 @@ struct xls_grid_s {
   int* stage_ex = nullptr;
   std::vector<double> host_bounds;
   double wave_stage_ms[4] = {0, 0, 0, 0};
+  // carry mode (xls_wave_carry): no orbital store; one worker grid, re-targeted to every wave in
+  // turn, whose rotated block starts the next wave's passes; the core rows of every subdomain's
+  // orbitals stay on the device (compact store) for the density after the Fermi level
+  bool carry = false, carry_primed = false;
+  xls_grid worker = nullptr;
+  void* core_store = nullptr;
+  SubDev* d_core_subs = nullptr;
+  std::vector<double> carry_ab;      // (a, a0) of every worker slot after its last pass
+  std::vector<char> wave_ran;        // waves that have run since the orbitals were set
   // geometry of the last xls_hamiltonian_set (for the pseudocharge of the SCF step)
   std::vector<double> atom_pos;
   std::vector<int> atom_sp;
@@ -1130,20 +1140,12 @@ xls_status create_grid(const xls_cell* cell, const xls_dc* dc, int precision, si
       for (SubDev& S : staged) S.off_blk = 0;
       cudaMemcpy(g->d_subs, staged.data(), staged.size() * sizeof(SubDev), cudaMemcpyHostToDevice);
     }
-    long long max_blk = 0;
-    for (const SubDev& S : g->subs) max_blk = std::max(max_blk, S.nd * S.ns);
-    ALLOC(g->blk[0], max_blk * std::max<size_t>(g->elem, 8));   // staging block of one subdomain
     cudaMemset(g->status, 0, 2 * sizeof(int));
     cudaMemset(g->lam, 0, g->tot_states * sizeof(double));
     cudaMemset(g->cw, 0, g->tot_states * sizeof(double));
     for (int i = 0; i < 6; ++i) cudaEventCreate(&g->ev[i]);
-    if (cudaMallocHost(&g->store, g->tot_blk * g->elem) != cudaSuccess) {
-      cudaGetLastError();
-      g->store = nullptr;
-      xls_grid_destroy(g);
-      return fail(XLS_ENOMEM, "wave mode: pinned host store for the orbitals could not be allocated");
-    }
-    std::memset(g->store, 0, g->tot_blk * g->elem);
+    // the pinned orbital store and the device staging block are allocated at first use (carry
+    // mode needs neither)
     g->host_bounds.assign(3 * (size_t)g->n_sub, 0.0);
     *out = g;
     return XLS_OK;
@@ -1350,6 +1352,27 @@ size_t sub_footprint(const SubDev& S, size_t elem) {
 size_t store_elem(xls_grid g) { return g->store16 ? 2 : g->elem; }
 char* store_ptr(xls_grid g, int sub) { return (char*)g->store + (size_t)g->subs[sub].off_blk * store_elem(g); }
 
+// the pinned host store of every subdomain's orbitals (compute precision), allocated at first use
+xls_status ensure_store(xls_grid g) {
+  if (g->store) return XLS_OK;
+  if (g->carry) return fail(XLS_EINVAL, "wave carry mode keeps no orbital store");
+  if (cudaMallocHost(&g->store, g->tot_blk * g->elem) != cudaSuccess) {
+    cudaGetLastError();
+    g->store = nullptr;
+    return fail(XLS_ENOMEM, "wave mode: pinned host store for the orbitals could not be allocated");
+  }
+  std::memset(g->store, 0, g->tot_blk * g->elem);
+  return XLS_OK;
+}
+
+// device staging block of one subdomain (wave mode), allocated at first use
+xls_status ensure_stage(xls_grid g) {
+  if (g->blk[0]) return XLS_OK;
+  long long max_blk = 0;
+  for (const SubDev& S : g->subs) max_blk = std::max(max_blk, S.nd * S.ns);
+  return g->alloc(&g->blk[0], max_blk * std::max<size_t>(g->elem, 8));
+}
+
 // the stored block of subdomain `sub` into device memory `dev` in the compute precision of the
 // wave grid g (the store's format: a plain copy, or halves + exponents converted on the device)
 xls_status store_to_device(xls_grid g, int sub, void* dev, cudaStream_t st) {
@@ -1416,10 +1439,14 @@ xls_status wave_hamiltonian_set(xls_grid g, const double* veff, int veff_on_devi
   g->species.assign(sp, sp + n_species);
   g->ham_set = true;
   g->have_ritz = false;
+  std::fill(g->wave_ran.begin(), g->wave_ran.end(), 0);   // Ritz values of the old potential
   return XLS_OK;
 }
 
 xls_status wave_orbitals_set(xls_grid g, int sub, const double* psi, int on_device) {
+  if (g->carry) return fail(XLS_EINVAL, "xls_orbitals_set: wave carry mode draws its start block with xls_orbitals_random");
+  XLS_TRY(ensure_store(g));
+  XLS_TRY(ensure_stage(g));
   const SubDev& S = g->subs[sub];
   const size_t n = (size_t)S.nd * S.ns;
   std::vector<double> tmp;
@@ -1449,6 +1476,9 @@ xls_status wave_orbitals_set(xls_grid g, int sub, const double* psi, int on_devi
 }
 
 xls_status wave_orbitals_get(xls_grid g, int sub, double* out, int on_device) {
+  if (g->carry) return fail(XLS_EINVAL, "xls_orbitals_get: wave carry mode keeps no orbital store");
+  XLS_TRY(ensure_store(g));
+  XLS_TRY(ensure_stage(g));
   const SubDev& S = g->subs[sub];
   const size_t n = (size_t)S.nd * S.ns;
   std::vector<double> tmp;
@@ -1472,7 +1502,12 @@ xls_status wave_orbitals_get(xls_grid g, int sub, double* out, int on_device) {
   return XLS_OK;
 }
 
+xls_status carry_orbitals_random(xls_grid g, uint64_t seed);
+
 xls_status wave_orbitals_random(xls_grid g, uint64_t seed) {
+  if (g->carry) return carry_orbitals_random(g, seed);
+  XLS_TRY(ensure_store(g));
+  XLS_TRY(ensure_stage(g));
   for (int a = 0; a < g->n_sub; ++a) {
     const SubDev& S = g->subs[a];
     const long long n = S.nd * S.ns;
@@ -1486,48 +1521,154 @@ xls_status wave_orbitals_random(xls_grid g, uint64_t seed) {
   return XLS_OK;
 }
 
-// every wave in turn: partial grid, orbitals up, passes, orbitals / Ritz values / weights /
-// bounds back, partial grid released
+// one wave of a wave-mode grid with an orbital store: partial grid, orbitals up, passes,
+// orbitals / Ritz values / weights / bounds back, partial grid released
 // fresh_b: the potential changed since the last pass (an SCF step): the upper bound b of every
 // subdomain is the worker's new Lanczos bound, a and a0 stay those of the last pass's Ritz values
 // (what the resident grid's SCF step does with its Lanczos bounds)
+xls_status wave_run(xls_grid g, int w, int degree, int n_passes, const double* bounds, bool fresh_b, int& launches) {
+  XLS_TRY(ensure_store(g));
+  const int first = g->waves[w].first, cnt = g->waves[w].second;
+  xls_grid k = nullptr;
+  XLS_TRY(wave_worker(g, w, &k));
+  xls_status s = XLS_OK;
+  for (int j = 0; j < cnt && s == XLS_OK; ++j)
+    s = store_to_device(g, first + j, (char*)k->blk[k->cur] + (size_t)k->subs[j].off_blk * k->elem, g->st);
+  k->orb_set = true;
+  const double* bw = bounds ? bounds + 3 * (size_t)first
+                            : (g->have_ritz ? g->host_bounds.data() + 3 * (size_t)first : nullptr);
+  std::vector<double> mixed;
+  if (s == XLS_OK && fresh_b && bw) {
+    mixed.assign(bw, bw + 3 * (size_t)cnt);
+    std::vector<double> wb(3 * (size_t)cnt);
+    s = xls_get_bounds(k, wb.data());
+    for (int j = 0; j < cnt; ++j) mixed[3 * (size_t)j] = wb[3 * (size_t)j];
+    bw = mixed.data();
+  }
+  if (s == XLS_OK) s = xls_chefsi_batch(k, degree, n_passes, bw);
+  if (s == XLS_OK) {
+    const SubDev& S0 = g->subs[first];
+    cudaMemcpyAsync(g->lam + S0.off_state, k->lam, k->tot_states * sizeof(double), cudaMemcpyDeviceToDevice, g->st);
+    cudaMemcpyAsync(g->cw + S0.off_state, k->cw, k->tot_states * sizeof(double), cudaMemcpyDeviceToDevice, g->st);
+    s = xls_get_bounds(k, g->host_bounds.data() + 3 * (size_t)first);
+  }
+  for (int j = 0; j < cnt && s == XLS_OK; ++j)
+    s = device_to_store(g, first + j, (const char*)k->blk[k->cur] + (size_t)k->subs[j].off_blk * k->elem, g->st);
+  if (s == XLS_OK && cudaStreamSynchronize(g->st) != cudaSuccess) s = fail(XLS_ECUDA, "wave: synchronisation failed");
+  if (s == XLS_OK) {
+    for (int i = 0; i < 4; ++i) g->wave_stage_ms[i] += k->stage_ms[i];
+    launches += k->last_launches;
+  }
+  xls_grid_destroy(k);
+  return s;
+}
+
+// ---- carry mode -----------------------------------------------------------------------------
+// every subdomain of the grid has the shape of subdomain 0 (grid points, boundary conditions,
+// core box position inside the subdomain, states)
+bool uniform_shapes(xls_grid g) {
+  const SubDev& A = g->subs[0];
+  for (const SubDev& S : g->subs)
+    for (int d = 0; d < 3; ++d)
+      if (S.n[d] != A.n[d] || S.periodic[d] != A.periodic[d] || S.core_lo[d] != A.core_lo[d] ||
+          S.core_n[d] != A.core_n[d] || S.ns != A.ns)
+        return false;
+  return true;
+}
+
+// the worker's slots take the subdomains first .. first + W - 1 of the grid: descriptors moved
+// (same shapes, new positions), then V_eff restricted, projector tables rebuilt and the Lanczos
+// bound of every slot taken (xls_hamiltonian_set of the worker)
+xls_status carry_retarget(xls_grid g, int first) {
+  xls_grid k = g->worker;
+  for (int j = 0; j < k->n_sub; ++j) {
+    const SubDev& S = g->subs[first + j];
+    for (int d = 0; d < 3; ++d) {
+      k->subs[j].start[d] = k->subs1[j].start[d] = S.start[d];
+      k->subs[j].core_glo[d] = k->subs1[j].core_glo[d] = S.core_glo[d];
+    }
+  }
+  XLS_CUDA(cudaMemcpyAsync(k->d_subs, k->subs.data(), k->n_sub * sizeof(SubDev), cudaMemcpyHostToDevice, g->st));
+  XLS_CUDA(cudaMemcpyAsync(k->d_subs1, k->subs1.data(), k->n_sub * sizeof(SubDev), cudaMemcpyHostToDevice, g->st));
+  const int na = (int)g->atom_sp.size();
+  return xls_hamiltonian_set(k, g->Vg, 1, na, na ? g->atom_pos.data() : nullptr, na ? g->atom_sp.data() : nullptr,
+                             (int)g->species.size(), g->species.empty() ? nullptr : g->species.data());
+}
+
+xls_status carry_orbitals_random(xls_grid g, uint64_t seed) {
+  xls_grid k = g->worker;
+  // the stream values of the first wave's subdomains (blocks concatenated in subdomain order)
+  if (k->prec == XLS_FP64) launch_splitmix_fill_f64((double*)k->blk[k->cur], k->tot_blk, seed, 0, k->st);
+  else launch_splitmix_fill_f32((float*)k->blk[k->cur], k->tot_blk, seed, 0, k->st);
+  XLS_CUDA(cudaGetLastError());
+  k->orb_set = true;
+  k->have_ritz = false;
+  g->orb_set = true;
+  g->have_ritz = false;
+  g->carry_primed = false;
+  std::fill(g->wave_ran.begin(), g->wave_ran.end(), 0);
+  return XLS_OK;
+}
+
+// one wave in carry mode: the worker re-targeted to the wave, its passes from the block the
+// previous wave left (bounds: b from the new Lanczos run; a, a0 from the subdomain's own last pass
+// when it has one, else from the slot's last pass; the first wave after xls_orbitals_random
+// takes them from a Rayleigh-Ritz step of the random block), then the Ritz values, weights,
+// bounds and core rows of the orbitals copied out
+xls_status carry_run(xls_grid g, int w, int degree, int n_passes, const double* bounds, int& launches) {
+  xls_grid k = g->worker;
+  const int first = g->waves[w].first, cnt = g->waves[w].second;
+  XLS_TRY(carry_retarget(g, first));
+  k->orb_set = true;
+  std::vector<double> bw;
+  const double* bp = nullptr;
+  if (bounds) {
+    bp = bounds + 3 * (size_t)first;
+  } else if (g->carry_primed) {
+    bw.assign(3 * (size_t)cnt, 0.0);
+    XLS_TRY(xls_get_bounds(k, bw.data()));   // b of the new Lanczos run
+    for (int j = 0; j < cnt; ++j) {
+      const bool own = g->wave_ran[w] != 0;
+      const double* src = own ? g->host_bounds.data() + 3 * (size_t)(first + j) : g->carry_ab.data() + 3 * (size_t)j;
+      bw[3 * (size_t)j + 1] = src[1];
+      bw[3 * (size_t)j + 2] = src[2];
+    }
+    bp = bw.data();
+  }
+  XLS_TRY(xls_chefsi_batch(k, degree, n_passes, bp));
+  const SubDev& S0 = g->subs[first];
+  XLS_CUDA(cudaMemcpyAsync(g->lam + S0.off_state, k->lam, k->tot_states * sizeof(double), cudaMemcpyDeviceToDevice,
+                           g->st));
+  XLS_CUDA(cudaMemcpyAsync(g->cw + S0.off_state, k->cw, k->tot_states * sizeof(double), cudaMemcpyDeviceToDevice,
+                           g->st));
+  const long long per_sub = (long long)S0.core_n[0] * S0.core_n[1] * S0.core_n[2] * S0.ns;
+  if (g->prec == XLS_FP64)
+    launch_core_gather<double>(k->d_subs, cnt, k->max_ns, (const double*)k->blk[k->cur], (double*)g->core_store,
+                               (long long)first * per_sub, per_sub, g->st);
+  else
+    launch_core_gather<float>(k->d_subs, cnt, k->max_ns, (const float*)k->blk[k->cur], (float*)g->core_store,
+                              (long long)first * per_sub, per_sub, g->st);
+  XLS_CUDA(cudaGetLastError());
+  XLS_TRY(xls_get_bounds(k, g->host_bounds.data() + 3 * (size_t)first));
+  g->carry_ab.assign(g->host_bounds.begin() + 3 * (size_t)first, g->host_bounds.begin() + 3 * (size_t)(first + cnt));
+  for (int i = 0; i < 4; ++i) g->wave_stage_ms[i] += k->stage_ms[i];
+  // kernels of the re-targeting (restriction, projector norms and tables, reverse tables, unit
+  // coefficients; 10 Lanczos steps of one H application each) and of the core-row gather
+  const int setup = (k->prec == XLS_FP64 ? 7 : 9) + 2 + 10 * ((k->n_slot ? 3 : 1) + 1);
+  launches += k->last_launches + setup + 1;
+  g->carry_primed = true;
+  g->wave_ran[w] = 1;
+  g->have_ritz = std::all_of(g->wave_ran.begin(), g->wave_ran.end(), [](char c) { return c != 0; });
+  return XLS_OK;
+}
+
+// every wave in turn
 xls_status wave_chefsi(xls_grid g, int degree, int n_passes, const double* bounds, bool fresh_b = false) {
   for (double& t : g->wave_stage_ms) t = 0.0;
   int launches = 0;
   for (size_t w = 0; w < g->waves.size(); ++w) {
-    const int first = g->waves[w].first, cnt = g->waves[w].second;
-    xls_grid k = nullptr;
-    XLS_TRY(wave_worker(g, (int)w, &k));
-    xls_status s = XLS_OK;
-    for (int j = 0; j < cnt && s == XLS_OK; ++j)
-      s = store_to_device(g, first + j, (char*)k->blk[k->cur] + (size_t)k->subs[j].off_blk * k->elem, g->st);
-    k->orb_set = true;
-    const double* bw = bounds ? bounds + 3 * (size_t)first
-                              : (g->have_ritz ? g->host_bounds.data() + 3 * (size_t)first : nullptr);
-    std::vector<double> mixed;
-    if (s == XLS_OK && fresh_b && bw) {
-      mixed.assign(bw, bw + 3 * (size_t)cnt);
-      std::vector<double> wb(3 * (size_t)cnt);
-      s = xls_get_bounds(k, wb.data());
-      for (int j = 0; j < cnt; ++j) mixed[3 * (size_t)j] = wb[3 * (size_t)j];
-      bw = mixed.data();
-    }
-    if (s == XLS_OK) s = xls_chefsi_batch(k, degree, n_passes, bw);
-    if (s == XLS_OK) {
-      const SubDev& S0 = g->subs[first];
-      cudaMemcpyAsync(g->lam + S0.off_state, k->lam, k->tot_states * sizeof(double), cudaMemcpyDeviceToDevice, g->st);
-      cudaMemcpyAsync(g->cw + S0.off_state, k->cw, k->tot_states * sizeof(double), cudaMemcpyDeviceToDevice, g->st);
-      s = xls_get_bounds(k, g->host_bounds.data() + 3 * (size_t)first);
-    }
-    for (int j = 0; j < cnt && s == XLS_OK; ++j)
-      s = device_to_store(g, first + j, (const char*)k->blk[k->cur] + (size_t)k->subs[j].off_blk * k->elem, g->st);
-    if (s == XLS_OK && cudaStreamSynchronize(g->st) != cudaSuccess) s = fail(XLS_ECUDA, "wave: synchronisation failed");
-    if (s == XLS_OK) {
-      for (int i = 0; i < 4; ++i) g->wave_stage_ms[i] += k->stage_ms[i];
-      launches += k->last_launches;
-    }
-    xls_grid_destroy(k);
-    if (s != XLS_OK) return s;
+    if (g->carry) XLS_TRY(carry_run(g, (int)w, degree, n_passes, bounds, launches));
+    else XLS_TRY(wave_run(g, (int)w, degree, n_passes, bounds, fresh_b, launches));
   }
   g->last_launches = launches;
   g->have_ritz = true;
@@ -1536,6 +1677,10 @@ xls_status wave_chefsi(xls_grid g, int degree, int n_passes, const double* bound
 
 xls_status wave_density(xls_grid g, double n_electrons, double kT, double* mu_out, double* rho_out, int rho_on_device,
                         double* e_band_out, double* e_entropy_out) {
+  if (!g->carry) {
+    XLS_TRY(ensure_store(g));
+    XLS_TRY(ensure_stage(g));
+  }
   launch_fermi_occ(g->lam, g->cw, g->tot_states, n_electrons, kT, g->out4, g->occ, g->status, g->st);
   XLS_TRY(check_status(g));
   double h4[4];
@@ -1546,8 +1691,17 @@ xls_status wave_density(xls_grid g, double n_electrons, double kT, double* mu_ou
   if (!rho_out) return XLS_OK;
   const long long ng = (long long)g->gn[0] * g->gn[1] * g->gn[2];
   if (!g->rho) XLS_TRY(g->alloc(&g->rho, ng * sizeof(double)));
+  if (g->carry) {   // the compact device store of the core rows
+    if (g->prec == XLS_FP64)
+      launch_density_occ<double>(g->d_core_subs, g->n_sub, g->max_core, (const double*)g->core_store, g->occ, g->gn,
+                                 g->rho, g->st);
+    else
+      launch_density_occ<float>(g->d_core_subs, g->n_sub, g->max_core, (const float*)g->core_store, g->occ, g->gn,
+                                g->rho, g->st);
+    XLS_CUDA(cudaGetLastError());
+  }
   // second sweep: every subdomain's block staged alone; its core points of rho written
-  for (int a = 0; a < g->n_sub; ++a) {
+  for (int a = 0; a < g->n_sub && !g->carry; ++a) {
     const SubDev& S = g->subs[a];
     const long long core = (long long)S.core_n[0] * S.core_n[1] * S.core_n[2];
     XLS_TRY(store_to_device(g, a, g->blk[0], g->st));
@@ -1634,6 +1788,7 @@ xls_status xls_grid_destroy(xls_grid g) {
   if (g->side_st) cudaStreamDestroy(g->side_st);
   if (g->ev_side_in) cudaEventDestroy(g->ev_side_in);
   if (g->ev_side_out) cudaEventDestroy(g->ev_side_out);
+  if (g->worker) xls_grid_destroy(g->worker);
   if (g->store) cudaFreeHost(g->store);
   if (g->stage16) cudaFree(g->stage16);
   if (g->stage_ex) cudaFree(g->stage_ex);
@@ -1924,6 +2079,7 @@ xls_status xls_chefsi_batch(xls_grid g, int degree, int n_passes, const double* 
 
 xls_status xls_autotune(xls_grid g, int reps, int* choices_out) {
   if (!g || reps < 1 || reps > 100) return fail(XLS_EINVAL, "xls_autotune: bad arguments");
+  if (g->wave && g->carry && g->worker) return xls_autotune(g->worker, reps, choices_out);   // the worker's last wave
   if (g->wave) return fail(XLS_EINVAL, "xls_autotune: not in wave mode");
   if (!g->have_ritz) return fail(XLS_EINVAL, "xls_autotune: run a pass first (its subspace matrices are the input)");
   XLS_TRY(check_status(g));
@@ -2149,6 +2305,96 @@ xls_status xls_wave_store_fp16(xls_grid g, int on) {
   return XLS_OK;
 }
 
+xls_status xls_wave_carry(xls_grid g, int slots) {
+  if (!g) return fail(XLS_EINVAL, "xls_wave_carry: bad arguments");
+  if (!g->wave) return fail(XLS_EINVAL, "xls_wave_carry: the grid is not running in waves");
+  if (slots > 0 && (slots > g->n_sub || g->n_sub % slots != 0))
+    return fail(XLS_EINVAL, "xls_wave_carry: the slot count must divide the subdomain count");
+  if (g->carry && slots != 0) {   // already in carry mode: only a change of the slot count matters
+    if (slots < 0 || slots == g->worker->n_sub) return XLS_OK;
+    XLS_TRY(xls_wave_carry(g, 0));
+  }
+  XLS_CUDA(cudaStreamSynchronize(g->st));
+  if (slots == 0) {
+    if (!g->carry) return XLS_OK;
+    if (g->worker) xls_grid_destroy(g->worker);
+    g->worker = nullptr;
+    g->release(&g->core_store);
+    g->release(&g->d_core_subs);
+    g->carry = false;
+    g->orb_set = false;
+    g->have_ritz = false;
+    return XLS_OK;
+  }
+  if (!uniform_shapes(g))
+    return fail(XLS_EINVAL, "xls_wave_carry: every subdomain must have the shape of subdomain 0 (points, boundaries, "
+                            "core box, states)");
+  const SubDev& A = g->subs[0];
+  const size_t core_pts = (size_t)A.core_n[0] * A.core_n[1] * A.core_n[2];
+  const size_t store_bytes = core_pts * A.ns * g->elem * (size_t)g->n_sub;
+  const size_t f = sub_footprint(A, g->elem);
+  const size_t fixed = ((size_t)1 << 26) + g->bytes + store_bytes;
+  int W = 0;
+  for (int w = slots > 0 ? slots : g->n_sub; w >= 1; --w)
+    if (g->n_sub % w == 0 && (!g->budget || fixed + (size_t)w * f <= g->budget)) {
+      W = w;
+      break;
+    }
+  if (W == 0) return fail(XLS_ENOMEM, "xls_wave_carry: the core store and one subdomain exceed the HBM budget");
+  if (slots > 0 && W != slots)
+    return fail(XLS_ENOMEM, "xls_wave_carry: " + std::to_string(slots) + " slots and the core store exceed the HBM budget");
+  // the host store (if one was made) is no longer used
+  if (g->store) cudaFreeHost(g->store);
+  g->store = nullptr;
+  g->store16 = false;
+  XLS_TRY(g->alloc(&g->core_store, store_bytes));
+  XLS_TRY(g->alloc(&g->d_core_subs, g->n_sub * sizeof(SubDev)));
+  // density descriptors of the compact store: subdomain a's core box is a block of its own
+  std::vector<SubDev> cs(g->subs);
+  for (int a = 0; a < g->n_sub; ++a) {
+    SubDev& S = cs[a];
+    for (int d = 0; d < 3; ++d) {
+      S.n[d] = S.core_n[d];
+      S.periodic[d] = 0;
+      S.start[d] = S.core_glo[d];
+      S.core_lo[d] = 0;
+    }
+    S.nd = (long long)core_pts;
+    S.off_blk = (long long)a * (long long)(core_pts * A.ns);
+  }
+  XLS_CUDA(cudaMemcpy(g->d_core_subs, cs.data(), cs.size() * sizeof(SubDev), cudaMemcpyHostToDevice));
+  g->waves.clear();
+  for (int first = 0; first < g->n_sub; first += W) g->waves.push_back({first, W});
+  xls_dc dc{W, g->dc_core_lo.data(), g->dc_core_n.data(), g->dc_buf.data(), g->dc_ns.data()};
+  xls_grid k = nullptr;
+  const xls_status s = create_grid(&g->cell, &dc, g->prec, 0, g->st, &k, true, false);
+  if (s != XLS_OK) {
+    g->release(&g->core_store);
+    g->release(&g->d_core_subs);
+    return s;
+  }
+  g->worker = k;
+  g->carry = true;
+  g->carry_primed = false;
+  g->wave_ran.assign(g->waves.size(), 0);
+  g->orb_set = false;
+  g->have_ritz = false;
+  return XLS_OK;
+}
+
+xls_status xls_chefsi_wave(xls_grid g, int wave, int degree, int n_passes, const double* bounds) {
+  if (!g || degree < 1 || degree >= kMaxDegree - 1 || n_passes < 0) return fail(XLS_EINVAL, "xls_chefsi_wave: bad arguments");
+  if (!g->wave) return fail(XLS_EINVAL, "xls_chefsi_wave: the grid is not running in waves");
+  if (wave < 0 || wave >= (int)g->waves.size()) return fail(XLS_EINVAL, "xls_chefsi_wave: wave index out of range");
+  if (!g->ham_set || !g->orb_set) return fail(XLS_EINVAL, "xls_chefsi_wave: Hamiltonian or orbitals not set");
+  for (double& t : g->wave_stage_ms) t = 0.0;
+  int launches = 0;
+  if (g->carry) XLS_TRY(carry_run(g, wave, degree, n_passes, bounds, launches));
+  else XLS_TRY(wave_run(g, wave, degree, n_passes, bounds, false, launches));
+  g->last_launches = launches;
+  return XLS_OK;
+}
+
 xls_status xls_scf_cg_iterations(xls_grid g, long long* iterations_out) {
   if (!g || !iterations_out) return fail(XLS_EINVAL, "xls_scf_cg_iterations: bad arguments");
   *iterations_out = g->scf.cg_iters;
@@ -2210,6 +2456,7 @@ xls_status xls_get_bounds(xls_grid g, double* bounds_out) {
 
 xls_status xls_set_profiling(xls_grid g, int on) {
   if (!g) return fail(XLS_EINVAL, "null grid");
+  if (g->wave && g->carry && g->worker) return xls_set_profiling(g->worker, on);   // the worker's passes
   if (g->wave && on) return not_in_wave_mode("xls_set_profiling");
   g->profiling = on != 0;
   if (g->profiling && g->pev.empty()) {
@@ -2551,6 +2798,7 @@ xls_status xls_set_graphs(xls_grid g, int on) {
 
 xls_status xls_get_kernel_times(xls_grid g, double* ms8_out, int* count8_out) {
   if (!g) return fail(XLS_EINVAL, "null grid");
+  if (g->wave && g->carry && g->worker) return xls_get_kernel_times(g->worker, ms8_out, count8_out);
   for (int c = 0; c < 8; ++c) {
     if (ms8_out) ms8_out[c] = g->kms[c];
     if (count8_out) count8_out[c] = g->kcnt[c];

@@ -177,6 +177,9 @@ void launch_rotate(const SubDev* d_subs, int n_sub, int max_ns, long long max_nd
 template <typename T>
 void launch_core_weights(const SubDev* d_subs, int n_sub, int max_ns, const T* Psi, double* c, cudaStream_t st);
 template <typename T>
+void launch_core_gather(const SubDev* d_subs, int n_sub, int max_ns, const T* Psi, T* store, long long base,
+                        long long per_sub, cudaStream_t st);
+template <typename T>
 void launch_density_occ(const SubDev* d_subs, int n_sub, long long max_core, const T* Psi, const double* occ,
                         const int gn[3], double* rho, cudaStream_t st);
 void launch_dos(const double* lam, const double* c, int n, const double* energies, int n_e, double w, double* out,

@@ -60,6 +60,8 @@ _SIGS = {
     "xls_get_eigs": (c_int, [c_void_p, c_int, c_void_p, c_void_p]),
     "xls_get_subspace": (c_int, [c_void_p, c_int, c_void_p, c_void_p]),
     "xls_get_rotation": (c_int, [c_void_p, c_int, c_void_p]),
+    "xls_wave_carry": (c_int, [c_void_p, c_int]),
+    "xls_chefsi_wave": (c_int, [c_void_p, c_int, c_int, c_int, c_void_p]),
     "xls_dos": (c_int, [c_void_p, c_void_p, c_int, c_double, c_void_p]),
     "xls_scf_cg_iterations": (c_int, [c_void_p, c_void_p]),
     "xls_wave_store_fp16": (c_int, [c_void_p, c_int]),
@@ -246,8 +248,24 @@ def xls_get_eigs(g, sub, n_states):
     return lam, c
 
 
+def xls_get_eigs_into(g, sub, lam, c):
+    """xls_get_eigs into caller-owned contiguous float64 arrays (no allocation per call)."""
+    _check(load().xls_get_eigs(g, int(sub), lam.ctypes.data_as(c_void_p), c.ctypes.data_as(c_void_p)))
+
+
 def xls_wave_store_fp16(g, on=True):
     _check(load().xls_wave_store_fp16(g, 1 if on else 0))
+
+
+def xls_wave_carry(g, slots=-1):
+    """Carry mode with `slots` subdomains per wave (-1: as many as the HBM budget allows; 0: off)."""
+    _check(load().xls_wave_carry(g, int(slots)))
+
+
+def xls_chefsi_wave(g, wave, degree, n_passes=1, bounds=None):
+    b = None if bounds is None else np.ascontiguousarray(bounds, dtype=np.float64).ravel()
+    _check(load().xls_chefsi_wave(g, int(wave), int(degree), int(n_passes),
+                                  None if b is None else b.ctypes.data_as(c_void_p)))
 
 
 def xls_scf_cg_iterations(g):

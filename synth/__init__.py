@@ -205,20 +205,15 @@ def psi0_offsets(w: Workload) -> list:
     return out
 
 
-def veff_erf_wells(w: Workload, r_trunc: float = 8.0) -> np.ndarray:
-    """Stand-in effective potential on the global grid, shape (nz, ny, nx): the sum over atoms
-    of -Zv erf(r/rc)/r (minimum image, truncated at r_trunc), shifted to zero mean.  It has
-    the shape and scale of a self-consistent local potential of the workload and is used as
-    an input wherever the workload's electrostatics are not solved."""
-    n = np.asarray(w.n)
-    h = w.h
-    L = np.asarray(w.L, dtype=np.float64)
-    V = np.zeros((n[2], n[1], n[0]))
+def _erf_wells_slab(args):
+    """Contribution of every atom to the z-planes [z0, z1) of the stand-in potential (atoms in
+    index order, so that each grid value receives its terms in the same order as a serial sum)."""
+    n, h, L, pos, zv, rc, r_trunc, z0, z1 = args
+    from scipy.special import erf as erf_v
+    V = np.zeros((z1 - z0, n[1], n[0]))
     axes = [np.arange(n[d]) * h[d] for d in range(3)]
-    from math import erf
-    erf_v = np.vectorize(erf)
-    for I, R in enumerate(w.pos):
-        sp = w.species[w.species_index[I]]
+    axes[2] = axes[2][z0:z1]
+    for I, R in enumerate(pos):
         idx, dis = [], []
         for d in range(3):
             dd = axes[d] - R[d]
@@ -226,13 +221,40 @@ def veff_erf_wells(w: Workload, r_trunc: float = 8.0) -> np.ndarray:
             m = np.abs(dd) < r_trunc
             idx.append(np.nonzero(m)[0])
             dis.append(dd[m])
+        if idx[2].size == 0:
+            continue
         dz, dy, dx = np.meshgrid(dis[2], dis[1], dis[0], indexing="ij")
         r = np.sqrt(dx * dx + dy * dy + dz * dz)
         r_safe = np.where(r > 1e-12, r, 1.0)
-        v = np.where(r > 1e-12, -sp.Zv * erf_v(r_safe / sp.rc_loc) / r_safe,
-                     -sp.Zv * 2.0 / (math.sqrt(math.pi) * sp.rc_loc))
+        v = np.where(r > 1e-12, -zv[I] * erf_v(r_safe / rc[I]) / r_safe, -zv[I] * 2.0 / (math.sqrt(math.pi) * rc[I]))
         v = np.where(r < r_trunc, v, 0.0)
         V[np.ix_(idx[2], idx[1], idx[0])] += v
+    return V
+
+
+def veff_erf_wells(w: Workload, r_trunc: float = 8.0, processes: int | None = None) -> np.ndarray:
+    """Stand-in effective potential on the global grid, shape (nz, ny, nx): the sum over atoms
+    of -Zv erf(r/rc)/r (minimum image, truncated at r_trunc), shifted to zero mean.  It has
+    the shape and scale of a self-consistent local potential of the workload and is used as
+    an input wherever the workload's electrostatics are not solved.  Large grids are built in
+    z-slabs by a pool of processes (the same values as one process)."""
+    n = np.asarray(w.n)
+    h = w.h
+    L = np.asarray(w.L, dtype=np.float64)
+    zv = np.array([w.species[s].Zv for s in w.species_index], dtype=np.float64)
+    rc = np.array([w.species[s].rc_loc for s in w.species_index], dtype=np.float64)
+    if processes is None:
+        import os
+        processes = min(16, os.cpu_count() or 1) if int(np.prod(n)) * len(w.pos) > 2 ** 31 else 1
+    cuts = np.linspace(0, n[2], max(1, min(processes, n[2])) + 1).astype(int)
+    jobs = [(n, h, L, w.pos, zv, rc, r_trunc, int(cuts[k]), int(cuts[k + 1])) for k in range(len(cuts) - 1)]
+    if len(jobs) == 1:
+        V = _erf_wells_slab(jobs[0])
+    else:
+        import concurrent.futures as cf
+        import multiprocessing as mp
+        with cf.ProcessPoolExecutor(len(jobs), mp_context=mp.get_context("spawn")) as ex:
+            V = np.concatenate(list(ex.map(_erf_wells_slab, jobs)), axis=0)
     return V - V.mean()
 
 
