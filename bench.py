@@ -412,43 +412,18 @@ def si13824_workload(states: str, ncell: int = 12):
     return synth.workload(3, consistent=(states == "consistent"), ncell=ncell)
 
 
-def _near_atoms(w, start, size, margin):
-    """Indices (in order) of the atoms within `margin` of the subdomain box (minimum image)."""
-    h = w.h
-    L = np.asarray(w.L, dtype=np.float64)
-    lo = np.asarray(start) * h
-    hi = (np.asarray(start) + np.asarray(size) - 1) * h
-    c = 0.5 * (lo + hi)
-    half = 0.5 * (hi - lo) + margin
-    d = w.pos - c
-    d -= L * np.round(d / L)
-    return np.nonzero(np.all(np.abs(d) <= half, axis=1))[0]
-
-
 def _oracle_sample(args):
     """One host process: the oracle's CheFSI pass (Lanczos bound, Rayleigh-Ritz of the start
     block, filter, projection, eigensolve, rotation, interior weights) on subdomain `sub` of the
-    13,824-atom cell with the first n_vec start vectors.  The subdomain operator is the oracle's
-    own, built from the atoms near the subdomain (the others have no projector support in it);
-    each of those atoms' projector normalisation is the oracle's, evaluated on one conventional
-    cell that carries the atom at its position modulo the cell (the same grid displacements
-    within r_cut as on the 288^3 grid).  Returns (point-vectors, seconds of the pass)."""
+    13,824-atom cell with the first n_vec start vectors (the oracle's operator of the subdomain
+    from the atoms near it).  Returns (point-vectors, seconds of the pass)."""
     v_path, states, ncell, sub, n_vec = args
     import synth
-    from oracle import chefsi, dc, pseudo
+    from oracle import chefsi, dc
     w = si13824_workload(states, ncell)
     V = np.load(v_path, mmap_mode="r")
     s = dc.partition(w)[sub]
-    near = _near_atoms(w, s.start, s.size, max(sp.r_cut for sp in w.species) + 1.0)
-    a = synth.SI_LATTICE_BOHR
-    cell = synth.Workload("norms", (a, a, a), (synth.POINTS_PER_CELL,) * 3, np.mod(w.pos[near], a),
-                          w.species_index[near], w.species, core_lo=np.zeros((1, 3), int),
-                          core_n=np.full((1, 3), synth.POINTS_PER_CELL), buf=np.zeros((1, 3), int),
-                          n_states=np.array([1]), degree=1, n_passes=1, psi_seed=0)
-    norms = pseudo.projector_norms(cell)
-    local = synth.Workload("near", w.L, w.n, w.pos[near], w.species_index[near], w.species, w.core_lo, w.core_n,
-                           w.buf, w.n_states, w.degree, w.n_passes, w.psi_seed)
-    H = dc.subdomain_operator(local, s, V, norms)
+    H = dc.subdomain_operator_local(w, s, V)
     psi = synth.psi0_block(w.psi_seed, s.N, n_vec, synth.psi0_offsets(w)[sub])
     t0 = time.perf_counter()
     b = chefsi.lanczos_upper_bound(H, synth.lanczos_start(H.N))

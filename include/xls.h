@@ -183,6 +183,15 @@ xls_status xls_get_subspace(xls_grid g, int sub, double* Ms_out, double* Hs_out)
  * Test/readback helper; XLS_EINVAL in wave mode. */
 xls_status xls_get_rotation(xls_grid g, int sub, double* Y_out);
 
+/* Read back the work arrays of subdomain `sub`'s last generalised eigensolve (test/readback
+ * helper, Sec. 5.A.3 step (3)): L_out the Cholesky factor of M_s (lower, N_s x N_s row-major),
+ * A_out the reduced matrix after the tridiagonalisation (the Householder vectors below the
+ * subdiagonal), vecs_out [8*N_s]: the tridiagonal's diagonal, off-diagonal, Householder scalars,
+ * the FP32 bisection estimates of its eigenvalues, the cluster starts (then the cluster count and
+ * the norm estimate).  Any pointer may be NULL.  In wave carry mode: subdomains of the last wave
+ * run; XLS_EINVAL otherwise in wave mode. */
+xls_status xls_get_eig_work(xls_grid g, int sub, double* L_out, double* A_out, double* vecs_out);
+
 /* Read back the (b, a, a0) filter bounds the next pass will use, [3*n_sub]. */
 xls_status xls_get_bounds(xls_grid g, double* bounds_out);
 

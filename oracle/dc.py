@@ -79,6 +79,26 @@ def subdomain_operator(w, s: Subdomain, V: np.ndarray, norms: np.ndarray) -> Sub
     return SubdomainHamiltonian(s.size, w.h, s.periodic, restrict(V, s), proj)
 
 
+def subdomain_operator_local(w, s: Subdomain, V: np.ndarray) -> SubdomainHamiltonian:
+    """subdomain_operator for cells too large to normalise every projector on the whole grid:
+    only the atoms within r_cut + 1 bohr of the subdomain box are kept (the others have no
+    support in it), and each kept atom's normalisation sum runs over one conventional cell of the
+    same spacing carrying the atom at its position modulo the cell -- the grid points within
+    r_cut of the atom form the same set of displacements as on the global grid (r_cut is below
+    half the cell), so the sum has the same terms."""
+    import synth
+    near = synth.near_atoms(w, s.start, s.size, max(sp.r_cut for sp in w.species) + 1.0)
+    a = synth.SI_LATTICE_BOHR
+    cell = synth.Workload("norm_cell", (a, a, a), (synth.POINTS_PER_CELL,) * 3, np.mod(w.pos[near], a),
+                          w.species_index[near], w.species, core_lo=np.zeros((1, 3), int),
+                          core_n=np.full((1, 3), synth.POINTS_PER_CELL), buf=np.zeros((1, 3), int),
+                          n_states=np.array([1]), degree=1, n_passes=1, psi_seed=0)
+    norms = pseudo.projector_norms(cell)
+    local = synth.Workload("near", w.L, w.n, w.pos[near], w.species_index[near], w.species, w.core_lo, w.core_n,
+                           w.buf, w.n_states, w.degree, w.n_passes, w.psi_seed)
+    return subdomain_operator(local, s, V, norms)
+
+
 @dataclass
 class DCResult:
     lam: list

@@ -401,6 +401,16 @@ __global__ void k_tri_clusters(const SubDev* __restrict__ subs, double* vecs) {
 // (b) vectors: CTA (subdomain, group) handles the clusters c = group * blockDim + t (stride
 // gridDim.y * blockDim).  kSmemWork: per-thread work arrays in shared memory, else in the
 // interleaved global scratch.
+//
+// Attempt 0 (fast): two FP32 inverse iterations with an unpivoted LDL^T of T - sigma I, then FP64
+// iterations from that vector (singletons with Rayleigh-quotient shifts).  Every cluster is then
+// checked: each member's Ritz value must lie within 1e-5 |T| of the cluster's bisection range and
+// its residual |T z - lambda z| stay below 1e-9 |T|.  An unpivoted factorisation can lose the
+// iterate when a tiny pivot falls inside the recurrence (the iterate then drifts to another
+// eigenpair, or is noise); a cluster that fails the check is recomputed (attempt 1) in FP64 with
+// Gaussian elimination with partial pivoting of T - sigma I (backward stable for tridiagonal
+// matrices), the bisection shifts held fixed for two iterations before a guarded
+// Rayleigh-quotient step.
 template <bool kSmemWork>
 __global__ void __launch_bounds__(kTriThreads)
 k_tri_eig(const SubDev* __restrict__ subs, double* vecs, double* Zm, double* scratch_all, long long scr_stride,
@@ -423,228 +433,334 @@ k_tri_eig(const SubDev* __restrict__ subs, double* vecs, double* Zm, double* scr
   } else {
     scr = scratch_all + ((long long)blockIdx.x * gridDim.y + blockIdx.y) * scr_stride;
   }
-  // interleaved arrays: lm (n), dinv (n), x (n)
+  // interleaved arrays: lm (n), dinv (n), x (n), u2 (n); the pivoted solve keeps U's diagonal
+  // in dinv, its first and second superdiagonals in lm and u2
   auto LM = [&](int j) -> double& { return scr[(long long)j * T + t]; };
   auto DI = [&](int j) -> double& { return scr[(long long)(n + j) * T + t]; };
   auto X = [&](int j) -> double& { return scr[(long long)(2 * n + j) * T + t]; };
+  auto U2 = [&](int j) -> double& { return scr[(long long)(3 * n + j) * T + t]; };
   const double tiny = 1e-15 * tnorm;
+  // Rayleigh quotient x^T T x / x^T x of the work vector
+  auto rayleigh = [&]() -> double {
+    double rq = 0.0, xx = 0.0, xm = 0.0, x0 = X(0);
+    for (int j = 0; j < n; ++j) {
+      const double xp = (j + 1 < n) ? X(j + 1) : 0.0;
+      double tx = d[j] * x0 + (j + 1 < n ? e[j] * xp : 0.0);
+      if (j > 0) tx += e[j - 1] * xm;
+      rq += x0 * tx;
+      xx += x0 * x0;
+      xm = x0;
+      x0 = xp;
+    }
+    return rq / xx;
+  };
+  // scale by the largest entry (the solves grow entries far beyond the square root of the
+  // range), orthogonalise against the cluster's earlier members, normalise
+  auto finish_iterate = [&](int s, int mbr) {
+    double amax = 0.0;
+    for (int j = 0; j < n; ++j) amax = fmax(amax, fabs(X(j)));
+    if (!(amax > 0.0) || !isfinite(amax)) {   // restart from a fresh vector
+      for (int j = 0; j < n; ++j) X(j) = hash_unit((unsigned)mbr + 7u, (unsigned)j + 1u);
+      amax = 1.0;
+    }
+    const double asc = 1.0 / amax;
+    for (int j = 0; j < n; ++j) X(j) *= asc;
+    for (int pass = 0; pass < 2; ++pass)
+      for (int q = s; q < mbr; ++q) {
+        double dot = 0.0;
+        for (int j = 0; j < n; ++j) dot += Z[(long long)j * n + q] * X(j);
+        for (int j = 0; j < n; ++j) X(j) -= dot * Z[(long long)j * n + q];
+      }
+    double nrm = 0.0;
+    for (int j = 0; j < n; ++j) nrm += X(j) * X(j);
+    nrm = 1.0 / sqrt(nrm);
+    for (int j = 0; j < n; ++j) X(j) *= nrm;
+  };
   for (int c = blockIdx.y * T + t; c < ncl; c += gridDim.y * T) {
     const int s = (int)cst[c], tt = (int)cst[c + 1];
     const int k = tt - s;
-    for (int mbr = s; mbr < tt; ++mbr) {
-      // a singleton refines its shift to the Rayleigh quotient after every solve (Rayleigh
-      // quotient iteration); members of a cluster keep their bisection shifts
-      double sigma = lam32[mbr];
-      bool ok32;
-      // the first two iterations in FP32 (their dependent chains run at FP32 latency; the vector
-      // they give is good to FP32 rounding), the third in FP64 from that vector, with an FP64
-      // Rayleigh-quotient shift for singletons: the FP64 result of three FP64 iterations
-      {
-        float* fs = reinterpret_cast<float*>(scr);   // FP32 arrays in the space of lm / dinv
-        auto LMf = [&](int jj) -> float& { return fs[(long long)jj * T + t]; };
-        auto DIf = [&](int jj) -> float& { return fs[(long long)(n + jj) * T + t]; };
-        auto Xf = [&](int jj) -> float& { return fs[(long long)(2 * n + jj) * T + t]; };
-        const float tiny_f = (float)fmax(1e-7 * tnorm, 1e-30);   // FP32 rounding level of the shift
-        float sig_f = (float)sigma;
-        ok32 = true;
-        for (int jj = 0; jj < n; ++jj) Xf(jj) = (float)hash_unit((unsigned)mbr + 1u, (unsigned)jj);
-        for (int iter = 0; iter < 2; ++iter) {
-          if (iter == 0 || k == 1) {
-            float dp = (float)d[0] - sig_f;
-            if (fabsf(dp) < tiny_f) dp = dp < 0.f ? -tiny_f : tiny_f;
-            DIf(0) = 1.f / dp;
-            for (int jj = 1; jj < n; ++jj) {
-              const float ej = (float)e[jj - 1];
-              const float l = ej * DIf(jj - 1);
-              LMf(jj - 1) = l;
-              dp = ((float)d[jj] - sig_f) - l * ej;
-              if (fabsf(dp) < tiny_f) dp = dp < 0.f ? -tiny_f : tiny_f;
-              DIf(jj) = 1.f / dp;
-            }
-          }
-          float yv = Xf(0);
-          Xf(0) = yv * DIf(0);
-          for (int jj = 1; jj < n; ++jj) {
-            yv = Xf(jj) - LMf(jj - 1) * yv;
-            Xf(jj) = yv * DIf(jj);
-          }
-          float xn = Xf(n - 1);
-          for (int jj = n - 2; jj >= 0; --jj) {
-            xn = Xf(jj) - LMf(jj) * xn;
-            Xf(jj) = xn;
-          }
-          for (int pass = 0; pass < 2; ++pass)
-            for (int q = s; q < mbr; ++q) {
-              float dot = 0.f;
-              for (int jj = 0; jj < n; ++jj) dot += (float)Z[(long long)jj * n + q] * Xf(jj);
-              for (int jj = 0; jj < n; ++jj) Xf(jj) -= dot * (float)Z[(long long)jj * n + q];
-            }
-          float nrm = 0.f;
-          for (int jj = 0; jj < n; ++jj) nrm += Xf(jj) * Xf(jj);
-          if (!(nrm > 0.f) || isinf(nrm)) {   // FP32 range exceeded: redo the member in FP64
-            ok32 = false;
-            break;
-          }
-          nrm = rsqrtf(nrm);
-          for (int jj = 0; jj < n; ++jj) Xf(jj) *= nrm;
-          if (k == 1) {
-            float rq = 0.f, xm = 0.f, x0 = Xf(0);
-            for (int jj = 0; jj < n; ++jj) {
-              const float xp = (jj + 1 < n) ? Xf(jj + 1) : 0.f;
-              float tx = (float)d[jj] * x0 + (jj + 1 < n ? (float)e[jj] * xp : 0.f);
-              if (jj > 0) tx += (float)e[jj - 1] * xm;
-              rq += x0 * tx;
-              xm = x0;
-              x0 = xp;
-            }
-            sig_f = rq;
-          }
-        }
-        for (int jj = 0; jj < n; ++jj) X(jj) = (double)Xf(jj);
-      }
-      int it0 = 2;
-      if (!ok32) {
-        for (int j = 0; j < n; ++j) X(j) = hash_unit((unsigned)mbr + 1u, (unsigned)j);
-        it0 = 0;
-      } else if (k == 1) {   // FP64 Rayleigh quotient of the FP32 vector (error quadratic in the vector's)
-        double rq = 0.0, xx = 0.0, xm = 0.0, x0 = X(0);
-        for (int jj = 0; jj < n; ++jj) {
-          const double xp = (jj + 1 < n) ? X(jj + 1) : 0.0;
-          double tx = d[jj] * x0 + (jj + 1 < n ? e[jj] * xp : 0.0);
-          if (jj > 0) tx += e[jj - 1] * xm;
-          rq += x0 * tx;
-          xx += x0 * x0;
-          xm = x0;
-          x0 = xp;
-        }
-        sigma = rq / xx;
-      }
-      for (int iter = it0; iter < 3; ++iter) {
-        if (iter == it0 || k == 1) {
-          double dp = d[0] - sigma;  // LDL^T of T - sigma I
-          if (fabs(dp) < tiny) dp = dp < 0 ? -tiny : tiny;
-          DI(0) = 1.0 / dp;
-          for (int j = 1; j < n; ++j) {
-            const double l = e[j - 1] * DI(j - 1);   // e / dp through the reciprocal already formed
-            LM(j - 1) = l;
-            dp = (d[j] - sigma) - l * e[j - 1];
-            if (fabs(dp) < tiny) dp = dp < 0 ? -tiny : tiny;
-            DI(j) = 1.0 / dp;
-          }
-        }
-        double y = X(0);                      // forward: L y = b (in place), then z = D^-1 y
-        X(0) = y * DI(0);
-        for (int j = 1; j < n; ++j) {
-          y = X(j) - LM(j - 1) * y;
-          X(j) = y * DI(j);
-        }
-        double xn = X(n - 1);                 // back: L^T x = z
-        for (int j = n - 2; j >= 0; --j) {
-          xn = X(j) - LM(j) * xn;
-          X(j) = xn;
-        }
-        for (int pass = 0; pass < 2; ++pass)
-          for (int q = s; q < mbr; ++q) {
-            double dot = 0.0;
-            for (int j = 0; j < n; ++j) dot += Z[(long long)j * n + q] * X(j);
-            for (int j = 0; j < n; ++j) X(j) -= dot * Z[(long long)j * n + q];
-          }
-        double nrm = 0.0;
-        for (int j = 0; j < n; ++j) nrm += X(j) * X(j);
-        nrm = 1.0 / sqrt(nrm);
-        for (int j = 0; j < n; ++j) X(j) *= nrm;
-        if (k == 1 && iter < 2) {
-          double rq = 0.0, xm = 0.0, x0 = X(0);
-          for (int j = 0; j < n; ++j) {
-            const double xp = (j + 1 < n) ? X(j + 1) : 0.0;
-            double tx = d[j] * x0 + (j + 1 < n ? e[j] * xp : 0.0);
-            if (j > 0) tx += e[j - 1] * xm;
-            rq += x0 * tx;
-            xm = x0;
-            x0 = xp;
-          }
-          sigma = rq;
-        }
-      }
-      for (int j = 0; j < n; ++j) Z[(long long)j * n + mbr] = X(j);
-    }
-    double* Sm = Rb + (long long)s * n;
-    double* Rr = Sm + (long long)k * k;
-    const bool fits = (2LL * k * k <= (long long)k * n) && k <= 64;
-    if (k == 1 || !fits) {
+    for (int attempt = 0; attempt < 2; ++attempt) {
       for (int mbr = s; mbr < tt; ++mbr) {
-        double rq = 0.0;
+        double sigma = lam32[mbr];
+        if (attempt == 0) {
+          // ---- fast path: two FP32 iterations (FP32 latency on the dependent chains), then FP64
+          bool ok32 = true;
+          {
+            // FP32 arrays: element jj of this thread in the low half of the thread's own FP64 slot
+            // of the same array (an FP32 view indexed like the FP64 one would give each float an
+            // address inside another thread's FP64 slots, and the threads run their FP32 and FP64
+            // phases at different times)
+            float* fs = reinterpret_cast<float*>(scr);
+            auto LMf = [&](int jj) -> float& { return fs[2 * ((long long)jj * T + t)]; };
+            auto DIf = [&](int jj) -> float& { return fs[2 * ((long long)(n + jj) * T + t)]; };
+            auto Xf = [&](int jj) -> float& { return fs[2 * ((long long)(2 * n + jj) * T + t)]; };
+            const float tiny_f = (float)fmax(1e-7 * tnorm, 1e-30);   // FP32 rounding level of the shift
+            float sig_f = (float)sigma;
+            for (int jj = 0; jj < n; ++jj) Xf(jj) = (float)hash_unit((unsigned)mbr + 1u, (unsigned)jj);
+            for (int iter = 0; iter < 2; ++iter) {
+              if (iter == 0 || k == 1) {
+                float dp = (float)d[0] - sig_f;
+                if (fabsf(dp) < tiny_f) dp = dp < 0.f ? -tiny_f : tiny_f;
+                DIf(0) = 1.f / dp;
+                for (int jj = 1; jj < n; ++jj) {
+                  const float ej = (float)e[jj - 1];
+                  const float l = ej * DIf(jj - 1);
+                  LMf(jj - 1) = l;
+                  dp = ((float)d[jj] - sig_f) - l * ej;
+                  if (fabsf(dp) < tiny_f) dp = dp < 0.f ? -tiny_f : tiny_f;
+                  DIf(jj) = 1.f / dp;
+                }
+              }
+              float yv = Xf(0);
+              Xf(0) = yv * DIf(0);
+              for (int jj = 1; jj < n; ++jj) {
+                yv = Xf(jj) - LMf(jj - 1) * yv;
+                Xf(jj) = yv * DIf(jj);
+              }
+              float xn = Xf(n - 1);
+              for (int jj = n - 2; jj >= 0; --jj) {
+                xn = Xf(jj) - LMf(jj) * xn;
+                Xf(jj) = xn;
+              }
+              float amax = 0.f;
+              for (int jj = 0; jj < n; ++jj) amax = fmaxf(amax, fabsf(Xf(jj)));
+              if (!(amax > 0.f) || isinf(amax) || isnan(amax)) {   // FP32 range exceeded
+                ok32 = false;
+                break;
+              }
+              const float asc = 1.f / amax;
+              for (int jj = 0; jj < n; ++jj) Xf(jj) *= asc;
+              for (int pass = 0; pass < 2; ++pass)
+                for (int q = s; q < mbr; ++q) {
+                  float dot = 0.f;
+                  for (int jj = 0; jj < n; ++jj) dot += (float)Z[(long long)jj * n + q] * Xf(jj);
+                  for (int jj = 0; jj < n; ++jj) Xf(jj) -= dot * (float)Z[(long long)jj * n + q];
+                }
+              float nrm = 0.f;
+              for (int jj = 0; jj < n; ++jj) nrm += Xf(jj) * Xf(jj);
+              if (!(nrm > 0.f) || isinf(nrm)) {
+                ok32 = false;
+                break;
+              }
+              nrm = rsqrtf(nrm);
+              for (int jj = 0; jj < n; ++jj) Xf(jj) *= nrm;
+              if (k == 1) {
+                float rq = 0.f, xm = 0.f, x0 = Xf(0);
+                for (int jj = 0; jj < n; ++jj) {
+                  const float xp = (jj + 1 < n) ? Xf(jj + 1) : 0.f;
+                  float tx = (float)d[jj] * x0 + (jj + 1 < n ? (float)e[jj] * xp : 0.f);
+                  if (jj > 0) tx += (float)e[jj - 1] * xm;
+                  rq += x0 * tx;
+                  xm = x0;
+                  x0 = xp;
+                }
+                sig_f = rq;
+              }
+            }
+            for (int jj = 0; jj < n; ++jj) X(jj) = (double)Xf(jj);   // Xf(jj) is read before its slot is written
+          }
+          int it0 = 2;
+          if (!ok32) {
+            for (int j = 0; j < n; ++j) X(j) = hash_unit((unsigned)mbr + 1u, (unsigned)j);
+            it0 = 0;
+          } else if (k == 1) {
+            sigma = rayleigh();   // FP64 Rayleigh quotient of the FP32 vector
+          }
+          // members of a cluster take a second FP64 iteration: their shifts are the FP32
+          // bisection values
+          const int iters = k == 1 ? 3 : 4;
+          for (int iter = it0; iter < iters; ++iter) {
+            if (iter == it0 || k == 1) {
+              double dp = d[0] - sigma;  // LDL^T of T - sigma I
+              if (fabs(dp) < tiny) dp = dp < 0 ? -tiny : tiny;
+              DI(0) = 1.0 / dp;
+              for (int j = 1; j < n; ++j) {
+                const double l = e[j - 1] * DI(j - 1);   // e / dp through the reciprocal already formed
+                LM(j - 1) = l;
+                dp = (d[j] - sigma) - l * e[j - 1];
+                if (fabs(dp) < tiny) dp = dp < 0 ? -tiny : tiny;
+                DI(j) = 1.0 / dp;
+              }
+            }
+            double y = X(0);                      // forward: L y = b (in place), then z = D^-1 y
+            X(0) = y * DI(0);
+            for (int j = 1; j < n; ++j) {
+              y = X(j) - LM(j - 1) * y;
+              X(j) = y * DI(j);
+            }
+            double xn = X(n - 1);                 // back: L^T x = z
+            for (int j = n - 2; j >= 0; --j) {
+              xn = X(j) - LM(j) * xn;
+              X(j) = xn;
+            }
+            finish_iterate(s, mbr);
+            if (k == 1 && iter < 2) sigma = rayleigh();
+          }
+        } else {
+          // ---- robust path: FP64 Gaussian elimination with partial pivoting of T - sigma I,
+          // the factorisation and the forward substitution in one sweep (U: diagonal in DI, first
+          // and second superdiagonals in LM and U2), then back substitution
+          for (int j = 0; j < n; ++j) X(j) = hash_unit((unsigned)mbr + 3u, (unsigned)j);
+          for (int iter = 0; iter < 3; ++iter) {
+            if (k == 1 && iter == 2) {   // guarded Rayleigh-quotient shift of a singleton
+              const double rq = rayleigh();
+              if (fabs(rq - lam32[mbr]) <= 1e-5 * tnorm) sigma = rq;
+            }
+            double ak = d[0] - sigma, bk = (n > 1) ? e[0] : 0.0, yk = X(0);
+            for (int j = 0; j + 1 < n; ++j) {
+              const double cj = e[j];
+              const double ak1 = d[j + 1] - sigma, bk1 = (j + 2 < n) ? e[j + 1] : 0.0, yk1 = X(j + 1);
+              if (fabs(ak) >= fabs(cj)) {   // no interchange
+                const double m = ak != 0.0 ? cj / ak : 0.0;
+                DI(j) = ak;
+                LM(j) = bk;
+                U2(j) = 0.0;
+                X(j) = yk;
+                ak = ak1 - m * bk;
+                bk = bk1;
+                yk = yk1 - m * yk;
+              } else {                      // rows j and j + 1 interchanged
+                const double m = ak / cj;
+                DI(j) = cj;
+                LM(j) = ak1;
+                U2(j) = bk1;
+                X(j) = yk1;
+                ak = bk - m * ak1;
+                bk = -m * bk1;
+                yk = yk - m * yk1;
+              }
+            }
+            DI(n - 1) = ak;
+            X(n - 1) = yk;
+            for (int j = n - 1; j >= 0; --j) {
+              double u = DI(j);
+              if (fabs(u) < tiny) u = u < 0.0 ? -tiny : tiny;
+              double r = X(j);
+              if (j + 1 < n) r -= LM(j) * X(j + 1);
+              if (j + 2 < n) r -= U2(j) * X(j + 2);
+              X(j) = r / u;
+            }
+            finish_iterate(s, mbr);
+          }
+        }
+        for (int j = 0; j < n; ++j) Z[(long long)j * n + mbr] = X(j);
+      }
+      // Rayleigh-Ritz inside the cluster, in pieces of at most 64 members (a longer run of close
+      // eigenvalues is cut at its largest gaps; its vectors are orthogonal across the whole run)
+      for (int ps = s; ps < tt;) {
+        int pt = tt;
+        if (tt - ps > 64) {
+          double best = -1.0;
+          for (int p = ps + 16; p <= ps + 64; ++p)
+            if (lam32[p] - lam32[p - 1] > best) {
+              best = lam32[p] - lam32[p - 1];
+              pt = p;
+            }
+        }
+        const int kp = pt - ps, sp = ps;
+        ps = pt;
+        double* Sm = Rb + (long long)sp * n;
+        double* Rr = Sm + (long long)kp * kp;
+        const bool fits = (2LL * kp * kp <= (long long)kp * n) && kp <= 64;
+        if (kp == 1 || !fits) {
+          for (int mbr = sp; mbr < pt; ++mbr) {
+            double rq = 0.0;
+            for (int j = 0; j < n; ++j) {
+              double tx = d[j] * Z[(long long)j * n + mbr];
+              if (j > 0) tx += e[j - 1] * Z[(long long)(j - 1) * n + mbr];
+              if (j + 1 < n) tx += e[j] * Z[(long long)(j + 1) * n + mbr];
+              rq += Z[(long long)j * n + mbr] * tx;
+            }
+            lam_out[S.off_state + mbr] = rq;
+          }
+          continue;
+        }
+        for (int a = 0; a < kp; ++a)
+          for (int b = a; b < kp; ++b) {
+            double acc = 0.0;
+            for (int j = 0; j < n; ++j) {
+              double tx = d[j] * Z[(long long)j * n + sp + b];
+              if (j > 0) tx += e[j - 1] * Z[(long long)(j - 1) * n + sp + b];
+              if (j + 1 < n) tx += e[j] * Z[(long long)(j + 1) * n + sp + b];
+              acc += Z[(long long)j * n + sp + a] * tx;
+            }
+            Sm[a * kp + b] = acc;
+            Sm[b * kp + a] = acc;
+          }
+        for (int a = 0; a < kp; ++a)
+          for (int b = 0; b < kp; ++b) Rr[a * kp + b] = (a == b) ? 1.0 : 0.0;
+        for (int sweep = 0; sweep < 30; ++sweep) {
+          double off = 0.0, tot = 0.0;
+          for (int a = 0; a < kp; ++a)
+            for (int b = 0; b < kp; ++b) {
+              tot += Sm[a * kp + b] * Sm[a * kp + b];
+              if (a != b) off += Sm[a * kp + b] * Sm[a * kp + b];
+            }
+          if (off <= 1e-30 * tot || off == 0.0) break;
+          for (int p = 0; p < kp - 1; ++p)
+            for (int q = p + 1; q < kp; ++q) {
+              const double apq = Sm[p * kp + q];
+              if (apq == 0.0) continue;
+              const double theta = (Sm[q * kp + q] - Sm[p * kp + p]) / (2.0 * apq);
+              const double tq = copysign(1.0, theta) / (fabs(theta) + sqrt(theta * theta + 1.0));
+              const double cs = 1.0 / sqrt(tq * tq + 1.0), sn = tq * cs;
+              for (int r = 0; r < kp; ++r) {
+                const double a1 = Sm[r * kp + p], a2 = Sm[r * kp + q];
+                Sm[r * kp + p] = cs * a1 - sn * a2;
+                Sm[r * kp + q] = sn * a1 + cs * a2;
+              }
+              for (int r = 0; r < kp; ++r) {
+                const double a1 = Sm[p * kp + r], a2 = Sm[q * kp + r];
+                Sm[p * kp + r] = cs * a1 - sn * a2;
+                Sm[q * kp + r] = sn * a1 + cs * a2;
+              }
+              for (int r = 0; r < kp; ++r) {
+                const double rp = Rr[r * kp + p], rq = Rr[r * kp + q];
+                Rr[r * kp + p] = cs * rp - sn * rq;
+                Rr[r * kp + q] = sn * rp + cs * rq;
+              }
+            }
+        }
+        int order[64];
+        for (int a = 0; a < kp; ++a) order[a] = a;
+        for (int a = 0; a < kp; ++a)
+          for (int b = a + 1; b < kp; ++b)
+            if (Sm[order[b] * kp + order[b]] < Sm[order[a] * kp + order[a]]) {
+              const int tmp = order[a];
+              order[a] = order[b];
+              order[b] = tmp;
+            }
         for (int j = 0; j < n; ++j) {
-          double tx = d[j] * Z[(long long)j * n + mbr];
+          double row[64];
+          for (int b = 0; b < kp; ++b) {
+            double acc = 0.0;
+            for (int a = 0; a < kp; ++a) acc += Z[(long long)j * n + sp + a] * Rr[a * kp + order[b]];
+            row[b] = acc;
+          }
+          for (int b = 0; b < kp; ++b) Z[(long long)j * n + sp + b] = row[b];
+        }
+        for (int b = 0; b < kp; ++b) lam_out[S.off_state + sp + b] = Sm[order[b] * kp + order[b]];
+      }
+      // check of the cluster: Ritz values within the bisection range, small residuals
+      bool ok = true;
+      const double lo = lam32[s] - 1e-5 * tnorm, hi = lam32[tt - 1] + 1e-5 * tnorm;
+      for (int mbr = s; mbr < tt && ok; ++mbr) {
+        const double lm = lam_out[S.off_state + mbr];
+        if (!(lm >= lo && lm <= hi)) {
+          ok = false;
+          break;
+        }
+        double r2 = 0.0;
+        for (int j = 0; j < n; ++j) {
+          double tx = (d[j] - lm) * Z[(long long)j * n + mbr];
           if (j > 0) tx += e[j - 1] * Z[(long long)(j - 1) * n + mbr];
           if (j + 1 < n) tx += e[j] * Z[(long long)(j + 1) * n + mbr];
-          rq += Z[(long long)j * n + mbr] * tx;
+          r2 += tx * tx;
         }
-        lam_out[S.off_state + mbr] = rq;
+        if (!(sqrt(r2) <= 1e-9 * tnorm)) ok = false;
       }
-      continue;
+      if (ok) break;
     }
-    for (int a = 0; a < k; ++a)
-      for (int b = a; b < k; ++b) {
-        double acc = 0.0;
-        for (int j = 0; j < n; ++j) {
-          double tx = d[j] * Z[(long long)j * n + s + b];
-          if (j > 0) tx += e[j - 1] * Z[(long long)(j - 1) * n + s + b];
-          if (j + 1 < n) tx += e[j] * Z[(long long)(j + 1) * n + s + b];
-          acc += Z[(long long)j * n + s + a] * tx;
-        }
-        Sm[a * k + b] = acc;
-        Sm[b * k + a] = acc;
-      }
-    for (int a = 0; a < k; ++a)
-      for (int b = 0; b < k; ++b) Rr[a * k + b] = (a == b) ? 1.0 : 0.0;
-    for (int sweep = 0; sweep < 30; ++sweep) {
-      double off = 0.0, tot = 0.0;
-      for (int a = 0; a < k; ++a)
-        for (int b = 0; b < k; ++b) {
-          tot += Sm[a * k + b] * Sm[a * k + b];
-          if (a != b) off += Sm[a * k + b] * Sm[a * k + b];
-        }
-      if (off <= 1e-30 * tot || off == 0.0) break;
-      for (int p = 0; p < k - 1; ++p)
-        for (int q = p + 1; q < k; ++q) {
-          const double apq = Sm[p * k + q];
-          if (apq == 0.0) continue;
-          const double theta = (Sm[q * k + q] - Sm[p * k + p]) / (2.0 * apq);
-          const double tq = copysign(1.0, theta) / (fabs(theta) + sqrt(theta * theta + 1.0));
-          const double cs = 1.0 / sqrt(tq * tq + 1.0), sn = tq * cs;
-          for (int r = 0; r < k; ++r) {
-            const double sp = Sm[r * k + p], sq = Sm[r * k + q];
-            Sm[r * k + p] = cs * sp - sn * sq;
-            Sm[r * k + q] = sn * sp + cs * sq;
-          }
-          for (int r = 0; r < k; ++r) {
-            const double sp = Sm[p * k + r], sq = Sm[q * k + r];
-            Sm[p * k + r] = cs * sp - sn * sq;
-            Sm[q * k + r] = sn * sp + cs * sq;
-          }
-          for (int r = 0; r < k; ++r) {
-            const double rp = Rr[r * k + p], rq = Rr[r * k + q];
-            Rr[r * k + p] = cs * rp - sn * rq;
-            Rr[r * k + q] = sn * rp + cs * rq;
-          }
-        }
-    }
-    int order[64];
-    for (int a = 0; a < k; ++a) order[a] = a;
-    for (int a = 0; a < k; ++a)
-      for (int b = a + 1; b < k; ++b)
-        if (Sm[order[b] * k + order[b]] < Sm[order[a] * k + order[a]]) { const int tmp = order[a]; order[a] = order[b]; order[b] = tmp; }
-    for (int j = 0; j < n; ++j) {
-      double row[64];
-      for (int b = 0; b < k; ++b) {
-        double acc = 0.0;
-        for (int a = 0; a < k; ++a) acc += Z[(long long)j * n + s + a] * Rr[a * k + order[b]];
-        row[b] = acc;
-      }
-      for (int b = 0; b < k; ++b) Z[(long long)j * n + s + b] = row[b];
-    }
-    for (int b = 0; b < k; ++b) lam_out[S.off_state + s + b] = Sm[order[b] * k + order[b]];
   }
 }
 
@@ -891,14 +1007,14 @@ void launch_eig(const SubDev* d_subs, int n_sub, int max_ns, double* Ms, double*
     // CTA, spreading the clusters over more SMs, measured no faster: the longest cluster's
     // dependent FP64 chain sets the time)
     constexpr int kVecThreads = 32;
-    const size_t per_thread = 3 * (size_t)max_ns * sizeof(double);
+    const size_t per_thread = 4 * (size_t)max_ns * sizeof(double);
     const int groups = (max_ns + kVecThreads - 1) / kVecThreads;
     if (per_thread * kVecThreads <= 200 * 1024 && smem_ok(k_tri_eig<true>, per_thread * kVecThreads)) {
       dim3 gv(n_sub, groups);
       k_tri_eig<true><<<gv, kVecThreads, per_thread * kVecThreads, st>>>(d_subs, vecs, W, scratch, 0, R, lam, max_ns);
     } else {
       dim3 gv(n_sub, 1);
-      k_tri_eig<false><<<gv, kTriThreads, 0, st>>>(d_subs, vecs, W, scratch, 3LL * max_ns * kTriThreads, R, lam,
+      k_tri_eig<false><<<gv, kTriThreads, 0, st>>>(d_subs, vecs, W, scratch, 4LL * max_ns * kTriThreads, R, lam,
                                                    max_ns);
     }
   }
@@ -912,6 +1028,6 @@ void launch_eig(const SubDev* d_subs, int n_sub, int max_ns, double* Ms, double*
   trsm(true, max_ns, gt, d_subs, Ms, W, 0, Y, st, cluster != 0);     // Y = L^-T Z
 }
 
-size_t eig_scratch_doubles(int n_sub, int max_ns) { return (size_t)n_sub * kTriThreads * 3 * max_ns; }
+size_t eig_scratch_doubles(int n_sub, int max_ns) { return (size_t)n_sub * kTriThreads * 4 * max_ns; }
 
 }  // namespace xls

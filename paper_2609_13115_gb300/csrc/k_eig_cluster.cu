@@ -676,13 +676,11 @@ bool launch_cholesky_cluster(const SubDev* d_subs, int n_sub, int max_ns, double
 bool launch_tridiag_cluster(const SubDev* d_subs, int n_sub, int max_ns, double* A, double* vecs, int cl_first,
                             cudaStream_t st) {
   size_t smem = 0;
-  // one barrier per column: partials [2][8][n], pivot rows [2][n], v, w, p
-  // k_tridiag_cl2 on 8-CTA clusters; 16-CTA clusters (only where 8 do not fit) take k_tridiag_cl1:
-  // k_tridiag_cl2 on 16 CTAs ended a bench run with a non-positive-definite Gram matrix in the next
-  // pass (cause not found), k_tridiag_cl1 on 16 CTAs passes every test
+  // one barrier per column: partials [2][CL][n], pivot rows [2][n], v, w, p (k_tridiag_cl2; the
+  // two-barrier k_tridiag_cl1 with XLS_TRIDIAG_CL1=1)
   for (int CL : {cl_first == 16 ? 16 : 8, cl_first == 16 ? 8 : 16}) {
     const size_t exact = ((size_t)(max_ns + CL - 1) / CL * max_ns + (2 * (size_t)CL + 5) * max_ns) * sizeof(double);
-    const bool cl2 = CL <= 8 && !std::getenv("XLS_TRIDIAG_CL1");
+    const bool cl2 = !std::getenv("XLS_TRIDIAG_CL1");
     if (exact <= 200 * 1024 && launch_cluster(cl2 ? k_tridiag_cl2 : k_tridiag_cl1, n_sub, CL, exact, st, d_subs, A, vecs,
                                               true))
       return true;

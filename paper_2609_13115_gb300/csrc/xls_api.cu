@@ -95,6 +95,7 @@ struct xls_grid_s {
   SubDev* d_core_subs = nullptr;
   std::vector<double> carry_ab;      // (a, a0) of every worker slot after its last pass
   std::vector<char> wave_ran;        // waves that have run since the orbitals were set
+  int carry_last = -1;               // the wave the worker holds (its last run)
   // geometry of the last xls_hamiltonian_set (for the pseudocharge of the SCF step)
   std::vector<double> atom_pos;
   std::vector<int> atom_sp;
@@ -1241,6 +1242,8 @@ xls_status create_grid(const xls_cell* cell, const xls_dc* dc, int precision, si
   {
     const char* env = std::getenv("XLS_EIG");
     g->eig_cluster = !(env && std::string(env) == "single");
+    const char* ecl = std::getenv("XLS_EIG_CL");   // cluster size tried first (xls_autotune changes it)
+    if (ecl && std::atoi(ecl) == 16) g->eig_cl = 16;
   }
   if (precision != XLS_FP64) {
     const char* env = std::getenv("XLS_GEMM");
@@ -1475,8 +1478,14 @@ xls_status wave_orbitals_set(xls_grid g, int sub, const double* psi, int on_devi
   return XLS_OK;
 }
 
+int carry_slot(xls_grid g, int sub);
+
 xls_status wave_orbitals_get(xls_grid g, int sub, double* out, int on_device) {
-  if (g->carry) return fail(XLS_EINVAL, "xls_orbitals_get: wave carry mode keeps no orbital store");
+  if (g->carry) {
+    const int j = carry_slot(g, sub);
+    if (j < 0) return fail(XLS_EINVAL, "xls_orbitals_get: in wave carry mode only the subdomains of the last wave run");
+    return xls_orbitals_get(g->worker, j, out, on_device);
+  }
   XLS_TRY(ensure_store(g));
   XLS_TRY(ensure_stage(g));
   const SubDev& S = g->subs[sub];
@@ -1595,6 +1604,13 @@ xls_status carry_retarget(xls_grid g, int first) {
                              (int)g->species.size(), g->species.empty() ? nullptr : g->species.data());
 }
 
+// the worker slot holding subdomain `sub` (carry mode: only the subdomains of the wave it ran last)
+int carry_slot(xls_grid g, int sub) {
+  if (!g->carry || !g->worker || g->carry_last < 0) return -1;
+  const int first = g->waves[g->carry_last].first, cnt = g->waves[g->carry_last].second;
+  return (sub >= first && sub < first + cnt) ? sub - first : -1;
+}
+
 xls_status carry_orbitals_random(xls_grid g, uint64_t seed) {
   xls_grid k = g->worker;
   // the stream values of the first wave's subdomains (blocks concatenated in subdomain order)
@@ -1619,6 +1635,7 @@ xls_status carry_run(xls_grid g, int w, int degree, int n_passes, const double* 
   xls_grid k = g->worker;
   const int first = g->waves[w].first, cnt = g->waves[w].second;
   XLS_TRY(carry_retarget(g, first));
+  g->carry_last = w;   // the worker's slots now hold this wave's subdomains
   k->orb_set = true;
   std::vector<double> bw;
   const double* bp = nullptr;
@@ -2425,6 +2442,7 @@ xls_status xls_dos(xls_grid g, const double* energies, int n_energies, double wi
 
 xls_status xls_get_subspace(xls_grid g, int sub, double* Ms_out, double* Hs_out) {
   if (!g || sub < 0 || sub >= g->n_sub) return fail(XLS_EINVAL, "xls_get_subspace: bad arguments");
+  if (g->wave && carry_slot(g, sub) >= 0) return xls_get_subspace(g->worker, carry_slot(g, sub), Ms_out, Hs_out);
   if (g->wave) return not_in_wave_mode("xls_get_subspace");
   const SubDev& S = g->subs[sub];
   XLS_CUDA(cudaStreamSynchronize(g->st));
@@ -2436,10 +2454,25 @@ xls_status xls_get_subspace(xls_grid g, int sub, double* Ms_out, double* Hs_out)
 
 xls_status xls_get_rotation(xls_grid g, int sub, double* Y_out) {
   if (!g || !Y_out || sub < 0 || sub >= g->n_sub) return fail(XLS_EINVAL, "xls_get_rotation: bad arguments");
+  if (g->wave && carry_slot(g, sub) >= 0) return xls_get_rotation(g->worker, carry_slot(g, sub), Y_out);
   if (g->wave) return not_in_wave_mode("xls_get_rotation");
   const SubDev& S = g->subs[sub];
   XLS_CUDA(cudaStreamSynchronize(g->st));
   XLS_CUDA(cudaMemcpy(Y_out, g->Y + S.off_ss, (size_t)S.ns * S.ns * sizeof(double), cudaMemcpyDeviceToHost));
+  return XLS_OK;
+}
+
+xls_status xls_get_eig_work(xls_grid g, int sub, double* L_out, double* A_out, double* vecs_out) {
+  if (!g || sub < 0 || sub >= g->n_sub) return fail(XLS_EINVAL, "xls_get_eig_work: bad arguments");
+  if (g->wave && carry_slot(g, sub) >= 0) return xls_get_eig_work(g->worker, carry_slot(g, sub), L_out, A_out, vecs_out);
+  if (g->wave) return not_in_wave_mode("xls_get_eig_work");
+  const SubDev& S = g->subs[sub];
+  XLS_CUDA(cudaStreamSynchronize(g->st));
+  const size_t b = (size_t)S.ns * S.ns * sizeof(double);
+  if (L_out) XLS_CUDA(cudaMemcpy(L_out, g->Lb + S.off_ss, b, cudaMemcpyDeviceToHost));
+  if (A_out) XLS_CUDA(cudaMemcpy(A_out, g->Ab + S.off_ss, b, cudaMemcpyDeviceToHost));
+  if (vecs_out) XLS_CUDA(cudaMemcpy(vecs_out, g->vecs + 8LL * S.off_state, 8 * (size_t)S.ns * sizeof(double),
+                                    cudaMemcpyDeviceToHost));
   return XLS_OK;
 }
 

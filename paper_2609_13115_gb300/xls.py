@@ -60,6 +60,7 @@ _SIGS = {
     "xls_get_eigs": (c_int, [c_void_p, c_int, c_void_p, c_void_p]),
     "xls_get_subspace": (c_int, [c_void_p, c_int, c_void_p, c_void_p]),
     "xls_get_rotation": (c_int, [c_void_p, c_int, c_void_p]),
+    "xls_get_eig_work": (c_int, [c_void_p, c_int, c_void_p, c_void_p, c_void_p]),
     "xls_wave_carry": (c_int, [c_void_p, c_int]),
     "xls_chefsi_wave": (c_int, [c_void_p, c_int, c_int, c_int, c_void_p]),
     "xls_dos": (c_int, [c_void_p, c_void_p, c_int, c_double, c_void_p]),
@@ -293,6 +294,16 @@ def xls_get_rotation(g, sub, n_states):
     Y = np.zeros((n_states, n_states))
     _check(load().xls_get_rotation(g, int(sub), Y.ctypes.data_as(c_void_p)))
     return Y
+
+
+def xls_get_eig_work(g, sub, n_states):
+    """(L, A after tridiagonalisation, vecs[8, n]) of the last eigensolve of subdomain `sub`."""
+    L = np.zeros((n_states, n_states))
+    A = np.zeros((n_states, n_states))
+    v = np.zeros(8 * n_states)
+    _check(load().xls_get_eig_work(g, int(sub), L.ctypes.data_as(c_void_p), A.ctypes.data_as(c_void_p),
+                                   v.ctypes.data_as(c_void_p)))
+    return L, A, v.reshape(8, n_states)
 
 
 def xls_get_bounds(g, n_sub):

@@ -183,6 +183,20 @@ def workload(cfg: int, consistent: bool = True, ncell: int | None = None) -> Wor
     raise ValueError(f"unknown workload {cfg}")
 
 
+def near_atoms(w: Workload, start, size, margin: float) -> np.ndarray:
+    """Indices (in order) of the atoms within `margin` of the box of grid points start .. start +
+    size - 1 (minimum image): the atoms that can meet a subdomain of that box."""
+    h = w.h
+    L = np.asarray(w.L, dtype=np.float64)
+    lo = np.asarray(start) * h
+    hi = (np.asarray(start) + np.asarray(size) - 1) * h
+    c = 0.5 * (lo + hi)
+    half = 0.5 * (hi - lo) + margin
+    d = w.pos - c
+    d -= L * np.round(d / L)
+    return np.nonzero(np.all(np.abs(d) <= half, axis=1))[0]
+
+
 def psi0_block(seed: int, n_points: int, n_states: int, offset: int = 0) -> np.ndarray:
     """Start block of one subdomain: (n_states, n_points), vector-major, U[-0.5, 0.5)."""
     u = uniform_pm_half(seed, n_points * n_states, offset)

@@ -52,7 +52,7 @@ def oracle_carry(w, V, slots, cycles):
                 a = first + j
                 H = ops[a]
                 b = chefsi.lanczos_upper_bound(H, synth.lanczos_start(H.N))
-                prev = own[a] if own[a] is not None else slot_lam[j]
+                prev = own[a][0] if own[a] is not None else slot_lam[j]
                 if prev is None:
                     prev = chefsi.ritz_values(H, slot_psi[j])
                 lam, P = chefsi.chefsi_pass(H, slot_psi[j], w.degree, float(prev.max()), b, float(prev.min()))
@@ -75,7 +75,7 @@ def test_carry_waves_match_oracle_schedule(prec):
     V = pseudo.local_potential(w)
     slots, cycles = 2, 3
     lam_o, mu_o, rho_o, eb_o, es_o = oracle_carry(w, V, slots, cycles)
-    budget = (1 << 26) + 30 * (1 << 20)          # below the footprint of all eight subdomains
+    budget = (1 << 26) + 20 * (1 << 20)          # below the footprint of all eight subdomains
     with xls.Grid(w, prec, hbm_budget_bytes=budget) as g:
         g.set_hamiltonian(V)
         n_waves, _ = xls.xls_get_waves(g.h, w.n_sub)
@@ -111,20 +111,21 @@ def test_carry_waves_match_oracle_schedule(prec):
 def test_carry_mode_rejects_what_it_cannot_do():
     w = dirichlet_cell()
     V = pseudo.local_potential(w)
-    with xls.Grid(w, xls.XLS_FP64, hbm_budget_bytes=(1 << 26) + 30 * (1 << 20)) as g:
+    with xls.Grid(w, xls.XLS_FP64, hbm_budget_bytes=(1 << 26) + 20 * (1 << 20)) as g:
         g.set_hamiltonian(V)
         with pytest.raises(xls.XlsError) as e:
             xls.xls_wave_carry(g.h, 3)                   # does not divide 8
         assert e.value.status == xls.XLS_EINVAL
-        xls.xls_wave_carry(g.h, 4)
+        xls.xls_wave_carry(g.h, 2)
         with pytest.raises(xls.XlsError) as e:
             xls.xls_orbitals_set(g.h, 0, np.zeros((16, 18 ** 3)))
         assert e.value.status == xls.XLS_EINVAL
+        xls.xls_orbitals_random(g.h, w.psi_seed)
         with pytest.raises(xls.XlsError):
-            xls.xls_chefsi_wave(g.h, 5, w.degree, 1)     # only two waves
+            xls.xls_chefsi_wave(g.h, 5, w.degree, 1)     # only four waves
     u = dirichlet_cell()
     u.n_states = np.array([16, 16, 16, 16, 16, 16, 16, 24])
-    with xls.Grid(u, xls.XLS_FP64, hbm_budget_bytes=(1 << 26) + 30 * (1 << 20)) as g:
+    with xls.Grid(u, xls.XLS_FP64, hbm_budget_bytes=(1 << 26) + 20 * (1 << 20)) as g:
         with pytest.raises(xls.XlsError) as e:
             xls.xls_wave_carry(g.h, 2)                   # unequal shapes
         assert e.value.status == xls.XLS_EINVAL

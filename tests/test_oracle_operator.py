@@ -166,3 +166,19 @@ def test_restriction_wraps_periodically():
     for s in subs:
         seen[dc.core_global_indices(s, n)] += 1
     assert (seen == 1).all()
+
+
+def test_local_subdomain_operator_equals_global_one():
+    """The operator built from the atoms near a subdomain, with projector norms summed on one
+    conventional cell, equals the operator with norms summed on the whole periodic grid."""
+    from oracle import dc
+    w = synth.workload(1)
+    V = synth.veff_erf_wells(w)
+    subs = dc.partition(w)
+    norms = pseudo.projector_norms(w)
+    x = synth.psi0_block(5, subs[3].N, 2)
+    H_glob = dc.subdomain_operator(w, subs[3], V, norms)
+    H_loc = dc.subdomain_operator_local(w, subs[3], V)
+    assert len(H_loc.projectors) == len(H_glob.projectors)
+    y0, y1 = H_glob.apply(x), H_loc.apply(x)
+    assert np.abs(y1 - y0).max() < 1e-13 * np.abs(y0).max()
