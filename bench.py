@@ -42,7 +42,7 @@ UNIT = "Gpt*vec/s"
 def parse_args():
     p = argparse.ArgumentParser()
     p.add_argument("--gpus", type=int, default=1)
-    p.add_argument("--steps", type=int, default=30)
+    p.add_argument("--steps", type=int, default=24)
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
     p.add_argument("--precision", default="fp16", choices=["fp16", "bf16", "fp64"],
@@ -57,7 +57,7 @@ def parse_args():
     p.add_argument("--states", default="consistent", choices=["consistent", "literal"],
                    help="si13824: 528 states per subdomain (consistent) or 240 (literal count, timing only)")
     p.add_argument("--budget-gb", type=float, default=250.0, help="si13824: HBM budget of the wave grid")
-    p.add_argument("--fp64-cycles", type=int, default=3,
+    p.add_argument("--fp64-cycles", type=int, default=1,
                    help="si13824: carry cycles of the FP64 and mixed forms on the 512-atom crystal of the same "
                         "subdomain geometry (mixed-vs-FP64 factor and energy difference); 0 skips")
     p.add_argument("--sample-vectors", type=int, default=16, help="si13824: vectors per oracle sample pass")
