@@ -258,16 +258,23 @@ k_proj_fill(const SubDev* __restrict__ subs, const ProjSlot* __restrict__ slots,
 // w / kVH; a lane two points at a time (16 loads in flight); lanes (transpose reduction) and
 // warps are reduced at the end.
 constexpr int kPV = 8;
+constexpr int kPChunk = 32;   // slots per chunk of the projection's CTA order
 constexpr int kVH = kPV / 8, kPH = 8 / kVH;   // vector halves and point phases of the 8 warps
 
 template <typename T>
 __global__ void __launch_bounds__(256)
 k_nl_project(const SubDev* __restrict__ subs, const ProjSlot* __restrict__ slots, int slot_off, int n_slot,
-             const int* __restrict__ idx, const typename Vec4<T>::type* __restrict__ chi, const T* __restrict__ Y,
-             double* __restrict__ P) {
+             int n_groups, const int* __restrict__ idx, const typename Vec4<T>::type* __restrict__ chi,
+             const T* __restrict__ Y, double* __restrict__ P) {
   using T4 = typename Vec4<T>::type;
   __shared__ T red[kPH][kPV * 4];
-  const int slot = slot_off + (int)(blockIdx.x % n_slot), grp = blockIdx.x / n_slot;
+  // CTAs walk the slots in chunks of kPChunk: every vector group runs over the chunk before the
+  // next chunk starts, so the chunk's tables stay in L2 for all groups while the Y values of the
+  // chunk's supports (neighbouring atoms share points) are gathered once per group
+  const int chunk = (int)(blockIdx.x / (kPChunk * n_groups)), rem = (int)(blockIdx.x % (kPChunk * n_groups));
+  const int grp = rem / kPChunk, sic = chunk * kPChunk + rem % kPChunk;
+  if (sic >= n_slot) return;
+  const int slot = slot_off + sic;
   const ProjSlot& A = slots[slot];
   const SubDev& S = subs[A.sub];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -398,29 +405,188 @@ __global__ void k_rcsr_fill(const SubDev* __restrict__ subs, const ProjSlot* __r
   }
 }
 
-constexpr int kBackPts = 2048, kBackVec = 8;
+constexpr int kBackVec = 8;
 constexpr int kBackRow = kBackVec + 1;   // padded slot row of Q (consecutive slots in different bank groups)
+constexpr int kLocBits = 32768;          // slots per subdomain the localisation handles (bitmap in shared memory)
+
+// One CTA per point block: mark the slots named by the block's reverse-table rows in a bitmap;
+// pass 0 stores their number, pass 1 replaces every entry's slot by its rank among the marked
+// slots (ascending slot order, so the ranks do not depend on the order of the entries) and lists
+// the marked slots in that order.
+__global__ void __launch_bounds__(256)
+k_rcsr_localize(const SubDev* __restrict__ subs, const int* __restrict__ blk_sub, const long long* __restrict__ row_ptr,
+                int* rslot, int* blk_cnt, int* blk_list, int list_max, int pass) {
+  __shared__ unsigned bits[kLocBits / 32];
+  __shared__ int wpre[kLocBits / 32];
+  const int b = blockIdx.x;
+  const SubDev& S = subs[blk_sub[b]];
+  const int nw = (S.slot_n + 31) / 32;
+  const long long p0 = (long long)(b - S.off_nlb) * kBackPts;
+  const long long p1 = min(S.nd, p0 + kBackPts);
+  const long long e0 = row_ptr[S.off_pt + p0], e1 = row_ptr[S.off_pt + p1];
+  for (int w = threadIdx.x; w < nw; w += blockDim.x) bits[w] = 0u;
+  __syncthreads();
+  for (long long e = e0 + threadIdx.x; e < e1; e += blockDim.x) {
+    const int sl = rslot[e];
+    atomicOr(&bits[sl >> 5], 1u << (sl & 31));
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {   // exclusive prefix of the words' populations (at most 1024 words)
+    int acc = 0;
+    for (int w = 0; w < nw; ++w) {
+      wpre[w] = acc;
+      acc += __popc(bits[w]);
+    }
+    if (pass == 0) blk_cnt[b] = acc;
+  }
+  __syncthreads();
+  if (pass == 0) return;
+  for (long long e = e0 + threadIdx.x; e < e1; e += blockDim.x) {
+    const int sl = rslot[e];
+    rslot[e] = wpre[sl >> 5] + __popc(bits[sl >> 5] & ((1u << (sl & 31)) - 1u));
+  }
+  for (int w = threadIdx.x; w < nw; w += blockDim.x) {
+    unsigned m = bits[w];
+    int r = wpre[w];
+    while (m) {
+      const int bit = __ffs(m) - 1;
+      if (r < list_max) blk_list[(long long)b * list_max + r] = w * 32 + bit;
+      ++r;
+      m &= m - 1u;
+    }
+  }
+}
+
+// ---- exclusive prefix sum of the reverse-table row counts on the device: rp[i] = sum_{j<i} cnt[j],
+// rp[n] = the total (three launches: block sums, one-block scan of the block sums, block scans) ----
+constexpr int kScanT = 256, kScanPer = 8, kScanBlk = kScanT * kScanPer;
+
+__global__ void __launch_bounds__(kScanT) k_scan_blocksum(const int* __restrict__ cnt, long long n, long long* bsum) {
+  __shared__ long long red[kScanT / 32];
+  const long long base = (long long)blockIdx.x * kScanBlk;
+  long long acc = 0;
+  for (int k = 0; k < kScanPer; ++k) {
+    const long long i = base + (long long)k * kScanT + threadIdx.x;
+    if (i < n) acc += cnt[i];
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    long long t = 0;
+    for (int w = 0; w < kScanT / 32; ++w) t += red[w];
+    bsum[blockIdx.x] = t;
+  }
+}
+
+// one CTA: exclusive scan of the nb block sums in place, the total in bsum[nb]
+__global__ void __launch_bounds__(1024) k_scan_blocks(long long* bsum, int nb) {
+  __shared__ long long wsum[32];
+  __shared__ long long carry;
+  if (threadIdx.x == 0) carry = 0;
+  __syncthreads();
+  for (int c0 = 0; c0 < nb; c0 += 1024) {
+    const int i = c0 + threadIdx.x;
+    const long long x = i < nb ? bsum[i] : 0;
+    long long v = x;   // inclusive warp scan
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const long long y = __shfl_up_sync(0xffffffffu, v, o);
+      if ((threadIdx.x & 31) >= o) v += y;
+    }
+    if ((threadIdx.x & 31) == 31) wsum[threadIdx.x >> 5] = v;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+      long long w = wsum[threadIdx.x];
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const long long y = __shfl_up_sync(0xffffffffu, w, o);
+        if (threadIdx.x >= o) w += y;
+      }
+      wsum[threadIdx.x] = w;   // inclusive over warps
+    }
+    __syncthreads();
+    const long long before = carry + ((threadIdx.x >> 5) ? wsum[(threadIdx.x >> 5) - 1] : 0) + v - x;
+    __syncthreads();
+    if (i < nb) bsum[i] = before;
+    if (threadIdx.x == 1023) carry = before + x;
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) bsum[nb] = carry;
+}
+
+__global__ void __launch_bounds__(kScanT)
+k_scan_apply(const int* __restrict__ cnt, long long n, const long long* __restrict__ boff, long long* rp) {
+  __shared__ long long wsum[kScanT / 32];
+  const long long base = (long long)blockIdx.x * kScanBlk + (long long)threadIdx.x * kScanPer;
+  long long loc[kScanPer];
+  long long acc = 0;
+#pragma unroll
+  for (int k = 0; k < kScanPer; ++k) {
+    loc[k] = acc;
+    acc += (base + k < n) ? cnt[base + k] : 0;
+  }
+  long long v = acc;   // inclusive scan of the threads' totals
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const long long y = __shfl_up_sync(0xffffffffu, v, o);
+    if ((threadIdx.x & 31) >= o) v += y;
+  }
+  if ((threadIdx.x & 31) == 31) wsum[threadIdx.x >> 5] = v;
+  __syncthreads();
+  long long wbefore = 0;
+  for (int w = 0; w < (int)(threadIdx.x >> 5); ++w) wbefore += wsum[w];
+  const long long start = boff[blockIdx.x] + wbefore + v - acc;
+#pragma unroll
+  for (int k = 0; k < kScanPer; ++k)
+    if (base + k < n) rp[base + k] = start + loc[k];
+  if (base + kScanPer >= n && base < n) rp[n] = start + acc;   // the thread holding the last element
+}
+
+long long scan_temp_count(long long n) { return (n + kScanBlk - 1) / kScanBlk + 1; }
+
+void launch_exclusive_scan(const int* cnt, long long n, long long* tmp, long long* rp, cudaStream_t st) {
+  const int nb = (int)((n + kScanBlk - 1) / kScanBlk);
+  if (nb == 0) return;
+  k_scan_blocksum<<<nb, kScanT, 0, st>>>(cnt, n, tmp);
+  k_scan_blocks<<<1, 1024, 0, st>>>(tmp, nb);
+  k_scan_apply<<<nb, kScanT, 0, st>>>(cnt, n, tmp, rp);
+}
+
+void launch_rcsr_localize(const SubDev* d_subs, const int* d_blk_sub, int n_blk, const long long* row_ptr, int* rslot,
+                          int* blk_cnt, int* blk_list, int list_max, int pass, cudaStream_t st) {
+  if (n_blk > 0) k_rcsr_localize<<<n_blk, 256, 0, st>>>(d_subs, d_blk_sub, row_ptr, rslot, blk_cnt, blk_list, list_max, pass);
+}
 
 // Y_out[v][g] += scale * sum over the slots s of point g of sum_l chi_l(g) P[s][l][v]
 template <typename T>
 __global__ void __launch_bounds__(256)
 k_nl_back_csr(const SubDev* __restrict__ subs, const long long* __restrict__ row_ptr, const int* __restrict__ rslot,
-              const typename Vec4<T>::type* __restrict__ rchi, const double* __restrict__ P, T* Yout,
+              const typename Vec4<T>::type* __restrict__ rchi, const int* __restrict__ blk_cnt,
+              const int* __restrict__ blk_list, int list_max, const double* __restrict__ P, T* Yout,
               const StepCoef* __restrict__ coef, int step) {
   using T4 = typename Vec4<T>::type;
   extern __shared__ __align__(16) unsigned char qsm[];
   T4* Qs = reinterpret_cast<T4*>(qsm);   // [slot][kBackRow]
-  const SubDev& S = subs[blockIdx.y];
-  const int v0 = blockIdx.z * kBackVec;
-  const long long p0 = (long long)blockIdx.x * kBackPts;
+  // the vector groups of one point block are consecutive CTAs: the block's reverse-table rows
+  // are read once from DRAM and then from L2
+  const SubDev& S = subs[blockIdx.z];
+  const int v0 = blockIdx.x * kBackVec;
+  const long long p0 = (long long)blockIdx.y * kBackPts;
   if (v0 >= S.ns || p0 >= S.nd || S.slot_n == 0) return;
   const int nv = min(kBackVec, S.ns - v0);
-  const double scale = coef[blockIdx.y * kMaxDegree + step].scale;
-  for (int q = threadIdx.x; q < S.slot_n * kBackVec; q += blockDim.x) {
+  const double scale = coef[blockIdx.z * kMaxDegree + step].scale;
+  // the projector coefficients of the slots this point block meets (its rows name them by rank
+  // in the block's list)
+  const int nb = S.off_nlb + (int)blockIdx.y;
+  const int nloc = blk_cnt[nb];
+  const int* list = blk_list + (long long)nb * list_max;
+  for (int q = threadIdx.x; q < nloc * kBackVec; q += blockDim.x) {
     const int sl = q / kBackVec, v = q % kBackVec;
     T4 x;
     if (v < nv) {
-      const double* pa = P + S.off_proj + (long long)sl * 4 * S.ns + v0 + v;
+      const double* pa = P + S.off_proj + (long long)list[sl] * 4 * S.ns + v0 + v;
       x.x = (T)(scale * pa[0]); x.y = (T)(scale * pa[S.ns]); x.z = (T)(scale * pa[2 * S.ns]); x.w = (T)(scale * pa[3 * S.ns]);
     } else {
       x.x = x.y = x.z = x.w = (T)0;
@@ -482,18 +648,17 @@ void launch_rcsr_count(const SubDev* d_subs, const ProjSlot* d_slots, int n_slot
 }
 
 template <typename T>
-void launch_nl_back_csr(const SubDev* d_subs, int n_sub, long long max_nd, int max_ns, int max_slots,
+void launch_nl_back_csr(const SubDev* d_subs, int n_sub, long long max_nd, int max_ns, int list_max,
                         const long long* row_ptr, const int* rslot, const typename Vec4<T>::type* rchi,
-                        const double* P, T* Yout, const StepCoef* coef, int step, cudaStream_t st) {
-  if (max_slots == 0) return;
-  const size_t smem = (size_t)max_slots * kBackRow * sizeof(typename Vec4<T>::type);
-  static size_t attr = 0;
-  if (smem > 48 * 1024 && smem > attr) {
+                        const int* blk_cnt, const int* blk_list, const double* P, T* Yout, const StepCoef* coef,
+                        int step, cudaStream_t st) {
+  if (list_max == 0) return;
+  const size_t smem = (size_t)list_max * kBackRow * sizeof(typename Vec4<T>::type);
+  if (smem > 48 * 1024)
     cudaFuncSetAttribute(k_nl_back_csr<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    attr = smem;
-  }
-  dim3 grid((unsigned)((max_nd + kBackPts - 1) / kBackPts), n_sub, (max_ns + kBackVec - 1) / kBackVec);
-  k_nl_back_csr<T><<<grid, 256, smem, st>>>(d_subs, row_ptr, rslot, rchi, P, Yout, coef, step);
+  dim3 grid((max_ns + kBackVec - 1) / kBackVec, (unsigned)((max_nd + kBackPts - 1) / kBackPts), n_sub);
+  k_nl_back_csr<T><<<grid, 256, smem, st>>>(d_subs, row_ptr, rslot, rchi, blk_cnt, blk_list, list_max, P, Yout, coef,
+                                            step);
 }
 
 template <typename T>
@@ -512,7 +677,9 @@ void launch_nl_project(const SubDev* d_subs, const ProjSlot* d_slots, int slot_o
                        const typename Vec4<T>::type* chi, int max_ns, const T* Y, double* P, cudaStream_t st) {
   if (n_slot == 0) return;
   const int groups = (max_ns + kPV - 1) / kPV;
-  k_nl_project<T><<<n_slot * groups, 256, 0, st>>>(d_subs, d_slots, slot_off, n_slot, idx, chi, Y, P);
+  const int chunks = (n_slot + kPChunk - 1) / kPChunk;
+  k_nl_project<T><<<chunks * kPChunk * groups, 256, 0, st>>>(d_subs, d_slots, slot_off, n_slot, groups, idx, chi, Y,
+                                                             P);
 }
 
 template <typename T>
@@ -535,7 +702,8 @@ void launch_nl_back(const SubDev* d_subs, const ProjSlot* d_slots, int n_slot, c
   template void launch_rcsr_build<T>(const SubDev*, const ProjSlot*, int, const int*, const Vec4<T>::type*,         \
                                      const long long*, int*, int*, Vec4<T>::type*, cudaStream_t);                    \
   template void launch_nl_back_csr<T>(const SubDev*, int, long long, int, int, const long long*, const int*,        \
-                                      const Vec4<T>::type*, const double*, T*, const StepCoef*, int, cudaStream_t);
+                                      const Vec4<T>::type*, const int*, const int*, const double*, T*,                \
+                                      const StepCoef*, int, cudaStream_t);
 XLS_INST_NL(double)
 XLS_INST_NL(float)
 

@@ -179,6 +179,11 @@ struct xls_grid_s {
   double4* d_rchi64 = nullptr;
   float4* d_rchi32 = nullptr;
   int max_slots = 0;
+  // back-projection point blocks: subdomain of each block, slots per block, the blocks' slot lists
+  int* d_nlb_sub = nullptr;
+  int* d_nlb_cnt = nullptr;
+  int* d_nlb_list = nullptr;
+  int nlb_max = 0;
   double *P = nullptr, *P1 = nullptr;
   // Lanczos (single-vector view, FP64)
   double *lz_v = nullptr, *lz_vp = nullptr, *lz_f = nullptr, *lz_Hv = nullptr, *lz_a = nullptr, *lz_b = nullptr;
@@ -313,7 +318,8 @@ void h_step(xls_grid g, bool one, const T* yin, const T* yprev, T* yout, int ste
   { ProfScope ps(g, K_NLPROJ); launch_nl_project<T>(ds, g->d_slots, 0, g->n_slot, g->d_pidx, chi_table<T>(g), mns, yin, P, g->st); }
   { ProfScope ps(g, K_STENCIL); launch_stencil<T>(ds, g->n_sub, pl, yin, yprev, yout, V, g->coef, step, g->st); }
   { ProfScope ps(g, K_NLBACK);
-    launch_nl_back_csr<T>(ds, g->n_sub, g->max_nd, mns, g->max_slots, g->d_rptr, g->d_rslot, rchi_table<T>(g), P, yout,
+    launch_nl_back_csr<T>(ds, g->n_sub, g->max_nd, mns, g->nlb_max, g->d_rptr, g->d_rslot, rchi_table<T>(g),
+                          g->d_nlb_cnt, g->d_nlb_list, P, yout,
                           g->coef, step, g->st); }
   g->launches += (g->n_slot ? 3 : 1);
 }
@@ -357,7 +363,8 @@ void h_step_main(xls_grid g, const xls_grid_s::View& v, int bin, int bprev, int 
   }
   if (side) cudaStreamWaitEvent(v.st, g->ev_side_out, 0);
   { ProfScope ps(g, K_NLBACK);
-    launch_nl_back_csr<T>(v.ds, v.n, v.max_nd, v.max_ns, g->max_slots, g->d_rptr, g->d_rslot, rchi_table<T>(g), g->P,
+    launch_nl_back_csr<T>(v.ds, v.n, v.max_nd, v.max_ns, g->nlb_max, g->d_rptr, g->d_rslot, rchi_table<T>(g),
+                          g->d_nlb_cnt, g->d_nlb_list, g->P,
                           yout, v.coef, step, v.st); }
   g->launches += (v.n_slot ? 2 : 0);
 }
@@ -607,39 +614,42 @@ xls_status lanczos_bounds(xls_grid g) {
 // periodic images of one atom that touch a subdomain (local frame of the subdomain)
 void atom_images(xls_grid g, int a, const double R[3], const xls_species& sp, int slot, std::vector<AtomImg>& out) {
   const SubDev& S = g->subs[a];
-  std::vector<double> cand[3];
-  int lo[3][5], cnt[3][5];
+  // candidate positions per axis in the subdomain's frame (one on a periodic axis, the five
+  // nearest periodic images on a Dirichlet axis) whose r_cut interval meets the subdomain;
+  // fixed-size arrays: this runs for every atom and subdomain of a set-up
+  double cand[3][5];
+  int lo[3][5], cnt[3][5], nc[3];
   for (int d = 0; d < 3; ++d) {
     const double h = g->gh[d], L = g->gL[d];
     const double Rl = R[d] - S.start[d] * h;
+    nc[d] = 0;
     if (S.periodic[d]) {
       double r = std::fmod(Rl, L);
       if (r < 0) r += L;
-      cand[d].push_back(r);
+      cand[d][nc[d]] = r;
+      lo[d][nc[d]] = (int)std::floor((r - sp.r_cut) / h);
+      cnt[d][nc[d]] = (int)std::ceil((r + sp.r_cut) / h) - lo[d][nc[d]] + 1;
+      ++nc[d];
     } else {
-      for (int s = -2; s <= 2; ++s) cand[d].push_back(Rl + s * L);
-    }
-    int c = 0;
-    std::vector<double> keep;
-    for (double r : cand[d]) {
-      int b0 = (int)std::floor((r - sp.r_cut) / h), b1 = (int)std::ceil((r + sp.r_cut) / h);
-      if (!S.periodic[d]) {
+      for (int sh = -2; sh <= 2; ++sh) {
+        const double r = Rl + sh * L;
+        int b0 = (int)std::floor((r - sp.r_cut) / h), b1 = (int)std::ceil((r + sp.r_cut) / h);
         b0 = std::max(b0, 0);
         b1 = std::min(b1, S.n[d] - 1);
         if (b1 < b0) continue;
+        cand[d][nc[d]] = r;
+        lo[d][nc[d]] = b0;
+        cnt[d][nc[d]] = b1 - b0 + 1;
+        ++nc[d];
       }
-      lo[d][c] = b0;
-      cnt[d][c] = b1 - b0 + 1;
-      keep.push_back(r);
-      ++c;
     }
-    cand[d] = keep;
+    if (nc[d] == 0) return;   // no image meets the subdomain along this axis
   }
-  for (size_t ix = 0; ix < cand[0].size(); ++ix)
-    for (size_t iy = 0; iy < cand[1].size(); ++iy)
-      for (size_t iz = 0; iz < cand[2].size(); ++iz) {
+  for (int ix = 0; ix < nc[0]; ++ix)
+    for (int iy = 0; iy < nc[1]; ++iy)
+      for (int iz = 0; iz < nc[2]; ++iz) {
         AtomImg A{};
-        const size_t ii[3] = {ix, iy, iz};
+        const int ii[3] = {ix, iy, iz};
         double dist2 = 0.0;
         for (int d = 0; d < 3; ++d) {
           A.R[d] = cand[d][ii[d]];
@@ -1904,6 +1914,12 @@ xls_status xls_hamiltonian_set(xls_grid g, const double* veff, int veff_on_devic
     poff += 4LL * g->subs[a].ns * g->subs[a].slot_n;
     g->subs1[a].off_proj = 4LL * (long long)first;
   }
+  std::vector<int> nlb_sub;   // subdomain of every back-projection point block
+  for (int a = 0; a < g->n_sub; ++a) {
+    g->subs[a].off_nlb = g->subs1[a].off_nlb = (int)nlb_sub.size();
+    for (long long p = 0; p < g->subs[a].nd; p += kBackPts) nlb_sub.push_back(a);
+    if (g->subs[a].slot_n > 32768) return fail(XLS_EINVAL, "more than 32768 projector slots in one subdomain");
+  }
   g->release(&g->d_imgs);
   g->release(&g->d_slots);
   g->release(&g->P);
@@ -1957,15 +1973,18 @@ xls_status xls_hamiltonian_set(xls_grid g, const double* veff, int veff_on_devic
     XLS_CUDA(cudaMalloc(&dcur, g->tot_pts * sizeof(int)));
     XLS_CUDA(cudaMemsetAsync(dc, 0, g->tot_pts * sizeof(int), g->st));
     launch_rcsr_count(g->d_subs, g->d_slots, g->n_slot, g->d_pidx, dc, g->st);
-    std::vector<int> hc(g->tot_pts);
-    XLS_CUDA(cudaMemcpyAsync(hc.data(), dc, g->tot_pts * sizeof(int), cudaMemcpyDeviceToHost, g->st));
+    // row pointers by a device prefix sum; only the total comes back to size the tables
+    if ((s = g->alloc(&g->d_rptr, (g->tot_pts + 1) * sizeof(long long))) != XLS_OK) return s;
+    long long* dtmp = nullptr;
+    XLS_CUDA(cudaMalloc(&dtmp, scan_temp_count(g->tot_pts) * sizeof(long long)));
+    launch_exclusive_scan(dc, g->tot_pts, dtmp, g->d_rptr, g->st);
+    long long n_entries = 0;
+    XLS_CUDA(cudaMemcpyAsync(&n_entries, g->d_rptr + g->tot_pts, sizeof(long long), cudaMemcpyDeviceToHost, g->st));
     XLS_CUDA(cudaStreamSynchronize(g->st));
-    std::vector<long long> rp(g->tot_pts + 1, 0);
-    for (long long q = 0; q < g->tot_pts; ++q) rp[q + 1] = rp[q] + hc[q];
-    if ((s = g->alloc(&g->d_rptr, rp.size() * sizeof(long long))) != XLS_OK) return s;
+    cudaFree(dtmp);
+    const std::vector<long long> rp{0, n_entries};   // rp.back(): the number of table entries
     if ((s = g->alloc(&g->d_rslot, std::max<long long>(rp.back(), 1) * sizeof(int))) != XLS_OK) return s;
     if ((s = g->alloc(&g->d_rchi64, std::max<long long>(rp.back(), 1) * sizeof(double4))) != XLS_OK) return s;
-    XLS_CUDA(cudaMemcpyAsync(g->d_rptr, rp.data(), rp.size() * sizeof(long long), cudaMemcpyHostToDevice, g->st));
     XLS_CUDA(cudaMemsetAsync(dcur, 0, g->tot_pts * sizeof(int), g->st));
     launch_rcsr_build<double>(g->d_subs, g->d_slots, g->n_slot, g->d_pidx, g->d_chi64, g->d_rptr, dcur, g->d_rslot,
                               g->d_rchi64, g->st);
@@ -1979,6 +1998,25 @@ xls_status xls_hamiltonian_set(xls_grid g, const double* veff, int veff_on_devic
     cudaFree(dcur);
     g->max_slots = 0;
     for (const SubDev& S : g->subs) g->max_slots = std::max(g->max_slots, S.slot_n);
+    // per point block of the back-projection: the slots its rows name (rows' entries as ranks)
+    g->release(&g->d_nlb_sub);
+    g->release(&g->d_nlb_cnt);
+    g->release(&g->d_nlb_list);
+    const int n_nlb = (int)nlb_sub.size();
+    if ((s = g->alloc(&g->d_nlb_sub, n_nlb * sizeof(int))) != XLS_OK) return s;
+    if ((s = g->alloc(&g->d_nlb_cnt, n_nlb * sizeof(int))) != XLS_OK) return s;
+    XLS_CUDA(cudaMemcpyAsync(g->d_nlb_sub, nlb_sub.data(), n_nlb * sizeof(int), cudaMemcpyHostToDevice, g->st));
+    launch_rcsr_localize(g->d_subs, g->d_nlb_sub, n_nlb, g->d_rptr, g->d_rslot, g->d_nlb_cnt, nullptr, 0, 0, g->st);
+    std::vector<int> cnt_b(n_nlb);
+    XLS_CUDA(cudaMemcpyAsync(cnt_b.data(), g->d_nlb_cnt, n_nlb * sizeof(int), cudaMemcpyDeviceToHost, g->st));
+    XLS_CUDA(cudaStreamSynchronize(g->st));
+    g->nlb_max = 0;
+    for (int c : cnt_b) g->nlb_max = std::max(g->nlb_max, c);
+    if ((s = g->alloc(&g->d_nlb_list, std::max<size_t>((size_t)n_nlb * g->nlb_max, 1) * sizeof(int))) != XLS_OK)
+      return s;
+    launch_rcsr_localize(g->d_subs, g->d_nlb_sub, n_nlb, g->d_rptr, g->d_rslot, g->d_nlb_cnt, g->d_nlb_list,
+                         g->nlb_max, 1, g->st);
+    XLS_CUDA(cudaGetLastError());
   }
   set_view_slots(g, g->full);
   if (g->concurrent)

@@ -31,6 +31,7 @@ struct SubDev {
   long long off_pt;      // offset into per-point arrays (V)
   long long off_ss;      // offset into N_s x N_s arrays
   int slot_lo, slot_n;   // range in the projector-slot array (one slot per atom meeting the subdomain)
+  int off_nlb;           // first back-projection point block of the subdomain (blocks of kBackPts points)
   long long off_proj;    // offset into the projection array P (4 * ns per slot)
   double h[3];
   double dV;
@@ -148,10 +149,19 @@ template <typename T>
 void launch_rcsr_build(const SubDev* d_subs, const ProjSlot* d_slots, int n_slot, const int* idx,
                        const typename Vec4<T>::type* chi, const long long* row_ptr, int* cursor, int* rslot,
                        typename Vec4<T>::type* rchi, cudaStream_t st);
+// back-projection point blocks: the slots each block's reverse-table rows name, and the rows'
+// slot entries rewritten to ranks in that list (pass 0 counts, pass 1 ranks and lists)
+constexpr int kBackPts = 2048;
+// exclusive prefix sum of n counts into rp[0..n] on the device; tmp holds scan_temp_count(n) values
+long long scan_temp_count(long long n);
+void launch_exclusive_scan(const int* cnt, long long n, long long* tmp, long long* rp, cudaStream_t st);
+void launch_rcsr_localize(const SubDev* d_subs, const int* d_blk_sub, int n_blk, const long long* row_ptr,
+                          int* rslot, int* blk_cnt, int* blk_list, int list_max, int pass, cudaStream_t st);
 template <typename T>
-void launch_nl_back_csr(const SubDev* d_subs, int n_sub, long long max_nd, int max_ns, int max_slots,
+void launch_nl_back_csr(const SubDev* d_subs, int n_sub, long long max_nd, int max_ns, int list_max,
                         const long long* row_ptr, const int* rslot, const typename Vec4<T>::type* rchi,
-                        const double* P, T* Yout, const StepCoef* coef, int step, cudaStream_t st);
+                        const int* blk_cnt, const int* blk_list, const double* P, T* Yout, const StepCoef* coef,
+                        int step, cudaStream_t st);
 template <typename T>
 void launch_nl_back(const SubDev* d_subs, const ProjSlot* d_slots, int n_slot, const int* idx,
                     const typename Vec4<T>::type* chi, int max_ns, const double* P, T* Yout, const StepCoef* coef,
