@@ -705,7 +705,9 @@ def si13824_precision(args, prec) -> dict:
 
 # DRAM bytes (read + write) of one FP32 stencil launch over a wave of 72 subdomains of 72^3 with
 # 528 states, measured by ncu for the kernel source whose SHA-256 starts with the key
-STENCIL_TRAFFIC_13824 = {}
+# (ncu on waves of 2 subdomains: 4.699759e9 bytes per launch, scaled by 36 to a wave of 72; the traffic grows
+# with the subdomains a launch covers)
+STENCIL_TRAFFIC_13824 = {"056189a407e3c6e6": 4.699759e9 * 36}
 
 
 def stencil_traffic_13824():

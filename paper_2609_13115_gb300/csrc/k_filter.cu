@@ -600,11 +600,34 @@ k_nl_back_csr(const SubDev* __restrict__ subs, const long long* __restrict__ row
   // added to Y_out with fire-and-forget reductions (red.global.add): the read-modify-write happens
   // in L2, no load of Y sits on the thread's critical path, and each element receives exactly one
   // addition (deterministic)
-  for (long long g = p0 + threadIdx.x; g < end; g += 2 * blockDim.x) {
+  // the row bounds of the next iteration's two points are fetched one iteration ahead, so that
+  // only the table entries (not the row pointers before them) wait on memory
+  const long long* rp = row_ptr + S.off_pt;
+  long long g = p0 + threadIdx.x;
+  long long nA0 = 0, nA1 = 0, nB0 = 0, nB1 = 0;
+  if (g < end) {
+    nA0 = rp[g];
+    nA1 = rp[g + 1];
+    if (g + blockDim.x < end) {
+      nB0 = rp[g + blockDim.x];
+      nB1 = rp[g + blockDim.x + 1];
+    }
+  }
+  for (; g < end; g += 2 * blockDim.x) {
     const long long gB = g + blockDim.x;
     const bool hasB = gB < end;
-    const long long rA0 = row_ptr[S.off_pt + g], rA1 = row_ptr[S.off_pt + g + 1];
-    const long long rB0 = hasB ? row_ptr[S.off_pt + gB] : 0, rB1 = hasB ? row_ptr[S.off_pt + gB + 1] : 0;
+    const long long rA0 = nA0, rA1 = nA1, rB0 = hasB ? nB0 : 0, rB1 = hasB ? nB1 : 0;
+    {
+      const long long gn = g + 2 * blockDim.x;
+      if (gn < end) {
+        nA0 = rp[gn];
+        nA1 = rp[gn + 1];
+        if (gn + blockDim.x < end) {
+          nB0 = rp[gn + blockDim.x];
+          nB1 = rp[gn + blockDim.x + 1];
+        }
+      }
+    }
     T yA[kBackVec], yB[kBackVec];
 #pragma unroll
     for (int v = 0; v < kBackVec; ++v) yA[v] = yB[v] = (T)0;

@@ -3,6 +3,7 @@
 // every arithmetic step of the pass runs in the kernels of k_filter.cu, k_dense.cu, k_eig.cu
 // and k_tc.cu.
 #include <algorithm>
+#include <chrono>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -1326,8 +1327,10 @@ xls_status create_grid(const xls_cell* cell, const xls_dc* dc, int precision, si
     }
   }
   {
+    // the projection of a filter step on a side stream beside the stencil (XLS_PROJ_SIDE=1): off by
+    // default -- on 72^3 subdomains the two kernels contend for L2 and DRAM and the step is slower
     const char* env = std::getenv("XLS_PROJ_SIDE");
-    if (!(env && env[0] == '0') && !dry) {
+    if (env && env[0] == '1' && !dry) {
       const bool ok = cudaStreamCreateWithFlags(&g->side_st, cudaStreamNonBlocking) == cudaSuccess &&
                       cudaEventCreateWithFlags(&g->ev_side_in, cudaEventDisableTiming) == cudaSuccess &&
                       cudaEventCreateWithFlags(&g->ev_side_out, cudaEventDisableTiming) == cudaSuccess;
@@ -1644,7 +1647,12 @@ xls_status carry_orbitals_random(xls_grid g, uint64_t seed) {
 xls_status carry_run(xls_grid g, int w, int degree, int n_passes, const double* bounds, int& launches) {
   xls_grid k = g->worker;
   const int first = g->waves[w].first, cnt = g->waves[w].second;
+  // XLS_TRACE=1: host wall times of the wave's phases on stderr (diagnostics)
+  static const bool trace = std::getenv("XLS_TRACE") != nullptr;
+  const auto t0 = std::chrono::steady_clock::now();
   XLS_TRY(carry_retarget(g, first));
+  if (trace) cudaStreamSynchronize(g->st);
+  const auto t1 = std::chrono::steady_clock::now();
   g->carry_last = w;   // the worker's slots now hold this wave's subdomains
   k->orb_set = true;
   std::vector<double> bw;
@@ -1663,6 +1671,7 @@ xls_status carry_run(xls_grid g, int w, int degree, int n_passes, const double* 
     bp = bw.data();
   }
   XLS_TRY(xls_chefsi_batch(k, degree, n_passes, bp));
+  const auto t2 = std::chrono::steady_clock::now();
   const SubDev& S0 = g->subs[first];
   XLS_CUDA(cudaMemcpyAsync(g->lam + S0.off_state, k->lam, k->tot_states * sizeof(double), cudaMemcpyDeviceToDevice,
                            g->st));
@@ -1683,6 +1692,15 @@ xls_status carry_run(xls_grid g, int w, int degree, int n_passes, const double* 
   // coefficients; 10 Lanczos steps of one H application each) and of the core-row gather
   const int setup = (k->prec == XLS_FP64 ? 7 : 9) + 2 + 10 * ((k->n_slot ? 3 : 1) + 1);
   launches += k->last_launches + setup + 1;
+  if (trace) {
+    cudaStreamSynchronize(g->st);
+    const auto t3 = std::chrono::steady_clock::now();
+    auto ms = [](std::chrono::steady_clock::time_point a, std::chrono::steady_clock::time_point b) {
+      return std::chrono::duration<double, std::milli>(b - a).count();
+    };
+    std::fprintf(stderr, "[xls] wave %d: set-up %.1f ms, passes %.1f ms, copies %.1f ms\n", w, ms(t0, t1), ms(t1, t2),
+                 ms(t2, t3));
+  }
   g->carry_primed = true;
   g->wave_ran[w] = 1;
   g->have_ritz = std::all_of(g->wave_ran.begin(), g->wave_ran.end(), [](char c) { return c != 0; });
@@ -1838,6 +1856,12 @@ xls_status xls_hamiltonian_set(xls_grid g, const double* veff, int veff_on_devic
       if (!(sp[s].r_cut > 0) || !(sp[s].w_proj > 0) || 2 * sp[s].r_cut >= g->gL[d])
         return fail(XLS_EINVAL, "projector cutoff must be positive and below half of every cell edge");
   if (g->wave) return wave_hamiltonian_set(g, veff, veff_on_device, n_atoms, pos, species, n_species, sp);
+  static const bool trace = std::getenv("XLS_TRACE") != nullptr;
+  auto tnow = []() { return std::chrono::steady_clock::now(); };
+  auto tms = [](std::chrono::steady_clock::time_point a, std::chrono::steady_clock::time_point b) {
+    return std::chrono::duration<double, std::milli>(b - a).count();
+  };
+  const auto h0 = tnow();
   const long long ng = (long long)g->gn[0] * g->gn[1] * g->gn[2];
   if (!g->Vg) {
     xls_status s = g->alloc(&g->Vg, ng * sizeof(double));
@@ -1885,13 +1909,35 @@ xls_status xls_hamiltonian_set(xls_grid g, const double* veff, int veff_on_devic
     cudaFree(dgs);
     cudaFree(dn);
   }
-  // projector slots (atom x subdomain) and their periodic images
+  const auto h1 = tnow();
+  // projector slots (atom x subdomain) and their periodic images; the atoms are visited in the
+  // Z-order (Morton order) of their grid cells of 8 points, so that consecutive slots of a
+  // subdomain are spatial neighbours (the projection walks slots in chunks that then share points)
+  std::vector<int> aorder(n_atoms);
+  {
+    std::vector<std::pair<unsigned long long, int>> key(n_atoms);
+    for (int i = 0; i < n_atoms; ++i) {
+      unsigned long long m = 0;
+      unsigned c[3];
+      for (int d = 0; d < 3; ++d) {
+        double r = std::fmod(pos[3 * i + d], g->gL[d]);
+        if (r < 0) r += g->gL[d];
+        c[d] = (unsigned)(r / (8.0 * g->gh[d]));
+      }
+      for (int bit = 0; bit < 20; ++bit)
+        for (int d = 0; d < 3; ++d) m |= (unsigned long long)((c[d] >> bit) & 1u) << (3 * bit + d);
+      key[i] = {m, i};
+    }
+    std::stable_sort(key.begin(), key.end());
+    for (int i = 0; i < n_atoms; ++i) aorder[i] = key[i].second;
+  }
   std::vector<AtomImg> imgs;
   std::vector<ProjSlot> slots;
   long long poff = 0;
   for (int a = 0; a < g->n_sub; ++a) {
     const size_t first = slots.size();
-    for (int i = 0; i < n_atoms; ++i) {
+    for (int ii = 0; ii < n_atoms; ++ii) {
+      const int i = aorder[ii];
       const xls_species& q = sp[species[i]];
       const size_t before = imgs.size();
       atom_images(g, a, pos + 3 * i, q, (int)slots.size(), imgs);
@@ -2018,6 +2064,7 @@ xls_status xls_hamiltonian_set(xls_grid g, const double* veff, int veff_on_devic
                          g->nlb_max, 1, g->st);
     XLS_CUDA(cudaGetLastError());
   }
+  const auto h2 = tnow();
   set_view_slots(g, g->full);
   if (g->concurrent)
     for (auto& v : g->halves) set_view_slots(g, v);
@@ -2027,6 +2074,11 @@ xls_status xls_hamiltonian_set(xls_grid g, const double* veff, int veff_on_devic
   XLS_CUDA(cudaMemcpyAsync(g->bounds, bz.data(), bz.size() * sizeof(double), cudaMemcpyHostToDevice, g->st));
   launch_filter_coef(g->n_sub, g->bounds, 1, g->coef, g->st);
   XLS_TRY(lanczos_bounds(g));
+  if (trace) {
+    cudaStreamSynchronize(g->st);
+    std::fprintf(stderr, "[xls] hamiltonian_set: potential + norms %.1f ms, slots + tables %.1f ms, Lanczos %.1f ms\n",
+                 tms(h0, h1), tms(h1, h2), tms(h2, tnow()));
+  }
   g->ham_set = true;
   g->have_ritz = false;
   return XLS_OK;

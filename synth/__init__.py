@@ -169,6 +169,34 @@ def workload(cfg: int, consistent: bool = True, ncell: int | None = None) -> Wor
         return Workload(f"si64_dc8_48cube_ns{ns}_m20", L, (k * P,) * 3, pos, np.zeros(len(pos), int), [SI],
                         core_lo=cores, core_n=np.full((nsub, 3), P), buf=np.full((nsub, 3), P // 2),
                         n_states=np.full(nsub, ns), degree=20, n_passes=1, psi_seed=1001)
+    if cfg == 2:
+        # 2 % vacancies (round half up) by a seeded shuffle, displacements sigma = 0.1 bohr; every subdomain
+        # a 1-cell core with a buffer of 0.5, 0.75 or 1 cell (12, 18 or 24 points) drawn from the seed
+        k = 8 if ncell is None else ncell
+        L = (k * a,) * 3
+        full = si_diamond((k, k, k))
+        n_vac = int(math.floor(0.02 * len(full) + 0.5))
+        vac = set(seeded_permutation(2002 ^ 0x5A5A, len(full))[:n_vac].tolist())
+        keep = np.array([i for i in range(len(full)) if i not in vac])
+        pos = displace(full[keep], 0.1, 2002, L)
+        cores = np.array([(i, j, l) for l in range(k) for j in range(k) for i in range(k)]) * P
+        nsub = len(cores)
+        widths = np.array([P // 2, (3 * P) // 4, P])[(splitmix64(1002 ^ 0x3C3C, nsub) % np.uint64(3)).astype(int)]
+        buf = np.repeat(widths[:, None], 3, axis=1)
+        w0 = Workload(f"si{len(pos)}_dc{nsub}_uneven", L, (k * P,) * 3, pos, np.zeros(len(pos), int), [SI],
+                      core_lo=cores, core_n=np.full((nsub, 3), P), buf=buf, n_states=np.zeros(nsub, int),
+                      degree=20, n_passes=1, psi_seed=1002)
+        if consistent:   # electrons of the atoms inside each subdomain's box
+            ns = []
+            for aa in range(nsub):
+                start = cores[aa] - buf[aa]
+                inside = near_atoms(w0, start, w0.sub_size(aa), 0.0)
+                ns.append(consistent_states(4.0 * len(inside)))
+            w0.n_states = np.array(ns)
+        else:
+            w0.n_states = np.array([{P // 2: 80, (3 * P) // 4: 160, P: 240}[int(x)] for x in widths])
+        w0.name = f"si{len(pos)}_dc{nsub}_uneven_m20"
+        return w0
     if cfg == 3:
         k = 12 if ncell is None else ncell
         L = (k * a,) * 3
