@@ -12,7 +12,9 @@ left; the core rows of every subdomain's orbitals kept on the device for the den
 one wave: restriction, projector tables and Lanczos bound of its subdomains, one CheFSI pass
 (filter, projection, eigensolve, rotation, interior weights), core rows out; every completed
 cycle of waves adds the Fermi level, energies and the density on the global grid.
-`--workload si64` runs the 64-atom cell (8 resident subdomains of 48^3, 160 states) instead.
+`--workload si64` runs the 64-atom cell (8 resident subdomains of 48^3, 160 states) instead, and
+`--workload si4014` the uneven 4,014-atom cell (512 subdomains of 48^3 / 60^3 / 72^3 with their own
+state counts, in store-mode waves with an FP16 host store; one step = one full pass).
 
 metric: CheFSI throughput in Gpt.vec/s = sum_alpha m N_d N_s / time, one point-vector being one
 Hamiltonian application (+ recurrence) to one grid value of one vector.
@@ -53,7 +55,7 @@ def parse_args():
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--cpu-baseline-worker", action="store_true", help=argparse.SUPPRESS)
     p.add_argument("--sample-states", type=int, default=32)
-    p.add_argument("--workload", default="si13824", choices=["si13824", "si64"])
+    p.add_argument("--workload", default="si13824", choices=["si13824", "si4014", "si64"])
     p.add_argument("--states", default="consistent", choices=["consistent", "literal"],
                    help="si13824: 528 states per subdomain (consistent) or 240 (literal count, timing only)")
     p.add_argument("--budget-gb", type=float, default=250.0, help="si13824: HBM budget of the wave grid")
@@ -613,7 +615,7 @@ def run_si13824(args):
     achieved = bytes_launch / (stencil_avg_ms / 1e3) / 1e9
     roofline = {"bound": "hbm", "kernel": "k_stencil_tma" if prec != xls.XLS_FP64 else "k_stencil",
                 "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s", "frac": round(achieved / peak, 4),
-                "traffic": stencil_traffic_13824() if prec != xls.XLS_FP64 else None,
+                "traffic": stencil_traffic_13824(W, ns) if prec != xls.XLS_FP64 else None,
                 "peak_source": "measured" if "hbm_gbs" in peaks else "fallback",
                 "bytes_per_launch": bytes_launch, "avg_launch_ms": round(stencil_avg_ms, 4)}
     kernel_share = {n: round(float(kms[i] / max(kms.sum(), 1e-9)), 4)
@@ -705,16 +707,20 @@ def si13824_precision(args, prec) -> dict:
 
 # DRAM bytes (read + write) of one FP32 stencil launch over a wave of 72 subdomains of 72^3 with
 # 528 states, measured by ncu for the kernel source whose SHA-256 starts with the key
-# (ncu on waves of 2 subdomains: 4.699759e9 bytes per launch, scaled by 36 to a wave of 72; the traffic grows
-# with the subdomains a launch covers)
-STENCIL_TRAFFIC_13824 = {"056189a407e3c6e6": 4.699759e9 * 36}
+# DRAM bytes (read + write) per 72^3 subdomain with 528 states of one FP32 stencil launch, measured by ncu
+# on a wave of 2 subdomains (4.699759e9 bytes) for the kernel source whose SHA-256 starts with the key; a
+# launch over W subdomains moves W times this (the traffic grows with the subdomains a launch covers)
+STENCIL_TRAFFIC_13824 = {"056189a407e3c6e6": 4.699759e9 / 2}
 
 
-def stencil_traffic_13824():
+def stencil_traffic_13824(n_sub_launch: int, n_states: int):
     import hashlib
     src = os.path.join(ROOT, "paper_2609_13115_gb300", "csrc", "k_stencil_tma.cu")
     h = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
-    return STENCIL_TRAFFIC_13824.get(h)
+    per_sub = STENCIL_TRAFFIC_13824.get(h)
+    if per_sub is None or n_states != 528:
+        return None
+    return per_sub * n_sub_launch
 
 
 def run_reference_si13824(args):
@@ -750,6 +756,80 @@ def run_reference_si13824(args):
                                        f"72^3 subdomain with {n_vec} of {int(w.n_states[0])} start vectors"},
             "e2e": {"value": round(value, 6), "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line))
+
+
+# ---------------------------------------------------------------------------------------------
+# The 4,014-atom uneven cell (store-mode waves with an FP16 host store)
+# ---------------------------------------------------------------------------------------------
+def run_si4014(args):
+    """Every step one full pass over the 512 uneven subdomains (48^3 / 60^3 / 72^3, their own state
+    counts, all sizes in the same launches of a wave): the waves run in store mode, the orbitals of
+    every subdomain between passes in a pinned FP16 host store, then the Fermi level and the
+    density (a second sweep over the stored orbitals)."""
+    import torch
+    import synth
+    ws, rank, local = dist_setup()
+    w = synth.workload(2, consistent=(args.states == "consistent"))
+    V = synth.veff_erf_wells(w)
+    from paper_2609_13115_gb300 import xls
+    xls.load()
+    stream = torch.cuda.current_stream()
+    prec = {"fp16": xls.XLS_MIXED_FP16, "bf16": xls.XLS_MIXED_BF16, "fp64": xls.XLS_FP64}[args.precision]
+    ng = int(np.prod(w.n))
+    rho_dev = torch.zeros(ng, dtype=torch.float64, device="cuda")
+    g = xls.Grid(w, prec, hbm_budget_bytes=int(args.budget_gb * 1e9), stream=stream.cuda_stream)
+    g.set_hamiltonian(V)
+    xls.xls_wave_store_fp16(g.h, 1)
+    n_waves, _ = xls.xls_get_waves(g.h, w.n_sub)
+    xls.xls_orbitals_random(g.h, w.psi_seed)
+
+    def step():
+        xls.xls_chefsi_batch(g.h, w.degree, 1)
+        return xls.xls_density(g.h, w.n_electrons, w.kT, rho_dev)
+
+    for _ in range(max(args.warmup, 3)):
+        step()
+    sampler = ClockSampler(local)
+    sampler.start()
+    barrier(ws)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        step()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    barrier(ws)
+    clocks = sampler.stop()
+    ms_step = allreduce_max(e0.elapsed_time(e1) / args.steps, ws)
+    stage_ms, launches = xls.xls_get_timings(g.h)
+    mu, eb, es = xls.xls_density(g.h, w.n_electrons, w.kT)
+    g.close()
+    units = point_vectors(w)
+    if rank == 0:
+        sizes = {}
+        for a in range(w.n_sub):
+            key = f"{int(w.sub_size(a)[0])}^3"
+            sizes.setdefault(key, set()).add(int(w.n_states[a]))
+        print(json.dumps({
+            "metric": METRIC, "value": round(units * ws / (ms_step / 1e3) / 1e9, 3), "unit": UNIT, "n_gpus": ws,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms_step, 1), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None,
+            "dtype": {xls.XLS_MIXED_FP16: "f32 filter + fp16x3 tensor GEMM (f64 eig/fermi)",
+                      xls.XLS_MIXED_BF16: "f32 filter + bf16x3 tensor GEMM (f64 eig/fermi)",
+                      xls.XLS_FP64: "f64"}[prec],
+            "data": "synthetic",
+            "config": {"workload": w.name, "atoms": len(w.pos), "subdomains": w.n_sub,
+                       "sizes_and_states": {k: sorted(v) for k, v in sorted(sizes.items())},
+                       "degree": w.degree, "waves": n_waves, "host_store": "fp16",
+                       "step": "one full pass over every wave (orbitals up from and back to the host store), "
+                               "Fermi level and density"},
+            "stage_ms": {k: round(float(v), 1) for k, v in zip(["filter", "projection", "eig", "rotation"], stage_ms)},
+            "gpu_launches": int(launches) * args.steps, "clocks": clocks,
+            "mu": mu, "e_band_per_atom": eb / len(w.pos)}))
+    if ws > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
 
 
 def run_reference(args):
@@ -788,6 +868,8 @@ def main():
             run_reference(args)
     elif args.workload == "si13824":
         run_si13824(args)
+    elif args.workload == "si4014":
+        run_si4014(args)
     else:
         run_si64(args)
 

@@ -258,7 +258,9 @@ k_proj_fill(const SubDev* __restrict__ subs, const ProjSlot* __restrict__ slots,
 // w / kVH; a lane two points at a time (16 loads in flight); lanes (transpose reduction) and
 // warps are reduced at the end.
 constexpr int kPV = 8;
-constexpr int kPChunk = 32;   // slots per chunk of the projection's CTA order
+// slots per chunk of the projection's CTA order: about one 72^3 subdomain's slots, whose tables
+// (~30 MB) and one vector group's Y slice (~12 MB) stay in L2 while the chunk is walked
+constexpr int kPChunk = 512;
 constexpr int kVH = kPV / 8, kPH = 8 / kVH;   // vector halves and point phases of the 8 warps
 
 template <typename T>
@@ -269,8 +271,8 @@ k_nl_project(const SubDev* __restrict__ subs, const ProjSlot* __restrict__ slots
   using T4 = typename Vec4<T>::type;
   __shared__ T red[kPH][kPV * 4];
   // CTAs walk the slots in chunks of kPChunk: every vector group runs over the chunk before the
-  // next chunk starts, so the chunk's tables stay in L2 for all groups while the Y values of the
-  // chunk's supports (neighbouring atoms share points) are gathered once per group
+  // next chunk starts, so the chunk's tables stay in L2 for all groups, and within a group the
+  // points that neighbouring slots share are read from DRAM once
   const int chunk = (int)(blockIdx.x / (kPChunk * n_groups)), rem = (int)(blockIdx.x % (kPChunk * n_groups));
   const int grp = rem / kPChunk, sic = chunk * kPChunk + rem % kPChunk;
   if (sic >= n_slot) return;
