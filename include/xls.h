@@ -390,8 +390,9 @@ xls_status xls_get_kernel_times(xls_grid g, double* ms8_out, int* count8_out);
  *                  off-diagonal 128 x 128 blocks are mirrored, so both outputs are symmetric.
  * It allocates nothing: its scratch is a fixed 8 MiB + 256 B device array of the library, which
  * every GPU that loads the library holds until the process exits; larger n_states are rejected
- * with XLS_EINVAL.  The first call on a device looks up that array's device address (make it
- * before any stream capture).  All calls share the array and it keeps the last call's
+ * with XLS_EINVAL.  The first call on a device looks up that array's device address.  A CUDA
+ * error already pending on the calling thread is reported as XLS_ECUDA before any work is
+ * queued.  All calls share the array and it keeps the last call's
  * contents: calls that can overlap on the GPU (other host threads, other streams) race and
  * must be serialised by the caller.  The call queues its work on cuda_stream (NULL = legacy
  * default stream) and returns after it has completed. */
