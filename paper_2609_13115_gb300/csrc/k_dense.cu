@@ -204,19 +204,20 @@ void launch_core_weights(const SubDev* d_subs, int n_sub, int max_ns, const T* P
   k_core_weights<T><<<grid, 256, 0, st>>>(d_subs, Psi, c);
 }
 
-// ---- core rows of every vector into a compact store (wave carry mode): subdomain j of the
-// launch, vector v at store + base + j * per_sub + v * core_points, x fastest; the density is
-// formed from it after the Fermi level of all subdomains is known ------------------------------
+// ---- core rows of every vector into a compact store (waves): subdomain j of the launch, vector
+// v at store + dst[j].off_blk + v * core_points, x fastest (dst: the store's descriptors of the
+// launch's subdomains); the density is formed from it after the Fermi level of all subdomains
+// is known ----------------------------------------------------------------------------------------
 template <typename T>
 __global__ void __launch_bounds__(256)
-k_core_gather(const SubDev* __restrict__ subs, const T* __restrict__ Psi, T* __restrict__ store, long long base,
-              long long per_sub) {
+k_core_gather(const SubDev* __restrict__ subs, const T* __restrict__ Psi, T* __restrict__ store,
+              const SubDev* __restrict__ dst) {
   const SubDev& S = subs[blockIdx.y];
   const int v = blockIdx.x;
   if (v >= S.ns) return;
   const int cx = S.core_n[0], cy = S.core_n[1], cz = S.core_n[2];
   const T* p = Psi + S.off_blk + (long long)v * S.nd;
-  T* q = store + base + (long long)blockIdx.y * per_sub + (long long)v * cx * cy * cz;
+  T* q = store + dst[blockIdx.y].off_blk + (long long)v * cx * cy * cz;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
   for (int r = warp; r < cy * cz; r += nw) {
     const int j = r % cy, k = r / cy;
@@ -227,10 +228,10 @@ k_core_gather(const SubDev* __restrict__ subs, const T* __restrict__ Psi, T* __r
 }
 
 template <typename T>
-void launch_core_gather(const SubDev* d_subs, int n_sub, int max_ns, const T* Psi, T* store, long long base,
-                        long long per_sub, cudaStream_t st) {
+void launch_core_gather(const SubDev* d_subs, int n_sub, int max_ns, const T* Psi, T* store, const SubDev* d_dst,
+                        cudaStream_t st) {
   dim3 grid(max_ns, n_sub);
-  k_core_gather<T><<<grid, 256, 0, st>>>(d_subs, Psi, store, base, per_sub);
+  k_core_gather<T><<<grid, 256, 0, st>>>(d_subs, Psi, store, d_dst);
 }
 
 // ---- density on the core points: rho = (2/dV) sum_n occ_n psi_n^2 (Eq. density) ----------
@@ -942,9 +943,9 @@ template void launch_rotate<double>(const SubDev*, int, int, long long, const do
                                     cudaStream_t);
 template void launch_rotate<float>(const SubDev*, int, int, long long, const float*, const double*, float*,
                                    cudaStream_t);
-template void launch_core_gather<double>(const SubDev*, int, int, const double*, double*, long long, long long,
+template void launch_core_gather<double>(const SubDev*, int, int, const double*, double*, const SubDev*,
                                          cudaStream_t);
-template void launch_core_gather<float>(const SubDev*, int, int, const float*, float*, long long, long long,
+template void launch_core_gather<float>(const SubDev*, int, int, const float*, float*, const SubDev*,
                                         cudaStream_t);
 template void launch_core_weights<double>(const SubDev*, int, int, const double*, double*, cudaStream_t);
 template void launch_core_weights<float>(const SubDev*, int, int, const float*, double*, cudaStream_t);

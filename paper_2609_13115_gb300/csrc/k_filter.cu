@@ -661,6 +661,106 @@ k_nl_back_csr(const SubDev* __restrict__ subs, const long long* __restrict__ row
   }
 }
 
+// ---- single-vector views (one vector per subdomain: the Lanczos bound) -----------------------
+// Projection: one warp per slot walks all the slot's points, four per lane at a time.
+template <typename T>
+__global__ void __launch_bounds__(256)
+k_nl_project1(const SubDev* __restrict__ subs, const ProjSlot* __restrict__ slots, int n_slot,
+              const int* __restrict__ idx, const typename Vec4<T>::type* __restrict__ chi, const T* __restrict__ Y,
+              double* __restrict__ P) {
+  using T4 = typename Vec4<T>::type;
+  const int slot = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5), lane = threadIdx.x & 31;
+  if (slot >= n_slot) return;   // warp-uniform
+  const ProjSlot& A = slots[slot];
+  const SubDev& S = subs[A.sub];
+  const T* yb = Y + S.off_blk;
+  const int* ib = idx + A.pt_off;
+  const T4* cb = chi + A.pt_off;
+  T a0 = (T)0, a1 = (T)0, a2 = (T)0, a3 = (T)0;
+  for (int p = lane; p < A.pt_n; p += 128) {
+    int g[4];
+    T4 c[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const int q = p + 32 * u;
+      g[u] = q < A.pt_n ? ib[q] : -1;
+    }
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const int q = p + 32 * u;
+      if (q < A.pt_n) c[u] = cb[q];
+    }
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      if (g[u] >= 0) {
+        const T y = yb[g[u]];
+        a0 += c[u].x * y;
+        a1 += c[u].y * y;
+        a2 += c[u].z * y;
+        a3 += c[u].w * y;
+      }
+    }
+  }
+#pragma unroll
+  for (int o = 16; o >= 1; o >>= 1) {
+    a0 += __shfl_xor_sync(0xffffffffu, a0, o);
+    a1 += __shfl_xor_sync(0xffffffffu, a1, o);
+    a2 += __shfl_xor_sync(0xffffffffu, a2, o);
+    a3 += __shfl_xor_sync(0xffffffffu, a3, o);
+  }
+  if (lane == 0) {
+    double* pa = P + S.off_proj + (long long)(slot - S.slot_lo) * 4;
+    pa[0] = (double)a0 * A.E[0] * S.dV;
+    pa[1] = (double)a1 * A.E[1] * S.dV;
+    pa[2] = (double)a2 * A.E[2] * S.dV;
+    pa[3] = (double)a3 * A.E[3] * S.dV;
+  }
+}
+
+// Back-projection: one thread per grid point adds the sum over its reverse-table row (entries name
+// slots by rank in the list of the point's block) to its element; no two threads share an element.
+template <typename T>
+__global__ void __launch_bounds__(256)
+k_nl_back1(const SubDev* __restrict__ subs, const long long* __restrict__ row_ptr, const int* __restrict__ rslot,
+           const typename Vec4<T>::type* __restrict__ rchi, const int* __restrict__ blk_list, int list_max,
+           const double* __restrict__ P, T* Yout, const StepCoef* __restrict__ coef, int step) {
+  using T4 = typename Vec4<T>::type;
+  const SubDev& S = subs[blockIdx.y];
+  const long long g = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (g >= S.nd || S.slot_n == 0) return;
+  const long long* rp = row_ptr + S.off_pt;
+  const long long e0 = rp[g], e1 = rp[g + 1];
+  if (e1 == e0) return;
+  const int* list = blk_list + (long long)(S.off_nlb + (int)(g / kBackPts)) * list_max;
+  const double* pb = P + S.off_proj;
+  double sum = 0.0;
+  for (long long e = e0; e < e1; ++e) {
+    const int sl = list[rslot[e]];
+    const T4 c = rchi[e];
+    const double* pa = pb + (long long)sl * 4;
+    sum += (double)c.x * pa[0] + (double)c.y * pa[1] + (double)c.z * pa[2] + (double)c.w * pa[3];
+  }
+  T* y = Yout + S.off_blk + g;
+  *y += (T)(coef[blockIdx.y * kMaxDegree + step].scale * sum);
+}
+
+template <typename T>
+void launch_nl_project1(const SubDev* d_subs, const ProjSlot* d_slots, int n_slot, const int* idx,
+                        const typename Vec4<T>::type* chi, const T* Y, double* P, cudaStream_t st) {
+  if (n_slot == 0) return;
+  const long long threads = (long long)n_slot * 32;
+  k_nl_project1<T><<<(unsigned)((threads + 255) / 256), 256, 0, st>>>(d_subs, d_slots, n_slot, idx, chi, Y, P);
+}
+
+template <typename T>
+void launch_nl_back1(const SubDev* d_subs, int n_sub, long long max_nd, int list_max, const long long* row_ptr,
+                     const int* rslot, const typename Vec4<T>::type* rchi, const int* blk_list, const double* P,
+                     T* Yout, const StepCoef* coef, int step, cudaStream_t st) {
+  if (list_max == 0) return;
+  dim3 grid((unsigned)((max_nd + 255) / 256), n_sub);
+  k_nl_back1<T><<<grid, 256, 0, st>>>(d_subs, row_ptr, rslot, rchi, blk_list, list_max, P, Yout, coef, step);
+}
+
 template <typename T>
 void launch_rcsr_build(const SubDev* d_subs, const ProjSlot* d_slots, int n_slot, const int* idx,
                        const typename Vec4<T>::type* chi, const long long* row_ptr, int* cursor, int* rslot,
@@ -728,7 +828,12 @@ void launch_nl_back(const SubDev* d_subs, const ProjSlot* d_slots, int n_slot, c
                                      const long long*, int*, int*, Vec4<T>::type*, cudaStream_t);                    \
   template void launch_nl_back_csr<T>(const SubDev*, int, long long, int, int, const long long*, const int*,        \
                                       const Vec4<T>::type*, const int*, const int*, const double*, T*,                \
-                                      const StepCoef*, int, cudaStream_t);
+                                      const StepCoef*, int, cudaStream_t);                                            \
+  template void launch_nl_project1<T>(const SubDev*, const ProjSlot*, int, const int*, const Vec4<T>::type*,         \
+                                      const T*, double*, cudaStream_t);                                               \
+  template void launch_nl_back1<T>(const SubDev*, int, long long, int, const long long*, const int*,                \
+                                   const Vec4<T>::type*, const int*, const double*, T*, const StepCoef*, int,          \
+                                   cudaStream_t);
 XLS_INST_NL(double)
 XLS_INST_NL(float)
 

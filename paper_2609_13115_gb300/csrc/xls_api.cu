@@ -82,9 +82,8 @@ struct xls_grid_s {
   // FP16 store (xls_wave_store_fp16): half(psi_v 2^e_v) per value, the exponents per state on the
   // host, converted on the device through a half staging block and an exponent array
   bool store16 = false;
-  std::vector<int> store_ex;
   void* stage16 = nullptr;
-  int* stage_ex = nullptr;
+  int* d_store_ex = nullptr;   // exponents of every stored state, kept on the device
   std::vector<double> host_bounds;
   double wave_stage_ms[4] = {0, 0, 0, 0};
   // carry mode (xls_wave_carry): no orbital store; one worker grid, re-targeted to every wave in
@@ -94,6 +93,11 @@ struct xls_grid_s {
   xls_grid worker = nullptr;
   void* core_store = nullptr;
   SubDev* d_core_subs = nullptr;
+  // store mode: the same compact core store when it was reserved in the wave plan (core_reserve
+  // bytes), filled after every wave's passes; core_fresh marks the subdomains whose core rows are
+  // those of the orbitals held in the host store
+  size_t core_reserve = 0;
+  std::vector<char> core_fresh;
   std::vector<double> carry_ab;      // (a, a0) of every worker slot after its last pass
   std::vector<char> wave_ran;        // waves that have run since the orbitals were set
   int carry_last = -1;               // the wave the worker holds (its last run)
@@ -101,6 +105,11 @@ struct xls_grid_s {
   std::vector<double> atom_pos;
   std::vector<int> atom_sp;
   std::vector<xls_species> species;
+  // projector normalisations of the last geometry (reused while the atoms, their species
+  // parameters and the grid stay the same: a carry-mode worker re-targeted to every wave)
+  std::vector<double> norm_cache;
+  bool norm_valid = false;
+  int setup_launches = 0;   // kernels of the last xls_hamiltonian_set
   // concurrent halves (XLS_CONCURRENT=1): the subdomains split in two views whose passes run on
   // two streams, half 1's filter beside half 0's projection, eigensolve and rotation
   struct View {
@@ -316,12 +325,17 @@ void h_step(xls_grid g, bool one, const T* yin, const T* yprev, T* yout, int ste
   double* P = one ? g->P1 : g->P;
   const int mns = one ? 1 : g->max_ns;
   const T* V = (sizeof(T) == 8) ? (const T*)g->V : (const T*)g->Vf;
-  { ProfScope ps(g, K_NLPROJ); launch_nl_project<T>(ds, g->d_slots, 0, g->n_slot, g->d_pidx, chi_table<T>(g), mns, yin, P, g->st); }
+  { ProfScope ps(g, K_NLPROJ);
+    if (one) launch_nl_project1<T>(ds, g->d_slots, g->n_slot, g->d_pidx, chi_table<T>(g), yin, P, g->st);
+    else launch_nl_project<T>(ds, g->d_slots, 0, g->n_slot, g->d_pidx, chi_table<T>(g), mns, yin, P, g->st); }
   { ProfScope ps(g, K_STENCIL); launch_stencil<T>(ds, g->n_sub, pl, yin, yprev, yout, V, g->coef, step, g->st); }
   { ProfScope ps(g, K_NLBACK);
-    launch_nl_back_csr<T>(ds, g->n_sub, g->max_nd, mns, g->nlb_max, g->d_rptr, g->d_rslot, rchi_table<T>(g),
-                          g->d_nlb_cnt, g->d_nlb_list, P, yout,
-                          g->coef, step, g->st); }
+    if (one)
+      launch_nl_back1<T>(ds, g->n_sub, g->max_nd, g->nlb_max, g->d_rptr, g->d_rslot, rchi_table<T>(g), g->d_nlb_list,
+                         P, yout, g->coef, step, g->st);
+    else
+      launch_nl_back_csr<T>(ds, g->n_sub, g->max_nd, mns, g->nlb_max, g->d_rptr, g->d_rslot, rchi_table<T>(g),
+                            g->d_nlb_cnt, g->d_nlb_list, P, yout, g->coef, step, g->st); }
   g->launches += (g->n_slot ? 3 : 1);
 }
 
@@ -1399,16 +1413,16 @@ xls_status store_to_device(xls_grid g, int sub, void* dev, cudaStream_t st) {
     return XLS_OK;
   }
   XLS_CUDA(cudaMemcpyAsync(g->stage16, store_ptr(g, sub), n * 2, cudaMemcpyHostToDevice, st));
-  XLS_CUDA(cudaMemcpyAsync(g->stage_ex, g->store_ex.data() + S.off_state, S.ns * sizeof(int), cudaMemcpyHostToDevice,
-                           st));
-  if (g->prec == XLS_FP64) launch_load_half<double>(g->stage16, S.nd, S.ns, g->stage_ex, (double*)dev, st);
-  else launch_load_half<float>(g->stage16, S.nd, S.ns, g->stage_ex, (float*)dev, st);
+  const int* ex = g->d_store_ex + S.off_state;
+  if (g->prec == XLS_FP64) launch_load_half<double>(g->stage16, S.nd, S.ns, ex, (double*)dev, st);
+  else launch_load_half<float>(g->stage16, S.nd, S.ns, ex, (float*)dev, st);
   XLS_CUDA(cudaGetLastError());
   return XLS_OK;
 }
 
-// device block `dev` (compute precision) of subdomain `sub` into the store; synchronous for the
-// FP16 store (its exponents land in a host vector)
+// device block `dev` (compute precision) of subdomain `sub` into the store, queued on st (the
+// FP16 store's exponents stay on the device; the halves go through the one staging buffer, whose
+// reuse the stream orders)
 xls_status device_to_store(xls_grid g, int sub, const void* dev, cudaStream_t st) {
   const SubDev& S = g->subs[sub];
   const size_t n = (size_t)S.nd * S.ns;
@@ -1416,13 +1430,11 @@ xls_status device_to_store(xls_grid g, int sub, const void* dev, cudaStream_t st
     XLS_CUDA(cudaMemcpyAsync(store_ptr(g, sub), dev, n * g->elem, cudaMemcpyDeviceToHost, st));
     return XLS_OK;
   }
-  if (g->prec == XLS_FP64) launch_store_half<double>((const double*)dev, S.nd, S.ns, g->stage_ex, g->stage16, st);
-  else launch_store_half<float>((const float*)dev, S.nd, S.ns, g->stage_ex, g->stage16, st);
+  int* ex = g->d_store_ex + S.off_state;
+  if (g->prec == XLS_FP64) launch_store_half<double>((const double*)dev, S.nd, S.ns, ex, g->stage16, st);
+  else launch_store_half<float>((const float*)dev, S.nd, S.ns, ex, g->stage16, st);
   XLS_CUDA(cudaGetLastError());
   XLS_CUDA(cudaMemcpyAsync(store_ptr(g, sub), g->stage16, n * 2, cudaMemcpyDeviceToHost, st));
-  XLS_CUDA(cudaMemcpyAsync(g->store_ex.data() + S.off_state, g->stage_ex, S.ns * sizeof(int), cudaMemcpyDeviceToHost,
-                           st));
-  XLS_CUDA(cudaStreamSynchronize(st));
   return XLS_OK;
 }
 
@@ -1474,11 +1486,9 @@ xls_status wave_orbitals_set(xls_grid g, int sub, const double* psi, int on_devi
   }
   if (g->store16) {   // FP64 up, halves + exponents back
     XLS_CUDA(cudaMemcpyAsync(g->blk[0], src, n * sizeof(double), cudaMemcpyHostToDevice, g->st));
-    launch_store_half<double>((const double*)g->blk[0], S.nd, S.ns, g->stage_ex, g->stage16, g->st);
+    launch_store_half<double>((const double*)g->blk[0], S.nd, S.ns, g->d_store_ex + S.off_state, g->stage16, g->st);
     XLS_CUDA(cudaGetLastError());
     XLS_CUDA(cudaMemcpyAsync(store_ptr(g, sub), g->stage16, n * 2, cudaMemcpyDeviceToHost, g->st));
-    XLS_CUDA(cudaMemcpyAsync(g->store_ex.data() + S.off_state, g->stage_ex, S.ns * sizeof(int), cudaMemcpyDeviceToHost,
-                             g->st));
     XLS_CUDA(cudaStreamSynchronize(g->st));
   } else if (g->prec == XLS_FP64) {
     std::memcpy(store_ptr(g, sub), src, n * sizeof(double));
@@ -1508,9 +1518,7 @@ xls_status wave_orbitals_get(xls_grid g, int sub, double* out, int on_device) {
   double* dst = on_device ? tmp.data() : out;
   if (g->store16) {   // halves + exponents up, FP64 back
     XLS_CUDA(cudaMemcpyAsync(g->stage16, store_ptr(g, sub), n * 2, cudaMemcpyHostToDevice, g->st));
-    XLS_CUDA(cudaMemcpyAsync(g->stage_ex, g->store_ex.data() + S.off_state, S.ns * sizeof(int), cudaMemcpyHostToDevice,
-                             g->st));
-    launch_load_half<double>(g->stage16, S.nd, S.ns, g->stage_ex, (double*)g->blk[0], g->st);
+    launch_load_half<double>(g->stage16, S.nd, S.ns, g->d_store_ex + S.off_state, (double*)g->blk[0], g->st);
     XLS_CUDA(cudaGetLastError());
     XLS_CUDA(cudaMemcpyAsync(dst, g->blk[0], n * sizeof(double), cudaMemcpyDeviceToHost, g->st));
     XLS_CUDA(cudaStreamSynchronize(g->st));
@@ -1548,14 +1556,61 @@ xls_status wave_orbitals_random(xls_grid g, uint64_t seed) {
 // fresh_b: the potential changed since the last pass (an SCF step): the upper bound b of every
 // subdomain is the worker's new Lanczos bound, a and a0 stay those of the last pass's Ritz values
 // (what the resident grid's SCF step does with its Lanczos bounds)
+// the compact core store and its density descriptors (subdomain a's core box is a block of its
+// own, at the prefix of the core points x states before it)
+xls_status alloc_core_store(xls_grid g) {
+  std::vector<SubDev> cs(g->subs);
+  long long off = 0;
+  for (SubDev& S : cs) {
+    const long long core_pts = (long long)S.core_n[0] * S.core_n[1] * S.core_n[2];
+    for (int d = 0; d < 3; ++d) {
+      S.n[d] = S.core_n[d];
+      S.periodic[d] = 0;
+      S.start[d] = S.core_glo[d];
+      S.core_lo[d] = 0;
+    }
+    S.nd = core_pts;
+    S.off_blk = off;
+    off += core_pts * S.ns;
+  }
+  XLS_TRY(g->alloc(&g->core_store, (size_t)off * g->elem));
+  const xls_status s = g->alloc(&g->d_core_subs, g->n_sub * sizeof(SubDev));
+  if (s != XLS_OK) {
+    g->release(&g->core_store);
+    return s;
+  }
+  XLS_CUDA(cudaMemcpy(g->d_core_subs, cs.data(), cs.size() * sizeof(SubDev), cudaMemcpyHostToDevice));
+  return XLS_OK;
+}
+
+// core rows of the worker k's blocks (subdomains first .. first + k->n_sub - 1) into the store
+void gather_cores(xls_grid g, xls_grid k, int first) {
+  if (g->prec == XLS_FP64)
+    launch_core_gather<double>(k->d_subs, k->n_sub, k->max_ns, (const double*)k->blk[k->cur], (double*)g->core_store,
+                               g->d_core_subs + first, g->st);
+  else
+    launch_core_gather<float>(k->d_subs, k->n_sub, k->max_ns, (const float*)k->blk[k->cur], (float*)g->core_store,
+                              g->d_core_subs + first, g->st);
+}
+
 xls_status wave_run(xls_grid g, int w, int degree, int n_passes, const double* bounds, bool fresh_b, int& launches) {
   XLS_TRY(ensure_store(g));
+  // XLS_TRACE=1: host wall times of the wave's phases on stderr (diagnostics)
+  static const bool trace = std::getenv("XLS_TRACE") != nullptr;
+  auto tnow = []() { return std::chrono::steady_clock::now(); };
+  auto tms = [](std::chrono::steady_clock::time_point a, std::chrono::steady_clock::time_point b) {
+    return std::chrono::duration<double, std::milli>(b - a).count();
+  };
+  const auto t0 = tnow();
   const int first = g->waves[w].first, cnt = g->waves[w].second;
   xls_grid k = nullptr;
   XLS_TRY(wave_worker(g, w, &k));
+  const auto t1 = tnow();
   xls_status s = XLS_OK;
   for (int j = 0; j < cnt && s == XLS_OK; ++j)
     s = store_to_device(g, first + j, (char*)k->blk[k->cur] + (size_t)k->subs[j].off_blk * k->elem, g->st);
+  if (trace) cudaStreamSynchronize(g->st);
+  const auto t2 = tnow();
   k->orb_set = true;
   const double* bw = bounds ? bounds + 3 * (size_t)first
                             : (g->have_ritz ? g->host_bounds.data() + 3 * (size_t)first : nullptr);
@@ -1568,6 +1623,14 @@ xls_status wave_run(xls_grid g, int w, int degree, int n_passes, const double* b
     bw = mixed.data();
   }
   if (s == XLS_OK) s = xls_chefsi_batch(k, degree, n_passes, bw);
+  if (s == XLS_OK && g->core_reserve && !g->core_store) s = alloc_core_store(g);
+  if (s == XLS_OK && g->core_store) {
+    gather_cores(g, k, first);
+    if (cudaGetLastError() != cudaSuccess) s = fail(XLS_ECUDA, "wave: core-row gather failed");
+    std::fill(g->core_fresh.begin() + first, g->core_fresh.begin() + first + cnt, (char)1);
+  }
+  if (trace) cudaStreamSynchronize(g->st);
+  const auto t3 = tnow();
   if (s == XLS_OK) {
     const SubDev& S0 = g->subs[first];
     cudaMemcpyAsync(g->lam + S0.off_state, k->lam, k->tot_states * sizeof(double), cudaMemcpyDeviceToDevice, g->st);
@@ -1577,11 +1640,18 @@ xls_status wave_run(xls_grid g, int w, int degree, int n_passes, const double* b
   for (int j = 0; j < cnt && s == XLS_OK; ++j)
     s = device_to_store(g, first + j, (const char*)k->blk[k->cur] + (size_t)k->subs[j].off_blk * k->elem, g->st);
   if (s == XLS_OK && cudaStreamSynchronize(g->st) != cudaSuccess) s = fail(XLS_ECUDA, "wave: synchronisation failed");
+  const auto t4 = tnow();
   if (s == XLS_OK) {
     for (int i = 0; i < 4; ++i) g->wave_stage_ms[i] += k->stage_ms[i];
-    launches += k->last_launches;
+    launches += k->last_launches + (g->core_store ? 1 : 0);
   }
   xls_grid_destroy(k);
+  if (trace) {
+    const auto t5 = tnow();
+    std::fprintf(stderr, "[xls] store wave %d (%d subdomains): worker + Hamiltonian %.1f ms, load %.1f ms, passes %.1f ms, "
+                 "store %.1f ms, destroy %.1f ms\n", w, cnt, tms(t0, t1), tms(t1, t2), tms(t2, t3), tms(t3, t4),
+                 tms(t4, t5));
+  }
   return s;
 }
 
@@ -1677,21 +1747,14 @@ xls_status carry_run(xls_grid g, int w, int degree, int n_passes, const double* 
                            g->st));
   XLS_CUDA(cudaMemcpyAsync(g->cw + S0.off_state, k->cw, k->tot_states * sizeof(double), cudaMemcpyDeviceToDevice,
                            g->st));
-  const long long per_sub = (long long)S0.core_n[0] * S0.core_n[1] * S0.core_n[2] * S0.ns;
-  if (g->prec == XLS_FP64)
-    launch_core_gather<double>(k->d_subs, cnt, k->max_ns, (const double*)k->blk[k->cur], (double*)g->core_store,
-                               (long long)first * per_sub, per_sub, g->st);
-  else
-    launch_core_gather<float>(k->d_subs, cnt, k->max_ns, (const float*)k->blk[k->cur], (float*)g->core_store,
-                              (long long)first * per_sub, per_sub, g->st);
+  gather_cores(g, k, first);
   XLS_CUDA(cudaGetLastError());
   XLS_TRY(xls_get_bounds(k, g->host_bounds.data() + 3 * (size_t)first));
   g->carry_ab.assign(g->host_bounds.begin() + 3 * (size_t)first, g->host_bounds.begin() + 3 * (size_t)(first + cnt));
   for (int i = 0; i < 4; ++i) g->wave_stage_ms[i] += k->stage_ms[i];
   // kernels of the re-targeting (restriction, projector norms and tables, reverse tables, unit
   // coefficients; 10 Lanczos steps of one H application each) and of the core-row gather
-  const int setup = (k->prec == XLS_FP64 ? 7 : 9) + 2 + 10 * ((k->n_slot ? 3 : 1) + 1);
-  launches += k->last_launches + setup + 1;
+  launches += k->last_launches + k->setup_launches + 1;
   if (trace) {
     cudaStreamSynchronize(g->st);
     const auto t3 = std::chrono::steady_clock::now();
@@ -1736,7 +1799,9 @@ xls_status wave_density(xls_grid g, double n_electrons, double kT, double* mu_ou
   if (!rho_out) return XLS_OK;
   const long long ng = (long long)g->gn[0] * g->gn[1] * g->gn[2];
   if (!g->rho) XLS_TRY(g->alloc(&g->rho, ng * sizeof(double)));
-  if (g->carry) {   // the compact device store of the core rows
+  const bool from_cores =
+      g->carry || (g->core_store && std::all_of(g->core_fresh.begin(), g->core_fresh.end(), [](char c) { return c != 0; }));
+  if (from_cores) {   // the compact device store of the core rows
     if (g->prec == XLS_FP64)
       launch_density_occ<double>(g->d_core_subs, g->n_sub, g->max_core, (const double*)g->core_store, g->occ, g->gn,
                                  g->rho, g->st);
@@ -1746,7 +1811,9 @@ xls_status wave_density(xls_grid g, double n_electrons, double kT, double* mu_ou
     XLS_CUDA(cudaGetLastError());
   }
   // second sweep: every subdomain's block staged alone; its core points of rho written
-  for (int a = 0; a < g->n_sub && !g->carry; ++a) {
+  static const bool trace = std::getenv("XLS_TRACE") != nullptr;
+  const auto ts0 = std::chrono::steady_clock::now();
+  for (int a = 0; a < g->n_sub && !from_cores; ++a) {
     const SubDev& S = g->subs[a];
     const long long core = (long long)S.core_n[0] * S.core_n[1] * S.core_n[2];
     XLS_TRY(store_to_device(g, a, g->blk[0], g->st));
@@ -1758,6 +1825,9 @@ xls_status wave_density(xls_grid g, double n_electrons, double kT, double* mu_ou
   XLS_CUDA(cudaMemcpyAsync(rho_out, g->rho, ng * sizeof(double),
                            rho_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, g->st));
   XLS_CUDA(cudaStreamSynchronize(g->st));
+  if (trace)
+    std::fprintf(stderr, "[xls] density: %s %.1f ms\n", from_cores ? "device core store" : "second sweep over the store",
+                 std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - ts0).count());
   return XLS_OK;
 }
 
@@ -1785,7 +1855,12 @@ xls_status xls_grid_create(const xls_cell* cell, const xls_dc* dc, int precision
   size_t total = 1 << 26, run = 0;
   std::vector<std::pair<int, int>> waves;
   int first = 0;
-  const size_t fixed = (size_t)1 << 26;  // per-grid plans, events and small tables
+  // the compact store of the core rows (density without a second sweep over the host store) is
+  // reserved when it takes at most an eighth of the budget
+  size_t core_bytes = 0;
+  for (const SubDev& S : probe->subs) core_bytes += (size_t)S.core_n[0] * S.core_n[1] * S.core_n[2] * S.ns * elem;
+  const size_t core_reserve = core_bytes <= hbm_budget_bytes / 8 ? core_bytes : 0;
+  const size_t fixed = ((size_t)1 << 26) + core_reserve;  // per-grid plans, events and small tables
   for (int a = 0; a < probe->n_sub; ++a) {
     const size_t f = sub_footprint(probe->subs[a], elem);
     total += f;
@@ -1806,6 +1881,8 @@ xls_status xls_grid_create(const xls_cell* cell, const xls_dc* dc, int precision
   xls_grid g = nullptr;
   XLS_TRY(create_grid(cell, dc, precision, hbm_budget_bytes, cuda_stream, &g, false, true));
   g->waves = waves;
+  g->core_reserve = core_reserve;
+  g->core_fresh.assign(g->n_sub, 0);
   g->dc_core_lo.assign(dc->core_lo, dc->core_lo + 3 * (size_t)dc->n_sub);
   g->dc_core_n.assign(dc->core_n, dc->core_n + 3 * (size_t)dc->n_sub);
   g->dc_buf.assign(dc->buf, dc->buf + 3 * (size_t)dc->n_sub);
@@ -1836,7 +1913,7 @@ xls_status xls_grid_destroy(xls_grid g) {
   if (g->worker) xls_grid_destroy(g->worker);
   if (g->store) cudaFreeHost(g->store);
   if (g->stage16) cudaFree(g->stage16);
-  if (g->stage_ex) cudaFree(g->stage_ex);
+  if (g->d_store_ex) cudaFree(g->d_store_ex);
   delete g;
   return XLS_OK;
 }
@@ -1862,21 +1939,29 @@ xls_status xls_hamiltonian_set(xls_grid g, const double* veff, int veff_on_devic
     return std::chrono::duration<double, std::milli>(b - a).count();
   };
   const auto h0 = tnow();
+  int nl = 0;   // kernels launched by the set-up (for the caller's launch count)
   const long long ng = (long long)g->gn[0] * g->gn[1] * g->gn[2];
   if (!g->Vg) {
     xls_status s = g->alloc(&g->Vg, ng * sizeof(double));
     if (s != XLS_OK) return s;
   }
+  const bool same_geometry =
+      g->norm_valid && g->atom_pos.size() == 3 * (size_t)n_atoms && g->atom_sp.size() == (size_t)n_atoms &&
+      g->species.size() == (size_t)n_species &&
+      (n_atoms == 0 || (std::memcmp(g->atom_pos.data(), pos, 3 * (size_t)n_atoms * sizeof(double)) == 0 &&
+                        std::memcmp(g->atom_sp.data(), species, (size_t)n_atoms * sizeof(int)) == 0 &&
+                        std::memcmp(g->species.data(), sp, (size_t)n_species * sizeof(xls_species)) == 0));
   g->atom_pos.assign(pos, pos + 3 * (size_t)n_atoms);
   g->atom_sp.assign(species, species + n_atoms);
   g->species.assign(sp, sp + n_species);
   g->scf.pc_ready = false;
   XLS_CUDA(cudaMemcpyAsync(g->Vg, veff, ng * sizeof(double),
                            veff_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, g->st));
-  launch_restrict(g->d_subs, g->n_sub, g->max_nd, g->Vg, g->gn, g->V, g->Vf, g->st);
+  launch_restrict(g->d_subs, g->n_sub, g->max_nd, g->Vg, g->gn, g->V, g->Vf, g->st); ++nl;
   // projector normalisation on the global grid (one image per atom, wrapped box)
   std::vector<double> norms(4 * (size_t)n_atoms, 1.0);
-  if (n_atoms > 0) {
+  if (same_geometry) norms = g->norm_cache;
+  if (n_atoms > 0 && !same_geometry) {
     std::vector<AtomImg> glob(n_atoms);
     std::vector<ProjSlot> gslot(n_atoms);
     for (int i = 0; i < n_atoms; ++i) {
@@ -1902,13 +1987,15 @@ xls_status xls_hamiltonian_set(xls_grid g, const double* veff, int veff_on_devic
     XLS_CUDA(cudaMalloc(&dn, 4 * (size_t)n_atoms * sizeof(double)));
     XLS_CUDA(cudaMemcpyAsync(dglob, glob.data(), n_atoms * sizeof(AtomImg), cudaMemcpyHostToDevice, g->st));
     XLS_CUDA(cudaMemcpyAsync(dgs, gslot.data(), n_atoms * sizeof(ProjSlot), cudaMemcpyHostToDevice, g->st));
-    launch_proj_norms(dglob, dgs, n_atoms, g->gn, g->gh, dn, g->st);
+    launch_proj_norms(dglob, dgs, n_atoms, g->gn, g->gh, dn, g->st); ++nl;
     XLS_CUDA(cudaMemcpyAsync(norms.data(), dn, 4 * (size_t)n_atoms * sizeof(double), cudaMemcpyDeviceToHost, g->st));
     XLS_CUDA(cudaStreamSynchronize(g->st));
     cudaFree(dglob);
     cudaFree(dgs);
     cudaFree(dn);
   }
+  g->norm_cache = norms;
+  g->norm_valid = true;
   const auto h1 = tnow();
   // projector slots (atom x subdomain) and their periodic images; the atoms are visited in the
   // Z-order (Morton order) of their grid cells of 8 points, so that consecutive slots of a
@@ -1989,7 +2076,7 @@ xls_status xls_hamiltonian_set(xls_grid g, const double* veff, int veff_on_devic
   if (!slots.empty()) {
     int* dcnt = nullptr;
     XLS_CUDA(cudaMalloc(&dcnt, slots.size() * sizeof(int)));
-    launch_proj_table_count<double>(g->d_subs, g->d_slots, g->n_slot, g->d_imgs, dcnt, g->st);
+    launch_proj_table_count<double>(g->d_subs, g->d_slots, g->n_slot, g->d_imgs, dcnt, g->st); ++nl;
     std::vector<int> cnt(slots.size());
     XLS_CUDA(cudaMemcpyAsync(cnt.data(), dcnt, cnt.size() * sizeof(int), cudaMemcpyDeviceToHost, g->st));
     XLS_CUDA(cudaStreamSynchronize(g->st));
@@ -2003,10 +2090,10 @@ xls_status xls_hamiltonian_set(xls_grid g, const double* veff, int veff_on_devic
     XLS_CUDA(cudaMemcpyAsync(g->d_slots, slots.data(), slots.size() * sizeof(ProjSlot), cudaMemcpyHostToDevice, g->st));
     if ((s = g->alloc(&g->d_pidx, std::max<long long>(tot, 1) * sizeof(int))) != XLS_OK) return s;
     if ((s = g->alloc(&g->d_chi64, std::max<long long>(tot, 1) * sizeof(double4))) != XLS_OK) return s;
-    launch_proj_table_fill<double>(g->d_subs, g->d_slots, g->n_slot, g->d_imgs, g->d_pidx, g->d_chi64, g->st);
+    launch_proj_table_fill<double>(g->d_subs, g->d_slots, g->n_slot, g->d_imgs, g->d_pidx, g->d_chi64, g->st); ++nl;
     if (g->prec != XLS_FP64) {
       if ((s = g->alloc(&g->d_chi32, std::max<long long>(tot, 1) * sizeof(float4))) != XLS_OK) return s;
-      launch_proj_table_fill<float>(g->d_subs, g->d_slots, g->n_slot, g->d_imgs, g->d_pidx, g->d_chi32, g->st);
+      launch_proj_table_fill<float>(g->d_subs, g->d_slots, g->n_slot, g->d_imgs, g->d_pidx, g->d_chi32, g->st); ++nl;
     }
     // reverse tables: count per grid point, exclusive prefix (host), fill
     g->release(&g->d_rptr);
@@ -2018,12 +2105,12 @@ xls_status xls_hamiltonian_set(xls_grid g, const double* veff, int veff_on_devic
     XLS_CUDA(cudaMalloc(&dc, g->tot_pts * sizeof(int)));
     XLS_CUDA(cudaMalloc(&dcur, g->tot_pts * sizeof(int)));
     XLS_CUDA(cudaMemsetAsync(dc, 0, g->tot_pts * sizeof(int), g->st));
-    launch_rcsr_count(g->d_subs, g->d_slots, g->n_slot, g->d_pidx, dc, g->st);
+    launch_rcsr_count(g->d_subs, g->d_slots, g->n_slot, g->d_pidx, dc, g->st); ++nl;
     // row pointers by a device prefix sum; only the total comes back to size the tables
     if ((s = g->alloc(&g->d_rptr, (g->tot_pts + 1) * sizeof(long long))) != XLS_OK) return s;
     long long* dtmp = nullptr;
     XLS_CUDA(cudaMalloc(&dtmp, scan_temp_count(g->tot_pts) * sizeof(long long)));
-    launch_exclusive_scan(dc, g->tot_pts, dtmp, g->d_rptr, g->st);
+    launch_exclusive_scan(dc, g->tot_pts, dtmp, g->d_rptr, g->st); nl += 3;
     long long n_entries = 0;
     XLS_CUDA(cudaMemcpyAsync(&n_entries, g->d_rptr + g->tot_pts, sizeof(long long), cudaMemcpyDeviceToHost, g->st));
     XLS_CUDA(cudaStreamSynchronize(g->st));
@@ -2033,11 +2120,11 @@ xls_status xls_hamiltonian_set(xls_grid g, const double* veff, int veff_on_devic
     if ((s = g->alloc(&g->d_rchi64, std::max<long long>(rp.back(), 1) * sizeof(double4))) != XLS_OK) return s;
     XLS_CUDA(cudaMemsetAsync(dcur, 0, g->tot_pts * sizeof(int), g->st));
     launch_rcsr_build<double>(g->d_subs, g->d_slots, g->n_slot, g->d_pidx, g->d_chi64, g->d_rptr, dcur, g->d_rslot,
-                              g->d_rchi64, g->st);
+                              g->d_rchi64, g->st); ++nl;
     if (g->prec != XLS_FP64) {
       if ((s = g->alloc(&g->d_rchi32, std::max<long long>(rp.back(), 1) * sizeof(float4))) != XLS_OK) return s;
       // same entry order as the FP64 table (the fill order of the atomics is not reproducible)
-      launch_convert_f64_f32((const double*)g->d_rchi64, (float*)g->d_rchi32, 4 * rp.back(), g->st);
+      launch_convert_f64_f32((const double*)g->d_rchi64, (float*)g->d_rchi32, 4 * rp.back(), g->st); ++nl;
     }
     XLS_CUDA(cudaStreamSynchronize(g->st));
     cudaFree(dc);
@@ -2053,6 +2140,7 @@ xls_status xls_hamiltonian_set(xls_grid g, const double* veff, int veff_on_devic
     if ((s = g->alloc(&g->d_nlb_cnt, n_nlb * sizeof(int))) != XLS_OK) return s;
     XLS_CUDA(cudaMemcpyAsync(g->d_nlb_sub, nlb_sub.data(), n_nlb * sizeof(int), cudaMemcpyHostToDevice, g->st));
     launch_rcsr_localize(g->d_subs, g->d_nlb_sub, n_nlb, g->d_rptr, g->d_rslot, g->d_nlb_cnt, nullptr, 0, 0, g->st);
+    ++nl;
     std::vector<int> cnt_b(n_nlb);
     XLS_CUDA(cudaMemcpyAsync(cnt_b.data(), g->d_nlb_cnt, n_nlb * sizeof(int), cudaMemcpyDeviceToHost, g->st));
     XLS_CUDA(cudaStreamSynchronize(g->st));
@@ -2061,7 +2149,7 @@ xls_status xls_hamiltonian_set(xls_grid g, const double* veff, int veff_on_devic
     if ((s = g->alloc(&g->d_nlb_list, std::max<size_t>((size_t)n_nlb * g->nlb_max, 1) * sizeof(int))) != XLS_OK)
       return s;
     launch_rcsr_localize(g->d_subs, g->d_nlb_sub, n_nlb, g->d_rptr, g->d_rslot, g->d_nlb_cnt, g->d_nlb_list,
-                         g->nlb_max, 1, g->st);
+                         g->nlb_max, 1, g->st); ++nl;
     XLS_CUDA(cudaGetLastError());
   }
   const auto h2 = tnow();
@@ -2072,8 +2160,9 @@ xls_status xls_hamiltonian_set(xls_grid g, const double* veff, int veff_on_devic
   std::vector<double> bz(3 * g->n_sub, 1.0);
   for (int a = 0; a < g->n_sub; ++a) { bz[3 * a] = 2.0; bz[3 * a + 1] = 1.0; bz[3 * a + 2] = 0.0; }
   XLS_CUDA(cudaMemcpyAsync(g->bounds, bz.data(), bz.size() * sizeof(double), cudaMemcpyHostToDevice, g->st));
-  launch_filter_coef(g->n_sub, g->bounds, 1, g->coef, g->st);
+  launch_filter_coef(g->n_sub, g->bounds, 1, g->coef, g->st); ++nl;
   XLS_TRY(lanczos_bounds(g));
+  g->setup_launches = nl + 2 + 10 * ((g->n_slot ? 3 : 1) + 1);   // with the Lanczos steps
   if (trace) {
     cudaStreamSynchronize(g->st);
     std::fprintf(stderr, "[xls] hamiltonian_set: potential + norms %.1f ms, slots + tables %.1f ms, Lanczos %.1f ms\n",
@@ -2373,17 +2462,14 @@ xls_status xls_wave_store_fp16(xls_grid g, int on) {
   if (!g->wave) return fail(XLS_EINVAL, "xls_wave_store_fp16: the grid is not running in waves");
   if ((on != 0) == g->store16) return XLS_OK;
   long long max_blk = 0;
-  int max_ns = 0;
-  for (const SubDev& S : g->subs) {
-    max_blk = std::max(max_blk, S.nd * S.ns);
-    max_ns = std::max(max_ns, S.ns);
-  }
+  for (const SubDev& S : g->subs) max_blk = std::max(max_blk, S.nd * S.ns);
   if (!g->stage16) {
     if (cudaMalloc(&g->stage16, (size_t)max_blk * 2) != cudaSuccess ||
-        cudaMalloc((void**)&g->stage_ex, (size_t)max_ns * sizeof(int)) != cudaSuccess) {
+        cudaMalloc((void**)&g->d_store_ex, (size_t)g->tot_states * sizeof(int)) != cudaSuccess) {
       cudaGetLastError();
       return fail(XLS_ENOMEM, "xls_wave_store_fp16: device staging could not be allocated");
     }
+    XLS_CUDA(cudaMemsetAsync(g->d_store_ex, 0, (size_t)g->tot_states * sizeof(int), g->st));
   }
   // new store; the orbitals held so far move over through the device
   const bool to16 = on != 0;
@@ -2396,7 +2482,6 @@ xls_status xls_wave_store_fp16(xls_grid g, int on) {
   std::memset(ns_, 0, (size_t)g->tot_blk * new_elem);
   void* old = g->store;
   const bool was16 = g->store16;
-  if (to16) g->store_ex.assign((size_t)g->tot_states, 0);
   for (int a = 0; a < g->n_sub && g->orb_set; ++a) {
     g->store = old;
     g->store16 = was16;

@@ -162,6 +162,14 @@ void launch_nl_back_csr(const SubDev* d_subs, int n_sub, long long max_nd, int m
                         const long long* row_ptr, const int* rslot, const typename Vec4<T>::type* rchi,
                         const int* blk_cnt, const int* blk_list, const double* P, T* Yout, const StepCoef* coef,
                         int step, cudaStream_t st);
+// single-vector views (ns = 1 per subdomain): one warp per slot; one thread per grid point
+template <typename T>
+void launch_nl_project1(const SubDev* d_subs, const ProjSlot* d_slots, int n_slot, const int* idx,
+                        const typename Vec4<T>::type* chi, const T* Y, double* P, cudaStream_t st);
+template <typename T>
+void launch_nl_back1(const SubDev* d_subs, int n_sub, long long max_nd, int list_max, const long long* row_ptr,
+                     const int* rslot, const typename Vec4<T>::type* rchi, const int* blk_list, const double* P,
+                     T* Yout, const StepCoef* coef, int step, cudaStream_t st);
 template <typename T>
 void launch_nl_back(const SubDev* d_subs, const ProjSlot* d_slots, int n_slot, const int* idx,
                     const typename Vec4<T>::type* chi, int max_ns, const double* P, T* Yout, const StepCoef* coef,
@@ -187,8 +195,8 @@ void launch_rotate(const SubDev* d_subs, int n_sub, int max_ns, long long max_nd
 template <typename T>
 void launch_core_weights(const SubDev* d_subs, int n_sub, int max_ns, const T* Psi, double* c, cudaStream_t st);
 template <typename T>
-void launch_core_gather(const SubDev* d_subs, int n_sub, int max_ns, const T* Psi, T* store, long long base,
-                        long long per_sub, cudaStream_t st);
+void launch_core_gather(const SubDev* d_subs, int n_sub, int max_ns, const T* Psi, T* store, const SubDev* d_dst,
+                        cudaStream_t st);
 template <typename T>
 void launch_density_occ(const SubDev* d_subs, int n_sub, long long max_core, const T* Psi, const double* occ,
                         const int gn[3], double* rho, cudaStream_t st);
