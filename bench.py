@@ -387,7 +387,8 @@ def run_si64(args):
                        "states": int(w.n_states[0]), "degree": w.degree,
                        "l2": "inputs larger than L2 (each orbital block 566 MB)",
                        "parallelism": f"replicas x{ws}" if ws > 1 else "single GPU",
-                       "autotuned": {"eig_cluster_ctas": tune[0], "gram_ctas_per_sm": tune[1]}},
+                       "autotuned": {"eig_cluster_ctas": tune[0], "gram_ctas_per_sm": tune[1],
+                                     "projection_vectors_per_cta": tune[2]}},
             "stage_ms": dict({k: round(float(v), 3) for k, v in zip(["filter", "projection", "eig", "rotation"], stage_ms)},
                              density=round(density_ms, 3)),
             "kernel_share": kernel_share,
@@ -645,7 +646,8 @@ def run_si13824(args):
                        "l2": "inputs larger than L2 (each subdomain's orbital block "
                              f"{nd * ns * elem / 1e6:.0f} MB)",
                        "parallelism": f"replicas x{ws}" if ws > 1 else "single GPU",
-                       "autotuned": {"eig_cluster_ctas": tune[0], "gram_ctas_per_sm": tune[1]}},
+                       "autotuned": {"eig_cluster_ctas": tune[0], "gram_ctas_per_sm": tune[1],
+                                     "projection_vectors_per_cta": tune[2]}},
             "pass_ms": round(pass_ms, 1),
             "stage_ms_per_wave": dict({k: round(float(v), 3) for k, v in
                                        zip(["filter", "projection", "eig", "rotation"], stage_ms)},

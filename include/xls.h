@@ -136,13 +136,15 @@ xls_status xls_chefsi_batch(xls_grid g, int degree, int n_passes, const double* 
  *   choices_out[0]: CTAs per subdomain cluster of the Cholesky factorisation and the
  *                   tridiagonalisation, 8 or 16 (0: clusters off, not tuned);
  *   choices_out[1]: K split of the tensor-core Gram, in CTAs per SM aimed at, one of 1, 2, 3, 4,
- *                   6, 8 (0: no tensor-core Gram on this grid, not tuned).
+ *                   6, 8 (0: no tensor-core Gram on this grid, not tuned);
+ *   choices_out[2]: vectors per CTA of the nonlocal projection, 8, 16 or 32 (0: no projectors).
  * Every candidate runs `reps` (1..100) times after one warm-up call, timed with CUDA events on
  * the grid's stream.  The input is the last pass's M_s and H_s: they and the split exponents are
  * saved and put back, the eigenpairs recomputed with the chosen configuration, so the next pass
  * differs from an untuned one by rounding only.  Captured pass graphs are dropped (the next
  * graphed pass captures the tuned launches).  In wave carry mode it tunes the worker on the last
- * wave it ran (the choices hold for every wave: all have the same shapes).  choices_out may be NULL.
+ * wave it ran (the choices hold for every wave: all have the same shapes).  choices_out: NULL or
+ * room for 3 ints.
  * Errors: XLS_EINVAL (bad arguments, store-mode waves, no pass run yet), XLS_ENOMEM (no room for the
  * saved matrices), XLS_ECUDA, and the status of the eigensolve (XLS_ENOTSPD). */
 xls_status xls_autotune(xls_grid g, int reps, int* choices_out);

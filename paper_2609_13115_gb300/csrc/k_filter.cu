@@ -251,25 +251,26 @@ k_proj_fill(const SubDev* __restrict__ subs, const ProjSlot* __restrict__ slots,
 }
 
 // Projection P[slot][l][v] = E_l dV sum_g chi_l(g) Y_v(g).  A CTA takes one slot and a group of
-// kPV = 8 vectors; the grid runs group-major, so that the CTAs resident at any time read the
-// same 8-vector slice of every subdomain's block (tens of MB: it stays in L2 and each Y element,
-// shared by the about two spheres that contain its point, comes from DRAM about once).  Warp w
-// takes vectors 8 (w % kVH) .. +7 and every kPH-th 32-point chunk of the table from chunk
-// w / kVH; a lane two points at a time (16 loads in flight); lanes (transpose reduction) and
-// warps are reduced at the end.
-constexpr int kPV = 8;
+// KPV = 8, 16 or 32 vectors (the autotuner's choice); the grid runs group-major, so that the CTAs
+// resident at any time read the same KPV-vector slice of every subdomain's block (tens of MB: it
+// stays in L2 and each Y element, shared by the about two spheres that contain its point, comes
+// from DRAM about once).  Warp w takes vectors 8 (w % kVH) .. +7 and every kPH-th 32-point chunk
+// of the table from chunk w / kVH; a lane two points at a time (16 loads in flight); lanes
+// (transpose reduction) and warps are reduced at the end.  Wider groups read each table entry
+// once for more vectors (the warps of a CTA share it through L1) and split the slot's points
+// over fewer warps.
 // slots per chunk of the projection's CTA order: about one 72^3 subdomain's slots, whose tables
-// (~30 MB) and one vector group's Y slice (~12 MB) stay in L2 while the chunk is walked
+// (~30 MB) and one vector group's Y slice (~12 MB per 8 vectors) stay in L2 while the chunk is walked
 constexpr int kPChunk = 512;
-constexpr int kVH = kPV / 8, kPH = 8 / kVH;   // vector halves and point phases of the 8 warps
 
-template <typename T>
+template <typename T, int KPV>
 __global__ void __launch_bounds__(256)
 k_nl_project(const SubDev* __restrict__ subs, const ProjSlot* __restrict__ slots, int slot_off, int n_slot,
              int n_groups, const int* __restrict__ idx, const typename Vec4<T>::type* __restrict__ chi,
              const T* __restrict__ Y, double* __restrict__ P) {
   using T4 = typename Vec4<T>::type;
-  __shared__ T red[kPH][kPV * 4];
+  constexpr int kVH = KPV / 8, kPH = 8 / kVH;   // vector eighths and point phases of the 8 warps
+  __shared__ T red[kPH][KPV * 4];
   // CTAs walk the slots in chunks of kPChunk: every vector group runs over the chunk before the
   // next chunk starts, so the chunk's tables stay in L2 for all groups, and within a group the
   // points that neighbouring slots share are read from DRAM once
@@ -281,9 +282,9 @@ k_nl_project(const SubDev* __restrict__ subs, const ProjSlot* __restrict__ slots
   const SubDev& S = subs[A.sub];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int vh = warp % kVH, ph = warp / kVH;
-  const int v0 = grp * kPV + vh * 8;
+  const int v0 = grp * KPV + vh * 8;
   const int nv = max(0, min(8, S.ns - v0));
-  if (grp * kPV >= S.ns) return;   // uniform per CTA
+  if (grp * KPV >= S.ns) return;   // uniform per CTA
   T acc[4][8];
 #pragma unroll
   for (int l = 0; l < 4; ++l)
@@ -338,9 +339,9 @@ k_nl_project(const SubDev* __restrict__ subs, const ProjSlot* __restrict__ slots
   }
   red[ph][vh * 32 + lane] = a[0];
   __syncthreads();
-  if (threadIdx.x < kPV * 4) {
+  if (threadIdx.x < KPV * 4) {
     const int h = threadIdx.x / 32, l = (threadIdx.x / 8) % 4, v = threadIdx.x % 8;
-    const int vg = grp * kPV + h * 8 + v;
+    const int vg = grp * KPV + h * 8 + v;
     if (vg < S.ns) {
       T s = (T)0;
 #pragma unroll
@@ -797,14 +798,22 @@ void launch_proj_table_fill(const SubDev* d_subs, const ProjSlot* d_slots, int n
   if (n_slot) k_proj_fill<T><<<n_slot, 256, 0, st>>>(d_subs, d_slots, d_imgs, idx, chi);
 }
 
+template <typename T, int KPV>
+void launch_nl_project_w(const SubDev* d_subs, const ProjSlot* d_slots, int slot_off, int n_slot, const int* idx,
+                         const typename Vec4<T>::type* chi, int max_ns, const T* Y, double* P, cudaStream_t st) {
+  const int groups = (max_ns + KPV - 1) / KPV;
+  const int chunks = (n_slot + kPChunk - 1) / kPChunk;
+  k_nl_project<T, KPV><<<chunks * kPChunk * groups, 256, 0, st>>>(d_subs, d_slots, slot_off, n_slot, groups, idx, chi,
+                                                                  Y, P);
+}
+
 template <typename T>
 void launch_nl_project(const SubDev* d_subs, const ProjSlot* d_slots, int slot_off, int n_slot, const int* idx,
-                       const typename Vec4<T>::type* chi, int max_ns, const T* Y, double* P, cudaStream_t st) {
+                       const typename Vec4<T>::type* chi, int max_ns, const T* Y, double* P, int kpv, cudaStream_t st) {
   if (n_slot == 0) return;
-  const int groups = (max_ns + kPV - 1) / kPV;
-  const int chunks = (n_slot + kPChunk - 1) / kPChunk;
-  k_nl_project<T><<<chunks * kPChunk * groups, 256, 0, st>>>(d_subs, d_slots, slot_off, n_slot, groups, idx, chi, Y,
-                                                             P);
+  if (kpv == 32) launch_nl_project_w<T, 32>(d_subs, d_slots, slot_off, n_slot, idx, chi, max_ns, Y, P, st);
+  else if (kpv == 16) launch_nl_project_w<T, 16>(d_subs, d_slots, slot_off, n_slot, idx, chi, max_ns, Y, P, st);
+  else launch_nl_project_w<T, 8>(d_subs, d_slots, slot_off, n_slot, idx, chi, max_ns, Y, P, st);
 }
 
 template <typename T>
@@ -821,7 +830,7 @@ void launch_nl_back(const SubDev* d_subs, const ProjSlot* d_slots, int n_slot, c
   template void launch_proj_table_fill<T>(const SubDev*, const ProjSlot*, int, const AtomImg*, int*,                 \
                                           Vec4<T>::type*, cudaStream_t);                                             \
   template void launch_nl_project<T>(const SubDev*, const ProjSlot*, int, int, const int*, const Vec4<T>::type*,     \
-                                     int, const T*, double*, cudaStream_t);                                          \
+                                     int, const T*, double*, int, cudaStream_t);                                     \
   template void launch_nl_back<T>(const SubDev*, const ProjSlot*, int, const int*, const Vec4<T>::type*, int,        \
                                   const double*, T*, const StepCoef*, int, cudaStream_t);                            \
   template void launch_rcsr_build<T>(const SubDev*, const ProjSlot*, int, const int*, const Vec4<T>::type*,         \

@@ -110,6 +110,7 @@ struct xls_grid_s {
   std::vector<double> norm_cache;
   bool norm_valid = false;
   int setup_launches = 0;   // kernels of the last xls_hamiltonian_set
+  int proj_vec = 8;         // vectors per CTA of the projection (8, 16 or 32; xls_autotune)
   // concurrent halves (XLS_CONCURRENT=1): the subdomains split in two views whose passes run on
   // two streams, half 1's filter beside half 0's projection, eigensolve and rotation
   struct View {
@@ -327,7 +328,8 @@ void h_step(xls_grid g, bool one, const T* yin, const T* yprev, T* yout, int ste
   const T* V = (sizeof(T) == 8) ? (const T*)g->V : (const T*)g->Vf;
   { ProfScope ps(g, K_NLPROJ);
     if (one) launch_nl_project1<T>(ds, g->d_slots, g->n_slot, g->d_pidx, chi_table<T>(g), yin, P, g->st);
-    else launch_nl_project<T>(ds, g->d_slots, 0, g->n_slot, g->d_pidx, chi_table<T>(g), mns, yin, P, g->st); }
+    else launch_nl_project<T>(ds, g->d_slots, 0, g->n_slot, g->d_pidx, chi_table<T>(g), mns, yin, P, g->proj_vec,
+                              g->st); }
   { ProfScope ps(g, K_STENCIL); launch_stencil<T>(ds, g->n_sub, pl, yin, yprev, yout, V, g->coef, step, g->st); }
   { ProfScope ps(g, K_NLBACK);
     if (one)
@@ -364,7 +366,7 @@ void h_step_main(xls_grid g, const xls_grid_s::View& v, int bin, int bprev, int 
   }
   { ProfScope ps(g, K_NLPROJ);
     launch_nl_project<T>(g->d_subs, g->d_slots, v.slot_off, v.n_slot, g->d_pidx, chi_table<T>(g), v.max_ns, yin, g->P,
-                         side ? g->side_st : v.st); }
+                         g->proj_vec, side ? g->side_st : v.st); }
   if (side) cudaEventRecord(g->ev_side_out, g->side_st);
   if (sizeof(T) == 4 && g->use_tma) {
     ProfScope ps(g, K_STENCIL);
@@ -1269,6 +1271,8 @@ xls_status create_grid(const xls_cell* cell, const xls_dc* dc, int precision, si
     g->eig_cluster = !(env && std::string(env) == "single");
     const char* ecl = std::getenv("XLS_EIG_CL");   // cluster size tried first (xls_autotune changes it)
     if (ecl && std::atoi(ecl) == 16) g->eig_cl = 16;
+    const char* pv = std::getenv("XLS_PROJ_VEC");  // projection vectors per CTA (xls_autotune changes it)
+    if (pv && (std::atoi(pv) == 16 || std::atoi(pv) == 32)) g->proj_vec = std::atoi(pv);
   }
   if (precision != XLS_FP64) {
     const char* env = std::getenv("XLS_GEMM");
@@ -2360,6 +2364,29 @@ xls_status xls_autotune(xls_grid g, int reps, int* choices_out) {
     g->gram_cps = best;
     replan_all();
   }
+  // (3) vectors per CTA of the nonlocal projection, timed on the current block (the projection
+  // coefficients it overwrites are recomputed at the start of every filter step)
+  if (rc == XLS_OK && g->n_slot > 0) {
+    int best = g->proj_vec;
+    float bt = -1.f;
+    for (int kpv : {8, 16, 32}) {
+      const float t = time_it([&] {
+        if (g->prec == XLS_FP64)
+          launch_nl_project<double>(g->d_subs, g->d_slots, 0, g->n_slot, g->d_pidx, g->d_chi64, g->max_ns,
+                                    (const double*)g->blk[g->cur], g->P, kpv, st);
+        else
+          launch_nl_project<float>(g->d_subs, g->d_slots, 0, g->n_slot, g->d_pidx, g->d_chi32, g->max_ns,
+                                   (const float*)g->blk[g->cur], g->P, kpv, st);
+      });
+      if (rc != XLS_OK) break;
+      if (std::getenv("XLS_TRACE")) std::fprintf(stderr, "[xls] autotune: projection %d vectors per CTA %.3f ms\n", kpv, t);
+      if (bt < 0.f || t < bt) {
+        bt = t;
+        best = kpv;
+      }
+    }
+    g->proj_vec = best;
+  }
   // the saved matrices and exponents back; eigenpairs of the last pass recomputed with the
   // chosen configuration; passes captured with the old launch shapes dropped
   cuda_ok(cudaMemcpyAsync(g->Ms, save, ss, cudaMemcpyDeviceToDevice, st));
@@ -2380,6 +2407,7 @@ xls_status xls_autotune(xls_grid g, int reps, int* choices_out) {
   if (choices_out) {
     choices_out[0] = g->eig_cluster ? g->eig_cl : 0;
     choices_out[1] = tc_gram ? g->gram_cps : 0;
+    choices_out[2] = g->n_slot > 0 ? g->proj_vec : 0;
   }
   return rc;
 }

@@ -214,10 +214,11 @@ def xls_chefsi_batch(g, degree, n_passes, bounds=None):
 
 def xls_autotune(g, reps=5):
     """Time the tunable launch configurations on the grid's data, keep the fastest; returns
-    (cluster CTAs of the factorisations, Gram CTAs per SM aimed at), 0 where not tuned."""
-    out = np.zeros(2, dtype=np.int32)
+    (cluster CTAs of the factorisations, Gram CTAs per SM aimed at, projection vectors per CTA),
+    0 where not tuned."""
+    out = np.zeros(3, dtype=np.int32)
     _check(load().xls_autotune(g, int(reps), out.ctypes.data_as(c_void_p)))
-    return int(out[0]), int(out[1])
+    return int(out[0]), int(out[1]), int(out[2])
 
 
 def xls_chefsi_stage(g, stage, degree, bounds=None):

@@ -860,9 +860,10 @@ def test_autotune_keeps_results(prec):
             xls.xls_chefsi_batch(g.h, w.degree, 2)
             if mode == "tuned":
                 before = [xls.xls_get_subspace(g.h, a, int(w.n_states[a])) for a in range(w.n_sub)]
-                cl, cps = xls.xls_autotune(g.h, 2)
+                cl, cps, kpv = xls.xls_autotune(g.h, 2)
                 assert cl in (8, 16), cl
                 assert cps in ((0,) if prec == xls.XLS_FP64 else (1, 2, 3, 4, 6, 8)), cps
+                assert kpv in (8, 16, 32), kpv
                 for a in range(w.n_sub):
                     ms, hs = xls.xls_get_subspace(g.h, a, int(w.n_states[a]))
                     assert np.array_equal(ms, before[a][0]) and np.array_equal(hs, before[a][1])
