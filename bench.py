@@ -707,18 +707,18 @@ def si13824_precision(args, prec) -> dict:
             "mu_fp64": mu64, "mu_mixed": mum}
 
 
-# DRAM bytes (read + write) of one FP32 stencil launch over a wave of 72 subdomains of 72^3 with
-# 528 states, measured by ncu for the kernel source whose SHA-256 starts with the key
 # DRAM bytes (read + write) per 72^3 subdomain with 528 states of one FP32 stencil launch, measured by ncu
-# on a wave of 2 subdomains (4.699759e9 bytes) for the kernel source whose SHA-256 starts with the key; a
-# launch over W subdomains moves W times this (the traffic grows with the subdomains a launch covers)
-STENCIL_TRAFFIC_13824 = {"056189a407e3c6e6": 4.699759e9 / 2}
+# on a wave of 2 subdomains (4.699759e9 bytes) for the device code (k_stencil_tma.cu from the namespace
+# to the host-side section) whose SHA-256 starts with the key; a launch over W subdomains moves W times
+# this (the traffic grows with the subdomains a launch covers)
+STENCIL_TRAFFIC_13824 = {"5838d36516e2b97b": 4.699759e9 / 2}
 
 
 def stencil_traffic_13824(n_sub_launch: int, n_states: int):
     import hashlib
-    src = os.path.join(ROOT, "paper_2609_13115_gb300", "csrc", "k_stencil_tma.cu")
-    h = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+    src = open(os.path.join(ROOT, "paper_2609_13115_gb300", "csrc", "k_stencil_tma.cu"), "rb").read()
+    dev = src[src.index(b"namespace xls {"):src.index(b"// ---- host side")]
+    h = hashlib.sha256(dev).hexdigest()[:16]
     per_sub = STENCIL_TRAFFIC_13824.get(h)
     if per_sub is None or n_states != 528:
         return None

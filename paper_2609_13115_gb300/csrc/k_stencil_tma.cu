@@ -533,8 +533,9 @@ void launch_stencil_tma(const SubDev* d_subs, const TmaClass& cls, const CUtenso
     sw.wz[p] = both((float)fdw[p] * ihz);
   }
   sw.wc = both((float)fdw[0] * ihx + (float)fdw[0] * ihy + (float)fdw[0] * ihz);
-  // row pitches of the common subdomain widths as compile-time constants (immediate offsets)
-  switch (cls.W) {
+  // row pitches of the common subdomain widths as compile-time constants (immediate offsets),
+  // unless the class asks for the runtime pitch (xls_autotune times both)
+  switch (cls.rt_pitch ? 0 : cls.W) {
     case 80: launch_variant<80>(cls, smem, d_subs, d_maps, buf_in, buf_prev, Yout, coef, step, status, sw, st); break;
     case 112: launch_variant<112>(cls, smem, d_subs, d_maps, buf_in, buf_prev, Yout, coef, step, status, sw, st); break;
     default: launch_variant<0>(cls, smem, d_subs, d_maps, buf_in, buf_prev, Yout, coef, step, status, sw, st);

@@ -2387,6 +2387,39 @@ xls_status xls_autotune(xls_grid g, int reps, int* choices_out) {
     }
     g->proj_vec = best;
   }
+  // (4) slot pitch of the TMA stencil per class: compile-time (where one exists: 80, 112 floats)
+  // or runtime, timed on the current block into a free arena (its contents are scratch between
+  // passes); the choice goes to every view's class of the same pitch
+  if (rc == XLS_OK && g->prec != XLS_FP64 && g->use_tma) {
+    const int bin = g->cur, bprev = (g->cur + 2) % 3, bout = (g->cur + 1) % 3;
+    xls_grid_s::View& v = fv(g);
+    for (size_t i = 0; i < v.tcls.size(); ++i) {
+      if (v.tcls[i].W != 80 && v.tcls[i].W != 112) continue;
+      int best = v.tcls[i].rt_pitch;
+      float bt = -1.f;
+      for (int rt : {0, 1}) {
+        v.tcls[i].rt_pitch = rt;
+        const float t = time_it([&] {
+          launch_stencil_tma(v.ds, v.tcls[i], v.maps, bin, bprev, (float*)g->blk[bout], v.coef, 0, g->status, st);
+        });
+        if (rc != XLS_OK) break;
+        if (std::getenv("XLS_TRACE"))
+          std::fprintf(stderr, "[xls] autotune: stencil pitch %d (%s) %.3f ms\n", v.tcls[i].W, rt ? "runtime" : "compile-time", t);
+        if (bt < 0.f || t < bt) {
+          bt = t;
+          best = rt;
+        }
+      }
+      v.tcls[i].rt_pitch = best;
+      auto apply = [&](std::vector<TmaClass>& cl) {
+        for (TmaClass& c : cl)
+          if (c.W == v.tcls[i].W) c.rt_pitch = best;
+      };
+      apply(g->tcls);
+      if (g->concurrent)
+        for (auto& h : g->halves) apply(h.tcls);
+    }
+  }
   // the saved matrices and exponents back; eigenpairs of the last pass recomputed with the
   // chosen configuration; passes captured with the old launch shapes dropped
   cuda_ok(cudaMemcpyAsync(g->Ms, save, ss, cudaMemcpyDeviceToDevice, st));

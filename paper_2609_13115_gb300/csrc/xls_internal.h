@@ -78,6 +78,8 @@ struct TmaClass {
   int nq = 0, TY = 0, W = 0;   // threads per row (x-points / 4), rows per tile, row width
   double h[3] = {0, 0, 0};     // grid spacing shared by the class
   int n_jobs = 0, total = 0;   // subdomains and CTAs of the class
+  int rt_pitch = 1;            // 1: the runtime-pitch variant (the default: it measured faster for
+                               // 48- and 72-point rows); 0: the compile-time variant where one exists
   TmaJob* d_jobs = nullptr;
   int* d_job_off = nullptr;    // [n_jobs + 1] CTA prefix
 };
