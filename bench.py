@@ -389,6 +389,7 @@ def run_si64(args):
                        "parallelism": f"replicas x{ws}" if ws > 1 else "single GPU",
                        "autotuned": {"eig_cluster_ctas": tune[0], "gram_ctas_per_sm": tune[1],
                                      "projection_vectors_per_cta": tune[2]}},
+            "filter_gpt_vec_s": round(units / (float(stage_ms[0]) / 1e3) / 1e9, 3),
             "stage_ms": dict({k: round(float(v), 3) for k, v in zip(["filter", "projection", "eig", "rotation"], stage_ms)},
                              density=round(density_ms, 3)),
             "kernel_share": kernel_share,
@@ -649,6 +650,8 @@ def run_si13824(args):
                        "autotuned": {"eig_cluster_ctas": tune[0], "gram_ctas_per_sm": tune[1],
                                      "projection_vectors_per_cta": tune[2]}},
             "pass_ms": round(pass_ms, 1),
+            # the same point-vectors over the filter stage's time alone (the filter-only rate)
+            "filter_gpt_vec_s": round(units_wave / (float(stage_ms[0]) / 1e3) / 1e9, 3),
             "stage_ms_per_wave": dict({k: round(float(v), 3) for k, v in
                                        zip(["filter", "projection", "eig", "rotation"], stage_ms)},
                                       density_per_cycle=round(density_ms, 3)),
@@ -826,6 +829,7 @@ def run_si4014(args):
                        "degree": w.degree, "waves": n_waves, "host_store": "fp16",
                        "step": "one full pass over every wave (orbitals up from and back to the host store), "
                                "Fermi level and density"},
+            "filter_gpt_vec_s": round(units / (float(stage_ms[0]) / 1e3) / 1e9, 3),
             "stage_ms": {k: round(float(v), 1) for k, v in zip(["filter", "projection", "eig", "rotation"], stage_ms)},
             "gpu_launches": int(launches) * args.steps, "clocks": clocks,
             "mu": mu, "e_band_per_atom": eb / len(w.pos)}))

@@ -138,7 +138,8 @@ xls_status xls_chefsi_batch(xls_grid g, int degree, int n_passes, const double* 
  *   choices_out[1]: K split of the tensor-core Gram, in CTAs per SM aimed at, one of 1, 2, 3, 4,
  *                   6, 8 (0: no tensor-core Gram on this grid, not tuned);
  *   choices_out[2]: vectors per CTA of the nonlocal projection, 8, 16 or 32 (0: no projectors).
- * It also times, per class of the FP32 TMA stencil whose slot pitch has a compile-time variant
+ * It also times the back-projection with one and with two grid points per thread and, per class
+ * of the FP32 TMA stencil whose slot pitch has a compile-time variant
  * (80 or 112 floats), that variant against the runtime-pitch one (the default) and keeps the
  * faster (not reported; XLS_TRACE=1 prints the timings).
  * Every candidate runs `reps` (1..100) times after one warm-up call, timed with CUDA events on

@@ -562,8 +562,11 @@ void launch_rcsr_localize(const SubDev* d_subs, const int* d_blk_sub, int n_blk,
   if (n_blk > 0) k_rcsr_localize<<<n_blk, 256, 0, st>>>(d_subs, d_blk_sub, row_ptr, rslot, blk_cnt, blk_list, list_max, pass);
 }
 
-// Y_out[v][g] += scale * sum over the slots s of point g of sum_l chi_l(g) P[s][l][v]
-template <typename T>
+// Y_out[v][g] += scale * sum over the slots s of point g of sum_l chi_l(g) P[s][l][v]; PPT
+// points per thread per iteration (1 or 2, timed by xls_autotune: two give each thread more
+// loads in flight, one fewer registers and so more resident warps; one measured 9 % faster on
+// 72^3 subdomains with 528 states and is the default)
+template <typename T, int PPT>
 __global__ void __launch_bounds__(256)
 k_nl_back_csr(const SubDev* __restrict__ subs, const long long* __restrict__ row_ptr, const int* __restrict__ rslot,
               const typename Vec4<T>::type* __restrict__ rchi, const int* __restrict__ blk_cnt,
@@ -599,65 +602,52 @@ k_nl_back_csr(const SubDev* __restrict__ subs, const long long* __restrict__ row
   __syncthreads();
   T* yb = Yout + S.off_blk + (long long)v0 * S.nd;
   const long long end = min(S.nd, p0 + kBackPts);
-  // two points per thread per iteration; the sum over the table rows is formed in registers and
+  // PPT points per thread per iteration; the sum over the table rows is formed in registers and
   // added to Y_out with fire-and-forget reductions (red.global.add): the read-modify-write happens
   // in L2, no load of Y sits on the thread's critical path, and each element receives exactly one
   // addition (deterministic)
-  // the row bounds of the next iteration's two points are fetched one iteration ahead, so that
-  // only the table entries (not the row pointers before them) wait on memory
+  // the row bounds of the next iteration's points are fetched one iteration ahead, so that only
+  // the table entries (not the row pointers before them) wait on memory
   const long long* rp = row_ptr + S.off_pt;
+  const long long stride = (long long)PPT * blockDim.x;
   long long g = p0 + threadIdx.x;
-  long long nA0 = 0, nA1 = 0, nB0 = 0, nB1 = 0;
-  if (g < end) {
-    nA0 = rp[g];
-    nA1 = rp[g + 1];
-    if (g + blockDim.x < end) {
-      nB0 = rp[g + blockDim.x];
-      nB1 = rp[g + blockDim.x + 1];
-    }
+  long long nr0[PPT], nr1[PPT];
+#pragma unroll
+  for (int u = 0; u < PPT; ++u) {
+    const long long gu = g + (long long)u * blockDim.x;
+    nr0[u] = gu < end ? rp[gu] : 0;
+    nr1[u] = gu < end ? rp[gu + 1] : 0;
   }
-  for (; g < end; g += 2 * blockDim.x) {
-    const long long gB = g + blockDim.x;
-    const bool hasB = gB < end;
-    const long long rA0 = nA0, rA1 = nA1, rB0 = hasB ? nB0 : 0, rB1 = hasB ? nB1 : 0;
-    {
-      const long long gn = g + 2 * blockDim.x;
-      if (gn < end) {
-        nA0 = rp[gn];
-        nA1 = rp[gn + 1];
-        if (gn + blockDim.x < end) {
-          nB0 = rp[gn + blockDim.x];
-          nB1 = rp[gn + blockDim.x + 1];
+  for (; g < end; g += stride) {
+    long long r0[PPT], r1[PPT];
+#pragma unroll
+    for (int u = 0; u < PPT; ++u) {
+      r0[u] = nr0[u];
+      r1[u] = nr1[u];
+      const long long gn = g + stride + (long long)u * blockDim.x;
+      nr0[u] = gn < end ? rp[gn] : 0;
+      nr1[u] = gn < end ? rp[gn + 1] : 0;
+    }
+#pragma unroll
+    for (int u = 0; u < PPT; ++u) {
+      const long long gu = g + (long long)u * blockDim.x;
+      if (gu >= end || r1[u] == r0[u]) continue;
+      T y[kBackVec];
+#pragma unroll
+      for (int v = 0; v < kBackVec; ++v) y[v] = (T)0;
+      for (long long e = r0[u]; e < r1[u]; ++e) {
+        const int sl = rslot[e];
+        const T4 c = rchi[e];
+        const T4* qq = Qs + sl * kBackRow;
+#pragma unroll
+        for (int v = 0; v < kBackVec; ++v) {
+          const T4 q = qq[v];
+          y[v] += c.x * q.x + c.y * q.y + c.z * q.z + c.w * q.w;
         }
       }
-    }
-    T yA[kBackVec], yB[kBackVec];
 #pragma unroll
-    for (int v = 0; v < kBackVec; ++v) yA[v] = yB[v] = (T)0;
-    for (long long e = rA0; e < rA1; ++e) {
-      const int sl = rslot[e];
-      const T4 c = rchi[e];
-      const T4* qq = Qs + sl * kBackRow;
-#pragma unroll
-      for (int v = 0; v < kBackVec; ++v) {
-        const T4 q = qq[v];
-        yA[v] += c.x * q.x + c.y * q.y + c.z * q.z + c.w * q.w;
-      }
-    }
-    for (long long e = rB0; e < rB1; ++e) {
-      const int sl = rslot[e];
-      const T4 c = rchi[e];
-      const T4* qq = Qs + sl * kBackRow;
-#pragma unroll
-      for (int v = 0; v < kBackVec; ++v) {
-        const T4 q = qq[v];
-        yB[v] += c.x * q.x + c.y * q.y + c.z * q.z + c.w * q.w;
-      }
-    }
-#pragma unroll
-    for (int v = 0; v < kBackVec; ++v) {
-      if (v < nv && rA1 > rA0) atomicAdd(yb + (long long)v * S.nd + g, yA[v]);
-      if (v < nv && rB1 > rB0) atomicAdd(yb + (long long)v * S.nd + gB, yB[v]);
+      for (int v = 0; v < kBackVec; ++v)
+        if (v < nv) atomicAdd(yb + (long long)v * S.nd + gu, y[v]);
     }
   }
 }
@@ -777,14 +767,13 @@ template <typename T>
 void launch_nl_back_csr(const SubDev* d_subs, int n_sub, long long max_nd, int max_ns, int list_max,
                         const long long* row_ptr, const int* rslot, const typename Vec4<T>::type* rchi,
                         const int* blk_cnt, const int* blk_list, const double* P, T* Yout, const StepCoef* coef,
-                        int step, cudaStream_t st) {
+                        int step, int ppt, cudaStream_t st) {
   if (list_max == 0) return;
   const size_t smem = (size_t)list_max * kBackRow * sizeof(typename Vec4<T>::type);
-  if (smem > 48 * 1024)
-    cudaFuncSetAttribute(k_nl_back_csr<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  auto kern = ppt == 1 ? k_nl_back_csr<T, 1> : k_nl_back_csr<T, 2>;
+  if (smem > 48 * 1024) cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   dim3 grid((max_ns + kBackVec - 1) / kBackVec, (unsigned)((max_nd + kBackPts - 1) / kBackPts), n_sub);
-  k_nl_back_csr<T><<<grid, 256, smem, st>>>(d_subs, row_ptr, rslot, rchi, blk_cnt, blk_list, list_max, P, Yout, coef,
-                                            step);
+  kern<<<grid, 256, smem, st>>>(d_subs, row_ptr, rslot, rchi, blk_cnt, blk_list, list_max, P, Yout, coef, step);
 }
 
 template <typename T>
@@ -837,7 +826,7 @@ void launch_nl_back(const SubDev* d_subs, const ProjSlot* d_slots, int n_slot, c
                                      const long long*, int*, int*, Vec4<T>::type*, cudaStream_t);                    \
   template void launch_nl_back_csr<T>(const SubDev*, int, long long, int, int, const long long*, const int*,        \
                                       const Vec4<T>::type*, const int*, const int*, const double*, T*,                \
-                                      const StepCoef*, int, cudaStream_t);                                            \
+                                      const StepCoef*, int, int, cudaStream_t);                                       \
   template void launch_nl_project1<T>(const SubDev*, const ProjSlot*, int, const int*, const Vec4<T>::type*,         \
                                       const T*, double*, cudaStream_t);                                               \
   template void launch_nl_back1<T>(const SubDev*, int, long long, int, const long long*, const int*,                \

@@ -110,7 +110,11 @@ struct xls_grid_s {
   std::vector<double> norm_cache;
   bool norm_valid = false;
   int setup_launches = 0;   // kernels of the last xls_hamiltonian_set
+  void* scr_a = nullptr;    // set-up scratch (counts, row cursors, scan partial sums), reserved
+  void* scr_b = nullptr;
+  void* scr_c = nullptr;
   int proj_vec = 8;         // vectors per CTA of the projection (8, 16 or 32; xls_autotune)
+  int back_ppt = 1;         // points per thread of the back-projection (1 or 2; xls_autotune)
   // concurrent halves (XLS_CONCURRENT=1): the subdomains split in two views whose passes run on
   // two streams, half 1's filter beside half 0's projection, eigensolve and rotation
   struct View {
@@ -225,6 +229,24 @@ struct xls_grid_s {
   double kms[8] = {0, 0, 0, 0, 0, 0, 0, 0};
   int kcnt[8] = {0, 0, 0, 0, 0, 0, 0, 0};
 
+  // capacity of the arrays made by reserve(): the operator tables rebuilt by every
+  // xls_hamiltonian_set keep their device memory while the new tables fit (a carry-mode worker
+  // re-targeted to every wave allocates them once)
+  std::vector<std::pair<void*, size_t>> caps;
+  template <typename P_>
+  xls_status reserve(P_** p, size_t bytes_) {
+    if (bytes_ == 0) bytes_ = 16;
+    for (auto& c : caps)
+      if (*p && c.first == (void*)*p) {
+        if (c.second >= bytes_) return XLS_OK;
+        c.first = nullptr;
+      }
+    release(p);
+    const xls_status s = alloc(p, bytes_);
+    if (s == XLS_OK) caps.push_back({(void*)*p, bytes_});
+    return s;
+  }
+
   template <typename P_>
   xls_status alloc(P_** p, size_t bytes_) {
     if (bytes_ == 0) bytes_ = 16;
@@ -337,7 +359,7 @@ void h_step(xls_grid g, bool one, const T* yin, const T* yprev, T* yout, int ste
                          P, yout, g->coef, step, g->st);
     else
       launch_nl_back_csr<T>(ds, g->n_sub, g->max_nd, mns, g->nlb_max, g->d_rptr, g->d_rslot, rchi_table<T>(g),
-                            g->d_nlb_cnt, g->d_nlb_list, P, yout, g->coef, step, g->st); }
+                            g->d_nlb_cnt, g->d_nlb_list, P, yout, g->coef, step, g->back_ppt, g->st); }
   g->launches += (g->n_slot ? 3 : 1);
 }
 
@@ -382,7 +404,7 @@ void h_step_main(xls_grid g, const xls_grid_s::View& v, int bin, int bprev, int 
   { ProfScope ps(g, K_NLBACK);
     launch_nl_back_csr<T>(v.ds, v.n, v.max_nd, v.max_ns, g->nlb_max, g->d_rptr, g->d_rslot, rchi_table<T>(g),
                           g->d_nlb_cnt, g->d_nlb_list, g->P,
-                          yout, v.coef, step, v.st); }
+                          yout, v.coef, step, g->back_ppt, v.st); }
   g->launches += (v.n_slot ? 2 : 0);
 }
 
@@ -2057,16 +2079,12 @@ xls_status xls_hamiltonian_set(xls_grid g, const double* veff, int veff_on_devic
     for (long long p = 0; p < g->subs[a].nd; p += kBackPts) nlb_sub.push_back(a);
     if (g->subs[a].slot_n > 32768) return fail(XLS_EINVAL, "more than 32768 projector slots in one subdomain");
   }
-  g->release(&g->d_imgs);
-  g->release(&g->d_slots);
-  g->release(&g->P);
-  g->release(&g->P1);
   g->n_slot = (int)slots.size();
   xls_status s;
-  if ((s = g->alloc(&g->d_imgs, imgs.size() * sizeof(AtomImg))) != XLS_OK) return s;
-  if ((s = g->alloc(&g->d_slots, slots.size() * sizeof(ProjSlot))) != XLS_OK) return s;
-  if ((s = g->alloc(&g->P, std::max<long long>(poff, 1) * sizeof(double))) != XLS_OK) return s;
-  if ((s = g->alloc(&g->P1, std::max<size_t>(4 * slots.size(), 1) * sizeof(double))) != XLS_OK) return s;
+  if ((s = g->reserve(&g->d_imgs, imgs.size() * sizeof(AtomImg))) != XLS_OK) return s;
+  if ((s = g->reserve(&g->d_slots, slots.size() * sizeof(ProjSlot))) != XLS_OK) return s;
+  if ((s = g->reserve(&g->P, std::max<long long>(poff, 1) * sizeof(double))) != XLS_OK) return s;
+  if ((s = g->reserve(&g->P1, std::max<size_t>(4 * slots.size(), 1) * sizeof(double))) != XLS_OK) return s;
   if (!imgs.empty())
     XLS_CUDA(cudaMemcpyAsync(g->d_imgs, imgs.data(), imgs.size() * sizeof(AtomImg), cudaMemcpyHostToDevice, g->st));
   if (!slots.empty())
@@ -2074,17 +2092,14 @@ xls_status xls_hamiltonian_set(xls_grid g, const double* veff, int veff_on_devic
   XLS_CUDA(cudaMemcpyAsync(g->d_subs, g->subs.data(), g->n_sub * sizeof(SubDev), cudaMemcpyHostToDevice, g->st));
   XLS_CUDA(cudaMemcpyAsync(g->d_subs1, g->subs1.data(), g->n_sub * sizeof(SubDev), cudaMemcpyHostToDevice, g->st));
   // projector tables: count the points of every slot, lay the tables out, fill them
-  g->release(&g->d_pidx);
-  g->release(&g->d_chi64);
-  g->release(&g->d_chi32);
   if (!slots.empty()) {
     int* dcnt = nullptr;
-    XLS_CUDA(cudaMalloc(&dcnt, slots.size() * sizeof(int)));
+    if ((s = g->reserve(&g->scr_a, slots.size() * sizeof(int))) != XLS_OK) return s;
+    dcnt = (int*)g->scr_a;
     launch_proj_table_count<double>(g->d_subs, g->d_slots, g->n_slot, g->d_imgs, dcnt, g->st); ++nl;
     std::vector<int> cnt(slots.size());
     XLS_CUDA(cudaMemcpyAsync(cnt.data(), dcnt, cnt.size() * sizeof(int), cudaMemcpyDeviceToHost, g->st));
     XLS_CUDA(cudaStreamSynchronize(g->st));
-    cudaFree(dcnt);
     long long tot = 0;
     for (size_t k = 0; k < slots.size(); ++k) {
       slots[k].pt_off = tot;
@@ -2092,56 +2107,49 @@ xls_status xls_hamiltonian_set(xls_grid g, const double* veff, int veff_on_devic
       tot += cnt[k];
     }
     XLS_CUDA(cudaMemcpyAsync(g->d_slots, slots.data(), slots.size() * sizeof(ProjSlot), cudaMemcpyHostToDevice, g->st));
-    if ((s = g->alloc(&g->d_pidx, std::max<long long>(tot, 1) * sizeof(int))) != XLS_OK) return s;
-    if ((s = g->alloc(&g->d_chi64, std::max<long long>(tot, 1) * sizeof(double4))) != XLS_OK) return s;
+    if ((s = g->reserve(&g->d_pidx, std::max<long long>(tot, 1) * sizeof(int))) != XLS_OK) return s;
+    if ((s = g->reserve(&g->d_chi64, std::max<long long>(tot, 1) * sizeof(double4))) != XLS_OK) return s;
     launch_proj_table_fill<double>(g->d_subs, g->d_slots, g->n_slot, g->d_imgs, g->d_pidx, g->d_chi64, g->st); ++nl;
     if (g->prec != XLS_FP64) {
-      if ((s = g->alloc(&g->d_chi32, std::max<long long>(tot, 1) * sizeof(float4))) != XLS_OK) return s;
+      if ((s = g->reserve(&g->d_chi32, std::max<long long>(tot, 1) * sizeof(float4))) != XLS_OK) return s;
       launch_proj_table_fill<float>(g->d_subs, g->d_slots, g->n_slot, g->d_imgs, g->d_pidx, g->d_chi32, g->st); ++nl;
     }
-    // reverse tables: count per grid point, exclusive prefix (host), fill
-    g->release(&g->d_rptr);
-    g->release(&g->d_rslot);
-    g->release(&g->d_rchi64);
-    g->release(&g->d_rchi32);
+    // reverse tables: count per grid point, exclusive prefix (device), fill
     int* dc = nullptr;
     int* dcur = nullptr;
-    XLS_CUDA(cudaMalloc(&dc, g->tot_pts * sizeof(int)));
-    XLS_CUDA(cudaMalloc(&dcur, g->tot_pts * sizeof(int)));
+    if ((s = g->reserve(&g->scr_a, g->tot_pts * sizeof(int))) != XLS_OK) return s;
+    if ((s = g->reserve(&g->scr_b, g->tot_pts * sizeof(int))) != XLS_OK) return s;
+    dc = (int*)g->scr_a;
+    dcur = (int*)g->scr_b;
     XLS_CUDA(cudaMemsetAsync(dc, 0, g->tot_pts * sizeof(int), g->st));
     launch_rcsr_count(g->d_subs, g->d_slots, g->n_slot, g->d_pidx, dc, g->st); ++nl;
     // row pointers by a device prefix sum; only the total comes back to size the tables
-    if ((s = g->alloc(&g->d_rptr, (g->tot_pts + 1) * sizeof(long long))) != XLS_OK) return s;
+    if ((s = g->reserve(&g->d_rptr, (g->tot_pts + 1) * sizeof(long long))) != XLS_OK) return s;
     long long* dtmp = nullptr;
-    XLS_CUDA(cudaMalloc(&dtmp, scan_temp_count(g->tot_pts) * sizeof(long long)));
+    if ((s = g->reserve(&g->scr_c, scan_temp_count(g->tot_pts) * sizeof(long long))) != XLS_OK) return s;
+    dtmp = (long long*)g->scr_c;
     launch_exclusive_scan(dc, g->tot_pts, dtmp, g->d_rptr, g->st); nl += 3;
     long long n_entries = 0;
     XLS_CUDA(cudaMemcpyAsync(&n_entries, g->d_rptr + g->tot_pts, sizeof(long long), cudaMemcpyDeviceToHost, g->st));
     XLS_CUDA(cudaStreamSynchronize(g->st));
-    cudaFree(dtmp);
     const std::vector<long long> rp{0, n_entries};   // rp.back(): the number of table entries
-    if ((s = g->alloc(&g->d_rslot, std::max<long long>(rp.back(), 1) * sizeof(int))) != XLS_OK) return s;
-    if ((s = g->alloc(&g->d_rchi64, std::max<long long>(rp.back(), 1) * sizeof(double4))) != XLS_OK) return s;
+    if ((s = g->reserve(&g->d_rslot, std::max<long long>(rp.back(), 1) * sizeof(int))) != XLS_OK) return s;
+    if ((s = g->reserve(&g->d_rchi64, std::max<long long>(rp.back(), 1) * sizeof(double4))) != XLS_OK) return s;
     XLS_CUDA(cudaMemsetAsync(dcur, 0, g->tot_pts * sizeof(int), g->st));
     launch_rcsr_build<double>(g->d_subs, g->d_slots, g->n_slot, g->d_pidx, g->d_chi64, g->d_rptr, dcur, g->d_rslot,
                               g->d_rchi64, g->st); ++nl;
     if (g->prec != XLS_FP64) {
-      if ((s = g->alloc(&g->d_rchi32, std::max<long long>(rp.back(), 1) * sizeof(float4))) != XLS_OK) return s;
+      if ((s = g->reserve(&g->d_rchi32, std::max<long long>(rp.back(), 1) * sizeof(float4))) != XLS_OK) return s;
       // same entry order as the FP64 table (the fill order of the atomics is not reproducible)
       launch_convert_f64_f32((const double*)g->d_rchi64, (float*)g->d_rchi32, 4 * rp.back(), g->st); ++nl;
     }
     XLS_CUDA(cudaStreamSynchronize(g->st));
-    cudaFree(dc);
-    cudaFree(dcur);
     g->max_slots = 0;
     for (const SubDev& S : g->subs) g->max_slots = std::max(g->max_slots, S.slot_n);
     // per point block of the back-projection: the slots its rows name (rows' entries as ranks)
-    g->release(&g->d_nlb_sub);
-    g->release(&g->d_nlb_cnt);
-    g->release(&g->d_nlb_list);
-    const int n_nlb = (int)nlb_sub.size();
-    if ((s = g->alloc(&g->d_nlb_sub, n_nlb * sizeof(int))) != XLS_OK) return s;
-    if ((s = g->alloc(&g->d_nlb_cnt, n_nlb * sizeof(int))) != XLS_OK) return s;
+          const int n_nlb = (int)nlb_sub.size();
+    if ((s = g->reserve(&g->d_nlb_sub, n_nlb * sizeof(int))) != XLS_OK) return s;
+    if ((s = g->reserve(&g->d_nlb_cnt, n_nlb * sizeof(int))) != XLS_OK) return s;
     XLS_CUDA(cudaMemcpyAsync(g->d_nlb_sub, nlb_sub.data(), n_nlb * sizeof(int), cudaMemcpyHostToDevice, g->st));
     launch_rcsr_localize(g->d_subs, g->d_nlb_sub, n_nlb, g->d_rptr, g->d_rslot, g->d_nlb_cnt, nullptr, 0, 0, g->st);
     ++nl;
@@ -2150,7 +2158,7 @@ xls_status xls_hamiltonian_set(xls_grid g, const double* veff, int veff_on_devic
     XLS_CUDA(cudaStreamSynchronize(g->st));
     g->nlb_max = 0;
     for (int c : cnt_b) g->nlb_max = std::max(g->nlb_max, c);
-    if ((s = g->alloc(&g->d_nlb_list, std::max<size_t>((size_t)n_nlb * g->nlb_max, 1) * sizeof(int))) != XLS_OK)
+    if ((s = g->reserve(&g->d_nlb_list, std::max<size_t>((size_t)n_nlb * g->nlb_max, 1) * sizeof(int))) != XLS_OK)
       return s;
     launch_rcsr_localize(g->d_subs, g->d_nlb_sub, n_nlb, g->d_rptr, g->d_rslot, g->d_nlb_cnt, g->d_nlb_list,
                          g->nlb_max, 1, g->st); ++nl;
@@ -2386,6 +2394,31 @@ xls_status xls_autotune(xls_grid g, int reps, int* choices_out) {
       }
     }
     g->proj_vec = best;
+  }
+  // (3b) points per thread of the back-projection, adding into a free arena (scratch between
+  // passes) with the coefficients the projection timing left in P
+  if (rc == XLS_OK && g->n_slot > 0 && g->nlb_max > 0) {
+    int best = g->back_ppt;
+    float bt = -1.f;
+    const int bout = (g->cur + 1) % 3;
+    xls_grid_s::View& v = fv(g);
+    for (int ppt : {1, 2}) {
+      const float t = time_it([&] {
+        if (g->prec == XLS_FP64)
+          launch_nl_back_csr<double>(v.ds, v.n, v.max_nd, v.max_ns, g->nlb_max, g->d_rptr, g->d_rslot, g->d_rchi64,
+                                     g->d_nlb_cnt, g->d_nlb_list, g->P, (double*)g->blk[bout], v.coef, 0, ppt, st);
+        else
+          launch_nl_back_csr<float>(v.ds, v.n, v.max_nd, v.max_ns, g->nlb_max, g->d_rptr, g->d_rslot, g->d_rchi32,
+                                    g->d_nlb_cnt, g->d_nlb_list, g->P, (float*)g->blk[bout], v.coef, 0, ppt, st);
+      });
+      if (rc != XLS_OK) break;
+      if (std::getenv("XLS_TRACE")) std::fprintf(stderr, "[xls] autotune: back-projection %d points per thread %.3f ms\n", ppt, t);
+      if (bt < 0.f || t < bt) {
+        bt = t;
+        best = ppt;
+      }
+    }
+    g->back_ppt = best;
   }
   // (4) slot pitch of the TMA stencil per class: compile-time (where one exists: 80, 112 floats)
   // or runtime, timed on the current block into a free arena (its contents are scratch between

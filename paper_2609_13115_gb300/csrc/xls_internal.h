@@ -163,7 +163,7 @@ template <typename T>
 void launch_nl_back_csr(const SubDev* d_subs, int n_sub, long long max_nd, int max_ns, int list_max,
                         const long long* row_ptr, const int* rslot, const typename Vec4<T>::type* rchi,
                         const int* blk_cnt, const int* blk_list, const double* P, T* Yout, const StepCoef* coef,
-                        int step, cudaStream_t st);
+                        int step, int ppt, cudaStream_t st);
 // single-vector views (ns = 1 per subdomain): one warp per slot; one thread per grid point
 template <typename T>
 void launch_nl_project1(const SubDev* d_subs, const ProjSlot* d_slots, int n_slot, const int* idx,
