@@ -259,23 +259,23 @@ k_proj_fill(const SubDev* __restrict__ subs, const ProjSlot* __restrict__ slots,
 // (transpose reduction) and warps are reduced at the end.  Wider groups read each table entry
 // once for more vectors (the warps of a CTA share it through L1) and split the slot's points
 // over fewer warps.
-// slots per chunk of the projection's CTA order: about one 72^3 subdomain's slots, whose tables
-// (~30 MB) and one vector group's Y slice (~12 MB per 8 vectors) stay in L2 while the chunk is walked
-constexpr int kPChunk = 512;
+// slots per chunk of the projection's CTA order (256, 512 or 1024, xls_autotune; 512 by default:
+// about one 72^3 subdomain's slots, whose tables (~30 MB) and one vector group's Y slice (~12 MB
+// per 8 vectors) stay in L2 while the chunk is walked)
 
 template <typename T, int KPV>
 __global__ void __launch_bounds__(256)
 k_nl_project(const SubDev* __restrict__ subs, const ProjSlot* __restrict__ slots, int slot_off, int n_slot,
-             int n_groups, const int* __restrict__ idx, const typename Vec4<T>::type* __restrict__ chi,
+             int n_groups, int chunk_slots, const int* __restrict__ idx, const typename Vec4<T>::type* __restrict__ chi,
              const T* __restrict__ Y, double* __restrict__ P) {
   using T4 = typename Vec4<T>::type;
   constexpr int kVH = KPV / 8, kPH = 8 / kVH;   // vector eighths and point phases of the 8 warps
   __shared__ T red[kPH][KPV * 4];
-  // CTAs walk the slots in chunks of kPChunk: every vector group runs over the chunk before the
-  // next chunk starts, so the chunk's tables stay in L2 for all groups, and within a group the
+  // CTAs walk the slots in chunks of chunk_slots: every vector group runs over the chunk before
+  // the next chunk starts, so the chunk's tables stay in L2 for all groups, and within a group the
   // points that neighbouring slots share are read from DRAM once
-  const int chunk = (int)(blockIdx.x / (kPChunk * n_groups)), rem = (int)(blockIdx.x % (kPChunk * n_groups));
-  const int grp = rem / kPChunk, sic = chunk * kPChunk + rem % kPChunk;
+  const int chunk = (int)(blockIdx.x / (chunk_slots * n_groups)), rem = (int)(blockIdx.x % (chunk_slots * n_groups));
+  const int grp = rem / chunk_slots, sic = chunk * chunk_slots + rem % chunk_slots;
   if (sic >= n_slot) return;
   const int slot = slot_off + sic;
   const ProjSlot& A = slots[slot];
@@ -408,8 +408,8 @@ __global__ void k_rcsr_fill(const SubDev* __restrict__ subs, const ProjSlot* __r
   }
 }
 
-constexpr int kBackVec = 8;
-constexpr int kBackRow = kBackVec + 1;   // padded slot row of Q (consecutive slots in different bank groups)
+// vectors per CTA of the back-projection: KV = 8 (default) or 16, each slot's coefficient row of Q
+// padded to KV + 1 entries (consecutive slots in different bank groups)
 constexpr int kLocBits = 32768;          // slots per subdomain the localisation handles (bitmap in shared memory)
 
 // One CTA per point block: mark the slots named by the block's reverse-table rows in a bitmap;
@@ -563,10 +563,11 @@ void launch_rcsr_localize(const SubDev* d_subs, const int* d_blk_sub, int n_blk,
 }
 
 // Y_out[v][g] += scale * sum over the slots s of point g of sum_l chi_l(g) P[s][l][v]; PPT
-// points per thread per iteration (1 or 2, timed by xls_autotune: two give each thread more
-// loads in flight, one fewer registers and so more resident warps; one measured 9 % faster on
-// 72^3 subdomains with 528 states and is the default)
-template <typename T, int PPT>
+// points per thread per iteration and KV vectors per CTA (1 x 8, 2 x 8 or 1 x 16, timed by
+// xls_autotune: two points give each thread more loads in flight, one point fewer registers and
+// so more resident warps, 16 vectors read every table row once for twice the vectors; 1 x 8
+// measured 9 % faster than 2 x 8 on 72^3 subdomains with 528 states and is the default)
+template <typename T, int PPT, int KV>
 __global__ void __launch_bounds__(256)
 k_nl_back_csr(const SubDev* __restrict__ subs, const long long* __restrict__ row_ptr, const int* __restrict__ rslot,
               const typename Vec4<T>::type* __restrict__ rchi, const int* __restrict__ blk_cnt,
@@ -574,22 +575,22 @@ k_nl_back_csr(const SubDev* __restrict__ subs, const long long* __restrict__ row
               const StepCoef* __restrict__ coef, int step) {
   using T4 = typename Vec4<T>::type;
   extern __shared__ __align__(16) unsigned char qsm[];
-  T4* Qs = reinterpret_cast<T4*>(qsm);   // [slot][kBackRow]
+  T4* Qs = reinterpret_cast<T4*>(qsm);   // [slot][KV + 1]
   // the vector groups of one point block are consecutive CTAs: the block's reverse-table rows
   // are read once from DRAM and then from L2
   const SubDev& S = subs[blockIdx.z];
-  const int v0 = blockIdx.x * kBackVec;
+  const int v0 = blockIdx.x * KV;
   const long long p0 = (long long)blockIdx.y * kBackPts;
   if (v0 >= S.ns || p0 >= S.nd || S.slot_n == 0) return;
-  const int nv = min(kBackVec, S.ns - v0);
+  const int nv = min(KV, S.ns - v0);
   const double scale = coef[blockIdx.z * kMaxDegree + step].scale;
   // the projector coefficients of the slots this point block meets (its rows name them by rank
   // in the block's list)
   const int nb = S.off_nlb + (int)blockIdx.y;
   const int nloc = blk_cnt[nb];
   const int* list = blk_list + (long long)nb * list_max;
-  for (int q = threadIdx.x; q < nloc * kBackVec; q += blockDim.x) {
-    const int sl = q / kBackVec, v = q % kBackVec;
+  for (int q = threadIdx.x; q < nloc * KV; q += blockDim.x) {
+    const int sl = q / KV, v = q % KV;
     T4 x;
     if (v < nv) {
       const double* pa = P + S.off_proj + (long long)list[sl] * 4 * S.ns + v0 + v;
@@ -597,7 +598,7 @@ k_nl_back_csr(const SubDev* __restrict__ subs, const long long* __restrict__ row
     } else {
       x.x = x.y = x.z = x.w = (T)0;
     }
-    Qs[sl * kBackRow + v] = x;
+    Qs[sl * (KV + 1) + v] = x;
   }
   __syncthreads();
   T* yb = Yout + S.off_blk + (long long)v0 * S.nd;
@@ -632,21 +633,21 @@ k_nl_back_csr(const SubDev* __restrict__ subs, const long long* __restrict__ row
     for (int u = 0; u < PPT; ++u) {
       const long long gu = g + (long long)u * blockDim.x;
       if (gu >= end || r1[u] == r0[u]) continue;
-      T y[kBackVec];
+      T y[KV];
 #pragma unroll
-      for (int v = 0; v < kBackVec; ++v) y[v] = (T)0;
+      for (int v = 0; v < KV; ++v) y[v] = (T)0;
       for (long long e = r0[u]; e < r1[u]; ++e) {
         const int sl = rslot[e];
         const T4 c = rchi[e];
-        const T4* qq = Qs + sl * kBackRow;
+        const T4* qq = Qs + sl * (KV + 1);
 #pragma unroll
-        for (int v = 0; v < kBackVec; ++v) {
+        for (int v = 0; v < KV; ++v) {
           const T4 q = qq[v];
           y[v] += c.x * q.x + c.y * q.y + c.z * q.z + c.w * q.w;
         }
       }
 #pragma unroll
-      for (int v = 0; v < kBackVec; ++v)
+      for (int v = 0; v < KV; ++v)
         if (v < nv) atomicAdd(yb + (long long)v * S.nd + gu, y[v]);
     }
   }
@@ -769,10 +770,11 @@ void launch_nl_back_csr(const SubDev* d_subs, int n_sub, long long max_nd, int m
                         const int* blk_cnt, const int* blk_list, const double* P, T* Yout, const StepCoef* coef,
                         int step, int ppt, cudaStream_t st) {
   if (list_max == 0) return;
-  const size_t smem = (size_t)list_max * kBackRow * sizeof(typename Vec4<T>::type);
-  auto kern = ppt == 1 ? k_nl_back_csr<T, 1> : k_nl_back_csr<T, 2>;
+  const int kv = ppt == 16 ? 16 : 8;   // ppt 16: one point per thread, 16 vectors per CTA
+  const size_t smem = (size_t)list_max * (kv + 1) * sizeof(typename Vec4<T>::type);
+  auto kern = ppt == 16 ? k_nl_back_csr<T, 1, 16> : (ppt == 2 ? k_nl_back_csr<T, 2, 8> : k_nl_back_csr<T, 1, 8>);
   if (smem > 48 * 1024) cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  dim3 grid((max_ns + kBackVec - 1) / kBackVec, (unsigned)((max_nd + kBackPts - 1) / kBackPts), n_sub);
+  dim3 grid((max_ns + kv - 1) / kv, (unsigned)((max_nd + kBackPts - 1) / kBackPts), n_sub);
   kern<<<grid, 256, smem, st>>>(d_subs, row_ptr, rslot, rchi, blk_cnt, blk_list, list_max, P, Yout, coef, step);
 }
 
@@ -789,20 +791,23 @@ void launch_proj_table_fill(const SubDev* d_subs, const ProjSlot* d_slots, int n
 
 template <typename T, int KPV>
 void launch_nl_project_w(const SubDev* d_subs, const ProjSlot* d_slots, int slot_off, int n_slot, const int* idx,
-                         const typename Vec4<T>::type* chi, int max_ns, const T* Y, double* P, cudaStream_t st) {
+                         const typename Vec4<T>::type* chi, int max_ns, const T* Y, double* P, int chunk_slots,
+                         cudaStream_t st) {
   const int groups = (max_ns + KPV - 1) / KPV;
-  const int chunks = (n_slot + kPChunk - 1) / kPChunk;
-  k_nl_project<T, KPV><<<chunks * kPChunk * groups, 256, 0, st>>>(d_subs, d_slots, slot_off, n_slot, groups, idx, chi,
-                                                                  Y, P);
+  const int chunks = (n_slot + chunk_slots - 1) / chunk_slots;
+  k_nl_project<T, KPV><<<chunks * chunk_slots * groups, 256, 0, st>>>(d_subs, d_slots, slot_off, n_slot, groups,
+                                                                      chunk_slots, idx, chi, Y, P);
 }
 
 template <typename T>
 void launch_nl_project(const SubDev* d_subs, const ProjSlot* d_slots, int slot_off, int n_slot, const int* idx,
-                       const typename Vec4<T>::type* chi, int max_ns, const T* Y, double* P, int kpv, cudaStream_t st) {
+                       const typename Vec4<T>::type* chi, int max_ns, const T* Y, double* P, int kpv, int chunk_slots,
+                       cudaStream_t st) {
   if (n_slot == 0) return;
-  if (kpv == 32) launch_nl_project_w<T, 32>(d_subs, d_slots, slot_off, n_slot, idx, chi, max_ns, Y, P, st);
-  else if (kpv == 16) launch_nl_project_w<T, 16>(d_subs, d_slots, slot_off, n_slot, idx, chi, max_ns, Y, P, st);
-  else launch_nl_project_w<T, 8>(d_subs, d_slots, slot_off, n_slot, idx, chi, max_ns, Y, P, st);
+  if (chunk_slots != 256 && chunk_slots != 1024) chunk_slots = 512;
+  if (kpv == 32) launch_nl_project_w<T, 32>(d_subs, d_slots, slot_off, n_slot, idx, chi, max_ns, Y, P, chunk_slots, st);
+  else if (kpv == 16) launch_nl_project_w<T, 16>(d_subs, d_slots, slot_off, n_slot, idx, chi, max_ns, Y, P, chunk_slots, st);
+  else launch_nl_project_w<T, 8>(d_subs, d_slots, slot_off, n_slot, idx, chi, max_ns, Y, P, chunk_slots, st);
 }
 
 template <typename T>
@@ -819,7 +824,7 @@ void launch_nl_back(const SubDev* d_subs, const ProjSlot* d_slots, int n_slot, c
   template void launch_proj_table_fill<T>(const SubDev*, const ProjSlot*, int, const AtomImg*, int*,                 \
                                           Vec4<T>::type*, cudaStream_t);                                             \
   template void launch_nl_project<T>(const SubDev*, const ProjSlot*, int, int, const int*, const Vec4<T>::type*,     \
-                                     int, const T*, double*, int, cudaStream_t);                                     \
+                                     int, const T*, double*, int, int, cudaStream_t);                                \
   template void launch_nl_back<T>(const SubDev*, const ProjSlot*, int, const int*, const Vec4<T>::type*, int,        \
                                   const double*, T*, const StepCoef*, int, cudaStream_t);                            \
   template void launch_rcsr_build<T>(const SubDev*, const ProjSlot*, int, const int*, const Vec4<T>::type*,         \

@@ -114,7 +114,8 @@ struct xls_grid_s {
   void* scr_b = nullptr;
   void* scr_c = nullptr;
   int proj_vec = 8;         // vectors per CTA of the projection (8, 16 or 32; xls_autotune)
-  int back_ppt = 1;         // points per thread of the back-projection (1 or 2; xls_autotune)
+  int back_var = 1;         // back-projection variant: 1 (1 point x 8 vectors per CTA), 2 (2 x 8), 16 (1 x 16)
+  int proj_chunk = 512;     // slots per chunk of the projection's CTA order (256, 512, 1024)
   // concurrent halves (XLS_CONCURRENT=1): the subdomains split in two views whose passes run on
   // two streams, half 1's filter beside half 0's projection, eigensolve and rotation
   struct View {
@@ -351,7 +352,7 @@ void h_step(xls_grid g, bool one, const T* yin, const T* yprev, T* yout, int ste
   { ProfScope ps(g, K_NLPROJ);
     if (one) launch_nl_project1<T>(ds, g->d_slots, g->n_slot, g->d_pidx, chi_table<T>(g), yin, P, g->st);
     else launch_nl_project<T>(ds, g->d_slots, 0, g->n_slot, g->d_pidx, chi_table<T>(g), mns, yin, P, g->proj_vec,
-                              g->st); }
+                              g->proj_chunk, g->st); }
   { ProfScope ps(g, K_STENCIL); launch_stencil<T>(ds, g->n_sub, pl, yin, yprev, yout, V, g->coef, step, g->st); }
   { ProfScope ps(g, K_NLBACK);
     if (one)
@@ -359,7 +360,7 @@ void h_step(xls_grid g, bool one, const T* yin, const T* yprev, T* yout, int ste
                          P, yout, g->coef, step, g->st);
     else
       launch_nl_back_csr<T>(ds, g->n_sub, g->max_nd, mns, g->nlb_max, g->d_rptr, g->d_rslot, rchi_table<T>(g),
-                            g->d_nlb_cnt, g->d_nlb_list, P, yout, g->coef, step, g->back_ppt, g->st); }
+                            g->d_nlb_cnt, g->d_nlb_list, P, yout, g->coef, step, g->back_var, g->st); }
   g->launches += (g->n_slot ? 3 : 1);
 }
 
@@ -388,7 +389,7 @@ void h_step_main(xls_grid g, const xls_grid_s::View& v, int bin, int bprev, int 
   }
   { ProfScope ps(g, K_NLPROJ);
     launch_nl_project<T>(g->d_subs, g->d_slots, v.slot_off, v.n_slot, g->d_pidx, chi_table<T>(g), v.max_ns, yin, g->P,
-                         g->proj_vec, side ? g->side_st : v.st); }
+                         g->proj_vec, g->proj_chunk, side ? g->side_st : v.st); }
   if (side) cudaEventRecord(g->ev_side_out, g->side_st);
   if (sizeof(T) == 4 && g->use_tma) {
     ProfScope ps(g, K_STENCIL);
@@ -404,7 +405,7 @@ void h_step_main(xls_grid g, const xls_grid_s::View& v, int bin, int bprev, int 
   { ProfScope ps(g, K_NLBACK);
     launch_nl_back_csr<T>(v.ds, v.n, v.max_nd, v.max_ns, g->nlb_max, g->d_rptr, g->d_rslot, rchi_table<T>(g),
                           g->d_nlb_cnt, g->d_nlb_list, g->P,
-                          yout, v.coef, step, g->back_ppt, v.st); }
+                          yout, v.coef, step, g->back_var, v.st); }
   g->launches += (v.n_slot ? 2 : 0);
 }
 
@@ -2372,53 +2373,60 @@ xls_status xls_autotune(xls_grid g, int reps, int* choices_out) {
     g->gram_cps = best;
     replan_all();
   }
-  // (3) vectors per CTA of the nonlocal projection, timed on the current block (the projection
-  // coefficients it overwrites are recomputed at the start of every filter step)
+  // (3) vectors per CTA and slots per chunk of the nonlocal projection, timed on the current
+  // block (the projection coefficients it overwrites are recomputed at the start of every filter
+  // step)
   if (rc == XLS_OK && g->n_slot > 0) {
-    int best = g->proj_vec;
+    int best_v = g->proj_vec, best_c = g->proj_chunk;
     float bt = -1.f;
-    for (int kpv : {8, 16, 32}) {
-      const float t = time_it([&] {
-        if (g->prec == XLS_FP64)
-          launch_nl_project<double>(g->d_subs, g->d_slots, 0, g->n_slot, g->d_pidx, g->d_chi64, g->max_ns,
-                                    (const double*)g->blk[g->cur], g->P, kpv, st);
-        else
-          launch_nl_project<float>(g->d_subs, g->d_slots, 0, g->n_slot, g->d_pidx, g->d_chi32, g->max_ns,
-                                   (const float*)g->blk[g->cur], g->P, kpv, st);
-      });
-      if (rc != XLS_OK) break;
-      if (std::getenv("XLS_TRACE")) std::fprintf(stderr, "[xls] autotune: projection %d vectors per CTA %.3f ms\n", kpv, t);
-      if (bt < 0.f || t < bt) {
-        bt = t;
-        best = kpv;
+    for (int kpv : {8, 16, 32})
+      for (int chunk : {256, 512, 1024}) {
+        const float t = time_it([&] {
+          if (g->prec == XLS_FP64)
+            launch_nl_project<double>(g->d_subs, g->d_slots, 0, g->n_slot, g->d_pidx, g->d_chi64, g->max_ns,
+                                      (const double*)g->blk[g->cur], g->P, kpv, chunk, st);
+          else
+            launch_nl_project<float>(g->d_subs, g->d_slots, 0, g->n_slot, g->d_pidx, g->d_chi32, g->max_ns,
+                                     (const float*)g->blk[g->cur], g->P, kpv, chunk, st);
+        });
+        if (rc != XLS_OK) break;
+        if (std::getenv("XLS_TRACE"))
+          std::fprintf(stderr, "[xls] autotune: projection %d vectors per CTA, chunks of %d slots %.3f ms\n", kpv, chunk, t);
+        if (bt < 0.f || t < bt) {
+          bt = t;
+          best_v = kpv;
+          best_c = chunk;
+        }
       }
-    }
-    g->proj_vec = best;
+    g->proj_vec = best_v;
+    g->proj_chunk = best_c;
   }
-  // (3b) points per thread of the back-projection, adding into a free arena (scratch between
-  // passes) with the coefficients the projection timing left in P
+  // (3b) back-projection variant (points per thread x vectors per CTA), adding into a free arena
+  // (scratch between passes) with the coefficients the projection timing left in P
   if (rc == XLS_OK && g->n_slot > 0 && g->nlb_max > 0) {
-    int best = g->back_ppt;
+    int best = g->back_var;
     float bt = -1.f;
     const int bout = (g->cur + 1) % 3;
     xls_grid_s::View& v = fv(g);
-    for (int ppt : {1, 2}) {
+    for (int var : {1, 2, 16}) {
       const float t = time_it([&] {
         if (g->prec == XLS_FP64)
           launch_nl_back_csr<double>(v.ds, v.n, v.max_nd, v.max_ns, g->nlb_max, g->d_rptr, g->d_rslot, g->d_rchi64,
-                                     g->d_nlb_cnt, g->d_nlb_list, g->P, (double*)g->blk[bout], v.coef, 0, ppt, st);
+                                     g->d_nlb_cnt, g->d_nlb_list, g->P, (double*)g->blk[bout], v.coef, 0, var, st);
         else
           launch_nl_back_csr<float>(v.ds, v.n, v.max_nd, v.max_ns, g->nlb_max, g->d_rptr, g->d_rslot, g->d_rchi32,
-                                    g->d_nlb_cnt, g->d_nlb_list, g->P, (float*)g->blk[bout], v.coef, 0, ppt, st);
+                                    g->d_nlb_cnt, g->d_nlb_list, g->P, (float*)g->blk[bout], v.coef, 0, var, st);
       });
       if (rc != XLS_OK) break;
-      if (std::getenv("XLS_TRACE")) std::fprintf(stderr, "[xls] autotune: back-projection %d points per thread %.3f ms\n", ppt, t);
+      if (std::getenv("XLS_TRACE"))
+        std::fprintf(stderr, "[xls] autotune: back-projection variant %d (%s) %.3f ms\n", var,
+                     var == 16 ? "1 point x 16 vectors" : (var == 2 ? "2 points x 8 vectors" : "1 point x 8 vectors"), t);
       if (bt < 0.f || t < bt) {
         bt = t;
-        best = ppt;
+        best = var;
       }
     }
-    g->back_ppt = best;
+    g->back_var = best;
   }
   // (4) slot pitch of the TMA stencil per class: compile-time (where one exists: 80, 112 floats)
   // or runtime, timed on the current block into a free arena (its contents are scratch between

@@ -144,7 +144,8 @@ void launch_proj_table_fill(const SubDev* d_subs, const ProjSlot* d_slots, int n
                             int* idx, typename Vec4<T>::type* chi, cudaStream_t st);
 template <typename T>
 void launch_nl_project(const SubDev* d_subs, const ProjSlot* d_slots, int slot_off, int n_slot, const int* idx,
-                       const typename Vec4<T>::type* chi, int max_ns, const T* Y, double* P, int kpv, cudaStream_t st);
+                       const typename Vec4<T>::type* chi, int max_ns, const T* Y, double* P, int kpv, int chunk_slots,
+                       cudaStream_t st);
 void launch_rcsr_count(const SubDev* d_subs, const ProjSlot* d_slots, int n_slot, const int* idx, int* cnt,
                        cudaStream_t st);
 template <typename T>
@@ -163,7 +164,7 @@ template <typename T>
 void launch_nl_back_csr(const SubDev* d_subs, int n_sub, long long max_nd, int max_ns, int list_max,
                         const long long* row_ptr, const int* rslot, const typename Vec4<T>::type* rchi,
                         const int* blk_cnt, const int* blk_list, const double* P, T* Yout, const StepCoef* coef,
-                        int step, int ppt, cudaStream_t st);
+                        int step, int variant, cudaStream_t st);   // variant: 1 (1 point x 8 vectors), 2 (2 x 8), 16 (1 x 16)
 // single-vector views (ns = 1 per subdomain): one warp per slot; one thread per grid point
 template <typename T>
 void launch_nl_project1(const SubDev* d_subs, const ProjSlot* d_slots, int n_slot, const int* idx,
