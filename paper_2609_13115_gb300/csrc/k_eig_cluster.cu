@@ -446,12 +446,16 @@ k_tridiag_cl1(const SubDev* __restrict__ subs, double* Am, double* vecs) {
 // Same reduction with the redundant vector work of each column on four warps (one per SM
 // sub-partition, so that their FP64 instructions -- each of which holds a sub-partition's FP64
 // pipe for tens of cycles on GB300 -- spread over all four pipes): after the cluster barrier
-// warps 0-3 form p, p.v, K and w, update the pushed row k+1 and derive the next reflector from it
+// warps 0-3 form p.v, K and w, update the pushed row k+1 and derive the next reflector from it
 // (into the other half of a double-buffered v), synchronising among themselves with a named
 // barrier, while the other warps wait at the one block barrier before the row update; a second
-// block barrier separates the update from the next column's partial sums.  Per column: one
-// cluster barrier and two block barriers (the block-wide reductions of k_tridiag_cl1 take nine).
-// shared memory: own rows [nloc][n], partials [2][CL][n], pivot rows [2][n], v [2][n], w [n]
+// block barrier separates the update from the next column's products.  p = A v is formed row by
+// row (the stored rows are full rows of the symmetric matrix): each CTA takes the entries of its
+// own rows, one warp per row, and pushes each into every CTA's copy of p, so a CTA receives n
+// values per column instead of CL partial vectors and no sum over the cluster is left on the
+// vector warps' path.  Per column: one cluster barrier and two block barriers (the block-wide
+// reductions of k_tridiag_cl1 take nine).
+// shared memory: own rows [nloc][n], p [2][n], pivot rows [2][n], v [2][n], w [n]
 __global__ void __launch_bounds__(256)
 k_tridiag_cl2(const SubDev* __restrict__ subs, double* Am, double* vecs) {
   cg::cluster_group cl = cg::this_cluster();
@@ -466,8 +470,8 @@ k_tridiag_cl2(const SubDev* __restrict__ subs, double* Am, double* vecs) {
   double* tau = d + 2 * n;
   extern __shared__ __align__(16) double tsm[];
   double* Ar = tsm;
-  double* qb = Ar + (size_t)nloc * n;          // [2][CL][n]
-  double* rb = qb + 2 * (size_t)CL * n;        // [2][n]
+  double* pb = Ar + (size_t)nloc * n;          // [2][n]
+  double* rb = pb + 2 * (size_t)n;             // [2][n]
   double* vb = rb + 2 * (size_t)n;             // [2][n]
   double* wf = vb + 2 * (size_t)n;             // [n]
   __shared__ double s_t[2];                    // tau of the reflector in vb[0], vb[1]
@@ -532,15 +536,16 @@ k_tridiag_cl2(const SubDev* __restrict__ subs, double* Am, double* vecs) {
       const int i = r * CL + rank;
       if (i >= k + 2 && i < n) Ar[(size_t)r * n + k] = vf[i];
     }
-    // partial column sums of the own rows, pushed into every CTA
-    double* qmine = qb + ((size_t)par * CL + rank) * n;
-    for (int j = k + 1 + threadIdx.x; j < n; j += blockDim.x) {
+    // p_i = (A v)_i for the own rows i > k (one warp per row), pushed into every CTA's p
+    double* pcur = pb + (size_t)par * n;
+    for (int r = warp; r < nloc; r += nw) {
+      const int i = r * CL + rank;
+      if (i <= k || i >= n) continue;   // uniform in the warp
+      const double* row = Ar + (size_t)r * n;
       double acc = 0.0;
-      for (int r = 0; r < nloc; ++r) {
-        const int i = r * CL + rank;
-        if (i > k && i < n) acc += Ar[(size_t)r * n + j] * vf[i];
-      }
-      for (int q = 0; q < CL; ++q) cl.map_shared_rank(qmine, q)[j] = acc;
+      for (int j = k + 1 + lane; j < n; j += 32) acc += row[j] * vf[j];
+      acc = wsum(acc);
+      if (lane < CL) cl.map_shared_rank(pcur, lane)[i] = acc;
     }
     // the owner of row k+1 pushes it (before this column's update) for the next reflector
     if ((k + 1) % CL == rank) {
@@ -552,12 +557,10 @@ k_tridiag_cl2(const SubDev* __restrict__ subs, double* Am, double* vecs) {
     }
     cl.sync();
     if (warp < 4) {
-      // p = tau sum_r q_r, K = tau p.v / 2, w = p - K v (j > k); then row k+1 and the next reflector
+      // p = tau A v, K = tau p.v / 2, w = p - K v (j > k); then row k+1 and the next reflector
       double pv = 0.0;
       for (int j = k + 1 + tv; j < n; j += 128) {
-        double sacc = 0.0;
-        for (int q = 0; q < CL; ++q) sacc += qb[((size_t)par * CL + q) * n + j];
-        sacc *= t;
+        const double sacc = t * pcur[j];
         wf[j] = sacc;
         pv += sacc * vf[j];
       }
@@ -676,11 +679,12 @@ bool launch_cholesky_cluster(const SubDev* d_subs, int n_sub, int max_ns, double
 bool launch_tridiag_cluster(const SubDev* d_subs, int n_sub, int max_ns, double* A, double* vecs, int cl_first,
                             cudaStream_t st) {
   size_t smem = 0;
-  // one barrier per column: partials [2][CL][n], pivot rows [2][n], v, w, p (k_tridiag_cl2; the
-  // two-barrier k_tridiag_cl1 with XLS_TRIDIAG_CL1=1)
+  // one barrier per column: own rows, p [2][n], pivot rows [2][n], v [2][n], w [n] (k_tridiag_cl2;
+  // the two-barrier k_tridiag_cl1 with XLS_TRIDIAG_CL1=1 keeps CL partial vectors: [2][CL][n])
   for (int CL : {cl_first == 16 ? 16 : 8, cl_first == 16 ? 8 : 16}) {
-    const size_t exact = ((size_t)(max_ns + CL - 1) / CL * max_ns + (2 * (size_t)CL + 5) * max_ns) * sizeof(double);
     const bool cl2 = !std::getenv("XLS_TRIDIAG_CL1");
+    const size_t rows = (size_t)(max_ns + CL - 1) / CL * max_ns;
+    const size_t exact = (rows + (cl2 ? 7 : 2 * (size_t)CL + 5) * max_ns) * sizeof(double);
     if (exact <= 200 * 1024 && launch_cluster(cl2 ? k_tridiag_cl2 : k_tridiag_cl1, n_sub, CL, exact, st, d_subs, A, vecs,
                                               true))
       return true;
