@@ -263,13 +263,14 @@ k_proj_fill(const SubDev* __restrict__ subs, const ProjSlot* __restrict__ slots,
 // about one 72^3 subdomain's slots, whose tables (~30 MB) and one vector group's Y slice (~12 MB
 // per 8 vectors) stay in L2 while the chunk is walked)
 
-template <typename T, int KPV>
-__global__ void __launch_bounds__(256)
+template <typename T, int KPV, int NW>
+__global__ void __launch_bounds__(NW * 32)
 k_nl_project(const SubDev* __restrict__ subs, const ProjSlot* __restrict__ slots, int slot_off, int n_slot,
              int n_groups, int chunk_slots, const int* __restrict__ idx, const typename Vec4<T>::type* __restrict__ chi,
              const T* __restrict__ Y, double* __restrict__ P) {
   using T4 = typename Vec4<T>::type;
-  constexpr int kVH = KPV / 8, kPH = 8 / kVH;   // vector eighths and point phases of the 8 warps
+  constexpr int kVH = KPV / 8, kPH = NW / kVH;   // vector eighths and point phases of the NW warps
+  static_assert(kPH >= 1, "at least one point phase");
   __shared__ T red[kPH][KPV * 4];
   // CTAs walk the slots in chunks of chunk_slots: every vector group runs over the chunk before
   // the next chunk starts, so the chunk's tables stay in L2 for all groups, and within a group the
@@ -789,25 +790,31 @@ void launch_proj_table_fill(const SubDev* d_subs, const ProjSlot* d_slots, int n
   if (n_slot) k_proj_fill<T><<<n_slot, 256, 0, st>>>(d_subs, d_slots, d_imgs, idx, chi);
 }
 
-template <typename T, int KPV>
+template <typename T, int KPV, int NW>
 void launch_nl_project_w(const SubDev* d_subs, const ProjSlot* d_slots, int slot_off, int n_slot, const int* idx,
                          const typename Vec4<T>::type* chi, int max_ns, const T* Y, double* P, int chunk_slots,
                          cudaStream_t st) {
   const int groups = (max_ns + KPV - 1) / KPV;
   const int chunks = (n_slot + chunk_slots - 1) / chunk_slots;
-  k_nl_project<T, KPV><<<chunks * chunk_slots * groups, 256, 0, st>>>(d_subs, d_slots, slot_off, n_slot, groups,
-                                                                      chunk_slots, idx, chi, Y, P);
+  k_nl_project<T, KPV, NW><<<chunks * chunk_slots * groups, NW * 32, 0, st>>>(d_subs, d_slots, slot_off, n_slot, groups,
+                                                                              chunk_slots, idx, chi, Y, P);
 }
 
+// kpv: vectors per CTA (8, 16, 32); a negative kpv selects the CTAs of 4 warps (8 or 16 vectors),
+// else 8 warps; chunk_slots: 256, 512 or 1024
 template <typename T>
 void launch_nl_project(const SubDev* d_subs, const ProjSlot* d_slots, int slot_off, int n_slot, const int* idx,
                        const typename Vec4<T>::type* chi, int max_ns, const T* Y, double* P, int kpv, int chunk_slots,
                        cudaStream_t st) {
   if (n_slot == 0) return;
   if (chunk_slots != 256 && chunk_slots != 1024) chunk_slots = 512;
-  if (kpv == 32) launch_nl_project_w<T, 32>(d_subs, d_slots, slot_off, n_slot, idx, chi, max_ns, Y, P, chunk_slots, st);
-  else if (kpv == 16) launch_nl_project_w<T, 16>(d_subs, d_slots, slot_off, n_slot, idx, chi, max_ns, Y, P, chunk_slots, st);
-  else launch_nl_project_w<T, 8>(d_subs, d_slots, slot_off, n_slot, idx, chi, max_ns, Y, P, chunk_slots, st);
+  switch (kpv) {
+    case 32: launch_nl_project_w<T, 32, 8>(d_subs, d_slots, slot_off, n_slot, idx, chi, max_ns, Y, P, chunk_slots, st); break;
+    case 16: launch_nl_project_w<T, 16, 8>(d_subs, d_slots, slot_off, n_slot, idx, chi, max_ns, Y, P, chunk_slots, st); break;
+    case -8: launch_nl_project_w<T, 8, 4>(d_subs, d_slots, slot_off, n_slot, idx, chi, max_ns, Y, P, chunk_slots, st); break;
+    case -16: launch_nl_project_w<T, 16, 4>(d_subs, d_slots, slot_off, n_slot, idx, chi, max_ns, Y, P, chunk_slots, st); break;
+    default: launch_nl_project_w<T, 8, 8>(d_subs, d_slots, slot_off, n_slot, idx, chi, max_ns, Y, P, chunk_slots, st);
+  }
 }
 
 template <typename T>

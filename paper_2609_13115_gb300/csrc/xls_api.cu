@@ -113,7 +113,7 @@ struct xls_grid_s {
   void* scr_a = nullptr;    // set-up scratch (counts, row cursors, scan partial sums), reserved
   void* scr_b = nullptr;
   void* scr_c = nullptr;
-  int proj_vec = 8;         // vectors per CTA of the projection (8, 16 or 32; xls_autotune)
+  int proj_vec = 8;         // vectors per CTA of the projection (8, 16 or 32; -8, -16: CTAs of 4 warps; xls_autotune)
   int back_var = 1;         // back-projection variant: 1 (1 point x 8 vectors per CTA), 2 (2 x 8), 16 (1 x 16)
   int proj_chunk = 512;     // slots per chunk of the projection's CTA order (256, 512, 1024)
   // concurrent halves (XLS_CONCURRENT=1): the subdomains split in two views whose passes run on
@@ -2379,7 +2379,7 @@ xls_status xls_autotune(xls_grid g, int reps, int* choices_out) {
   if (rc == XLS_OK && g->n_slot > 0) {
     int best_v = g->proj_vec, best_c = g->proj_chunk;
     float bt = -1.f;
-    for (int kpv : {8, 16, 32})
+    for (int kpv : {8, 16, 32, -8, -16})   // negative: CTAs of 4 warps
       for (int chunk : {256, 512, 1024}) {
         const float t = time_it([&] {
           if (g->prec == XLS_FP64)
@@ -2391,7 +2391,8 @@ xls_status xls_autotune(xls_grid g, int reps, int* choices_out) {
         });
         if (rc != XLS_OK) break;
         if (std::getenv("XLS_TRACE"))
-          std::fprintf(stderr, "[xls] autotune: projection %d vectors per CTA, chunks of %d slots %.3f ms\n", kpv, chunk, t);
+          std::fprintf(stderr, "[xls] autotune: projection %d vectors per CTA of %d warps, chunks of %d slots %.3f ms\n",
+                       kpv < 0 ? -kpv : kpv, kpv < 0 ? 4 : 8, chunk, t);
         if (bt < 0.f || t < bt) {
           bt = t;
           best_v = kpv;
@@ -2481,7 +2482,7 @@ xls_status xls_autotune(xls_grid g, int reps, int* choices_out) {
   if (choices_out) {
     choices_out[0] = g->eig_cluster ? g->eig_cl : 0;
     choices_out[1] = tc_gram ? g->gram_cps : 0;
-    choices_out[2] = g->n_slot > 0 ? g->proj_vec : 0;
+    choices_out[2] = g->n_slot > 0 ? (g->proj_vec < 0 ? -g->proj_vec : g->proj_vec) : 0;
   }
   return rc;
 }
