@@ -259,9 +259,10 @@ k_proj_fill(const SubDev* __restrict__ subs, const ProjSlot* __restrict__ slots,
 // (transpose reduction) and warps are reduced at the end.  Wider groups read each table entry
 // once for more vectors (the warps of a CTA share it through L1) and split the slot's points
 // over fewer warps.
-// slots per chunk of the projection's CTA order (256, 512 or 1024, xls_autotune; 512 by default:
-// about one 72^3 subdomain's slots, whose tables (~30 MB) and one vector group's Y slice (~12 MB
-// per 8 vectors) stay in L2 while the chunk is walked)
+// slots per chunk of the projection's CTA order (256, 512 or 1024, xls_autotune; 256 by default,
+// with 8 vectors on CTAs of 4 warps: measured fastest on 72^3 subdomains with 528 states; a
+// 72^3 subdomain has about 430 slots, whose tables (~30 MB) and one vector group's Y slice
+// (~12 MB per 8 vectors) stay in L2 while a chunk is walked)
 
 template <typename T, int KPV, int NW>
 __global__ void __launch_bounds__(NW * 32)

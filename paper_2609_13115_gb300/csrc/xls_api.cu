@@ -113,9 +113,9 @@ struct xls_grid_s {
   void* scr_a = nullptr;    // set-up scratch (counts, row cursors, scan partial sums), reserved
   void* scr_b = nullptr;
   void* scr_c = nullptr;
-  int proj_vec = 8;         // vectors per CTA of the projection (8, 16 or 32; -8, -16: CTAs of 4 warps; xls_autotune)
+  int proj_vec = -8;        // vectors per CTA of the projection (8, 16 or 32; -8, -16: CTAs of 4 warps; xls_autotune)
   int back_var = 1;         // back-projection variant: 1 (1 point x 8 vectors per CTA), 2 (2 x 8), 16 (1 x 16)
-  int proj_chunk = 512;     // slots per chunk of the projection's CTA order (256, 512, 1024)
+  int proj_chunk = 256;     // slots per chunk of the projection's CTA order (256, 512, 1024)
   // concurrent halves (XLS_CONCURRENT=1): the subdomains split in two views whose passes run on
   // two streams, half 1's filter beside half 0's projection, eigensolve and rotation
   struct View {
