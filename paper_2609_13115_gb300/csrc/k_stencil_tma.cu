@@ -12,6 +12,7 @@
 #include <cuda.h>
 #include <cudaTypedefs.h>
 
+#include <cstdlib>
 #include <cstring>
 
 #include "xls_internal.h"
@@ -390,14 +391,21 @@ static PFN_cuTensorMapEncodeTiled_v12000 get_encode() {
   return fn;
 }
 
+// rows per tile: the largest candidate with at most 288 consumer threads (x-points / 4 per row)
+// that, along a periodic y axis, divides n_y (the wrapped halo boxes then start exactly at the
+// tile edges); XLS_STENCIL_TY (24, 16, 12, 8 or 6) asks for a smaller eligible candidate
+static bool ty_ok(const SubDev& S, int ty) {
+  return (S.n[0] / 4) * ty <= kMaxThreads - 32 && (!S.periodic[1] || S.n[1] % ty == 0);
+}
 int tma_tile_rows(const SubDev& S) {
-  // rows per tile: the largest candidate with at most 288 consumer threads (x-points / 4 per
-  // row) that, along a periodic y axis, divides n_y (the wrapped halo boxes then start exactly
-  // at the tile edges)
-  const int nq = S.n[0] / 4;
+  static const int want = std::getenv("XLS_STENCIL_TY") ? std::atoi(std::getenv("XLS_STENCIL_TY")) : 0;
+  int first = 0;
   for (int ty : {24, 16, 12, 8, 6})
-    if (nq * ty <= kMaxThreads - 32 && (!S.periodic[1] || S.n[1] % ty == 0)) return ty;
-  return 0;
+    if (ty_ok(S, ty)) {
+      if (!first) first = ty;
+      if (ty == want) return ty;
+    }
+  return first;
 }
 
 // Shared-memory wavefronts of one plane's y-neighbour loads (16-byte loads of consecutive rows
@@ -435,13 +443,11 @@ static long long smem_wavefronts(int W, int nq, int TY) {
 // the halo are out of range for the TMA box and cost no memory traffic).
 int tma_row_width(const SubDev& S) {
   const int nq = S.n[0] / 4;
-  int ty = 0;
-  for (int t : {24, 16, 12, 8, 6})
-    if (nq * t <= kMaxThreads - 32 && (!S.periodic[1] || S.n[1] % t == 0)) {
-      ty = t;
-      break;
-    }
+  const int ty = tma_tile_rows(S);
   const int w0 = ((S.n[0] + 2 * kHaloX + 15) / 16) * 16;
+  // XLS_STENCIL_W asks for one of the candidate pitches (w0, w0 + 16, w0 + 32)
+  static const int want_w = std::getenv("XLS_STENCIL_W") ? std::atoi(std::getenv("XLS_STENCIL_W")) : 0;
+  if (want_w >= w0 && want_w <= w0 + 32 && want_w <= 256 && (want_w - w0) % 16 == 0) return want_w;
   int best = w0;
   long long best_w = -1;
   for (int W = w0; W <= w0 + 32 && W <= 256; W += 16) {
