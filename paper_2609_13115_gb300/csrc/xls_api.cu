@@ -205,7 +205,7 @@ struct xls_grid_s {
   double *lz_v = nullptr, *lz_vp = nullptr, *lz_f = nullptr, *lz_Hv = nullptr, *lz_a = nullptr, *lz_b = nullptr;
   bool ham_set = false, orb_set = false, have_ritz = false;
   size_t bytes = 0, budget = 0;
-  std::vector<void*> allocs;
+  std::vector<std::pair<void*, size_t>> allocs;   // device arrays of the grid and their sizes
   cudaEvent_t ev[6];
   double stage_ms[4] = {0, 0, 0, 0};
   int last_launches = 0;
@@ -256,16 +256,18 @@ struct xls_grid_s {
     void* q = nullptr;
     cudaError_t e = cudaMalloc(&q, bytes_);
     if (e != cudaSuccess) return fail(XLS_ENOMEM, std::string("cudaMalloc: ") + cudaGetErrorString(e));
-    allocs.push_back(q);
+    allocs.push_back({q, bytes_});
     bytes += bytes_;
     *p = (P_*)q;
     return XLS_OK;
   }
+  // frees an array of the grid and returns its bytes to the budget
   template <typename P_>
   void release(P_** p) {
     if (!*p) return;
     for (size_t i = 0; i < allocs.size(); ++i)
-      if (allocs[i] == (void*)*p) {
+      if (allocs[i].first == (void*)*p) {
+        bytes -= allocs[i].second;
         allocs.erase(allocs.begin() + i);
         break;
       }
@@ -1922,7 +1924,7 @@ xls_status xls_grid_destroy(xls_grid g) {
   if (!g) return XLS_OK;
   if (g->st) cudaStreamSynchronize(g->st);
   else cudaDeviceSynchronize();
-  for (void* p : g->allocs) cudaFree(p);
+  for (const auto& a : g->allocs) cudaFree(a.first);
   for (int i = 0; i < 6; ++i)
     if (g->ev[i]) cudaEventDestroy(g->ev[i]);
   for (auto& e : g->pev) cudaEventDestroy(e);
