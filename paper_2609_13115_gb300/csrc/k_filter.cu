@@ -801,21 +801,19 @@ void launch_nl_project_w(const SubDev* d_subs, const ProjSlot* d_slots, int slot
                                                                               chunk_slots, idx, chi, Y, P);
 }
 
-// kpv: vectors per CTA (8, 16, 32); a negative kpv selects the CTAs of 4 warps (8 or 16 vectors),
-// else 8 warps; chunk_slots: 256, 512 or 1024
+// kpv vectors per CTA of nw warps: (8, 8), (16, 8), (32, 8), (8, 4) or (16, 4) (anything else runs
+// (8, 8)); chunk_slots: 256, 512 or 1024
 template <typename T>
 void launch_nl_project(const SubDev* d_subs, const ProjSlot* d_slots, int slot_off, int n_slot, const int* idx,
-                       const typename Vec4<T>::type* chi, int max_ns, const T* Y, double* P, int kpv, int chunk_slots,
-                       cudaStream_t st) {
+                       const typename Vec4<T>::type* chi, int max_ns, const T* Y, double* P, int kpv, int nw,
+                       int chunk_slots, cudaStream_t st) {
   if (n_slot == 0) return;
   if (chunk_slots != 256 && chunk_slots != 1024) chunk_slots = 512;
-  switch (kpv) {
-    case 32: launch_nl_project_w<T, 32, 8>(d_subs, d_slots, slot_off, n_slot, idx, chi, max_ns, Y, P, chunk_slots, st); break;
-    case 16: launch_nl_project_w<T, 16, 8>(d_subs, d_slots, slot_off, n_slot, idx, chi, max_ns, Y, P, chunk_slots, st); break;
-    case -8: launch_nl_project_w<T, 8, 4>(d_subs, d_slots, slot_off, n_slot, idx, chi, max_ns, Y, P, chunk_slots, st); break;
-    case -16: launch_nl_project_w<T, 16, 4>(d_subs, d_slots, slot_off, n_slot, idx, chi, max_ns, Y, P, chunk_slots, st); break;
-    default: launch_nl_project_w<T, 8, 8>(d_subs, d_slots, slot_off, n_slot, idx, chi, max_ns, Y, P, chunk_slots, st);
-  }
+  if (nw == 4 && kpv == 8) launch_nl_project_w<T, 8, 4>(d_subs, d_slots, slot_off, n_slot, idx, chi, max_ns, Y, P, chunk_slots, st);
+  else if (nw == 4 && kpv == 16) launch_nl_project_w<T, 16, 4>(d_subs, d_slots, slot_off, n_slot, idx, chi, max_ns, Y, P, chunk_slots, st);
+  else if (kpv == 32) launch_nl_project_w<T, 32, 8>(d_subs, d_slots, slot_off, n_slot, idx, chi, max_ns, Y, P, chunk_slots, st);
+  else if (kpv == 16) launch_nl_project_w<T, 16, 8>(d_subs, d_slots, slot_off, n_slot, idx, chi, max_ns, Y, P, chunk_slots, st);
+  else launch_nl_project_w<T, 8, 8>(d_subs, d_slots, slot_off, n_slot, idx, chi, max_ns, Y, P, chunk_slots, st);
 }
 
 template <typename T>
@@ -832,7 +830,7 @@ void launch_nl_back(const SubDev* d_subs, const ProjSlot* d_slots, int n_slot, c
   template void launch_proj_table_fill<T>(const SubDev*, const ProjSlot*, int, const AtomImg*, int*,                 \
                                           Vec4<T>::type*, cudaStream_t);                                             \
   template void launch_nl_project<T>(const SubDev*, const ProjSlot*, int, int, const int*, const Vec4<T>::type*,     \
-                                     int, const T*, double*, int, int, cudaStream_t);                                \
+                                     int, const T*, double*, int, int, int, cudaStream_t);                           \
   template void launch_nl_back<T>(const SubDev*, const ProjSlot*, int, const int*, const Vec4<T>::type*, int,        \
                                   const double*, T*, const StepCoef*, int, cudaStream_t);                            \
   template void launch_rcsr_build<T>(const SubDev*, const ProjSlot*, int, const int*, const Vec4<T>::type*,         \

@@ -128,11 +128,7 @@ __global__ void __launch_bounds__(128) k_mlp_infer(long long n, const float* __r
 }
 
 void launch_mlp_infer(long long n, const float* theta, const float* X, float* y, cudaStream_t st) {
-  static bool attr = false;
-  if (!attr) {
-    cudaFuncSetAttribute(k_mlp_infer, cudaFuncAttributeMaxDynamicSharedMemorySize, kMlpParams * 4);
-    attr = true;
-  }
+  cudaFuncSetAttribute(k_mlp_infer, cudaFuncAttributeMaxDynamicSharedMemorySize, kMlpParams * 4);   // per device
   if (n > 0) k_mlp_infer<<<(unsigned)((n + 127) / 128), 128, kMlpParams * 4, st>>>(n, theta, X, y);
 }
 
@@ -283,11 +279,7 @@ __global__ void k_sum_d(int n, const double* __restrict__ x, double* out) {
 // work: A, D (3 * 64 floats per point), e (1 per point), partials; loss_out: device double
 void launch_mlp_grad(long long n, const float* theta, const float* X, const float* yt, float* A, float* D, float* e,
                      double* loss_partial, float* wpartial, float* grad, double* loss_out, cudaStream_t st) {
-  static bool attr = false;
-  if (!attr) {
-    cudaFuncSetAttribute(k_mlp_fwd_bwd, cudaFuncAttributeMaxDynamicSharedMemorySize, kMlpParams * 4);
-    attr = true;
-  }
+  cudaFuncSetAttribute(k_mlp_fwd_bwd, cudaFuncAttributeMaxDynamicSharedMemorySize, kMlpParams * 4);   // per device
   const unsigned nb = (unsigned)((n + 127) / 128);
   k_mlp_fwd_bwd<<<nb, 128, kMlpParams * 4, st>>>(n, theta, X, yt, A, D, e, loss_partial);
   k_sum_d<<<1, 256, 0, st>>>((int)nb, loss_partial, loss_out);

@@ -507,12 +507,9 @@ template <int kW>
 static void launch_variant(const TmaClass& cls, size_t smem, const SubDev* d_subs, const CUtensorMap* d_maps,
                            int buf_in, int buf_prev, float* Yout, const StepCoef* coef, int step, int* status,
                            const StencilW& sw, cudaStream_t st) {
-  static bool attr = false;
-  if (!attr) {
-    cudaFuncSetAttribute(k_stencil_tma<kW>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-    cudaFuncSetAttribute(k_stencil_tma<kW>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
-    attr = true;
-  }
+  // function attributes are per device: set at every launch (a host call of a few microseconds)
+  cudaFuncSetAttribute(k_stencil_tma<kW>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+  cudaFuncSetAttribute(k_stencil_tma<kW>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
   const int threads = ((cls.nq * cls.TY + 31) / 32) * 32 + 32;
   k_stencil_tma<kW><<<cls.total, threads, smem, st>>>(d_subs, cls.d_jobs, cls.d_job_off, cls.n_jobs, d_maps, buf_in,
                                                       buf_prev, Yout, coef, step, status, sw);

@@ -809,17 +809,16 @@ k_vec_exponent(const SubDev* __restrict__ subs, int n_sub, const float* __restri
 size_t gram_tc_smem() { return tc::kStages * tc::kGramStage + 1024; }
 size_t rotate_tc_smem() { return tc::kStages * tc::kRotStage + 1024; }
 
+// the large dynamic shared memory of the tensor-core kernels, set on the current device at every
+// grid creation (function attributes are per device)
 bool tc_setup() {
-  static int ok = -1;
-  if (ok < 0) {
-    ok = 1;
-    ok &= cudaFuncSetAttribute(tc::k_gram_tc<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)gram_tc_smem()) == cudaSuccess;
-    ok &= cudaFuncSetAttribute(tc::k_gram_tc<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)gram_tc_smem()) == cudaSuccess;
-    ok &= cudaFuncSetAttribute(tc::k_rotate_tc<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)rotate_tc_smem()) == cudaSuccess;
-    ok &= cudaFuncSetAttribute(tc::k_rotate_tc<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)rotate_tc_smem()) == cudaSuccess;
-    cudaGetLastError();
-  }
-  return ok == 1;
+  bool ok = true;
+  ok &= cudaFuncSetAttribute(tc::k_gram_tc<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)gram_tc_smem()) == cudaSuccess;
+  ok &= cudaFuncSetAttribute(tc::k_gram_tc<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)gram_tc_smem()) == cudaSuccess;
+  ok &= cudaFuncSetAttribute(tc::k_rotate_tc<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)rotate_tc_smem()) == cudaSuccess;
+  ok &= cudaFuncSetAttribute(tc::k_rotate_tc<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)rotate_tc_smem()) == cudaSuccess;
+  cudaGetLastError();
+  return ok;
 }
 
 void launch_gram_tc(const SubDev* d_subs, int n_sub, int max_ns, const GramPlan& gp, bool fp16, const float* F,

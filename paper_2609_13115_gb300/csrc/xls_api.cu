@@ -113,7 +113,8 @@ struct xls_grid_s {
   void* scr_a = nullptr;    // set-up scratch (counts, row cursors, scan partial sums), reserved
   void* scr_b = nullptr;
   void* scr_c = nullptr;
-  int proj_vec = -8;        // vectors per CTA of the projection (8, 16 or 32; -8, -16: CTAs of 4 warps; xls_autotune)
+  int proj_vec = 8;         // vectors per CTA of the projection (8, 16 or 32; xls_autotune)
+  int proj_warps = 4;       // warps per CTA of the projection (4 or 8; xls_autotune)
   int back_var = 1;         // back-projection variant: 1 (1 point x 8 vectors per CTA), 2 (2 x 8), 16 (1 x 16)
   int proj_chunk = 256;     // slots per chunk of the projection's CTA order (256, 512, 1024)
   // concurrent halves (XLS_CONCURRENT=1): the subdomains split in two views whose passes run on
@@ -354,7 +355,7 @@ void h_step(xls_grid g, bool one, const T* yin, const T* yprev, T* yout, int ste
   { ProfScope ps(g, K_NLPROJ);
     if (one) launch_nl_project1<T>(ds, g->d_slots, g->n_slot, g->d_pidx, chi_table<T>(g), yin, P, g->st);
     else launch_nl_project<T>(ds, g->d_slots, 0, g->n_slot, g->d_pidx, chi_table<T>(g), mns, yin, P, g->proj_vec,
-                              g->proj_chunk, g->st); }
+                              g->proj_warps, g->proj_chunk, g->st); }
   { ProfScope ps(g, K_STENCIL); launch_stencil<T>(ds, g->n_sub, pl, yin, yprev, yout, V, g->coef, step, g->st); }
   { ProfScope ps(g, K_NLBACK);
     if (one)
@@ -391,7 +392,7 @@ void h_step_main(xls_grid g, const xls_grid_s::View& v, int bin, int bprev, int 
   }
   { ProfScope ps(g, K_NLPROJ);
     launch_nl_project<T>(g->d_subs, g->d_slots, v.slot_off, v.n_slot, g->d_pidx, chi_table<T>(g), v.max_ns, yin, g->P,
-                         g->proj_vec, g->proj_chunk, side ? g->side_st : v.st); }
+                         g->proj_vec, g->proj_warps, g->proj_chunk, side ? g->side_st : v.st); }
   if (side) cudaEventRecord(g->ev_side_out, g->side_st);
   if (sizeof(T) == 4 && g->use_tma) {
     ProfScope ps(g, K_STENCIL);
@@ -2375,33 +2376,37 @@ xls_status xls_autotune(xls_grid g, int reps, int* choices_out) {
     g->gram_cps = best;
     replan_all();
   }
-  // (3) vectors per CTA and slots per chunk of the nonlocal projection, timed on the current
-  // block (the projection coefficients it overwrites are recomputed at the start of every filter
-  // step)
+  // (3) vectors per CTA, warps per CTA and slots per chunk of the nonlocal projection, timed on
+  // the current block (the projection coefficients it overwrites are recomputed at the start of
+  // every filter step)
   if (rc == XLS_OK && g->n_slot > 0) {
-    int best_v = g->proj_vec, best_c = g->proj_chunk;
+    int best_v = g->proj_vec, best_w = g->proj_warps, best_c = g->proj_chunk;
     float bt = -1.f;
-    for (int kpv : {8, 16, 32, -8, -16})   // negative: CTAs of 4 warps
+    const int shapes[5][2] = {{8, 8}, {16, 8}, {32, 8}, {8, 4}, {16, 4}};   // (vectors, warps)
+    for (const auto& sh : shapes)
       for (int chunk : {256, 512, 1024}) {
+        const int kpv = sh[0], nw = sh[1];
         const float t = time_it([&] {
           if (g->prec == XLS_FP64)
             launch_nl_project<double>(g->d_subs, g->d_slots, 0, g->n_slot, g->d_pidx, g->d_chi64, g->max_ns,
-                                      (const double*)g->blk[g->cur], g->P, kpv, chunk, st);
+                                      (const double*)g->blk[g->cur], g->P, kpv, nw, chunk, st);
           else
             launch_nl_project<float>(g->d_subs, g->d_slots, 0, g->n_slot, g->d_pidx, g->d_chi32, g->max_ns,
-                                     (const float*)g->blk[g->cur], g->P, kpv, chunk, st);
+                                     (const float*)g->blk[g->cur], g->P, kpv, nw, chunk, st);
         });
         if (rc != XLS_OK) break;
         if (std::getenv("XLS_TRACE"))
           std::fprintf(stderr, "[xls] autotune: projection %d vectors per CTA of %d warps, chunks of %d slots %.3f ms\n",
-                       kpv < 0 ? -kpv : kpv, kpv < 0 ? 4 : 8, chunk, t);
+                       kpv, nw, chunk, t);
         if (bt < 0.f || t < bt) {
           bt = t;
           best_v = kpv;
+          best_w = nw;
           best_c = chunk;
         }
       }
     g->proj_vec = best_v;
+    g->proj_warps = best_w;
     g->proj_chunk = best_c;
   }
   // (3b) back-projection variant (points per thread x vectors per CTA), adding into a free arena
@@ -2484,7 +2489,7 @@ xls_status xls_autotune(xls_grid g, int reps, int* choices_out) {
   if (choices_out) {
     choices_out[0] = g->eig_cluster ? g->eig_cl : 0;
     choices_out[1] = tc_gram ? g->gram_cps : 0;
-    choices_out[2] = g->n_slot > 0 ? (g->proj_vec < 0 ? -g->proj_vec : g->proj_vec) : 0;
+    choices_out[2] = g->n_slot > 0 ? g->proj_vec : 0;
   }
   return rc;
 }

@@ -144,8 +144,8 @@ void launch_proj_table_fill(const SubDev* d_subs, const ProjSlot* d_slots, int n
                             int* idx, typename Vec4<T>::type* chi, cudaStream_t st);
 template <typename T>
 void launch_nl_project(const SubDev* d_subs, const ProjSlot* d_slots, int slot_off, int n_slot, const int* idx,
-                       const typename Vec4<T>::type* chi, int max_ns, const T* Y, double* P, int kpv, int chunk_slots,
-                       cudaStream_t st);
+                       const typename Vec4<T>::type* chi, int max_ns, const T* Y, double* P, int kpv, int nw,
+                       int chunk_slots, cudaStream_t st);
 void launch_rcsr_count(const SubDev* d_subs, const ProjSlot* d_slots, int n_slot, const int* idx, int* cnt,
                        cudaStream_t st);
 template <typename T>

@@ -29,8 +29,11 @@ def relerr(a, b):
 def check_generalised_eigenvectors(Y, lam, Ms, Hs):
     """Y^T M_s Y = I and Y^T H_s Y = Lambda.  LAPACK's solver on the same matrices reaches a few
     units of rounding; the library's inverse iteration orthogonalises only inside clusters of close
-    eigenvalues (|d lambda| < 1e-4 |T|), and the vectors of neighbouring clusters meet to about
-    1e-9: the bar is 1e-8 (a wrong or duplicated vector is off by O(1))."""
+    eigenvalues (|d lambda| < 1e-4 |T|) and accepts a cluster whose residuals are below 1e-9 |T|, so
+    two vectors of neighbouring clusters may overlap by up to residual / gap = 1e-9 / 1e-4 = 1e-5
+    (typically 1e-10 to 1e-9; 1.9e-7 seen once at 272 states, where the tensor-core Gram's
+    unordered FP32 reductions had moved a gap close to the cluster threshold).  The bar is that
+    bound, 1e-5: a wrong or duplicated vector is off by O(1)."""
     ns = len(lam)
     lam_r, Y_r = scipy.linalg.eigh(Hs, Ms)
     e_m = np.abs(Y.T @ Ms @ Y - np.eye(ns)).max()
@@ -38,8 +41,8 @@ def check_generalised_eigenvectors(Y, lam, Ms, Hs):
     e_h = np.abs(Y.T @ Hs @ Y - np.diag(lam)).max()
     e_h_ref = np.abs(Y_r.T @ Hs @ Y_r - np.diag(lam_r)).max()
     scale = max(1.0, np.abs(lam).max())
-    assert e_m < 20 * e_m_ref + 1e-8, (e_m, e_m_ref)
-    assert e_h < 20 * e_h_ref + 1e-8 * scale, (e_h, e_h_ref)
+    assert e_m < 20 * e_m_ref + 1e-5, (e_m, e_m_ref)
+    assert e_h < 20 * e_h_ref + 1e-5 * scale, (e_h, e_h_ref)
 
 
 def crystal_4cells(n_states):
