@@ -769,8 +769,8 @@ def run_reference_si13824(args):
 def run_si4014(args):
     """Every step one full pass over the 512 uneven subdomains (48^3 / 60^3 / 72^3, their own state
     counts, all sizes in the same launches of a wave): the waves run in store mode, the orbitals of
-    every subdomain between passes in a pinned FP16 host store, then the Fermi level and the
-    density (a second sweep over the stored orbitals)."""
+    every subdomain between passes in a pinned FP16 host store and their core rows on the device,
+    then the Fermi level and the density (from the core rows)."""
     import torch
     import synth
     ws, rank, local = dist_setup()
