@@ -410,8 +410,6 @@ __global__ void k_rcsr_fill(const SubDev* __restrict__ subs, const ProjSlot* __r
   }
 }
 
-// vectors per CTA of the back-projection: KV = 8 (default) or 16, each slot's coefficient row of Q
-// padded to KV + 1 entries (consecutive slots in different bank groups)
 constexpr int kLocBits = 32768;          // slots per subdomain the localisation handles (bitmap in shared memory)
 
 // One CTA per point block: mark the slots named by the block's reverse-table rows in a bitmap;
@@ -577,7 +575,7 @@ k_nl_back_csr(const SubDev* __restrict__ subs, const long long* __restrict__ row
               const StepCoef* __restrict__ coef, int step) {
   using T4 = typename Vec4<T>::type;
   extern __shared__ __align__(16) unsigned char qsm[];
-  T4* Qs = reinterpret_cast<T4*>(qsm);   // [slot][KV + 1]
+  T4* Qs = reinterpret_cast<T4*>(qsm);   // [slot][KV + 1]: rows padded so consecutive slots use other bank groups
   // the vector groups of one point block are consecutive CTAs: the block's reverse-table rows
   // are read once from DRAM and then from L2
   const SubDev& S = subs[blockIdx.z];
