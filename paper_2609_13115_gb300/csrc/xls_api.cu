@@ -1526,6 +1526,7 @@ xls_status wave_orbitals_set(xls_grid g, int sub, const double* psi, int on_devi
     float* dst = (float*)store_ptr(g, sub);
     for (size_t i = 0; i < n; ++i) dst[i] = (float)src[i];   // the rounding of the FP32 block
   }
+  if (!g->core_fresh.empty()) g->core_fresh[sub] = 0;   // the device core rows are those of the old block
   g->orb_set = true;
   g->have_ritz = false;
   return XLS_OK;
@@ -1576,6 +1577,7 @@ xls_status wave_orbitals_random(xls_grid g, uint64_t seed) {
     XLS_TRY(device_to_store(g, a, g->blk[0], g->st));
   }
   XLS_CUDA(cudaStreamSynchronize(g->st));
+  std::fill(g->core_fresh.begin(), g->core_fresh.end(), (char)0);
   g->orb_set = true;
   g->have_ritz = false;
   return XLS_OK;
@@ -1610,6 +1612,7 @@ xls_status alloc_core_store(xls_grid g) {
     return s;
   }
   XLS_CUDA(cudaMemcpy(g->d_core_subs, cs.data(), cs.size() * sizeof(SubDev), cudaMemcpyHostToDevice));
+  std::fill(g->core_fresh.begin(), g->core_fresh.end(), (char)0);
   return XLS_OK;
 }
 
@@ -2604,6 +2607,8 @@ xls_status xls_wave_store_fp16(xls_grid g, int on) {
   g->store = ns_;
   g->store16 = to16;
   cudaFreeHost(old);
+  // the stored orbitals are now rounded to the new format; the device core rows are not
+  std::fill(g->core_fresh.begin(), g->core_fresh.end(), (char)0);
   return XLS_OK;
 }
 
@@ -2623,6 +2628,7 @@ xls_status xls_wave_carry(xls_grid g, int slots) {
     g->worker = nullptr;
     g->release(&g->core_store);
     g->release(&g->d_core_subs);
+    std::fill(g->core_fresh.begin(), g->core_fresh.end(), (char)0);
     g->carry = false;
     g->orb_set = false;
     g->have_ritz = false;
@@ -2634,6 +2640,10 @@ xls_status xls_wave_carry(xls_grid g, int slots) {
   const SubDev& A = g->subs[0];
   const size_t core_pts = (size_t)A.core_n[0] * A.core_n[1] * A.core_n[2];
   const size_t store_bytes = core_pts * A.ns * g->elem * (size_t)g->n_sub;
+  // a core store of store-mode waves (if one was made) is replaced by carry mode's own
+  g->release(&g->core_store);
+  g->release(&g->d_core_subs);
+  std::fill(g->core_fresh.begin(), g->core_fresh.end(), (char)0);
   const size_t f = sub_footprint(A, g->elem);
   const size_t fixed = ((size_t)1 << 26) + g->bytes + store_bytes;
   int W = 0;
@@ -2649,22 +2659,7 @@ xls_status xls_wave_carry(xls_grid g, int slots) {
   if (g->store) cudaFreeHost(g->store);
   g->store = nullptr;
   g->store16 = false;
-  XLS_TRY(g->alloc(&g->core_store, store_bytes));
-  XLS_TRY(g->alloc(&g->d_core_subs, g->n_sub * sizeof(SubDev)));
-  // density descriptors of the compact store: subdomain a's core box is a block of its own
-  std::vector<SubDev> cs(g->subs);
-  for (int a = 0; a < g->n_sub; ++a) {
-    SubDev& S = cs[a];
-    for (int d = 0; d < 3; ++d) {
-      S.n[d] = S.core_n[d];
-      S.periodic[d] = 0;
-      S.start[d] = S.core_glo[d];
-      S.core_lo[d] = 0;
-    }
-    S.nd = (long long)core_pts;
-    S.off_blk = (long long)a * (long long)(core_pts * A.ns);
-  }
-  XLS_CUDA(cudaMemcpy(g->d_core_subs, cs.data(), cs.size() * sizeof(SubDev), cudaMemcpyHostToDevice));
+  XLS_TRY(alloc_core_store(g));   // store_bytes of core rows and their density descriptors
   g->waves.clear();
   for (int first = 0; first < g->n_sub; first += W) g->waves.push_back({first, W});
   xls_dc dc{W, g->dc_core_lo.data(), g->dc_core_n.data(), g->dc_buf.data(), g->dc_ns.data()};
