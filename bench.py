@@ -371,7 +371,7 @@ def run_si64(args):
                 "passes_compared": args.compare_passes}
 
     cpu = None
-    if rank == 0 and not args.no_cpu_baseline:
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:   # the host baseline belongs to the 1-GPU line
         cpu = run_cpu_baseline(args.sample_states)
 
     if rank == 0:
@@ -623,12 +623,13 @@ def run_si13824(args):
     kernel_share = {n: round(float(kms[i] / max(kms.sum(), 1e-9)), 4)
                     for i, n in enumerate(["stencil", "nl_project", "nl_back", "gram", "eig", "rotate", "other"])}
 
+    # the FP64 comparison and the host baseline belong to the 1-GPU line (scaling runs skip them)
     fp64 = None
-    if args.fp64_cycles > 0 and prec != xls.XLS_FP64:
+    if args.fp64_cycles > 0 and prec != xls.XLS_FP64 and ws == 1:
         fp64 = si13824_precision(args, prec)
 
     cpu = None
-    if rank == 0 and not args.no_cpu_baseline:
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         cpu = si13824_cpu_baseline(w, V, args.states, args.ncell, args.sample_vectors)
 
     if rank == 0:
