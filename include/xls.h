@@ -286,7 +286,9 @@ xls_status xls_density_at(xls_grid g, double mu, double kT, double* rho_out, int
  * xls_chefsi_batch runs the waves in turn (per wave: a partial grid, the projector tables and
  * Lanczos bounds of its subdomains, orbitals up, passes, orbitals, Ritz values, weights and
  * bounds back), xls_density finds mu from all Ritz values and weights on the device and forms
- * rho in a second sweep over the stored orbitals; xls_scf_step solves the global-grid parts as
+ * rho from the core rows of every subdomain's orbitals, gathered on the device after its wave's
+ * passes when they take at most an eighth of the HBM budget (else in a second sweep over the
+ * stored orbitals, as also after the store's format changed); xls_scf_step solves the global-grid parts as
  * on a resident grid and runs the passes in waves (each wave's partial grid restricts the new
  * V_eff and takes its own Lanczos upper bound).  xls_chefsi_stage, xls_hamiltonian_apply,
  * xls_get_subspace and profiling return XLS_EINVAL in wave mode.
@@ -328,8 +330,8 @@ xls_status xls_chefsi_wave(xls_grid g, int wave, int degree, int n_passes, const
 /* Wave mode only: keep the host store of the orbitals in FP16 (on != 0) or in the compute
  * precision (on == 0).  FP16: every vector v of a subdomain is stored as half(psi_v 2^e_v) with
  * the power of two e_v putting max |psi_v| 2^e_v into [2^13, 2^14) (the FP16 warm-start storage of
- * Sec. 5.B.3), half the FP32 store; conversions run on the device when a wave's orbitals go up or
- * come back.  Orbitals already stored are converted.  XLS_EINVAL on a resident grid, XLS_ENOMEM
+ * Sec. 5.B.3), half the FP32 store (the exponents stay in device memory); conversions run on the
+ * device when a wave's orbitals go up or come back.  Orbitals already stored are converted.  XLS_EINVAL on a resident grid, XLS_ENOMEM
  * if the new pinned store cannot be allocated. */
 xls_status xls_wave_store_fp16(xls_grid g, int on);
 
