@@ -1,4 +1,4 @@
-"""Host side of the multi-rank path on CPU ranks (gloo, world size 2): the distributed Fermi level
+"""Host side of the multi-rank path on CPU ranks (gloo, world sizes 2 and 4): the distributed Fermi level
 (histogram + Newton with allreduces, Sec. 5.A.5) against the oracle's bisection on the union of
 all states, and the assembly of core-owned grid fields."""
 import os
@@ -124,10 +124,11 @@ def _start_block(w, subs, a):
     return synth.psi0_block(w.psi_seed + a, subs[a].N, int(w.n_states[a]))
 
 
-def test_partitioned_subdomains_reproduce_single_process_run():
-    """Two ranks, each owning half of the subdomains, give the single-process oracle run's mu,
-    density and band energy (the ranks exchange only the Fermi-level sums and the core-owned
-    density field)."""
+@pytest.mark.parametrize("world", [2, 4])
+def test_partitioned_subdomains_reproduce_single_process_run(world):
+    """Two or four ranks, each owning every world-th subdomain, give the single-process oracle
+    run's mu, density and band energy (the ranks exchange only the Fermi-level sums and the
+    core-owned density field)."""
     import torch.multiprocessing as mp
     from oracle import dc, pseudo
     w = _dirichlet_cell()
@@ -136,10 +137,10 @@ def test_partitioned_subdomains_reproduce_single_process_run():
     ctx = mp.get_context("spawn")
     q = ctx.Queue()
     port = _free_port()
-    procs = [ctx.Process(target=_partition_worker, args=(r, 2, port, q)) for r in range(2)]
+    procs = [ctx.Process(target=_partition_worker, args=(r, world, port, q)) for r in range(world)]
     for p in procs:
         p.start()
-    res = [q.get(timeout=300) for _ in range(2)]   # read before joining: a full pipe blocks the put
+    res = [q.get(timeout=300) for _ in range(world)]   # read before joining: a full pipe blocks the put
     for p in procs:
         p.join(timeout=300)
     assert all(p.exitcode == 0 for p in procs)
