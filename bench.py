@@ -437,6 +437,28 @@ def _oracle_sample(args):
     return float(H.N) * n_vec * w.degree, time.perf_counter() - t0
 
 
+def _oracle_subspace_sample(args):
+    """One host process: the oracle's N_s-quadratic and -cubic steps at the full state count (the
+    Gram matrices and the rotation as in chefsi.projection / chefsi.rotate, on n_pts of a
+    subdomain's points, and chefsi.generalized_eig) on seeded blocks.  Returns (seconds of the
+    products, seconds of the eigensolve)."""
+    ns, n_pts = args
+    from oracle import chefsi
+    rng = np.random.default_rng(2609)
+    F = rng.standard_normal((ns, n_pts))
+    HF = F + 0.1 * rng.standard_normal((ns, n_pts))
+    t0 = time.perf_counter()
+    Ms = F @ F.T
+    Hs = F @ HF.T
+    Hs = 0.5 * (Hs + Hs.T)
+    t1 = time.perf_counter()
+    _, Y = chefsi.generalized_eig(Hs, Ms)
+    t2 = time.perf_counter()
+    chefsi.rotate(F, Y)
+    t3 = time.perf_counter()
+    return (t1 - t0) + (t3 - t2), t2 - t1
+
+
 class OraclePool:
     """Host processes (spawned, one BLAS thread each) that run oracle samples side by side."""
 
@@ -459,6 +481,10 @@ class OraclePool:
         out = list(self.ex.map(_oracle_sample, [(self.v_path, self.states, self.ncell, int(a), n_vec) for a in subs]))
         return sum(u for u, _ in out), time.perf_counter() - t0, [t for _, t in out]
 
+    def subspace(self, ns, n_pts):
+        """(seconds of the Gram and rotation products, seconds of the eigensolve) in one process."""
+        return self.ex.submit(_oracle_subspace_sample, (int(ns), int(n_pts))).result()
+
     def close(self):
         import shutil
         self.ex.shutdown()
@@ -470,22 +496,34 @@ def si13824_cpu_baseline(w, V, states, ncell, n_vec) -> dict:
     side by side; the rate of the latter is the line's value, and the oracle's full pass of the
     cell is extrapolated from it."""
     cores = os.cpu_count() or 1
+    ns, nd = int(w.n_states[0]), w.sub_points(0)
+    n_pts = nd // 16
     pool = OraclePool(states, ncell, V, cores)
     try:
         u1, _, t1 = pool.run([0], n_vec)
         subs = np.linspace(0, w.n_sub - 1, cores).astype(int)
         uN, wall, _ = pool.run(subs, n_vec)
+        t_prod, t_eig = pool.subspace(ns, n_pts)
     finally:
         pool.close()
     full = point_vectors(w)
     rate = uN / wall / 1e9
+    # the full pass of the cell, extrapolated: the sample's pass scaled linearly in the vectors
+    # (filter and H applications), plus the N_s^2 products at the full state count (timed on a
+    # sixteenth of a subdomain's points, scaled by 16) and the N_s^3 eigensolve, each slowed by the
+    # side-by-side factor of the sample and spread over the processes
+    slow = wall / t1[0]
+    per_sub = t1[0] * ns / n_vec + t_prod * nd / n_pts + t_eig
+    full_s = per_sub * slow * w.n_sub / cores
     return {"value": round(rate, 6), "unit": UNIT, "cores": cores, "kind": "oracle",
             "single_thread_value": round(u1 / t1[0] / 1e9, 6),
-            "sample": f"{n_vec} of {int(w.n_states[0])} start vectors of one 72^3 subdomain per process, one full "
+            "sample": f"{n_vec} of {ns} start vectors of one 72^3 subdomain per process, one full "
                       f"pass each (Lanczos bound, Rayleigh-Ritz, degree-{w.degree} filter, projection, eigensolve, "
                       f"rotation), FP64 numpy, one BLAS thread per process; {cores} subdomains side by side took "
-                      f"{wall:.1f} s, one alone {t1[0]:.1f} s",
-            "extrapolated_full_pass_s": round(full / (rate * 1e9), 1)}
+                      f"{wall:.1f} s, one alone {t1[0]:.1f} s; the Gram and rotation products at {ns} states on "
+                      f"{n_pts} points {t_prod:.1f} s, the eigensolve at {ns} states {t_eig:.1f} s (one process)",
+            "extrapolated_full_pass_s": round(full_s, 1),
+            "extrapolated_full_pass_value": round(full / full_s / 1e9, 6)}
 
 
 # ---------------------------------------------------------------------------------------------
