@@ -185,3 +185,19 @@ def test_dc_with_covering_buffer_equals_undivided():
     # vectors converge as the square root of the Ritz values: rho agrees to ~1e-6 here
     assert np.linalg.norm(r2.rho - r1.rho) < 3e-6 * np.linalg.norm(r1.rho)
     assert r2.e_band == pytest.approx(r1.e_band, abs=1e-7)
+
+
+def test_interior_weights_count_core_points_only():
+    """c_n sums psi_n^2 over the core box alone (Sec. 5.A.4): with one unit vector per grid point
+    (x fastest), the weights are 1 exactly on the points of the core box and 0 on the buffer."""
+    s = dc.Subdomain(start=np.array([-2, -1, -3]), size=np.array([9, 8, 7]), periodic=np.zeros(3, bool),
+                     core_lo=np.array([2, 1, 3]), core_n=np.array([4, 5, 2]), core_global_lo=np.zeros(3, int))
+    c = dc.interior_weights(np.eye(s.N), s)
+    want = np.zeros(s.N)
+    for k in range(7):
+        for j in range(8):
+            for i in range(9):
+                if 2 <= i < 6 and 1 <= j < 6 and 3 <= k < 5:
+                    want[i + 9 * (j + 8 * k)] = 1.0
+    np.testing.assert_array_equal(c, want)
+    assert c.sum() == 4 * 5 * 2

@@ -82,6 +82,18 @@ def test_poisson_solution_satisfies_fd_equation():
     assert abs(phi.mean()) < 1e-12
 
 
+def test_poisson_on_orthorhombic_grid():
+    """The same equation, -Delta_h phi = 4 pi (f - mean f), on a grid with three different point
+    counts and spacings (each axis's symbol paired with its own spacing), phi of zero mean."""
+    rng = np.random.default_rng(8)
+    n, h = (14, 16, 18), (0.41, 0.47, 0.53)
+    f = rng.standard_normal((n[2], n[1], n[0]))
+    phi = pseudo.solve_poisson_periodic(f, h)
+    res = -fd.laplacian(phi, h, (True, True, True)) - 4 * math.pi * (f - f.mean())
+    assert np.linalg.norm(res) < 1e-11 * np.linalg.norm(4 * math.pi * f)
+    assert abs(phi.mean()) < 1e-12
+
+
 def test_single_atom_potential_matches_erf_coulomb():
     """One well-resolved pseudocharge in a large periodic cube: phi(r) = -Z erf(r/rc)/r
     - (2 pi Z / 3 Omega) r^2 + const near the atom (neutralising background, cubic images)."""
@@ -182,3 +194,60 @@ def test_local_subdomain_operator_equals_global_one():
     assert len(H_loc.projectors) == len(H_glob.projectors)
     y0, y1 = H_glob.apply(x), H_loc.apply(x)
     assert np.abs(y1 - y0).max() < 1e-13 * np.abs(y0).max()
+
+
+def _fd_matrix_1d(n, periodic):
+    """The 1-D second-difference matrix built entry by entry: row i takes w_|p| at column i + p
+    for |p| <= 6, wrapped modulo n on a periodic axis and dropped outside [0, n) on a Dirichlet one."""
+    w = fd.fd_weights(6)
+    D = np.zeros((n, n))
+    for i in range(n):
+        for p in range(-6, 7):
+            j = i + p
+            if periodic:
+                D[i, j % n] += w[abs(p)]
+            elif 0 <= j < n:
+                D[i, j] += w[abs(p)]
+    return D
+
+
+@pytest.mark.parametrize("periodic", [(False, False, False), (True, False, False), (False, True, True)])
+def test_hamiltonian_equals_kronecker_sum_matrix(periodic):
+    """H = -1/2 (D_x/h_x^2 (+) D_y/h_y^2 (+) D_z/h_z^2) + diag(V) on a grid with x fastest, from 1-D
+    matrices assembled entry by entry: pins the boundary handling of each axis (zero outside a
+    Dirichlet box, wrap on a periodic axis), which spacing goes with which axis, the kinetic factor
+    and where each value of V sits."""
+    size, h = (7, 13, 5), (0.31, 0.42, 0.57)
+    rng = np.random.default_rng(17)
+    V = rng.standard_normal(size[::-1])
+    H = SubdomainHamiltonian(size, h, periodic, V, [])
+    Dx, Dy, Dz = (_fd_matrix_1d(size[d], periodic[d]) / h[d] ** 2 for d in range(3))
+    Ix, Iy, Iz = (np.eye(s) for s in size)
+    lap = np.kron(Iz, np.kron(Iy, Dx)) + np.kron(Iz, np.kron(Dy, Ix)) + np.kron(Dz, np.kron(Iy, Ix))
+    ref = -0.5 * lap + np.diag(V.ravel())
+    np.testing.assert_allclose(H.dense(), ref, rtol=0, atol=1e-12 * np.abs(ref).max())
+
+
+def test_projectors_are_eigenvectors_of_the_nonlocal_term():
+    """One atom on a grid point of a periodic cube: its four projectors are orthonormal (parity
+    of the grid about the atom), so V_nl chi_l = E_l chi_l for each channel and V_nl vanishes on a
+    vector supported outside the projector sphere.  The spacing (12/28 bohr) puts no grid point
+    on the cut-off sphere, where rounding could keep a point on one side of the atom and drop its
+    mirror image."""
+    L, n = 12.0, 28
+    sp = synth.SI
+    w = synth.Workload("one_atom", (L,) * 3, (n,) * 3, np.array([[6.0, 6.0, 6.0]]), np.zeros(1, int), [sp],
+                       np.zeros((1, 3), int), np.full((1, 3), n), np.zeros((1, 3), int), np.array([4]), 1, 1, 0)
+    s = dc.partition(w)[0]
+    H = dc.subdomain_operator(w, s, np.zeros((n, n, n)), pseudo.projector_norms(w))
+    (flat, chi, E), = H.projectors
+    np.testing.assert_allclose(E, [sp.E_s, sp.E_p, sp.E_p, sp.E_p])
+    for l in range(4):
+        x = np.zeros((1, H.N))
+        x[0, flat] = chi[l]
+        y = H.apply_nonlocal(x)
+        np.testing.assert_allclose(y, E[l] * x, rtol=0, atol=1e-12 * abs(E[l]) * np.abs(x).max())
+    far = np.zeros((1, H.N))
+    far[0, 0] = 1.0                                       # the corner, 10.4 bohr from the atom
+    assert 0 not in set(flat)
+    assert np.abs(H.apply_nonlocal(far)).max() == 0.0

@@ -171,6 +171,10 @@ def test_periodic_pulay_alternates_linear_and_extrapolated_steps():
     np.testing.assert_allclose(x1, x0 + 0.3 * (A @ x0 + c - x0), rtol=1e-14)
     x2 = m.step(x1, A @ x1 + c)          # k = 1: extrapolated
     assert np.linalg.norm(x2 - (x1 + 0.3 * (A @ x1 + c - x1))) > 1e-6
+    x3 = m.step(x2, A @ x2 + c)          # k = 2: linear again, with a history to extrapolate from
+    np.testing.assert_allclose(x3, x2 + 0.3 * (A @ x2 + c - x2), rtol=1e-14)
+    x4 = m.step(x3, A @ x3 + c)          # k = 3: extrapolated
+    assert np.linalg.norm(x4 - (x3 + 0.3 * (A @ x3 + c - x3))) > 1e-6
 
 
 def _si2_cell():
