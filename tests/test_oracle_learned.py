@@ -90,3 +90,26 @@ def test_learned_start_normalised_and_nonnegative():
     rho = learned.learned_start(w, theta)
     assert rho.min() >= 0.0
     assert abs(rho.sum() * np.prod(w.h) - w.n_electrons) < 1e-9
+    # an output bias that drives the correction below the atomic density in the interstitial:
+    # there the start density is clipped to zero, elsewhere it is proportional to SAD + MLP
+    theta[-1] = -0.5 * float(learned.sad_density(w).mean())
+    rho = learned.learned_start(w, theta).ravel()
+    raw = learned.sad_density(w).ravel() + learned.forward_bf16(theta, learned.descriptors(w))
+    assert (raw < 0).any() and (raw > 0).any()
+    assert np.all(rho[raw <= 0] == 0.0) and rho.min() >= 0.0
+    ratio = rho[raw > 0] / raw[raw > 0]
+    np.testing.assert_allclose(ratio, ratio[0], rtol=1e-12)
+    assert abs(rho.sum() * np.prod(w.h) - w.n_electrons) < 1e-9
+
+
+def test_bf16_inference_within_rounding_of_full_precision():
+    """BF16 operands (unit roundoff 2^-9) on the four layers put the inference within a few per
+    mille of the FP64 forward pass and not equal to it: no rounding at all, a dropped bias, a
+    transposed weight or a missing tanh moves it out of that band."""
+    rng = np.random.default_rng(12)
+    theta = synth.mlp_init(31) + 0.05 * rng.standard_normal(learned.N_PARAMS)   # biases nonzero too
+    X = rng.standard_normal((400, 32))
+    y64 = learned.forward(theta, X)
+    y16 = learned.forward_bf16(theta, X)
+    rel = np.linalg.norm(y16 - y64) / np.linalg.norm(y64)
+    assert 1e-4 < rel < 2e-2, rel

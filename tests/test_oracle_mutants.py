@@ -531,6 +531,30 @@ def m_descriptor_species_blocks_swapped(mp):
     mp.setattr(learned, "descriptors", descriptors)
 
 
+def m_inference_unrounded(mp):
+    mp.setattr(learned, "forward_bf16", lambda theta, X: learned.forward(theta, X))
+
+
+def m_inference_drops_bias(mp):
+    def forward_bf16(theta, X):
+        h = learned.bf16(X)
+        layers = learned.unpack(theta)
+        for li, (W, b) in enumerate(layers):
+            z = h @ learned.bf16(W)
+            h = learned.bf16(np.tanh(z)) if li < len(layers) - 1 else z
+        return h[:, 0]
+    mp.setattr(learned, "forward_bf16", forward_bf16)
+
+
+def m_learned_start_unclipped(mp):
+    def learned_start(w, theta, n_species=2):
+        n = np.asarray(w.n)
+        corr = learned.forward_bf16(theta, learned.descriptors(w, n_species=n_species)).reshape(n[2], n[1], n[0])
+        rho = learned.sad_density(w) + corr
+        return rho * (w.n_electrons / (rho.sum() * float(np.prod(w.h))))
+    mp.setattr(learned, "learned_start", learned_start)
+
+
 # ---- SCF energy assembly (Sec. 5.A.4): the Janak pin, three converged SCF runs each -------------
 def _scf_step(variant):
     from synth import lanczos_start
@@ -632,6 +656,9 @@ MUTANTS = [
     (m_entropy_one_sided, pc.test_fermi_function_and_entropy),
     (m_last_hidden_layer_linear, pl.test_gradient_matches_finite_differences),
     (m_descriptor_species_blocks_swapped, pl.test_descriptors_single_atom_closed_form),
+    (m_inference_unrounded, pl.test_bf16_inference_within_rounding_of_full_precision),
+    (m_inference_drops_bias, pl.test_bf16_inference_within_rounding_of_full_precision),
+    (m_learned_start_unclipped, pl.test_learned_start_normalised_and_nonnegative),
     (m_occupations_times_kT, pc.test_energies_definitions_on_two_levels),
     (m_assemble_unoccupied_density, pc.test_config0_invariants),
     pytest.param(m_energy_hartree_sign, ps.test_scf_energy_derivative_is_chemical_potential, marks=pytest.mark.slow),
