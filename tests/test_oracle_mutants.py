@@ -588,6 +588,14 @@ def _scf_step(variant):
     return step
 
 
+def m_veff_minus_vxc(mp):
+    def effective_potential(w, rho, b):
+        phi = pseudo.solve_poisson_periodic(rho + b, w.h)
+        eps, vxc = scf.lda_pz81(rho)
+        return phi - vxc, phi, eps, vxc
+    mp.setattr(scf, "effective_potential", effective_potential)
+
+
 def m_energy_hartree_sign(mp):
     mp.setattr(scf, "step", _scf_step("hartree_sign"))
 
@@ -663,6 +671,7 @@ MUTANTS = [
     (m_assemble_unoccupied_density, pc.test_config0_invariants),
     pytest.param(m_energy_hartree_sign, ps.test_scf_energy_derivative_is_chemical_potential, marks=pytest.mark.slow),
     pytest.param(m_energy_drops_vxc_rho, ps.test_scf_energy_derivative_is_chemical_potential, marks=pytest.mark.slow),
+    pytest.param(m_veff_minus_vxc, ps.test_scf_energy_derivative_is_chemical_potential, marks=pytest.mark.slow),
 ]
 
 
