@@ -53,3 +53,23 @@ def test_bad_arguments_rejected_without_gpu(lib_path):
     lib = xls.load(lib_path)
     assert lib.xls_grid_create(None, None, 0, 0, None, None) == xls.XLS_EINVAL
     assert b"null" in lib.xls_last_error()
+
+
+def test_every_entry_point_rejects_null_handles_without_gpu(lib_path):
+    """Every declared call with null pointers and zero sizes returns XLS_EINVAL, with a message in
+    xls_last_error, before it touches the device: no GPU is needed to run this.  The destroy calls
+    accept a null handle and return XLS_OK."""
+    import ctypes
+    lib = xls.load(lib_path)
+    zero = {ctypes.c_int: 0, ctypes.c_double: 0.0, ctypes.c_size_t: 0, ctypes.c_uint64: 0, ctypes.c_longlong: 0}
+    for name in declared_functions():
+        if name == "xls_last_error":
+            continue
+        f = getattr(lib, name)
+        args = [zero.get(t) for t in f.argtypes]
+        rc = f(*args)
+        if name in ("xls_grid_destroy", "xls_mlp_destroy"):
+            assert rc == xls.XLS_OK, name
+        else:
+            assert rc == xls.XLS_EINVAL, (name, rc)
+            assert lib.xls_last_error(), name
