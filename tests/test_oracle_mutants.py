@@ -555,6 +555,13 @@ def m_learned_start_unclipped(mp):
     mp.setattr(learned, "learned_start", learned_start)
 
 
+def m_local_operator_near_radius(mp):
+    # the local operator keeps the atoms within r_cut - 1 bohr of the box instead of r_cut + 1
+    import synth
+    f = original(synth, "near_atoms")
+    mp.setattr(synth, "near_atoms", lambda w, start, size, margin: f(w, start, size, margin - 2.0))
+
+
 # ---- SCF energy assembly (Sec. 5.A.4): the Janak pin, three converged SCF runs each -------------
 def _scf_step(variant):
     from synth import lanczos_start
@@ -667,6 +674,7 @@ MUTANTS = [
     (m_inference_unrounded, pl.test_bf16_inference_within_rounding_of_full_precision),
     (m_inference_drops_bias, pl.test_bf16_inference_within_rounding_of_full_precision),
     (m_learned_start_unclipped, pl.test_learned_start_normalised_and_nonnegative),
+    (m_local_operator_near_radius, po.test_local_subdomain_operator_with_random_atoms),
     (m_occupations_times_kT, pc.test_energies_definitions_on_two_levels),
     (m_assemble_unoccupied_density, pc.test_config0_invariants),
     pytest.param(m_energy_hartree_sign, ps.test_scf_energy_derivative_is_chemical_potential, marks=pytest.mark.slow),

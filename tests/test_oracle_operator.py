@@ -251,3 +251,30 @@ def test_projectors_are_eigenvectors_of_the_nonlocal_term():
     far[0, 0] = 1.0                                       # the corner, 10.4 bohr from the atom
     assert 0 not in set(flat)
     assert np.abs(H.apply_nonlocal(far)).max() == 0.0
+
+
+def test_local_subdomain_operator_with_random_atoms():
+    """Random atom positions on a 3^3-cell box (72^3 grid) cut into Dirichlet subdomains of 48^3, so
+    that some atoms sit outside a subdomain within the projector cutoff of its faces: the local
+    operator keeps exactly the atoms whose spheres meet the subdomain, and equals the operator with
+    whole-grid norms.  (On the 64-atom cell every subdomain spans the period, so every atom meets
+    every subdomain and the choice of atoms is not exercised.)"""
+    a = synth.workload(0).L[0]
+    rng = np.random.default_rng(23)
+    n_at = 60
+    pos = rng.uniform(0.0, 3 * a, size=(n_at, 3))
+    cores = np.array([[0, 0, 0], [24, 36, 12], [48, 12, 36]])
+    w = synth.Workload("random_box3", (3 * a,) * 3, (72,) * 3, pos, np.zeros(n_at, int), [synth.SI],
+                       core_lo=cores, core_n=np.full((3, 3), 24), buf=np.full((3, 3), 12),
+                       n_states=np.full(3, 4), degree=4, n_passes=1, psi_seed=3)
+    subs = dc.partition(w)
+    assert not any(s.periodic.any() for s in subs)
+    norms = pseudo.projector_norms(w)
+    V = np.zeros((72, 72, 72))
+    for k, s in enumerate(subs):
+        H_glob = dc.subdomain_operator(w, s, V, norms)
+        H_loc = dc.subdomain_operator_local(w, s, V)
+        assert 0 < len(H_loc.projectors) == len(H_glob.projectors) < n_at
+        x = synth.psi0_block(9 + k, s.N, 2)
+        y0, y1 = H_glob.apply(x), H_loc.apply(x)
+        assert np.abs(y1 - y0).max() < 1e-13 * np.abs(y0).max()
