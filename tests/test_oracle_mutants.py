@@ -562,6 +562,28 @@ def m_local_operator_near_radius(mp):
     mp.setattr(synth, "near_atoms", lambda w, start, size, margin: f(w, start, size, margin - 2.0))
 
 
+def m_partition_core_at_origin(mp):
+    f = original(dc, "partition")
+
+    def partition(w):
+        subs = f(w)
+        for sd in subs:
+            sd.core_lo = np.zeros(3, dtype=int)
+        return subs
+    mp.setattr(dc, "partition", partition)
+
+
+def m_partition_start_after_core(mp):
+    f = original(dc, "partition")
+
+    def partition(w):
+        subs = f(w)
+        for sd in subs:
+            sd.start = sd.core_global_lo + sd.core_lo
+        return subs
+    mp.setattr(dc, "partition", partition)
+
+
 # ---- SCF energy assembly (Sec. 5.A.4): the Janak pin, three converged SCF runs each -------------
 def _scf_step(variant):
     from synth import lanczos_start
@@ -675,6 +697,8 @@ MUTANTS = [
     (m_inference_drops_bias, pl.test_bf16_inference_within_rounding_of_full_precision),
     (m_learned_start_unclipped, pl.test_learned_start_normalised_and_nonnegative),
     (m_local_operator_near_radius, po.test_local_subdomain_operator_with_random_atoms),
+    (m_partition_core_at_origin, po.test_partition_mixes_periodic_and_dirichlet_axes),
+    (m_partition_start_after_core, po.test_partition_mixes_periodic_and_dirichlet_axes),
     (m_occupations_times_kT, pc.test_energies_definitions_on_two_levels),
     (m_assemble_unoccupied_density, pc.test_config0_invariants),
     pytest.param(m_energy_hartree_sign, ps.test_scf_energy_derivative_is_chemical_potential, marks=pytest.mark.slow),

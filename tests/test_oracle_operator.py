@@ -278,3 +278,30 @@ def test_local_subdomain_operator_with_random_atoms():
         x = synth.psi0_block(9 + k, s.N, 2)
         y0, y1 = H_glob.apply(x), H_loc.apply(x)
         assert np.abs(y1 - y0).max() < 1e-13 * np.abs(y0).max()
+
+
+def test_partition_mixes_periodic_and_dirichlet_axes():
+    """A 2 x 4 x 2-cell box (48 x 96 x 48 points) with 24^3 cores and 12-point buffers: along x and
+    z a subdomain spans the period (48 points, periodic, one period long), along y it is a 48-point
+    Dirichlet box starting 12 points before its core; the core sits 12 points into the subdomain
+    on every axis, and the restriction reads V at the wrapped global indices."""
+    a = synth.workload(0).L[0]
+    cores = np.array([[0, 0, 0], [24, 72, 24], [0, 48, 24]])
+    w = synth.Workload("mixed", (2 * a, 4 * a, 2 * a), (48, 96, 48), np.zeros((0, 3)), np.zeros(0, int), [synth.SI],
+                       core_lo=cores, core_n=np.full((3, 3), 24), buf=np.full((3, 3), 12),
+                       n_states=np.full(3, 4), degree=4, n_passes=1, psi_seed=3)
+    V = np.arange(96 * 48 * 48, dtype=float).reshape(48, 96, 48)      # (nz, ny, nx), distinct values
+    for s, c in zip(dc.partition(w), cores):
+        assert list(s.periodic) == [True, False, True]
+        assert list(s.size) == [48, 48, 48]
+        assert list(s.start) == [c[0] - 12, c[1] - 12, c[2] - 12]
+        assert list(s.core_lo) == [12, 12, 12] and list(s.core_global_lo) == list(c)
+        Vs = dc.restrict(V, s)
+        for (i, j, k) in [(0, 0, 0), (47, 5, 30), (12, 12, 12), (3, 47, 47)]:
+            gi, gj, gk = (s.start[0] + i) % 48, (s.start[1] + j) % 96, (s.start[2] + k) % 48
+            assert Vs[k, j, i] == V[gk, gj, gi]
+        # the core box of the subdomain is the core box on the global grid
+        loc = dc.core_local_indices(s)
+        glob = dc.core_global_indices(s, w.n)
+        flatV = V.ravel()
+        np.testing.assert_array_equal(Vs.ravel()[loc], flatV[glob])
